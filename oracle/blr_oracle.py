@@ -1,0 +1,413 @@
+"""Plain FP64 CPU oracle for band-limited PDE-LDDMM (state-equation variant) with
+Gauss-Newton-Krylov optimisation.
+
+TEST INFRASTRUCTURE ONLY.  This module is the slow, obviously-correct reference
+that the CUDA library is compared against.  Only ``tests/``,
+``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline / reference arm may
+import it.  The product path (``paper_1807_05117_gb300``) never imports it, and
+this module imports nothing from the product.
+
+What is computed (Hernandez, "Newton-Krylov optimization in PDE-constrained
+diffeomorphic registration parameterized in the space of band-limited vector
+fields", arXiv 1807.05117):
+
+* band-limited space: inclusion iota and projection pi (Section 3.1, Eq. 33);
+* regulariser / preconditioner diagonal in the band (Section 3.1, Eq. 34, with
+  Eq. 1's operator family): A(k) = (alpha*omega(k) + gamma)^(2s), K~ = 1/A;
+* energy E(v~) = 1/2 <L~v~, v~> + sigma^-2 ||m(1) - I1||^2 (Section 3.2, Eq. 35)
+  subject to the state equation d_t m + grad m . iota(v~) = 0, m(0) = I0
+  (Eq. 36, Section 2.2 Eq. 5);
+* gradient  g~ = L~v~ + pi(lambda grad m)  (Section 3.2, Eq. 38; adjoint
+  equation Eq. 8 and its final condition lambda(1) = -(2/sigma^2)(m(1)-I1),
+  Section 2.2);
+* Gauss-Newton Hessian-vector product H~dv~ = L~dv~ + pi(dlambda grad m) with
+  the Gauss-Newton drops of Section 3.4 applied to Eq. 46;
+* PCG with preconditioner K~ and the reduced-space Newton update with a step
+  length (Section 3.4, Eqs. 54-55; Section 2.4, Eqs. 31-32).
+
+The paper states the continuous equations only (optimise-then-discretise).  The
+oracle fixes one discretisation and differentiates it exactly
+(discretise-then-optimise), so that finite differences and Hessian symmetry hold
+to rounding:
+
+* time: nt stationary steps, dt = 1/nt, semi-Lagrangian first-order departure
+  point x + d(x) with d = -dt * iota(v~) (voxel units, h = 1);
+* space: trilinear interpolation with periodic wrap; the interpolation cell of
+  voxel x on axis a is x_a + floor(d_a(x)), so the cell depends on the
+  displacement only;
+* the transport step is the sparse linear map S (8 weights per row), its exact
+  transpose S^T gives the adjoint step, and D_a holds the exact partial
+  derivatives of the trilinear polynomial inside the chosen cell;
+* frequencies are centred: k_d in {-B_d/2, ..., B_d/2 - 1}; iota takes the real
+  part of the sum; pi = iota^T under <a, b> = Re sum(a * conj(b));
+* omega(k) is the symbol of the periodic 7-point Laplacian with h = 1;
+* a Newton trial point whose displacement reaches one voxel per step on some
+  axis (the CFL bound of Section 2.4) is rejected by the line search.
+
+Every function works in float64 / complex128.  Parity status: every function
+here is pinned by ``tests/test_oracle_pins.py`` (brute force, closed forms,
+adjoint identities, finite differences, dense solves).
+"""
+
+from __future__ import annotations
+
+import itertools
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.sparse as sp
+
+
+# ----------------------------------------------------------------------------
+# Problem parameters
+# ----------------------------------------------------------------------------
+
+
+@dataclass(frozen=True)
+class Params:
+    """Grid, band and model constants.
+
+    n      -- grid (N1, N2, N3); array layout [N1][N2][N3], N3 fastest
+    band   -- (B1, B2, B3), each even; centred frequencies -B/2 .. B/2-1
+    nt     -- number of time steps (dt = 1/nt)
+    alpha, gamma, s -- L = (-alpha*Laplacian + gamma)^s, regulariser L^T L
+    sigma  -- weight of the image term sigma^-2 ||m(1) - I1||^2 (Eq. 35)
+    """
+
+    n: tuple
+    band: tuple
+    nt: int = 10
+    alpha: float = 3.0
+    gamma: float = 1.0
+    s: int = 2
+    sigma: float = 1.0
+
+    @property
+    def dt(self) -> float:
+        return 1.0 / self.nt
+
+
+# ----------------------------------------------------------------------------
+# Band-limited space (Section 3.1, Eq. 33)
+# ----------------------------------------------------------------------------
+
+
+def band_frequencies(B: int) -> np.ndarray:
+    """Centred integer frequencies -B/2 .. B/2-1 of one axis of the band."""
+    return np.arange(B) - B // 2
+
+
+def dft_matrix(N: int, B: int) -> np.ndarray:
+    """E[x, j] = exp(2 pi i k_j x / N) for voxel x and band frequency k_j."""
+    x = np.arange(N)
+    k = band_frequencies(B)
+    phase = np.outer(x, k) % N  # exact integer phase, reduced mod N
+    return np.exp(2j * np.pi * phase / N)
+
+
+def expand(vt: np.ndarray, n) -> np.ndarray:
+    """iota: band coefficients (3, B1, B2, B3) complex -> real field (3, N1, N2, N3).
+
+    iota(v~)_c(x) = Re sum_k v~_c(k) exp(2 pi i sum_d k_d x_d / N_d)   (Eq. 33)
+    The exponential factorises over the axes; einsum evaluates the sum.
+    """
+    E1, E2, E3 = (dft_matrix(n[d], vt.shape[1 + d]) for d in range(3))
+    return np.einsum("cabk,xa,yb,zk->cxyz", vt, E1, E2, E3, optimize=True).real
+
+
+def project(f: np.ndarray, band) -> np.ndarray:
+    """pi: real field (3, N1, N2, N3) -> band coefficients (3, B1, B2, B3).
+
+    pi(f)_c(k) = sum_x f_c(x) exp(-2 pi i sum_d k_d x_d / N_d), which is the
+    transpose of iota under <a, b> = Re sum a conj(b) (Section 3.1).
+    """
+    E1, E2, E3 = (dft_matrix(f.shape[1 + d], band[d]).conj() for d in range(3))
+    return np.einsum("cxyz,xa,yb,zk->cabk", f, E1, E2, E3, optimize=True)
+
+
+def inner(a: np.ndarray, b: np.ndarray) -> float:
+    """Real inner product of the parameter space R^(2*3*B1*B2*B3)."""
+    return float(np.real(np.vdot(b, a)))
+
+
+# ----------------------------------------------------------------------------
+# Regulariser (Eq. 1 operator family, Section 3.1 Eq. 34)
+# ----------------------------------------------------------------------------
+
+
+def laplacian_symbol(n, band) -> np.ndarray:
+    """omega(k) = sum_d 2 (1 - cos(2 pi k_d / N_d)): eigenvalue of the periodic
+    7-point negative Laplacian (h = 1) on the Fourier mode k."""
+    parts = [2.0 * (1.0 - np.cos(2.0 * np.pi * band_frequencies(band[d]) / n[d]))
+             for d in range(3)]
+    return parts[0][:, None, None] + parts[1][None, :, None] + parts[2][None, None, :]
+
+
+def regulariser_weights(p: Params) -> np.ndarray:
+    """A(k) = (alpha omega(k) + gamma)^(2s): symbol of L^T L, L = (-alpha Lap + gamma)^s.
+    The preconditioner K~ = (L^T L)^-1 is 1/A."""
+    return (p.alpha * laplacian_symbol(p.n, p.band) + p.gamma) ** (2 * p.s)
+
+
+def regulariser_energy(vt: np.ndarray, A: np.ndarray) -> float:
+    """1/2 <L~ v~, v~>_{l2} for a stationary velocity (time integral over [0, 1])."""
+    return 0.5 * float(np.sum(A[None] * np.abs(vt) ** 2))
+
+
+# ----------------------------------------------------------------------------
+# Semi-Lagrangian transport operator (state equation, Eq. 36 / Eq. 5)
+# ----------------------------------------------------------------------------
+
+
+def displacement(vt: np.ndarray, p: Params) -> np.ndarray:
+    """Per-step displacement d = -dt * iota(v~) in voxels; departure point x + d(x)."""
+    return -p.dt * expand(vt, p.n)
+
+
+def cfl_number(d: np.ndarray) -> float:
+    """Largest per-axis displacement per step, in voxels."""
+    return float(np.max(np.abs(d))) if d.size else 0.0
+
+
+class Stencil:
+    """Trilinear interpolation at x + d(x) with periodic wrap, as sparse matrices.
+
+    S   -- (S m)(x) = trilinear value of m at x + d(x)
+    D_a -- (D_a m)(x) = partial derivative along axis a of the trilinear
+           polynomial of the cell used at x (right derivative on a node)
+    The cell on axis a is x_a + floor(d_a(x)) and the local coordinate is
+    f_a = d_a - floor(d_a); corner o in {0,1}^3 has weight
+    prod_a (f_a if o_a else 1 - f_a).
+    """
+
+    def __init__(self, d: np.ndarray):
+        shape = d.shape[1:]
+        V = int(np.prod(shape))
+        fl = np.floor(d)
+        f = d - fl
+        fl = fl.astype(np.int64)
+        grid = np.indices(shape)
+        rows = np.arange(V)
+        w = [[1.0 - f[a], f[a]] for a in range(3)]       # weight of corner bit o_a
+        dw = [-1.0, 1.0]                                   # its derivative in p_a
+        cols, vals, dvals = [], [], [[], [], []]
+        for o in itertools.product((0, 1), repeat=3):
+            idx = [(grid[a] + fl[a] + o[a]) % shape[a] for a in range(3)]
+            cols.append(np.ravel_multi_index(idx, shape).ravel())
+            vals.append((w[0][o[0]] * w[1][o[1]] * w[2][o[2]]).ravel())
+            dvals[0].append((dw[o[0]] * w[1][o[1]] * w[2][o[2]]).ravel())
+            dvals[1].append((w[0][o[0]] * dw[o[1]] * w[2][o[2]]).ravel())
+            dvals[2].append((w[0][o[0]] * w[1][o[1]] * dw[o[2]]).ravel())
+        r = np.tile(rows, 8)
+        c = np.concatenate(cols)
+        self.shape = shape
+        self.S = sp.csr_matrix((np.concatenate(vals), (r, c)), shape=(V, V))
+        self.D = [sp.csr_matrix((np.concatenate(dv), (r, c)), shape=(V, V))
+                  for dv in dvals]
+
+    def apply(self, m: np.ndarray) -> np.ndarray:
+        return (self.S @ m.ravel()).reshape(self.shape)
+
+    def apply_transpose(self, lam: np.ndarray) -> np.ndarray:
+        return (self.S.T @ lam.ravel()).reshape(self.shape)
+
+    def gradient(self, m: np.ndarray) -> np.ndarray:
+        """(3, N1, N2, N3): exact gradient of the interpolant of m at x + d(x)."""
+        mf = m.ravel()
+        return np.stack([(Da @ mf).reshape(self.shape) for Da in self.D])
+
+
+def state(I0: np.ndarray, st: Stencil, nt: int) -> list:
+    """m^0 = I0, m^{n+1} = S m^n, n = 0 .. nt-1.  Returns [m^0, ..., m^nt]."""
+    m = [np.asarray(I0, dtype=np.float64)]
+    for _ in range(nt):
+        m.append(st.apply(m[-1]))
+    return m
+
+
+def data_energy(m1: np.ndarray, I1: np.ndarray, p: Params) -> float:
+    """sigma^-2 ||m(1) - I1||^2 with the voxel sum as the L2 integral (h = 1)."""
+    r = m1 - I1
+    return float(np.sum(r * r)) / p.sigma**2
+
+
+# ----------------------------------------------------------------------------
+# Energy, gradient and Gauss-Newton Hessian-vector product (Eqs. 35-38, 44-46)
+# ----------------------------------------------------------------------------
+
+
+class Point:
+    """Everything the gradient and the Hessian need at one velocity v~."""
+
+    def __init__(self, vt: np.ndarray, I0: np.ndarray, I1: np.ndarray, p: Params):
+        self.p = p
+        self.vt = np.asarray(vt, dtype=np.complex128)
+        self.I1 = np.asarray(I1, dtype=np.float64)
+        self.A = regulariser_weights(p)
+        self.d = displacement(self.vt, p)
+        self.cfl = cfl_number(self.d)
+        self.stencil = Stencil(self.d)
+        self.m = state(I0, self.stencil, p.nt)
+        self.energy_reg = regulariser_energy(self.vt, self.A)
+        self.energy_data = data_energy(self.m[-1], self.I1, p)
+        self.energy = self.energy_reg + self.energy_data
+        self._G = None
+
+    def grad_m(self, n: int) -> np.ndarray:
+        """G^n = gradient of the interpolant of m^n at the departure points."""
+        if self._G is None:
+            self._G = [None] * self.p.nt
+        if self._G[n] is None:
+            self._G[n] = self.stencil.gradient(self.m[n])
+        return self._G[n]
+
+    def adjoint_chain(self, lam_final: np.ndarray):
+        """lambda^n = S^T lambda^{n+1} (discrete adjoint equation, Eq. 8) and the
+        body force b = dt sum_{n<nt} lambda^{n+1} G^n (the lambda grad m of Eq. 38).
+        Returns (b, lambda^0)."""
+        p = self.p
+        lam = lam_final
+        b = np.zeros((3,) + tuple(p.n))
+        for n in range(p.nt - 1, -1, -1):
+            b += p.dt * lam[None] * self.grad_m(n)
+            lam = self.stencil.apply_transpose(lam)
+        return b, lam
+
+    def gradient(self):
+        """g~ = A v~ + pi(b), final condition lambda^nt = -(2/sigma^2)(m^nt - I1).
+        Returns (g~, b, lambda^0)."""
+        lam_final = -(2.0 / self.p.sigma**2) * (self.m[-1] - self.I1)
+        b, lam0 = self.adjoint_chain(lam_final)
+        g = self.A[None] * self.vt + project(b, self.p.band)
+        return g, b, lam0
+
+    def incremental_state(self, dvt: np.ndarray) -> np.ndarray:
+        """dm^0 = 0, dm^{n+1} = S dm^n - dt G^n . iota(dv~)  (linearised Eq. 36).
+        Returns dm^nt."""
+        p = self.p
+        dv = expand(dvt, p.n)
+        dm = np.zeros(tuple(p.n))
+        for n in range(p.nt):
+            dm = self.stencil.apply(dm) - p.dt * np.sum(self.grad_m(n) * dv, axis=0)
+        return dm
+
+    def gn_hessvec(self, dvt: np.ndarray):
+        """H~ dv~ = A dv~ + pi(db): incremental adjoint with dlambda^nt =
+        -(2/sigma^2) dm^nt, dlambda^n = S^T dlambda^{n+1},
+        db = dt sum dlambda^{n+1} G^n.  The Gauss-Newton drops of Section 3.4 remove
+        the pi(lambda grad dm) term and the dJ term (all second derivatives of
+        the transport).  Returns (H dv~, dm^nt, db)."""
+        dvt = np.asarray(dvt, dtype=np.complex128)
+        dm1 = self.incremental_state(dvt)
+        dlam_final = -(2.0 / self.p.sigma**2) * dm1
+        db, _ = self.adjoint_chain(dlam_final)
+        h = self.A[None] * dvt + project(db, self.p.band)
+        return h, dm1, db
+
+
+def energy(vt, I0, I1, p: Params) -> float:
+    return Point(vt, I0, I1, p).energy
+
+
+# ----------------------------------------------------------------------------
+# Krylov solver and reduced-space Newton (Section 3.4, Eqs. 54-55)
+# ----------------------------------------------------------------------------
+
+
+class NegativeCurvature(RuntimeError):
+    pass
+
+
+def pcg(apply_H, rhs: np.ndarray, Minv: np.ndarray, eta: float, maxit: int):
+    """Preconditioned CG on H x = rhs from x = 0 with M^-1 = K~ (elementwise Minv).
+    Stops when ||r_j|| <= eta ||r_0|| or after maxit iterations.
+    Returns (x, iterations, ||r|| / ||r_0||)."""
+    x = np.zeros_like(rhs)
+    r = rhs.copy()
+    r0 = np.sqrt(inner(r, r))
+    if r0 == 0.0:
+        return x, 0, 0.0
+    z = Minv * r
+    p = z.copy()
+    rz = inner(r, z)
+    it = 0
+    rel = 1.0
+    while it < maxit:
+        q = apply_H(p)
+        pq = inner(p, q)
+        if pq <= 0.0:
+            raise NegativeCurvature(f"<p, Hp> = {pq}")
+        alpha = rz / pq
+        x = x + alpha * p
+        r = r - alpha * q
+        it += 1
+        rel = np.sqrt(inner(r, r)) / r0
+        if rel <= eta:
+            break
+        z = Minv * r
+        rz_new = inner(r, z)
+        beta = rz_new / rz
+        rz = rz_new
+        p = z + beta * p
+    return x, it, rel
+
+
+def max_abs(g: np.ndarray) -> float:
+    """Infinity norm of the real parameter vector (real and imaginary parts)."""
+    return float(max(np.max(np.abs(g.real)), np.max(np.abs(g.imag))))
+
+
+@dataclass
+class NewtonReport:
+    iterations: int
+    pcg_iterations: list
+    energies: list
+    steps: list
+    grad_inf_rel: float
+    vt: np.ndarray
+
+
+def newton(vt0, I0, I1, p: Params, max_newton=5, max_pcg=10, gtol=1e-2,
+           forcing=None, c1=1e-4, max_halvings=10) -> NewtonReport:
+    """Gauss-Newton-Krylov: p from PCG on H p = -g (preconditioner K~), then
+    v~ <- v~ + eps p with Armijo backtracking from eps = 1 (halving).
+
+    The paper writes the update as v - eps dv with H dv = -g (Eqs. 54-55); read
+    literally that is an ascent step, so the descent direction p = dv is added.
+    forcing=None uses eta = min(0.5, sqrt(||g|| / ||g0||)); a number fixes eta.
+    Stops when ||g||_inf / ||g0||_inf < gtol, after max_newton updates, or when
+    the line search fails."""
+    pt = Point(vt0, I0, I1, p)
+    g, _, _ = pt.gradient()
+    g0_inf = max_abs(g)
+    g0_2 = np.sqrt(inner(g, g))
+    energies = [pt.energy]
+    pcg_its, steps = [], []
+    rel = 1.0
+    for _ in range(max_newton):
+        rel = max_abs(g) / g0_inf if g0_inf > 0 else 0.0
+        if rel < gtol:
+            break
+        eta = (min(0.5, np.sqrt(np.sqrt(inner(g, g)) / g0_2)) if forcing is None
+               else forcing)
+        cur = pt
+        step, its, _ = pcg(lambda v: cur.gn_hessvec(v)[0], -g, 1.0 / cur.A[None],
+                           eta, max_pcg)
+        pcg_its.append(its)
+        slope = inner(g, step)
+        eps = 1.0
+        accepted = None
+        for _ in range(max_halvings + 1):
+            trial = Point(pt.vt + eps * step, I0, I1, p)
+            if trial.cfl < 1.0 and trial.energy <= pt.energy + c1 * eps * slope:
+                accepted = trial
+                break
+            eps *= 0.5
+        if accepted is None:
+            break
+        steps.append(eps)
+        pt = accepted
+        g, _, _ = pt.gradient()
+        energies.append(pt.energy)
+    rel = max_abs(g) / g0_inf if g0_inf > 0 else 0.0
+    return NewtonReport(len(steps), pcg_its, energies, steps, rel, pt.vt)

@@ -1,0 +1,448 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself:
+brute-force sums, closed forms, library FFTs, exact shifts, finite differences,
+dense linear algebra.  Each test names the plausible mistake it would catch.
+
+These run on the CPU (not marked gpu)."""
+
+import cmath
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import blr_oracle as O
+from paper_1807_05117_gb300 import synth
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+# ----------------------------------------------------------------------------
+# iota / pi (Section 3.1, Eq. 33)
+# ----------------------------------------------------------------------------
+
+N_SMALL = (6, 5, 4)      # non-cubic so a transposed axis shows up
+B_SMALL = (4, 2, 4)
+
+
+def test_expand_brute_force_triple_sum():
+    """iota against the definition summed term by term with cmath.exp
+    (catches a wrong sign in the exponent, a transposed axis, an off-centre band)."""
+    vt = synth.random_direction(B_SMALL, 1) * 10
+    got = O.expand(vt, N_SMALL)
+    ks = [np.arange(B) - B // 2 for B in B_SMALL]
+    for c in range(3):
+        for x in itertools.product(*[range(N) for N in N_SMALL]):
+            acc = 0j
+            for j in itertools.product(*[range(B) for B in B_SMALL]):
+                ph = sum(ks[d][j[d]] * x[d] / N_SMALL[d] for d in range(3))
+                acc += vt[(c,) + j] * cmath.exp(2j * math.pi * ph)
+            assert abs(got[(c,) + x] - acc.real) < 1e-12
+
+
+def test_expand_single_mode_is_cosine():
+    """A unit coefficient at frequency k gives cos(2 pi k.x/N); i at k gives -sin."""
+    n = (8, 6, 10)
+    band = (4, 4, 6)
+    x = np.indices(n)
+    for c, j in [(0, (0, 0, 0)), (1, (3, 1, 5)), (2, (1, 2, 0))]:
+        k = [j[d] - band[d] // 2 for d in range(3)]
+        theta = sum(2 * np.pi * k[d] * x[d] / n[d] for d in range(3))
+        for coef, want in [(1.0, np.cos(theta)), (1j, -np.sin(theta))]:
+            vt = np.zeros((3,) + band, complex)
+            vt[(c,) + j] = coef
+            v = O.expand(vt, n)
+            assert np.max(np.abs(v[c] - want)) < 1e-12
+            others = [a for a in range(3) if a != c]
+            assert np.max(np.abs(v[others])) == 0.0
+
+
+def test_expand_matches_numpy_inverse_fft():
+    """iota(v) = Re(V * ifftn(v embedded at k mod N)) -- a library routine with
+    its own sign and normalisation conventions."""
+    n = (12, 10, 8)
+    band = (6, 4, 8)
+    vt = synth.random_direction(band, 2)
+    X = np.zeros((3,) + n, complex)
+    ks = [np.arange(B) - B // 2 for B in band]
+    for j in itertools.product(*[range(B) for B in band]):
+        idx = tuple(ks[d][j[d]] % n[d] for d in range(3))
+        X[(slice(None),) + idx] = vt[(slice(None),) + j]
+    want = np.real(np.fft.ifftn(X, axes=(1, 2, 3))) * np.prod(n)
+    assert rel(O.expand(vt, n), want) < 1e-13
+
+
+def test_project_matches_numpy_fft():
+    """pi(f)(k) = fftn(f)[k mod N] (numpy's forward FFT uses exp(-2 pi i k x/N))."""
+    n = (12, 10, 8)
+    band = (6, 4, 8)
+    f = np.random.default_rng(3).normal(size=(3,) + n)
+    F = np.fft.fftn(f, axes=(1, 2, 3))
+    got = O.project(f, band)
+    ks = [np.arange(B) - B // 2 for B in band]
+    for j in itertools.product(*[range(B) for B in band]):
+        idx = tuple(ks[d][j[d]] % n[d] for d in range(3))
+        assert np.max(np.abs(got[(slice(None),) + j] - F[(slice(None),) + idx])) < 1e-10
+
+
+def test_project_brute_force_triple_sum():
+    f = np.random.default_rng(4).normal(size=(3,) + N_SMALL)
+    got = O.project(f, B_SMALL)
+    ks = [np.arange(B) - B // 2 for B in B_SMALL]
+    for c in range(3):
+        for j in itertools.product(*[range(B) for B in B_SMALL]):
+            acc = 0j
+            for x in itertools.product(*[range(N) for N in N_SMALL]):
+                ph = sum(ks[d][j[d]] * x[d] / N_SMALL[d] for d in range(3))
+                acc += f[(c,) + x] * cmath.exp(-2j * math.pi * ph)
+            assert abs(got[(c,) + j] - acc) < 1e-11
+
+
+def test_project_is_transpose_of_expand():
+    """<iota v, f> = <v, pi f> under the real inner product of the parameters."""
+    n = (16, 12, 10)
+    band = (8, 6, 4)
+    vt = synth.random_direction(band, 5)
+    f = np.random.default_rng(6).normal(size=(3,) + n)
+    lhs = float(np.sum(O.expand(vt, n) * f))
+    rhs = O.inner(vt, O.project(f, band))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def _band_projector(f, n, band):
+    """P = iota o diag(c_k / V) o pi, c_k = 1 if -k is in the band, else 2."""
+    V = np.prod(n)
+    ks = [np.arange(B) - B // 2 for B in band]
+    c = np.ones(band)
+    for j in itertools.product(*[range(B) for B in band]):
+        neg_in = all(-ks[d][j[d]] >= -(band[d] // 2) and -ks[d][j[d]] <= band[d] // 2 - 1
+                     for d in range(3))
+        c[j] = 1.0 if neg_in else 2.0
+    return O.expand(c[None] * O.project(f, band) / V, n)
+
+
+def test_band_projector_idempotent_symmetric_parseval():
+    n = (12, 10, 14)
+    band = (6, 4, 8)
+    rng = np.random.default_rng(7)
+    f = rng.normal(size=(3,) + n)
+    g = rng.normal(size=(3,) + n)
+    Pf = _band_projector(f, n, band)
+    assert rel(_band_projector(Pf, n, band), Pf) < 1e-12                 # P^2 = P
+    a, b = np.sum(Pf * g), np.sum(f * _band_projector(g, n, band))
+    assert abs(a - b) < 1e-11 * abs(a)                                   # P = P^T
+    # Parseval on a band-limited field: ||iota v||^2 = V^-1 sum_{band u -band} |F|^2
+    vt = synth.random_direction(band, 8)
+    v = O.expand(vt, n)
+    F = np.fft.fftn(v, axes=(1, 2, 3))
+    mask = np.zeros(n, bool)
+    ks = [np.arange(B) - B // 2 for B in band]
+    for j in itertools.product(*[range(B) for B in band]):
+        mask[tuple(ks[d][j[d]] % n[d] for d in range(3))] = True
+        mask[tuple(-ks[d][j[d]] % n[d] for d in range(3))] = True
+    lhs = np.sum(v * v)
+    rhs = np.sum(np.abs(F[:, mask]) ** 2) / np.prod(n)
+    assert abs(lhs - rhs) < 1e-12 * lhs
+    assert np.sum(np.abs(F[:, ~mask]) ** 2) < 1e-20 * lhs
+
+
+# ----------------------------------------------------------------------------
+# Regulariser symbol (Eq. 1 family; Section 3.1)
+# ----------------------------------------------------------------------------
+
+
+def _neg_laplacian(u):
+    out = 6.0 * u
+    for ax in range(3):
+        out -= np.roll(u, 1, axis=ax) + np.roll(u, -1, axis=ax)
+    return out
+
+
+def test_regulariser_symbol_is_stencil_eigenvalue():
+    """A(k) = eigenvalue of (alpha(-Lap_h) + gamma) applied 2s times to the Fourier
+    mode k, with Lap_h the periodic 7-point stencil (catches a wrong exponent,
+    a missing 2 pi or a cos/sin mix-up)."""
+    p = O.Params(n=(10, 12, 8), band=(6, 8, 4), alpha=3.0, gamma=1.0, s=2)
+    A = O.regulariser_weights(p)
+    omega = O.laplacian_symbol(p.n, p.band)
+    x = np.indices(p.n)
+    for j in [(0, 0, 0), (1, 5, 2), (3, 4, 0), (5, 7, 3)]:
+        k = [j[d] - p.band[d] // 2 for d in range(3)]
+        mode = np.exp(2j * np.pi * sum(k[d] * x[d] / p.n[d] for d in range(3)))
+        lap = _neg_laplacian(mode)
+        assert np.max(np.abs(lap - omega[j] * mode)) < 1e-12
+        u = mode
+        for _ in range(2 * p.s):
+            u = p.alpha * _neg_laplacian(u) + p.gamma * u
+        assert np.max(np.abs(u - A[j] * mode)) < 1e-9 * A[j]
+
+
+# ----------------------------------------------------------------------------
+# Transport (state equation, Eq. 36)
+# ----------------------------------------------------------------------------
+
+
+def test_zero_velocity_leaves_template_unchanged():
+    p = O.Params(n=(9, 8, 7), band=(4, 4, 2), nt=5)
+    I0, I1, _ = synth.blob_pair(p.n, 11)
+    pt = O.Point(np.zeros((3,) + p.band, complex), I0, I1, p)
+    assert np.array_equal(pt.m[-1], I0)
+
+
+def test_constant_image_stays_constant():
+    p = O.Params(n=(9, 8, 7), band=(4, 4, 2), nt=6)
+    vt = synth.random_coefficients(p.band, 12, bound=3.0)
+    I0 = np.full(p.n, 0.37)
+    pt = O.Point(vt, I0, I0, p)
+    assert np.max(np.abs(pt.m[-1] - 0.37)) < 1e-15
+
+
+def test_integer_constant_velocity_is_exact_periodic_shift():
+    """v~(0) = c gives the constant velocity Re c; with dt*c integer every step is
+    an exact periodic shift m^{n+1}(x) = m^n(x - dt c)."""
+    p = O.Params(n=(9, 8, 7), band=(4, 4, 2), nt=2)
+    vt = np.zeros((3,) + p.band, complex)
+    zero = tuple(B // 2 for B in p.band)
+    vt[(slice(None),) + zero] = [2.0, -2.0, 4.0]          # d = -dt v = (-1, 1, -2)
+    I0, _, _ = synth.blob_pair(p.n, 13)
+    pt = O.Point(vt, I0, I0, p)
+    want = I0
+    for _ in range(p.nt):
+        want = np.roll(want, shift=(1, -1, 2), axis=(0, 1, 2))   # m(x) <- m(x + d)
+    assert np.array_equal(pt.m[-1], want)
+
+
+def test_interpolation_reproduces_affine_field():
+    """Trilinear interpolation is exact on affine fields and its gradient is the
+    slope (interior voxels, away from the periodic seam)."""
+    n = (12, 11, 10)
+    rng = np.random.default_rng(14)
+    a = rng.normal(size=3)
+    x = np.indices(n).astype(float)
+    m = 0.3 + sum(a[k] * x[k] for k in range(3))
+    d = rng.uniform(-0.95, 0.95, size=(3,) + n)
+    st = O.Stencil(d)
+    val = st.apply(m)
+    grad = st.gradient(m)
+    inner_sl = (slice(1, -1),) * 3
+    want = 0.3 + sum(a[k] * (x[k] + d[k]) for k in range(3))
+    assert np.max(np.abs(val[inner_sl] - want[inner_sl])) < 1e-12
+    for k in range(3):
+        assert np.max(np.abs(grad[k][inner_sl] - a[k])) < 1e-12
+
+
+def test_interpolation_separable_closed_form_with_wrap():
+    """On m = g1(x1) g2(x2) g3(x3) the trilinear value is the product of 1-D
+    periodic linear interpolants, and each partial derivative replaces one factor
+    by its slope; displacements up to 2.5 voxels exercise the periodic wrap and
+    the floor cell rule."""
+    n = (7, 6, 5)
+    rng = np.random.default_rng(15)
+    g = [rng.normal(size=N) for N in n]
+    m = g[0][:, None, None] * g[1][None, :, None] * g[2][None, None, :]
+    d = rng.uniform(-2.5, 2.5, size=(3,) + n)
+    st = O.Stencil(d)
+    val, grad = st.apply(m), st.gradient(m)
+    x = np.indices(n)
+    L, dL = [], []
+    for k in range(3):
+        pos = x[k] + d[k]
+        i = np.floor(pos).astype(int)
+        f = pos - i
+        g0, g1 = g[k][i % n[k]], g[k][(i + 1) % n[k]]
+        L.append((1 - f) * g0 + f * g1)
+        dL.append(g1 - g0)
+    assert np.max(np.abs(val - L[0] * L[1] * L[2])) < 1e-12
+    assert np.max(np.abs(grad[0] - dL[0] * L[1] * L[2])) < 1e-12
+    assert np.max(np.abs(grad[1] - L[0] * dL[1] * L[2])) < 1e-12
+    assert np.max(np.abs(grad[2] - L[0] * L[1] * dL[2])) < 1e-12
+
+
+def test_adjoint_step_is_exact_transpose():
+    """Dense S built column by column from the forward step, against the adjoint
+    step applied to unit vectors; plus the dot-product identity at a larger size."""
+    n = (3, 4, 5)
+    V = int(np.prod(n))
+    d = np.random.default_rng(16).uniform(-0.9, 0.9, size=(3,) + n)
+    st = O.Stencil(d)
+    S = np.zeros((V, V))
+    ST = np.zeros((V, V))
+    for j in range(V):
+        e = np.zeros(V)
+        e[j] = 1.0
+        S[:, j] = st.apply(e.reshape(n)).ravel()
+        ST[:, j] = st.apply_transpose(e.reshape(n)).ravel()
+    assert np.max(np.abs(ST - S.T)) == 0.0
+    assert np.allclose(S.sum(axis=1), 1.0, atol=1e-14)     # weights sum to one
+    n2 = (14, 13, 12)
+    rng = np.random.default_rng(17)
+    st2 = O.Stencil(rng.uniform(-0.9, 0.9, size=(3,) + n2))
+    a, b = rng.normal(size=n2), rng.normal(size=n2)
+    lhs, rhs = np.sum(st2.apply(a) * b), np.sum(a * st2.apply_transpose(b))
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+# ----------------------------------------------------------------------------
+# Gradient (Eq. 38) against central finite differences of the energy (Eq. 35)
+# ----------------------------------------------------------------------------
+
+
+def _kink_free(vt, dvt, eps, p):
+    """True when no voxel changes interpolation cell between v -+ eps dv."""
+    lo = np.floor(O.displacement(vt - eps * dvt, p))
+    hi = np.floor(O.displacement(vt + eps * dvt, p))
+    return np.array_equal(lo, hi)
+
+
+def test_gradient_matches_central_finite_differences():
+    """32 random directions on a 16^3 grid, step 1e-6, relative error 1e-6."""
+    p = O.Params(n=(16, 16, 16), band=(6, 6, 6), nt=10)
+    I0, I1, _ = synth.blob_pair(p.n, 21, max_disp=2.0)
+    vt = synth.random_coefficients(p.band, 22, bound=2.5)
+    pt = O.Point(vt, I0, I1, p)
+    g, _, _ = pt.gradient()
+    eps = 1e-6
+    checked = 0
+    for s in range(48):
+        dvt = synth.random_direction(p.band, 100 + s)
+        if not _kink_free(vt, dvt, eps, p):
+            continue
+        fd = (O.energy(vt + eps * dvt, I0, I1, p) - O.energy(vt - eps * dvt, I0, I1, p)) / (2 * eps)
+        dd = O.inner(g, dvt)
+        assert abs(fd - dd) <= 1e-6 * abs(dd), (s, fd, dd)
+        checked += 1
+        if checked == 32:
+            break
+    assert checked == 32
+
+
+def test_gradient_regulariser_part_only():
+    """With I1 equal to the transported template the data term is zero and the
+    gradient's data part vanishes: g = A v (catches a missing 1/2 or a square)."""
+    p = O.Params(n=(10, 9, 8), band=(4, 4, 4), nt=4)
+    I0, _, _ = synth.blob_pair(p.n, 23)
+    vt = synth.random_coefficients(p.band, 24, bound=1.5)
+    pt0 = O.Point(vt, I0, I0, p)
+    pt = O.Point(vt, I0, pt0.m[-1], p)
+    g, _, _ = pt.gradient()
+    A = O.regulariser_weights(p)
+    assert rel(g, A[None] * vt) < 1e-14
+    assert abs(pt.energy - 0.5 * np.sum(A[None] * np.abs(vt) ** 2)) < 1e-12 * pt.energy
+
+
+# ----------------------------------------------------------------------------
+# Gauss-Newton Hessian (Eq. 46 with the Section 3.4 drops)
+# ----------------------------------------------------------------------------
+
+
+def _theta(z):
+    return np.concatenate([z.real.ravel(), z.imag.ravel()])
+
+
+def _from_theta(t, shape):
+    h = t.size // 2
+    return (t[:h] + 1j * t[h:]).reshape(shape)
+
+
+def test_gn_hessian_symmetric_positive_16cube():
+    p = O.Params(n=(16, 16, 16), band=(6, 6, 6), nt=10)
+    I0, I1, _ = synth.blob_pair(p.n, 31, max_disp=2.0)
+    vt = synth.random_coefficients(p.band, 32, bound=2.5)
+    pt = O.Point(vt, I0, I1, p)
+    for s in range(3):
+        v = synth.random_direction(p.band, 300 + s)
+        w = synth.random_direction(p.band, 400 + s)
+        Hv, Hw = pt.gn_hessvec(v)[0], pt.gn_hessvec(w)[0]
+        a, b = O.inner(Hv, w), O.inner(v, Hw)
+        assert abs(a - b) <= 1e-10 * max(abs(a), abs(b))
+        assert O.inner(Hv, v) > 0.0
+
+
+def test_gn_hessian_equals_dense_jacobian_bruteforce():
+    """8^3 grid, band 4^3 (384 real parameters): J = dm^nt/dtheta by central
+    differences of the state, H = A + (2/sigma^2) J^T J, compared with the
+    incremental state / incremental adjoint chain."""
+    p = O.Params(n=(8, 8, 8), band=(4, 4, 4), nt=3, sigma=0.7)
+    I0, I1, _ = synth.blob_pair(p.n, 41, max_disp=1.5)
+    # first seeded point whose displacements keep >= 1e-4 voxel from every cell
+    # boundary, so no per-parameter difference straddles a kink
+    for seed in range(42, 80):
+        vt = synth.random_coefficients(p.band, seed, bound=1.2)
+        d = O.displacement(vt, p)
+        if np.min(np.abs(d - np.round(d))) >= 1e-4:
+            break
+    else:
+        raise AssertionError("no kink-free point")
+    pt = O.Point(vt, I0, I1, p)
+    P = 2 * 3 * 64
+    eps = 1e-6
+    J = np.zeros((int(np.prod(p.n)), P))
+    for j in range(P):
+        e = np.zeros(P)
+        e[j] = eps
+        de = _from_theta(e, vt.shape)
+        mp = O.Point(vt + de, I0, I1, p).m[-1]
+        mm = O.Point(vt - de, I0, I1, p).m[-1]
+        J[:, j] = ((mp - mm) / (2 * eps)).ravel()
+    A = O.regulariser_weights(p)
+    Ad = np.concatenate([np.tile(A.ravel(), 3)] * 2)
+    H = np.diag(Ad) + (2.0 / p.sigma**2) * J.T @ J
+    for s in range(4):
+        v = synth.random_direction(p.band, 500 + s)
+        got = _theta(pt.gn_hessvec(v)[0])
+        assert rel(got, H @ _theta(v)) < 1e-7
+
+
+def test_gn_hessian_is_fd_of_gradient_at_zero_residual():
+    """At zero residual (I1 = m^nt(v)) the terms the Gauss-Newton step drops are
+    zero, so H_GN dv equals the central difference of the gradient."""
+    p = O.Params(n=(12, 12, 12), band=(4, 6, 4), nt=5)
+    I0, _, _ = synth.blob_pair(p.n, 51, max_disp=2.0)
+    vt = synth.random_coefficients(p.band, 52, bound=2.0)
+    I1 = O.Point(vt, I0, I0, p).m[-1]
+    pt = O.Point(vt, I0, I1, p)
+    eps = 1e-6
+    for s in range(3):
+        dvt = synth.random_direction(p.band, 600 + s)
+        if not _kink_free(vt, dvt, eps, p):
+            continue
+        gp = O.Point(vt + eps * dvt, I0, I1, p).gradient()[0]
+        gm = O.Point(vt - eps * dvt, I0, I1, p).gradient()[0]
+        assert rel(pt.gn_hessvec(dvt)[0], (gp - gm) / (2 * eps)) < 1e-6
+
+
+# ----------------------------------------------------------------------------
+# PCG and Newton (Section 3.4)
+# ----------------------------------------------------------------------------
+
+
+def test_pcg_to_convergence_equals_dense_solve():
+    p = O.Params(n=(8, 8, 8), band=(4, 4, 4), nt=3)
+    I0, I1, _ = synth.blob_pair(p.n, 61, max_disp=1.5)
+    vt = synth.random_coefficients(p.band, 62, bound=1.0)
+    pt = O.Point(vt, I0, I1, p)
+    P = 2 * 3 * 64
+    H = np.zeros((P, P))
+    for j in range(P):
+        e = np.zeros(P)
+        e[j] = 1.0
+        H[:, j] = _theta(pt.gn_hessvec(_from_theta(e, vt.shape))[0])
+    g, _, _ = pt.gradient()
+    want = np.linalg.solve(H, -_theta(g))
+    x, its, r = O.pcg(lambda v: pt.gn_hessvec(v)[0], -g, 1.0 / pt.A[None], 1e-13, 500)
+    assert r <= 1e-13
+    assert rel(_theta(x), want) < 1e-9
+
+
+def test_newton_decreases_energy_and_gradient():
+    p = O.Params(n=(16, 16, 16), band=(4, 4, 4), nt=5)
+    I0, I1, _ = synth.blob_pair(p.n, 71, max_disp=2.0)
+    rep = O.newton(np.zeros((3,) + p.band, complex), I0, I1, p, max_newton=4, max_pcg=8,
+                   gtol=1e-6)
+    assert rep.iterations >= 3
+    assert all(b < a for a, b in zip(rep.energies, rep.energies[1:]))
+    assert rep.grad_inf_rel < 0.5
