@@ -1,0 +1,193 @@
+/*
+ * blr.h -- C-ABI of the band-limited PDE-LDDMM Gauss-Newton-Krylov library
+ * (libblr.so, CUDA kernels for sm_103a).
+ *
+ * Method: Hernandez, "Newton-Krylov optimization in PDE-constrained
+ * diffeomorphic registration parameterized in the space of band-limited vector
+ * fields" (arXiv 1807.05117), state-equation variant, stationary velocity,
+ * Gauss-Newton Hessian.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid      N = (N1, N2, N3), V = N1*N2*N3 voxels, voxel spacing 1.
+ * Fields    float32, C order [N1][N2][N3] (N3 fastest).  Vector fields are
+ *           [3][N1][N2][N3] (component-major).
+ * Band      B = (B1, B2, B3), each even, 2 <= B_d <= N_d.  Centred integer
+ *           frequencies k_d = -B_d/2 ... B_d/2-1 (Section 3.1, Eq. 33 read as a
+ *           centred truncation).  Coefficient arrays are complex64 stored as
+ *           interleaved float pairs (re, im), layout [3][B1][B2][B3]:
+ *           2*3*B1*B2*B3 floats.
+ * iota      iota(v~)_c(x) = Re sum_k v~_c(k) exp(2 pi i sum_d k_d x_d / N_d).
+ * pi        pi(f)_c(k) = sum_x f_c(x) exp(-2 pi i sum_d k_d x_d / N_d) = iota^T
+ *           under <a, b> = Re sum a conj(b).
+ * A(k)      (alpha*omega(k) + gamma)^(2s), omega(k) = sum_d 2(1 - cos(2 pi k_d/N_d));
+ *           the regulariser L~ of Eq. 34 with L = (-alpha Lap + gamma)^s, and
+ *           the preconditioner K~ = 1/A (Sections 3.1, 3.4).
+ * Transport nt steps, dt = 1/nt; d = -dt * iota(v~) is the per-step
+ *           displacement in voxels; m^{n+1}(x) = trilinear value of m^n at
+ *           x + d(x) with periodic wrap (semi-Lagrangian solve of the state
+ *           equation, Eq. 36).  The discrete adjoint uses the exact transpose
+ *           of that step, which the kernels evaluate as a gather; it requires
+ *           |d_a(x)| < 1 voxel on every axis (the CFL bound of Section 2.4).
+ *
+ * Pointers  "device" = memory the GPU can read (cudaMalloc / torch CUDA
+ *           tensors).  "host or device" = either; the library copies it with
+ *           cudaMemcpyDefault (pinned host memory gives asynchronous copies).
+ *           All caller pointers are borrowed for the duration of the call only;
+ *           the plan never keeps them.
+ * Streams   Every call is ordered on `stream` (NULL = legacy default stream)
+ *           and is asynchronous unless stated otherwise.  A plan may be used
+ *           by one stream at a time; plans are independent of each other.
+ * Errors    Functions return BLR_OK (0) or a negative code; nothing throws
+ *           across the ABI.  Conditions detected on the device (a displacement
+ *           that breaks the CFL bound, a non-finite energy) are latched in the
+ *           plan and returned by blr_status(), which synchronises the stream.
+ */
+#ifndef BLR_H
+#define BLR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define BLR_OK        0
+#define BLR_EINVAL   (-1)  /* bad argument, shape or call order            */
+#define BLR_ENOMEM   (-2)  /* device allocation failed                     */
+#define BLR_ECUDA    (-3)  /* CUDA runtime error                           */
+#define BLR_ECFL     (-4)  /* |d_a(x)| >= 1 voxel per step somewhere        */
+#define BLR_ENAN     (-5)  /* non-finite energy or residual                */
+#define BLR_ESTATE   (-6)  /* needs a prior blr_state / blr_gradient        */
+#define BLR_ECURV    (-7)  /* PCG met <p, Hp> <= 0                          */
+
+/* Precision of the truncated-DFT contractions (the transport is always FP32). */
+#define BLR_FP32   0       /* FP32 FMA contractions                         */
+#define BLR_MIXED  1       /* BF16 hi+lo split operands on tensor cores,     */
+                           /* FP32 accumulation                             */
+
+typedef struct CUstream_st *blr_stream_t;   /* identical to cudaStream_t */
+typedef struct blr_plan *blr_plan_t;
+
+/* Problem description (Section 3.2, Eq. 35 and the constants of L). */
+typedef struct blr_params {
+    int n[3];        /* grid N1, N2, N3 (each >= 1)                         */
+    int band[3];     /* B1, B2, B3 (each even, 2 <= B_d <= N_d)             */
+    int nt;          /* number of time steps, >= 1                          */
+    double alpha;    /* L = (-alpha Lap + gamma)^s, alpha >= 0              */
+    double gamma;    /* gamma > 0                                           */
+    int s;           /* s >= 0                                              */
+    double sigma;    /* image term weight 1/sigma^2, sigma > 0              */
+    int precision;   /* BLR_FP32 or BLR_MIXED                               */
+    int reserved;    /* must be 0                                           */
+} blr_params;
+
+/* Result of blr_newton (host struct filled by the library). */
+typedef struct blr_report {
+    int newton_iters;      /* accepted Newton updates                       */
+    int pcg_iters;         /* PCG iterations summed over the run            */
+    int n_state;           /* forward solves (gradients + line-search trials) */
+    int n_hessvec;         /* Gauss-Newton Hessian-vector products          */
+    int n_halvings;        /* step-length halvings in the line search       */
+    int status;            /* BLR_OK, or why the run stopped early          */
+    double energy0;        /* E at the initial velocity                     */
+    double energy;         /* E at the returned velocity                    */
+    double grad_inf_rel;   /* ||g||_inf / ||g_0||_inf at the returned velocity */
+} blr_report;
+
+/* Create a plan: validates `p`, allocates every device buffer the hot path
+ * needs for this grid/band/nt (state stack of nt+1 fields, adjoint and
+ * incremental fields, DFT tables and intermediates, PCG vectors, reduction
+ * scratch) and builds the DFT tables on the current device.
+ * `p` is host memory, read once.  On success *out owns the allocations.
+ * Returns BLR_EINVAL for an invalid `p`, BLR_ENOMEM / BLR_ECUDA otherwise. */
+int blr_plan_create(const blr_params *p, blr_plan_t *out);
+
+/* Release every allocation of the plan (synchronises the device first).
+ * NULL is accepted. */
+int blr_plan_destroy(blr_plan_t plan);
+
+/* Template I0 and reference I1 of the registration (Section 2.2: m(0) = I0,
+ * the image term compares m(1) with I1).  Host or device, V floats each; the
+ * plan keeps its own copies.  Invalidates any stored state. */
+int blr_set_images(blr_plan_t plan, const float *I0, const float *I1,
+                   blr_stream_t stream);
+
+/* iota (Section 3.1, Eq. 33): band coefficients -> spatial vector field.
+ * vt: device, 2*3*B1*B2*B3 floats (interleaved complex).
+ * v : device, 3*V floats, written. */
+int blr_expand(blr_plan_t plan, const float *vt, float *v, blr_stream_t stream);
+
+/* pi = iota^T (Section 3.1): spatial vector field -> band coefficients.
+ * f : device, 3*V floats.   ft: device, 2*3*B1*B2*B3 floats, written. */
+int blr_project(blr_plan_t plan, const float *f, float *ft, blr_stream_t stream);
+
+/* Forward solve of the state equation (Section 3.2, Eq. 36, m(0) = I0) at the
+ * velocity vt and the energy of Eq. 35.  Stores vt, the displacement and all
+ * states m^0..m^nt in the plan (the "current point" used by blr_adjoint,
+ * blr_hessvec and blr_pcg).
+ * vt    : device, 2*3*B1*B2*B3 floats.
+ * m1    : device, V floats, receives m^nt; may be NULL.
+ * energy: device, 3 doubles {E, regulariser part, image part}; may be NULL.
+ * A displacement with |d| >= 1 latches BLR_ECFL (see blr_status). */
+int blr_state(blr_plan_t plan, const float *vt, float *m1, double *energy,
+              blr_stream_t stream);
+
+/* Adjoint solve (Eq. 8 with lambda(1) = -(2/sigma^2)(m(1) - I1)) at the current
+ * point, and the body force b = dt sum_n lambda^{n+1} grad m^n(x + d), the
+ * discrete lambda grad m of Eq. 38.  Needs a prior blr_state (BLR_ESTATE).
+ * b      : device, 3*V floats, written.
+ * lambda0: device, V floats, receives lambda^0; may be NULL. */
+int blr_adjoint(blr_plan_t plan, float *b, float *lambda0, blr_stream_t stream);
+
+/* Reduced gradient (Section 3.2, Eq. 38): g~ = A v~ + pi(b), i.e. blr_state +
+ * blr_adjoint + blr_project + the regulariser term, at vt.
+ * vt: device (input), g: device, 2*3*B1*B2*B3 floats (written),
+ * energy: device, 3 doubles, may be NULL. */
+int blr_gradient(blr_plan_t plan, const float *vt, float *g, double *energy,
+                 blr_stream_t stream);
+
+/* Gauss-Newton Hessian-vector product at the current point (Section 3.2,
+ * Eqs. 44-46 with the Gauss-Newton drops of Section 3.4):
+ *   H~ dv~ = A dv~ + pi(db), incremental state dm^0 = 0,
+ *   dm^{n+1} = S dm^n - dt grad m^n(x+d) . iota(dv~), dlambda^nt =
+ *   -(2/sigma^2) dm^nt, dlambda^n = S^T dlambda^{n+1},
+ *   db = dt sum_n dlambda^{n+1} grad m^n(x + d).
+ * dvt: device input, hdv: device output, 2*3*B1*B2*B3 floats each.
+ * Needs a prior blr_state / blr_gradient (BLR_ESTATE). */
+int blr_hessvec(blr_plan_t plan, const float *dvt, float *hdv,
+                blr_stream_t stream);
+
+/* Preconditioned CG (Section 3.4, Eq. 55) on H~ x = rhs from x = 0 with the
+ * preconditioner K~ = 1/A, at the current point.  Inner products and step
+ * scalars are FP64 on the device.  Stops when ||r|| <= eta ||r_0|| or after
+ * maxit iterations.  Synchronises the stream once per iteration.
+ * rhs, x: device, 2*3*B1*B2*B3 floats (x written).
+ * iters, relres: host, may be NULL (iterations run, final ||r||/||r_0||).
+ * Returns BLR_ECURV if <p, Hp> <= 0. */
+int blr_pcg(blr_plan_t plan, const float *rhs, float *x, int maxit, double eta,
+            int *iters, double *relres, blr_stream_t stream);
+
+/* Gauss-Newton-Krylov registration (Section 3.4, Eqs. 54-55): from vt, up to
+ * max_newton updates v~ <- v~ + eps p with H~ p = -g~ solved by blr_pcg
+ * (<= max_pcg iterations) and eps from Armijo backtracking (c1 = 1e-4,
+ * eps = 1, 1/2, ..., at most 10 halvings; a trial breaking the CFL bound is
+ * rejected).  The paper's "v - eps dv" is read as this descent step.
+ * PCG tolerance: eta = forcing if forcing >= 0, else
+ * min(0.5, sqrt(||g|| / ||g_0||)).  Stops when ||g||_inf / ||g_0||_inf < gtol.
+ * vt : host or device, 2*3*B1*B2*B3 floats, in: initial velocity, out: result.
+ * rep: host, may be NULL.  Synchronous. */
+int blr_newton(blr_plan_t plan, float *vt, int max_newton, int max_pcg,
+               double gtol, double forcing, blr_report *rep,
+               blr_stream_t stream);
+
+/* Synchronise `stream`, return the first latched device condition
+ * (BLR_ECFL, BLR_ENAN) or BLR_OK, and clear it. */
+int blr_status(blr_plan_t plan, blr_stream_t stream);
+
+/* Human-readable text for a status code (static storage). */
+const char *blr_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BLR_H */

@@ -1,0 +1,298 @@
+"""Thin ctypes binding of libblr.so (include/blr.h).
+
+Argument marshalling only: every function passes tensor data pointers and the
+current CUDA stream to the C entry point of the same name and raises
+``BlrError`` on a non-zero status.  There is no fallback: if the library is not
+built, importing this module raises.
+
+Coefficient tensors are torch.complex64 of shape (3, B1, B2, B3) (interleaved
+complex, as the C-ABI expects); fields are torch.float32 of shape (N1, N2, N3)
+or (3, N1, N2, N3); energies are torch.float64 of shape (3,) on the device.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+from .build import LIB_PATH
+
+BLR_OK = 0
+BLR_EINVAL = -1
+BLR_ENOMEM = -2
+BLR_ECUDA = -3
+BLR_ECFL = -4
+BLR_ENAN = -5
+BLR_ESTATE = -6
+BLR_ECURV = -7
+
+BLR_FP32 = 0
+BLR_MIXED = 1
+
+
+class blr_params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("band", ctypes.c_int * 3), ("nt", ctypes.c_int),
+                ("alpha", ctypes.c_double), ("gamma", ctypes.c_double), ("s", ctypes.c_int),
+                ("sigma", ctypes.c_double), ("precision", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
+
+
+class blr_report(ctypes.Structure):
+    _fields_ = [("newton_iters", ctypes.c_int), ("pcg_iters", ctypes.c_int),
+                ("n_state", ctypes.c_int), ("n_hessvec", ctypes.c_int),
+                ("n_halvings", ctypes.c_int), ("status", ctypes.c_int),
+                ("energy0", ctypes.c_double), ("energy", ctypes.c_double),
+                ("grad_inf_rel", ctypes.c_double)]
+
+
+class BlrError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {blr_strerror(code)} (status {code})")
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "blr_plan_create": (ctypes.POINTER(blr_params), ctypes.POINTER(_P)),
+    "blr_plan_destroy": (_P,),
+    "blr_set_images": (_P, _P, _P, _P),
+    "blr_expand": (_P, _P, _P, _P),
+    "blr_project": (_P, _P, _P, _P),
+    "blr_state": (_P, _P, _P, _P, _P),
+    "blr_adjoint": (_P, _P, _P, _P),
+    "blr_gradient": (_P, _P, _P, _P, _P),
+    "blr_hessvec": (_P, _P, _P, _P),
+    "blr_pcg": (_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                ctypes.POINTER(ctypes.c_double), _P),
+    "blr_newton": (_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                   ctypes.POINTER(blr_report), _P),
+    "blr_status": (_P, _P),
+}
+
+#: every symbol include/blr.h declares
+EXPORTED = tuple(_SIGS) + ("blr_strerror",)
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run paper_1807_05117_gb300.build.build_library()")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, args in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = list(args)
+        fn.restype = ctypes.c_int
+    lib.blr_strerror.argtypes = [ctypes.c_int]
+    lib.blr_strerror.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = _load()
+
+
+def blr_strerror(code: int) -> str:
+    return _lib.blr_strerror(int(code)).decode()
+
+
+def _check(rc: int, where: str):
+    if rc != BLR_OK:
+        raise BlrError(rc, where)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return _P(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return _P(stream)
+    return _P(stream.cuda_stream)
+
+
+def _ptr(t, *, device_only=True, dtype=None, numel=None, optional=False, name="tensor"):
+    if t is None:
+        if optional:
+            return None
+        raise ValueError(f"{name} is required")
+    if device_only and not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return _P(t.data_ptr())
+
+
+def make_params(n, band, nt=10, alpha=3.0, gamma=1.0, s=2, sigma=1.0, precision=BLR_FP32):
+    p = blr_params()
+    p.n[:] = [int(v) for v in n]
+    p.band[:] = [int(v) for v in band]
+    p.nt = int(nt)
+    p.alpha, p.gamma, p.s, p.sigma = float(alpha), float(gamma), int(s), float(sigma)
+    p.precision = int(precision)
+    p.reserved = 0
+    return p
+
+
+# --- entry points (same names as the C-ABI) ---------------------------------
+
+
+def blr_plan_create(params: blr_params) -> int:
+    h = _P()
+    _check(_lib.blr_plan_create(ctypes.byref(params), ctypes.byref(h)), "blr_plan_create")
+    return h.value
+
+
+def blr_plan_destroy(plan: int):
+    _check(_lib.blr_plan_destroy(_P(plan)), "blr_plan_destroy")
+
+
+def blr_set_images(plan, I0, I1, stream=None):
+    import torch
+    _check(_lib.blr_set_images(_P(plan), _ptr(I0, device_only=False, dtype=torch.float32, name="I0"),
+                               _ptr(I1, device_only=False, dtype=torch.float32, name="I1"),
+                               _stream(stream)), "blr_set_images")
+
+
+def blr_expand(plan, vt, v, stream=None):
+    import torch
+    _check(_lib.blr_expand(_P(plan), _ptr(vt, dtype=torch.complex64, name="vt"),
+                           _ptr(v, dtype=torch.float32, name="v"), _stream(stream)), "blr_expand")
+
+
+def blr_project(plan, f, ft, stream=None):
+    import torch
+    _check(_lib.blr_project(_P(plan), _ptr(f, dtype=torch.float32, name="f"),
+                            _ptr(ft, dtype=torch.complex64, name="ft"), _stream(stream)),
+           "blr_project")
+
+
+def blr_state(plan, vt, m1=None, energy=None, stream=None):
+    import torch
+    _check(_lib.blr_state(_P(plan), _ptr(vt, dtype=torch.complex64, name="vt"),
+                          _ptr(m1, dtype=torch.float32, optional=True, name="m1"),
+                          _ptr(energy, dtype=torch.float64, numel=3, optional=True, name="energy"),
+                          _stream(stream)), "blr_state")
+
+
+def blr_adjoint(plan, b, lambda0=None, stream=None):
+    import torch
+    _check(_lib.blr_adjoint(_P(plan), _ptr(b, dtype=torch.float32, name="b"),
+                            _ptr(lambda0, dtype=torch.float32, optional=True, name="lambda0"),
+                            _stream(stream)), "blr_adjoint")
+
+
+def blr_gradient(plan, vt, g, energy=None, stream=None):
+    import torch
+    _check(_lib.blr_gradient(_P(plan), _ptr(vt, dtype=torch.complex64, name="vt"),
+                             _ptr(g, dtype=torch.complex64, name="g"),
+                             _ptr(energy, dtype=torch.float64, numel=3, optional=True, name="energy"),
+                             _stream(stream)), "blr_gradient")
+
+
+def blr_hessvec(plan, dvt, hdv, stream=None):
+    import torch
+    _check(_lib.blr_hessvec(_P(plan), _ptr(dvt, dtype=torch.complex64, name="dvt"),
+                            _ptr(hdv, dtype=torch.complex64, name="hdv"), _stream(stream)),
+           "blr_hessvec")
+
+
+def blr_pcg(plan, rhs, x, maxit, eta, stream=None):
+    import torch
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    _check(_lib.blr_pcg(_P(plan), _ptr(rhs, dtype=torch.complex64, name="rhs"),
+                        _ptr(x, dtype=torch.complex64, name="x"), int(maxit), float(eta),
+                        ctypes.byref(it), ctypes.byref(rel), _stream(stream)), "blr_pcg")
+    return it.value, rel.value
+
+
+@dataclass
+class Report:
+    newton_iters: int
+    pcg_iters: int
+    n_state: int
+    n_hessvec: int
+    n_halvings: int
+    status: int
+    energy0: float
+    energy: float
+    grad_inf_rel: float
+
+
+def blr_newton(plan, vt, max_newton, max_pcg, gtol, forcing=-1.0, stream=None,
+               raise_on_error=True) -> Report:
+    import torch
+    rep = blr_report()
+    rc = _lib.blr_newton(_P(plan), _ptr(vt, device_only=False, dtype=torch.complex64, name="vt"),
+                         int(max_newton), int(max_pcg), float(gtol), float(forcing),
+                         ctypes.byref(rep), _stream(stream))
+    if raise_on_error:
+        _check(rc, "blr_newton")
+    return Report(*[getattr(rep, f) for f, _ in blr_report._fields_])
+
+
+def blr_status(plan, stream=None) -> int:
+    return int(_lib.blr_status(_P(plan), _stream(stream)))
+
+
+class Plan:
+    """Owning handle: ``with Plan(n, band, nt) as P: P.gradient(vt, g)``."""
+
+    def __init__(self, n, band, nt=10, alpha=3.0, gamma=1.0, s=2, sigma=1.0,
+                 precision=BLR_FP32):
+        self.params = make_params(n, band, nt, alpha, gamma, s, sigma, precision)
+        self.n = tuple(int(v) for v in n)
+        self.band = tuple(int(v) for v in band)
+        self.nt = int(nt)
+        self.handle = blr_plan_create(self.params)
+
+    def close(self):
+        if self.handle:
+            blr_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_images(self, I0, I1, stream=None):
+        blr_set_images(self.handle, I0, I1, stream)
+
+    def expand(self, vt, v, stream=None):
+        blr_expand(self.handle, vt, v, stream)
+
+    def project(self, f, ft, stream=None):
+        blr_project(self.handle, f, ft, stream)
+
+    def state(self, vt, m1=None, energy=None, stream=None):
+        blr_state(self.handle, vt, m1, energy, stream)
+
+    def adjoint(self, b, lambda0=None, stream=None):
+        blr_adjoint(self.handle, b, lambda0, stream)
+
+    def gradient(self, vt, g, energy=None, stream=None):
+        blr_gradient(self.handle, vt, g, energy, stream)
+
+    def hessvec(self, dvt, hdv, stream=None):
+        blr_hessvec(self.handle, dvt, hdv, stream)
+
+    def pcg(self, rhs, x, maxit, eta, stream=None):
+        return blr_pcg(self.handle, rhs, x, maxit, eta, stream)
+
+    def newton(self, vt, max_newton, max_pcg, gtol, forcing=-1.0, stream=None,
+               raise_on_error=True):
+        return blr_newton(self.handle, vt, max_newton, max_pcg, gtol, forcing, stream,
+                          raise_on_error)
+
+    def status(self, stream=None):
+        return blr_status(self.handle, stream)

@@ -1,0 +1,380 @@
+// C-ABI entry points of libblr (declared and documented in include/blr.h).
+//
+// Host-side control only: every arithmetic step of the hot path runs in the
+// kernels of dft.cu, sweeps.cu and reduce.cu.  The Newton and PCG drivers read
+// FP64 scalars back from the device to take their stop / accept decisions.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "blr_internal.cuh"
+
+namespace {
+
+int validate(const blr_params *p) {
+    if (!p) return BLR_EINVAL;
+    for (int d = 0; d < 3; ++d) {
+        if (p->n[d] < 1 || p->band[d] < 2 || (p->band[d] & 1) || p->band[d] > p->n[d])
+            return BLR_EINVAL;
+    }
+    if (p->band[2] > 64) return BLR_EINVAL;      // stage A' keeps <= 64 frequencies per lane pair
+    if (p->nt < 1 || !(p->sigma > 0) || !(p->gamma > 0) || !(p->alpha >= 0) || p->s < 0)
+        return BLR_EINVAL;
+    if (p->precision != BLR_FP32 && p->precision != BLR_MIXED) return BLR_EINVAL;
+    if (p->precision == BLR_MIXED) return BLR_EINVAL;   // tensor-core contractions not built
+    if (p->reserved != 0) return BLR_EINVAL;
+    long long V = (long long)p->n[0] * p->n[1] * p->n[2];
+    if (V > (1LL << 31)) return BLR_EINVAL;
+    return BLR_OK;
+}
+
+struct Arena {
+    char *base = nullptr;
+    size_t used = 0;
+    template <typename T>
+    T *take(size_t count) {
+        size_t bytes = (count * sizeof(T) + 255) & ~(size_t)255;
+        T *r = reinterpret_cast<T *>(base + used);
+        used += bytes;
+        return r;
+    }
+};
+
+// Lay out (or, with base == nullptr, size) every device buffer of the plan.
+size_t layout(blr_plan *P, char *base) {
+    Arena a;
+    a.base = base;
+    const long long V = P->V;
+    P->m = a.take<float>((size_t)(P->p.nt + 1) * V);
+    P->I0 = P->m;                        // m^0 = I0 lives in the first slot
+    P->I1 = a.take<float>(V);
+    P->d = a.take<float>(3 * V);
+    P->lam[0] = a.take<float>(V);
+    P->lam[1] = a.take<float>(V);
+    P->b = a.take<float>(3 * V);
+    P->dv = a.take<float>(3 * V);
+    P->dm[0] = a.take<float>(V);
+    P->dm[1] = a.take<float>(V);
+    P->W1 = a.take<float>((size_t)2 * P->B1 * P->N1);
+    P->T2c = a.take<float>((size_t)P->B2 * P->N2);
+    P->T2s = a.take<float>((size_t)P->B2 * P->N2);
+    P->T3c = a.take<float>((size_t)P->B3 * P->N3);
+    P->T3s = a.take<float>((size_t)P->B3 * P->N3);
+    P->A = a.take<float>(P->nb);
+    P->dft_big = a.take<float>((size_t)3 * P->B1 * P->N2 * P->N3 * 2);
+    P->dft_small = a.take<float>((size_t)3 * P->B1 * P->B2 * P->N3 * 2);
+    float **vecs[] = {&P->vt, &P->g, &P->r, &P->pv, &P->q, &P->x, &P->trial, &P->step, &P->vtmp};
+    for (float **v : vecs) *v = a.take<float>(P->nfloat);
+    P->dsc = a.take<double>(SC_COUNT);
+    P->dstatus = a.take<int>(1);
+    P->ticket = a.take<unsigned int>(1);
+    P->partials = a.take<double>(P->npart);
+    return a.used;
+}
+
+char *arena_base(blr_plan *P) { return reinterpret_cast<char *>(P->m); }
+
+// Copy the device scalars and the latched flags to the host and wait.
+int fetch_scalars(blr_plan *P, cudaStream_t s, int *flags) {
+    BLR_CK(cudaMemcpyAsync(P->hsc, P->dsc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (flags) {
+        BLR_CK(cudaMemcpyAsync(P->hsc + SC_COUNT, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+        BLR_CK(cudaMemsetAsync(P->dstatus, 0, sizeof(int), s));
+    }
+    BLR_CK(cudaStreamSynchronize(s));
+    if (flags) memcpy(flags, P->hsc + SC_COUNT, sizeof(int));
+    return BLR_OK;
+}
+
+int flags_to_status(int flags) {
+    if (flags & BLR_FLAG_NAN) return BLR_ENAN;
+    if (flags & BLR_FLAG_CFL) return BLR_ECFL;
+    return BLR_OK;
+}
+
+// Forward solve at vt (device) -> current point; energy into dsc (and energy_out).
+int state_at(blr_plan *P, const float *vt, double *energy_out, cudaStream_t s) {
+    if (vt != P->vt)
+        BLR_CK(cudaMemcpyAsync(P->vt, vt, P->nfloat * sizeof(float), cudaMemcpyDefault, s));
+    int rc = dft_expand(P, P->vt, P->d, 1, s);
+    if (rc) return rc;
+    if ((rc = sweep_state(P, s))) return rc;
+    if ((rc = energy_finalize(P, P->vt, energy_out, (int)sweep_blocks(P), s))) return rc;
+    P->have_state = true;
+    return BLR_OK;
+}
+
+// g = A v~ + pi(b) at the current point.
+int gradient_here(blr_plan *P, float *g, cudaStream_t s) {
+    int rc = sweep_adjoint(P, P->b, nullptr, s);
+    if (rc) return rc;
+    return dft_project(P, P->b, g, P->vt, s);
+}
+
+int hessvec_here(blr_plan *P, const float *dvt, float *hdv, cudaStream_t s) {
+    int rc = dft_expand(P, dvt, P->dv, 0, s);
+    if (rc) return rc;
+    if ((rc = sweep_incremental(P, s))) return rc;
+    if ((rc = sweep_adjoint(P, P->b, nullptr, s))) return rc;
+    return dft_project(P, P->b, hdv, dvt, s);
+}
+
+int pcg_run(blr_plan *P, const float *rhs, float *x, int maxit, double eta, int *iters,
+            double *relres, int *n_hv, cudaStream_t s) {
+    int rc = pcg_init(P, rhs, x, s);
+    if (rc) return rc;
+    if ((rc = fetch_scalars(P, s, nullptr))) return rc;
+    const double rr0 = P->hsc[SC_RR0];
+    int it = 0;
+    double rel = rr0 > 0 ? 1.0 : 0.0;
+    rc = BLR_OK;
+    while (rr0 > 0 && it < maxit) {
+        if ((rc = hessvec_here(P, P->pv, P->q, s))) break;
+        if (n_hv) ++*n_hv;
+        if ((rc = vec_dot(P, P->pv, P->q, nullptr, P->dsc + SC_PQ, s))) break;
+        if ((rc = pcg_update(P, x, s))) break;
+        if ((rc = fetch_scalars(P, s, nullptr))) break;
+        if (!(P->hsc[SC_PQ] > 0)) {
+            rc = isfinite(P->hsc[SC_PQ]) ? BLR_ECURV : BLR_ENAN;
+            break;
+        }
+        ++it;
+        rel = sqrt(P->hsc[SC_RR] / rr0);
+        if (!isfinite(rel)) {
+            rc = BLR_ENAN;
+            break;
+        }
+        if (rel <= eta) break;
+        if ((rc = pcg_direction(P, s))) break;
+    }
+    if (iters) *iters = it;
+    if (relres) *relres = rel;
+    return rc;
+}
+
+int check_plan(blr_plan_t P) { return P ? BLR_OK : BLR_EINVAL; }
+
+}  // namespace
+
+extern "C" {
+
+int blr_plan_create(const blr_params *p, blr_plan_t *out) {
+    if (!out) return BLR_EINVAL;
+    *out = nullptr;
+    int rc = validate(p);
+    if (rc) return rc;
+    blr_plan *P = new (std::nothrow) blr_plan();
+    if (!P) return BLR_ENOMEM;
+    P->p = *p;
+    P->N1 = p->n[0];
+    P->N2 = p->n[1];
+    P->N3 = p->n[2];
+    P->B1 = p->band[0];
+    P->B2 = p->band[1];
+    P->B3 = p->band[2];
+    P->V = (long long)P->N1 * P->N2 * P->N3;
+    P->nb = (long long)P->B1 * P->B2 * P->B3;
+    P->nfloat = 6 * P->nb;
+    P->dt = (float)(1.0 / p->nt);
+    P->grid = Grid3{P->N1, P->N2, P->N3, P->V};
+    long long nsweep = sweep_blocks(P);
+    long long nred = reduce_partials_needed();
+    P->npart = (int)(nsweep > nred ? nsweep : nred);
+    if (cudaGetDevice(&P->device) != cudaSuccess) {
+        delete P;
+        return BLR_ECUDA;
+    }
+    size_t bytes = layout(P, nullptr);
+    char *base = nullptr;
+    if (cudaMalloc(&base, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete P;
+        return BLR_ENOMEM;
+    }
+    layout(P, base);
+    if (cudaMallocHost(&P->hsc, (SC_COUNT + 1) * sizeof(double)) != cudaSuccess) {
+        cudaFree(base);
+        delete P;
+        return BLR_ENOMEM;
+    }
+    if (cudaMemset(base, 0, bytes) != cudaSuccess || sweep_setup() != BLR_OK ||
+        dft_init_tables(P, 0) != BLR_OK || cudaDeviceSynchronize() != cudaSuccess) {
+        cudaFreeHost(P->hsc);
+        cudaFree(base);
+        delete P;
+        return BLR_ECUDA;
+    }
+    *out = P;
+    return BLR_OK;
+}
+
+int blr_plan_destroy(blr_plan_t P) {
+    if (!P) return BLR_OK;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(P->device);
+    cudaError_t e1 = cudaFree(arena_base(P));
+    cudaError_t e2 = cudaFreeHost(P->hsc);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete P;
+    return (e1 == cudaSuccess && e2 == cudaSuccess) ? BLR_OK : BLR_ECUDA;
+}
+
+int blr_set_images(blr_plan_t P, const float *I0, const float *I1, blr_stream_t stream) {
+    if (check_plan(P) || !I0 || !I1) return BLR_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    BLR_CK(cudaMemcpyAsync(P->I0, I0, P->V * sizeof(float), cudaMemcpyDefault, s));
+    BLR_CK(cudaMemcpyAsync(P->I1, I1, P->V * sizeof(float), cudaMemcpyDefault, s));
+    P->have_state = false;
+    return BLR_OK;
+}
+
+int blr_expand(blr_plan_t P, const float *vt, float *v, blr_stream_t stream) {
+    if (check_plan(P) || !vt || !v) return BLR_EINVAL;
+    return dft_expand(P, vt, v, 0, (cudaStream_t)stream);
+}
+
+int blr_project(blr_plan_t P, const float *f, float *ft, blr_stream_t stream) {
+    if (check_plan(P) || !f || !ft) return BLR_EINVAL;
+    return dft_project(P, f, ft, nullptr, (cudaStream_t)stream);
+}
+
+int blr_state(blr_plan_t P, const float *vt, float *m1, double *energy, blr_stream_t stream) {
+    if (check_plan(P) || !vt) return BLR_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = state_at(P, vt, energy, s);
+    if (rc) return rc;
+    if (m1)
+        BLR_CK(cudaMemcpyAsync(m1, P->m + (long long)P->p.nt * P->V, P->V * sizeof(float),
+                               cudaMemcpyDeviceToDevice, s));
+    return BLR_OK;
+}
+
+int blr_adjoint(blr_plan_t P, float *b, float *lambda0, blr_stream_t stream) {
+    if (check_plan(P) || !b) return BLR_EINVAL;
+    if (!P->have_state) return BLR_ESTATE;
+    return sweep_adjoint(P, b, lambda0, (cudaStream_t)stream);
+}
+
+int blr_gradient(blr_plan_t P, const float *vt, float *g, double *energy, blr_stream_t stream) {
+    if (check_plan(P) || !vt || !g) return BLR_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = state_at(P, vt, energy, s);
+    if (rc) return rc;
+    return gradient_here(P, g, s);
+}
+
+int blr_hessvec(blr_plan_t P, const float *dvt, float *hdv, blr_stream_t stream) {
+    if (check_plan(P) || !dvt || !hdv) return BLR_EINVAL;
+    if (!P->have_state) return BLR_ESTATE;
+    return hessvec_here(P, dvt, hdv, (cudaStream_t)stream);
+}
+
+int blr_pcg(blr_plan_t P, const float *rhs, float *x, int maxit, double eta, int *iters,
+            double *relres, blr_stream_t stream) {
+    if (check_plan(P) || !rhs || !x || maxit < 0) return BLR_EINVAL;
+    if (!P->have_state) return BLR_ESTATE;
+    return pcg_run(P, rhs, x, maxit, eta, iters, relres, nullptr, (cudaStream_t)stream);
+}
+
+int blr_newton(blr_plan_t P, float *vt, int max_newton, int max_pcg, double gtol,
+               double forcing, blr_report *rep, blr_stream_t stream) {
+    if (check_plan(P) || !vt || max_newton < 0 || max_pcg < 0) return BLR_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    blr_report R;
+    memset(&R, 0, sizeof(R));
+    const size_t vbytes = P->nfloat * sizeof(float);
+    int flags = 0, rc;
+    BLR_CK(cudaMemsetAsync(P->dstatus, 0, sizeof(int), s));
+    BLR_CK(cudaMemcpyAsync(P->vtmp, vt, vbytes, cudaMemcpyDefault, s));
+    if ((rc = state_at(P, P->vtmp, nullptr, s))) return rc;
+    R.n_state = 1;
+    if ((rc = gradient_here(P, P->g, s))) return rc;
+    if ((rc = vec_maxabs(P, P->g, P->dsc + SC_GINF, s))) return rc;
+    if ((rc = vec_dot(P, P->g, P->g, nullptr, P->dsc + SC_DOT, s))) return rc;
+    if ((rc = fetch_scalars(P, s, &flags))) return rc;
+    if ((rc = flags_to_status(flags))) return rc;
+    double E = P->hsc[SC_E];
+    const double g0inf = P->hsc[SC_GINF], g0n = sqrt(P->hsc[SC_DOT]);
+    double ginf = g0inf, gn = g0n;
+    R.energy0 = E;
+    const double c1 = 1e-4;
+    for (int it = 0; it < max_newton; ++it) {
+        if (!(g0inf > 0) || ginf / g0inf < gtol) break;
+        const double eta = forcing >= 0 ? forcing : fmin(0.5, sqrt(gn / g0n));
+        // rhs = -g (exact: g + (-2) g)
+        if ((rc = vec_axpy(P, P->trial, P->g, P->g, -2.0, s))) break;
+        int its = 0;
+        double relres = 0;
+        rc = pcg_run(P, P->trial, P->step, max_pcg, eta, &its, &relres, &R.n_hessvec, s);
+        R.pcg_iters += its;
+        if (rc) break;
+        if ((rc = vec_dot(P, P->g, P->step, nullptr, P->dsc + SC_DOT, s))) break;
+        if ((rc = fetch_scalars(P, s, nullptr))) break;
+        const double slope = P->hsc[SC_DOT];
+        double eps = 1.0;
+        bool accepted = false;
+        for (int h = 0; h <= 10; ++h) {
+            if ((rc = vec_axpy(P, P->trial, P->vtmp, P->step, eps, s))) break;
+            if ((rc = state_at(P, P->trial, nullptr, s))) break;
+            ++R.n_state;
+            if ((rc = fetch_scalars(P, s, &flags))) break;
+            const double Et = P->hsc[SC_E];
+            if (flags == 0 && isfinite(Et) && Et <= E + c1 * eps * slope) {
+                accepted = true;
+                E = Et;
+                break;
+            }
+            eps *= 0.5;
+            ++R.n_halvings;
+        }
+        if (rc) break;
+        if (!accepted) {
+            // restore the last accepted point as the plan's current point
+            if ((rc = state_at(P, P->vtmp, nullptr, s))) break;
+            ++R.n_state;
+            break;
+        }
+        BLR_CK(cudaMemcpyAsync(P->vtmp, P->trial, vbytes, cudaMemcpyDeviceToDevice, s));
+        ++R.newton_iters;
+        if ((rc = gradient_here(P, P->g, s))) break;
+        if ((rc = vec_maxabs(P, P->g, P->dsc + SC_GINF, s))) break;
+        if ((rc = vec_dot(P, P->g, P->g, nullptr, P->dsc + SC_DOT, s))) break;
+        if ((rc = fetch_scalars(P, s, nullptr))) break;
+        ginf = P->hsc[SC_GINF];
+        gn = sqrt(P->hsc[SC_DOT]);
+    }
+    BLR_CK(cudaMemcpyAsync(vt, P->vtmp, vbytes, cudaMemcpyDefault, s));
+    BLR_CK(cudaStreamSynchronize(s));
+    R.energy = E;
+    R.grad_inf_rel = g0inf > 0 ? ginf / g0inf : 0.0;
+    R.status = rc;
+    if (rep) *rep = R;
+    return rc;
+}
+
+int blr_status(blr_plan_t P, blr_stream_t stream) {
+    if (check_plan(P)) return BLR_EINVAL;
+    int flags = 0;
+    int rc = fetch_scalars(P, (cudaStream_t)stream, &flags);
+    if (rc) return rc;
+    return flags_to_status(flags);
+}
+
+const char *blr_strerror(int code) {
+    switch (code) {
+        case BLR_OK: return "ok";
+        case BLR_EINVAL: return "invalid argument, shape or call order";
+        case BLR_ENOMEM: return "device allocation failed";
+        case BLR_ECUDA: return "CUDA runtime error";
+        case BLR_ECFL: return "displacement per time step reached one voxel (CFL bound)";
+        case BLR_ENAN: return "non-finite value";
+        case BLR_ESTATE: return "no forward solve at the current point (call blr_state first)";
+        case BLR_ECURV: return "PCG met non-positive curvature";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,109 @@
+// Internal definitions shared by the libblr translation units.
+//
+// Notation: fields are [N1][N2][N3] with N3 fastest; (i, j, k) index (x1, x2, x3).
+// Vector component c displaces along array axis c (component 0 along x1).
+// Band coefficients are interleaved complex [3][B1][B2][B3].
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/blr.h"
+
+#define BLR_CK(call)                                   \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return BLR_ECUDA;       \
+    } while (0)
+
+#define BLR_CK_LAUNCH() BLR_CK(cudaGetLastError())
+
+// Device-latched conditions (bit flags in blr_plan::dstatus).
+enum { BLR_FLAG_CFL = 1, BLR_FLAG_NAN = 2 };
+
+// Slots of the device scalar block blr_plan::dsc (doubles).
+enum {
+    SC_E = 0, SC_EREG = 1, SC_EDATA = 2,       // energy of blr_state
+    SC_RZ = 3, SC_PQ = 4, SC_RR = 5, SC_BETA = 6, SC_RR0 = 7,
+    SC_GINF = 8, SC_DOT = 9, SC_ALPHA = 10,
+    SC_COUNT = 16
+};
+
+// Sweep tile: TK x TJ x TI outputs per block (k fastest), halo of one voxel.
+constexpr int TK = 32, TJ = 8, TI = 8;
+constexpr int HK = TK + 2, HJ = TJ + 2, HI = TI + 2;
+constexpr int HJK = HJ * HK;
+constexpr int SWEEP_THREADS = TK * TJ;
+
+struct Grid3 {
+    int N1, N2, N3;
+    long long V;
+};
+
+struct blr_plan {
+    blr_params p;
+    int N1, N2, N3, B1, B2, B3;
+    long long V;       // voxels
+    long long nb;      // B1*B2*B3
+    long long nfloat;  // floats in one coefficient array: 2*3*nb
+    float dt;
+    int device;
+    Grid3 grid;
+
+    float *I0, *I1;
+    float *vt;          // current point (2*3*nb)
+    float *d;           // 3V displacement -dt*iota(vt), clamped to [-1, 1)
+    float *m;           // (nt+1)*V states
+    bool have_state;
+    float *lam[2];      // V each (adjoint / incremental adjoint ping-pong)
+    float *b;           // 3V body force
+    float *dv;          // 3V iota(dv~)
+    float *dm[2];       // V each (incremental state ping-pong)
+
+    // truncated-DFT tables and intermediates
+    float *W1;          // [2*B1][N1]: row 2j = cos, row 2j+1 = -sin (2 pi k_j x / N1)
+    float *T2c, *T2s;   // [B2][N2]
+    float *T3c, *T3s;   // [B3][N3]
+    float *A;           // [B1][B2][B3] regulariser weights
+    float *dft_big;     // 3*B1*N2*N3*2 floats
+    float *dft_small;   // 3*B1*B2*N3*2 floats
+
+    // Krylov / Newton vectors (nfloat each)
+    float *g, *r, *pv, *q, *x, *trial, *step, *vtmp;
+
+    double *dsc;        // device scalars (SC_COUNT)
+    double *hsc;        // pinned host mirror
+    int *dstatus;
+    double *partials;   // per-block partial sums
+    unsigned int *ticket;
+    int npart;
+};
+
+__host__ __device__ inline long long ceil_div_ll(long long a, long long b) { return (a + b - 1) / b; }
+
+// ---- launchers implemented in the .cu files (return BLR_OK / BLR_ECUDA) ----
+
+// dft.cu
+int dft_init_tables(blr_plan *P, cudaStream_t s);
+// iota into out (3V). mode 0: out = v; mode 1: out = clamp(-dt*v) + CFL/NaN flags.
+int dft_expand(blr_plan *P, const float *vt, float *out, int mode, cudaStream_t s);
+// pi(f) (+ A * vadd when vadd != nullptr) into ft.
+int dft_project(blr_plan *P, const float *f, float *ft, const float *vadd, cudaStream_t s);
+
+// sweeps.cu
+int sweep_setup();
+long long sweep_blocks(const blr_plan *P);
+int sweep_state(blr_plan *P, cudaStream_t s);                  // m^1..m^nt, lambda^nt, partials
+int sweep_adjoint(blr_plan *P, float *b, float *lambda0, cudaStream_t s);
+int sweep_incremental(blr_plan *P, cudaStream_t s);            // dm -> dlambda^nt in lam[0]
+
+// reduce.cu
+int energy_finalize(blr_plan *P, const float *vt, double *energy_out, int nblocks, cudaStream_t s);
+int vec_dot(blr_plan *P, const float *a, const float *b, const float *w, double *out, cudaStream_t s);
+int vec_maxabs(blr_plan *P, const float *a, double *out, cudaStream_t s);
+int pcg_init(blr_plan *P, const float *rhs, float *x, cudaStream_t s);
+int pcg_update(blr_plan *P, float *x, cudaStream_t s);
+int pcg_direction(blr_plan *P, cudaStream_t s);
+// y = a + alpha * x
+int vec_axpy(blr_plan *P, float *y, const float *a, const float *x, double alpha, cudaStream_t s);
+int reduce_partials_needed();

@@ -1,0 +1,253 @@
+// Reductions and Krylov vector updates on band coefficients (Sections 3.2, 3.4).
+//
+// Energy (Eq. 35): E = 1/2 sum A |v~|^2 + sigma^-2 sum_x (m^nt - I1)^2, FP64.
+// PCG (Eq. 55) with preconditioner K~ = 1/A: FP32 vectors, FP64 inner products
+// and step scalars kept on the device.  Every reduction writes one partial per
+// block and the last block to finish (ticket counter) sums the partials in
+// block order, so results do not depend on scheduling.
+#include "blr_internal.cuh"
+
+namespace {
+
+constexpr int RT = 256;        // threads of the vector kernels
+constexpr int RBLOCKS = 120;   // blocks of the vector kernels
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < NT / 32; ++w) t += red[w];
+    return t;   // valid in thread 0
+}
+
+// Returns true in every thread of the last block to arrive.
+__device__ __forceinline__ bool last_block(unsigned int *ticket) {
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    return is_last;
+}
+
+// Sum `count` partial slots (stride `stride`, offset `slot`) in block order.
+__device__ __forceinline__ double ordered_sum(const double *part, int count, int stride, int slot) {
+    double t = 0.0;
+    for (int i = 0; i < count; ++i) t += part[i * stride + slot];
+    return t;
+}
+
+__global__ void __launch_bounds__(1024)
+k_energy_finalize(const double *__restrict__ partials, int np, const float *__restrict__ vt,
+                  const float *__restrict__ A, long long nb, double inv_sigma2,
+                  double *__restrict__ sc, double *__restrict__ out, int *status) {
+    __shared__ double red[32];
+    double sd = 0.0;
+    for (int i = threadIdx.x; i < np; i += 1024) sd += partials[i];
+    sd = block_sum<1024>(sd, red);
+    double sr = 0.0;
+    for (long long i = threadIdx.x; i < 3 * nb; i += 1024) {
+        const double re = vt[2 * i], im = vt[2 * i + 1];
+        sr += (double)A[i % nb] * (re * re + im * im);
+    }
+    sr = block_sum<1024>(sr, red);
+    if (threadIdx.x == 0) {
+        const double edata = sd * inv_sigma2, ereg = 0.5 * sr, e = ereg + edata;
+        sc[SC_E] = e;
+        sc[SC_EREG] = ereg;
+        sc[SC_EDATA] = edata;
+        if (out) {
+            out[0] = e;
+            out[1] = ereg;
+            out[2] = edata;
+        }
+        if (!isfinite(e)) atomicOr(status, BLR_FLAG_NAN);
+    }
+}
+
+// out = sum a_i b_i (w == nullptr) or sum a_i b_i / w_{coef(i)} over 2*3*nb floats.
+__global__ void __launch_bounds__(RT)
+k_dot(const float *__restrict__ a, const float *__restrict__ b, const float *__restrict__ w,
+      long long n, long long nb, double *__restrict__ part, unsigned int *ticket,
+      double *__restrict__ out) {
+    __shared__ double red[RT / 32];
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT) {
+        double t = (double)a[i] * (double)b[i];
+        if (w) t /= (double)w[(i >> 1) % nb];
+        acc += t;
+    }
+    acc = block_sum<RT>(acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    if (last_block(ticket)) {
+        if (threadIdx.x == 0) {
+            *out = ordered_sum(part, gridDim.x, 1, 0);
+            *ticket = 0;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(RT)
+k_maxabs(const float *__restrict__ a, long long n, double *__restrict__ part,
+         unsigned int *ticket, double *__restrict__ out) {
+    __shared__ float red[RT / 32];
+    float m = 0.f;
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT)
+        m = fmaxf(m, fabsf(a[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < RT / 32; ++w) t = fmaxf(t, red[w]);
+        part[blockIdx.x] = (double)t;
+    }
+    if (last_block(ticket)) {
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (unsigned i = 0; i < gridDim.x; ++i) t = fmax(t, part[i]);
+            *out = t;
+            *ticket = 0;
+        }
+    }
+}
+
+// x = 0, r = rhs, p = rhs / A; rz = <r, r/A>, rr = <r, r>, rr0 = rr.
+__global__ void __launch_bounds__(RT)
+k_pcg_init(const float *__restrict__ rhs, float *__restrict__ x, float *__restrict__ r,
+           float *__restrict__ p, const float *__restrict__ A, long long n, long long nb,
+           double *__restrict__ part, unsigned int *ticket, double *__restrict__ sc) {
+    __shared__ double red[RT / 32];
+    double rz = 0.0, rr = 0.0;
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT) {
+        const float ri = rhs[i];
+        const float a = A[(i >> 1) % nb];
+        x[i] = 0.f;
+        r[i] = ri;
+        p[i] = ri / a;
+        rz += (double)ri * (double)ri / (double)a;
+        rr += (double)ri * (double)ri;
+    }
+    rz = block_sum<RT>(rz, red);
+    if (threadIdx.x == 0) part[2 * blockIdx.x] = rz;
+    rr = block_sum<RT>(rr, red);
+    if (threadIdx.x == 0) part[2 * blockIdx.x + 1] = rr;
+    if (last_block(ticket)) {
+        if (threadIdx.x == 0) {
+            sc[SC_RZ] = ordered_sum(part, gridDim.x, 2, 0);
+            sc[SC_RR] = sc[SC_RR0] = ordered_sum(part, gridDim.x, 2, 1);
+            *ticket = 0;
+        }
+    }
+}
+
+// alpha = rz / <p, q>; x += alpha p; r -= alpha q; rz' = <r, r/A>, rr = <r, r>;
+// beta = rz' / rz.
+__global__ void __launch_bounds__(RT)
+k_pcg_update(float *__restrict__ x, float *__restrict__ r, const float *__restrict__ p,
+             const float *__restrict__ q, const float *__restrict__ A, long long n, long long nb,
+             double *__restrict__ part, unsigned int *ticket, double *__restrict__ sc) {
+    __shared__ double red[RT / 32];
+    const double alpha_d = sc[SC_RZ] / sc[SC_PQ];
+    const float alpha = (float)alpha_d;
+    double rz = 0.0, rr = 0.0;
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT) {
+        x[i] = fmaf(alpha, p[i], x[i]);
+        const float ri = fmaf(-alpha, q[i], r[i]);
+        r[i] = ri;
+        const double a = (double)A[(i >> 1) % nb];
+        rz += (double)ri * (double)ri / a;
+        rr += (double)ri * (double)ri;
+    }
+    rz = block_sum<RT>(rz, red);
+    if (threadIdx.x == 0) part[2 * blockIdx.x] = rz;
+    rr = block_sum<RT>(rr, red);
+    if (threadIdx.x == 0) part[2 * blockIdx.x + 1] = rr;
+    if (last_block(ticket)) {
+        if (threadIdx.x == 0) {
+            const double rz_new = ordered_sum(part, gridDim.x, 2, 0);
+            sc[SC_BETA] = rz_new / sc[SC_RZ];
+            sc[SC_ALPHA] = alpha_d;
+            sc[SC_RZ] = rz_new;
+            sc[SC_RR] = ordered_sum(part, gridDim.x, 2, 1);
+            *ticket = 0;
+        }
+    }
+}
+
+// p = r / A + beta p.
+__global__ void __launch_bounds__(RT)
+k_pcg_direction(float *__restrict__ p, const float *__restrict__ r, const float *__restrict__ A,
+                long long n, long long nb, const double *__restrict__ sc) {
+    const float beta = (float)sc[SC_BETA];
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT)
+        p[i] = fmaf(beta, p[i], r[i] / A[(i >> 1) % nb]);
+}
+
+// y = a + alpha x (FP32; alpha from the host).
+__global__ void __launch_bounds__(RT)
+k_axpy(float *__restrict__ y, const float *__restrict__ a, const float *__restrict__ x,
+       float alpha, long long n) {
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT)
+        y[i] = fmaf(alpha, x[i], a[i]);
+}
+
+int vec_blocks(const blr_plan *P) {
+    long long b = ceil_div_ll(P->nfloat, RT);
+    return (int)(b < RBLOCKS ? (b < 1 ? 1 : b) : RBLOCKS);
+}
+
+}  // namespace
+
+int reduce_partials_needed() { return 2 * RBLOCKS; }
+
+int energy_finalize(blr_plan *P, const float *vt, double *energy_out, int nblocks, cudaStream_t s) {
+    k_energy_finalize<<<1, 1024, 0, s>>>(P->partials, nblocks, vt, P->A, P->nb,
+                                         1.0 / (P->p.sigma * P->p.sigma), P->dsc, energy_out,
+                                         P->dstatus);
+    BLR_CK_LAUNCH();
+    return BLR_OK;
+}
+
+int vec_dot(blr_plan *P, const float *a, const float *b, const float *w, double *out, cudaStream_t s) {
+    k_dot<<<vec_blocks(P), RT, 0, s>>>(a, b, w, P->nfloat, P->nb, P->partials, P->ticket, out);
+    BLR_CK_LAUNCH();
+    return BLR_OK;
+}
+
+int vec_maxabs(blr_plan *P, const float *a, double *out, cudaStream_t s) {
+    k_maxabs<<<vec_blocks(P), RT, 0, s>>>(a, P->nfloat, P->partials, P->ticket, out);
+    BLR_CK_LAUNCH();
+    return BLR_OK;
+}
+
+int pcg_init(blr_plan *P, const float *rhs, float *x, cudaStream_t s) {
+    k_pcg_init<<<vec_blocks(P), RT, 0, s>>>(rhs, x, P->r, P->pv, P->A, P->nfloat, P->nb,
+                                            P->partials, P->ticket, P->dsc);
+    BLR_CK_LAUNCH();
+    return BLR_OK;
+}
+
+int pcg_update(blr_plan *P, float *x, cudaStream_t s) {
+    k_pcg_update<<<vec_blocks(P), RT, 0, s>>>(x, P->r, P->pv, P->q, P->A, P->nfloat, P->nb,
+                                              P->partials, P->ticket, P->dsc);
+    BLR_CK_LAUNCH();
+    return BLR_OK;
+}
+
+int pcg_direction(blr_plan *P, cudaStream_t s) {
+    k_pcg_direction<<<vec_blocks(P), RT, 0, s>>>(P->pv, P->r, P->A, P->nfloat, P->nb, P->dsc);
+    BLR_CK_LAUNCH();
+    return BLR_OK;
+}
+
+int vec_axpy(blr_plan *P, float *y, const float *a, const float *x, double alpha, cudaStream_t s) {
+    k_axpy<<<vec_blocks(P), RT, 0, s>>>(y, a, x, (float)alpha, P->nfloat);
+    BLR_CK_LAUNCH();
+    return BLR_OK;
+}
