@@ -1,0 +1,443 @@
+#!/usr/bin/env python3
+"""Throughput of band-limited PDE-LDDMM Gauss-Newton-Krylov registration on GB300.
+
+One step = one full registration of a synthetic 128^3 brain-like phantom pair
+(band 32^3, 10 time steps) through the library's public call blr_newton:
+10 Newton updates, each with a gradient (expand, state sweep, energy, adjoint
+sweep with body force, project, regulariser), 20 PCG iterations of
+Gauss-Newton Hessian-vector products (expand, incremental state, incremental
+adjoint, project) with FP64 inner products, and an Armijo line search
+(forward solves + FP64 energies).  The PCG tolerance is 0 and the gradient
+tolerance is 0, so every step does the same fixed work.
+
+Printed: one JSON line (rank 0).  `value` = registrations/s over all ranks
+(device time of K timed steps, inputs resident, L2 flushed between steps);
+`hvp_per_s` = Gauss-Newton HVP/s at the registration's final point; `e2e` =
+the same registration metric with host buffers (pinned) through the C-ABI;
+`roofline` = the adjoint sweep kernel against the measured HBM copy bandwidth;
+`cpu_baseline` = the FP64 oracle on the host cores, timed on a bounded sample.
+
+`--impl reference` times the FP64 oracle alone (host cores) on the same
+workload and prints the same line with "impl": "reference".
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gauss-Newton HVP/s and registrations/s at 128³, mixed vs FP32, at ≤5e-4 error"
+N = (128, 128, 128)
+BAND = (32, 32, 32)
+NT = 10
+NEWTON = 10
+PCG = 20
+SEED = 2000
+MAX_DISP = 6.0
+SAMPLE_BOUND = 120.0      # coefficient bound of the HVP sample point (CFL ~0.6 voxel)
+WORKLOAD = ("128^3 phantom pair (3 nested ellipsoids, blur 1 voxel, noise 0.01, "
+            "6-voxel warp), band 32^3, 10 time steps, Gauss-Newton-Krylov "
+            "10 Newton x 20 PCG (fixed work), Armijo")
+# Adjoint sweep step: read lambda^{n+1} 4 B, d 12 B, m^n 4 B, body force read 12 B
+# + write 12 B, write lambda^n 4 B = 48 B/voxel; the first step of a solve does
+# not read b (36 B), the last does not write lambda (44 B).
+ADJ_BYTES = lambda nt: ((36 + 44 + 48 * (nt - 2)) if nt > 1 else 32)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# oracle sample (runs in a fresh single-threaded process)
+# ----------------------------------------------------------------------------
+
+
+def oracle_sample(out_path: str, samples: int):
+    import numpy as np
+
+    from oracle import blr_oracle as O
+    from paper_1807_05117_gb300 import synth
+
+    I0, I1, _ = synth.phantom_pair(N, SEED, max_disp=MAX_DISP)
+    vt = synth.random_coefficients(BAND, SEED + 1, SAMPLE_BOUND)
+    dvt = synth.random_direction(BAND, SEED + 2)
+    (_, I0d), (_, I1d), (_, vtd), (_, dvd) = synth.as_device_inputs(I0, I1, vt, dvt)
+    p = O.Params(N, BAND, NT)
+    times = []
+    for _ in range(samples):
+        t0 = time.perf_counter()
+        pt = O.Point(vtd, I0d, I1d, p)
+        t1 = time.perf_counter()
+        g = pt.gradient()[0]
+        t2 = time.perf_counter()
+        h = pt.gn_hessvec(dvd)[0]
+        t3 = time.perf_counter()
+        times.append((t1 - t0, t2 - t1, t3 - t2))
+    np.savez(out_path, times=np.array(times), g=g, h=h, energy=pt.energy)
+
+
+def run_oracle_subprocess(samples: int):
+    import numpy as np
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    fd, path = tempfile.mkstemp(suffix=".npz")
+    os.close(fd)
+    try:
+        subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", path,
+                        "--samples", str(samples)], check=True, env=env, cwd=ROOT)
+        with np.load(path) as z:
+            return {k: z[k] for k in z.files}
+    finally:
+        os.unlink(path)
+
+
+def registration_seconds(t_state, t_grad, t_hvp, n_state, n_grad, n_hvp):
+    return n_state * t_state + n_grad * t_grad + n_hvp * t_hvp
+
+
+# nominal operation counts of one fixed-work registration (no line-search halvings)
+NOMINAL_COUNTS = dict(n_state=NEWTON + 1, n_grad=NEWTON + 1, n_hvp=NEWTON * PCG)
+
+
+def config(precision: str, world: int):
+    return {"workload": WORKLOAD, "grid": list(N), "band": list(BAND), "nt": NT,
+            "newton": NEWTON, "pcg": PCG, "precision": precision,
+            "l2": "flushed between timed steps (512 MiB write); the step's working set "
+                  "(~230 MB) also exceeds L2",
+            "parallelism": f"replicas x{world} (one independent pair per GPU)"}
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ----------------------------------------------------------------------------
+
+
+def main_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    res = run_oracle_subprocess(args.warmup + args.steps)
+    t = res["times"][args.warmup:]
+    per = [registration_seconds(a, b, c, **NOMINAL_COUNTS) for a, b, c in t]
+    s_per_reg = sum(per) / len(per)
+    value = 1.0 / s_per_reg
+    sample = (f"per step: one FP64 forward solve, gradient and Gauss-Newton HVP at 128^3 "
+              f"(band 32^3, nt 10), scaled by the registration's nominal counts "
+              f"{NOMINAL_COUNTS}; oracle wall time {sum(sum(x) for x in t) / len(t):.2f} s per sample")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "registrations/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * s_per_reg, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config("f64 oracle", 1),
+            "cpu_baseline": {"value": value, "unit": "registrations/s", "cores": 1,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "registrations/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, index=None):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        if index is not None:
+            mine = [r for r in rows if r[0] == str(index)]
+            rows = mine or rows
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def main_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1807_05117_gb300 import blr, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    precision = blr.BLR_MIXED if args.precision == "mixed" else blr.BLR_FP32
+
+    I0, I1, _ = synth.phantom_pair(N, SEED + 1000 * rank, max_disp=MAX_DISP)
+    (I0f, _), (I1f, _) = synth.as_device_inputs(I0, I1)
+    I0g, I1g = torch.from_numpy(I0f).to(dev), torch.from_numpy(I1f).to(dev)
+    plan = blr.Plan(N, BAND, NT, precision=precision)
+    plan.set_images(I0g, I1g)
+    vt = torch.zeros((3,) + BAND, dtype=torch.complex64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        vt.zero_()
+        return plan.newton(vt, NEWTON, PCG, 0.0, 0.0)
+
+    for _ in range(args.warmup):
+        step()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler()
+    barrier()
+    sampler.start()
+    launches0 = blr.blr_kernel_launches()
+    total_ms = 0.0
+    rep = None
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rep = step()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    launches = blr.blr_kernel_launches() - launches0
+    barrier()
+    clocks = sampler.stop(local)
+    ms = total_ms / max(args.steps, 1)
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 1000.0 / ms
+
+    # Gauss-Newton HVP/s at the final point of the last registration
+    dvt = torch.from_numpy(synth.random_direction(BAND, SEED + 2).astype(np.complex64)).to(dev)
+    hout = torch.empty_like(dvt)
+    for _ in range(3):
+        plan.hessvec(dvt, hout)
+    reps = args.hvp_reps
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        plan.hessvec(dvt, hout)
+    e1.record(stream)
+    e1.synchronize()
+    hvp_ms = e0.elapsed_time(e1) / reps
+
+    # roofline of the dominant kernel (adjoint sweep step): blr_adjoint launches
+    # exactly nt adjoint-step kernels and nothing else
+    bforce = torch.empty((3,) + N, dtype=torch.float32, device=dev)
+    for _ in range(2):
+        plan.adjoint(bforce)
+    areps = 20
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(areps):
+        plan.adjoint(bforce)
+    e1.record(stream)
+    e1.synchronize()
+    adj_launch_s = e0.elapsed_time(e1) / 1000.0 / (areps * NT)
+    V = N[0] * N[1] * N[2]
+    adj_bytes = ADJ_BYTES(NT) * V / NT
+    peak, peak_kind = peaks()
+    achieved = adj_bytes / adj_launch_s / 1e9
+    roofline = {"kernel": "k_adjoint_step", "bound": "hbm", "achieved": achieved,
+                "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": f"{peak_kind} hbm_gbs (copy, burst)",
+                "algorithmic_bytes_per_launch": adj_bytes, "launch_us": adj_launch_s * 1e6,
+                "traffic": args.adjoint_traffic}
+
+    line = {"metric": METRIC, "value": value, "unit": "registrations/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic", "config": config(args.precision, world),
+            "hvp_per_s": world * 1000.0 / hvp_ms, "hvp_ms": hvp_ms,
+            "gpu_launches": int(launches), "roofline": roofline, "clocks": clocks,
+            "report": {k: getattr(rep, k) for k in ("newton_iters", "pcg_iters", "n_state",
+                                                     "n_hessvec", "n_halvings", "energy0",
+                                                     "energy", "grad_inf_rel")}}
+
+    # end to end through the C-ABI with pinned host buffers
+    if not args.no_e2e:
+        hI0 = torch.from_numpy(I0f).pin_memory()
+        hI1 = torch.from_numpy(I1f).pin_memory()
+        hvt = torch.zeros((3,) + BAND, dtype=torch.complex64).pin_memory()
+
+        def e2e_step():
+            hvt.zero_()
+            plan.set_images(hI0, hI1)
+            return plan.newton(hvt, NEWTON, PCG, 0.0, 0.0)
+
+        e2e_step()
+        barrier()
+        tot = 0.0
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            e0.record(stream)
+            e2e_step()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        e2e_ms = tot / max(args.steps, 1)
+        if dist is not None:
+            t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        line["e2e"] = {"value": world * 1000.0 / e2e_ms, "unit": "registrations/s",
+                       "ms_per_step": e2e_ms,
+                       "h2d_bytes_per_step": 2 * I0f.nbytes + hvt.numel() * 8,
+                       "d2h_bytes_per_step": hvt.numel() * 8}
+
+    # FP64 oracle on the host cores (rank 0, one GPU only) and the HVP error
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res = run_oracle_subprocess(1)
+        ts, tg, th = res["times"][0]
+        counts = dict(n_state=rep.n_state, n_grad=rep.newton_iters + 1, n_hvp=rep.n_hessvec)
+        sec = registration_seconds(ts, tg, th, **counts)
+        line["cpu_baseline"] = {
+            "value": 1.0 / sec, "unit": "registrations/s", "cores": 1, "kind": "oracle",
+            "sample": (f"one FP64 forward solve ({ts:.2f} s), gradient ({tg:.2f} s) and "
+                       f"Gauss-Newton HVP ({th:.2f} s) at 128^3, single thread, scaled by "
+                       f"this run's operation counts {counts}")}
+        # the sample point on the GPU, for the FP32-vs-FP64 errors
+        vt_s = synth.random_coefficients(BAND, SEED + 1, SAMPLE_BOUND)
+        I0s, I1s, _ = synth.phantom_pair(N, SEED, max_disp=MAX_DISP)
+        (a, _), (b, _), (c, _) = synth.as_device_inputs(I0s, I1s, vt_s)
+        plan.set_images(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev))
+        g = torch.empty_like(dvt)
+        plan.gradient(torch.from_numpy(c).to(dev), g)
+        plan.hessvec(dvt, hout)
+        gref, href = res["g"], res["h"]
+        line["hvp_rel_err"] = float(np.linalg.norm(hout.cpu().numpy() - href) / np.linalg.norm(href))
+        line["grad_rel_err"] = float(np.linalg.norm(g.cpu().numpy() - gref) / np.linalg.norm(gref))
+        line["cpu_baseline"]["hvp_per_s"] = 1.0 / th
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def probe():
+    """A few launches of every hot-path kernel at the benchmark size, for ncu."""
+    import numpy as np
+    import torch
+
+    from paper_1807_05117_gb300 import blr, synth
+
+    dev = torch.device("cuda", 0)
+    I0, I1, _ = synth.phantom_pair(N, SEED, max_disp=MAX_DISP)
+    vt = synth.random_coefficients(BAND, SEED + 1, SAMPLE_BOUND)
+    dvt = synth.random_direction(BAND, SEED + 2)
+    (a, _), (b, _), (c, _), (d, _) = synth.as_device_inputs(I0, I1, vt, dvt)
+    with blr.Plan(N, BAND, NT) as plan:
+        plan.set_images(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev))
+        g = torch.empty((3,) + BAND, dtype=torch.complex64, device=dev)
+        plan.gradient(torch.from_numpy(c).to(dev), g)
+        h = torch.empty_like(g)
+        dv = torch.from_numpy(d).to(dev)
+        for _ in range(3):
+            plan.hessvec(dv, h)
+        bf = torch.empty((3,) + N, dtype=torch.float32, device=dev)
+        for _ in range(2):
+            plan.adjoint(bf)
+        torch.cuda.synchronize()
+        assert plan.status() == blr.BLR_OK
+    print("probe ok", float(np.abs(h.cpu().numpy()).max()))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "mixed"], default="fp32")
+    ap.add_argument("--hvp-reps", type=int, default=50)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--adjoint-traffic", type=float, default=None,
+                    help="dram bytes per adjoint-step launch from an ncu capture of this kernel")
+    ap.add_argument("--probe", action="store_true",
+                    help="short run for profilers: one gradient, 3 HVPs, 2 adjoint solves")
+    ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--samples", type=int, default=1, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.oracle_sample:
+        oracle_sample(args.oracle_sample, args.samples)
+        return 0
+    if args.probe:
+        return probe()
+    if args.impl == "reference":
+        return main_reference(args)
+    return main_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

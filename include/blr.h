@@ -184,6 +184,10 @@ int blr_newton(blr_plan_t plan, float *vt, int max_newton, int max_pcg,
  * (BLR_ECFL, BLR_ENAN) or BLR_OK, and clear it. */
 int blr_status(blr_plan_t plan, blr_stream_t stream);
 
+/* Diagnostic (no counterpart in the paper): number of kernels this library
+ * has launched since it was loaded, over all plans and threads. */
+unsigned long long blr_kernel_launches(void);
+
 /* Human-readable text for a status code (static storage). */
 const char *blr_strerror(int code);
 

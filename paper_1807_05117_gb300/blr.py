@@ -71,7 +71,7 @@ _SIGS = {
 }
 
 #: every symbol include/blr.h declares
-EXPORTED = tuple(_SIGS) + ("blr_strerror",)
+EXPORTED = tuple(_SIGS) + ("blr_strerror", "blr_kernel_launches")
 
 
 def _load():
@@ -84,6 +84,8 @@ def _load():
         fn.restype = ctypes.c_int
     lib.blr_strerror.argtypes = [ctypes.c_int]
     lib.blr_strerror.restype = ctypes.c_char_p
+    lib.blr_kernel_launches.argtypes = []
+    lib.blr_kernel_launches.restype = ctypes.c_ulonglong
     return lib
 
 
@@ -92,6 +94,10 @@ _lib = _load()
 
 def blr_strerror(code: int) -> str:
     return _lib.blr_strerror(int(code)).decode()
+
+
+def blr_kernel_launches() -> int:
+    return int(_lib.blr_kernel_launches())
 
 
 def _check(rc: int, where: str):

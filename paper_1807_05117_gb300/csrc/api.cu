@@ -11,6 +11,8 @@
 
 #include "blr_internal.cuh"
 
+unsigned long long g_blr_launches = 0;
+
 namespace {
 
 int validate(const blr_params *p) {
@@ -361,6 +363,10 @@ int blr_status(blr_plan_t P, blr_stream_t stream) {
     int rc = fetch_scalars(P, (cudaStream_t)stream, &flags);
     if (rc) return rc;
     return flags_to_status(flags);
+}
+
+unsigned long long blr_kernel_launches(void) {
+    return __atomic_load_n(&g_blr_launches, __ATOMIC_RELAXED);
 }
 
 const char *blr_strerror(int code) {

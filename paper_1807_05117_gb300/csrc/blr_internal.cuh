@@ -16,7 +16,13 @@
         if (e_ != cudaSuccess) return BLR_ECUDA;       \
     } while (0)
 
-#define BLR_CK_LAUNCH() BLR_CK(cudaGetLastError())
+// Every kernel launch of the library is counted (blr_kernel_launches()).
+extern unsigned long long g_blr_launches;
+#define BLR_CK_LAUNCH()                                                   \
+    do {                                                                  \
+        __atomic_fetch_add(&g_blr_launches, 1ULL, __ATOMIC_RELAXED);      \
+        BLR_CK(cudaGetLastError());                                       \
+    } while (0)
 
 // Device-latched conditions (bit flags in blr_plan::dstatus).
 enum { BLR_FLAG_CFL = 1, BLR_FLAG_NAN = 2 };
