@@ -184,6 +184,33 @@ int blr_newton(blr_plan_t plan, float *vt, int max_newton, int max_pcg,
  * (BLR_ECFL, BLR_ENAN) or BLR_OK, and clear it. */
 int blr_status(blr_plan_t plan, blr_stream_t stream);
 
+/* Allocation-free iota.  The paper has no counterpart: this is a convenience of
+ * the library for callers that cannot allocate device memory, such as a host
+ * framework that owns every device allocation through its own pool (nothing else
+ * may call cudaMalloc, so its accounting stays exact) or a latency-critical loop
+ * that cannot accept cudaMalloc / cudaFree, which may synchronise the device.
+ * Result: the same field as blr_expand for the same grid and band.
+ * n, band: host arrays of 3 ints with the rules of blr_params (band even,
+ *          2 <= band[d] <= n[d], band[2] <= 64).
+ * vt     : device, 2*3*B1*B2*B3 floats;  v: device, 3*N1*N2*N3 floats, written.
+ * Storage: no plan and no allocation.  The DFT tables and intermediates live in
+ *   one fixed device array of BLR_NOALLOC_SCRATCH_BYTES that the library keeps
+ *   in every GPU that loads it until the process exits.  A call needs
+ *   4 * (2 B1 N1 + 2 B2 N2 + 2 B3 N3 + B1 B2 B3 + 6 B1 B2 N3 + 6 B1 N2 N3) bytes
+ *   (each term rounded up to 256 bytes); larger problems are rejected with
+ *   BLR_EINVAL before anything runs (a 128^3 grid with a 32^3 band fits).
+ * Set-up: the first call on each device, with that device current, looks up
+ *   the array's device address (cudaGetSymbolAddress); make that first call
+ *   before any stream capture.
+ * Sharing: every call on a device uses the same array.  Calls whose work
+ *   overlaps on the GPU (other streams, other host threads) race and corrupt
+ *   each other's results: order them on one stream.  Each call writes every
+ *   scratch element before reading it, so nothing carries over between calls.
+ * Never calls cudaMalloc, cudaFree or any allocating routine. */
+#define BLR_NOALLOC_SCRATCH_BYTES (16u << 20)
+int blr_expand_noalloc(const int n[3], const int band[3], const float *vt, float *v,
+                       blr_stream_t stream);
+
 /* Diagnostic (no counterpart in the paper): number of kernels this library
  * has launched since it was loaded, over all plans and threads. */
 unsigned long long blr_kernel_launches(void);

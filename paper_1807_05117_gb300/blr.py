@@ -71,7 +71,7 @@ _SIGS = {
 }
 
 #: every symbol include/blr.h declares
-EXPORTED = tuple(_SIGS) + ("blr_strerror", "blr_kernel_launches")
+EXPORTED = tuple(_SIGS) + ("blr_strerror", "blr_kernel_launches", "blr_expand_noalloc")
 
 
 def _load():
@@ -86,6 +86,9 @@ def _load():
     lib.blr_strerror.restype = ctypes.c_char_p
     lib.blr_kernel_launches.argtypes = []
     lib.blr_kernel_launches.restype = ctypes.c_ulonglong
+    lib.blr_expand_noalloc.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       _P, _P, _P]
+    lib.blr_expand_noalloc.restype = ctypes.c_int
     return lib
 
 
@@ -165,6 +168,17 @@ def blr_expand(plan, vt, v, stream=None):
     import torch
     _check(_lib.blr_expand(_P(plan), _ptr(vt, dtype=torch.complex64, name="vt"),
                            _ptr(v, dtype=torch.float32, name="v"), _stream(stream)), "blr_expand")
+
+
+def blr_expand_noalloc(n, band, vt, v, stream=None):
+    """iota without a plan and without allocating (see include/blr.h): the
+    library's fixed device scratch array holds the tables and intermediates."""
+    import torch
+    cn = (ctypes.c_int * 3)(*[int(x) for x in n])
+    cb = (ctypes.c_int * 3)(*[int(x) for x in band])
+    _check(_lib.blr_expand_noalloc(cn, cb, _ptr(vt, dtype=torch.complex64, name="vt"),
+                                   _ptr(v, dtype=torch.float32, name="v"), _stream(stream)),
+           "blr_expand_noalloc")
 
 
 def blr_project(plan, f, ft, stream=None):
