@@ -181,13 +181,14 @@ int blr_plan_create(const blr_params *p, blr_plan_t *out) {
     P->nfloat = 6 * P->nb;
     P->dt = (float)(1.0 / p->nt);
     P->grid = Grid3{P->N1, P->N2, P->N3, P->V};
-    long long nsweep = sweep_blocks(P);
-    long long nred = reduce_partials_needed();
-    P->npart = (int)(nsweep > nred ? nsweep : nred);
     if (cudaGetDevice(&P->device) != cudaSuccess) {
         delete P;
         return BLR_ECUDA;
     }
+    sweep_setup(P);
+    long long nsweep = sweep_blocks(P);
+    long long nred = reduce_partials_needed();
+    P->npart = (int)(nsweep > nred ? nsweep : nred);
     size_t bytes = layout(P, nullptr);
     char *base = nullptr;
     if (cudaMalloc(&base, bytes) != cudaSuccess) {
@@ -201,7 +202,7 @@ int blr_plan_create(const blr_params *p, blr_plan_t *out) {
         delete P;
         return BLR_ENOMEM;
     }
-    if (cudaMemset(base, 0, bytes) != cudaSuccess || sweep_setup() != BLR_OK ||
+    if (cudaMemset(base, 0, bytes) != cudaSuccess ||
         dft_init_tables(P, 0) != BLR_OK || cudaDeviceSynchronize() != cudaSuccess) {
         cudaFreeHost(P->hsc);
         cudaFree(base);

@@ -35,12 +35,6 @@ enum {
     SC_COUNT = 16
 };
 
-// Sweep tile: TK x TJ x TI outputs per block (k fastest), halo of one voxel.
-constexpr int TK = 32, TJ = 8, TI = 8;
-constexpr int HK = TK + 2, HJ = TJ + 2, HI = TI + 2;
-constexpr int HJK = HJ * HK;
-constexpr int SWEEP_THREADS = TK * TJ;
-
 struct Grid3 {
     int N1, N2, N3;
     long long V;
@@ -54,6 +48,7 @@ struct blr_plan {
     long long nfloat;  // floats in one coefficient array: 2*3*nb
     float dt;
     int device;
+    int chunk;          // x1 planes per sweep block (set by sweep_setup)
     Grid3 grid;
 
     float *I0, *I1;
@@ -97,7 +92,7 @@ int dft_expand(blr_plan *P, const float *vt, float *out, int mode, cudaStream_t 
 int dft_project(blr_plan *P, const float *f, float *ft, const float *vadd, cudaStream_t s);
 
 // sweeps.cu
-int sweep_setup();
+int sweep_setup(blr_plan *P);
 long long sweep_blocks(const blr_plan *P);
 int sweep_state(blr_plan *P, cudaStream_t s);                  // m^1..m^nt, lambda^nt, partials
 int sweep_adjoint(blr_plan *P, float *b, float *lambda0, cudaStream_t s);

@@ -10,63 +10,45 @@
 // give the exact transpose S^T as a 27-neighbour gather, so the adjoint needs
 // no atomics and is deterministic.
 //
-// Every kernel stages the fields it interpolates in shared memory as a tile of
-// TI x TJ x TK voxels plus a one-voxel halo (periodic wrap on load); the
-// per-voxel inputs (d, dv) and outputs stream through registers.
+// Every kernel marches along x1: a block owns a 32 (x3) x MJ (x2) column of
+// voxels over a chunk of x1 planes and keeps a ring of one-voxel-haloed planes
+// in shared memory (periodic wrap on load), filled by cp.async two planes ahead
+// of use; per-voxel operands of the next output plane are prefetched into
+// registers.  In the adjoint each source plane is
+// read once and scattered in registers into the three output planes it reaches,
+// so a voxel costs 9 shared-memory reads instead of 27.
 #include "blr_internal.cuh"
 
 namespace {
+
+constexpr int MK = 32;            // x3 extent of a block (one warp)
+constexpr int MJ = 8;             // x2 extent of a block
+constexpr int MHK = MK + 2, MHJ = MJ + 2, MHP = MHJ * MHK;   // haloed plane
+constexpr int MT = MK * MJ;       // threads per block
+static_assert(MHP <= 2 * MT, "two halo slots per thread");
 
 __device__ __forceinline__ int wrapi(int i, int N) {
     int r = i % N;
     return r < 0 ? r + N : r;
 }
 
-// Offsets (within one x1-plane) of the halo positions p and p + SWEEP_THREADS.
-struct PlaneSlots {
+// In-plane offsets (wrapped x2, x3) of the halo positions tid and tid + MT.
+struct Slots {
     long long off0, off1;
     bool ok1;
 };
 
-__device__ __forceinline__ PlaneSlots plane_slots(const Grid3 &g, int k0, int j0) {
-    PlaneSlots ps;
+__device__ __forceinline__ Slots plane_slots(const Grid3 &g, int k0, int j0) {
+    Slots ps;
     int p = threadIdx.x;
-    int hj = p / HK, hk = p - hj * HK;
+    int hj = p / MHK, hk = p - hj * MHK;
     ps.off0 = (long long)wrapi(j0 + hj - 1, g.N2) * g.N3 + wrapi(k0 + hk - 1, g.N3);
-    p += SWEEP_THREADS;
-    ps.ok1 = p < HJK;
-    hj = p / HK;
-    hk = p - hj * HK;
+    p += MT;
+    ps.ok1 = p < MHP;
+    hj = p / MHK;
+    hk = p - hj * MHK;
     ps.off1 = ps.ok1 ? (long long)wrapi(j0 + hj - 1, g.N2) * g.N3 + wrapi(k0 + hk - 1, g.N3) : 0;
     return ps;
-}
-
-__device__ __forceinline__ void load_scalar_halo(float *s, const float *__restrict__ f,
-                                                 const Grid3 &g, const PlaneSlots &ps, int i0) {
-    const long long plane = (long long)g.N2 * g.N3;
-    for (int hi = 0; hi < HI; ++hi) {
-        const float *fp = f + (long long)wrapi(i0 + hi - 1, g.N1) * plane;
-        s[hi * HJK + threadIdx.x] = __ldg(fp + ps.off0);
-        if (ps.ok1) s[hi * HJK + threadIdx.x + SWEEP_THREADS] = __ldg(fp + ps.off1);
-    }
-}
-
-// (d0, d1, d2, lambda) per halo voxel.
-__device__ __forceinline__ void load_dlam_halo(float4 *s, const float *__restrict__ d,
-                                               const float *__restrict__ lam, const Grid3 &g,
-                                               const PlaneSlots &ps, int i0) {
-    const long long plane = (long long)g.N2 * g.N3;
-    for (int hi = 0; hi < HI; ++hi) {
-        long long base = (long long)wrapi(i0 + hi - 1, g.N1) * plane;
-        long long o = base + ps.off0;
-        s[hi * HJK + threadIdx.x] =
-            make_float4(__ldg(d + o), __ldg(d + g.V + o), __ldg(d + 2 * g.V + o), __ldg(lam + o));
-        if (ps.ok1) {
-            o = base + ps.off1;
-            s[hi * HJK + threadIdx.x + SWEEP_THREADS] = make_float4(
-                __ldg(d + o), __ldg(d + g.V + o), __ldg(d + 2 * g.V + o), __ldg(lam + o));
-        }
-    }
 }
 
 struct AxisW {
@@ -98,15 +80,15 @@ __device__ __forceinline__ float hat(float d) {
     return fmaxf(-d, 0.f);
 }
 
-// Trilinear value (and optionally the exact gradient of the cell's trilinear
-// polynomial) of the halo tile s at halo coordinates (hi, hj, hk) + cell.
+// Trilinear value (and optionally the gradient of the cell's trilinear
+// polynomial) from two haloed planes: P0 holds x1 = x + lo0, P1 holds x + lo0 + 1.
+// (hj, hk) is the voxel's halo position; a1/a2 select the cell in-plane.
 template <bool GRAD>
-__device__ __forceinline__ float trilinear(const float *s, int hi, int hj, int hk, AxisW a0,
-                                           AxisW a1, AxisW a2, float *G) {
-    const int b = (hi + a0.lo) * HJK + (hj + a1.lo) * HK + (hk + a2.lo);
-    const float c000 = s[b], c001 = s[b + 1], c010 = s[b + HK], c011 = s[b + HK + 1];
-    const float c100 = s[b + HJK], c101 = s[b + HJK + 1], c110 = s[b + HJK + HK],
-                c111 = s[b + HJK + HK + 1];
+__device__ __forceinline__ float trilinear2(const float *P0, const float *P1, int hj, int hk,
+                                            AxisW a0, AxisW a1, AxisW a2, float *G) {
+    const int b = (hj + a1.lo) * MHK + (hk + a2.lo);
+    const float c000 = P0[b], c001 = P0[b + 1], c010 = P0[b + MHK], c011 = P0[b + MHK + 1];
+    const float c100 = P1[b], c101 = P1[b + 1], c110 = P1[b + MHK], c111 = P1[b + MHK + 1];
     const float l00 = fmaf(a2.wl, c000, a2.wh * c001), l01 = fmaf(a2.wl, c010, a2.wh * c011);
     const float l10 = fmaf(a2.wl, c100, a2.wh * c101), l11 = fmaf(a2.wl, c110, a2.wh * c111);
     const float m0 = fmaf(a1.wl, l00, a1.wh * l01), m1 = fmaf(a1.wl, l10, a1.wh * l11);
@@ -120,14 +102,14 @@ __device__ __forceinline__ float trilinear(const float *s, int hi, int hj, int h
     return fmaf(a0.wl, m0, a0.wh * m1);
 }
 
-__device__ __forceinline__ double block_sum_256(double v, double *red) {
+__device__ __forceinline__ double block_sum(double v, double *red) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) red[warp] = v;
     __syncthreads();
     double t = 0.0;
     if (threadIdx.x == 0)
-        for (int w = 0; w < SWEEP_THREADS / 32; ++w) t += red[w];
+        for (int w = 0; w < MT / 32; ++w) t += red[w];
     return t;
 }
 
@@ -135,42 +117,89 @@ __device__ __forceinline__ long long block_linear() {
     return ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
 }
 
+// Ring slots of plane s, with r = s - i0 + 1 >= 0.
+__device__ __forceinline__ int ring4(int r) { return r & 3; }
+__device__ __forceinline__ int ring8(int r) { return r & 7; }
+
+// Plane index with periodic wrap for s in [-1, N].
+__device__ __forceinline__ int wrap1(int s, int N) { return s < 0 ? s + N : (s >= N ? s - N : s); }
+
+// Asynchronous 4-byte global -> shared copies (one commit group per plane).
+__device__ __forceinline__ void cp4(uint32_t dst, const float *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
 // ---------------------------------------------------------------------------
 // State step m^{n+1} = S m^n.  LAST also writes lambda^nt = lam_scale (m^nt - I1)
 // and the block's sum of (m^nt - I1)^2 (FP32 terms, FP64 block sum).
+// Plane s of m^n completes output plane s - 1 (its cells reach x1 - 1 .. x1 + 1);
+// planes arrive by cp.async two iterations ahead (8-slot ring).
 template <bool LAST>
-__global__ void __launch_bounds__(SWEEP_THREADS)
-k_state_step(const float *__restrict__ m_in, const float *__restrict__ d,
-             float *__restrict__ m_out, Grid3 g, const float *__restrict__ I1,
-             float *__restrict__ lam_out, float lam_scale, double *__restrict__ partials) {
-    __shared__ float s[HI * HJK];
-    __shared__ double red[SWEEP_THREADS / 32];
-    const int k0 = blockIdx.x * TK, j0 = blockIdx.y * TJ, i0 = blockIdx.z * TI;
-    const PlaneSlots ps = plane_slots(g, k0, j0);
-    load_scalar_halo(s, m_in, g, ps, i0);
-    __syncthreads();
+__global__ void __launch_bounds__(MT, 4)
+k_state_march(const float *__restrict__ m_in, const float *__restrict__ d,
+              float *__restrict__ m_out, Grid3 g, int CH, const float *__restrict__ I1,
+              float *__restrict__ lam_out, float lam_scale, double *__restrict__ partials) {
+    __shared__ __align__(16) float sM[8][MHP];
+    __shared__ double red[MT / 32];
+    const int k0 = blockIdx.x * MK, j0 = blockIdx.y * MJ, i0 = blockIdx.z * CH;
+    const int i_end = min(i0 + CH, g.N1);
+    const Slots ps = plane_slots(g, k0, j0);
+    const long long plane = (long long)g.N2 * g.N3;
     const int tk = threadIdx.x & 31, tj = threadIdx.x >> 5;
     const int k = k0 + tk, j = j0 + tj;
+    const bool active = k < g.N3 && j < g.N2;
+    const long long col = (long long)j * g.N3 + k;
+    const int hj = tj + 1, hk = tk + 1;
+    const uint32_t m_base = smem_u32(&sM[0][threadIdx.x]);
+
+    auto issue = [&](int s, int r) {
+        if (s <= i_end) {
+            const float *f = m_in + (long long)wrap1(s, g.N1) * plane;
+            const uint32_t off = (uint32_t)(r & 7) * (MHP * 4);
+            cp4(m_base + off, f + ps.off0);
+            if (ps.ok1) cp4(m_base + off + MT * 4, f + ps.off1);
+        }
+        cp_commit();
+    };
+    issue(i0 - 1, 0);
+    issue(i0, 1);
     float e2 = 0.f;
-    if (k < g.N3 && j < g.N2) {
-        for (int t = 0; t < TI; ++t) {
-            const int i = i0 + t;
-            if (i >= g.N1) break;
-            const long long idx = ((long long)i * g.N2 + j) * g.N3 + k;
-            const AxisW a0 = axis_weights(__ldg(d + idx));
-            const AxisW a1 = axis_weights(__ldg(d + g.V + idx));
-            const AxisW a2 = axis_weights(__ldg(d + 2 * g.V + idx));
-            const float val = trilinear<false>(s, t + 1, tj + 1, tk + 1, a0, a1, a2, nullptr);
+    float dd0 = 0.f, dd1 = 0.f, dd2 = 0.f;   // d at the output voxel of the next plane
+    for (int s = i0 - 1; s <= i_end; ++s) {
+        const int r = s - i0 + 1;
+        cp_wait1();
+        __syncthreads();
+        issue(s + 2, r + 2);
+        const int o = s - 1;
+        if (active && o >= i0) {
+            const long long idx = (long long)o * plane + col;
+            const AxisW a0 = axis_weights(dd0);
+            const AxisW a1 = axis_weights(dd1);
+            const AxisW a2 = axis_weights(dd2);
+            const float *P0 = a0.lo < 0 ? sM[ring8(r + 6)] : sM[ring8(r + 7)];
+            const float *P1 = a0.lo < 0 ? sM[ring8(r + 7)] : sM[ring8(r)];
+            const float val = trilinear2<false>(P0, P1, hj, hk, a0, a1, a2, nullptr);
             m_out[idx] = val;
             if (LAST) {
-                const float r = val - __ldg(I1 + idx);
-                e2 = fmaf(r, r, e2);
-                lam_out[idx] = lam_scale * r;
+                const float res = val - __ldg(I1 + idx);
+                e2 = fmaf(res, res, e2);
+                lam_out[idx] = lam_scale * res;
             }
+        }
+        if (active && s >= i0 && s < i_end) {
+            const long long nidx = (long long)s * plane + col;
+            dd0 = __ldg(d + nidx);
+            dd1 = __ldg(d + g.V + nidx);
+            dd2 = __ldg(d + 2 * g.V + nidx);
         }
     }
     if (LAST) {
-        const double t = block_sum_256((double)e2, red);
+        const double t = block_sum((double)e2, red);
         if (threadIdx.x == 0) partials[block_linear()] = t;
     }
 }
@@ -179,118 +208,196 @@ k_state_step(const float *__restrict__ m_in, const float *__restrict__ d,
 // Adjoint step at time n (also the Gauss-Newton incremental adjoint):
 //   b(x) (+)= dt lambda^{n+1}(x) grad m^n(x + d(x))     (body force)
 //   lambda^n(y) = sum_{e in {-1,0,1}^3} lambda^{n+1}(y-e) prod_a hat(d_a(y-e) - e_a)
+// Source plane s adds to output planes s-1, s, s+1 (registers acc_a/b/c);
+// output plane s-1 is then complete.  Planes arrive by cp.async two iterations
+// ahead: (d, lambda) in a 4-slot ring, m^n in an 8-slot ring.
 template <bool FIRST, bool WRITE_LAM>
-__global__ void __launch_bounds__(SWEEP_THREADS, 3)
-k_adjoint_step(const float *__restrict__ lam_in, const float *__restrict__ m_n,
-               const float *__restrict__ d, float *__restrict__ lam_out,
-               float *__restrict__ b, float dt, Grid3 g) {
-    extern __shared__ float4 smem4[];
-    float4 *sq = smem4;
-    float *sm = reinterpret_cast<float *>(smem4 + HI * HJK);
-    const int k0 = blockIdx.x * TK, j0 = blockIdx.y * TJ, i0 = blockIdx.z * TI;
-    const PlaneSlots ps = plane_slots(g, k0, j0);
-    load_dlam_halo(sq, d, lam_in, g, ps, i0);
-    load_scalar_halo(sm, m_n, g, ps, i0);
-    __syncthreads();
+__global__ void __launch_bounds__(MT, 4)
+k_adjoint_march(const float *__restrict__ lam_in, const float *__restrict__ m_n,
+                const float *__restrict__ d, float *__restrict__ lam_out,
+                float *__restrict__ b, float dt, Grid3 g, int CH) {
+    __shared__ __align__(16) float4 sQ[4][MHP];   // (d0, d1, d2, lambda^{n+1})
+    __shared__ __align__(16) float sM[8][MHP];    // m^n
+    const int k0 = blockIdx.x * MK, j0 = blockIdx.y * MJ, i0 = blockIdx.z * CH;
+    const int i_end = min(i0 + CH, g.N1);
+    const Slots ps = plane_slots(g, k0, j0);
+    const long long plane = (long long)g.N2 * g.N3;
     const int tk = threadIdx.x & 31, tj = threadIdx.x >> 5;
     const int k = k0 + tk, j = j0 + tj;
-    if (k >= g.N3 || j >= g.N2) return;
-    for (int t = 0; t < TI; ++t) {
-        const int i = i0 + t;
-        if (i >= g.N1) break;
-        const long long idx = ((long long)i * g.N2 + j) * g.N3 + k;
-        const int c = (t + 1) * HJK + (tj + 1) * HK + (tk + 1);
-        const float4 q = sq[c];
-        float G[3];
-        trilinear<true>(sm, t + 1, tj + 1, tk + 1, axis_weights(q.x), axis_weights(q.y),
-                        axis_weights(q.z), G);
-        const float sl = dt * q.w;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            float *bp = b + a * g.V + idx;
-            *bp = FIRST ? sl * G[a] : fmaf(sl, G[a], *bp);
+    const bool active = k < g.N3 && j < g.N2;
+    const long long col = (long long)j * g.N3 + k;
+    const int hj = tj + 1, hk = tk + 1;
+    const int c = hj * MHK + hk;
+    const uint32_t q_base = smem_u32(&sQ[0][threadIdx.x]);
+    const uint32_t m_base = smem_u32(&sM[0][threadIdx.x]);
+
+    // copy plane s (if it belongs to this chunk's window) into ring slot r
+    auto issue = [&](int s, int r) {
+        if (s <= i_end) {
+            const long long base = (long long)wrap1(s, g.N1) * plane;
+            const float *src = d + base + ps.off0;
+            const uint32_t dq = q_base + (uint32_t)(r & 3) * (MHP * 16);
+            cp4(dq, src);
+            cp4(dq + 4, src + g.V);
+            cp4(dq + 8, src + 2 * g.V);
+            cp4(dq + 12, lam_in + base + ps.off0);
+            cp4(m_base + (uint32_t)(r & 7) * (MHP * 4), m_n + base + ps.off0);
+            if (ps.ok1) {
+                const float *src1 = d + base + ps.off1;
+                const uint32_t dq1 = dq + MT * 16;
+                cp4(dq1, src1);
+                cp4(dq1 + 4, src1 + g.V);
+                cp4(dq1 + 8, src1 + 2 * g.V);
+                cp4(dq1 + 12, lam_in + base + ps.off1);
+                cp4(m_base + (uint32_t)(r & 7) * (MHP * 4) + MT * 4, m_n + base + ps.off1);
+            }
         }
-        if (WRITE_LAM) {
-            float acc = 0.f;
-#define BLR_NB(E0, E1, E2)                                                           \
-    {                                                                                \
-        const float4 n = sq[c - (E0) * HJK - (E1) * HK - (E2)];                     \
-        acc = fmaf(hat<E0>(n.x) * hat<E1>(n.y) * hat<E2>(n.z), n.w, acc);           \
+        cp_commit();
+    };
+    issue(i0 - 1, 0);
+    issue(i0, 1);
+    float acc_a = 0.f, acc_b = 0.f, acc_c = 0.f;
+    float bb[3] = {0.f, 0.f, 0.f};   // body force at the output voxel of the next plane
+    for (int s = i0 - 1; s <= i_end; ++s) {
+        const int r = s - i0 + 1;
+        cp_wait1();
+        __syncthreads();
+        issue(s + 2, r + 2);
+        if (active) {
+            if (WRITE_LAM) {
+                const float4 *Q = sQ[ring4(r)];
+#define BLR_SRC(DJ, DK)                                                       \
+    {                                                                         \
+        const float4 q = Q[c + (DJ) * MHK + (DK)];                            \
+        const float w = q.w * hat<-(DJ)>(q.y) * hat<-(DK)>(q.z);              \
+        acc_a = fmaf(w, fmaxf(-q.x, 0.f), acc_a);                             \
+        acc_b = fmaf(w, 1.f - fabsf(q.x), acc_b);                             \
+        acc_c = fmaf(w, fmaxf(q.x, 0.f), acc_c);                              \
     }
-#define BLR_NB3(E0, E1) BLR_NB(E0, E1, -1) BLR_NB(E0, E1, 0) BLR_NB(E0, E1, 1)
-#define BLR_NB9(E0) BLR_NB3(E0, -1) BLR_NB3(E0, 0) BLR_NB3(E0, 1)
-            BLR_NB9(-1) BLR_NB9(0) BLR_NB9(1)
-#undef BLR_NB9
-#undef BLR_NB3
-#undef BLR_NB
-            lam_out[idx] = acc;
+                BLR_SRC(-1, -1) BLR_SRC(-1, 0) BLR_SRC(-1, 1)
+                BLR_SRC(0, -1) BLR_SRC(0, 0) BLR_SRC(0, 1)
+                BLR_SRC(1, -1) BLR_SRC(1, 0) BLR_SRC(1, 1)
+#undef BLR_SRC
+            }
+            const int o = s - 1;
+            if (o >= i0) {
+                const long long idx = (long long)o * plane + col;
+                const float4 q0 = sQ[ring4(r + 3)][c];
+                const AxisW a0 = axis_weights(q0.x);
+                const float *P0 = a0.lo < 0 ? sM[ring8(r + 6)] : sM[ring8(r + 7)];
+                const float *P1 = a0.lo < 0 ? sM[ring8(r + 7)] : sM[ring8(r)];
+                float G[3];
+                trilinear2<true>(P0, P1, hj, hk, a0, axis_weights(q0.y), axis_weights(q0.z), G);
+                const float sl = dt * q0.w;
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    b[a * g.V + idx] = FIRST ? sl * G[a] : fmaf(sl, G[a], bb[a]);
+                if (WRITE_LAM) lam_out[idx] = acc_a;
+            }
+            if (!FIRST && s >= i0 && s < i_end) {
+                const long long nidx = (long long)s * plane + col;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) bb[a] = b[a * g.V + nidx];
+            }
         }
+        acc_a = acc_b;
+        acc_b = acc_c;
+        acc_c = 0.f;
     }
 }
 
 // ---------------------------------------------------------------------------
 // Incremental state step (linearised Eq. 36):
 //   dm^{n+1}(x) = (S dm^n)(x) - dt grad m^n(x + d(x)) . dv(x),   dm^0 = 0.
-// LAST writes dlambda^nt = lam_scale dm^nt instead of dm^nt.
+// LAST writes dlambda^nt = lam_scale dm^nt instead of dm^nt.  m^n and dm^n
+// planes arrive by cp.async two iterations ahead (8-slot rings).
 template <bool FIRST, bool LAST>
-__global__ void __launch_bounds__(SWEEP_THREADS)
-k_incstate_step(const float *__restrict__ dm_in, const float *__restrict__ m_n,
-                const float *__restrict__ d, const float *__restrict__ dv,
-                float *__restrict__ dm_out, float dt, float lam_scale, Grid3 g) {
-    __shared__ float sm[HI * HJK];
-    __shared__ float sdm[FIRST ? 1 : HI * HJK];
-    const int k0 = blockIdx.x * TK, j0 = blockIdx.y * TJ, i0 = blockIdx.z * TI;
-    const PlaneSlots ps = plane_slots(g, k0, j0);
-    load_scalar_halo(sm, m_n, g, ps, i0);
-    if (!FIRST) load_scalar_halo(sdm, dm_in, g, ps, i0);
-    __syncthreads();
+__global__ void __launch_bounds__(MT, 4)
+k_incstate_march(const float *__restrict__ dm_in, const float *__restrict__ m_n,
+                 const float *__restrict__ d, const float *__restrict__ dv,
+                 float *__restrict__ dm_out, float dt, float lam_scale, Grid3 g, int CH) {
+    __shared__ __align__(16) float sM[8][MHP];
+    __shared__ __align__(16) float sD[FIRST ? 1 : 8][FIRST ? 1 : MHP];
+    const int k0 = blockIdx.x * MK, j0 = blockIdx.y * MJ, i0 = blockIdx.z * CH;
+    const int i_end = min(i0 + CH, g.N1);
+    const Slots ps = plane_slots(g, k0, j0);
+    const long long plane = (long long)g.N2 * g.N3;
     const int tk = threadIdx.x & 31, tj = threadIdx.x >> 5;
     const int k = k0 + tk, j = j0 + tj;
-    if (k >= g.N3 || j >= g.N2) return;
-    for (int t = 0; t < TI; ++t) {
-        const int i = i0 + t;
-        if (i >= g.N1) break;
-        const long long idx = ((long long)i * g.N2 + j) * g.N3 + k;
-        const AxisW a0 = axis_weights(__ldg(d + idx));
-        const AxisW a1 = axis_weights(__ldg(d + g.V + idx));
-        const AxisW a2 = axis_weights(__ldg(d + 2 * g.V + idx));
-        float G[3];
-        trilinear<true>(sm, t + 1, tj + 1, tk + 1, a0, a1, a2, G);
-        float out = FIRST ? 0.f : trilinear<false>(sdm, t + 1, tj + 1, tk + 1, a0, a1, a2, nullptr);
-        const float gdv = fmaf(G[0], __ldg(dv + idx),
-                               fmaf(G[1], __ldg(dv + g.V + idx), G[2] * __ldg(dv + 2 * g.V + idx)));
-        out = fmaf(-dt, gdv, out);
-        dm_out[idx] = LAST ? lam_scale * out : out;
+    const bool active = k < g.N3 && j < g.N2;
+    const long long col = (long long)j * g.N3 + k;
+    const int hj = tj + 1, hk = tk + 1;
+    const uint32_t m_base = smem_u32(&sM[0][threadIdx.x]);
+    const uint32_t d_base = FIRST ? 0u : smem_u32(&sD[0][threadIdx.x]);
+
+    auto issue = [&](int s, int r) {
+        if (s <= i_end) {
+            const long long base = (long long)wrap1(s, g.N1) * plane;
+            const uint32_t off = (uint32_t)(r & 7) * (MHP * 4);
+            cp4(m_base + off, m_n + base + ps.off0);
+            if (!FIRST) cp4(d_base + off, dm_in + base + ps.off0);
+            if (ps.ok1) {
+                cp4(m_base + off + MT * 4, m_n + base + ps.off1);
+                if (!FIRST) cp4(d_base + off + MT * 4, dm_in + base + ps.off1);
+            }
+        }
+        cp_commit();
+    };
+    issue(i0 - 1, 0);
+    issue(i0, 1);
+    float dd[3] = {0.f, 0.f, 0.f}, vv[3] = {0.f, 0.f, 0.f};   // next output voxel's d, dv
+    for (int s = i0 - 1; s <= i_end; ++s) {
+        const int r = s - i0 + 1;
+        cp_wait1();
+        __syncthreads();
+        issue(s + 2, r + 2);
+        const int o = s - 1;
+        if (active && o >= i0) {
+            const long long idx = (long long)o * plane + col;
+            const AxisW a0 = axis_weights(dd[0]);
+            const AxisW a1 = axis_weights(dd[1]);
+            const AxisW a2 = axis_weights(dd[2]);
+            const int s0 = a0.lo < 0 ? ring8(r + 6) : ring8(r + 7);
+            const int s1 = a0.lo < 0 ? ring8(r + 7) : ring8(r);
+            float G[3];
+            trilinear2<true>(sM[s0], sM[s1], hj, hk, a0, a1, a2, G);
+            float out = 0.f;
+            if (!FIRST) out = trilinear2<false>(sD[s0], sD[s1], hj, hk, a0, a1, a2, nullptr);
+            const float gdv = fmaf(G[0], vv[0], fmaf(G[1], vv[1], G[2] * vv[2]));
+            out = fmaf(-dt, gdv, out);
+            dm_out[idx] = LAST ? lam_scale * out : out;
+        }
+        if (active && s >= i0 && s < i_end) {
+            const long long nidx = (long long)s * plane + col;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                dd[a] = __ldg(d + a * g.V + nidx);
+                vv[a] = __ldg(dv + a * g.V + nidx);
+            }
+        }
     }
 }
 
-constexpr size_t ADJ_SMEM = HI * HJK * (sizeof(float4) + sizeof(float));
-
 dim3 sweep_grid(const blr_plan *P) {
-    return dim3((unsigned)ceil_div_ll(P->N3, TK), (unsigned)ceil_div_ll(P->N2, TJ),
-                (unsigned)ceil_div_ll(P->N1, TI));
-}
-
-template <bool F, bool W>
-int launch_adjoint(dim3 grid, cudaStream_t s, const float *lin, const float *mn, const float *d,
-                   float *lout, float *b, float dt, Grid3 g) {
-    k_adjoint_step<F, W><<<grid, SWEEP_THREADS, ADJ_SMEM, s>>>(lin, mn, d, lout, b, dt, g);
-    BLR_CK_LAUNCH();
-    return BLR_OK;
+    return dim3((unsigned)ceil_div_ll(P->N3, MK), (unsigned)ceil_div_ll(P->N2, MJ),
+                (unsigned)ceil_div_ll(P->N1, P->chunk));
 }
 
 }  // namespace
 
-// Opt the adjoint kernels into their dynamic shared memory on the current device.
-int sweep_setup() {
-    BLR_CK(cudaFuncSetAttribute(k_adjoint_step<true, true>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ADJ_SMEM));
-    BLR_CK(cudaFuncSetAttribute(k_adjoint_step<true, false>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ADJ_SMEM));
-    BLR_CK(cudaFuncSetAttribute(k_adjoint_step<false, true>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ADJ_SMEM));
-    BLR_CK(cudaFuncSetAttribute(k_adjoint_step<false, false>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ADJ_SMEM));
+// Chunk of x1 planes per block.  Four blocks fit on an SM (register bound), so
+// the grid is sized to at most one wave of 4 x SMs blocks: a partial second wave
+// would cost a whole extra block duration.  Each chunk loads chunk + 2 planes.
+int sweep_setup(blr_plan *P) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device) != cudaSuccess || sms < 1)
+        sms = 148;
+    const long long cols = ceil_div_ll(P->N3, MK) * ceil_div_ll(P->N2, MJ);
+    long long slices = (4LL * sms) / cols;          // floor: never exceed one wave
+    if (slices < 1) slices = 1;
+    long long ch = ceil_div_ll(P->N1, slices);
+    if (ch < 2) ch = 2;
+    P->chunk = (int)ch;
     return BLR_OK;
 }
 
@@ -307,11 +414,11 @@ int sweep_state(blr_plan *P, cudaStream_t s) {
         const float *min_ = P->m + (long long)n * P->V;
         float *mout = P->m + (long long)(n + 1) * P->V;
         if (n == nt - 1)
-            k_state_step<true><<<grid, SWEEP_THREADS, 0, s>>>(min_, P->d, mout, P->grid, P->I1,
-                                                              P->lam[0], lam_scale, P->partials);
+            k_state_march<true><<<grid, MT, 0, s>>>(min_, P->d, mout, P->grid, P->chunk, P->I1,
+                                                    P->lam[0], lam_scale, P->partials);
         else
-            k_state_step<false><<<grid, SWEEP_THREADS, 0, s>>>(min_, P->d, mout, P->grid, nullptr,
-                                                               nullptr, 0.f, nullptr);
+            k_state_march<false><<<grid, MT, 0, s>>>(min_, P->d, mout, P->grid, P->chunk, nullptr,
+                                                     nullptr, 0.f, nullptr);
         BLR_CK_LAUNCH();
     }
     return BLR_OK;
@@ -329,12 +436,15 @@ int sweep_adjoint(blr_plan *P, float *b, float *lambda0, cudaStream_t s) {
         const float *mn = P->m + (long long)n * P->V;
         const bool first = (n == nt - 1);
         const bool wlam = (n > 0) || (lambda0 != nullptr);
-        int rc;
-        if (first && wlam) rc = launch_adjoint<true, true>(grid, s, lin, mn, P->d, lout, b, P->dt, P->grid);
-        else if (first) rc = launch_adjoint<true, false>(grid, s, lin, mn, P->d, lout, b, P->dt, P->grid);
-        else if (wlam) rc = launch_adjoint<false, true>(grid, s, lin, mn, P->d, lout, b, P->dt, P->grid);
-        else rc = launch_adjoint<false, false>(grid, s, lin, mn, P->d, lout, b, P->dt, P->grid);
-        if (rc != BLR_OK) return rc;
+        if (first && wlam)
+            k_adjoint_march<true, true><<<grid, MT, 0, s>>>(lin, mn, P->d, lout, b, P->dt, P->grid, P->chunk);
+        else if (first)
+            k_adjoint_march<true, false><<<grid, MT, 0, s>>>(lin, mn, P->d, lout, b, P->dt, P->grid, P->chunk);
+        else if (wlam)
+            k_adjoint_march<false, true><<<grid, MT, 0, s>>>(lin, mn, P->d, lout, b, P->dt, P->grid, P->chunk);
+        else
+            k_adjoint_march<false, false><<<grid, MT, 0, s>>>(lin, mn, P->d, lout, b, P->dt, P->grid, P->chunk);
+        BLR_CK_LAUNCH();
         cur = 1 - cur;
     }
     return BLR_OK;
@@ -352,13 +462,13 @@ int sweep_incremental(blr_plan *P, cudaStream_t s) {
         const float *mn = P->m + (long long)n * P->V;
         const bool first = n == 0, last = n == nt - 1;
         if (first && last)
-            k_incstate_step<true, true><<<grid, SWEEP_THREADS, 0, s>>>(din, mn, P->d, P->dv, dout, P->dt, lam_scale, P->grid);
+            k_incstate_march<true, true><<<grid, MT, 0, s>>>(din, mn, P->d, P->dv, dout, P->dt, lam_scale, P->grid, P->chunk);
         else if (first)
-            k_incstate_step<true, false><<<grid, SWEEP_THREADS, 0, s>>>(din, mn, P->d, P->dv, dout, P->dt, lam_scale, P->grid);
+            k_incstate_march<true, false><<<grid, MT, 0, s>>>(din, mn, P->d, P->dv, dout, P->dt, lam_scale, P->grid, P->chunk);
         else if (last)
-            k_incstate_step<false, true><<<grid, SWEEP_THREADS, 0, s>>>(din, mn, P->d, P->dv, dout, P->dt, lam_scale, P->grid);
+            k_incstate_march<false, true><<<grid, MT, 0, s>>>(din, mn, P->d, P->dv, dout, P->dt, lam_scale, P->grid, P->chunk);
         else
-            k_incstate_step<false, false><<<grid, SWEEP_THREADS, 0, s>>>(din, mn, P->d, P->dv, dout, P->dt, lam_scale, P->grid);
+            k_incstate_march<false, false><<<grid, MT, 0, s>>>(din, mn, P->d, P->dv, dout, P->dt, lam_scale, P->grid, P->chunk);
         BLR_CK_LAUNCH();
         cur = 1 - cur;
     }
