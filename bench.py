@@ -16,6 +16,9 @@ Printed: one JSON line (rank 0).  `value` = registrations/s over all ranks
 the same registration metric with host buffers (pinned) through the C-ABI;
 `roofline` = the adjoint sweep kernel against the measured HBM copy bandwidth;
 `cpu_baseline` = the FP64 oracle on the host cores, timed on a bounded sample.
+The headline is the mixed-precision path (BF16 hi+lo tensor-core DFT
+contractions); `by_precision` reports the plain FP32 path beside it, with each
+path's HVP error against the FP64 oracle.
 
 `--impl reference` times the FP64 oracle alone (host cores) on the same
 workload and prints the same line with "impl": "reference".
@@ -206,38 +209,21 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def main_ours(args):
+def measure_precision(precision, args, dev, I0g, I1g, flush, stream, dist, world):
+    """Timed registrations, HVP loop and adjoint-kernel roofline for one precision."""
     import numpy as np
     import torch
 
     from paper_1807_05117_gb300 import blr, synth
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", local)
-    precision = blr.BLR_MIXED if args.precision == "mixed" else blr.BLR_FP32
-
-    I0, I1, _ = synth.phantom_pair(N, SEED + 1000 * rank, max_disp=MAX_DISP)
-    (I0f, _), (I1f, _) = synth.as_device_inputs(I0, I1)
-    I0g, I1g = torch.from_numpy(I0f).to(dev), torch.from_numpy(I1f).to(dev)
-    plan = blr.Plan(N, BAND, NT, precision=precision)
+    prec = blr.BLR_MIXED if precision == "mixed" else blr.BLR_FP32
+    plan = blr.Plan(N, BAND, NT, precision=prec)
     plan.set_images(I0g, I1g)
     vt = torch.zeros((3,) + BAND, dtype=torch.complex64, device=dev)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
 
     def step():
         vt.zero_()
         return plan.newton(vt, NEWTON, PCG, 0.0, 0.0)
-
-    for _ in range(args.warmup):
-        step()
 
     def barrier():
         torch.cuda.synchronize()
@@ -245,16 +231,18 @@ def main_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    for _ in range(args.warmup):
+        step()
     sampler = ClockSampler()
     barrier()
     sampler.start()
     launches0 = blr.blr_kernel_launches()
     total_ms = 0.0
     rep = None
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
     for k in range(args.steps):
         flush.fill_(k & 0xFF)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         rep = step()
         e1.record(stream)
@@ -262,13 +250,12 @@ def main_ours(args):
         total_ms += e0.elapsed_time(e1)
     launches = blr.blr_kernel_launches() - launches0
     barrier()
-    clocks = sampler.stop(local)
+    clocks = sampler.stop(int(os.environ.get("LOCAL_RANK", "0")))
     ms = total_ms / max(args.steps, 1)
     if dist is not None:
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    value = world * 1000.0 / ms
 
     # Gauss-Newton HVP/s at the final point of the last registration
     dvt = torch.from_numpy(synth.random_direction(BAND, SEED + 2).astype(np.complex64)).to(dev)
@@ -276,8 +263,6 @@ def main_ours(args):
     for _ in range(3):
         plan.hessvec(dvt, hout)
     reps = args.hvp_reps
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(reps):
@@ -303,27 +288,72 @@ def main_ours(args):
     adj_bytes = ADJ_BYTES(NT) * V / NT
     peak, peak_kind = peaks()
     achieved = adj_bytes / adj_launch_s / 1e9
-    roofline = {"kernel": "k_adjoint_step", "bound": "hbm", "achieved": achieved,
+    roofline = {"kernel": "k_adjoint_march", "bound": "hbm", "achieved": achieved,
                 "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": f"{peak_kind} hbm_gbs (copy, burst)",
+                "peak_source": f"{peak_kind} hbm_gbs (copy, burst; kernel timed alone)",
                 "algorithmic_bytes_per_launch": adj_bytes, "launch_us": adj_launch_s * 1e6,
                 "traffic": args.adjoint_traffic}
+    return dict(plan=plan, ms=ms, launches=launches, clocks=clocks, rep=rep, hvp_ms=hvp_ms,
+                roofline=roofline, dvt=dvt)
 
-    line = {"metric": METRIC, "value": value, "unit": "registrations/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic", "config": config(args.precision, world),
-            "hvp_per_s": world * 1000.0 / hvp_ms, "hvp_ms": hvp_ms,
-            "gpu_launches": int(launches), "roofline": roofline, "clocks": clocks,
+
+def main_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1807_05117_gb300 import blr, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    I0, I1, _ = synth.phantom_pair(N, SEED + 1000 * rank, max_disp=MAX_DISP)
+    (I0f, _), (I1f, _) = synth.as_device_inputs(I0, I1)
+    I0g, I1g = torch.from_numpy(I0f).to(dev), torch.from_numpy(I1f).to(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    order = [args.precision] + [p for p in ("fp32", "mixed") if p != args.precision]
+    if args.only:
+        order = [args.precision]
+    res = {p: measure_precision(p, args, dev, I0g, I1g, flush, stream, dist, world) for p in order}
+    head = res[args.precision]
+    rep = head["rep"]
+    line = {"metric": METRIC, "value": world * 1000.0 / head["ms"], "unit": "registrations/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32 fields; bf16 hi+lo split x3 products (fp32 accumulate) in the axis-1 DFT contractions"
+                     if args.precision == "mixed" else "f32",
+            "data": "synthetic", "config": config(args.precision, world),
+            "hvp_per_s": world * 1000.0 / head["hvp_ms"], "hvp_ms": head["hvp_ms"],
+            "gpu_launches": int(head["launches"]), "roofline": head["roofline"],
+            "clocks": head["clocks"],
             "report": {k: getattr(rep, k) for k in ("newton_iters", "pcg_iters", "n_state",
                                                      "n_hessvec", "n_halvings", "energy0",
-                                                     "energy", "grad_inf_rel")}}
+                                                     "energy", "grad_inf_rel")},
+            "by_precision": {p: {"registrations_per_s": world * 1000.0 / r["ms"],
+                                 "ms_per_registration": r["ms"],
+                                 "hvp_per_s": world * 1000.0 / r["hvp_ms"],
+                                 "final_energy": r["rep"].energy,
+                                 "pcg_iters": r["rep"].pcg_iters,
+                                 "adjoint_step_us": r["roofline"]["launch_us"]}
+                             for p, r in res.items()}}
+    plan = head["plan"]
 
     # end to end through the C-ABI with pinned host buffers
     if not args.no_e2e:
         hI0 = torch.from_numpy(I0f).pin_memory()
         hI1 = torch.from_numpy(I1f).pin_memory()
         hvt = torch.zeros((3,) + BAND, dtype=torch.complex64).pin_memory()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
 
         def e2e_step():
             hvt.zero_()
@@ -331,7 +361,9 @@ def main_ours(args):
             return plan.newton(hvt, NEWTON, PCG, 0.0, 0.0)
 
         e2e_step()
-        barrier()
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
         tot = 0.0
         for k in range(args.steps):
             flush.fill_(k & 0xFF)
@@ -350,40 +382,47 @@ def main_ours(args):
                        "h2d_bytes_per_step": 2 * I0f.nbytes + hvt.numel() * 8,
                        "d2h_bytes_per_step": hvt.numel() * 8}
 
-    # FP64 oracle on the host cores (rank 0, one GPU only) and the HVP error
+    # FP64 oracle on the host cores (rank 0, one GPU only) and the HVP errors
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        res = run_oracle_subprocess(1)
-        ts, tg, th = res["times"][0]
+        out = run_oracle_subprocess(1)
+        ts, tg, th = out["times"][0]
         counts = dict(n_state=rep.n_state, n_grad=rep.newton_iters + 1, n_hvp=rep.n_hessvec)
         sec = registration_seconds(ts, tg, th, **counts)
         line["cpu_baseline"] = {
             "value": 1.0 / sec, "unit": "registrations/s", "cores": 1, "kind": "oracle",
+            "hvp_per_s": 1.0 / th,
             "sample": (f"one FP64 forward solve ({ts:.2f} s), gradient ({tg:.2f} s) and "
                        f"Gauss-Newton HVP ({th:.2f} s) at 128^3, single thread, scaled by "
                        f"this run's operation counts {counts}")}
-        # the sample point on the GPU, for the FP32-vs-FP64 errors
+        # the sample point on the GPU, for the errors against the FP64 oracle
         vt_s = synth.random_coefficients(BAND, SEED + 1, SAMPLE_BOUND)
         I0s, I1s, _ = synth.phantom_pair(N, SEED, max_disp=MAX_DISP)
         (a, _), (b, _), (c, _) = synth.as_device_inputs(I0s, I1s, vt_s)
-        plan.set_images(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev))
-        g = torch.empty_like(dvt)
-        plan.gradient(torch.from_numpy(c).to(dev), g)
-        plan.hessvec(dvt, hout)
-        gref, href = res["g"], res["h"]
-        line["hvp_rel_err"] = float(np.linalg.norm(hout.cpu().numpy() - href) / np.linalg.norm(href))
-        line["grad_rel_err"] = float(np.linalg.norm(g.cpu().numpy() - gref) / np.linalg.norm(gref))
-        line["cpu_baseline"]["hvp_per_s"] = 1.0 / th
+        gref, href = out["g"], out["h"]
+        for p, r in res.items():
+            pl = r["plan"]
+            pl.set_images(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev))
+            g = torch.empty_like(r["dvt"])
+            h = torch.empty_like(r["dvt"])
+            pl.gradient(torch.from_numpy(c).to(dev), g)
+            pl.hessvec(r["dvt"], h)
+            eh = float(np.linalg.norm(h.cpu().numpy() - href) / np.linalg.norm(href))
+            eg = float(np.linalg.norm(g.cpu().numpy() - gref) / np.linalg.norm(gref))
+            line["by_precision"][p]["hvp_rel_err_vs_fp64"] = eh
+            line["by_precision"][p]["grad_rel_err_vs_fp64"] = eg
+        line["hvp_rel_err"] = line["by_precision"][args.precision]["hvp_rel_err_vs_fp64"]
 
     if rank == 0:
         print(json.dumps(line), flush=True)
-    plan.close()
+    for r in res.values():
+        r["plan"].close()
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
     return 0
 
 
-def probe():
+def probe(precision="fp32"):
     """A few launches of every hot-path kernel at the benchmark size, for ncu."""
     import numpy as np
     import torch
@@ -395,7 +434,8 @@ def probe():
     vt = synth.random_coefficients(BAND, SEED + 1, SAMPLE_BOUND)
     dvt = synth.random_direction(BAND, SEED + 2)
     (a, _), (b, _), (c, _), (d, _) = synth.as_device_inputs(I0, I1, vt, dvt)
-    with blr.Plan(N, BAND, NT) as plan:
+    prec = blr.BLR_MIXED if precision == "mixed" else blr.BLR_FP32
+    with blr.Plan(N, BAND, NT, precision=prec) as plan:
         plan.set_images(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev))
         g = torch.empty((3,) + BAND, dtype=torch.complex64, device=dev)
         plan.gradient(torch.from_numpy(c).to(dev), g)
@@ -418,7 +458,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "mixed"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "mixed"], default="mixed",
+                    help="headline path; the other precision is measured beside it")
+    ap.add_argument("--only", action="store_true", help="measure the headline precision only")
     ap.add_argument("--hvp-reps", type=int, default=50)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -433,7 +475,7 @@ def main():
         oracle_sample(args.oracle_sample, args.samples)
         return 0
     if args.probe:
-        return probe()
+        return probe(args.precision)
     if args.impl == "reference":
         return main_reference(args)
     return main_ours(args)

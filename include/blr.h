@@ -59,6 +59,7 @@ extern "C" {
 #define BLR_ENAN     (-5)  /* non-finite energy or residual                */
 #define BLR_ESTATE   (-6)  /* needs a prior blr_state / blr_gradient        */
 #define BLR_ECURV    (-7)  /* PCG met <p, Hp> <= 0                          */
+#define BLR_ETIMEOUT (-8)  /* a bounded device wait expired (tensor cores)  */
 
 /* Precision of the truncated-DFT contractions (the transport is always FP32). */
 #define BLR_FP32   0       /* FP32 FMA contractions                         */

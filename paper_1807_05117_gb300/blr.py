@@ -26,6 +26,7 @@ BLR_ECFL = -4
 BLR_ENAN = -5
 BLR_ESTATE = -6
 BLR_ECURV = -7
+BLR_ETIMEOUT = -8
 
 BLR_FP32 = 0
 BLR_MIXED = 1

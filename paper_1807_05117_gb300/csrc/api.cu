@@ -25,7 +25,6 @@ int validate(const blr_params *p) {
     if (p->nt < 1 || !(p->sigma > 0) || !(p->gamma > 0) || !(p->alpha >= 0) || p->s < 0)
         return BLR_EINVAL;
     if (p->precision != BLR_FP32 && p->precision != BLR_MIXED) return BLR_EINVAL;
-    if (p->precision == BLR_MIXED) return BLR_EINVAL;   // tensor-core contractions not built
     if (p->reserved != 0) return BLR_EINVAL;
     long long V = (long long)p->n[0] * p->n[1] * p->n[2];
     if (V > (1LL << 31)) return BLR_EINVAL;
@@ -67,12 +66,19 @@ size_t layout(blr_plan *P, char *base) {
     P->A = a.take<float>(P->nb);
     P->dft_big = a.take<float>((size_t)3 * P->B1 * P->N2 * P->N3 * 2);
     P->dft_small = a.take<float>((size_t)3 * P->B1 * P->B2 * P->N3 * 2);
+    if (P->p.precision == BLR_MIXED) {
+        P->tc_tab_expand = a.take<uint8_t>(tc_table_bytes(P, 0));
+        P->tc_tab_project = a.take<uint8_t>(tc_table_bytes(P, 1));
+    } else {
+        P->tc_tab_expand = P->tc_tab_project = nullptr;
+    }
     float **vecs[] = {&P->vt, &P->g, &P->r, &P->pv, &P->q, &P->x, &P->trial, &P->step, &P->vtmp};
     for (float **v : vecs) *v = a.take<float>(P->nfloat);
     P->dsc = a.take<double>(SC_COUNT);
     P->dstatus = a.take<int>(1);
     P->ticket = a.take<unsigned int>(1);
     P->partials = a.take<double>(P->npart);
+    P->partials2 = a.take<double>(reduce_partials_needed());
     return a.used;
 }
 
@@ -91,6 +97,7 @@ int fetch_scalars(blr_plan *P, cudaStream_t s, int *flags) {
 }
 
 int flags_to_status(int flags) {
+    if (flags & BLR_FLAG_TIMEOUT) return BLR_ETIMEOUT;
     if (flags & BLR_FLAG_NAN) return BLR_ENAN;
     if (flags & BLR_FLAG_CFL) return BLR_ECFL;
     return BLR_OK;
@@ -185,6 +192,10 @@ int blr_plan_create(const blr_params *p, blr_plan_t *out) {
         delete P;
         return BLR_ECUDA;
     }
+    if (p->precision == BLR_MIXED && !tc_supported(P)) {
+        delete P;
+        return BLR_EINVAL;
+    }
     sweep_setup(P);
     long long nsweep = sweep_blocks(P);
     long long nred = reduce_partials_needed();
@@ -203,7 +214,9 @@ int blr_plan_create(const blr_params *p, blr_plan_t *out) {
         return BLR_ENOMEM;
     }
     if (cudaMemset(base, 0, bytes) != cudaSuccess ||
-        dft_init_tables(P, 0) != BLR_OK || cudaDeviceSynchronize() != cudaSuccess) {
+        dft_init_tables(P, 0) != BLR_OK ||
+        (p->precision == BLR_MIXED && tc_init_tables(P, 0) != BLR_OK) ||
+        cudaDeviceSynchronize() != cudaSuccess) {
         cudaFreeHost(P->hsc);
         cudaFree(base);
         delete P;
@@ -380,6 +393,7 @@ const char *blr_strerror(int code) {
         case BLR_ENAN: return "non-finite value";
         case BLR_ESTATE: return "no forward solve at the current point (call blr_state first)";
         case BLR_ECURV: return "PCG met non-positive curvature";
+        case BLR_ETIMEOUT: return "a bounded device wait expired (tensor-core stage)";
         default: return "unknown status";
     }
 }

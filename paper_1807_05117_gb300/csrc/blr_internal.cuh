@@ -25,7 +25,7 @@ extern unsigned long long g_blr_launches;
     } while (0)
 
 // Device-latched conditions (bit flags in blr_plan::dstatus).
-enum { BLR_FLAG_CFL = 1, BLR_FLAG_NAN = 2 };
+enum { BLR_FLAG_CFL = 1, BLR_FLAG_NAN = 2, BLR_FLAG_TIMEOUT = 4 };
 
 // Slots of the device scalar block blr_plan::dsc (doubles).
 enum {
@@ -68,6 +68,8 @@ struct blr_plan {
     float *A;           // [B1][B2][B3] regulariser weights
     float *dft_big;     // 3*B1*N2*N3*2 floats
     float *dft_small;   // 3*B1*B2*N3*2 floats
+    uint8_t *tc_tab_expand;    // BLR_MIXED: swizzled BF16 hi/lo table tiles (dft_tc.cu)
+    uint8_t *tc_tab_project;
 
     // Krylov / Newton vectors (nfloat each)
     float *g, *r, *pv, *q, *x, *trial, *step, *vtmp;
@@ -76,6 +78,7 @@ struct blr_plan {
     double *hsc;        // pinned host mirror
     int *dstatus;
     double *partials;   // per-block partial sums
+    double *partials2;  // second-level partials (energy)
     unsigned int *ticket;
     int npart;
 };
@@ -90,6 +93,13 @@ int dft_init_tables(blr_plan *P, cudaStream_t s);
 int dft_expand(blr_plan *P, const float *vt, float *out, int mode, cudaStream_t s);
 // pi(f) (+ A * vadd when vadd != nullptr) into ft.
 int dft_project(blr_plan *P, const float *f, float *ft, const float *vadd, cudaStream_t s);
+
+// dft_tc.cu (BLR_MIXED)
+size_t tc_table_bytes(const blr_plan *P, int project);
+bool tc_supported(const blr_plan *P);
+int tc_init_tables(blr_plan *P, cudaStream_t s);
+int tc_axis1(blr_plan *P, int project, const float *X, float *D, float scale, int mode,
+             cudaStream_t s);
 
 // sweeps.cu
 int sweep_setup(blr_plan *P);

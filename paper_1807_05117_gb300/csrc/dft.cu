@@ -232,9 +232,10 @@ k_gemm_axis1(const float *__restrict__ A, int lda, const float *__restrict__ B,
 }
 
 // ---------------------------------------------------------------------------
-// stage A': axis 3, grid -> band.  Block: 32 rows x all k3; x3 in chunks of 32.
+// stage A': axis 3, grid -> band.  Block: 8 rows (one per warp) x all k3;
+// x3 in chunks of 32.
 //   out[row][k3] = sum_x3 (c - i s)[k3][x3] P2[row][x3]  (+ A * vadd)
-constexpr int PA_ROWS = 32;
+constexpr int PA_ROWS = 8;
 __global__ void __launch_bounds__(256)
 k_project_axis3(const float *__restrict__ in, const float *__restrict__ T3c,
                 const float *__restrict__ T3s, float *__restrict__ out,
@@ -245,9 +246,10 @@ k_project_axis3(const float *__restrict__ in, const float *__restrict__ T3c,
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int row0 = blockIdx.x * PA_ROWS;
     const int nk = (B3 + 31) / 32;     // k3 sub-blocks per lane (B3 <= 64)
-    float are[4][2], aim[4][2];
+    constexpr int RW = PA_ROWS / 8;    // rows per warp
+    float are[RW][2], aim[RW][2];
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < RW; ++r)
 #pragma unroll
         for (int t = 0; t < 2; ++t) are[r][t] = aim[r][t] = 0.f;
     for (int x0 = 0; x0 < N3; x0 += 32) {
@@ -281,8 +283,8 @@ k_project_axis3(const float *__restrict__ in, const float *__restrict__ T3c,
                 if (t >= nk) break;
                 float c = tc[xx][lane + 32 * t], s = ts[xx][lane + 32 * t];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    float pr = pre[warp * 4 + r][xx], pi = pim[warp * 4 + r][xx];
+                for (int r = 0; r < RW; ++r) {
+                    float pr = pre[warp * RW + r][xx], pi = pim[warp * RW + r][xx];
                     are[r][t] = fmaf(c, pr, fmaf(s, pi, are[r][t]));
                     aim[r][t] = fmaf(c, pi, fmaf(-s, pr, aim[r][t]));
                 }
@@ -291,8 +293,8 @@ k_project_axis3(const float *__restrict__ in, const float *__restrict__ T3c,
         __syncthreads();
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        int row = row0 + warp * 4 + r;
+    for (int r = 0; r < RW; ++r) {
+        int row = row0 + warp * RW + r;
         if (row >= rows) continue;
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
@@ -340,6 +342,8 @@ int dft_expand(blr_plan *P, const float *vt, float *out, int mode, cudaStream_t 
                                    P->N2, P->N3);
     BLR_CK_LAUNCH();
     // stage C
+    if (P->p.precision == BLR_MIXED)
+        return tc_axis1(P, 0, P->dft_big, out, mode == 0 ? 1.f : -P->dt, mode, s);
     const long long ncol = (long long)P->N2 * P->N3;
     dim3 gc((unsigned)ceil_div_ll(ncol, 128), (unsigned)ceil_div_ll(P->N1, 64), 3u);
     if (mode == 0)
@@ -357,11 +361,16 @@ int dft_expand(blr_plan *P, const float *vt, float *out, int mode, cudaStream_t 
 int dft_project(blr_plan *P, const float *f, float *ft, const float *vadd, cudaStream_t s) {
     const long long ncol = (long long)P->N2 * P->N3;
     // stage C'
-    dim3 gc((unsigned)ceil_div_ll(ncol, 128), (unsigned)ceil_div_ll(2 * P->B1, 64), 3u);
-    k_gemm_axis1<false, 0><<<gc, 256, 0, s>>>(P->W1, P->N1, f, P->V, P->dft_big,
-                                              2LL * P->B1 * ncol, 2 * P->B1, P->N1, ncol, 1.f,
-                                              P->dstatus);
-    BLR_CK_LAUNCH();
+    if (P->p.precision == BLR_MIXED) {
+        int rc = tc_axis1(P, 1, f, P->dft_big, 1.f, 0, s);
+        if (rc) return rc;
+    } else {
+        dim3 gc((unsigned)ceil_div_ll(ncol, 128), (unsigned)ceil_div_ll(2 * P->B1, 64), 3u);
+        k_gemm_axis1<false, 0><<<gc, 256, 0, s>>>(P->W1, P->N1, f, P->V, P->dft_big,
+                                                  2LL * P->B1 * ncol, 2 * P->B1, P->N1, ncol,
+                                                  1.f, P->dstatus);
+        BLR_CK_LAUNCH();
+    }
     // stage B'
     dim3 gb((unsigned)ceil_div_ll(P->N3, 32), (unsigned)ceil_div_ll(P->B2, 32), 3u * P->B1);
     k_axis2<-1><<<gb, 256, 0, s>>>(P->dft_big, P->T2c, P->T2s, P->dft_small, P->N2, P->B2,

@@ -1,0 +1,482 @@
+// Mixed-precision axis-1 contractions of the truncated DFTs on tcgen05 tensor
+// cores (BLR_MIXED): the two largest stages of iota and pi (Section 3.1, Eq. 33),
+//   expand : v[c][x1][col]  = sum_kappa W1[kappa][x1] A2[c][kappa][col]
+//   project: P1[c][kappa][col] = sum_x1  W1[kappa][x1] f[c][x1][col]
+// with kappa = (k1, re|im) and col = (x2, x3).
+//
+// Both operands are split into BF16 hi + lo parts (x = hi + lo, lo = bf16(x - hi))
+// and the product is accumulated in FP32 in tensor memory as
+// Ah Bh + Ah Bl + Al Bh (the lo*lo term is below FP32 resolution).  The DFT table
+// operand (A, 128-row M tiles, K-major, 128-byte swizzle) is built once per plan in
+// FP64 and stored pre-swizzled; the field operand (B, N = columns of the tile) is
+// read as FP32, split and transposed into the same K-major swizzled layout in
+// shared memory by the CTA itself, so nothing extra goes through HBM.
+// One elected thread issues the MMAs; completion is signalled through an mbarrier
+// whose wait is bounded (timeout -> BLR_FLAG_TIMEOUT, TMEM freed, no output).
+#include <cuda_bf16.h>
+
+#include "blr_internal.cuh"
+
+namespace {
+
+constexpr int TC_THREADS = 256;
+constexpr int TC_M = 128;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Byte offset of the 16-byte chunk (row r, k-chunk kc = k/8) in a K-major,
+// 128-byte-swizzled BF16 tile with `rows` rows: 64-element K atoms stacked
+// along K, 8-row groups of 1024 bytes, chunk index XOR-ed with the row.
+__host__ __device__ __forceinline__ uint32_t swz_chunk(int r, int kc, int rows) {
+    return (uint32_t)((kc >> 3) * rows * 128 + (r >> 3) * 1024 + (r & 7) * 128 +
+                      (((kc & 7) ^ (r & 7)) << 4));
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor for kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t umma_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t *r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// Split 8 floats into BF16 hi and lo halves, each packed into a uint4.
+__device__ __forceinline__ void split8(const float *x, uint4 &hi, uint4 &lo) {
+    float h[8], l[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        h[i] = __bfloat162float(__float2bfloat16_rn(x[i]));
+        l[i] = x[i] - h[i];
+    }
+    hi = make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]),
+                    pack_bf16(h[6], h[7]));
+    lo = make_uint4(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]), pack_bf16(l[4], l[5]),
+                    pack_bf16(l[6], l[7]));
+}
+
+struct TcArgs {
+    const uint8_t *tab;      // [mtiles][hi|lo][128 x Kpad] BF16, swizzled
+    int mtiles, M;           // M tiles of 128 rows; rows written (< M)
+    int K, Kpad;             // contraction length and its multiple of 64
+    const float *X;          // field operand, per batch [K][ncols]
+    long long xstride;       // batch stride of X (floats)
+    float *D;                // output, per batch [M][ncols]
+    long long dstride;
+    long long ncols;
+    int ntile;               // columns per tile (multiple of 32, <= 256)
+    int col_tiles, tiles;    // column tiles per batch, tiles over the 3 batches
+    int nstage;              // FP32 staging buffers (2: next tile prefetched)
+    int bulk;                // rows may be fetched with cp.async.bulk (16-byte aligned)
+    int tmem_cols;           // power of two >= mtiles * ntile
+    float scale;
+    int mode;                // 0 store scale*acc; 1 displacement (clamp + flags)
+    int *status;
+};
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_arrive(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+// Bounded wait for the phase of the given parity; false after ~2 s.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    uint32_t done = 0;
+    const long long t0 = clock64();
+    while (true) {
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > 4000000000LL) return false;
+    }
+}
+
+// Persistent: each CTA loads the table once, then walks column tiles
+// t = blockIdx.x, blockIdx.x + gridDim.x, ...; with two staging buffers the next
+// tile's rows stream in (cp.async.bulk) while the current one is converted,
+// multiplied and written.
+__global__ void __launch_bounds__(TC_THREADS, 1) k_tc_axis1(TcArgs p) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    uint8_t *base = smem_raw + (((raw + 1023) & ~1023u) - raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const size_t tab_bytes = (size_t)TC_M * p.Kpad * 2;            // one hi or lo table tile
+    const size_t all_tab = 2 * tab_bytes * p.mtiles;
+    const size_t stage_bytes = (size_t)p.K * p.ntile * 4;
+    const size_t b_bytes = (size_t)p.ntile * p.Kpad * 2;           // one hi or lo field tile
+    uint8_t *sA = base;
+    float *stage0 = reinterpret_cast<float *>(sA + all_tab);
+    uint8_t *sBh = reinterpret_cast<uint8_t *>(stage0) + p.nstage * stage_bytes;
+    uint8_t *sBl = sBh + b_bytes;
+    float *sE = reinterpret_cast<float *>(sBl + b_bytes);             // 8 warps x 32 x 32 floats
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sE + TC_THREADS / 32 * 1024);   // load[0], load[1], mma
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 3);
+    __shared__ int s_fail;
+    const uint32_t bar_load0 = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[2]);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tslot)),
+                     "r"(p.tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        mbar_init(bar_load0, 1);
+        mbar_init(bar_load0 + 8, 1);
+        mbar_init(bar_mma, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        s_fail = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tslot;
+
+    // rows of tile t into staging buffer sb (warp 0; bulk path only)
+    auto tile_cols = [&](int t, long long *col0, int *w, const float **src) {
+        const int batch = t / p.col_tiles, ct = t - batch * p.col_tiles;
+        *col0 = (long long)ct * p.ntile;
+        const long long left = p.ncols - *col0;
+        *w = (int)(left < p.ntile ? left : p.ntile);
+        *src = p.X + batch * p.xstride + *col0;
+    };
+    auto issue_tile = [&](int t, int sb, uint32_t extra_bytes) {
+        long long col0;
+        int w;
+        const float *src;
+        tile_cols(t, &col0, &w, &src);
+        const uint32_t bar = bar_load0 + 8u * sb;
+        const uint32_t row_bytes = (uint32_t)w * 4u;
+        if (lane == 0) mbar_expect_arrive(bar, row_bytes * (uint32_t)p.K + extra_bytes);
+        __syncwarp();
+        const uint32_t dst0 = smem_u32(stage0) + (uint32_t)(sb * stage_bytes);
+        for (int k = lane; k < p.K; k += 32)
+            bulk_g2s(dst0 + (uint32_t)k * p.ntile * 4u, src + (long long)k * p.ncols, row_bytes, bar);
+    };
+
+    int first = blockIdx.x;
+    if (warp == 0) {
+        if (p.bulk && first < p.tiles) {
+            if (lane == 0) bulk_g2s(smem_u32(sA), p.tab, (uint32_t)all_tab, bar_load0);
+            issue_tile(first, 0, (uint32_t)all_tab);
+        } else {
+            if (lane == 0) mbar_expect_arrive(bar_load0, (uint32_t)all_tab);
+            __syncwarp();
+            if (lane == 0) bulk_g2s(smem_u32(sA), p.tab, (uint32_t)all_tab, bar_load0);
+        }
+    }
+
+    const uint32_t idesc = umma_idesc(TC_M, p.ntile);
+    uint32_t pend_bar = 0, pend_par = 0;   // prefetch issued this iteration
+    uint32_t own_bar = 0, own_par = 0;     // load whose wait expired
+    int i = 0;
+    for (int t = first; t < p.tiles; t += gridDim.x, ++i) {
+        const int sb = (p.nstage == 2) ? (i & 1) : 0;
+        const int nxt = t + gridDim.x;
+        long long col0;
+        int w;
+        const float *src;
+        tile_cols(t, &col0, &w, &src);
+        float *stage = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(stage0) + sb * stage_bytes);
+        bool ok = true;
+        if (p.bulk) {
+            if (p.nstage == 2) {
+                if (nxt < p.tiles) {
+                    if (warp == 0) issue_tile(nxt, sb ^ 1, 0u);
+                    pend_bar = bar_load0 + 8u * (sb ^ 1);
+                    pend_par = (uint32_t)((i + 1) >> 1) & 1u;
+                } else {
+                    pend_bar = 0;
+                }
+            } else if (i > 0 && warp == 0) {
+                issue_tile(t, 0, 0u);   // the only buffer is free again
+            }
+            const uint32_t use = (p.nstage == 2) ? (uint32_t)(i >> 1) : (uint32_t)i;
+            ok = mbar_wait(bar_load0 + 8u * sb, use & 1u);
+            if (!ok) {
+                own_bar = bar_load0 + 8u * sb;
+                own_par = use & 1u;
+            }
+        } else {
+            if (i == 0) ok = mbar_wait(bar_load0, 0u);   // table
+            for (int e = tid; e < p.K * p.ntile; e += TC_THREADS) {
+                const int k = e / p.ntile, r = e - k * p.ntile;
+                stage[e] = r < w ? __ldg(src + (long long)k * p.ncols + r) : 0.f;
+            }
+            __syncthreads();
+        }
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) s_fail = 1;
+            break;
+        }
+        // FP32 staging [K][ntile] -> BF16 hi / lo, K-major swizzled [ntile][Kpad]
+        const int nkc = p.Kpad >> 3;
+        for (int it = tid; it < p.ntile * nkc; it += TC_THREADS) {
+            const int r = it % p.ntile, kc = it / p.ntile;
+            float x[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int k = kc * 8 + q;
+                x[q] = (k < p.K && r < w) ? stage[k * p.ntile + r] : 0.f;
+            }
+            uint4 hi, lo;
+            split8(x, hi, lo);
+            const uint32_t off = swz_chunk(r, kc, p.ntile);
+            *reinterpret_cast<uint4 *>(sBh + off) = hi;
+            *reinterpret_cast<uint4 *>(sBl + off) = lo;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (tid == 0) {
+            const uint32_t bh0 = smem_u32(sBh), bl0 = smem_u32(sBl);
+            for (int mt = 0; mt < p.mtiles; ++mt) {
+                const uint32_t ah0 = smem_u32(sA + (size_t)(2 * mt) * tab_bytes);
+                const uint32_t al0 = ah0 + (uint32_t)tab_bytes;
+                const uint32_t d = tmem + (uint32_t)(mt * p.ntile);
+                for (int j = 0; j < p.Kpad / 16; ++j) {
+                    // K step of 16 elements: atom column j/4, 32 bytes per step inside it
+                    const uint32_t oa = (uint32_t)((j >> 2) * TC_M * 128 + (j & 3) * 32);
+                    const uint32_t ob = (uint32_t)((j >> 2) * p.ntile * 128 + (j & 3) * 32);
+                    const uint64_t ah = umma_desc(ah0 + oa), al = umma_desc(al0 + oa);
+                    const uint64_t bh = umma_desc(bh0 + ob), bl = umma_desc(bl0 + ob);
+                    umma_bf16(d, ah, bh, idesc, j > 0);
+                    umma_bf16(d, ah, bl, idesc, 1u);
+                    umma_bf16(d, al, bh, idesc, 1u);
+                }
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    bar_mma));
+        }
+        ok = mbar_wait(bar_mma, (uint32_t)(i & 1));
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) s_fail = 1;
+            break;
+        }
+        // epilogue: warp w reads TMEM lanes 32*(w%4).. (rows), columns of half w/4,
+        // 32 x 32 blocks transposed through an XOR-swizzled buffer so that each
+        // store instruction writes 128 contiguous bytes of one output row
+        float *D = p.D + (t / p.col_tiles) * p.dstride;
+        const int lg = warp & 3, half = warp >> 2;
+        const int cols_half = p.ntile >> 1;
+        float *T = sE + warp * 1024;
+        int flags = 0;
+        for (int mt = 0; mt < p.mtiles; ++mt) {
+            const int row0 = mt * TC_M + lg * 32;
+            for (int c = half * cols_half; c < (half + 1) * cols_half; c += 32) {
+                uint32_t rv[32];
+                tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(mt * p.ntile + c), rv);
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    float v = __uint_as_float(rv[q]) * p.scale;
+                    if (p.mode == 1) {
+                        const bool valid = (row0 + lane < p.M) && (c + q < w);
+                        if (valid && !(fabsf(v) < 1.f)) flags |= (v != v) ? BLR_FLAG_NAN : BLR_FLAG_CFL;
+                        v = fminf(fmaxf(v, -1.f), 0.99999994f);
+                    }
+                    T[lane * 32 + (q ^ lane)] = v;
+                }
+                __syncwarp();
+                const bool col_ok = (c + lane) < w;
+                for (int q = 0; q < 32; ++q) {
+                    const int row = row0 + q;
+                    if (row < p.M && col_ok)
+                        D[(long long)row * p.ncols + col0 + c + lane] = T[q * 32 + (lane ^ q)];
+                }
+                __syncwarp();
+            }
+        }
+        if (flags) atomicOr(p.status, flags);
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+    }
+    if (s_fail) {
+        // a wait expired: record it, give this CTA's outstanding bulk copies a
+        // bounded time to land, then release TMEM
+        if (tid == 0) atomicOr(p.status, BLR_FLAG_TIMEOUT);
+        if (own_bar) mbar_wait(own_bar, own_par);
+        if (pend_bar) mbar_wait(pend_bar, pend_par);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(p.tmem_cols));
+}
+
+// Table tiles, FP64 phases split into BF16 hi/lo.  transpose == 0: row = x1,
+// k = kappa (expand); transpose == 1: row = kappa, k = x1 (project).
+// W(kappa, x1) = cos(2 pi k_j x1 / N1) for kappa = 2j, -sin(...) for 2j+1.
+__global__ void k_tc_table(uint8_t *tab, int mtiles, int M, int K, int Kpad, int N1, int B1,
+                           int project) {
+    const long long total = (long long)mtiles * TC_M * Kpad;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(e % Kpad);
+        const int rr = (int)((e / Kpad) % TC_M);
+        const int mt = (int)(e / ((long long)Kpad * TC_M));
+        const int row = mt * TC_M + rr;
+        double w = 0.0;
+        if (row < M && k < K) {
+            const int kappa = project ? row : k, x1 = project ? k : row;
+            const int j = kappa >> 1;
+            long long ph = ((long long)(j - B1 / 2) * x1) % N1;
+            if (ph < 0) ph += N1;
+            double s, c;
+            sincospi(2.0 * (double)ph / (double)N1, &s, &c);
+            w = (kappa & 1) ? -s : c;
+        }
+        const __nv_bfloat16 h = __double2bfloat16(w);
+        const __nv_bfloat16 l = __double2bfloat16(w - (double)__bfloat162float(h));
+        const size_t tile = (size_t)TC_M * Kpad * 2;
+        uint8_t *hi = tab + (size_t)(2 * mt) * tile, *lo = hi + tile;
+        const uint32_t off = swz_chunk(rr, k >> 3, TC_M) + (uint32_t)((k & 7) * 2);
+        *reinterpret_cast<__nv_bfloat16 *>(hi + off) = h;
+        *reinterpret_cast<__nv_bfloat16 *>(lo + off) = l;
+    }
+}
+
+int pow2_at_least(int v) {
+    int p = 32;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+constexpr size_t TC_SMEM_MAX = 225 * 1024;
+
+size_t tc_smem_bytes(int mtiles, int K, int Kpad, int nt, int nstage) {
+    return 1024 + 2 * (size_t)TC_M * Kpad * 2 * mtiles + (size_t)nstage * K * nt * 4 +
+           2 * (size_t)nt * Kpad * 2 + (size_t)TC_THREADS / 32 * 1024 * 4 + 3 * 8 + 16;
+}
+
+// Largest column tile (256 .. 32) whose shared memory and TMEM fit, preferring
+// two staging buffers (prefetch) over a larger tile.
+bool tc_shape(int mtiles, int K, int Kpad, int *ntile, int *nstage, size_t *smem) {
+    for (int ns = 2; ns >= 1; --ns)
+        for (int nt = 256; nt >= 32; nt >>= 1) {
+            if (mtiles * nt > 512) continue;
+            const size_t sb = tc_smem_bytes(mtiles, K, Kpad, nt, ns);
+            if (sb <= TC_SMEM_MAX) {
+                *ntile = nt;
+                *nstage = ns;
+                *smem = sb;
+                return true;
+            }
+        }
+    return false;
+}
+
+}  // namespace
+
+// Geometry of the two tensor-core contractions of a plan.
+void tc_geometry(const blr_plan *P, int project, int *mtiles, int *M, int *K, int *Kpad) {
+    *M = project ? 2 * P->B1 : P->N1;
+    *K = project ? P->N1 : 2 * P->B1;
+    *mtiles = (*M + TC_M - 1) / TC_M;
+    *Kpad = (*K + 63) / 64 * 64;
+}
+
+size_t tc_table_bytes(const blr_plan *P, int project) {
+    int mt, M, K, Kp;
+    tc_geometry(P, project, &mt, &M, &K, &Kp);
+    return (size_t)mt * 2 * TC_M * Kp * 2;
+}
+
+// Whether the mixed path supports this plan's shapes.
+bool tc_supported(const blr_plan *P) {
+    for (int pr = 0; pr < 2; ++pr) {
+        int mt, M, K, Kp, nt, ns;
+        size_t sm;
+        tc_geometry(P, pr, &mt, &M, &K, &Kp);
+        if (!tc_shape(mt, K, Kp, &nt, &ns, &sm)) return false;
+    }
+    return true;
+}
+
+int tc_init_tables(blr_plan *P, cudaStream_t s) {
+    for (int pr = 0; pr < 2; ++pr) {
+        int mt, M, K, Kp;
+        tc_geometry(P, pr, &mt, &M, &K, &Kp);
+        k_tc_table<<<256, 256, 0, s>>>(pr ? P->tc_tab_project : P->tc_tab_expand, mt, M, K, Kp,
+                                        P->N1, P->B1, pr);
+        BLR_CK_LAUNCH();
+    }
+    return BLR_OK;
+}
+
+// D[c] = W (x) X[c] on tensor cores; see TcArgs.
+int tc_axis1(blr_plan *P, int project, const float *X, float *D, float scale, int mode,
+             cudaStream_t s) {
+    TcArgs a;
+    tc_geometry(P, project, &a.mtiles, &a.M, &a.K, &a.Kpad);
+    size_t smem = 0;
+    if (!tc_shape(a.mtiles, a.K, a.Kpad, &a.ntile, &a.nstage, &smem)) return BLR_EINVAL;
+    a.tab = project ? P->tc_tab_project : P->tc_tab_expand;
+    a.ncols = (long long)P->N2 * P->N3;
+    a.X = X;
+    a.xstride = (long long)a.K * a.ncols;
+    a.D = D;
+    a.dstride = (long long)a.M * a.ncols;
+    a.col_tiles = (int)ceil_div_ll(a.ncols, a.ntile);
+    a.tiles = 3 * a.col_tiles;
+    // bulk row copies need 16-byte aligned rows and sizes
+    a.bulk = (a.ncols % 4 == 0) && ((uintptr_t)X % 16 == 0);
+    a.tmem_cols = pow2_at_least(a.mtiles * a.ntile);
+    a.scale = scale;
+    a.mode = mode;
+    a.status = P->dstatus;
+    int sms = 0;
+    BLR_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device));
+    BLR_CK(cudaFuncSetAttribute(k_tc_axis1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = a.tiles < sms ? a.tiles : sms;
+    k_tc_axis1<<<grid, TC_THREADS, smem, s>>>(a);
+    BLR_CK_LAUNCH();
+    return BLR_OK;
+}

@@ -25,6 +25,12 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
     return t;   // valid in thread 0
 }
 
+// Band index of float i of an interleaved complex [3][B1][B2][B3] array.
+__device__ __forceinline__ long long coef_index(long long i, long long nb) {
+    const long long c = i >> 1;
+    return c < nb ? c : (c < 2 * nb ? c - nb : c - 2 * nb);
+}
+
 // Returns true in every thread of the last block to arrive.
 __device__ __forceinline__ bool last_block(unsigned int *ticket) {
     __shared__ bool is_last;
@@ -42,22 +48,34 @@ __device__ __forceinline__ double ordered_sum(const double *part, int count, int
     return t;
 }
 
-__global__ void __launch_bounds__(1024)
-k_energy_finalize(const double *__restrict__ partials, int np, const float *__restrict__ vt,
-                  const float *__restrict__ A, long long nb, double inv_sigma2,
-                  double *__restrict__ sc, double *__restrict__ out, int *status) {
-    __shared__ double red[32];
+// Energy of Eq. 35: every block sums a strided share of the per-block image-term
+// partials of the last state step and of A |v~|^2; the last block adds the
+// block partials in block order.
+__global__ void __launch_bounds__(RT)
+k_energy(const double *__restrict__ partials, int np, const float *__restrict__ vt,
+         const float *__restrict__ A, long long nb, double inv_sigma2,
+         double *__restrict__ part2, unsigned int *ticket, double *__restrict__ sc,
+         double *__restrict__ out, int *status) {
+    __shared__ double red[RT / 32];
     double sd = 0.0;
-    for (int i = threadIdx.x; i < np; i += 1024) sd += partials[i];
-    sd = block_sum<1024>(sd, red);
+    for (int i = blockIdx.x * RT + threadIdx.x; i < np; i += gridDim.x * RT) sd += partials[i];
+    sd = block_sum<RT>(sd, red);
+    if (threadIdx.x == 0) part2[2 * blockIdx.x] = sd;
     double sr = 0.0;
-    for (long long i = threadIdx.x; i < 3 * nb; i += 1024) {
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < 3 * nb;
+         i += (long long)gridDim.x * RT) {
+        const long long kk = i < nb ? i : (i < 2 * nb ? i - nb : i - 2 * nb);
         const double re = vt[2 * i], im = vt[2 * i + 1];
-        sr += (double)A[i % nb] * (re * re + im * im);
+        sr += (double)A[kk] * (re * re + im * im);
     }
-    sr = block_sum<1024>(sr, red);
+    sr = block_sum<RT>(sr, red);
+    if (threadIdx.x == 0) part2[2 * blockIdx.x + 1] = sr;
+    if (!last_block(ticket)) return;
     if (threadIdx.x == 0) {
-        const double edata = sd * inv_sigma2, ereg = 0.5 * sr, e = ereg + edata;
+        *ticket = 0;
+        const double sdt = ordered_sum(part2, gridDim.x, 2, 0);
+        const double srt = ordered_sum(part2, gridDim.x, 2, 1);
+        const double edata = sdt * inv_sigma2, ereg = 0.5 * srt, e = ereg + edata;
         sc[SC_E] = e;
         sc[SC_EREG] = ereg;
         sc[SC_EDATA] = edata;
@@ -79,7 +97,7 @@ k_dot(const float *__restrict__ a, const float *__restrict__ b, const float *__r
     double acc = 0.0;
     for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT) {
         double t = (double)a[i] * (double)b[i];
-        if (w) t /= (double)w[(i >> 1) % nb];
+        if (w) t /= (double)w[coef_index(i, nb)];
         acc += t;
     }
     acc = block_sum<RT>(acc, red);
@@ -126,11 +144,11 @@ k_pcg_init(const float *__restrict__ rhs, float *__restrict__ x, float *__restri
     double rz = 0.0, rr = 0.0;
     for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT) {
         const float ri = rhs[i];
-        const float a = A[(i >> 1) % nb];
+        const float zi = ri / A[coef_index(i, nb)];
         x[i] = 0.f;
         r[i] = ri;
-        p[i] = ri / a;
-        rz += (double)ri * (double)ri / (double)a;
+        p[i] = zi;
+        rz += (double)ri * (double)zi;
         rr += (double)ri * (double)ri;
     }
     rz = block_sum<RT>(rz, red);
@@ -160,8 +178,8 @@ k_pcg_update(float *__restrict__ x, float *__restrict__ r, const float *__restri
         x[i] = fmaf(alpha, p[i], x[i]);
         const float ri = fmaf(-alpha, q[i], r[i]);
         r[i] = ri;
-        const double a = (double)A[(i >> 1) % nb];
-        rz += (double)ri * (double)ri / a;
+        const float zi = ri / A[coef_index(i, nb)];
+        rz += (double)ri * (double)zi;
         rr += (double)ri * (double)ri;
     }
     rz = block_sum<RT>(rz, red);
@@ -186,7 +204,7 @@ k_pcg_direction(float *__restrict__ p, const float *__restrict__ r, const float 
                 long long n, long long nb, const double *__restrict__ sc) {
     const float beta = (float)sc[SC_BETA];
     for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT)
-        p[i] = fmaf(beta, p[i], r[i] / A[(i >> 1) % nb]);
+        p[i] = fmaf(beta, p[i], r[i] / A[coef_index(i, nb)]);
 }
 
 // y = a + alpha x (FP32; alpha from the host).
@@ -207,9 +225,9 @@ int vec_blocks(const blr_plan *P) {
 int reduce_partials_needed() { return 2 * RBLOCKS; }
 
 int energy_finalize(blr_plan *P, const float *vt, double *energy_out, int nblocks, cudaStream_t s) {
-    k_energy_finalize<<<1, 1024, 0, s>>>(P->partials, nblocks, vt, P->A, P->nb,
-                                         1.0 / (P->p.sigma * P->p.sigma), P->dsc, energy_out,
-                                         P->dstatus);
+    k_energy<<<vec_blocks(P), RT, 0, s>>>(P->partials, nblocks, vt, P->A, P->nb,
+                                          1.0 / (P->p.sigma * P->p.sigma), P->partials2,
+                                          P->ticket, P->dsc, energy_out, P->dstatus);
     BLR_CK_LAUNCH();
     return BLR_OK;
 }

@@ -1,8 +1,12 @@
 """CUDA path (through the C-ABI) against the FP64 oracle on identical seeded
-inputs.  Tolerances (relative L2, FP32 path): 1e-5 on iota / pi, the state and
-the adjoint fields; 1e-4 on the gradient and the Gauss-Newton HVP; PCG
-iterates 1e-4; a full registration's final energy 1e-3 with PCG iteration
-counts within +-1 per Newton step."""
+inputs.  Tolerances (relative L2):
+  FP32 path : 1e-5 on iota / pi, the state and the adjoint fields; 1e-4 on the
+              gradient and the Gauss-Newton HVP; PCG iterates 1e-4;
+  mixed path: (BF16 hi+lo split operands on tensor cores, FP32 accumulation in
+              the axis-1 DFT stages; everything else FP32) 5e-5 on the fields,
+              5e-4 on the gradient, the HVP and the PCG iterates;
+a full registration's final energy within 1e-3 with PCG iteration counts within
++-1 per Newton step."""
 
 import numpy as np
 import pytest
@@ -27,10 +31,15 @@ def blr():
     return _blr
 
 
+TOL = {"fp32": dict(field=1e-5, grad=1e-4, pcg=1e-4),
+       "mixed": dict(field=5e-5, grad=5e-4, pcg=5e-4)}
+
+
 class Case:
     """Seeded inputs, rounded once to FP32 and given to both sides."""
 
-    def __init__(self, blr, n, band, nt, seed, bound, sigma=1.0, pair="blob", max_disp=2.0):
+    def __init__(self, blr, n, band, nt, seed, bound, sigma=1.0, pair="blob", max_disp=2.0,
+                 precision="fp32"):
         n, band = tuple(n), tuple(band)
         if pair == "blob":
             I0, I1, _ = synth.blob_pair(n, seed, max_disp=max_disp)
@@ -41,7 +50,10 @@ class Case:
         (self.I0f, self.I0), (self.I1f, self.I1), (self.vtf, self.vt), (self.dvf, self.dv) = \
             synth.as_device_inputs(I0, I1, vt, dvt)
         self.p = O.Params(n=n, band=band, nt=nt, sigma=sigma)
-        self.plan = blr.Plan(n, band, nt, sigma=sigma)
+        self.precision = precision
+        self.tol = TOL[precision]
+        self.plan = blr.Plan(n, band, nt, sigma=sigma,
+                             precision=blr.BLR_MIXED if precision == "mixed" else blr.BLR_FP32)
         self.dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
         self.plan.set_images(self.dev(self.I0f), self.dev(self.I1f))
         self.n, self.band = n, band
@@ -66,19 +78,21 @@ CASES = {
 }
 
 
-@pytest.fixture(scope="module", params=sorted(CASES))
+@pytest.fixture(scope="module", params=[(c, pr) for c in sorted(CASES) for pr in ("fp32", "mixed")],
+                ids=lambda t: f"{t[0]}-{t[1]}")
 def case(request, blr):
-    return Case(blr, **CASES[request.param])
+    name, precision = request.param
+    return Case(blr, precision=precision, **CASES[name])
 
 
 def test_expand_project_parity(case):
     v = case.field()
     case.plan.expand(case.dev(case.vtf), v)
-    assert rel(v.cpu().numpy(), O.expand(case.vt, case.p.n)) <= 1e-5
+    assert rel(v.cpu().numpy(), O.expand(case.vt, case.p.n)) <= case.tol["field"]
     f = np.random.default_rng(7).normal(size=(3,) + case.n).astype(np.float32)
     ft = case.coef()
     case.plan.project(case.dev(f), ft)
-    assert rel(ft.cpu().numpy(), O.project(f.astype(np.float64), case.band)) <= 1e-5
+    assert rel(ft.cpu().numpy(), O.project(f.astype(np.float64), case.band)) <= case.tol["field"]
 
 
 def test_state_and_adjoint_parity(case):
@@ -91,12 +105,13 @@ def test_state_and_adjoint_parity(case):
     assert case.plan.status() == 0
     pt = O.Point(case.vt, case.I0, case.I1, case.p)
     _, b_ref, lam0_ref = pt.gradient()
-    assert rel(m1.cpu().numpy(), pt.m[-1]) <= 1e-5
+    tol = case.tol["field"]
+    assert rel(m1.cpu().numpy(), pt.m[-1]) <= tol
     E = e.cpu().numpy()
-    assert abs(E[0] - pt.energy) <= 1e-5 * pt.energy
+    assert abs(E[0] - pt.energy) <= tol * pt.energy
     assert abs(E[1] - pt.energy_reg) <= 1e-5 * pt.energy_reg
-    assert rel(lam0.cpu().numpy(), lam0_ref) <= 1e-5
-    assert rel(b.cpu().numpy(), b_ref) <= 1e-5
+    assert rel(lam0.cpu().numpy(), lam0_ref) <= tol
+    assert rel(b.cpu().numpy(), b_ref) <= tol
 
 
 def test_gradient_and_hessvec_parity(case):
@@ -105,8 +120,8 @@ def test_gradient_and_hessvec_parity(case):
     h = case.coef()
     case.plan.hessvec(case.dev(case.dvf), h)
     pt = O.Point(case.vt, case.I0, case.I1, case.p)
-    assert rel(g.cpu().numpy(), pt.gradient()[0]) <= 1e-4
-    assert rel(h.cpu().numpy(), pt.gn_hessvec(case.dv)[0]) <= 1e-4
+    assert rel(g.cpu().numpy(), pt.gradient()[0]) <= case.tol["grad"]
+    assert rel(h.cpu().numpy(), pt.gn_hessvec(case.dv)[0]) <= case.tol["grad"]
 
 
 def test_pcg_iterates_parity(case):
@@ -120,8 +135,8 @@ def test_pcg_iterates_parity(case):
     x_ref, its_ref, rel_ref = O.pcg(lambda v: pt.gn_hessvec(v)[0], rhs_ref, 1.0 / pt.A[None],
                                     0.0, 4)
     assert its == its_ref == 4
-    assert rel(x.cpu().numpy(), x_ref) <= 1e-4
-    assert abs(relres - rel_ref) <= 1e-3 * rel_ref
+    assert rel(x.cpu().numpy(), x_ref) <= case.tol["pcg"]
+    assert abs(relres - rel_ref) <= 10 * case.tol["pcg"] * rel_ref
 
 
 def test_deterministic_bitwise(case):
@@ -177,11 +192,13 @@ def test_hessvec_needs_a_forward_solve(blr):
 # --- full registration (the 32^3 blob workload) --------------------------------
 
 
-def test_newton_registration_matches_oracle(blr):
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_newton_registration_matches_oracle(blr, precision):
     n, band, nt = (32, 32, 32), (8, 8, 8), 10
     I0, I1, _ = synth.blob_pair(n, 1001, max_disp=2.0)
     (I0f, I0d), (I1f, I1d) = synth.as_device_inputs(I0, I1)
-    plan = blr.Plan(n, band, nt)
+    plan = blr.Plan(n, band, nt,
+                    precision=blr.BLR_MIXED if precision == "mixed" else blr.BLR_FP32)
     plan.set_images(torch.from_numpy(I0f).cuda(), torch.from_numpy(I1f).cuda())
     vt = torch.zeros((3,) + band, dtype=torch.complex64, device="cuda")
     rep = plan.newton(vt, 5, 10, 1e-6)
@@ -198,9 +215,10 @@ def test_newton_registration_matches_oracle(blr):
 
 
 @pytest.mark.slow
-def test_full_size_gradient_and_hessvec(blr):
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_full_size_gradient_and_hessvec(blr, precision):
     c = Case(blr, n=(128, 128, 128), band=(32, 32, 32), nt=10, seed=2002, bound=120.0,
-             pair="phantom", max_disp=6.0)
+             pair="phantom", max_disp=6.0, precision=precision)
     g = c.coef()
     e = torch.zeros(3, dtype=torch.float64, device="cuda")
     c.plan.gradient(c.dev(c.vtf), g, e)
@@ -208,6 +226,6 @@ def test_full_size_gradient_and_hessvec(blr):
     c.plan.hessvec(c.dev(c.dvf), h)
     assert c.plan.status() == 0
     pt = O.Point(c.vt, c.I0, c.I1, c.p)
-    assert abs(float(e[0]) - pt.energy) <= 1e-5 * pt.energy
-    assert rel(g.cpu().numpy(), pt.gradient()[0]) <= 1e-4
-    assert rel(h.cpu().numpy(), pt.gn_hessvec(c.dv)[0]) <= 1e-4
+    assert abs(float(e[0]) - pt.energy) <= c.tol["field"] * pt.energy
+    assert rel(g.cpu().numpy(), pt.gradient()[0]) <= c.tol["grad"]
+    assert rel(h.cpu().numpy(), pt.gn_hessvec(c.dv)[0]) <= c.tol["grad"]
