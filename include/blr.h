@@ -79,7 +79,10 @@ typedef struct blr_params {
     int s;           /* s >= 0                                              */
     double sigma;    /* image term weight 1/sigma^2, sigma > 0              */
     int precision;   /* BLR_FP32 or BLR_MIXED                               */
-    int reserved;    /* must be 0                                           */
+    int ckpt_every;  /* 0: keep all nt+1 states.  k in 1..nt-1: keep only   */
+                     /* m^0, m^k, m^2k, ... and m^nt; adjoint and HVP sweeps */
+                     /* recompute each segment's states from its checkpoint  */
+                     /* (same FP32 arithmetic, so results are bit-identical) */
 } blr_params;
 
 /* Result of blr_newton (host struct filled by the library). */
@@ -96,7 +99,8 @@ typedef struct blr_report {
 } blr_report;
 
 /* Create a plan: validates `p`, allocates every device buffer the hot path
- * needs for this grid/band/nt (state stack of nt+1 fields, adjoint and
+ * needs for this grid/band/nt (state stack: nt+1 fields, or ceil(nt/k) + k with
+ * checkpoints every k steps; adjoint and
  * incremental fields, DFT tables and intermediates, PCG vectors, reduction
  * scratch) and builds the DFT tables on the current device.
  * `p` is host memory, read once.  On success *out owns the allocations.
@@ -146,6 +150,13 @@ int blr_adjoint(blr_plan_t plan, float *b, float *lambda0, blr_stream_t stream);
  * energy: device, 3 doubles, may be NULL. */
 int blr_gradient(blr_plan_t plan, const float *vt, float *g, double *energy,
                  blr_stream_t stream);
+
+/* Reduced gradient (Eq. 38) at the current point, i.e. the velocity of the last
+ * blr_state / blr_gradient, without a new forward solve: the adjoint solve (with
+ * segment recomputation when checkpointing), pi(b) and A v~.  This is the
+ * backward of the energy returned by blr_state.
+ * g: device, 2*3*B1*B2*B3 floats (written).  Needs a prior blr_state (BLR_ESTATE). */
+int blr_gradient_at_state(blr_plan_t plan, float *g, blr_stream_t stream);
 
 /* Gauss-Newton Hessian-vector product at the current point (Section 3.2,
  * Eqs. 44-46 with the Gauss-Newton drops of Section 3.4):

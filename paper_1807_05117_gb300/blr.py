@@ -36,7 +36,7 @@ class blr_params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("band", ctypes.c_int * 3), ("nt", ctypes.c_int),
                 ("alpha", ctypes.c_double), ("gamma", ctypes.c_double), ("s", ctypes.c_int),
                 ("sigma", ctypes.c_double), ("precision", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("ckpt_every", ctypes.c_int)]
 
 
 class blr_report(ctypes.Structure):
@@ -63,6 +63,7 @@ _SIGS = {
     "blr_state": (_P, _P, _P, _P, _P),
     "blr_adjoint": (_P, _P, _P, _P),
     "blr_gradient": (_P, _P, _P, _P, _P),
+    "blr_gradient_at_state": (_P, _P, _P),
     "blr_hessvec": (_P, _P, _P, _P),
     "blr_pcg": (_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
                 ctypes.POINTER(ctypes.c_double), _P),
@@ -134,14 +135,15 @@ def _ptr(t, *, device_only=True, dtype=None, numel=None, optional=False, name="t
     return _P(t.data_ptr())
 
 
-def make_params(n, band, nt=10, alpha=3.0, gamma=1.0, s=2, sigma=1.0, precision=BLR_FP32):
+def make_params(n, band, nt=10, alpha=3.0, gamma=1.0, s=2, sigma=1.0, precision=BLR_FP32,
+                ckpt_every=0):
     p = blr_params()
     p.n[:] = [int(v) for v in n]
     p.band[:] = [int(v) for v in band]
     p.nt = int(nt)
     p.alpha, p.gamma, p.s, p.sigma = float(alpha), float(gamma), int(s), float(sigma)
     p.precision = int(precision)
-    p.reserved = 0
+    p.ckpt_every = int(ckpt_every)
     return p
 
 
@@ -212,6 +214,12 @@ def blr_gradient(plan, vt, g, energy=None, stream=None):
                              _stream(stream)), "blr_gradient")
 
 
+def blr_gradient_at_state(plan, g, stream=None):
+    import torch
+    _check(_lib.blr_gradient_at_state(_P(plan), _ptr(g, dtype=torch.complex64, name="g"),
+                                      _stream(stream)), "blr_gradient_at_state")
+
+
 def blr_hessvec(plan, dvt, hdv, stream=None):
     import torch
     _check(_lib.blr_hessvec(_P(plan), _ptr(dvt, dtype=torch.complex64, name="dvt"),
@@ -262,12 +270,13 @@ class Plan:
     """Owning handle: ``with Plan(n, band, nt) as P: P.gradient(vt, g)``."""
 
     def __init__(self, n, band, nt=10, alpha=3.0, gamma=1.0, s=2, sigma=1.0,
-                 precision=BLR_FP32):
-        self.params = make_params(n, band, nt, alpha, gamma, s, sigma, precision)
+                 precision=BLR_FP32, ckpt_every=0):
+        self.params = make_params(n, band, nt, alpha, gamma, s, sigma, precision, ckpt_every)
         self.n = tuple(int(v) for v in n)
         self.band = tuple(int(v) for v in band)
         self.nt = int(nt)
         self.handle = blr_plan_create(self.params)
+        self.point = 0          # bumped whenever the current point changes
 
     def close(self):
         if self.handle:
@@ -288,6 +297,7 @@ class Plan:
 
     def set_images(self, I0, I1, stream=None):
         blr_set_images(self.handle, I0, I1, stream)
+        self.point += 1
 
     def expand(self, vt, v, stream=None):
         blr_expand(self.handle, vt, v, stream)
@@ -297,12 +307,17 @@ class Plan:
 
     def state(self, vt, m1=None, energy=None, stream=None):
         blr_state(self.handle, vt, m1, energy, stream)
+        self.point += 1
 
     def adjoint(self, b, lambda0=None, stream=None):
         blr_adjoint(self.handle, b, lambda0, stream)
 
     def gradient(self, vt, g, energy=None, stream=None):
         blr_gradient(self.handle, vt, g, energy, stream)
+        self.point += 1
+
+    def gradient_at_state(self, g, stream=None):
+        blr_gradient_at_state(self.handle, g, stream)
 
     def hessvec(self, dvt, hdv, stream=None):
         blr_hessvec(self.handle, dvt, hdv, stream)
@@ -312,6 +327,7 @@ class Plan:
 
     def newton(self, vt, max_newton, max_pcg, gtol, forcing=-1.0, stream=None,
                raise_on_error=True):
+        self.point += 1
         return blr_newton(self.handle, vt, max_newton, max_pcg, gtol, forcing, stream,
                           raise_on_error)
 

@@ -25,7 +25,7 @@ int validate(const blr_params *p) {
     if (p->nt < 1 || !(p->sigma > 0) || !(p->gamma > 0) || !(p->alpha >= 0) || p->s < 0)
         return BLR_EINVAL;
     if (p->precision != BLR_FP32 && p->precision != BLR_MIXED) return BLR_EINVAL;
-    if (p->reserved != 0) return BLR_EINVAL;
+    if (p->ckpt_every < 0) return BLR_EINVAL;
     long long V = (long long)p->n[0] * p->n[1] * p->n[2];
     if (V > (1LL << 31)) return BLR_EINVAL;
     return BLR_OK;
@@ -48,7 +48,7 @@ size_t layout(blr_plan *P, char *base) {
     Arena a;
     a.base = base;
     const long long V = P->V;
-    P->m = a.take<float>((size_t)(P->p.nt + 1) * V);
+    P->m = a.take<float>((size_t)(P->nseg + P->ck) * V);
     P->I0 = P->m;                        // m^0 = I0 lives in the first slot
     P->I1 = a.take<float>(V);
     P->d = a.take<float>(3 * V);
@@ -187,6 +187,9 @@ int blr_plan_create(const blr_params *p, blr_plan_t *out) {
     P->nb = (long long)P->B1 * P->B2 * P->B3;
     P->nfloat = 6 * P->nb;
     P->dt = (float)(1.0 / p->nt);
+    P->ck = (p->ckpt_every > 0 && p->ckpt_every < p->nt) ? p->ckpt_every : p->nt;
+    P->nseg = (int)ceil_div_ll(p->nt, P->ck);
+    P->seg_valid = -1;
     P->grid = Grid3{P->N1, P->N2, P->N3, P->V};
     if (cudaGetDevice(&P->device) != cudaSuccess) {
         delete P;
@@ -244,6 +247,7 @@ int blr_set_images(blr_plan_t P, const float *I0, const float *I1, blr_stream_t 
     BLR_CK(cudaMemcpyAsync(P->I0, I0, P->V * sizeof(float), cudaMemcpyDefault, s));
     BLR_CK(cudaMemcpyAsync(P->I1, I1, P->V * sizeof(float), cudaMemcpyDefault, s));
     P->have_state = false;
+    P->seg_valid = -1;
     return BLR_OK;
 }
 
@@ -263,7 +267,7 @@ int blr_state(blr_plan_t P, const float *vt, float *m1, double *energy, blr_stre
     int rc = state_at(P, vt, energy, s);
     if (rc) return rc;
     if (m1)
-        BLR_CK(cudaMemcpyAsync(m1, P->m + (long long)P->p.nt * P->V, P->V * sizeof(float),
+        BLR_CK(cudaMemcpyAsync(m1, state_slot(P, P->p.nt), P->V * sizeof(float),
                                cudaMemcpyDeviceToDevice, s));
     return BLR_OK;
 }
@@ -280,6 +284,12 @@ int blr_gradient(blr_plan_t P, const float *vt, float *g, double *energy, blr_st
     int rc = state_at(P, vt, energy, s);
     if (rc) return rc;
     return gradient_here(P, g, s);
+}
+
+int blr_gradient_at_state(blr_plan_t P, float *g, blr_stream_t stream) {
+    if (check_plan(P) || !g) return BLR_EINVAL;
+    if (!P->have_state) return BLR_ESTATE;
+    return gradient_here(P, g, (cudaStream_t)stream);
 }
 
 int blr_hessvec(blr_plan_t P, const float *dvt, float *hdv, blr_stream_t stream) {

@@ -54,7 +54,10 @@ struct blr_plan {
     float *I0, *I1;
     float *vt;          // current point (2*3*nb)
     float *d;           // 3V displacement -dt*iota(vt), clamped to [-1, 1)
-    float *m;           // (nt+1)*V states
+    float *m;           // state slots (see state_slot): checkpoints, segment, final
+    int ck;             // checkpoint interval k (nt when every state is kept)
+    int nseg;           // segments ceil(nt / k)
+    int seg_valid;      // segment whose interior states the segment buffer holds
     bool have_state;
     float *lam[2];      // V each (adjoint / incremental adjoint ping-pong)
     float *b;           // 3V body force
@@ -84,6 +87,17 @@ struct blr_plan {
 };
 
 __host__ __device__ inline long long ceil_div_ll(long long a, long long b) { return (a + b - 1) / b; }
+
+// Storage of m^n.  Slots: checkpoints C_j = m^{j k} (j < nseg), then the k-1
+// interior states of one segment, then m^nt.  With k = nt this is m^n in slot n.
+inline float *state_slot(const blr_plan *P, int n) {
+    const int k = P->ck;
+    long long slot;
+    if (n == P->p.nt) slot = P->nseg + k - 1;
+    else if (n % k == 0) slot = n / k;
+    else slot = P->nseg + (n % k) - 1;
+    return P->m + slot * P->V;
+}
 
 // ---- launchers implemented in the .cu files (return BLR_OK / BLR_ECUDA) ----
 

@@ -406,46 +406,74 @@ long long sweep_blocks(const blr_plan *P) {
     return (long long)gr.x * gr.y * gr.z;
 }
 
+namespace {
+
+// m^{n+1} from m^n in the slots given by state_slot (not the last step).
+int state_step(blr_plan *P, const dim3 &grid, int n, cudaStream_t s) {
+    k_state_march<false><<<grid, MT, 0, s>>>(state_slot(P, n), P->d, state_slot(P, n + 1), P->grid,
+                                             P->chunk, nullptr, nullptr, 0.f, nullptr);
+    BLR_CK_LAUNCH();
+    return BLR_OK;
+}
+
+// Make the segment buffer hold the interior states of segment j, recomputing
+// them from checkpoint C_j when it holds another segment.
+int ensure_segment(blr_plan *P, const dim3 &grid, int j, cudaStream_t s) {
+    if (P->seg_valid == j) return BLR_OK;
+    const int n0 = j * P->ck, n1 = n0 + P->ck < P->p.nt ? n0 + P->ck : P->p.nt;
+    for (int n = n0; n < n1 - 1; ++n) {
+        int rc = state_step(P, grid, n, s);
+        if (rc) return rc;
+    }
+    P->seg_valid = j;
+    return BLR_OK;
+}
+
+}  // namespace
+
 int sweep_state(blr_plan *P, cudaStream_t s) {
     const dim3 grid = sweep_grid(P);
     const int nt = P->p.nt;
     const float lam_scale = (float)(-2.0 / (P->p.sigma * P->p.sigma));
-    for (int n = 0; n < nt; ++n) {
-        const float *min_ = P->m + (long long)n * P->V;
-        float *mout = P->m + (long long)(n + 1) * P->V;
-        if (n == nt - 1)
-            k_state_march<true><<<grid, MT, 0, s>>>(min_, P->d, mout, P->grid, P->chunk, P->I1,
-                                                    P->lam[0], lam_scale, P->partials);
-        else
-            k_state_march<false><<<grid, MT, 0, s>>>(min_, P->d, mout, P->grid, P->chunk, nullptr,
-                                                     nullptr, 0.f, nullptr);
-        BLR_CK_LAUNCH();
+    for (int n = 0; n < nt - 1; ++n) {
+        int rc = state_step(P, grid, n, s);
+        if (rc) return rc;
     }
+    k_state_march<true><<<grid, MT, 0, s>>>(state_slot(P, nt - 1), P->d, state_slot(P, nt), P->grid,
+                                            P->chunk, P->I1, P->lam[0], lam_scale, P->partials);
+    BLR_CK_LAUNCH();
+    P->seg_valid = P->nseg - 1;   // the forward sweep leaves the last segment's states
     return BLR_OK;
 }
 
 // lambda^nt must be in lam[0].  Writes the body force into b (3V) and, when
-// lambda0 != nullptr, lambda^0 into lambda0.
+// lambda0 != nullptr, lambda^0 into lambda0.  Segments are visited backwards,
+// each recomputed from its checkpoint when needed.
 int sweep_adjoint(blr_plan *P, float *b, float *lambda0, cudaStream_t s) {
     const dim3 grid = sweep_grid(P);
     const int nt = P->p.nt;
     int cur = 0;
-    for (int n = nt - 1; n >= 0; --n) {
-        const float *lin = P->lam[cur];
-        float *lout = (n == 0 && lambda0) ? lambda0 : P->lam[1 - cur];
-        const float *mn = P->m + (long long)n * P->V;
-        const bool first = (n == nt - 1);
-        const bool wlam = (n > 0) || (lambda0 != nullptr);
-        if (first && wlam)
-            k_adjoint_march<true, true><<<grid, MT, 0, s>>>(lin, mn, P->d, lout, b, P->dt, P->grid, P->chunk);
-        else if (first)
-            k_adjoint_march<true, false><<<grid, MT, 0, s>>>(lin, mn, P->d, lout, b, P->dt, P->grid, P->chunk);
-        else if (wlam)
-            k_adjoint_march<false, true><<<grid, MT, 0, s>>>(lin, mn, P->d, lout, b, P->dt, P->grid, P->chunk);
-        else
-            k_adjoint_march<false, false><<<grid, MT, 0, s>>>(lin, mn, P->d, lout, b, P->dt, P->grid, P->chunk);
-        BLR_CK_LAUNCH();
-        cur = 1 - cur;
+    for (int j = P->nseg - 1; j >= 0; --j) {
+        int rc = ensure_segment(P, grid, j, s);
+        if (rc) return rc;
+        const int n0 = j * P->ck, n1 = n0 + P->ck < nt ? n0 + P->ck : nt;
+        for (int n = n1 - 1; n >= n0; --n) {
+            const float *lin = P->lam[cur];
+            float *lout = (n == 0 && lambda0) ? lambda0 : P->lam[1 - cur];
+            const float *mn = state_slot(P, n);
+            const bool first = (n == nt - 1);
+            const bool wlam = (n > 0) || (lambda0 != nullptr);
+            if (first && wlam)
+                k_adjoint_march<true, true><<<grid, MT, 0, s>>>(lin, mn, P->d, lout, b, P->dt, P->grid, P->chunk);
+            else if (first)
+                k_adjoint_march<true, false><<<grid, MT, 0, s>>>(lin, mn, P->d, lout, b, P->dt, P->grid, P->chunk);
+            else if (wlam)
+                k_adjoint_march<false, true><<<grid, MT, 0, s>>>(lin, mn, P->d, lout, b, P->dt, P->grid, P->chunk);
+            else
+                k_adjoint_march<false, false><<<grid, MT, 0, s>>>(lin, mn, P->d, lout, b, P->dt, P->grid, P->chunk);
+            BLR_CK_LAUNCH();
+            cur = 1 - cur;
+        }
     }
     return BLR_OK;
 }
@@ -456,21 +484,26 @@ int sweep_incremental(blr_plan *P, cudaStream_t s) {
     const int nt = P->p.nt;
     const float lam_scale = (float)(-2.0 / (P->p.sigma * P->p.sigma));
     int cur = 0;
-    for (int n = 0; n < nt; ++n) {
-        const float *din = P->dm[cur];
-        float *dout = (n == nt - 1) ? P->lam[0] : P->dm[1 - cur];
-        const float *mn = P->m + (long long)n * P->V;
-        const bool first = n == 0, last = n == nt - 1;
-        if (first && last)
-            k_incstate_march<true, true><<<grid, MT, 0, s>>>(din, mn, P->d, P->dv, dout, P->dt, lam_scale, P->grid, P->chunk);
-        else if (first)
-            k_incstate_march<true, false><<<grid, MT, 0, s>>>(din, mn, P->d, P->dv, dout, P->dt, lam_scale, P->grid, P->chunk);
-        else if (last)
-            k_incstate_march<false, true><<<grid, MT, 0, s>>>(din, mn, P->d, P->dv, dout, P->dt, lam_scale, P->grid, P->chunk);
-        else
-            k_incstate_march<false, false><<<grid, MT, 0, s>>>(din, mn, P->d, P->dv, dout, P->dt, lam_scale, P->grid, P->chunk);
-        BLR_CK_LAUNCH();
-        cur = 1 - cur;
+    for (int j = 0; j < P->nseg; ++j) {
+        int rc = ensure_segment(P, grid, j, s);
+        if (rc) return rc;
+        const int n0 = j * P->ck, n1 = n0 + P->ck < nt ? n0 + P->ck : nt;
+        for (int n = n0; n < n1; ++n) {
+            const float *din = P->dm[cur];
+            float *dout = (n == nt - 1) ? P->lam[0] : P->dm[1 - cur];
+            const float *mn = state_slot(P, n);
+            const bool first = n == 0, last = n == nt - 1;
+            if (first && last)
+                k_incstate_march<true, true><<<grid, MT, 0, s>>>(din, mn, P->d, P->dv, dout, P->dt, lam_scale, P->grid, P->chunk);
+            else if (first)
+                k_incstate_march<true, false><<<grid, MT, 0, s>>>(din, mn, P->d, P->dv, dout, P->dt, lam_scale, P->grid, P->chunk);
+            else if (last)
+                k_incstate_march<false, true><<<grid, MT, 0, s>>>(din, mn, P->d, P->dv, dout, P->dt, lam_scale, P->grid, P->chunk);
+            else
+                k_incstate_march<false, false><<<grid, MT, 0, s>>>(din, mn, P->d, P->dv, dout, P->dt, lam_scale, P->grid, P->chunk);
+            BLR_CK_LAUNCH();
+            cur = 1 - cur;
+        }
     }
     return BLR_OK;
 }

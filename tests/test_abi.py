@@ -55,7 +55,7 @@ def test_strerror_and_invalid_params(lib):
         assert lib.blr_plan_create(ctypes.byref(p), ctypes.byref(h)) == blr.BLR_EINVAL
         assert not h.value
     p = blr.make_params((16, 16, 16), (4, 4, 4))
-    p.reserved = 1
+    p.ckpt_every = -1
     h = ctypes.c_void_p()
     assert lib.blr_plan_create(ctypes.byref(p), ctypes.byref(h)) == blr.BLR_EINVAL
     # NULL plan handles are rejected, destroy(NULL) is a no-op
