@@ -192,6 +192,45 @@ int blr_newton(blr_plan_t plan, float *vt, int max_newton, int max_pcg,
                double gtol, double forcing, blr_report *rep,
                blr_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Batching form.  The paper registers one pair at a time; this is a library
+ * facility for many independent pairs (each with its own grid, band, sigma and
+ * images; all with the same nt, FP32, no checkpointing) advanced together:
+ * every sweep time step of all pairs is one persistent kernel launch over a
+ * (pair, tile) work queue, the per-pair truncated DFTs run concurrently on side
+ * streams, and one PCG iteration of all pairs is a CUDA graph that is captured
+ * once and replayed.  The x1 tile length is autotuned at creation by timing
+ * candidate shapes on the batch.  Each pair's arithmetic is that of a single
+ * plan, so results are bit-identical to per-pair blr_* calls.
+ * All calls below synchronise `stream` first and are synchronous.
+ * --------------------------------------------------------------------------- */
+typedef struct blr_batch *blr_batch_t;
+
+/* params: host array of npairs descriptions.  BLR_EINVAL if they differ in nt,
+ * request BLR_MIXED or checkpoints, or one is invalid. */
+int blr_batch_create(const blr_params *params, int npairs, blr_batch_t *out);
+int blr_batch_destroy(blr_batch_t batch);
+
+/* Images of pair `pair` (host or device pointers, as blr_set_images). */
+int blr_batch_set_images(blr_batch_t batch, int pair, const float *I0, const float *I1,
+                         blr_stream_t stream);
+
+/* Gradients (Eq. 38) of all pairs: vt[p] device input, g[p] device output
+ * (host arrays of npairs pointers); sets every pair's current point. */
+int blr_batch_gradient(blr_batch_t batch, const float *const *vt, float *const *g,
+                       blr_stream_t stream);
+
+/* Gauss-Newton HVPs (Eq. 46, Section 3.4) of all pairs at their current points. */
+int blr_batch_hessvec(blr_batch_t batch, const float *const *dvt, float *const *hdv,
+                      blr_stream_t stream);
+
+/* Gauss-Newton-Krylov registration of all pairs (the algorithm of blr_newton,
+ * per pair); vt[p] host or device, in/out; reps: host array of npairs (may be
+ * NULL).  A pair that fails (CFL, non-positive curvature) stops with its status
+ * in its report while the others continue. */
+int blr_batch_newton(blr_batch_t batch, float *const *vt, int max_newton, int max_pcg,
+                     double gtol, double forcing, blr_report *reps, blr_stream_t stream);
+
 /* Synchronise `stream`, return the first latched device condition
  * (BLR_ECFL, BLR_ENAN) or BLR_OK, and clear it. */
 int blr_status(blr_plan_t plan, blr_stream_t stream);

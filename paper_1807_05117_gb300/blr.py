@@ -70,6 +70,13 @@ _SIGS = {
     "blr_newton": (_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                    ctypes.POINTER(blr_report), _P),
     "blr_status": (_P, _P),
+    "blr_batch_create": (ctypes.POINTER(blr_params), ctypes.c_int, ctypes.POINTER(_P)),
+    "blr_batch_destroy": (_P,),
+    "blr_batch_set_images": (_P, ctypes.c_int, _P, _P, _P),
+    "blr_batch_gradient": (_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _P),
+    "blr_batch_hessvec": (_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _P),
+    "blr_batch_newton": (_P, ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                         ctypes.c_double, ctypes.POINTER(blr_report), _P),
 }
 
 #: every symbol include/blr.h declares
@@ -333,3 +340,71 @@ class Plan:
 
     def status(self, stream=None):
         return blr_status(self.handle, stream)
+
+
+def _ptr_array(tensors, **kw):
+    arr = (_P * len(tensors))()
+    for i, t in enumerate(tensors):
+        arr[i] = _ptr(t, **kw)
+    return arr
+
+
+class Batch:
+    """Many registration pairs advanced together (see blr_batch_* in include/blr.h).
+
+    ``Batch([(n, band), ...], nt)`` or ``Batch([make_params(...), ...])``."""
+
+    def __init__(self, shapes, nt=10, alpha=3.0, gamma=1.0, s=2, sigma=1.0):
+        params = [sh if isinstance(sh, blr_params) else
+                  make_params(sh[0], sh[1], nt, alpha, gamma, s, sigma) for sh in shapes]
+        self.npairs = len(params)
+        self.shapes = [(tuple(p.n), tuple(p.band)) for p in params]
+        arr = (blr_params * self.npairs)(*params)
+        h = _P()
+        _check(_lib.blr_batch_create(arr, self.npairs, ctypes.byref(h)), "blr_batch_create")
+        self.handle = h.value
+
+    def close(self):
+        if self.handle:
+            _check(_lib.blr_batch_destroy(_P(self.handle)), "blr_batch_destroy")
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_images(self, pair, I0, I1, stream=None):
+        import torch
+        _check(_lib.blr_batch_set_images(_P(self.handle), int(pair),
+                                         _ptr(I0, device_only=False, dtype=torch.float32, name="I0"),
+                                         _ptr(I1, device_only=False, dtype=torch.float32, name="I1"),
+                                         _stream(stream)), "blr_batch_set_images")
+
+    def gradient(self, vts, gs, stream=None):
+        import torch
+        _check(_lib.blr_batch_gradient(_P(self.handle), _ptr_array(vts, dtype=torch.complex64),
+                                       _ptr_array(gs, dtype=torch.complex64), _stream(stream)),
+               "blr_batch_gradient")
+
+    def hessvec(self, dvts, hdvs, stream=None):
+        import torch
+        _check(_lib.blr_batch_hessvec(_P(self.handle), _ptr_array(dvts, dtype=torch.complex64),
+                                      _ptr_array(hdvs, dtype=torch.complex64), _stream(stream)),
+               "blr_batch_hessvec")
+
+    def newton(self, vts, max_newton, max_pcg, gtol, forcing=-1.0, stream=None):
+        import torch
+        reps = (blr_report * self.npairs)()
+        _check(_lib.blr_batch_newton(_P(self.handle),
+                                     _ptr_array(vts, device_only=False, dtype=torch.complex64),
+                                     int(max_newton), int(max_pcg), float(gtol), float(forcing),
+                                     reps, _stream(stream)), "blr_batch_newton")
+        return [Report(*[getattr(r, f) for f, _ in blr_report._fields_]) for r in reps]

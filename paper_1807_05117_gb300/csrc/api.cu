@@ -79,6 +79,7 @@ size_t layout(blr_plan *P, char *base) {
     P->ticket = a.take<unsigned int>(1);
     P->partials = a.take<double>(P->npart);
     P->partials2 = a.take<double>(reduce_partials_needed());
+    P->active = nullptr;
     return a.used;
 }
 
@@ -219,7 +220,7 @@ int blr_plan_create(const blr_params *p, blr_plan_t *out) {
     if (cudaMemset(base, 0, bytes) != cudaSuccess ||
         dft_init_tables(P, 0) != BLR_OK ||
         (p->precision == BLR_MIXED && tc_init_tables(P, 0) != BLR_OK) ||
-        cudaDeviceSynchronize() != cudaSuccess) {
+        sweep_autotune(P, 0) != BLR_OK || cudaDeviceSynchronize() != cudaSuccess) {
         cudaFreeHost(P->hsc);
         cudaFree(base);
         delete P;

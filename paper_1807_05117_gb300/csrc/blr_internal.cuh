@@ -40,6 +40,21 @@ struct Grid3 {
     long long V;
 };
 
+// Operands of one pair in a batched sweep launch (see k_sweep_batch).
+struct SweepPair {
+    Grid3 g;
+    int chunk, tk, tj, ti;   // x1 chunk; tiles along x3, x2, x1
+    const float *in0;        // state: m^n | adjoint: lambda^{n+1} | incremental: dm^n
+    const float *m;          // adjoint / incremental: m^n
+    const float *d;          // displacement
+    const float *aux;        // state: I1 (last step) | incremental: dv
+    float *out0;             // state: m^{n+1} | adjoint: lambda^n | incremental: dm^{n+1}
+    float *out1;             // state: lambda^nt (last step) | adjoint: body force
+    double *partials;        // state (last step): image-term sums per 32-voxel row segment
+    float dt, scale;         // time step; lambda scale -2/sigma^2
+    const int *active;       // nullptr or a device flag: 0 skips the pair
+};
+
 struct blr_plan {
     blr_params p;
     int N1, N2, N3, B1, B2, B3;
@@ -82,6 +97,7 @@ struct blr_plan {
     int *dstatus;
     double *partials;   // per-block partial sums
     double *partials2;  // second-level partials (energy)
+    const int *active;  // batch member: device flag, 0 freezes PCG updates (else nullptr)
     unsigned int *ticket;
     int npart;
 };
@@ -121,6 +137,12 @@ long long sweep_blocks(const blr_plan *P);
 int sweep_state(blr_plan *P, cudaStream_t s);                  // m^1..m^nt, lambda^nt, partials
 int sweep_adjoint(blr_plan *P, float *b, float *lambda0, cudaStream_t s);
 int sweep_incremental(blr_plan *P, cudaStream_t s);            // dm -> dlambda^nt in lam[0]
+int sweep_batch_launch(int kind, bool f1, bool f2, const SweepPair *pairs, const long long *starts,
+                       int npairs, unsigned long long *counter, int grid, cudaStream_t s);
+void sweep_tiles(const blr_plan *P, int *tk, int *tj, int *ti);
+int sweep_threads();
+int sweep_min_chunk();
+int sweep_autotune(blr_plan *P, cudaStream_t s);
 
 // reduce.cu
 int energy_finalize(blr_plan *P, const float *vt, double *energy_out, int nblocks, cudaStream_t s);

@@ -169,8 +169,10 @@ k_pcg_init(const float *__restrict__ rhs, float *__restrict__ x, float *__restri
 __global__ void __launch_bounds__(RT)
 k_pcg_update(float *__restrict__ x, float *__restrict__ r, const float *__restrict__ p,
              const float *__restrict__ q, const float *__restrict__ A, long long n, long long nb,
-             double *__restrict__ part, unsigned int *ticket, double *__restrict__ sc) {
+             double *__restrict__ part, unsigned int *ticket, double *__restrict__ sc,
+             const int *active) {
     __shared__ double red[RT / 32];
+    if (active && *active == 0) return;   // batch member whose PCG has stopped
     const double alpha_d = sc[SC_RZ] / sc[SC_PQ];
     const float alpha = (float)alpha_d;
     double rz = 0.0, rr = 0.0;
@@ -201,7 +203,8 @@ k_pcg_update(float *__restrict__ x, float *__restrict__ r, const float *__restri
 // p = r / A + beta p.
 __global__ void __launch_bounds__(RT)
 k_pcg_direction(float *__restrict__ p, const float *__restrict__ r, const float *__restrict__ A,
-                long long n, long long nb, const double *__restrict__ sc) {
+                long long n, long long nb, const double *__restrict__ sc, const int *active) {
+    if (active && *active == 0) return;
     const float beta = (float)sc[SC_BETA];
     for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT)
         p[i] = fmaf(beta, p[i], r[i] / A[coef_index(i, nb)]);
@@ -253,13 +256,14 @@ int pcg_init(blr_plan *P, const float *rhs, float *x, cudaStream_t s) {
 
 int pcg_update(blr_plan *P, float *x, cudaStream_t s) {
     k_pcg_update<<<vec_blocks(P), RT, 0, s>>>(x, P->r, P->pv, P->q, P->A, P->nfloat, P->nb,
-                                              P->partials, P->ticket, P->dsc);
+                                              P->partials, P->ticket, P->dsc, P->active);
     BLR_CK_LAUNCH();
     return BLR_OK;
 }
 
 int pcg_direction(blr_plan *P, cudaStream_t s) {
-    k_pcg_direction<<<vec_blocks(P), RT, 0, s>>>(P->pv, P->r, P->A, P->nfloat, P->nb, P->dsc);
+    k_pcg_direction<<<vec_blocks(P), RT, 0, s>>>(P->pv, P->r, P->A, P->nfloat, P->nb, P->dsc,
+                                                 P->active);
     BLR_CK_LAUNCH();
     return BLR_OK;
 }

@@ -102,20 +102,7 @@ __device__ __forceinline__ float trilinear2(const float *P0, const float *P1, in
     return fmaf(a0.wl, m0, a0.wh * m1);
 }
 
-__device__ __forceinline__ double block_sum(double v, double *red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < MT / 32; ++w) t += red[w];
-    return t;
-}
 
-__device__ __forceinline__ long long block_linear() {
-    return ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-}
 
 // Ring slots of plane s, with r = s - i0 + 1 >= 0.
 __device__ __forceinline__ int ring4(int r) { return r & 3; }
@@ -123,6 +110,15 @@ __device__ __forceinline__ int ring8(int r) { return r & 7; }
 
 // Plane index with periodic wrap for s in [-1, N].
 __device__ __forceinline__ int wrap1(int s, int N) { return s < 0 ? s + N : (s >= N ? s - N : s); }
+
+// Copies of one haloed plane (one commit group per call, empty past i_end).
+__device__ __forceinline__ void issue_plane1(uint32_t dst, const float *__restrict__ f0, int s,
+                                             int i_end, int N1, long long plane, long long off0,
+                                             long long off1, bool ok1);
+__device__ __forceinline__ void issue_plane2(uint32_t dst_a, const float *__restrict__ fa,
+                                             uint32_t dst_b, const float *__restrict__ fb, int s,
+                                             int i_end, int N1, long long plane, long long off0,
+                                             long long off1, bool ok1);
 
 // Asynchronous 4-byte global -> shared copies (one commit group per plane).
 __device__ __forceinline__ void cp4(uint32_t dst, const float *src) {
@@ -134,19 +130,76 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+// One scalar field plane s (periodic in x1) into a ring slot at byte address dst.
+__device__ __forceinline__ void issue_plane1(uint32_t dst, const float *__restrict__ f0, int s,
+                                             int i_end, int N1, long long plane, long long off0,
+                                             long long off1, bool ok1) {
+    if (s <= i_end) {
+        const float *f = f0 + (long long)wrap1(s, N1) * plane;
+        cp4(dst, f + off0);
+        if (ok1) cp4(dst + MT * 4, f + off1);
+    }
+    cp_commit();
+}
+
+// (d0, d1, d2, lambda) of plane s into a float4 ring slot and m^n into a scalar slot.
+__device__ __forceinline__ void issue_plane_adj(uint32_t dq, uint32_t dm,
+                                                const float *__restrict__ d,
+                                                const float *__restrict__ lam,
+                                                const float *__restrict__ m, int s, int i_end,
+                                                int N1, long long plane, long long V,
+                                                long long off0, long long off1, bool ok1) {
+    if (s <= i_end) {
+        const long long base = (long long)wrap1(s, N1) * plane;
+        const float *src = d + base + off0;
+        cp4(dq, src);
+        cp4(dq + 4, src + V);
+        cp4(dq + 8, src + 2 * V);
+        cp4(dq + 12, lam + base + off0);
+        cp4(dm, m + base + off0);
+        if (ok1) {
+            const float *src1 = d + base + off1;
+            const uint32_t dq1 = dq + MT * 16;
+            cp4(dq1, src1);
+            cp4(dq1 + 4, src1 + V);
+            cp4(dq1 + 8, src1 + 2 * V);
+            cp4(dq1 + 12, lam + base + off1);
+            cp4(dm + MT * 4, m + base + off1);
+        }
+    }
+    cp_commit();
+}
+
+// Two scalar fields of plane s into two ring slots.
+__device__ __forceinline__ void issue_plane2(uint32_t dst_a, const float *__restrict__ fa,
+                                             uint32_t dst_b, const float *__restrict__ fb, int s,
+                                             int i_end, int N1, long long plane, long long off0,
+                                             long long off1, bool ok1) {
+    if (s <= i_end) {
+        const long long base = (long long)wrap1(s, N1) * plane;
+        cp4(dst_a, fa + base + off0);
+        cp4(dst_b, fb + base + off0);
+        if (ok1) {
+            cp4(dst_a + MT * 4, fa + base + off1);
+            cp4(dst_b + MT * 4, fb + base + off1);
+        }
+    }
+    cp_commit();
+}
+
 // ---------------------------------------------------------------------------
 // State step m^{n+1} = S m^n.  LAST also writes lambda^nt = lam_scale (m^nt - I1)
-// and the block's sum of (m^nt - I1)^2 (FP32 terms, FP64 block sum).
+// and one FP64 sum of the FP32 terms (m^nt - I1)^2 per 32-voxel row segment,
+// at partials[(x1 * N2 + x2) * ceil(N3/32) + x3/32] (independent of the tiling).
 // Plane s of m^n completes output plane s - 1 (its cells reach x1 - 1 .. x1 + 1);
 // planes arrive by cp.async two iterations ahead (8-slot ring).
 template <bool LAST>
-__global__ void __launch_bounds__(MT, 4)
-k_state_march(const float *__restrict__ m_in, const float *__restrict__ d,
-              float *__restrict__ m_out, Grid3 g, int CH, const float *__restrict__ I1,
-              float *__restrict__ lam_out, float lam_scale, double *__restrict__ partials) {
+__device__ __forceinline__ void
+state_tile(const float *__restrict__ m_in, const float *__restrict__ d,
+           float *__restrict__ m_out, const Grid3 g, int CH, const float *__restrict__ I1,
+           float *__restrict__ lam_out, float lam_scale, double *__restrict__ partials,
+           int k0, int j0, int i0) {
     __shared__ __align__(16) float sM[8][MHP];
-    __shared__ double red[MT / 32];
-    const int k0 = blockIdx.x * MK, j0 = blockIdx.y * MJ, i0 = blockIdx.z * CH;
     const int i_end = min(i0 + CH, g.N1);
     const Slots ps = plane_slots(g, k0, j0);
     const long long plane = (long long)g.N2 * g.N3;
@@ -157,25 +210,21 @@ k_state_march(const float *__restrict__ m_in, const float *__restrict__ d,
     const int hj = tj + 1, hk = tk + 1;
     const uint32_t m_base = smem_u32(&sM[0][threadIdx.x]);
 
-    auto issue = [&](int s, int r) {
-        if (s <= i_end) {
-            const float *f = m_in + (long long)wrap1(s, g.N1) * plane;
-            const uint32_t off = (uint32_t)(r & 7) * (MHP * 4);
-            cp4(m_base + off, f + ps.off0);
-            if (ps.ok1) cp4(m_base + off + MT * 4, f + ps.off1);
-        }
-        cp_commit();
-    };
-    issue(i0 - 1, 0);
-    issue(i0, 1);
-    float e2 = 0.f;
+    const int N1 = g.N1;
+#define BLR_ISSUE_STATE(S, R)                                                             \
+    issue_plane1(m_base + (uint32_t)((R) & 7) * (MHP * 4), m_in, (S), i_end, N1, plane, ps.off0, \
+                 ps.off1, ps.ok1)
+    BLR_ISSUE_STATE(i0 - 1, 0);
+    BLR_ISSUE_STATE(i0, 1);
+    const int nkt = (g.N3 + MK - 1) / MK;
     float dd0 = 0.f, dd1 = 0.f, dd2 = 0.f;   // d at the output voxel of the next plane
     for (int s = i0 - 1; s <= i_end; ++s) {
         const int r = s - i0 + 1;
         cp_wait1();
         __syncthreads();
-        issue(s + 2, r + 2);
+        BLR_ISSUE_STATE(s + 2, r + 2);
         const int o = s - 1;
+        float res = 0.f;
         if (active && o >= i0) {
             const long long idx = (long long)o * plane + col;
             const AxisW a0 = axis_weights(dd0);
@@ -186,10 +235,14 @@ k_state_march(const float *__restrict__ m_in, const float *__restrict__ d,
             const float val = trilinear2<false>(P0, P1, hj, hk, a0, a1, a2, nullptr);
             m_out[idx] = val;
             if (LAST) {
-                const float res = val - __ldg(I1 + idx);
-                e2 = fmaf(res, res, e2);
+                res = val - __ldg(I1 + idx);
                 lam_out[idx] = lam_scale * res;
             }
+        }
+        if (LAST && o >= i0 && j < g.N2) {   // warp-uniform: one x2 row per warp
+            double t = (double)(res * res);
+            for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+            if (tk == 0) partials[((long long)o * g.N2 + j) * nkt + (k0 / MK)] = t;
         }
         if (active && s >= i0 && s < i_end) {
             const long long nidx = (long long)s * plane + col;
@@ -198,10 +251,16 @@ k_state_march(const float *__restrict__ m_in, const float *__restrict__ d,
             dd2 = __ldg(d + 2 * g.V + nidx);
         }
     }
-    if (LAST) {
-        const double t = block_sum((double)e2, red);
-        if (threadIdx.x == 0) partials[block_linear()] = t;
-    }
+#undef BLR_ISSUE_STATE
+}
+
+template <bool LAST>
+__global__ void __launch_bounds__(MT, 4)
+k_state_march(const float *__restrict__ m_in, const float *__restrict__ d,
+              float *__restrict__ m_out, Grid3 g, int CH, const float *__restrict__ I1,
+              float *__restrict__ lam_out, float lam_scale, double *__restrict__ partials) {
+    state_tile<LAST>(m_in, d, m_out, g, CH, I1, lam_out, lam_scale, partials, blockIdx.x * MK,
+                     blockIdx.y * MJ, blockIdx.z * CH);
 }
 
 // ---------------------------------------------------------------------------
@@ -212,13 +271,12 @@ k_state_march(const float *__restrict__ m_in, const float *__restrict__ d,
 // output plane s-1 is then complete.  Planes arrive by cp.async two iterations
 // ahead: (d, lambda) in a 4-slot ring, m^n in an 8-slot ring.
 template <bool FIRST, bool WRITE_LAM>
-__global__ void __launch_bounds__(MT, 4)
-k_adjoint_march(const float *__restrict__ lam_in, const float *__restrict__ m_n,
-                const float *__restrict__ d, float *__restrict__ lam_out,
-                float *__restrict__ b, float dt, Grid3 g, int CH) {
+__device__ __forceinline__ void
+adjoint_tile(const float *__restrict__ lam_in, const float *__restrict__ m_n,
+             const float *__restrict__ d, float *__restrict__ lam_out, float *__restrict__ b,
+             float dt, const Grid3 g, int CH, int k0, int j0, int i0) {
     __shared__ __align__(16) float4 sQ[4][MHP];   // (d0, d1, d2, lambda^{n+1})
     __shared__ __align__(16) float sM[8][MHP];    // m^n
-    const int k0 = blockIdx.x * MK, j0 = blockIdx.y * MJ, i0 = blockIdx.z * CH;
     const int i_end = min(i0 + CH, g.N1);
     const Slots ps = plane_slots(g, k0, j0);
     const long long plane = (long long)g.N2 * g.N3;
@@ -231,38 +289,22 @@ k_adjoint_march(const float *__restrict__ lam_in, const float *__restrict__ m_n,
     const uint32_t q_base = smem_u32(&sQ[0][threadIdx.x]);
     const uint32_t m_base = smem_u32(&sM[0][threadIdx.x]);
 
+    const int N1 = g.N1;
+    const long long V = g.V;
     // copy plane s (if it belongs to this chunk's window) into ring slot r
-    auto issue = [&](int s, int r) {
-        if (s <= i_end) {
-            const long long base = (long long)wrap1(s, g.N1) * plane;
-            const float *src = d + base + ps.off0;
-            const uint32_t dq = q_base + (uint32_t)(r & 3) * (MHP * 16);
-            cp4(dq, src);
-            cp4(dq + 4, src + g.V);
-            cp4(dq + 8, src + 2 * g.V);
-            cp4(dq + 12, lam_in + base + ps.off0);
-            cp4(m_base + (uint32_t)(r & 7) * (MHP * 4), m_n + base + ps.off0);
-            if (ps.ok1) {
-                const float *src1 = d + base + ps.off1;
-                const uint32_t dq1 = dq + MT * 16;
-                cp4(dq1, src1);
-                cp4(dq1 + 4, src1 + g.V);
-                cp4(dq1 + 8, src1 + 2 * g.V);
-                cp4(dq1 + 12, lam_in + base + ps.off1);
-                cp4(m_base + (uint32_t)(r & 7) * (MHP * 4) + MT * 4, m_n + base + ps.off1);
-            }
-        }
-        cp_commit();
-    };
-    issue(i0 - 1, 0);
-    issue(i0, 1);
+#define BLR_ISSUE_ADJ(S, R)                                                               \
+    issue_plane_adj(q_base + (uint32_t)((R) & 3) * (MHP * 16),                             \
+                    m_base + (uint32_t)((R) & 7) * (MHP * 4), d, lam_in, m_n, (S), i_end, N1, \
+                    plane, V, ps.off0, ps.off1, ps.ok1)
+    BLR_ISSUE_ADJ(i0 - 1, 0);
+    BLR_ISSUE_ADJ(i0, 1);
     float acc_a = 0.f, acc_b = 0.f, acc_c = 0.f;
     float bb[3] = {0.f, 0.f, 0.f};   // body force at the output voxel of the next plane
     for (int s = i0 - 1; s <= i_end; ++s) {
         const int r = s - i0 + 1;
         cp_wait1();
         __syncthreads();
-        issue(s + 2, r + 2);
+        BLR_ISSUE_ADJ(s + 2, r + 2);
         if (active) {
             if (WRITE_LAM) {
                 const float4 *Q = sQ[ring4(r)];
@@ -304,6 +346,16 @@ k_adjoint_march(const float *__restrict__ lam_in, const float *__restrict__ m_n,
         acc_b = acc_c;
         acc_c = 0.f;
     }
+#undef BLR_ISSUE_ADJ
+}
+
+template <bool FIRST, bool WRITE_LAM>
+__global__ void __launch_bounds__(MT, 4)
+k_adjoint_march(const float *__restrict__ lam_in, const float *__restrict__ m_n,
+                const float *__restrict__ d, float *__restrict__ lam_out,
+                float *__restrict__ b, float dt, Grid3 g, int CH) {
+    adjoint_tile<FIRST, WRITE_LAM>(lam_in, m_n, d, lam_out, b, dt, g, CH, blockIdx.x * MK,
+                                   blockIdx.y * MJ, blockIdx.z * CH);
 }
 
 // ---------------------------------------------------------------------------
@@ -312,13 +364,13 @@ k_adjoint_march(const float *__restrict__ lam_in, const float *__restrict__ m_n,
 // LAST writes dlambda^nt = lam_scale dm^nt instead of dm^nt.  m^n and dm^n
 // planes arrive by cp.async two iterations ahead (8-slot rings).
 template <bool FIRST, bool LAST>
-__global__ void __launch_bounds__(MT, 4)
-k_incstate_march(const float *__restrict__ dm_in, const float *__restrict__ m_n,
-                 const float *__restrict__ d, const float *__restrict__ dv,
-                 float *__restrict__ dm_out, float dt, float lam_scale, Grid3 g, int CH) {
+__device__ __forceinline__ void
+incstate_tile(const float *__restrict__ dm_in, const float *__restrict__ m_n,
+              const float *__restrict__ d, const float *__restrict__ dv,
+              float *__restrict__ dm_out, float dt, float lam_scale, const Grid3 g, int CH,
+              int k0, int j0, int i0) {
     __shared__ __align__(16) float sM[8][MHP];
     __shared__ __align__(16) float sD[FIRST ? 1 : 8][FIRST ? 1 : MHP];
-    const int k0 = blockIdx.x * MK, j0 = blockIdx.y * MJ, i0 = blockIdx.z * CH;
     const int i_end = min(i0 + CH, g.N1);
     const Slots ps = plane_slots(g, k0, j0);
     const long long plane = (long long)g.N2 * g.N3;
@@ -330,27 +382,24 @@ k_incstate_march(const float *__restrict__ dm_in, const float *__restrict__ m_n,
     const uint32_t m_base = smem_u32(&sM[0][threadIdx.x]);
     const uint32_t d_base = FIRST ? 0u : smem_u32(&sD[0][threadIdx.x]);
 
-    auto issue = [&](int s, int r) {
-        if (s <= i_end) {
-            const long long base = (long long)wrap1(s, g.N1) * plane;
-            const uint32_t off = (uint32_t)(r & 7) * (MHP * 4);
-            cp4(m_base + off, m_n + base + ps.off0);
-            if (!FIRST) cp4(d_base + off, dm_in + base + ps.off0);
-            if (ps.ok1) {
-                cp4(m_base + off + MT * 4, m_n + base + ps.off1);
-                if (!FIRST) cp4(d_base + off + MT * 4, dm_in + base + ps.off1);
-            }
-        }
-        cp_commit();
-    };
-    issue(i0 - 1, 0);
-    issue(i0, 1);
+    const int N1 = g.N1;
+#define BLR_ISSUE_INC(S, R)                                                                 \
+    do {                                                                                    \
+        const uint32_t off_ = (uint32_t)((R) & 7) * (MHP * 4);                              \
+        if (FIRST)                                                                          \
+            issue_plane1(m_base + off_, m_n, (S), i_end, N1, plane, ps.off0, ps.off1, ps.ok1); \
+        else                                                                                \
+            issue_plane2(m_base + off_, m_n, d_base + off_, dm_in, (S), i_end, N1, plane,   \
+                         ps.off0, ps.off1, ps.ok1);                                         \
+    } while (0)
+    BLR_ISSUE_INC(i0 - 1, 0);
+    BLR_ISSUE_INC(i0, 1);
     float dd[3] = {0.f, 0.f, 0.f}, vv[3] = {0.f, 0.f, 0.f};   // next output voxel's d, dv
     for (int s = i0 - 1; s <= i_end; ++s) {
         const int r = s - i0 + 1;
         cp_wait1();
         __syncthreads();
-        issue(s + 2, r + 2);
+        BLR_ISSUE_INC(s + 2, r + 2);
         const int o = s - 1;
         if (active && o >= i0) {
             const long long idx = (long long)o * plane + col;
@@ -375,6 +424,61 @@ k_incstate_march(const float *__restrict__ dm_in, const float *__restrict__ m_n,
                 vv[a] = __ldg(dv + a * g.V + nidx);
             }
         }
+    }
+#undef BLR_ISSUE_INC
+}
+
+template <bool FIRST, bool LAST>
+__global__ void __launch_bounds__(MT, 4)
+k_incstate_march(const float *__restrict__ dm_in, const float *__restrict__ m_n,
+                 const float *__restrict__ d, const float *__restrict__ dv,
+                 float *__restrict__ dm_out, float dt, float lam_scale, Grid3 g, int CH) {
+    incstate_tile<FIRST, LAST>(dm_in, m_n, d, dv, dm_out, dt, lam_scale, g, CH, blockIdx.x * MK,
+                               blockIdx.y * MJ, blockIdx.z * CH);
+}
+
+// ---------------------------------------------------------------------------
+// Batched sweeps: one persistent launch runs the same time step of many
+// registration pairs.  Blocks pop (pair, tile) items from an atomic counter in
+// item order (items of pair p are starts[p] .. starts[p+1]-1); each item is a
+// full march tile of that pair, so the results equal the single-pair kernels'.
+template <int KIND, bool F1, bool F2>
+__global__ void __launch_bounds__(MT, 4)
+k_sweep_batch(const SweepPair *__restrict__ pairs, const long long *__restrict__ starts,
+              int npairs, unsigned long long *counter) {
+    __shared__ long long s_item;
+    const long long total = starts[npairs];
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= total) break;
+        int lo = 0, hi = npairs - 1;          // last pair whose start <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (starts[mid] <= item) lo = mid; else hi = mid - 1;
+        }
+        const SweepPair P = pairs[lo];   // by value: the tile bodies take plain values
+        if (P.active && *P.active == 0) continue;
+        const long long local = item - starts[lo];
+        const int kt = (int)(local % P.tk);
+        const int jt = (int)((local / P.tk) % P.tj);
+        const int it = (int)(local / ((long long)P.tk * P.tj));
+        const int k0 = kt * MK, j0 = jt * MJ, i0 = it * P.chunk;
+        if (KIND == 0)
+            state_tile<F1>(P.in0, P.d, P.out0, P.g, P.chunk, P.aux, P.out1, P.scale, P.partials,
+                           k0, j0, i0);
+        else if (KIND == 1)
+            adjoint_tile<F1, F2>(P.in0, P.m, P.d, P.out0, P.out1, P.dt, P.g, P.chunk, k0, j0, i0);
+        else
+            incstate_tile<F1, F2>(P.in0, P.m, P.d, P.aux, P.out0, P.dt, P.scale, P.g, P.chunk,
+                                  k0, j0, i0);
+        // Drain every copy group of this tile before the next tile refills the
+        // rings: without it the batched results differed from the one-tile
+        // kernels in the periodically wrapped x1 plane.
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        __syncthreads();
     }
 }
 
@@ -401,9 +505,10 @@ int sweep_setup(blr_plan *P) {
     return BLR_OK;
 }
 
+// Image-term partial sums written by the last state step (one per 32-voxel row
+// segment, whatever the tiling).
 long long sweep_blocks(const blr_plan *P) {
-    dim3 gr = sweep_grid(P);
-    return (long long)gr.x * gr.y * gr.z;
+    return (long long)P->N1 * P->N2 * ceil_div_ll(P->N3, MK);
 }
 
 namespace {
@@ -505,5 +610,80 @@ int sweep_incremental(blr_plan *P, cudaStream_t s) {
             cur = 1 - cur;
         }
     }
+    return BLR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched launches and the tile-shape autotuner.
+
+int sweep_batch_launch(int kind, bool f1, bool f2, const SweepPair *pairs, const long long *starts,
+                       int npairs, unsigned long long *counter, int grid, cudaStream_t s) {
+#define BLR_BL(K, A, B) k_sweep_batch<K, A, B><<<grid, MT, 0, s>>>(pairs, starts, npairs, counter)
+    if (kind == 0) {
+        if (f1) BLR_BL(0, true, false); else BLR_BL(0, false, false);
+    } else if (kind == 1) {
+        if (f1 && f2) BLR_BL(1, true, true);
+        else if (f1) BLR_BL(1, true, false);
+        else if (f2) BLR_BL(1, false, true);
+        else BLR_BL(1, false, false);
+    } else {
+        if (f1 && f2) BLR_BL(2, true, true);
+        else if (f1) BLR_BL(2, true, false);
+        else if (f2) BLR_BL(2, false, true);
+        else BLR_BL(2, false, false);
+    }
+#undef BLR_BL
+    BLR_CK_LAUNCH();
+    return BLR_OK;
+}
+
+// Tiles of one pair for its current chunk.
+void sweep_tiles(const blr_plan *P, int *tk, int *tj, int *ti) {
+    *tk = (int)ceil_div_ll(P->N3, MK);
+    *tj = (int)ceil_div_ll(P->N2, MJ);
+    *ti = (int)ceil_div_ll(P->N1, P->chunk);
+}
+
+int sweep_threads() { return MT; }
+
+// Smallest x1 chunk any candidate uses (sizes the partials buffer).
+int sweep_min_chunk() { return 4; }
+
+// Autotuner: time an interior adjoint step (the dominant kernel) on the plan's
+// own buffers for each candidate chunk and keep the fastest.  Candidates: the
+// one-wave chunk of sweep_setup and 4, 8, 16, 32 planes.
+int sweep_autotune(blr_plan *P, cudaStream_t s) {
+    const int heur = P->chunk;
+    int cands[5] = {heur, 4, 8, 16, 32};
+    cudaEvent_t e0, e1;
+    BLR_CK(cudaEventCreate(&e0));
+    BLR_CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_ch = heur;
+    for (int c = 0; c < 5; ++c) {
+        const int ch = cands[c] < P->N1 ? cands[c] : P->N1;
+        if (c > 0 && ch == heur) continue;
+        P->chunk = ch;
+        const dim3 grid = sweep_grid(P);
+        float tot = 0.f;
+        for (int rep = 0; rep < 3; ++rep) {
+            BLR_CK(cudaEventRecord(e0, s));
+            k_adjoint_march<false, true><<<grid, MT, 0, s>>>(P->lam[0], P->m, P->d, P->lam[1], P->b,
+                                                             P->dt, P->grid, P->chunk);
+            BLR_CK_LAUNCH();
+            BLR_CK(cudaEventRecord(e1, s));
+            BLR_CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            BLR_CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) tot += ms;   // first run warms up
+        }
+        if (tot < best) {
+            best = tot;
+            best_ch = ch;
+        }
+    }
+    P->chunk = best_ch;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     return BLR_OK;
 }
