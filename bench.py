@@ -22,11 +22,18 @@ path's HVP error against the FP64 oracle.
 
 `--impl reference` times the FP64 oracle alone (host cores) on the same
 workload and prints the same line with "impl": "reference".
+
+`--workload uneven64` measures the batching form instead: one step = one
+fixed-work registration (10 Newton x 20 PCG) of each of 64 pairs of uneven
+grid (64^3 .. 160x192x160) and band (16^3 .. 32^3) through blr_batch_newton,
+with the same pairs registered one after another through single plans timed
+beside it.
 """
 
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -54,6 +61,19 @@ WORKLOAD = ("128^3 phantom pair (3 nested ellipsoids, blur 1 voxel, noise 0.01, 
 # + write 12 B, write lambda^n 4 B = 48 B/voxel; the first step of a solve does
 # not read b (36 B), the last does not write lambda (44 B).
 ADJ_BYTES = lambda nt: ((36 + 44 + 48 * (nt - 2)) if nt > 1 else 32)
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one interior adjoint-step
+# launch (k_adjoint_march<false, true>) at 128^3 from an ncu capture, valid only
+# for the sweep source it was captured from (SHA-256 of csrc/sweeps.cu).
+ADJ_TRAFFIC = {"sweeps_sha256": None, "bytes": None}
+
+
+def adjoint_traffic():
+    path = os.path.join(ROOT, "paper_1807_05117_gb300", "csrc", "sweeps.cu")
+    with open(path, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    return ADJ_TRAFFIC["bytes"] if sha == ADJ_TRAFFIC["sweeps_sha256"] else None
 
 
 def peaks():
@@ -292,7 +312,10 @@ def measure_precision(precision, args, dev, I0g, I1g, flush, stream, dist, world
                 "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": f"{peak_kind} hbm_gbs (copy, burst; kernel timed alone)",
                 "algorithmic_bytes_per_launch": adj_bytes, "launch_us": adj_launch_s * 1e6,
-                "traffic": args.adjoint_traffic}
+                "traffic": (args.adjoint_traffic if args.adjoint_traffic is not None
+                            else adjoint_traffic()),
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                  "interior launch at 128^3 (null once the kernel source changed)"}
     return dict(plan=plan, ms=ms, launches=launches, clocks=clocks, rep=rep, hvp_ms=hvp_ms,
                 roofline=roofline, dvt=dvt)
 
@@ -422,6 +445,100 @@ def main_ours(args):
     return 0
 
 
+UNEVEN_PAIRS, UNEVEN_SEED = 64, 4
+
+
+def main_batch(args):
+    """The batching form on the 64-pair workload (FP32, 10 time steps)."""
+    import multiprocessing as mp
+
+    import torch
+
+    from paper_1807_05117_gb300 import blr, synth
+
+    pairs = synth.uneven_pairs(UNEVEN_PAIRS, UNEVEN_SEED)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        imgs = pool.starmap(synth.phantom_pair_f32,
+                            [(p["n"], p["seed"], p["max_disp"]) for p in pairs])
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    t0 = time.perf_counter()
+    batch = blr.Batch([(p["n"], p["band"]) for p in pairs], NT)
+    create_s = time.perf_counter() - t0
+    for i, (I0, I1) in enumerate(imgs):
+        batch.set_images(i, torch.from_numpy(I0).to(dev), torch.from_numpy(I1).to(dev))
+    vts = [torch.zeros((3,) + p["band"], dtype=torch.complex64, device=dev) for p in pairs]
+
+    def step():
+        for v in vts:
+            v.zero_()
+        return batch.newton(vts, NEWTON, PCG, 0.0, 0.0)
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, steps):
+        tot = 0.0
+        out = None
+        for k in range(steps):
+            flush.fill_(k & 0xFF)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / max(steps, 1), out
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler()
+    sampler.start()
+    l0 = blr.blr_kernel_launches()
+    ms, reps = timed(step, args.steps)
+    launches = blr.blr_kernel_launches() - l0
+    clocks = sampler.stop(0)
+
+    # the same registrations one pair at a time through single plans
+    plans = []
+    for i, p in enumerate(pairs):
+        pl = blr.Plan(p["n"], p["band"], NT)
+        pl.set_images(torch.from_numpy(imgs[i][0]).to(dev), torch.from_numpy(imgs[i][1]).to(dev))
+        plans.append(pl)
+
+    def serial():
+        for pl, v in zip(plans, vts):
+            v.zero_()
+            pl.newton(v, NEWTON, PCG, 0.0, 0.0)
+
+    serial()
+    ms_serial, _ = timed(serial, max(1, min(args.steps, 2)))
+    for pl in plans:
+        pl.close()
+    voxels = sum(p["n"][0] * p["n"][1] * p["n"][2] for p in pairs)
+    grids = sorted({tuple(p["n"]) for p in pairs})
+    line = {"metric": "registrations/s, 64 uneven pairs (batching form)",
+            "value": UNEVEN_PAIRS * 1000.0 / ms, "unit": "registrations/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": (f"{UNEVEN_PAIRS} phantom pairs, grids {grids}, bands "
+                                    "16^3/24^3/32^3, 3-8 voxel warps, 10 time steps, "
+                                    "10 Newton x 20 PCG (fixed work) per pair"),
+                       "voxels_total": voxels, "l2": "flushed between timed steps"},
+            "gpu_launches": int(launches), "clocks": clocks,
+            "batch_create_s": create_s,
+            "one_by_one": {"value": UNEVEN_PAIRS * 1000.0 / ms_serial,
+                           "unit": "registrations/s", "ms_per_step": ms_serial},
+            "gvoxel_steps_per_s": voxels * NT * (NEWTON * PCG) / (ms / 1000.0) / 1e9,
+            "status": sorted({r.status for r in reps})}
+    print(json.dumps(line), flush=True)
+    batch.close()
+    return 0
+
+
 def probe(precision="fp32"):
     """A few launches of every hot-path kernel at the benchmark size, for ncu."""
     import numpy as np
@@ -466,6 +583,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--adjoint-traffic", type=float, default=None,
                     help="dram bytes per adjoint-step launch from an ncu capture of this kernel")
+    ap.add_argument("--workload", choices=["phantom128", "uneven64"], default="phantom128",
+                    help="phantom128: the 128^3 registration (default); uneven64: the batching form")
     ap.add_argument("--probe", action="store_true",
                     help="short run for profilers: one gradient, 3 HVPs, 2 adjoint solves")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
@@ -478,6 +597,8 @@ def main():
         return probe(args.precision)
     if args.impl == "reference":
         return main_reference(args)
+    if args.workload == "uneven64":
+        return main_batch(args)
     return main_ours(args)
 
 

@@ -27,7 +27,7 @@ struct Batch {
     int npairs = 0, nt = 0, device = 0, grid = 0;
     std::vector<blr_plan_t> plans;
     SweepPair *d_desc = nullptr;              // [KINDS][nt][npairs]
-    long long *d_starts = nullptr;            // [npairs + 1]
+    long long *d_starts = nullptr;            // [KINDS][npairs + 1]
     unsigned long long *d_counters = nullptr; // [KINDS][nt]
     int *d_active = nullptr;                  // [npairs]
     std::vector<int> h_active;                // pageable: cudaMemcpyAsync stages it before returning
@@ -46,26 +46,32 @@ Batch *as_batch(blr_batch_t b) { return reinterpret_cast<Batch *>(b); }
 int fill_descriptors(Batch *B) {
     const int np = B->npairs, nt = B->nt;
     std::vector<SweepPair> h((size_t)KINDS * nt * np);
-    std::vector<long long> starts(np + 1, 0);
+    std::vector<long long> starts((size_t)KINDS * (np + 1), 0);
     for (int p = 0; p < np; ++p) {
         blr_plan *P = B->plans[p];
-        int tk, tj, ti;
-        sweep_tiles(P, &tk, &tj, &ti);
-        starts[p + 1] = starts[p] + (long long)tk * tj * ti;
+        int tiles[KINDS][3];
+        for (int kind = 0; kind < KINDS; ++kind) {
+            sweep_tiles(P, kind, &tiles[kind][0], &tiles[kind][1], &tiles[kind][2]);
+            long long *st = starts.data() + (size_t)kind * (np + 1);
+            st[p + 1] = st[p] + (long long)tiles[kind][0] * tiles[kind][1] * tiles[kind][2];
+        }
         const float lam_scale = (float)(-2.0 / (P->p.sigma * P->p.sigma));
+        auto base_for = [&](int kind) {
+            SweepPair b{};
+            b.g = P->grid;
+            b.chunk = sweep_chunk(P, kind);
+            b.tk = tiles[kind][0];
+            b.tj = tiles[kind][1];
+            b.ti = tiles[kind][2];
+            b.d = P->d;
+            b.dt = P->dt;
+            b.scale = lam_scale;
+            b.active = B->d_active + p;
+            return b;
+        };
         for (int n = 0; n < nt; ++n) {
-            SweepPair base{};
-            base.g = P->grid;
-            base.chunk = P->chunk;
-            base.tk = tk;
-            base.tj = tj;
-            base.ti = ti;
-            base.d = P->d;
-            base.dt = P->dt;
-            base.scale = lam_scale;
-            base.active = B->d_active + p;
             // state step n: m^n -> m^{n+1}; the last step also writes lambda^nt
-            SweepPair st = base;
+            SweepPair st = base_for(0);
             st.in0 = state_slot(P, n);
             st.out0 = state_slot(P, n + 1);
             if (n == nt - 1) {
@@ -75,7 +81,7 @@ int fill_descriptors(Batch *B) {
             }
             h[((size_t)0 * nt + n) * np + p] = st;
             // adjoint step n: lambda ping-pong starts in lam[0] at n = nt - 1
-            SweepPair ad = base;
+            SweepPair ad = base_for(1);
             const int ca = (nt - 1 - n) & 1;
             ad.in0 = P->lam[ca];
             ad.m = state_slot(P, n);
@@ -83,7 +89,7 @@ int fill_descriptors(Batch *B) {
             ad.out1 = P->b;
             h[((size_t)1 * nt + n) * np + p] = ad;
             // incremental state step n: dm ping-pong, dlambda^nt into lam[0]
-            SweepPair in = base;
+            SweepPair in = base_for(2);
             const int ci = n & 1;
             in.in0 = P->dm[ci];
             in.m = state_slot(P, n);
@@ -112,8 +118,9 @@ int launch_sweep(Batch *B, int kind, int n, cudaStream_t s) {
         f2 = n == nt - 1;
     }
     return sweep_batch_launch(kind, f1, f2, B->d_desc + ((size_t)kind * nt + n) * B->npairs,
-                              B->d_starts, B->npairs, B->d_counters + (size_t)kind * nt + n,
-                              B->grid, s);
+                              B->d_starts + (size_t)kind * (B->npairs + 1), B->npairs,
+                              B->d_counters + (size_t)kind * nt + n,
+                              sweep_blocks_per_sm(kind) * B->grid, s);
 }
 
 int reset_counters(Batch *B, cudaStream_t s) {
@@ -261,44 +268,51 @@ int fetch_all(Batch *B, bool flags) {
 
 double sc(Batch *B, int p, int slot) { return B->h_sc[(size_t)p * SC_COUNT + slot]; }
 
-// Time one interior batched adjoint step for candidate x1 chunks; keep the best.
+// For the adjoint and the incremental-state sweeps, time one interior batched
+// step for candidate x1 chunks (each plan's own autotuned chunk, or 4, 8, 16, 32
+// planes for every pair) and keep the best; the state sweep shares the
+// incremental-state chunk.
 int batch_autotune(Batch *B) {
-    const int cands[5] = {0, 4, 8, 16, 32};   // 0: each plan's own (autotuned) chunk
-    std::vector<int> own(B->npairs);
-    for (int p = 0; p < B->npairs; ++p) own[p] = B->plans[p]->chunk;
+    const int cands[5] = {0, 4, 8, 16, 32};   // 0: each plan's own chunk
     cudaEvent_t e0, e1;
     BLR_CK(cudaEventCreate(&e0));
     BLR_CK(cudaEventCreate(&e1));
     std::vector<int> all(B->npairs, 1);
     int rc = upload_active(B, all);
-    float best = 1e30f;
-    int best_c = 0;
-    const int n = B->nt > 1 ? 1 : 0;
-    for (int c = 0; c < 5 && !rc; ++c) {
-        for (int p = 0; p < B->npairs; ++p)
-            B->plans[p]->chunk = cands[c] ? (cands[c] < B->plans[p]->N1 ? cands[c] : B->plans[p]->N1)
-                                          : own[p];
-        if ((rc = fill_descriptors(B))) break;
-        float tot = 0.f;
-        for (int rep = 0; rep < 3 && !rc; ++rep) {
-            if ((rc = reset_counters(B, B->s))) break;
-            BLR_CK(cudaEventRecord(e0, B->s));
-            if ((rc = launch_sweep(B, 1, n, B->s))) break;
-            BLR_CK(cudaEventRecord(e1, B->s));
-            BLR_CK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            BLR_CK(cudaEventElapsedTime(&ms, e0, e1));
-            if (rep) tot += ms;
+    const int n = B->nt > 2 ? 1 : 0;
+    for (int kind = 1; kind <= 2 && !rc; ++kind) {
+        std::vector<int> own(B->npairs);
+        for (int p = 0; p < B->npairs; ++p) own[p] = sweep_chunk(B->plans[p], kind);
+        auto apply = [&](int c) {
+            for (int p = 0; p < B->npairs; ++p) {
+                blr_plan *P = B->plans[p];
+                sweep_set_chunk(P, kind, cands[c] ? (cands[c] < P->N1 ? cands[c] : P->N1) : own[p]);
+            }
+        };
+        float best = 1e30f;
+        int best_c = 0;
+        for (int c = 0; c < 5 && !rc; ++c) {
+            apply(c);
+            if ((rc = fill_descriptors(B))) break;
+            float tot = 0.f;
+            for (int rep = 0; rep < 3 && !rc; ++rep) {
+                if ((rc = reset_counters(B, B->s))) break;
+                if (cudaEventRecord(e0, B->s) != cudaSuccess) rc = BLR_ECUDA;
+                if (!rc) rc = launch_sweep(B, kind, n, B->s);
+                if (!rc && (cudaEventRecord(e1, B->s) != cudaSuccess ||
+                            cudaEventSynchronize(e1) != cudaSuccess))
+                    rc = BLR_ECUDA;
+                float ms = 0.f;
+                if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = BLR_ECUDA;
+                if (rep) tot += ms;
+            }
+            if (tot < best) {
+                best = tot;
+                best_c = c;
+            }
         }
-        if (tot < best) {
-            best = tot;
-            best_c = c;
-        }
+        apply(best_c);
     }
-    for (int p = 0; p < B->npairs; ++p)
-        B->plans[p]->chunk = cands[best_c] ? (cands[best_c] < B->plans[p]->N1 ? cands[best_c]
-                                                                              : B->plans[p]->N1)
-                                           : own[p];
     if (!rc) rc = fill_descriptors(B);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -347,11 +361,11 @@ int blr_batch_create(const blr_params *params, int npairs, blr_batch_t *out) {
     int sms = 0;
     if (!rc && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, B->device) != cudaSuccess)
         rc = BLR_ECUDA;
-    B->grid = 4 * (sms > 0 ? sms : 148);
+    B->grid = sms > 0 ? sms : 148;   // SMs; persistent grids are blocks-per-SM multiples
     const int nside = npairs < 8 ? npairs : 8;
     if (!rc &&
         (cudaMalloc(&B->d_desc, sizeof(SweepPair) * KINDS * B->nt * npairs) != cudaSuccess ||
-         cudaMalloc(&B->d_starts, sizeof(long long) * (npairs + 1)) != cudaSuccess ||
+         cudaMalloc(&B->d_starts, sizeof(long long) * KINDS * (npairs + 1)) != cudaSuccess ||
          cudaMalloc(&B->d_counters, sizeof(unsigned long long) * KINDS * B->nt) != cudaSuccess ||
          cudaMalloc(&B->d_active, sizeof(int) * npairs) != cudaSuccess ||
          cudaMallocHost(&B->h_sc, sizeof(double) * SC_COUNT * npairs) != cudaSuccess ||

@@ -43,7 +43,7 @@ struct Grid3 {
 // Operands of one pair in a batched sweep launch (see k_sweep_batch).
 struct SweepPair {
     Grid3 g;
-    int chunk, tk, tj, ti;   // x1 chunk; tiles along x3, x2, x1
+    int chunk, tk, tj, ti;   // x1 chunk; tiles along x3, x2, x1 (for this kind)
     const float *in0;        // state: m^n | adjoint: lambda^{n+1} | incremental: dm^n
     const float *m;          // adjoint / incremental: m^n
     const float *d;          // displacement
@@ -63,7 +63,8 @@ struct blr_plan {
     long long nfloat;  // floats in one coefficient array: 2*3*nb
     float dt;
     int device;
-    int chunk;          // x1 planes per sweep block (set by sweep_setup)
+    int chunk;          // x1 planes per state / incremental-state sweep block
+    int chunk_adj;      // x1 planes per adjoint sweep block (both set by sweep_setup)
     Grid3 grid;
 
     float *I0, *I1;
@@ -139,9 +140,11 @@ int sweep_adjoint(blr_plan *P, float *b, float *lambda0, cudaStream_t s);
 int sweep_incremental(blr_plan *P, cudaStream_t s);            // dm -> dlambda^nt in lam[0]
 int sweep_batch_launch(int kind, bool f1, bool f2, const SweepPair *pairs, const long long *starts,
                        int npairs, unsigned long long *counter, int grid, cudaStream_t s);
-void sweep_tiles(const blr_plan *P, int *tk, int *tj, int *ti);
-int sweep_threads();
-int sweep_min_chunk();
+// kind: 0 state, 1 adjoint, 2 incremental state
+void sweep_tiles(const blr_plan *P, int kind, int *tk, int *tj, int *ti);
+int sweep_chunk(const blr_plan *P, int kind);
+int sweep_blocks_per_sm(int kind);
+void sweep_set_chunk(blr_plan *P, int kind, int chunk);
 int sweep_autotune(blr_plan *P, cudaStream_t s);
 
 // reduce.cu

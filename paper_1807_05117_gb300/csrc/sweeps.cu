@@ -11,12 +11,13 @@
 // no atomics and is deterministic.
 //
 // Every kernel marches along x1: a block owns a 32 (x3) x MJ (x2) column of
-// voxels over a chunk of x1 planes and keeps a ring of one-voxel-haloed planes
-// in shared memory (periodic wrap on load), filled by cp.async two planes ahead
-// of use; per-voxel operands of the next output plane are prefetched into
-// registers.  In the adjoint each source plane is
-// read once and scattered in registers into the three output planes it reaches,
-// so a voxel costs 9 shared-memory reads instead of 27.
+// voxels (32 x AJ for the adjoint) over a chunk of x1 planes and keeps a ring of
+// one-voxel-haloed planes in shared memory (periodic wrap on load), filled by
+// cp.async two planes ahead of use; per-voxel operands of the next output plane
+// are prefetched into registers.  In the adjoint each source plane is read once
+// and scattered in registers into the three output planes it reaches, and each
+// thread serves ARJ x2 rows, so a voxel costs 3 (ARJ + 2) / ARJ float4 shared-memory reads
+// for its 27 transpose neighbours.
 #include "blr_internal.cuh"
 
 namespace {
@@ -142,34 +143,6 @@ __device__ __forceinline__ void issue_plane1(uint32_t dst, const float *__restri
     cp_commit();
 }
 
-// (d0, d1, d2, lambda) of plane s into a float4 ring slot and m^n into a scalar slot.
-__device__ __forceinline__ void issue_plane_adj(uint32_t dq, uint32_t dm,
-                                                const float *__restrict__ d,
-                                                const float *__restrict__ lam,
-                                                const float *__restrict__ m, int s, int i_end,
-                                                int N1, long long plane, long long V,
-                                                long long off0, long long off1, bool ok1) {
-    if (s <= i_end) {
-        const long long base = (long long)wrap1(s, N1) * plane;
-        const float *src = d + base + off0;
-        cp4(dq, src);
-        cp4(dq + 4, src + V);
-        cp4(dq + 8, src + 2 * V);
-        cp4(dq + 12, lam + base + off0);
-        cp4(dm, m + base + off0);
-        if (ok1) {
-            const float *src1 = d + base + off1;
-            const uint32_t dq1 = dq + MT * 16;
-            cp4(dq1, src1);
-            cp4(dq1 + 4, src1 + V);
-            cp4(dq1 + 8, src1 + 2 * V);
-            cp4(dq1 + 12, lam + base + off1);
-            cp4(dm + MT * 4, m + base + off1);
-        }
-    }
-    cp_commit();
-}
-
 // Two scalar fields of plane s into two ring slots.
 __device__ __forceinline__ void issue_plane2(uint32_t dst_a, const float *__restrict__ fa,
                                              uint32_t dst_b, const float *__restrict__ fb, int s,
@@ -269,93 +242,186 @@ k_state_march(const float *__restrict__ m_in, const float *__restrict__ d,
 //   lambda^n(y) = sum_{e in {-1,0,1}^3} lambda^{n+1}(y-e) prod_a hat(d_a(y-e) - e_a)
 // Source plane s adds to output planes s-1, s, s+1 (registers acc_a/b/c);
 // output plane s-1 is then complete.  Planes arrive by cp.async two iterations
-// ahead: (d, lambda) in a 4-slot ring, m^n in an 8-slot ring.
+// ahead: (d, lambda) in a 4-slot float4 ring, m^n in an 8-slot ring.
+//
+// Each thread owns ARJ consecutive x2 rows of one x3 column (a block: 32 x3
+// columns x 8 ARJ rows), so a source voxel read from shared memory serves every
+// one of its targets in those rows from registers: ARJ + 2 source rows x 3
+// columns = 3 (ARJ + 2) float4 reads per ARJ voxels instead of 9 per voxel.
+constexpr int ARJ = 2;                         // x2 rows per thread
+constexpr int AJ = 8 * ARJ;                    // x2 extent of an adjoint block
+constexpr int ADJ_BLOCKS = ARJ >= 4 ? 2 : 3;   // resident adjoint blocks per SM
+constexpr int AHP = (AJ + 2) * MHK;            // haloed plane
+constexpr int ANC = (AHP + MT - 1) / MT;       // halo positions per thread
+// Dynamic shared memory of an adjoint block: float4 ring [4][AHP], m^n ring [8][AHP].
+constexpr int ADJ_SMEM = 4 * AHP * 16 + 8 * AHP * 4;
+
+// Hat weight of a neighbour at offset e (target - source) for a displacement d.
+__device__ __forceinline__ float hat_e(int e, float d) {
+    return e == 0 ? 1.f - fabsf(d) : (e == 1 ? fmaxf(d, 0.f) : fmaxf(-d, 0.f));
+}
+
+// (d0, d1, d2, lambda) and m^n of plane s into ring slots (byte addresses of the
+// slots' first elements).  Copy i of a halo position writes component
+// (i + lane / 8) mod 4, so the 32 lanes of a copy hit 32 distinct banks.
+__device__ __forceinline__ void issue_plane_adj_c(uint32_t q_slot, uint32_t m_slot,
+                                                  const float *__restrict__ d,
+                                                  const float *__restrict__ lam,
+                                                  const float *__restrict__ m, int s, int i_end,
+                                                  int N1, long long plane, long long V,
+                                                  const int (&off)[ANC]) {
+    if (s <= i_end) {
+        const long long base = (long long)wrap1(s, N1) * plane;
+        const int rot = (threadIdx.x >> 3) & 3;
+#pragma unroll
+        for (int c = 0; c < ANC; ++c) {
+            const int p = threadIdx.x + c * MT;
+            if (c + 1 < ANC || p < AHP) {
+                const long long o = base + off[c];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int comp = (i + rot) & 3;
+                    const float *src = comp == 3 ? lam + o : d + comp * V + o;
+                    cp4(q_slot + (uint32_t)(p * 16 + comp * 4), src);
+                }
+                cp4(m_slot + (uint32_t)(p * 4), m + o);
+            }
+        }
+    }
+    cp_commit();
+}
+
+// Shared-memory rings of one adjoint block, carved from dynamic shared memory.
+struct AdjRings {
+    float4 (*Q)[AHP];   // [4][AHP]: (d0, d1, d2, lambda^{n+1})
+    float (*M)[AHP];    // [8][AHP]: m^n
+};
+
+__device__ __forceinline__ AdjRings adj_rings() {
+    extern __shared__ __align__(16) unsigned char blr_dyn_smem[];
+    AdjRings R;
+    R.Q = reinterpret_cast<float4 (*)[AHP]>(blr_dyn_smem);
+    R.M = reinterpret_cast<float (*)[AHP]>(blr_dyn_smem + 4 * AHP * 16);
+    return R;
+}
+
 template <bool FIRST, bool WRITE_LAM>
 __device__ __forceinline__ void
 adjoint_tile(const float *__restrict__ lam_in, const float *__restrict__ m_n,
              const float *__restrict__ d, float *__restrict__ lam_out, float *__restrict__ b,
              float dt, const Grid3 g, int CH, int k0, int j0, int i0) {
-    __shared__ __align__(16) float4 sQ[4][MHP];   // (d0, d1, d2, lambda^{n+1})
-    __shared__ __align__(16) float sM[8][MHP];    // m^n
+    const AdjRings rings = adj_rings();
+    float4 (*sQ)[AHP] = rings.Q;
+    float (*sM)[AHP] = rings.M;
     const int i_end = min(i0 + CH, g.N1);
-    const Slots ps = plane_slots(g, k0, j0);
     const long long plane = (long long)g.N2 * g.N3;
-    const int tk = threadIdx.x & 31, tj = threadIdx.x >> 5;
-    const int k = k0 + tk, j = j0 + tj;
-    const bool active = k < g.N3 && j < g.N2;
-    const long long col = (long long)j * g.N3 + k;
-    const int hj = tj + 1, hk = tk + 1;
-    const int c = hj * MHK + hk;
-    const uint32_t q_base = smem_u32(&sQ[0][threadIdx.x]);
-    const uint32_t m_base = smem_u32(&sM[0][threadIdx.x]);
-
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int k = k0 + lane;
+    const int jb = j0 + ARJ * w;                  // first row of this thread
+    const bool kin = k < g.N3;
+    const int hk = 1 + lane;
+    int off[ANC];                                 // in-plane offsets of the halo positions
+#pragma unroll
+    for (int c = 0; c < ANC; ++c) {
+        const int p = threadIdx.x + c * MT;
+        const int hj = p / MHK, hkk = p - hj * MHK;
+        off[c] = p < AHP ? wrapi(j0 + hj - 1, g.N2) * g.N3 + wrapi(k0 + hkk - 1, g.N3) : 0;
+    }
+    const uint32_t q0s = smem_u32(&sQ[0][0]);
+    const uint32_t m0s = smem_u32(&sM[0][0]);
     const int N1 = g.N1;
     const long long V = g.V;
-    // copy plane s (if it belongs to this chunk's window) into ring slot r
-#define BLR_ISSUE_ADJ(S, R)                                                               \
-    issue_plane_adj(q_base + (uint32_t)((R) & 3) * (MHP * 16),                             \
-                    m_base + (uint32_t)((R) & 7) * (MHP * 4), d, lam_in, m_n, (S), i_end, N1, \
-                    plane, V, ps.off0, ps.off1, ps.ok1)
+#define BLR_ISSUE_ADJ(S, R)                                                                  \
+    issue_plane_adj_c(q0s + (uint32_t)((R) & 3) * (AHP * 16), m0s + (uint32_t)((R) & 7) * (AHP * 4), \
+                      d, lam_in, m_n, (S), i_end, N1, plane, V, off)
     BLR_ISSUE_ADJ(i0 - 1, 0);
     BLR_ISSUE_ADJ(i0, 1);
-    float acc_a = 0.f, acc_b = 0.f, acc_c = 0.f;
-    float bb[3] = {0.f, 0.f, 0.f};   // body force at the output voxel of the next plane
+    float acc_a[ARJ], acc_b[ARJ], acc_c[ARJ], bb[ARJ][3];
+#pragma unroll
+    for (int jj = 0; jj < ARJ; ++jj) {
+        acc_a[jj] = acc_b[jj] = acc_c[jj] = 0.f;
+        bb[jj][0] = bb[jj][1] = bb[jj][2] = 0.f;
+    }
     for (int s = i0 - 1; s <= i_end; ++s) {
         const int r = s - i0 + 1;
         cp_wait1();
         __syncthreads();
         BLR_ISSUE_ADJ(s + 2, r + 2);
-        if (active) {
+        if (kin) {
             if (WRITE_LAM) {
                 const float4 *Q = sQ[ring4(r)];
-#define BLR_SRC(DJ, DK)                                                       \
-    {                                                                         \
-        const float4 q = Q[c + (DJ) * MHK + (DK)];                            \
-        const float w = q.w * hat<-(DJ)>(q.y) * hat<-(DK)>(q.z);              \
-        acc_a = fmaf(w, fmaxf(-q.x, 0.f), acc_a);                             \
-        acc_b = fmaf(w, 1.f - fabsf(q.x), acc_b);                             \
-        acc_c = fmaf(w, fmaxf(q.x, 0.f), acc_c);                              \
-    }
-                BLR_SRC(-1, -1) BLR_SRC(-1, 0) BLR_SRC(-1, 1)
-                BLR_SRC(0, -1) BLR_SRC(0, 0) BLR_SRC(0, 1)
-                BLR_SRC(1, -1) BLR_SRC(1, 0) BLR_SRC(1, 1)
-#undef BLR_SRC
+#pragma unroll
+                for (int sr = 0; sr < ARJ + 2; ++sr) {        // source halo row ARJ w + sr
+#pragma unroll
+                    for (int dk = -1; dk <= 1; ++dk) {
+                        const float4 q = Q[(ARJ * w + sr) * MHK + hk + dk];
+                        const float wl = q.w * hat_e(-dk, q.z);
+                        const float xa = fmaxf(-q.x, 0.f), xb = 1.f - fabsf(q.x), xc = fmaxf(q.x, 0.f);
+#pragma unroll
+                        for (int jj = 0; jj < ARJ; ++jj) {
+                            const int dj = sr - 1 - jj;      // source row - target row
+                            if (dj >= -1 && dj <= 1) {
+                                const float wt = wl * hat_e(-dj, q.y);
+                                acc_a[jj] = fmaf(wt, xa, acc_a[jj]);
+                                acc_b[jj] = fmaf(wt, xb, acc_b[jj]);
+                                acc_c[jj] = fmaf(wt, xc, acc_c[jj]);
+                            }
+                        }
+                    }
+                }
             }
             const int o = s - 1;
             if (o >= i0) {
-                const long long idx = (long long)o * plane + col;
-                const float4 q0 = sQ[ring4(r + 3)][c];
-                const AxisW a0 = axis_weights(q0.x);
-                const float *P0 = a0.lo < 0 ? sM[ring8(r + 6)] : sM[ring8(r + 7)];
-                const float *P1 = a0.lo < 0 ? sM[ring8(r + 7)] : sM[ring8(r)];
-                float G[3];
-                trilinear2<true>(P0, P1, hj, hk, a0, axis_weights(q0.y), axis_weights(q0.z), G);
-                const float sl = dt * q0.w;
+                const float4 *Qo = sQ[ring4(r + 3)];
+                const float *Ma = sM[ring8(r + 6)], *Mb = sM[ring8(r + 7)], *Mc = sM[ring8(r)];
 #pragma unroll
-                for (int a = 0; a < 3; ++a)
-                    b[a * g.V + idx] = FIRST ? sl * G[a] : fmaf(sl, G[a], bb[a]);
-                if (WRITE_LAM) lam_out[idx] = acc_a;
+                for (int jj = 0; jj < ARJ; ++jj) {
+                    const int j = jb + jj;
+                    if (j < g.N2) {
+                        const int hj = 1 + ARJ * w + jj;
+                        const float4 q0 = Qo[hj * MHK + hk];
+                        const AxisW a0 = axis_weights(q0.x);
+                        float G[3];
+                        trilinear2<true>(a0.lo < 0 ? Ma : Mb, a0.lo < 0 ? Mb : Mc, hj, hk, a0,
+                                         axis_weights(q0.y), axis_weights(q0.z), G);
+                        const float sl = dt * q0.w;
+                        const long long idx = (long long)o * plane + (long long)j * g.N3 + k;
+#pragma unroll
+                        for (int a = 0; a < 3; ++a)
+                            b[a * V + idx] = FIRST ? sl * G[a] : fmaf(sl, G[a], bb[jj][a]);
+                        if (WRITE_LAM) lam_out[idx] = acc_a[jj];
+                    }
+                }
             }
             if (!FIRST && s >= i0 && s < i_end) {
-                const long long nidx = (long long)s * plane + col;
 #pragma unroll
-                for (int a = 0; a < 3; ++a) bb[a] = b[a * g.V + nidx];
+                for (int jj = 0; jj < ARJ; ++jj) {
+                    const int j = jb + jj;
+                    if (j < g.N2) {
+                        const long long nidx = (long long)s * plane + (long long)j * g.N3 + k;
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) bb[jj][a] = b[a * V + nidx];
+                    }
+                }
             }
         }
-        acc_a = acc_b;
-        acc_b = acc_c;
-        acc_c = 0.f;
+#pragma unroll
+        for (int jj = 0; jj < ARJ; ++jj) {
+            acc_a[jj] = acc_b[jj];
+            acc_b[jj] = acc_c[jj];
+            acc_c[jj] = 0.f;
+        }
     }
 #undef BLR_ISSUE_ADJ
 }
 
 template <bool FIRST, bool WRITE_LAM>
-__global__ void __launch_bounds__(MT, 4)
+__global__ void __launch_bounds__(MT, ADJ_BLOCKS)
 k_adjoint_march(const float *__restrict__ lam_in, const float *__restrict__ m_n,
                 const float *__restrict__ d, float *__restrict__ lam_out,
                 float *__restrict__ b, float dt, Grid3 g, int CH) {
     adjoint_tile<FIRST, WRITE_LAM>(lam_in, m_n, d, lam_out, b, dt, g, CH, blockIdx.x * MK,
-                                   blockIdx.y * MJ, blockIdx.z * CH);
+                                   blockIdx.y * AJ, blockIdx.z * CH);
 }
 
 // ---------------------------------------------------------------------------
@@ -443,7 +509,7 @@ k_incstate_march(const float *__restrict__ dm_in, const float *__restrict__ m_n,
 // item order (items of pair p are starts[p] .. starts[p+1]-1); each item is a
 // full march tile of that pair, so the results equal the single-pair kernels'.
 template <int KIND, bool F1, bool F2>
-__global__ void __launch_bounds__(MT, 4)
+__global__ void __launch_bounds__(MT, KIND == 1 ? ADJ_BLOCKS : 4)
 k_sweep_batch(const SweepPair *__restrict__ pairs, const long long *__restrict__ starts,
               int npairs, unsigned long long *counter) {
     __shared__ long long s_item;
@@ -465,11 +531,11 @@ k_sweep_batch(const SweepPair *__restrict__ pairs, const long long *__restrict__
         const int kt = (int)(local % P.tk);
         const int jt = (int)((local / P.tk) % P.tj);
         const int it = (int)(local / ((long long)P.tk * P.tj));
-        const int k0 = kt * MK, j0 = jt * MJ, i0 = it * P.chunk;
-        if (KIND == 0)
+        const int k0 = kt * MK, j0 = jt * (KIND == 1 ? AJ : MJ), i0 = it * P.chunk;
+        if constexpr (KIND == 0)
             state_tile<F1>(P.in0, P.d, P.out0, P.g, P.chunk, P.aux, P.out1, P.scale, P.partials,
                            k0, j0, i0);
-        else if (KIND == 1)
+        else if constexpr (KIND == 1)
             adjoint_tile<F1, F2>(P.in0, P.m, P.d, P.out0, P.out1, P.dt, P.g, P.chunk, k0, j0, i0);
         else
             incstate_tile<F1, F2>(P.in0, P.m, P.d, P.aux, P.out0, P.dt, P.scale, P.g, P.chunk,
@@ -487,22 +553,50 @@ dim3 sweep_grid(const blr_plan *P) {
                 (unsigned)ceil_div_ll(P->N1, P->chunk));
 }
 
+dim3 adjoint_grid(const blr_plan *P) {
+    return dim3((unsigned)ceil_div_ll(P->N3, MK), (unsigned)ceil_div_ll(P->N2, AJ),
+                (unsigned)ceil_div_ll(P->N1, P->chunk_adj));
+}
+
+// The adjoint kernels' shared memory exceeds the default 48 KB window.
+int adjoint_smem_attributes() {
+    static bool done = false;
+    if (done) return BLR_OK;
+    BLR_CK(cudaFuncSetAttribute(k_adjoint_march<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_adjoint_march<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_adjoint_march<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_adjoint_march<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
+    done = true;
+    return BLR_OK;
+}
+
 }  // namespace
 
-// Chunk of x1 planes per block.  Four blocks fit on an SM (register bound), so
-// the grid is sized to at most one wave of 4 x SMs blocks: a partial second wave
-// would cost a whole extra block duration.  Each chunk loads chunk + 2 planes.
+// Chunk of x1 planes per block.  Four state / incremental blocks (register
+// bound) or ADJ_BLOCKS adjoint blocks (shared memory and registers) fit on an SM, so each grid
+// is sized to at most one wave: a partial second wave would cost a whole extra
+// block duration.  Each chunk loads chunk + 2 planes.
+namespace {
+int one_wave_chunk(long long N1, long long cols, long long blocks_per_wave) {
+    long long slices = blocks_per_wave / cols;      // floor: never exceed one wave
+    if (slices < 1) slices = 1;
+    long long ch = ceil_div_ll(N1, slices);
+    return (int)(ch < 2 ? 2 : ch);
+}
+}  // namespace
+
 int sweep_setup(blr_plan *P) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device) != cudaSuccess || sms < 1)
         sms = 148;
-    const long long cols = ceil_div_ll(P->N3, MK) * ceil_div_ll(P->N2, MJ);
-    long long slices = (4LL * sms) / cols;          // floor: never exceed one wave
-    if (slices < 1) slices = 1;
-    long long ch = ceil_div_ll(P->N1, slices);
-    if (ch < 2) ch = 2;
-    P->chunk = (int)ch;
-    return BLR_OK;
+    const long long k_tiles = ceil_div_ll(P->N3, MK);
+    P->chunk = one_wave_chunk(P->N1, k_tiles * ceil_div_ll(P->N2, MJ), 4LL * sms);
+    P->chunk_adj = one_wave_chunk(P->N1, k_tiles * ceil_div_ll(P->N2, AJ), (long long)ADJ_BLOCKS * sms);
+    return adjoint_smem_attributes();
 }
 
 // Image-term partial sums written by the last state step (one per 32-voxel row
@@ -555,8 +649,9 @@ int sweep_state(blr_plan *P, cudaStream_t s) {
 // lambda0 != nullptr, lambda^0 into lambda0.  Segments are visited backwards,
 // each recomputed from its checkpoint when needed.
 int sweep_adjoint(blr_plan *P, float *b, float *lambda0, cudaStream_t s) {
-    const dim3 grid = sweep_grid(P);
+    const dim3 grid = sweep_grid(P), agrid = adjoint_grid(P);
     const int nt = P->p.nt;
+    const int CH = P->chunk_adj;
     int cur = 0;
     for (int j = P->nseg - 1; j >= 0; --j) {
         int rc = ensure_segment(P, grid, j, s);
@@ -569,13 +664,13 @@ int sweep_adjoint(blr_plan *P, float *b, float *lambda0, cudaStream_t s) {
             const bool first = (n == nt - 1);
             const bool wlam = (n > 0) || (lambda0 != nullptr);
             if (first && wlam)
-                k_adjoint_march<true, true><<<grid, MT, 0, s>>>(lin, mn, P->d, lout, b, P->dt, P->grid, P->chunk);
+                k_adjoint_march<true, true><<<agrid, MT, ADJ_SMEM, s>>>(lin, mn, P->d, lout, b, P->dt, P->grid, CH);
             else if (first)
-                k_adjoint_march<true, false><<<grid, MT, 0, s>>>(lin, mn, P->d, lout, b, P->dt, P->grid, P->chunk);
+                k_adjoint_march<true, false><<<agrid, MT, ADJ_SMEM, s>>>(lin, mn, P->d, lout, b, P->dt, P->grid, CH);
             else if (wlam)
-                k_adjoint_march<false, true><<<grid, MT, 0, s>>>(lin, mn, P->d, lout, b, P->dt, P->grid, P->chunk);
+                k_adjoint_march<false, true><<<agrid, MT, ADJ_SMEM, s>>>(lin, mn, P->d, lout, b, P->dt, P->grid, CH);
             else
-                k_adjoint_march<false, false><<<grid, MT, 0, s>>>(lin, mn, P->d, lout, b, P->dt, P->grid, P->chunk);
+                k_adjoint_march<false, false><<<agrid, MT, ADJ_SMEM, s>>>(lin, mn, P->d, lout, b, P->dt, P->grid, CH);
             BLR_CK_LAUNCH();
             cur = 1 - cur;
         }
@@ -618,7 +713,8 @@ int sweep_incremental(blr_plan *P, cudaStream_t s) {
 
 int sweep_batch_launch(int kind, bool f1, bool f2, const SweepPair *pairs, const long long *starts,
                        int npairs, unsigned long long *counter, int grid, cudaStream_t s) {
-#define BLR_BL(K, A, B) k_sweep_batch<K, A, B><<<grid, MT, 0, s>>>(pairs, starts, npairs, counter)
+#define BLR_BL(K, A, B) \
+    k_sweep_batch<K, A, B><<<grid, MT, (K) == 1 ? ADJ_SMEM : 0, s>>>(pairs, starts, npairs, counter)
     if (kind == 0) {
         if (f1) BLR_BL(0, true, false); else BLR_BL(0, false, false);
     } else if (kind == 1) {
@@ -637,53 +733,76 @@ int sweep_batch_launch(int kind, bool f1, bool f2, const SweepPair *pairs, const
     return BLR_OK;
 }
 
-// Tiles of one pair for its current chunk.
-void sweep_tiles(const blr_plan *P, int *tk, int *tj, int *ti) {
-    *tk = (int)ceil_div_ll(P->N3, MK);
-    *tj = (int)ceil_div_ll(P->N2, MJ);
-    *ti = (int)ceil_div_ll(P->N1, P->chunk);
+int sweep_blocks_per_sm(int kind) { return kind == 1 ? ADJ_BLOCKS : 4; }
+
+int sweep_chunk(const blr_plan *P, int kind) { return kind == 1 ? P->chunk_adj : P->chunk; }
+
+void sweep_set_chunk(blr_plan *P, int kind, int chunk) {
+    if (kind == 1) P->chunk_adj = chunk;
+    else P->chunk = chunk;
 }
 
-int sweep_threads() { return MT; }
+// Tiles of one pair for a sweep kind at its current chunk.
+void sweep_tiles(const blr_plan *P, int kind, int *tk, int *tj, int *ti) {
+    *tk = (int)ceil_div_ll(P->N3, MK);
+    *tj = (int)ceil_div_ll(P->N2, kind == 1 ? AJ : MJ);
+    *ti = (int)ceil_div_ll(P->N1, sweep_chunk(P, kind));
+}
 
-// Smallest x1 chunk any candidate uses (sizes the partials buffer).
-int sweep_min_chunk() { return 4; }
+namespace {
 
-// Autotuner: time an interior adjoint step (the dominant kernel) on the plan's
-// own buffers for each candidate chunk and keep the fastest.  Candidates: the
-// one-wave chunk of sweep_setup and 4, 8, 16, 32 planes.
+// One interior step of a sweep kind on the plan's own buffers (timing only;
+// the state kind shares the incremental-state chunk and is not timed).
+int time_step(blr_plan *P, int kind, cudaStream_t s) {
+    if (kind == 1) {
+        k_adjoint_march<false, true><<<adjoint_grid(P), MT, ADJ_SMEM, s>>>(
+            P->lam[0], P->m, P->d, P->lam[1], P->b, P->dt, P->grid, P->chunk_adj);
+    } else {
+        k_incstate_march<false, false><<<sweep_grid(P), MT, 0, s>>>(
+            P->dm[0], P->m, P->d, P->dv, P->dm[1], P->dt, 1.f, P->grid, P->chunk);
+    }
+    BLR_CK_LAUNCH();
+    return BLR_OK;
+}
+
+}  // namespace
+
+// Autotuner: for the adjoint and the incremental-state kernels, time an
+// interior step on the plan's own buffers for each candidate chunk (the
+// one-wave chunk of sweep_setup and 4, 8, 16, 32 planes) and keep the fastest.
 int sweep_autotune(blr_plan *P, cudaStream_t s) {
-    const int heur = P->chunk;
-    int cands[5] = {heur, 4, 8, 16, 32};
     cudaEvent_t e0, e1;
     BLR_CK(cudaEventCreate(&e0));
     BLR_CK(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int best_ch = heur;
-    for (int c = 0; c < 5; ++c) {
-        const int ch = cands[c] < P->N1 ? cands[c] : P->N1;
-        if (c > 0 && ch == heur) continue;
-        P->chunk = ch;
-        const dim3 grid = sweep_grid(P);
-        float tot = 0.f;
-        for (int rep = 0; rep < 3; ++rep) {
-            BLR_CK(cudaEventRecord(e0, s));
-            k_adjoint_march<false, true><<<grid, MT, 0, s>>>(P->lam[0], P->m, P->d, P->lam[1], P->b,
-                                                             P->dt, P->grid, P->chunk);
-            BLR_CK_LAUNCH();
-            BLR_CK(cudaEventRecord(e1, s));
-            BLR_CK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            BLR_CK(cudaEventElapsedTime(&ms, e0, e1));
-            if (rep > 0) tot += ms;   // first run warms up
+    int rc = BLR_OK;
+    for (int kind = 1; kind <= 2 && !rc; ++kind) {
+        const int heur = sweep_chunk(P, kind);
+        const int cands[5] = {heur, 4, 8, 16, 32};
+        float best = 1e30f;
+        int best_ch = heur;
+        for (int c = 0; c < 5 && !rc; ++c) {
+            const int ch = cands[c] < P->N1 ? cands[c] : P->N1;
+            if (c > 0 && ch == heur) continue;
+            sweep_set_chunk(P, kind, ch);
+            float tot = 0.f;
+            for (int rep = 0; rep < 3 && !rc; ++rep) {
+                if (cudaEventRecord(e0, s) != cudaSuccess) rc = BLR_ECUDA;
+                if (!rc) rc = time_step(P, kind, s);
+                if (!rc && (cudaEventRecord(e1, s) != cudaSuccess ||
+                            cudaEventSynchronize(e1) != cudaSuccess))
+                    rc = BLR_ECUDA;
+                float ms = 0.f;
+                if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = BLR_ECUDA;
+                if (rep > 0) tot += ms;   // the first run warms up
+            }
+            if (tot < best) {
+                best = tot;
+                best_ch = ch;
+            }
         }
-        if (tot < best) {
-            best = tot;
-            best_ch = ch;
-        }
+        sweep_set_chunk(P, kind, best_ch);
     }
-    P->chunk = best_ch;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    return BLR_OK;
+    return rc;
 }

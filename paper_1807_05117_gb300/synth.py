@@ -18,6 +18,9 @@ which are not available here):
   classes (intensities 0.2 / 0.5 / 0.8 outer to inner, semi-axes 0.40 / 0.30 /
   0.18 of the grid jittered +-10% per axis), periodic Gaussian blur of 1 voxel
   and N(0, 0.01^2) noise; the target is the same phantom evaluated at x - u(x).
+* ``uneven_pairs``   -- the many-pair batching workload: grids drawn from
+  {64^3, 96^3, 128^3, 160x192x160}, bands from {16^3, 24^3, 32^3}, maximum warp
+  uniform in [3, 8] voxels, one phantom seed per pair.
 * ``random_coefficients`` -- complex Gaussian band coefficients with a
   smoothness decay (1 + |k|^2)^-1, scaled so that sum_k |v_c(k)| equals a given
   bound; that bound caps the spatial velocity of every component.
@@ -136,6 +139,30 @@ def random_coefficients(band, seed: int, bound: float) -> np.ndarray:
     z *= (1.0 / (1.0 + k2))[None]
     l1 = np.abs(z).reshape(3, -1).sum(axis=1)
     return z * (bound / l1)[:, None, None, None]
+
+
+UNEVEN_GRIDS = ((64, 64, 64), (96, 96, 96), (128, 128, 128), (160, 192, 160))
+UNEVEN_BANDS = ((16, 16, 16), (24, 24, 24), (32, 32, 32))
+
+
+def uneven_pairs(npairs: int, seed: int) -> list:
+    """Shapes of a batch of independent registration pairs: per pair a dict
+    with ``n`` (grid), ``band``, ``max_disp`` (voxels) and ``seed`` (its
+    phantom_pair seed)."""
+    rng = _rng(seed)
+    out = []
+    for p in range(npairs):
+        out.append(dict(n=UNEVEN_GRIDS[int(rng.integers(len(UNEVEN_GRIDS)))],
+                        band=UNEVEN_BANDS[int(rng.integers(len(UNEVEN_BANDS)))],
+                        max_disp=float(rng.uniform(3.0, 8.0)), seed=int(seed) * 1000 + p))
+    return out
+
+
+def phantom_pair_f32(n, seed: int, max_disp: float):
+    """phantom_pair rounded to float32 (I0, I1): a picklable task for a process
+    pool that prepares many pairs."""
+    I0, I1, _ = phantom_pair(tuple(n), seed, max_disp=max_disp)
+    return I0.astype(np.float32), I1.astype(np.float32)
 
 
 def random_direction(band, seed: int) -> np.ndarray:

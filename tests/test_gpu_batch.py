@@ -2,7 +2,11 @@
 sweep kernels over a (pair, tile) work queue, PCG iterations replayed from a
 CUDA graph, autotuned tile length).  Each pair's arithmetic equals a single
 plan's, so gradients, Hessian-vector products and whole registrations must be
-bit-identical to per-pair calls."""
+bit-identical to per-pair calls: on six small pairs, and on the 64-pair
+workload (grids 64^3 to 160x192x160, bands 16^3 to 32^3) with one pair of every
+grid size rerun alone."""
+
+import os
 
 import numpy as np
 import pytest
@@ -78,3 +82,41 @@ def test_batch_rejects_mixed_shapes_of_time(setup):
         blr.Batch([blr.make_params((16, 16, 16), (4, 4, 4), 4),
                    blr.make_params((16, 16, 16), (4, 4, 4), 5)])
     assert ei.value.code == blr.BLR_EINVAL
+
+
+# --- the many-pair workload: 64 pairs, grids {64^3 .. 160x192x160}, bands
+# {16^3, 24^3, 32^3}, 3-8 voxel phantom warps, 10 Newton x <= 20 PCG ---------------
+
+
+@pytest.mark.slow
+def test_uneven_batch_of_64_pairs():
+    import multiprocessing as mp
+    from paper_1807_05117_gb300 import blr
+    pairs = synth.uneven_pairs(64, 4)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        imgs = pool.starmap(synth.phantom_pair_f32,
+                            [(p["n"], p["seed"], p["max_disp"]) for p in pairs])
+    batch = blr.Batch([(p["n"], p["band"]) for p in pairs], 10)
+    for i, (I0, I1) in enumerate(imgs):
+        batch.set_images(i, torch.from_numpy(I0).cuda(), torch.from_numpy(I1).cuda())
+    vb = [torch.zeros((3,) + p["band"], dtype=torch.complex64, device="cuda") for p in pairs]
+    reps = batch.newton(vb, 10, 20, 1e-2)
+    for r in reps:
+        assert r.status == blr.BLR_OK
+        assert r.energy < r.energy0
+    # one pair of every grid size against its own single plan, bit for bit
+    chosen = {}
+    for i, p in enumerate(pairs):
+        chosen.setdefault(p["n"], i)
+    for i in chosen.values():
+        p = pairs[i]
+        pl = blr.Plan(p["n"], p["band"], 10)
+        pl.set_images(torch.from_numpy(imgs[i][0]).cuda(), torch.from_numpy(imgs[i][1]).cuda())
+        vs = torch.zeros_like(vb[i])
+        rs = pl.newton(vs, 10, 20, 1e-2)
+        assert (reps[i].newton_iters, reps[i].pcg_iters, reps[i].n_halvings) == \
+            (rs.newton_iters, rs.pcg_iters, rs.n_halvings)
+        assert reps[i].energy == rs.energy
+        assert torch.equal(vb[i], vs)
+        pl.close()
+    batch.close()

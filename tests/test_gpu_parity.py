@@ -6,7 +6,10 @@ inputs.  Tolerances (relative L2):
               the axis-1 DFT stages; everything else FP32) 5e-5 on the fields,
               5e-4 on the gradient, the HVP and the PCG iterates;
 a full registration's final energy within 1e-3 with PCG iteration counts within
-+-1 per Newton step."""
++-1 per Newton step.  Cases: ragged tiles, a grid smaller than one tile, one
+time step, the 32^3 blob registration, the 128^3 phantom (band 32^3) and the
+192x224x192 phantom with band 48^3 (gradient and HVP against the oracle in both
+precisions; a 10-step registration mixed against FP32)."""
 
 import numpy as np
 import pytest
@@ -229,3 +232,62 @@ def test_full_size_gradient_and_hessvec(blr, precision):
     assert abs(float(e[0]) - pt.energy) <= c.tol["field"] * pt.energy
     assert rel(g.cpu().numpy(), pt.gradient()[0]) <= c.tol["grad"]
     assert rel(h.cpu().numpy(), pt.gn_hessvec(c.dv)[0]) <= c.tol["grad"]
+
+
+# --- precision form: 192x224x192 (the paper's 180x210x180 brains padded), band
+# 48^3, 10 steps, 8-voxel phantom warp --------------------------------------------
+
+N3C, B3C, SEED3 = (192, 224, 192), (48, 48, 48), 3001
+
+
+@pytest.fixture(scope="module")
+def big_point():
+    I0, I1, _ = synth.phantom_pair(N3C, SEED3, max_disp=8.0)
+    vt = synth.random_coefficients(B3C, SEED3 + 1, bound=200.0)   # 0.63 voxel per step
+    dvt = synth.random_direction(B3C, SEED3 + 2)
+    (I0f, I0d), (I1f, I1d), (vtf, vtd), (dvf, dvd) = synth.as_device_inputs(I0, I1, vt, dvt)
+    pt = O.Point(vtd, I0d, I1d, O.Params(N3C, B3C, 10))
+    g_ref = pt.gradient()[0]
+    h_ref = pt.gn_hessvec(dvd)[0]
+    return dict(I0f=I0f, I1f=I1f, vtf=vtf, dvf=dvf, energy=pt.energy, g=g_ref, h=h_ref)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_precision_form_gradient_and_hessvec(blr, big_point, precision):
+    b = big_point
+    plan = blr.Plan(N3C, B3C, 10,
+                    precision=blr.BLR_MIXED if precision == "mixed" else blr.BLR_FP32)
+    plan.set_images(torch.from_numpy(b["I0f"]).cuda(), torch.from_numpy(b["I1f"]).cuda())
+    g = torch.zeros((3,) + B3C, dtype=torch.complex64, device="cuda")
+    e = torch.zeros(3, dtype=torch.float64, device="cuda")
+    plan.gradient(torch.from_numpy(b["vtf"]).cuda(), g, e)
+    h = torch.zeros_like(g)
+    plan.hessvec(torch.from_numpy(b["dvf"]).cuda(), h)
+    assert plan.status() == 0
+    tol = TOL[precision]
+    assert abs(float(e[0]) - b["energy"]) <= tol["field"] * b["energy"]
+    assert rel(g.cpu().numpy(), b["g"]) <= tol["grad"]
+    assert rel(h.cpu().numpy(), b["h"]) <= tol["grad"]
+
+
+@pytest.mark.slow
+def test_precision_form_registration_mixed_against_fp32(blr, big_point):
+    """10 Newton x <= 20 PCG from zero: the mixed path's final energy within
+    1e-3 of the plain FP32 path's, PCG totals within +-1 per Newton step."""
+    b = big_point
+    reps = {}
+    for precision in ("fp32", "mixed"):
+        plan = blr.Plan(N3C, B3C, 10,
+                        precision=blr.BLR_MIXED if precision == "mixed" else blr.BLR_FP32)
+        plan.set_images(torch.from_numpy(b["I0f"]).cuda(), torch.from_numpy(b["I1f"]).cuda())
+        vt = torch.zeros((3,) + B3C, dtype=torch.complex64, device="cuda")
+        reps[precision] = plan.newton(vt, 10, 20, 0.0)
+        plan.close()
+    f, m = reps["fp32"], reps["mixed"]
+    assert f.status == m.status == blr.BLR_OK, reps
+    assert f.newton_iters == m.newton_iters == 10, reps
+    assert m.energy < 0.5 * m.energy0
+    assert abs(m.energy0 - f.energy0) <= 5e-5 * f.energy0
+    assert abs(m.energy - f.energy) <= 1e-3 * f.energy
+    assert abs(m.pcg_iters - f.pcg_iters) <= f.newton_iters, reps
