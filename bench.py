@@ -66,7 +66,8 @@ ADJ_BYTES = lambda nt: ((36 + 44 + 48 * (nt - 2)) if nt > 1 else 32)
 # dram__bytes_read.sum + dram__bytes_write.sum of one interior adjoint-step
 # launch (k_adjoint_march<false, true>) at 128^3 from an ncu capture, valid only
 # for the sweep source it was captured from (SHA-256 of csrc/sweeps.cu).
-ADJ_TRAFFIC = {"sweeps_sha256": None, "bytes": None}
+ADJ_TRAFFIC = {"sweeps_sha256": "cb4726cd386c3c4ddca2f543af69fde54eb1a85562e887ca29347a31c5ed106e",
+               "bytes": 67481856 + 1691904}
 
 
 def adjoint_traffic():
