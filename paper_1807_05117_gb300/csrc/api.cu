@@ -52,6 +52,7 @@ size_t layout(blr_plan *P, char *base) {
     P->I0 = P->m;                        // m^0 = I0 lives in the first slot
     P->I1 = a.take<float>(V);
     P->d = a.take<float>(3 * V);
+    P->d4 = P->sweep_wide ? a.take<float4>(V) : nullptr;
     P->lam[0] = a.take<float>(V);
     P->lam[1] = a.take<float>(V);
     P->b = a.take<float>(3 * V);

@@ -65,11 +65,18 @@ struct blr_plan {
     int device;
     int chunk;          // x1 planes per state / incremental-state sweep block
     int chunk_adj;      // x1 planes per adjoint sweep block (both set by sweep_setup)
+    int bal_sweep;      // state / incremental-state sweeps: balanced grid of bal_sweep
+                        // blocks per SM, or 0 for the chunked grid
+    int bal_adj;        // the same for the adjoint sweep (both chosen by sweep_autotune)
+    int sms;            // multiprocessors of the plan's device
     Grid3 grid;
 
     float *I0, *I1;
     float *vt;          // current point (2*3*nb)
     float *d;           // 3V displacement -dt*iota(vt), clamped to [-1, 1)
+    float4 *d4;         // V (d0, d1, d2, 0) copy of d for the wide-copy sweeps, or nullptr
+    bool sweep_wide;    // adjoint and incremental state use the wide-copy kernels (N3 % 4 == 0)
+    int bal_inc;        // blocks per SM of the wide-copy incremental-state grid (sweep_autotune)
     float *m;           // state slots (see state_slot): checkpoints, segment, final
     int ck;             // checkpoint interval k (nt when every state is kept)
     int nseg;           // segments ceil(nt / k)
@@ -146,6 +153,7 @@ int sweep_chunk(const blr_plan *P, int kind);
 int sweep_blocks_per_sm(int kind);
 void sweep_set_chunk(blr_plan *P, int kind, int chunk);
 int sweep_autotune(blr_plan *P, cudaStream_t s);
+int sweep_pack_d4(blr_plan *P, cudaStream_t s);               // d4 from d (when P->d4)
 
 // reduce.cu
 int energy_finalize(blr_plan *P, const float *vt, double *energy_out, int nblocks, cudaStream_t s);

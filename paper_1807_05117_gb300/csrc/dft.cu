@@ -342,8 +342,11 @@ int dft_expand(blr_plan *P, const float *vt, float *out, int mode, cudaStream_t 
                                    P->N2, P->N3);
     BLR_CK_LAUNCH();
     // stage C
-    if (P->p.precision == BLR_MIXED)
-        return tc_axis1(P, 0, P->dft_big, out, mode == 0 ? 1.f : -P->dt, mode, s);
+    if (P->p.precision == BLR_MIXED) {
+        int rc = tc_axis1(P, 0, P->dft_big, out, mode == 0 ? 1.f : -P->dt, mode, s);
+        if (rc || mode == 0 || out != P->d) return rc;
+        return sweep_pack_d4(P, s);
+    }
     const long long ncol = (long long)P->N2 * P->N3;
     dim3 gc((unsigned)ceil_div_ll(ncol, 128), (unsigned)ceil_div_ll(P->N1, 64), 3u);
     if (mode == 0)
@@ -355,6 +358,7 @@ int dft_expand(blr_plan *P, const float *vt, float *out, int mode, cudaStream_t 
                                                  out, P->V, P->N1, 2 * P->B1, ncol, -P->dt,
                                                  P->dstatus);
     BLR_CK_LAUNCH();
+    if (mode == 1 && out == P->d) return sweep_pack_d4(P, s);
     return BLR_OK;
 }
 

@@ -28,8 +28,13 @@ constexpr int MHK = MK + 2, MHJ = MJ + 2, MHP = MHJ * MHK;   // haloed plane
 constexpr int MT = MK * MJ;       // threads per block
 static_assert(MHP <= 2 * MT, "two halo slots per thread");
 
+// Periodic index; the integer remainder is taken only for indices more than one
+// period out of range (tiny grids), so the usual case costs a compare or two.
 __device__ __forceinline__ int wrapi(int i, int N) {
-    int r = i % N;
+    if (i >= 0 && i < N) return i;
+    if (i < 0 && i >= -N) return i + N;
+    if (i >= N && i < 2 * N) return i - N;
+    const int r = i % N;
     return r < 0 ? r + N : r;
 }
 
@@ -84,12 +89,13 @@ __device__ __forceinline__ float hat(float d) {
 // Trilinear value (and optionally the gradient of the cell's trilinear
 // polynomial) from two haloed planes: P0 holds x1 = x + lo0, P1 holds x + lo0 + 1.
 // (hj, hk) is the voxel's halo position; a1/a2 select the cell in-plane.
-template <bool GRAD>
+// RS is the row stride of the planes (floats).
+template <bool GRAD, int RS = MHK>
 __device__ __forceinline__ float trilinear2(const float *P0, const float *P1, int hj, int hk,
                                             AxisW a0, AxisW a1, AxisW a2, float *G) {
-    const int b = (hj + a1.lo) * MHK + (hk + a2.lo);
-    const float c000 = P0[b], c001 = P0[b + 1], c010 = P0[b + MHK], c011 = P0[b + MHK + 1];
-    const float c100 = P1[b], c101 = P1[b + 1], c110 = P1[b + MHK], c111 = P1[b + MHK + 1];
+    const int b = (hj + a1.lo) * RS + (hk + a2.lo);
+    const float c000 = P0[b], c001 = P0[b + 1], c010 = P0[b + RS], c011 = P0[b + RS + 1];
+    const float c100 = P1[b], c101 = P1[b + 1], c110 = P1[b + RS], c111 = P1[b + RS + 1];
     const float l00 = fmaf(a2.wl, c000, a2.wh * c001), l01 = fmaf(a2.wl, c010, a2.wh * c011);
     const float l10 = fmaf(a2.wl, c100, a2.wh * c101), l11 = fmaf(a2.wl, c110, a2.wh * c111);
     const float m0 = fmaf(a1.wl, l00, a1.wh * l01), m1 = fmaf(a1.wl, l10, a1.wh * l11);
@@ -548,6 +554,390 @@ k_sweep_batch(const SweepPair *__restrict__ pairs, const long long *__restrict__
     }
 }
 
+// ---------------------------------------------------------------------------
+// Balanced grids: the ncol * N1 (column tile, x1 plane) units of one step are
+// split evenly over the launch's G blocks (a multiple of the SM count), so that
+// every SM carries the same number of planes, where a chunked grid leaves some
+// SMs with one block fewer.  With G >= ncol every column is cut into
+// floor(G / ncol) or that + 1 chunks of near-equal length and each block
+// marches one chunk (a block that crossed a column boundary would march two
+// segments, each with its own halo planes, and finish last); with fewer blocks
+// than columns block b marches units [b W / G, (b + 1) W / G) in column-major
+// order, one segment per column it touches.  The arithmetic of a voxel does not
+// depend on the split, so results are bit-identical to chunked grids.
+template <typename F>
+__device__ __forceinline__ void for_segments(int N1, int ntk, long long W, F &&tile) {
+    const long long ncol_ll = W / N1;
+    if ((long long)gridDim.x >= ncol_ll) {
+        // 32-bit arithmetic: ncol * N1 = W < 2^31 (V < 2^31 voxels, >= 512 per column)
+        const unsigned G = gridDim.x, ncol = (unsigned)ncol_ll, bid = blockIdx.x;
+        const unsigned base = G / ncol, extra = G - base * ncol;
+        unsigned col, ch, n;
+        if (bid < extra * (base + 1)) {
+            n = base + 1;
+            col = bid / n;
+            ch = bid - col * n;
+        } else {
+            const unsigned b2 = bid - extra * (base + 1);
+            n = base;
+            col = extra + b2 / n;
+            ch = b2 - (col - extra) * n;
+        }
+        // chunk ch of n: the first N1 % n chunks take one plane more
+        const unsigned q = (unsigned)N1 / n, rm = (unsigned)N1 - q * n;
+        const int i0 = (int)(ch * q + (ch < rm ? ch : rm));
+        const int len = (int)(q + (ch < rm ? 1u : 0u));
+        const unsigned jt = col / (unsigned)ntk;
+        if (len > 0) tile((int)(col - jt * (unsigned)ntk), (int)jt, i0, len);
+        return;
+    }
+    const long long G = gridDim.x, bid = blockIdx.x;
+    long long p = bid * W / G;
+    const long long p1 = (bid + 1) * W / G;
+    bool first = true;
+    while (p < p1) {
+        const long long col = p / N1;
+        const int i0 = (int)(p - col * N1);
+        const long long left = p1 - p;
+        const int len = (int)(left < (long long)(N1 - i0) ? left : (long long)(N1 - i0));
+        if (!first) {
+            // the previous segment's copies land and its readers finish before
+            // the rings are refilled
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
+            __syncthreads();
+        }
+        tile((int)(col % ntk), (int)(col / ntk), i0, len);
+        first = false;
+        p += len;
+    }
+}
+
+template <bool LAST>
+__global__ void __launch_bounds__(MT, 4)
+k_state_bal(const float *__restrict__ m_in, const float *__restrict__ d,
+            float *__restrict__ m_out, Grid3 g, const float *__restrict__ I1,
+            float *__restrict__ lam_out, float lam_scale, double *__restrict__ partials, int ntk,
+            long long W) {
+    for_segments(g.N1, ntk, W, [&](int kt, int jt, int i0, int len) {
+        state_tile<LAST>(m_in, d, m_out, g, len, I1, lam_out, lam_scale, partials, kt * MK,
+                         jt * MJ, i0);
+    });
+}
+
+template <bool FIRST, bool WRITE_LAM>
+__global__ void __launch_bounds__(MT, ADJ_BLOCKS)
+k_adjoint_bal(const float *__restrict__ lam_in, const float *__restrict__ m_n,
+              const float *__restrict__ d, float *__restrict__ lam_out, float *__restrict__ b,
+              float dt, Grid3 g, int ntk, long long W) {
+    for_segments(g.N1, ntk, W, [&](int kt, int jt, int i0, int len) {
+        adjoint_tile<FIRST, WRITE_LAM>(lam_in, m_n, d, lam_out, b, dt, g, len, kt * MK, jt * AJ,
+                                       i0);
+    });
+}
+
+template <bool FIRST, bool LAST>
+__global__ void __launch_bounds__(MT, 4)
+k_incstate_bal(const float *__restrict__ dm_in, const float *__restrict__ m_n,
+               const float *__restrict__ d, const float *__restrict__ dv,
+               float *__restrict__ dm_out, float dt, float lam_scale, Grid3 g, int ntk,
+               long long W) {
+    for_segments(g.N1, ntk, W, [&](int kt, int jt, int i0, int len) {
+        incstate_tile<FIRST, LAST>(dm_in, m_n, d, dv, dm_out, dt, lam_scale, g, len, kt * MK,
+                                   jt * MJ, i0);
+    });
+}
+
+// ---------------------------------------------------------------------------
+// Wide-copy forms of the adjoint and incremental-state steps (N3 % 4 == 0):
+// the arithmetic of adjoint_tile / incstate_tile, with the haloed planes
+// fetched by 16-byte cp.async copies instead of one 4-byte copy per element.
+// A shared-memory row holds x3 = k0 - 4 .. k0 + 35, so every copy of a scalar
+// field moves 4 voxels that start on a 16-byte boundary (the periodic wrap in
+// x3 then moves whole groups of 4, since N3 % 4 == 0), and the displacement is
+// read from its float4 copy d4 = (d0, d1, d2, 0), one voxel per copy.  The
+// in-plane source offsets of a thread's copies are fixed for a tile and kept in
+// registers, so a copy costs one address add.
+constexpr int BW = 40;                       // row: x3 = k0 - 4 .. k0 + 35
+constexpr int BHK = 4;                       // column of x3 = k0
+constexpr int BG = BW / 4;                   // 16-byte groups of a scalar row
+
+__device__ __forceinline__ void cp16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+
+// In-plane offset (elements) of row hr, window column c of a tile at (j0, k0).
+__device__ __forceinline__ int win_off(const Grid3 &g, int j0, int k0, int hr, int c) {
+    return wrapi(j0 + hr - 1, g.N2) * g.N3 + wrapi(k0 - 4 + c, g.N3);
+}
+
+// Adjoint: rings of (d, 0) float4 and lambda^{n+1} in 4 slots (planes s-1 .. s+2),
+// m^n in 6 slots (planes s-2 .. s+2).  Per plane: 720 float4 copies of d4 (3 per
+// thread), 180 of lambda (threads 0..179) and 180 of m (threads 76..255).
+constexpr int BROWS = AJ + 2;                // haloed rows
+constexpr int BPL = BROWS * BW;              // positions per plane
+constexpr int BQ = 4, BM = 6;                // ring slots
+constexpr int ADJW_SMEM = BQ * BPL * 16 + BQ * BPL * 4 + BM * BPL * 4;
+constexpr int AQC = (BPL + MT - 1) / MT;     // d4 copies per thread
+constexpr int ASC = BROWS * BG;              // scalar-field copies per plane (180)
+constexpr int AM0 = MT - ASC;                // first thread copying m
+static_assert(ASC <= MT && AM0 >= 0, "one scalar copy of each field per thread at most");
+
+struct AdjWRings {
+    float4 *Q;        // [BQ][BPL]
+    float *L;         // [BQ][BPL]
+    float *M;         // [BM][BPL]
+};
+
+__device__ __forceinline__ AdjWRings adjw_rings() {
+    extern __shared__ __align__(16) unsigned char blr_dyn_smem[];
+    AdjWRings R;
+    R.Q = reinterpret_cast<float4 *>(blr_dyn_smem);
+    R.L = reinterpret_cast<float *>(blr_dyn_smem + BQ * BPL * 16);
+    R.M = R.L + BQ * BPL;
+    return R;
+}
+
+template <bool FIRST, bool WRITE_LAM>
+__device__ __forceinline__ void
+adjoint_tile_w(const float *__restrict__ lam_in, const float *__restrict__ m_n,
+               const float4 *__restrict__ d4, float *__restrict__ lam_out, float *__restrict__ b,
+               float dt, const Grid3 g, int CH, int k0, int j0, int i0) {
+    const AdjWRings R = adjw_rings();
+    const int i_end = min(i0 + CH, g.N1);
+    const long long plane = (long long)g.N2 * g.N3;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int k = k0 + lane;
+    const int jb = j0 + ARJ * w;
+    const bool kin = k < g.N3;
+    const int hk = BHK + lane;
+    const long long V = g.V;
+    // this thread's copies: d4 positions tid + MT i; lambda group tid; m group tid - AM0
+    int offq[AQC];
+#pragma unroll
+    for (int i = 0; i < AQC; ++i) {
+        const int c = tid + MT * i;
+        offq[i] = c < BPL ? win_off(g, j0, k0, c / BW, c % BW) : 0;
+    }
+    const bool cl = tid < ASC, cm = tid >= AM0;
+    const int offl = cl ? win_off(g, j0, k0, tid / BG, 4 * (tid % BG)) : 0;
+    const int offm = cm ? win_off(g, j0, k0, (tid - AM0) / BG, 4 * ((tid - AM0) % BG)) : 0;
+    const uint32_t q0s = smem_u32(R.Q) + (uint32_t)tid * 16u;
+    const uint32_t l0s = smem_u32(R.L) + (uint32_t)tid * 16u;
+    const uint32_t m0s = smem_u32(R.M) + (uint32_t)(tid - AM0) * 16u;
+    auto issue = [&](int sp, int r) {   // plane sp into ring position r (one commit group)
+        if (sp <= i_end) {
+            const long long pb = (long long)wrap1(sp, g.N1) * plane;
+            const uint32_t qs = q0s + (uint32_t)(r & (BQ - 1)) * (BPL * 16);
+#pragma unroll
+            for (int i = 0; i < AQC; ++i)
+                if (tid + MT * i < BPL) cp16(qs + (uint32_t)(MT * i) * 16u, d4 + pb + offq[i]);
+            if (cl) cp16(l0s + (uint32_t)(r & (BQ - 1)) * (BPL * 4), lam_in + pb + offl);
+            if (cm) cp16(m0s + ((uint32_t)r % BM) * (BPL * 4), m_n + pb + offm);
+        }
+        cp_commit();
+    };
+    issue(i0 - 1, 0);
+    issue(i0, 1);
+    float2 accA, accB, accC;   // rows (jb, jb + 1) of output planes s - 1, s, s + 1
+    accA = accB = accC = make_float2(0.f, 0.f);
+    float bb[ARJ][3];
+#pragma unroll
+    for (int jj = 0; jj < ARJ; ++jj) bb[jj][0] = bb[jj][1] = bb[jj][2] = 0.f;
+    for (int s = i0 - 1; s <= i_end; ++s) {
+        const int r = s - i0 + 1;
+        cp_wait1();
+        __syncthreads();
+        issue(s + 2, r + 2);
+        if (kin) {
+            if (WRITE_LAM) {
+                const float4 *Q = R.Q + (r & (BQ - 1)) * BPL;
+                const float *L = R.L + (r & (BQ - 1)) * BPL;
+#pragma unroll
+                for (int sr = 0; sr < ARJ + 2; ++sr) {        // source halo row ARJ w + sr
+#pragma unroll
+                    for (int dk = -1; dk <= 1; ++dk) {
+                        const int pos = (ARJ * w + sr) * BW + hk + dk;
+                        const float4 q = Q[pos];
+                        const float wl = L[pos] * hat_e(-dk, q.z);
+                        const float xa = fmaxf(-q.x, 0.f), xb = 1.f - fabsf(q.x), xc = fmaxf(q.x, 0.f);
+                        // target rows jb (source row offset sr - 1) and jb + 1 (sr - 2)
+                        if (sr == 0) {
+                            const float wt = wl * hat_e(1, q.y);
+                            accA.x = fmaf(wt, xa, accA.x);
+                            accB.x = fmaf(wt, xb, accB.x);
+                            accC.x = fmaf(wt, xc, accC.x);
+                        } else if (sr == ARJ + 1) {
+                            const float wt = wl * hat_e(-1, q.y);
+                            accA.y = fmaf(wt, xa, accA.y);
+                            accB.y = fmaf(wt, xb, accB.y);
+                            accC.y = fmaf(wt, xc, accC.y);
+                        } else {
+                            const float2 wt = __fmul2_rn(make_float2(wl, wl),
+                                                         make_float2(hat_e(1 - sr, q.y),
+                                                                     hat_e(2 - sr, q.y)));
+                            accA = __ffma2_rn(wt, make_float2(xa, xa), accA);
+                            accB = __ffma2_rn(wt, make_float2(xb, xb), accB);
+                            accC = __ffma2_rn(wt, make_float2(xc, xc), accC);
+                        }
+                    }
+                }
+            }
+            const int o = s - 1;
+            if (o >= i0) {
+                const float4 *Qo = R.Q + ((r + 3) & (BQ - 1)) * BPL;   // plane s - 1
+                const float *Lo = R.L + ((r + 3) & (BQ - 1)) * BPL;
+                const float *Ma = R.M + ((uint32_t)(r + 4) % BM) * BPL;          // plane s - 2
+                const float *Mb = R.M + ((uint32_t)(r + 5) % BM) * BPL;          // plane s - 1
+                const float *Mc = R.M + ((uint32_t)r % BM) * BPL;                // plane s
+#pragma unroll
+                for (int jj = 0; jj < ARJ; ++jj) {
+                    const int j = jb + jj;
+                    if (j < g.N2) {
+                        const int hj = 1 + ARJ * w + jj;
+                        const float4 q0 = Qo[hj * BW + hk];
+                        const AxisW a0 = axis_weights(q0.x);
+                        float G[3];
+                        trilinear2<true, BW>(a0.lo < 0 ? Ma : Mb, a0.lo < 0 ? Mb : Mc, hj, hk, a0,
+                                             axis_weights(q0.y), axis_weights(q0.z), G);
+                        const float sl = dt * Lo[hj * BW + hk];
+                        const long long idx = (long long)o * plane + (long long)j * g.N3 + k;
+#pragma unroll
+                        for (int a = 0; a < 3; ++a)
+                            b[a * V + idx] = FIRST ? sl * G[a] : fmaf(sl, G[a], bb[jj][a]);
+                        if (WRITE_LAM) lam_out[idx] = jj == 0 ? accA.x : accA.y;
+                    }
+                }
+            }
+            if (!FIRST && s >= i0 && s < i_end) {
+#pragma unroll
+                for (int jj = 0; jj < ARJ; ++jj) {
+                    const int j = jb + jj;
+                    if (j < g.N2) {
+                        const long long nidx = (long long)s * plane + (long long)j * g.N3 + k;
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) bb[jj][a] = b[a * V + nidx];
+                    }
+                }
+            }
+        }
+        accA = accB;
+        accB = accC;
+        accC = make_float2(0.f, 0.f);
+    }
+}
+
+template <bool FIRST, bool WRITE_LAM>
+__global__ void __launch_bounds__(MT, ADJ_BLOCKS)
+k_adjoint_wide(const float *__restrict__ lam_in, const float *__restrict__ m_n,
+               const float4 *__restrict__ d4, float *__restrict__ lam_out, float *__restrict__ b,
+               float dt, Grid3 g, int ntk, long long W) {
+    for_segments(g.N1, ntk, W, [&](int kt, int jt, int i0, int len) {
+        adjoint_tile_w<FIRST, WRITE_LAM>(lam_in, m_n, d4, lam_out, b, dt, g, len, kt * MK, jt * AJ,
+                                         i0);
+    });
+}
+
+// Incremental state: m^n and dm^n rings of 6 slots (planes s-2 .. s+2); per plane
+// 100 copies of each field (m: threads 0..99, dm: threads 128..227).
+constexpr int IROWS = MJ + 2;                // haloed rows
+constexpr int IPL = IROWS * BW;              // positions per plane
+constexpr int IM = 6;                        // ring slots
+constexpr int ISC = IROWS * BG;              // copies per field and plane (100)
+constexpr int ID0 = 128;                     // first thread copying dm
+static_assert(ISC <= ID0 && ID0 + ISC <= MT, "one copy per thread");
+template <bool FIRST>
+constexpr int incw_smem() { return (FIRST ? 1 : 2) * IM * IPL * 4; }
+
+template <bool FIRST, bool LAST>
+__device__ __forceinline__ void
+incstate_tile_w(const float *__restrict__ dm_in, const float *__restrict__ m_n,
+                const float4 *__restrict__ d4, const float *__restrict__ dv,
+                float *__restrict__ dm_out, float dt, float lam_scale, const Grid3 g, int CH,
+                int k0, int j0, int i0) {
+    extern __shared__ __align__(16) unsigned char blr_dyn_smem[];
+    float *RM = reinterpret_cast<float *>(blr_dyn_smem);    // [IM][IPL] m^n
+    float *RD = RM + IM * IPL;                               // [IM][IPL] dm^n
+    const int i_end = min(i0 + CH, g.N1);
+    const long long plane = (long long)g.N2 * g.N3;
+    const int tid = threadIdx.x, tk = tid & 31, tj = tid >> 5;
+    const int k = k0 + tk, j = j0 + tj;
+    const bool active = k < g.N3 && j < g.N2;
+    const long long col = (long long)j * g.N3 + k;
+    const int hj = tj + 1, hk = BHK + tk;
+    const bool cmf = tid < ISC, cdf = !FIRST && tid >= ID0 && tid < ID0 + ISC;
+    const int cc = cmf ? tid : tid - ID0;
+    const int off = (cmf || cdf) ? win_off(g, j0, k0, cc / BG, 4 * (cc % BG)) : 0;
+    const uint32_t dst0 = smem_u32(cmf ? RM : RD) + (uint32_t)cc * 16u;
+    const float *src0 = cmf ? m_n : dm_in;
+    auto issue = [&](int sp, int r) {
+        if (sp <= i_end && (cmf || cdf))
+            cp16(dst0 + ((uint32_t)r % IM) * (IPL * 4),
+                 src0 + (long long)wrap1(sp, g.N1) * plane + off);
+        cp_commit();
+    };
+    issue(i0 - 1, 0);
+    issue(i0, 1);
+    float4 dd = make_float4(0.f, 0.f, 0.f, 0.f);   // d, dv of the output voxel (plane s - 1)
+    float vv[3] = {0.f, 0.f, 0.f};
+    for (int s = i0 - 1; s <= i_end; ++s) {
+        const int r = s - i0 + 1;
+        cp_wait1();
+        __syncthreads();
+        issue(s + 2, r + 2);
+        // the next output voxel's operands are loaded before this plane's work,
+        // which then hides their latency
+        float4 nd = dd;
+        float nv[3] = {vv[0], vv[1], vv[2]};
+        if (active && s >= i0 && s < i_end) {
+            const long long nidx = (long long)s * plane + col;
+            nd = __ldg(d4 + nidx);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) nv[a] = __ldg(dv + a * g.V + nidx);
+        }
+        const int o = s - 1;
+        if (active && o >= i0) {
+            const long long idx = (long long)o * plane + col;
+            const AxisW a0 = axis_weights(dd.x);
+            const AxisW a1 = axis_weights(dd.y);
+            const AxisW a2 = axis_weights(dd.z);
+            // cell planes x1 - 1, x1 (a0.lo < 0) or x1, x1 + 1: ring positions r + 4, r + 5, r
+            const uint32_t s0 = a0.lo < 0 ? (uint32_t)(r + 4) % IM : (uint32_t)(r + 5) % IM;
+            const uint32_t s1 = a0.lo < 0 ? (uint32_t)(r + 5) % IM : (uint32_t)r % IM;
+            float G[3];
+            trilinear2<true, BW>(RM + s0 * IPL, RM + s1 * IPL, hj, hk, a0, a1, a2, G);
+            float out = 0.f;
+            if (!FIRST)
+                out = trilinear2<false, BW>(RD + s0 * IPL, RD + s1 * IPL, hj, hk, a0, a1, a2,
+                                            nullptr);
+            const float gdv = fmaf(G[0], vv[0], fmaf(G[1], vv[1], G[2] * vv[2]));
+            out = fmaf(-dt, gdv, out);
+            dm_out[idx] = LAST ? lam_scale * out : out;
+        }
+        dd = nd;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) vv[a] = nv[a];
+    }
+}
+
+template <bool FIRST, bool LAST>
+__global__ void __launch_bounds__(MT, 4)
+k_incstate_wide(const float *__restrict__ dm_in, const float *__restrict__ m_n,
+                const float4 *__restrict__ d4, const float *__restrict__ dv,
+                float *__restrict__ dm_out, float dt, float lam_scale, Grid3 g, int ntk,
+                long long W) {
+    for_segments(g.N1, ntk, W, [&](int kt, int jt, int i0, int len) {
+        incstate_tile_w<FIRST, LAST>(dm_in, m_n, d4, dv, dm_out, dt, lam_scale, g, len, kt * MK,
+                                     jt * MJ, i0);
+    });
+}
+
+// d4 = (d0, d1, d2, 0) per voxel from the planar displacement.
+__global__ void k_pack_d4(const float *__restrict__ d, float4 *__restrict__ d4, long long V) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V;
+         i += (long long)gridDim.x * blockDim.x)
+        d4[i] = make_float4(__ldg(d + i), __ldg(d + V + i), __ldg(d + 2 * V + i), 0.f);
+}
+
 dim3 sweep_grid(const blr_plan *P) {
     return dim3((unsigned)ceil_div_ll(P->N3, MK), (unsigned)ceil_div_ll(P->N2, MJ),
                 (unsigned)ceil_div_ll(P->N1, P->chunk));
@@ -570,6 +960,18 @@ int adjoint_smem_attributes() {
     BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
     BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
     BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_adjoint_bal<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_adjoint_bal<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_adjoint_bal<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_adjoint_bal<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_adjoint_wide<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_adjoint_wide<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_adjoint_wide<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_adjoint_wide<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_incstate_wide<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, incw_smem<true>()));
+    BLR_CK(cudaFuncSetAttribute(k_incstate_wide<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, incw_smem<true>()));
+    BLR_CK(cudaFuncSetAttribute(k_incstate_wide<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, incw_smem<false>()));
+    BLR_CK(cudaFuncSetAttribute(k_incstate_wide<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, incw_smem<false>()));
     done = true;
     return BLR_OK;
 }
@@ -593,9 +995,13 @@ int sweep_setup(blr_plan *P) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device) != cudaSuccess || sms < 1)
         sms = 148;
+    P->sms = sms;
     const long long k_tiles = ceil_div_ll(P->N3, MK);
     P->chunk = one_wave_chunk(P->N1, k_tiles * ceil_div_ll(P->N2, MJ), 4LL * sms);
     P->chunk_adj = one_wave_chunk(P->N1, k_tiles * ceil_div_ll(P->N2, AJ), (long long)ADJ_BLOCKS * sms);
+    P->bal_sweep = 0;
+    P->bal_adj = 0;
+    P->sweep_wide = (P->N3 % 4) == 0;
     return adjoint_smem_attributes();
 }
 
@@ -607,21 +1013,105 @@ long long sweep_blocks(const blr_plan *P) {
 
 namespace {
 
+// Geometry of a balanced grid with `bps` blocks per SM over column tiles of
+// MK x rows voxels.
+struct BalGeom {
+    unsigned G;
+    int ntk;
+    long long W;
+};
+
+BalGeom bal_geom(const blr_plan *P, int bps, int rows) {
+    BalGeom b;
+    b.ntk = (int)ceil_div_ll(P->N3, MK);
+    b.W = (long long)b.ntk * ceil_div_ll(P->N2, rows) * P->N1;
+    long long G = (long long)bps * P->sms;
+    if (G > b.W) G = b.W;
+    b.G = (unsigned)G;
+    return b;
+}
+
+// One state step m_out = S m_in; LAST also writes lambda^nt and the image-term partials.
+template <bool LAST>
+void launch_state(const blr_plan *P, const float *m_in, float *m_out, const float *I1, float *lam_out,
+                  float lam_scale, double *partials, cudaStream_t s) {
+    if (P->bal_sweep) {
+        const BalGeom b = bal_geom(P, P->bal_sweep, MJ);
+        k_state_bal<LAST><<<b.G, MT, 0, s>>>(m_in, P->d, m_out, P->grid, I1, lam_out, lam_scale,
+                                              partials, b.ntk, b.W);
+    } else {
+        k_state_march<LAST><<<sweep_grid(P), MT, 0, s>>>(m_in, P->d, m_out, P->grid, P->chunk, I1,
+                                                          lam_out, lam_scale, partials);
+    }
+}
+
+template <bool FIRST, bool WRITE_LAM>
+void launch_adjoint_t(const blr_plan *P, const float *lin, const float *mn, float *lout, float *b,
+                      cudaStream_t s) {
+    if (P->sweep_wide) {
+        const BalGeom g = bal_geom(P, P->bal_adj ? P->bal_adj : ADJ_BLOCKS, AJ);
+        k_adjoint_wide<FIRST, WRITE_LAM><<<g.G, MT, ADJW_SMEM, s>>>(
+            lin, mn, P->d4, lout, b, P->dt, P->grid, g.ntk, g.W);
+    } else if (P->bal_adj) {
+        const BalGeom g = bal_geom(P, P->bal_adj, AJ);
+        k_adjoint_bal<FIRST, WRITE_LAM><<<g.G, MT, ADJ_SMEM, s>>>(lin, mn, P->d, lout, b, P->dt,
+                                                                  P->grid, g.ntk, g.W);
+    } else {
+        k_adjoint_march<FIRST, WRITE_LAM><<<adjoint_grid(P), MT, ADJ_SMEM, s>>>(
+            lin, mn, P->d, lout, b, P->dt, P->grid, P->chunk_adj);
+    }
+}
+
+// One adjoint step: lambda^n = S^T lambda^{n+1} (when wlam) and b (+)= dt lambda grad m^n.
+void launch_adjoint(const blr_plan *P, bool first, bool wlam, const float *lin, const float *mn,
+                    float *lout, float *b, cudaStream_t s) {
+    if (first && wlam) launch_adjoint_t<true, true>(P, lin, mn, lout, b, s);
+    else if (first) launch_adjoint_t<true, false>(P, lin, mn, lout, b, s);
+    else if (wlam) launch_adjoint_t<false, true>(P, lin, mn, lout, b, s);
+    else launch_adjoint_t<false, false>(P, lin, mn, lout, b, s);
+}
+
+template <bool FIRST, bool LAST>
+void launch_incstate_t(const blr_plan *P, const float *din, const float *mn, float *dout,
+                       float lam_scale, cudaStream_t s, bool wide) {
+    if (wide && P->sweep_wide) {
+        const BalGeom b = bal_geom(P, P->bal_inc ? P->bal_inc : 4, MJ);
+        k_incstate_wide<FIRST, LAST><<<b.G, MT, incw_smem<FIRST>(), s>>>(
+            din, mn, P->d4, P->dv, dout, P->dt, lam_scale, P->grid, b.ntk, b.W);
+    } else if (P->bal_sweep) {
+        const BalGeom b = bal_geom(P, P->bal_sweep, MJ);
+        k_incstate_bal<FIRST, LAST><<<b.G, MT, 0, s>>>(din, mn, P->d, P->dv, dout, P->dt, lam_scale,
+                                                        P->grid, b.ntk, b.W);
+    } else {
+        k_incstate_march<FIRST, LAST><<<sweep_grid(P), MT, 0, s>>>(
+            din, mn, P->d, P->dv, dout, P->dt, lam_scale, P->grid, P->chunk);
+    }
+}
+
+// One incremental-state step dm^{n+1} = S dm^n - dt grad m^n . dv (wide: whether
+// the wide-copy kernel may be used).
+void launch_incstate(const blr_plan *P, bool first, bool last, const float *din, const float *mn,
+                     float *dout, float lam_scale, cudaStream_t s, bool wide = true) {
+    if (first && last) launch_incstate_t<true, true>(P, din, mn, dout, lam_scale, s, wide);
+    else if (first) launch_incstate_t<true, false>(P, din, mn, dout, lam_scale, s, wide);
+    else if (last) launch_incstate_t<false, true>(P, din, mn, dout, lam_scale, s, wide);
+    else launch_incstate_t<false, false>(P, din, mn, dout, lam_scale, s, wide);
+}
+
 // m^{n+1} from m^n in the slots given by state_slot (not the last step).
-int state_step(blr_plan *P, const dim3 &grid, int n, cudaStream_t s) {
-    k_state_march<false><<<grid, MT, 0, s>>>(state_slot(P, n), P->d, state_slot(P, n + 1), P->grid,
-                                             P->chunk, nullptr, nullptr, 0.f, nullptr);
+int state_step(blr_plan *P, int n, cudaStream_t s) {
+    launch_state<false>(P, state_slot(P, n), state_slot(P, n + 1), nullptr, nullptr, 0.f, nullptr, s);
     BLR_CK_LAUNCH();
     return BLR_OK;
 }
 
 // Make the segment buffer hold the interior states of segment j, recomputing
 // them from checkpoint C_j when it holds another segment.
-int ensure_segment(blr_plan *P, const dim3 &grid, int j, cudaStream_t s) {
+int ensure_segment(blr_plan *P, int j, cudaStream_t s) {
     if (P->seg_valid == j) return BLR_OK;
     const int n0 = j * P->ck, n1 = n0 + P->ck < P->p.nt ? n0 + P->ck : P->p.nt;
     for (int n = n0; n < n1 - 1; ++n) {
-        int rc = state_step(P, grid, n, s);
+        int rc = state_step(P, n, s);
         if (rc) return rc;
     }
     P->seg_valid = j;
@@ -631,15 +1121,14 @@ int ensure_segment(blr_plan *P, const dim3 &grid, int j, cudaStream_t s) {
 }  // namespace
 
 int sweep_state(blr_plan *P, cudaStream_t s) {
-    const dim3 grid = sweep_grid(P);
     const int nt = P->p.nt;
     const float lam_scale = (float)(-2.0 / (P->p.sigma * P->p.sigma));
     for (int n = 0; n < nt - 1; ++n) {
-        int rc = state_step(P, grid, n, s);
+        int rc = state_step(P, n, s);
         if (rc) return rc;
     }
-    k_state_march<true><<<grid, MT, 0, s>>>(state_slot(P, nt - 1), P->d, state_slot(P, nt), P->grid,
-                                            P->chunk, P->I1, P->lam[0], lam_scale, P->partials);
+    launch_state<true>(P, state_slot(P, nt - 1), state_slot(P, nt), P->I1, P->lam[0], lam_scale,
+                       P->partials, s);
     BLR_CK_LAUNCH();
     P->seg_valid = P->nseg - 1;   // the forward sweep leaves the last segment's states
     return BLR_OK;
@@ -649,28 +1138,18 @@ int sweep_state(blr_plan *P, cudaStream_t s) {
 // lambda0 != nullptr, lambda^0 into lambda0.  Segments are visited backwards,
 // each recomputed from its checkpoint when needed.
 int sweep_adjoint(blr_plan *P, float *b, float *lambda0, cudaStream_t s) {
-    const dim3 grid = sweep_grid(P), agrid = adjoint_grid(P);
     const int nt = P->p.nt;
-    const int CH = P->chunk_adj;
     int cur = 0;
     for (int j = P->nseg - 1; j >= 0; --j) {
-        int rc = ensure_segment(P, grid, j, s);
+        int rc = ensure_segment(P, j, s);
         if (rc) return rc;
         const int n0 = j * P->ck, n1 = n0 + P->ck < nt ? n0 + P->ck : nt;
         for (int n = n1 - 1; n >= n0; --n) {
             const float *lin = P->lam[cur];
             float *lout = (n == 0 && lambda0) ? lambda0 : P->lam[1 - cur];
-            const float *mn = state_slot(P, n);
             const bool first = (n == nt - 1);
             const bool wlam = (n > 0) || (lambda0 != nullptr);
-            if (first && wlam)
-                k_adjoint_march<true, true><<<agrid, MT, ADJ_SMEM, s>>>(lin, mn, P->d, lout, b, P->dt, P->grid, CH);
-            else if (first)
-                k_adjoint_march<true, false><<<agrid, MT, ADJ_SMEM, s>>>(lin, mn, P->d, lout, b, P->dt, P->grid, CH);
-            else if (wlam)
-                k_adjoint_march<false, true><<<agrid, MT, ADJ_SMEM, s>>>(lin, mn, P->d, lout, b, P->dt, P->grid, CH);
-            else
-                k_adjoint_march<false, false><<<agrid, MT, ADJ_SMEM, s>>>(lin, mn, P->d, lout, b, P->dt, P->grid, CH);
+            launch_adjoint(P, first, wlam, lin, state_slot(P, n), lout, b, s);
             BLR_CK_LAUNCH();
             cur = 1 - cur;
         }
@@ -680,27 +1159,17 @@ int sweep_adjoint(blr_plan *P, float *b, float *lambda0, cudaStream_t s) {
 
 // Incremental state from dv = iota(dv~) (in P->dv); leaves dlambda^nt in lam[0].
 int sweep_incremental(blr_plan *P, cudaStream_t s) {
-    const dim3 grid = sweep_grid(P);
     const int nt = P->p.nt;
     const float lam_scale = (float)(-2.0 / (P->p.sigma * P->p.sigma));
     int cur = 0;
     for (int j = 0; j < P->nseg; ++j) {
-        int rc = ensure_segment(P, grid, j, s);
+        int rc = ensure_segment(P, j, s);
         if (rc) return rc;
         const int n0 = j * P->ck, n1 = n0 + P->ck < nt ? n0 + P->ck : nt;
         for (int n = n0; n < n1; ++n) {
             const float *din = P->dm[cur];
             float *dout = (n == nt - 1) ? P->lam[0] : P->dm[1 - cur];
-            const float *mn = state_slot(P, n);
-            const bool first = n == 0, last = n == nt - 1;
-            if (first && last)
-                k_incstate_march<true, true><<<grid, MT, 0, s>>>(din, mn, P->d, P->dv, dout, P->dt, lam_scale, P->grid, P->chunk);
-            else if (first)
-                k_incstate_march<true, false><<<grid, MT, 0, s>>>(din, mn, P->d, P->dv, dout, P->dt, lam_scale, P->grid, P->chunk);
-            else if (last)
-                k_incstate_march<false, true><<<grid, MT, 0, s>>>(din, mn, P->d, P->dv, dout, P->dt, lam_scale, P->grid, P->chunk);
-            else
-                k_incstate_march<false, false><<<grid, MT, 0, s>>>(din, mn, P->d, P->dv, dout, P->dt, lam_scale, P->grid, P->chunk);
+            launch_incstate(P, n == 0, n == nt - 1, din, state_slot(P, n), dout, lam_scale, s);
             BLR_CK_LAUNCH();
             cur = 1 - cur;
         }
@@ -752,15 +1221,13 @@ void sweep_tiles(const blr_plan *P, int kind, int *tk, int *tj, int *ti) {
 namespace {
 
 // One interior step of a sweep kind on the plan's own buffers (timing only;
-// the state kind shares the incremental-state chunk and is not timed).
+// the state kind shares the incremental-state shape and is not timed).
+// Kind 3 is the wide-copy incremental-state kernel, kind 2 the march kernel.
 int time_step(blr_plan *P, int kind, cudaStream_t s) {
-    if (kind == 1) {
-        k_adjoint_march<false, true><<<adjoint_grid(P), MT, ADJ_SMEM, s>>>(
-            P->lam[0], P->m, P->d, P->lam[1], P->b, P->dt, P->grid, P->chunk_adj);
-    } else {
-        k_incstate_march<false, false><<<sweep_grid(P), MT, 0, s>>>(
-            P->dm[0], P->m, P->d, P->dv, P->dm[1], P->dt, 1.f, P->grid, P->chunk);
-    }
+    if (kind == 1)
+        launch_adjoint(P, false, true, P->lam[0], P->m, P->lam[1], P->b, s);
+    else
+        launch_incstate(P, false, false, P->dm[0], P->m, P->dm[1], 1.f, s, kind == 3);
     BLR_CK_LAUNCH();
     return BLR_OK;
 }
@@ -768,41 +1235,87 @@ int time_step(blr_plan *P, int kind, cudaStream_t s) {
 }  // namespace
 
 // Autotuner: for the adjoint and the incremental-state kernels, time an
-// interior step on the plan's own buffers for each candidate chunk (the
-// one-wave chunk of sweep_setup and 4, 8, 16, 32 planes) and keep the fastest.
+// interior step on the plan's own buffers for each candidate shape and keep the
+// fastest: chunked grids (the one-wave chunk of sweep_setup and 4, 8, 16, 32
+// planes) and balanced grids of 1 .. (blocks resident per SM) blocks per SM.
+// The best chunked chunk is kept either way (batched launches use it).
 int sweep_autotune(blr_plan *P, cudaStream_t s) {
     cudaEvent_t e0, e1;
     BLR_CK(cudaEventCreate(&e0));
     BLR_CK(cudaEventCreate(&e1));
     int rc = BLR_OK;
+    auto time_shape = [&](int kind, float *out) {
+        float tot = 0.f;
+        for (int rep = 0; rep < 3 && !rc; ++rep) {
+            if (cudaEventRecord(e0, s) != cudaSuccess) rc = BLR_ECUDA;
+            if (!rc) rc = time_step(P, kind, s);
+            if (!rc && (cudaEventRecord(e1, s) != cudaSuccess ||
+                        cudaEventSynchronize(e1) != cudaSuccess))
+                rc = BLR_ECUDA;
+            float ms = 0.f;
+            if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = BLR_ECUDA;
+            if (rep > 0) tot += ms;   // the first run warms up
+        }
+        *out = tot;
+    };
     for (int kind = 1; kind <= 2 && !rc; ++kind) {
+        int &bal = kind == 1 ? P->bal_adj : P->bal_sweep;
+        bal = 0;
+        // the wide-copy adjoint runs on balanced grids only
+        const bool bal_only = kind == 1 && P->sweep_wide;
         const int heur = sweep_chunk(P, kind);
         const int cands[5] = {heur, 4, 8, 16, 32};
         float best = 1e30f;
         int best_ch = heur;
-        for (int c = 0; c < 5 && !rc; ++c) {
+        for (int c = 0; c < 5 && !rc && !bal_only; ++c) {
             const int ch = cands[c] < P->N1 ? cands[c] : P->N1;
             if (c > 0 && ch == heur) continue;
             sweep_set_chunk(P, kind, ch);
-            float tot = 0.f;
-            for (int rep = 0; rep < 3 && !rc; ++rep) {
-                if (cudaEventRecord(e0, s) != cudaSuccess) rc = BLR_ECUDA;
-                if (!rc) rc = time_step(P, kind, s);
-                if (!rc && (cudaEventRecord(e1, s) != cudaSuccess ||
-                            cudaEventSynchronize(e1) != cudaSuccess))
-                    rc = BLR_ECUDA;
-                float ms = 0.f;
-                if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = BLR_ECUDA;
-                if (rep > 0) tot += ms;   // the first run warms up
-            }
-            if (tot < best) {
-                best = tot;
+            float t = 0.f;
+            time_shape(kind, &t);
+            if (t < best) {
+                best = t;
                 best_ch = ch;
             }
         }
         sweep_set_chunk(P, kind, best_ch);
+        int best_bal = bal_only ? sweep_blocks_per_sm(kind) : 0;
+        for (int bps = 1; bps <= sweep_blocks_per_sm(kind) && !rc; ++bps) {
+            bal = bps;
+            float t = 0.f;
+            time_shape(kind, &t);
+            if (t < best) {
+                best = t;
+                best_bal = bps;
+            }
+        }
+        bal = best_bal;
+    }
+    // blocks per SM of the wide-copy incremental-state grid
+    P->bal_inc = 0;
+    if (P->sweep_wide && !rc) {
+        float best = 1e30f;
+        int best_bps = 4;
+        for (int bps = 1; bps <= 4 && !rc; ++bps) {
+            P->bal_inc = bps;
+            float t = 0.f;
+            time_shape(3, &t);
+            if (t < best) {
+                best = t;
+                best_bps = bps;
+            }
+        }
+        P->bal_inc = best_bps;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return rc;
+}
+
+int sweep_pack_d4(blr_plan *P, cudaStream_t s) {
+    if (!P->d4) return BLR_OK;
+    const long long blocks = ceil_div_ll(P->V, 256);
+    k_pack_d4<<<(unsigned)(blocks < 4LL * P->sms ? blocks : 4LL * P->sms), 256, 0, s>>>(P->d, P->d4, P->V);
+    BLR_CK_LAUNCH();
+    return BLR_OK;
 }
