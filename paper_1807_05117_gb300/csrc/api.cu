@@ -70,8 +70,15 @@ size_t layout(blr_plan *P, char *base) {
     if (P->p.precision == BLR_MIXED) {
         P->tc_tab_expand = a.take<uint8_t>(tc_table_bytes(P, 0));
         P->tc_tab_project = a.take<uint8_t>(tc_table_bytes(P, 1));
+        if (tc_axis2_supported(P)) {
+            P->tc_tab2_expand = a.take<uint8_t>(tc_table_bytes(P, 2));
+            P->tc_tab2_project = a.take<uint8_t>(tc_table_bytes(P, 3));
+        } else {
+            P->tc_tab2_expand = P->tc_tab2_project = nullptr;
+        }
     } else {
         P->tc_tab_expand = P->tc_tab_project = nullptr;
+        P->tc_tab2_expand = P->tc_tab2_project = nullptr;
     }
     float **vecs[] = {&P->vt, &P->g, &P->r, &P->pv, &P->q, &P->x, &P->trial, &P->step, &P->vtmp};
     for (float **v : vecs) *v = a.take<float>(P->nfloat);
@@ -197,11 +204,11 @@ int blr_plan_create(const blr_params *p, blr_plan_t *out) {
         delete P;
         return BLR_ECUDA;
     }
+    sweep_setup(P);   // SM count and sweep shapes (the tensor-core tile shapes use the SM count)
     if (p->precision == BLR_MIXED && !tc_supported(P)) {
         delete P;
         return BLR_EINVAL;
     }
-    sweep_setup(P);
     long long nsweep = sweep_blocks(P);
     long long nred = reduce_partials_needed();
     P->npart = (int)(nsweep > nred ? nsweep : nred);

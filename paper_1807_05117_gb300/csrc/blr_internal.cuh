@@ -96,6 +96,8 @@ struct blr_plan {
     float *dft_small;   // 3*B1*B2*N3*2 floats
     uint8_t *tc_tab_expand;    // BLR_MIXED: swizzled BF16 hi/lo table tiles (dft_tc.cu)
     uint8_t *tc_tab_project;
+    uint8_t *tc_tab2_expand;   // BLR_MIXED axis-2 stages, or nullptr (SIMT axis 2)
+    uint8_t *tc_tab2_project;
 
     // Krylov / Newton vectors (nfloat each)
     float *g, *r, *pv, *q, *x, *trial, *step, *vtmp;
@@ -133,11 +135,14 @@ int dft_expand(blr_plan *P, const float *vt, float *out, int mode, cudaStream_t 
 int dft_project(blr_plan *P, const float *f, float *ft, const float *vadd, cudaStream_t s);
 
 // dft_tc.cu (BLR_MIXED)
-size_t tc_table_bytes(const blr_plan *P, int project);
-bool tc_supported(const blr_plan *P);
+// stage kinds: 0 / 1 axis-1 expand / project, 2 / 3 axis-2 expand / project
+size_t tc_table_bytes(const blr_plan *P, int kind);
+bool tc_supported(const blr_plan *P);          // axis-1 stages (required by BLR_MIXED)
+bool tc_axis2_supported(const blr_plan *P);    // axis-2 stages as well
 int tc_init_tables(blr_plan *P, cudaStream_t s);
 int tc_axis1(blr_plan *P, int project, const float *X, float *D, float scale, int mode,
              cudaStream_t s);
+int tc_axis2(blr_plan *P, int project, const float *X, float *D, cudaStream_t s);
 
 // sweeps.cu
 int sweep_setup(blr_plan *P);

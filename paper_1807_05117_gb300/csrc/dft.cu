@@ -337,10 +337,15 @@ int dft_expand(blr_plan *P, const float *vt, float *out, int mode, cudaStream_t 
         vt, P->T3c, P->T3s, P->dft_small, rows, P->B2, P->B3, P->N3);
     BLR_CK_LAUNCH();
     // stage B
-    dim3 gb((unsigned)ceil_div_ll(P->N3, 32), (unsigned)ceil_div_ll(P->N2, 32), 3u * P->B1);
-    k_axis2<+1><<<gb, 256, 0, s>>>(P->dft_small, P->T2c, P->T2s, P->dft_big, P->B2, P->N2,
-                                   P->N2, P->N3);
-    BLR_CK_LAUNCH();
+    if (P->tc_tab2_expand) {
+        int rc = tc_axis2(P, 0, P->dft_small, P->dft_big, s);
+        if (rc) return rc;
+    } else {
+        dim3 gb((unsigned)ceil_div_ll(P->N3, 32), (unsigned)ceil_div_ll(P->N2, 32), 3u * P->B1);
+        k_axis2<+1><<<gb, 256, 0, s>>>(P->dft_small, P->T2c, P->T2s, P->dft_big, P->B2, P->N2,
+                                       P->N2, P->N3);
+        BLR_CK_LAUNCH();
+    }
     // stage C
     if (P->p.precision == BLR_MIXED) {
         int rc = tc_axis1(P, 0, P->dft_big, out, mode == 0 ? 1.f : -P->dt, mode, s);
@@ -376,10 +381,15 @@ int dft_project(blr_plan *P, const float *f, float *ft, const float *vadd, cudaS
         BLR_CK_LAUNCH();
     }
     // stage B'
-    dim3 gb((unsigned)ceil_div_ll(P->N3, 32), (unsigned)ceil_div_ll(P->B2, 32), 3u * P->B1);
-    k_axis2<-1><<<gb, 256, 0, s>>>(P->dft_big, P->T2c, P->T2s, P->dft_small, P->N2, P->B2,
-                                   P->N2, P->N3);
-    BLR_CK_LAUNCH();
+    if (P->tc_tab2_project) {
+        int rc = tc_axis2(P, 1, P->dft_big, P->dft_small, s);
+        if (rc) return rc;
+    } else {
+        dim3 gb((unsigned)ceil_div_ll(P->N3, 32), (unsigned)ceil_div_ll(P->B2, 32), 3u * P->B1);
+        k_axis2<-1><<<gb, 256, 0, s>>>(P->dft_big, P->T2c, P->T2s, P->dft_small, P->N2, P->B2,
+                                       P->N2, P->N3);
+        BLR_CK_LAUNCH();
+    }
     // stage A'
     const int rows = 3 * P->B1 * P->B2;
     k_project_axis3<<<(unsigned)ceil_div_ll(rows, PA_ROWS), 256, 0, s>>>(

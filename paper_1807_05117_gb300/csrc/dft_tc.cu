@@ -13,6 +13,8 @@
 // shared memory by the CTA itself, so nothing extra goes through HBM.
 // One elected thread issues the MMAs; completion is signalled through an mbarrier
 // whose wait is bounded (timeout -> BLR_FLAG_TIMEOUT, TMEM freed, no output).
+#include <cuda.h>
+#include <string.h>
 #include <cuda_bf16.h>
 
 #include "blr_internal.cuh"
@@ -101,6 +103,7 @@ struct TcArgs {
     int col_tiles, tiles;    // column tiles per batch, tiles over the 3 batches
     int nstage;              // FP32 staging buffers (2: next tile prefetched)
     int bulk;                // rows may be fetched with cp.async.bulk (16-byte aligned)
+    int tma;                 // tiles are fetched by one 2-D TMA copy (tensor map of X)
     int tmem_cols;           // power of two >= mtiles * ntile
     float scale;
     int mode;                // 0 store scale*acc; 1 displacement (clamp + flags)
@@ -119,6 +122,16 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
         "l"(src), "r"(bytes), "r"(bar)
         : "memory");
 }
+// One 2-D tile of the tensor map (x = column, y = row) into shared memory.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
 // Bounded wait for the phase of the given parity; false after ~2 s.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     uint32_t done = 0;
@@ -139,7 +152,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 // t = blockIdx.x, blockIdx.x + gridDim.x, ...; with two staging buffers the next
 // tile's rows stream in (cp.async.bulk) while the current one is converted,
 // multiplied and written.
-__global__ void __launch_bounds__(TC_THREADS, 1) k_tc_axis1(TcArgs p) {
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_tc_axis1(TcArgs p, const __grid_constant__ CUtensorMap xmap) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     uint8_t *base = smem_raw + (((raw + 1023) & ~1023u) - raw);
@@ -152,8 +166,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_axis1(TcArgs p) {
     float *stage0 = reinterpret_cast<float *>(sA + all_tab);
     uint8_t *sBh = reinterpret_cast<uint8_t *>(stage0) + p.nstage * stage_bytes;
     uint8_t *sBl = sBh + b_bytes;
-    float *sE = reinterpret_cast<float *>(sBl + b_bytes);             // 8 warps x 32 x 32 floats
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sE + TC_THREADS / 32 * 1024);   // load[0], load[1], mma
+    // epilogue transpose buffer, 8 warps x 32 x 32 floats: the staging buffer
+    // itself when there is only one and it is large enough (tc_smem_bytes)
+    const size_t epi_bytes = (size_t)TC_THREADS / 32 * 1024 * 4;
+    const bool alias = p.nstage == 1 && stage_bytes >= epi_bytes;
+    float *sE = alias ? stage0 : reinterpret_cast<float *>(sBl + b_bytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sBl + b_bytes + (alias ? 0 : epi_bytes));   // load[0], load[1], mma
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 3);
     __shared__ int s_fail;
     const uint32_t bar_load0 = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[2]);
@@ -190,10 +208,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_axis1(TcArgs p) {
         const float *src;
         tile_cols(t, &col0, &w, &src);
         const uint32_t bar = bar_load0 + 8u * sb;
+        const uint32_t dst0 = smem_u32(stage0) + (uint32_t)(sb * stage_bytes);
+        if (p.tma) {
+            // the whole [K][ntile] box (columns past the end read as zeros)
+            if (lane == 0) {
+                mbar_expect_arrive(bar, (uint32_t)stage_bytes + extra_bytes);
+                tma_load_2d(dst0, &xmap, (int)col0, (t / p.col_tiles) * p.K, bar);
+            }
+            __syncwarp();
+            return;
+        }
         const uint32_t row_bytes = (uint32_t)w * 4u;
         if (lane == 0) mbar_expect_arrive(bar, row_bytes * (uint32_t)p.K + extra_bytes);
         __syncwarp();
-        const uint32_t dst0 = smem_u32(stage0) + (uint32_t)(sb * stage_bytes);
         for (int k = lane; k < p.K; k += 32)
             bulk_g2s(dst0 + (uint32_t)k * p.ntile * 4u, src + (long long)k * p.ncols, row_bytes, bar);
     };
@@ -304,13 +331,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_axis1(TcArgs p) {
         // 32 x 32 blocks transposed through an XOR-swizzled buffer so that each
         // store instruction writes 128 contiguous bytes of one output row
         float *D = p.D + (t / p.col_tiles) * p.dstride;
+        // 32-column chunks alternate between the two warp halves, so no load
+        // reaches past the tile's own TMEM columns (ntile may be 32)
         const int lg = warp & 3, half = warp >> 2;
-        const int cols_half = p.ntile >> 1;
         float *T = sE + warp * 1024;
         int flags = 0;
         for (int mt = 0; mt < p.mtiles; ++mt) {
             const int row0 = mt * TC_M + lg * 32;
-            for (int c = half * cols_half; c < (half + 1) * cols_half; c += 32) {
+            for (int c = half * 32; c < p.ntile; c += 64) {
                 uint32_t rv[32];
                 tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(mt * p.ntile + c), rv);
 #pragma unroll
@@ -334,6 +362,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_axis1(TcArgs p) {
             }
         }
         if (flags) atomicOr(p.status, flags);
+        // the epilogue's generic writes may share the staging buffer with the
+        // next tile's asynchronous load
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
     }
@@ -351,11 +382,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_axis1(TcArgs p) {
                      "r"(p.tmem_cols));
 }
 
-// Table tiles, FP64 phases split into BF16 hi/lo.  transpose == 0: row = x1,
-// k = kappa (expand); transpose == 1: row = kappa, k = x1 (project).
-// W(kappa, x1) = cos(2 pi k_j x1 / N1) for kappa = 2j, -sin(...) for 2j+1.
-__global__ void k_tc_table(uint8_t *tab, int mtiles, int M, int K, int Kpad, int N1, int B1,
-                           int project) {
+// Table tiles, FP64 phases split into BF16 hi/lo, for stage kind
+//   0 axis-1 expand : row x1, k kappa = 2 j + re/im       W = cos | -sin (2 pi k_j x1 / N)
+//   1 axis-1 project: row kappa, k x1                       (the same values)
+//   2 axis-2 expand : row (ro, x2), k (ri, j)   [[C, -S], [S, C]], C, S = cos, sin(2 pi k_j x2 / N)
+//   3 axis-2 project: row (ro, j), k (ri, x2)   [[C,  S], [-S, C]]
+// with k_j = j - B/2; the real and imaginary blocks are the real form of the
+// complex sums of Eq. 33 along one axis (3: its transpose, conjugated).
+__global__ void k_tc_table(uint8_t *tab, int mtiles, int M, int K, int Kpad, int N, int B,
+                           int kind) {
     const long long total = (long long)mtiles * TC_M * Kpad;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
@@ -365,13 +400,32 @@ __global__ void k_tc_table(uint8_t *tab, int mtiles, int M, int K, int Kpad, int
         const int row = mt * TC_M + rr;
         double w = 0.0;
         if (row < M && k < K) {
-            const int kappa = project ? row : k, x1 = project ? k : row;
-            const int j = kappa >> 1;
-            long long ph = ((long long)(j - B1 / 2) * x1) % N1;
-            if (ph < 0) ph += N1;
-            double s, c;
-            sincospi(2.0 * (double)ph / (double)N1, &s, &c);
-            w = (kappa & 1) ? -s : c;
+            int j, x, ro, ri;
+            if (kind <= 1) {
+                const int kappa = kind ? row : k;
+                x = kind ? k : row;
+                j = kappa >> 1;
+                ri = kappa & 1;
+                ro = 0;
+            } else if (kind == 2) {
+                ro = row / N;
+                x = row - ro * N;
+                ri = k / B;
+                j = k - ri * B;
+            } else {
+                ro = row / B;
+                j = row - ro * B;
+                ri = k / N;
+                x = k - ri * N;
+            }
+            long long ph = ((long long)(j - B / 2) * x) % N;
+            if (ph < 0) ph += N;
+            double sn, cs;
+            sincospi(2.0 * (double)ph / (double)N, &sn, &cs);
+            if (kind <= 1) w = ri ? -sn : cs;
+            else if (ro == ri) w = cs;
+            else if (kind == 2) w = ro ? sn : -sn;
+            else w = ro ? -sn : sn;
         }
         const __nv_bfloat16 h = __double2bfloat16(w);
         const __nv_bfloat16 l = __double2bfloat16(w - (double)__bfloat162float(h));
@@ -383,100 +437,198 @@ __global__ void k_tc_table(uint8_t *tab, int mtiles, int M, int K, int Kpad, int
     }
 }
 
+// cuTensorMapEncodeTiled from the driver (through the runtime, so the library
+// needs no link against libcuda); nullptr when no driver is present.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(ptr);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
 int pow2_at_least(int v) {
     int p = 32;
     while (p < v) p <<= 1;
     return p;
 }
 
-constexpr size_t TC_SMEM_MAX = 225 * 1024;
+// Largest dynamic shared memory of a block (227 KB); tc_smem_bytes includes the
+// 1024-byte alignment slack.
+constexpr size_t TC_SMEM_MAX = 227 * 1024;
 
+// With one staging buffer the epilogue's transpose buffer aliases it (the
+// staging data are consumed before the MMAs, and the next tile's load is issued
+// only after the epilogue), so it costs nothing extra when it fits there.
 size_t tc_smem_bytes(int mtiles, int K, int Kpad, int nt, int nstage) {
-    return 1024 + 2 * (size_t)TC_M * Kpad * 2 * mtiles + (size_t)nstage * K * nt * 4 +
-           2 * (size_t)nt * Kpad * 2 + (size_t)TC_THREADS / 32 * 1024 * 4 + 3 * 8 + 16;
+    const size_t stage = (size_t)nstage * K * nt * 4, epi = (size_t)TC_THREADS / 32 * 1024 * 4;
+    const bool alias = nstage == 1 && stage >= epi;
+    return 1024 + 2 * (size_t)TC_M * Kpad * 2 * mtiles + stage + 2 * (size_t)nt * Kpad * 2 +
+           (alias ? 0 : epi) + 3 * 8 + 16;
 }
 
-// Largest column tile (256 .. 32) whose shared memory and TMEM fit, preferring
-// two staging buffers (prefetch) over a larger tile.
-bool tc_shape(int mtiles, int K, int Kpad, int *ntile, int *nstage, size_t *smem) {
-    for (int ns = 2; ns >= 1; --ns)
-        for (int nt = 256; nt >= 32; nt >>= 1) {
-            if (mtiles * nt > 512) continue;
-            const size_t sb = tc_smem_bytes(mtiles, K, Kpad, nt, ns);
-            if (sb <= TC_SMEM_MAX) {
-                *ntile = nt;
-                *nstage = ns;
-                *smem = sb;
-                return true;
+// Column tile (256 .. 32) and staging depth: the largest tile whose shared
+// memory and TMEM fit and that still gives every SM a tile (when any does),
+// preferring two staging buffers (prefetch) over a larger tile.
+bool tc_shape(int mtiles, int K, int Kpad, long long ncols, int nbatch, int sms, int *ntile,
+              int *nstage, size_t *smem) {
+    for (int pass = 0; pass < 2; ++pass)
+        for (int ns = 2; ns >= 1; --ns)
+            for (int nt = 256; nt >= 32; nt >>= 1) {
+                if (mtiles * nt > 512) continue;
+                if (pass == 0 && ceil_div_ll(ncols, nt) * nbatch < sms) continue;
+                const size_t sb = tc_smem_bytes(mtiles, K, Kpad, nt, ns);
+                if (sb <= TC_SMEM_MAX) {
+                    *ntile = nt;
+                    *nstage = ns;
+                    *smem = sb;
+                    return true;
+                }
             }
-        }
     return false;
+}
+
+struct TcGeom {
+    int mtiles, M, K, Kpad, nbatch, N, B;
+    long long ncols;
+};
+
+// Geometry of tensor-core stage `kind` (see k_tc_table) of a plan.
+TcGeom tc_geometry(const blr_plan *P, int kind) {
+    TcGeom g;
+    if (kind <= 1) {
+        g.M = kind ? 2 * P->B1 : P->N1;
+        g.K = kind ? P->N1 : 2 * P->B1;
+        g.ncols = (long long)P->N2 * P->N3;
+        g.nbatch = 3;
+        g.N = P->N1;
+        g.B = P->B1;
+    } else {
+        g.M = kind == 3 ? 2 * P->B2 : 2 * P->N2;
+        g.K = kind == 3 ? 2 * P->N2 : 2 * P->B2;
+        g.ncols = P->N3;
+        g.nbatch = 3 * P->B1;
+        g.N = P->N2;
+        g.B = P->B2;
+    }
+    g.mtiles = (g.M + TC_M - 1) / TC_M;
+    g.Kpad = (g.K + 63) / 64 * 64;
+    return g;
+}
+
+int plan_sms(const blr_plan *P) { return P->sms > 0 ? P->sms : 148; }
+
+bool tc_kind_ok(const blr_plan *P, int kind) {
+    const TcGeom g = tc_geometry(P, kind);
+    int nt, ns;
+    size_t sm;
+    return tc_shape(g.mtiles, g.K, g.Kpad, g.ncols, g.nbatch, plan_sms(P), &nt, &ns, &sm);
 }
 
 }  // namespace
 
-// Geometry of the two tensor-core contractions of a plan.
-void tc_geometry(const blr_plan *P, int project, int *mtiles, int *M, int *K, int *Kpad) {
-    *M = project ? 2 * P->B1 : P->N1;
-    *K = project ? P->N1 : 2 * P->B1;
-    *mtiles = (*M + TC_M - 1) / TC_M;
-    *Kpad = (*K + 63) / 64 * 64;
+size_t tc_table_bytes(const blr_plan *P, int kind) {
+    const TcGeom g = tc_geometry(P, kind);
+    return (size_t)g.mtiles * 2 * TC_M * g.Kpad * 2;
 }
 
-size_t tc_table_bytes(const blr_plan *P, int project) {
-    int mt, M, K, Kp;
-    tc_geometry(P, project, &mt, &M, &K, &Kp);
-    return (size_t)mt * 2 * TC_M * Kp * 2;
-}
+// Whether the mixed path supports this plan's shapes (the axis-1 stages).
+bool tc_supported(const blr_plan *P) { return tc_kind_ok(P, 0) && tc_kind_ok(P, 1); }
 
-// Whether the mixed path supports this plan's shapes.
-bool tc_supported(const blr_plan *P) {
-    for (int pr = 0; pr < 2; ++pr) {
-        int mt, M, K, Kp, nt, ns;
-        size_t sm;
-        tc_geometry(P, pr, &mt, &M, &K, &Kp);
-        if (!tc_shape(mt, K, Kp, &nt, &ns, &sm)) return false;
-    }
-    return true;
+// Whether the axis-2 stages also run on tensor cores: their whole table must fit
+// in shared memory and the field tiles must be TMA-addressable (N3 % 4 == 0).
+bool tc_axis2_supported(const blr_plan *P) {
+    return P->N3 % 4 == 0 && 2 * P->N2 <= 256 && tc_kind_ok(P, 2) && tc_kind_ok(P, 3);
 }
 
 int tc_init_tables(blr_plan *P, cudaStream_t s) {
-    for (int pr = 0; pr < 2; ++pr) {
-        int mt, M, K, Kp;
-        tc_geometry(P, pr, &mt, &M, &K, &Kp);
-        k_tc_table<<<256, 256, 0, s>>>(pr ? P->tc_tab_project : P->tc_tab_expand, mt, M, K, Kp,
-                                        P->N1, P->B1, pr);
+    uint8_t *tabs[4] = {P->tc_tab_expand, P->tc_tab_project, P->tc_tab2_expand, P->tc_tab2_project};
+    for (int kind = 0; kind < 4; ++kind) {
+        if (!tabs[kind]) continue;
+        const TcGeom g = tc_geometry(P, kind);
+        k_tc_table<<<256, 256, 0, s>>>(tabs[kind], g.mtiles, g.M, g.K, g.Kpad, g.N, g.B, kind);
         BLR_CK_LAUNCH();
     }
     return BLR_OK;
 }
 
-// D[c] = W (x) X[c] on tensor cores; see TcArgs.
-int tc_axis1(blr_plan *P, int project, const float *X, float *D, float scale, int mode,
-             cudaStream_t s) {
+namespace {
+
+// D[b] = W (x) X[b] for every batch b of stage `kind` on tensor cores; see TcArgs.
+int tc_run(blr_plan *P, int kind, const float *X, float *D, float scale, int mode, cudaStream_t s) {
+    const TcGeom g = tc_geometry(P, kind);
     TcArgs a;
-    tc_geometry(P, project, &a.mtiles, &a.M, &a.K, &a.Kpad);
+    a.mtiles = g.mtiles;
+    a.M = g.M;
+    a.K = g.K;
+    a.Kpad = g.Kpad;
     size_t smem = 0;
-    if (!tc_shape(a.mtiles, a.K, a.Kpad, &a.ntile, &a.nstage, &smem)) return BLR_EINVAL;
-    a.tab = project ? P->tc_tab_project : P->tc_tab_expand;
-    a.ncols = (long long)P->N2 * P->N3;
+    const int sms = plan_sms(P);
+    if (!tc_shape(a.mtiles, a.K, a.Kpad, g.ncols, g.nbatch, sms, &a.ntile, &a.nstage, &smem))
+        return BLR_EINVAL;
+    uint8_t *tabs[4] = {P->tc_tab_expand, P->tc_tab_project, P->tc_tab2_expand, P->tc_tab2_project};
+    a.tab = tabs[kind];
+    if (!a.tab) return BLR_EINVAL;
+    a.ncols = g.ncols;
     a.X = X;
     a.xstride = (long long)a.K * a.ncols;
     a.D = D;
     a.dstride = (long long)a.M * a.ncols;
     a.col_tiles = (int)ceil_div_ll(a.ncols, a.ntile);
-    a.tiles = 3 * a.col_tiles;
+    a.tiles = g.nbatch * a.col_tiles;
     // bulk row copies need 16-byte aligned rows and sizes
     a.bulk = (a.ncols % 4 == 0) && ((uintptr_t)X % 16 == 0);
+    // one TMA box per tile: X as a 2-D tensor [nbatch K][ncols] (row stride a
+    // 16-byte multiple), box [K][ntile] with K, ntile <= 256 and the box no wider
+    // than the tensor
+    CUtensorMap xmap;
+    memset(&xmap, 0, sizeof(xmap));
+    a.tma = 0;
+    if (a.bulk && a.K <= 256 && a.ntile <= a.ncols) {
+        EncodeTiledFn enc = encode_tiled();
+        if (enc) {
+            const cuuint64_t dims[2] = {(cuuint64_t)a.ncols, (cuuint64_t)g.nbatch * a.K};
+            const cuuint64_t strides[1] = {(cuuint64_t)a.ncols * 4};
+            const cuuint32_t box[2] = {(cuuint32_t)a.ntile, (cuuint32_t)a.K};
+            const cuuint32_t estr[2] = {1, 1};
+            if (enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(X), dims, strides,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+                a.tma = 1;
+        }
+    }
     a.tmem_cols = pow2_at_least(a.mtiles * a.ntile);
     a.scale = scale;
     a.mode = mode;
     a.status = P->dstatus;
-    int sms = 0;
-    BLR_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device));
     BLR_CK(cudaFuncSetAttribute(k_tc_axis1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = a.tiles < sms ? a.tiles : sms;
-    k_tc_axis1<<<grid, TC_THREADS, smem, s>>>(a);
+    k_tc_axis1<<<grid, TC_THREADS, smem, s>>>(a, xmap);
     BLR_CK_LAUNCH();
     return BLR_OK;
+}
+
+}  // namespace
+
+int tc_axis1(blr_plan *P, int project, const float *X, float *D, float scale, int mode,
+             cudaStream_t s) {
+    return tc_run(P, project ? 1 : 0, X, D, scale, mode, s);
+}
+
+int tc_axis2(blr_plan *P, int project, const float *X, float *D, cudaStream_t s) {
+    return tc_run(P, project ? 3 : 2, X, D, 1.f, 0, s);
 }
