@@ -41,11 +41,15 @@ __device__ __forceinline__ bool last_block(unsigned int *ticket) {
     return is_last;
 }
 
-// Sum `count` partial slots (stride `stride`, offset `slot`) in block order.
-__device__ __forceinline__ double ordered_sum(const double *part, int count, int stride, int slot) {
+// Sum of `count` partial slots (stride `stride`, offset `slot`) by the whole
+// block, in a fixed tree order (thread i takes slots i, i + RT, ... in order,
+// then the block sum), so the result does not depend on scheduling.  Every
+// thread calls it; the result is valid in thread 0.
+__device__ __forceinline__ double ordered_sum(const double *part, int count, int stride, int slot,
+                                              double *red) {
     double t = 0.0;
-    for (int i = 0; i < count; ++i) t += part[i * stride + slot];
-    return t;
+    for (int i = threadIdx.x; i < count; i += RT) t += part[i * stride + slot];
+    return block_sum<RT>(t, red);
 }
 
 // Energy of Eq. 35: every block sums a strided share of the per-block image-term
@@ -71,10 +75,10 @@ k_energy(const double *__restrict__ partials, int np, const float *__restrict__ 
     sr = block_sum<RT>(sr, red);
     if (threadIdx.x == 0) part2[2 * blockIdx.x + 1] = sr;
     if (!last_block(ticket)) return;
+    const double sdt = ordered_sum(part2, gridDim.x, 2, 0, red);
+    const double srt = ordered_sum(part2, gridDim.x, 2, 1, red);
     if (threadIdx.x == 0) {
         *ticket = 0;
-        const double sdt = ordered_sum(part2, gridDim.x, 2, 0);
-        const double srt = ordered_sum(part2, gridDim.x, 2, 1);
         const double edata = sdt * inv_sigma2, ereg = 0.5 * srt, e = ereg + edata;
         sc[SC_E] = e;
         sc[SC_EREG] = ereg;
@@ -103,8 +107,9 @@ k_dot(const float *__restrict__ a, const float *__restrict__ b, const float *__r
     acc = block_sum<RT>(acc, red);
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
     if (last_block(ticket)) {
+        const double t = ordered_sum(part, gridDim.x, 1, 0, red);
         if (threadIdx.x == 0) {
-            *out = ordered_sum(part, gridDim.x, 1, 0);
+            *out = t;
             *ticket = 0;
         }
     }
@@ -126,10 +131,16 @@ k_maxabs(const float *__restrict__ a, long long n, double *__restrict__ part,
         part[blockIdx.x] = (double)t;
     }
     if (last_block(ticket)) {
+        double t = 0.0;
+        for (unsigned i = threadIdx.x; i < gridDim.x; i += RT) t = fmax(t, part[i]);
+        for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_down_sync(0xffffffffu, t, o));
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (float)t;
+        __syncthreads();
         if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (unsigned i = 0; i < gridDim.x; ++i) t = fmax(t, part[i]);
-            *out = t;
+            float m2 = 0.f;
+            for (int w = 0; w < RT / 32; ++w) m2 = fmaxf(m2, red[w]);
+            *out = (double)m2;
             *ticket = 0;
         }
     }
@@ -156,9 +167,11 @@ k_pcg_init(const float *__restrict__ rhs, float *__restrict__ x, float *__restri
     rr = block_sum<RT>(rr, red);
     if (threadIdx.x == 0) part[2 * blockIdx.x + 1] = rr;
     if (last_block(ticket)) {
+        const double trz = ordered_sum(part, gridDim.x, 2, 0, red);
+        const double trr = ordered_sum(part, gridDim.x, 2, 1, red);
         if (threadIdx.x == 0) {
-            sc[SC_RZ] = ordered_sum(part, gridDim.x, 2, 0);
-            sc[SC_RR] = sc[SC_RR0] = ordered_sum(part, gridDim.x, 2, 1);
+            sc[SC_RZ] = trz;
+            sc[SC_RR] = sc[SC_RR0] = trr;
             *ticket = 0;
         }
     }
@@ -189,12 +202,13 @@ k_pcg_update(float *__restrict__ x, float *__restrict__ r, const float *__restri
     rr = block_sum<RT>(rr, red);
     if (threadIdx.x == 0) part[2 * blockIdx.x + 1] = rr;
     if (last_block(ticket)) {
+        const double rz_new = ordered_sum(part, gridDim.x, 2, 0, red);
+        const double rr_new = ordered_sum(part, gridDim.x, 2, 1, red);
         if (threadIdx.x == 0) {
-            const double rz_new = ordered_sum(part, gridDim.x, 2, 0);
             sc[SC_BETA] = rz_new / sc[SC_RZ];
             sc[SC_ALPHA] = alpha_d;
             sc[SC_RZ] = rz_new;
-            sc[SC_RR] = ordered_sum(part, gridDim.x, 2, 1);
+            sc[SC_RR] = rr_new;
             *ticket = 0;
         }
     }

@@ -837,14 +837,14 @@ k_adjoint_wide(const float *__restrict__ lam_in, const float *__restrict__ m_n,
     });
 }
 
-// Incremental state: m^n and dm^n rings of 6 slots (planes s-2 .. s+2); per plane
-// 100 copies of each field (m: threads 0..99, dm: threads 128..227).
-constexpr int IROWS = MJ + 2;                // haloed rows
+// Incremental state: a block covers 32 (x3) x AJ (x2) voxels, each thread two
+// consecutive x2 rows of one column (the adjoint's tiling).  m^n and dm^n rings
+// of 6 slots (planes s-2 .. s+2); per plane 180 copies of each field (m:
+// threads 0..179, dm: threads 76..255).
+constexpr int IROWS = AJ + 2;                // haloed rows
 constexpr int IPL = IROWS * BW;              // positions per plane
 constexpr int IM = 6;                        // ring slots
-constexpr int ISC = IROWS * BG;              // copies per field and plane (100)
-constexpr int ID0 = 128;                     // first thread copying dm
-static_assert(ISC <= ID0 && ID0 + ISC <= MT, "one copy per thread");
+constexpr int INC_BLOCKS = 3;                // resident blocks per SM (registers)
 template <bool FIRST>
 constexpr int incw_smem() { return (FIRST ? 1 : 2) * IM * IPL * 4; }
 
@@ -859,75 +859,100 @@ incstate_tile_w(const float *__restrict__ dm_in, const float *__restrict__ m_n,
     float *RD = RM + IM * IPL;                               // [IM][IPL] dm^n
     const int i_end = min(i0 + CH, g.N1);
     const long long plane = (long long)g.N2 * g.N3;
-    const int tid = threadIdx.x, tk = tid & 31, tj = tid >> 5;
-    const int k = k0 + tk, j = j0 + tj;
-    const bool active = k < g.N3 && j < g.N2;
-    const long long col = (long long)j * g.N3 + k;
-    const int hj = tj + 1, hk = BHK + tk;
-    const bool cmf = tid < ISC, cdf = !FIRST && tid >= ID0 && tid < ID0 + ISC;
-    const int cc = cmf ? tid : tid - ID0;
-    const int off = (cmf || cdf) ? win_off(g, j0, k0, cc / BG, 4 * (cc % BG)) : 0;
-    const uint32_t dst0 = smem_u32(cmf ? RM : RD) + (uint32_t)cc * 16u;
-    const float *src0 = cmf ? m_n : dm_in;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int k = k0 + lane, jb = j0 + ARJ * w;
+    const bool kin = k < g.N3;
+    const int hk = BHK + lane;
+    const bool cmf = tid < ASC, cdf = !FIRST && tid >= AM0;
+    const int offm = cmf ? win_off(g, j0, k0, tid / BG, 4 * (tid % BG)) : 0;
+    const int offd = cdf ? win_off(g, j0, k0, (tid - AM0) / BG, 4 * ((tid - AM0) % BG)) : 0;
+    const uint32_t m0s = smem_u32(RM) + (uint32_t)tid * 16u;
+    const uint32_t d0s = smem_u32(RD) + (uint32_t)(tid - AM0) * 16u;
     auto issue = [&](int sp, int r) {
-        if (sp <= i_end && (cmf || cdf))
-            cp16(dst0 + ((uint32_t)r % IM) * (IPL * 4),
-                 src0 + (long long)wrap1(sp, g.N1) * plane + off);
+        if (sp <= i_end) {
+            const long long pb = (long long)wrap1(sp, g.N1) * plane;
+            const uint32_t slot = ((uint32_t)r % IM) * (IPL * 4);
+            if (cmf) cp16(m0s + slot, m_n + pb + offm);
+            if (cdf) cp16(d0s + slot, dm_in + pb + offd);
+        }
         cp_commit();
     };
     issue(i0 - 1, 0);
     issue(i0, 1);
-    float4 dd = make_float4(0.f, 0.f, 0.f, 0.f);   // d, dv of the output voxel (plane s - 1)
-    float vv[3] = {0.f, 0.f, 0.f};
+    float4 dd[ARJ];        // d of the output voxels (plane s - 1)
+    float vv[ARJ][3];      // dv of the output voxels
+#pragma unroll
+    for (int jj = 0; jj < ARJ; ++jj) {
+        dd[jj] = make_float4(0.f, 0.f, 0.f, 0.f);
+        vv[jj][0] = vv[jj][1] = vv[jj][2] = 0.f;
+    }
     for (int s = i0 - 1; s <= i_end; ++s) {
         const int r = s - i0 + 1;
         cp_wait1();
         __syncthreads();
         issue(s + 2, r + 2);
-        // the next output voxel's operands are loaded before this plane's work,
+        // the next output voxels' operands are loaded before this plane's work,
         // which then hides their latency
-        float4 nd = dd;
-        float nv[3] = {vv[0], vv[1], vv[2]};
-        if (active && s >= i0 && s < i_end) {
-            const long long nidx = (long long)s * plane + col;
-            nd = __ldg(d4 + nidx);
+        float4 nd[ARJ];
+        float nv[ARJ][3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) nv[a] = __ldg(dv + a * g.V + nidx);
+        for (int jj = 0; jj < ARJ; ++jj) {
+            nd[jj] = dd[jj];
+            nv[jj][0] = vv[jj][0];
+            nv[jj][1] = vv[jj][1];
+            nv[jj][2] = vv[jj][2];
+            if (kin && jb + jj < g.N2 && s >= i0 && s < i_end) {
+                const long long nidx = (long long)s * plane + (long long)(jb + jj) * g.N3 + k;
+                nd[jj] = __ldg(d4 + nidx);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) nv[jj][a] = __ldg(dv + a * g.V + nidx);
+            }
         }
         const int o = s - 1;
-        if (active && o >= i0) {
-            const long long idx = (long long)o * plane + col;
-            const AxisW a0 = axis_weights(dd.x);
-            const AxisW a1 = axis_weights(dd.y);
-            const AxisW a2 = axis_weights(dd.z);
-            // cell planes x1 - 1, x1 (a0.lo < 0) or x1, x1 + 1: ring positions r + 4, r + 5, r
-            const uint32_t s0 = a0.lo < 0 ? (uint32_t)(r + 4) % IM : (uint32_t)(r + 5) % IM;
-            const uint32_t s1 = a0.lo < 0 ? (uint32_t)(r + 5) % IM : (uint32_t)r % IM;
-            float G[3];
-            trilinear2<true, BW>(RM + s0 * IPL, RM + s1 * IPL, hj, hk, a0, a1, a2, G);
-            float out = 0.f;
-            if (!FIRST)
-                out = trilinear2<false, BW>(RD + s0 * IPL, RD + s1 * IPL, hj, hk, a0, a1, a2,
-                                            nullptr);
-            const float gdv = fmaf(G[0], vv[0], fmaf(G[1], vv[1], G[2] * vv[2]));
-            out = fmaf(-dt, gdv, out);
-            dm_out[idx] = LAST ? lam_scale * out : out;
-        }
-        dd = nd;
+        if (kin && o >= i0) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) vv[a] = nv[a];
+            for (int jj = 0; jj < ARJ; ++jj) {
+                const int j = jb + jj;
+                if (j < g.N2) {
+                    const long long idx = (long long)o * plane + (long long)j * g.N3 + k;
+                    const int hj = 1 + ARJ * w + jj;
+                    const AxisW a0 = axis_weights(dd[jj].x);
+                    const AxisW a1 = axis_weights(dd[jj].y);
+                    const AxisW a2 = axis_weights(dd[jj].z);
+                    // cell planes x1 - 1, x1 (a0.lo < 0) or x1, x1 + 1: ring positions r + 4, r + 5, r
+                    const uint32_t s0 = a0.lo < 0 ? (uint32_t)(r + 4) % IM : (uint32_t)(r + 5) % IM;
+                    const uint32_t s1 = a0.lo < 0 ? (uint32_t)(r + 5) % IM : (uint32_t)r % IM;
+                    float G[3];
+                    trilinear2<true, BW>(RM + s0 * IPL, RM + s1 * IPL, hj, hk, a0, a1, a2, G);
+                    float out = 0.f;
+                    if (!FIRST)
+                        out = trilinear2<false, BW>(RD + s0 * IPL, RD + s1 * IPL, hj, hk, a0, a1,
+                                                    a2, nullptr);
+                    const float gdv = fmaf(G[0], vv[jj][0], fmaf(G[1], vv[jj][1], G[2] * vv[jj][2]));
+                    out = fmaf(-dt, gdv, out);
+                    dm_out[idx] = LAST ? lam_scale * out : out;
+                }
+            }
+        }
+#pragma unroll
+        for (int jj = 0; jj < ARJ; ++jj) {
+            dd[jj] = nd[jj];
+            vv[jj][0] = nv[jj][0];
+            vv[jj][1] = nv[jj][1];
+            vv[jj][2] = nv[jj][2];
+        }
     }
 }
 
 template <bool FIRST, bool LAST>
-__global__ void __launch_bounds__(MT, 4)
+__global__ void __launch_bounds__(MT, INC_BLOCKS)
 k_incstate_wide(const float *__restrict__ dm_in, const float *__restrict__ m_n,
                 const float4 *__restrict__ d4, const float *__restrict__ dv,
                 float *__restrict__ dm_out, float dt, float lam_scale, Grid3 g, int ntk,
                 long long W) {
     for_segments(g.N1, ntk, W, [&](int kt, int jt, int i0, int len) {
         incstate_tile_w<FIRST, LAST>(dm_in, m_n, d4, dv, dm_out, dt, lam_scale, g, len, kt * MK,
-                                     jt * MJ, i0);
+                                     jt * AJ, i0);
     });
 }
 
@@ -1075,7 +1100,7 @@ template <bool FIRST, bool LAST>
 void launch_incstate_t(const blr_plan *P, const float *din, const float *mn, float *dout,
                        float lam_scale, cudaStream_t s, bool wide) {
     if (wide && P->sweep_wide) {
-        const BalGeom b = bal_geom(P, P->bal_inc ? P->bal_inc : 4, MJ);
+        const BalGeom b = bal_geom(P, P->bal_inc ? P->bal_inc : INC_BLOCKS, AJ);
         k_incstate_wide<FIRST, LAST><<<b.G, MT, incw_smem<FIRST>(), s>>>(
             din, mn, P->d4, P->dv, dout, P->dt, lam_scale, P->grid, b.ntk, b.W);
     } else if (P->bal_sweep) {
@@ -1295,8 +1320,8 @@ int sweep_autotune(blr_plan *P, cudaStream_t s) {
     P->bal_inc = 0;
     if (P->sweep_wide && !rc) {
         float best = 1e30f;
-        int best_bps = 4;
-        for (int bps = 1; bps <= 4 && !rc; ++bps) {
+        int best_bps = INC_BLOCKS;
+        for (int bps = 1; bps <= INC_BLOCKS && !rc; ++bps) {
             P->bal_inc = bps;
             float t = 0.f;
             time_shape(3, &t);
