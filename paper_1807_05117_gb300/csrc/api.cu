@@ -55,6 +55,7 @@ size_t layout(blr_plan *P, char *base) {
     P->d4 = P->sweep_wide ? a.take<float4>(V) : nullptr;
     P->lam[0] = a.take<float>(V);
     P->lam[1] = a.take<float>(V);
+    P->Gm = P->use_gm ? a.take<float>((size_t)3 * P->p.nt * V) : nullptr;
     P->b = a.take<float>(3 * V);
     P->dv = a.take<float>(3 * V);
     P->dm[0] = a.take<float>(V);
@@ -178,7 +179,11 @@ int check_plan(blr_plan_t P) { return P ? BLR_OK : BLR_EINVAL; }
 
 extern "C" {
 
-int blr_plan_create(const blr_params *p, blr_plan_t *out) {
+int blr_plan_create(const blr_params *p, blr_plan_t *out) { return plan_create(p, true, out); }
+
+}  // extern "C"
+
+int plan_create(const blr_params *p, bool grad_cache, blr_plan **out) {
     if (!out) return BLR_EINVAL;
     *out = nullptr;
     int rc = validate(p);
@@ -209,6 +214,7 @@ int blr_plan_create(const blr_params *p, blr_plan_t *out) {
         delete P;
         return BLR_EINVAL;
     }
+    P->use_gm = grad_cache && P->sweep_wide && P->ck == p->nt;
     long long nsweep = sweep_blocks(P);
     long long nred = reduce_partials_needed();
     P->npart = (int)(nsweep > nred ? nsweep : nred);
@@ -237,6 +243,8 @@ int blr_plan_create(const blr_params *p, blr_plan_t *out) {
     *out = P;
     return BLR_OK;
 }
+
+extern "C" {
 
 int blr_plan_destroy(blr_plan_t P) {
     if (!P) return BLR_OK;

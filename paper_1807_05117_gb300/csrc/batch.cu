@@ -355,7 +355,7 @@ int blr_batch_create(const blr_params *params, int npairs, blr_batch_t *out) {
     if (cudaGetDevice(&B->device) != cudaSuccess) rc = BLR_ECUDA;
     for (int p = 0; p < npairs && !rc; ++p) {
         blr_plan_t P = nullptr;
-        rc = blr_plan_create(&params[p], &P);
+        rc = plan_create(&params[p], false, &P);
         if (!rc) B->plans.push_back(P);
     }
     int sms = 0;

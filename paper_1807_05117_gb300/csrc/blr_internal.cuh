@@ -76,6 +76,7 @@ struct blr_plan {
     float *d;           // 3V displacement -dt*iota(vt), clamped to [-1, 1)
     float4 *d4;         // V (d0, d1, d2, 0) copy of d for the wide-copy sweeps, or nullptr
     bool sweep_wide;    // adjoint and incremental state use the wide-copy kernels (N3 % 4 == 0)
+    bool use_gm;        // Gm is kept (see Gm)
     int bal_inc;        // blocks per SM of the wide-copy incremental-state grid (sweep_autotune)
     float *m;           // state slots (see state_slot): checkpoints, segment, final
     int ck;             // checkpoint interval k (nt when every state is kept)
@@ -83,6 +84,9 @@ struct blr_plan {
     int seg_valid;      // segment whose interior states the segment buffer holds
     bool have_state;
     float *lam[2];      // V each (adjoint / incremental adjoint ping-pong)
+    float *Gm;          // [nt][3][V] grad of the trilinear cell of m^n at x + d(x) (written by
+                        // the state sweep, read by the adjoint and incremental sweeps), or
+                        // nullptr (checkpointed plans and batch members compute it on the fly)
     float *b;           // 3V body force
     float *dv;          // 3V iota(dv~)
     float *dm[2];       // V each (incremental state ping-pong)
@@ -124,6 +128,10 @@ inline float *state_slot(const blr_plan *P, int n) {
     else slot = P->nseg + (n % k) - 1;
     return P->m + slot * P->V;
 }
+
+// Plan creation (api.cu); grad_cache: keep the per-step state gradients Gm
+// when every state is stored (batch members run their own sweeps and skip it).
+int plan_create(const blr_params *p, bool grad_cache, blr_plan **out);
 
 // ---- launchers implemented in the .cu files (return BLR_OK / BLR_ECUDA) ----
 

@@ -172,12 +172,14 @@ __device__ __forceinline__ void issue_plane2(uint32_t dst_a, const float *__rest
 // at partials[(x1 * N2 + x2) * ceil(N3/32) + x3/32] (independent of the tiling).
 // Plane s of m^n completes output plane s - 1 (its cells reach x1 - 1 .. x1 + 1);
 // planes arrive by cp.async two iterations ahead (8-slot ring).
+// Gout (nullable): the gradient of the trilinear cell, grad m^n(x + d(x)), of
+// every voxel, [3][V] (read later by the adjoint and incremental sweeps).
 template <bool LAST>
 __device__ __forceinline__ void
 state_tile(const float *__restrict__ m_in, const float *__restrict__ d,
            float *__restrict__ m_out, const Grid3 g, int CH, const float *__restrict__ I1,
            float *__restrict__ lam_out, float lam_scale, double *__restrict__ partials,
-           int k0, int j0, int i0) {
+           int k0, int j0, int i0, float *__restrict__ Gout = nullptr) {
     __shared__ __align__(16) float sM[8][MHP];
     const int i_end = min(i0 + CH, g.N1);
     const Slots ps = plane_slots(g, k0, j0);
@@ -211,7 +213,16 @@ state_tile(const float *__restrict__ m_in, const float *__restrict__ d,
             const AxisW a2 = axis_weights(dd2);
             const float *P0 = a0.lo < 0 ? sM[ring8(r + 6)] : sM[ring8(r + 7)];
             const float *P1 = a0.lo < 0 ? sM[ring8(r + 7)] : sM[ring8(r)];
-            const float val = trilinear2<false>(P0, P1, hj, hk, a0, a1, a2, nullptr);
+            float val;
+            if (Gout) {
+                float G[3];
+                val = trilinear2<true>(P0, P1, hj, hk, a0, a1, a2, G);
+                Gout[idx] = G[0];
+                Gout[g.V + idx] = G[1];
+                Gout[2 * g.V + idx] = G[2];
+            } else {
+                val = trilinear2<false>(P0, P1, hj, hk, a0, a1, a2, nullptr);
+            }
             m_out[idx] = val;
             if (LAST) {
                 res = val - __ldg(I1 + idx);
@@ -237,9 +248,10 @@ template <bool LAST>
 __global__ void __launch_bounds__(MT, 4)
 k_state_march(const float *__restrict__ m_in, const float *__restrict__ d,
               float *__restrict__ m_out, Grid3 g, int CH, const float *__restrict__ I1,
-              float *__restrict__ lam_out, float lam_scale, double *__restrict__ partials) {
+              float *__restrict__ lam_out, float lam_scale, double *__restrict__ partials,
+              float *__restrict__ Gout) {
     state_tile<LAST>(m_in, d, m_out, g, CH, I1, lam_out, lam_scale, partials, blockIdx.x * MK,
-                     blockIdx.y * MJ, blockIdx.z * CH);
+                     blockIdx.y * MJ, blockIdx.z * CH, Gout);
 }
 
 // ---------------------------------------------------------------------------
@@ -617,10 +629,10 @@ __global__ void __launch_bounds__(MT, 4)
 k_state_bal(const float *__restrict__ m_in, const float *__restrict__ d,
             float *__restrict__ m_out, Grid3 g, const float *__restrict__ I1,
             float *__restrict__ lam_out, float lam_scale, double *__restrict__ partials, int ntk,
-            long long W) {
+            long long W, float *__restrict__ Gout) {
     for_segments(g.N1, ntk, W, [&](int kt, int jt, int i0, int len) {
         state_tile<LAST>(m_in, d, m_out, g, len, I1, lam_out, lam_scale, partials, kt * MK,
-                         jt * MJ, i0);
+                         jt * MJ, i0, Gout);
     });
 }
 
@@ -677,6 +689,7 @@ constexpr int BROWS = AJ + 2;                // haloed rows
 constexpr int BPL = BROWS * BW;              // positions per plane
 constexpr int BQ = 4, BM = 6;                // ring slots
 constexpr int ADJW_SMEM = BQ * BPL * 16 + BQ * BPL * 4 + BM * BPL * 4;
+constexpr int ADJW_SMEM_G = BQ * BPL * 16 + BQ * BPL * 4;   // USEG: no m^n ring
 constexpr int AQC = (BPL + MT - 1) / MT;     // d4 copies per thread
 constexpr int ASC = BROWS * BG;              // scalar-field copies per plane (180)
 constexpr int AM0 = MT - ASC;                // first thread copying m
@@ -697,11 +710,14 @@ __device__ __forceinline__ AdjWRings adjw_rings() {
     return R;
 }
 
-template <bool FIRST, bool WRITE_LAM>
+// USEG: grad m^n(x + d(x)) is read from Gn ([3][V], written by the state sweep)
+// instead of being interpolated from an m^n ring (which is then not kept).
+template <bool FIRST, bool WRITE_LAM, bool USEG>
 __device__ __forceinline__ void
 adjoint_tile_w(const float *__restrict__ lam_in, const float *__restrict__ m_n,
                const float4 *__restrict__ d4, float *__restrict__ lam_out, float *__restrict__ b,
-               float dt, const Grid3 g, int CH, int k0, int j0, int i0) {
+               float dt, const Grid3 g, int CH, int k0, int j0, int i0,
+               const float *__restrict__ Gn) {
     const AdjWRings R = adjw_rings();
     const int i_end = min(i0 + CH, g.N1);
     const long long plane = (long long)g.N2 * g.N3;
@@ -718,7 +734,7 @@ adjoint_tile_w(const float *__restrict__ lam_in, const float *__restrict__ m_n,
         const int c = tid + MT * i;
         offq[i] = c < BPL ? win_off(g, j0, k0, c / BW, c % BW) : 0;
     }
-    const bool cl = tid < ASC, cm = tid >= AM0;
+    const bool cl = tid < ASC, cm = !USEG && tid >= AM0;
     const int offl = cl ? win_off(g, j0, k0, tid / BG, 4 * (tid % BG)) : 0;
     const int offm = cm ? win_off(g, j0, k0, (tid - AM0) / BG, 4 * ((tid - AM0) % BG)) : 0;
     const uint32_t q0s = smem_u32(R.Q) + (uint32_t)tid * 16u;
@@ -740,9 +756,11 @@ adjoint_tile_w(const float *__restrict__ lam_in, const float *__restrict__ m_n,
     issue(i0, 1);
     float2 accA, accB, accC;   // rows (jb, jb + 1) of output planes s - 1, s, s + 1
     accA = accB = accC = make_float2(0.f, 0.f);
-    float bb[ARJ][3];
+    float bb[ARJ][3], gg[ARJ][3];   // b and (USEG) grad m^n of the next output voxels
 #pragma unroll
-    for (int jj = 0; jj < ARJ; ++jj) bb[jj][0] = bb[jj][1] = bb[jj][2] = 0.f;
+    for (int jj = 0; jj < ARJ; ++jj)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) bb[jj][a] = gg[jj][a] = 0.f;
     for (int s = i0 - 1; s <= i_end; ++s) {
         const int r = s - i0 + 1;
         cp_wait1();
@@ -794,11 +812,17 @@ adjoint_tile_w(const float *__restrict__ lam_in, const float *__restrict__ m_n,
                     const int j = jb + jj;
                     if (j < g.N2) {
                         const int hj = 1 + ARJ * w + jj;
-                        const float4 q0 = Qo[hj * BW + hk];
-                        const AxisW a0 = axis_weights(q0.x);
                         float G[3];
-                        trilinear2<true, BW>(a0.lo < 0 ? Ma : Mb, a0.lo < 0 ? Mb : Mc, hj, hk, a0,
-                                             axis_weights(q0.y), axis_weights(q0.z), G);
+                        if (USEG) {
+                            G[0] = gg[jj][0];
+                            G[1] = gg[jj][1];
+                            G[2] = gg[jj][2];
+                        } else {
+                            const float4 q0 = Qo[hj * BW + hk];
+                            const AxisW a0 = axis_weights(q0.x);
+                            trilinear2<true, BW>(a0.lo < 0 ? Ma : Mb, a0.lo < 0 ? Mb : Mc, hj, hk,
+                                                 a0, axis_weights(q0.y), axis_weights(q0.z), G);
+                        }
                         const float sl = dt * Lo[hj * BW + hk];
                         const long long idx = (long long)o * plane + (long long)j * g.N3 + k;
 #pragma unroll
@@ -808,14 +832,17 @@ adjoint_tile_w(const float *__restrict__ lam_in, const float *__restrict__ m_n,
                     }
                 }
             }
-            if (!FIRST && s >= i0 && s < i_end) {
+            if ((!FIRST || USEG) && s >= i0 && s < i_end) {
 #pragma unroll
                 for (int jj = 0; jj < ARJ; ++jj) {
                     const int j = jb + jj;
                     if (j < g.N2) {
                         const long long nidx = (long long)s * plane + (long long)j * g.N3 + k;
 #pragma unroll
-                        for (int a = 0; a < 3; ++a) bb[jj][a] = b[a * V + nidx];
+                        for (int a = 0; a < 3; ++a) {
+                            if (!FIRST) bb[jj][a] = b[a * V + nidx];
+                            if (USEG) gg[jj][a] = __ldg(Gn + a * V + nidx);
+                        }
                     }
                 }
             }
@@ -826,14 +853,14 @@ adjoint_tile_w(const float *__restrict__ lam_in, const float *__restrict__ m_n,
     }
 }
 
-template <bool FIRST, bool WRITE_LAM>
+template <bool FIRST, bool WRITE_LAM, bool USEG>
 __global__ void __launch_bounds__(MT, ADJ_BLOCKS)
 k_adjoint_wide(const float *__restrict__ lam_in, const float *__restrict__ m_n,
                const float4 *__restrict__ d4, float *__restrict__ lam_out, float *__restrict__ b,
-               float dt, Grid3 g, int ntk, long long W) {
+               float dt, Grid3 g, int ntk, long long W, const float *__restrict__ Gn) {
     for_segments(g.N1, ntk, W, [&](int kt, int jt, int i0, int len) {
-        adjoint_tile_w<FIRST, WRITE_LAM>(lam_in, m_n, d4, lam_out, b, dt, g, len, kt * MK, jt * AJ,
-                                         i0);
+        adjoint_tile_w<FIRST, WRITE_LAM, USEG>(lam_in, m_n, d4, lam_out, b, dt, g, len, kt * MK,
+                                               jt * AJ, i0, Gn);
     });
 }
 
@@ -845,29 +872,33 @@ constexpr int IROWS = AJ + 2;                // haloed rows
 constexpr int IPL = IROWS * BW;              // positions per plane
 constexpr int IM = 6;                        // ring slots
 constexpr int INC_BLOCKS = 3;                // resident blocks per SM (registers)
-template <bool FIRST>
-constexpr int incw_smem() { return (FIRST ? 1 : 2) * IM * IPL * 4; }
+// USEG: grad m^n(x + d(x)) is read from Gn instead of being interpolated from an
+// m^n ring (which is then not kept); the first step then needs no ring at all.
+template <bool FIRST, bool USEG>
+constexpr int incw_smem() { return ((USEG ? 0 : 1) + (FIRST ? 0 : 1)) * IM * IPL * 4; }
 
-template <bool FIRST, bool LAST>
+template <bool FIRST, bool LAST, bool USEG>
 __device__ __forceinline__ void
 incstate_tile_w(const float *__restrict__ dm_in, const float *__restrict__ m_n,
                 const float4 *__restrict__ d4, const float *__restrict__ dv,
                 float *__restrict__ dm_out, float dt, float lam_scale, const Grid3 g, int CH,
-                int k0, int j0, int i0) {
+                int k0, int j0, int i0, const float *__restrict__ Gn) {
     extern __shared__ __align__(16) unsigned char blr_dyn_smem[];
-    float *RM = reinterpret_cast<float *>(blr_dyn_smem);    // [IM][IPL] m^n
-    float *RD = RM + IM * IPL;                               // [IM][IPL] dm^n
+    float *RM = reinterpret_cast<float *>(blr_dyn_smem);    // [IM][IPL] m^n (not USEG)
+    float *RD = RM + (USEG ? 0 : IM * IPL);                  // [IM][IPL] dm^n (not FIRST)
     const int i_end = min(i0 + CH, g.N1);
     const long long plane = (long long)g.N2 * g.N3;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int k = k0 + lane, jb = j0 + ARJ * w;
     const bool kin = k < g.N3;
     const int hk = BHK + lane;
-    const bool cmf = tid < ASC, cdf = !FIRST && tid >= AM0;
+    // copies: m (threads 0..179) and dm (76..255); with USEG only dm (0..179)
+    const int D0 = USEG ? 0 : AM0;
+    const bool cmf = !USEG && tid < ASC, cdf = !FIRST && tid >= D0 && tid < D0 + ASC;
     const int offm = cmf ? win_off(g, j0, k0, tid / BG, 4 * (tid % BG)) : 0;
-    const int offd = cdf ? win_off(g, j0, k0, (tid - AM0) / BG, 4 * ((tid - AM0) % BG)) : 0;
+    const int offd = cdf ? win_off(g, j0, k0, (tid - D0) / BG, 4 * ((tid - D0) % BG)) : 0;
     const uint32_t m0s = smem_u32(RM) + (uint32_t)tid * 16u;
-    const uint32_t d0s = smem_u32(RD) + (uint32_t)(tid - AM0) * 16u;
+    const uint32_t d0s = smem_u32(RD) + (uint32_t)(tid - D0) * 16u;
     auto issue = [&](int sp, int r) {
         if (sp <= i_end) {
             const long long pb = (long long)wrap1(sp, g.N1) * plane;
@@ -881,10 +912,12 @@ incstate_tile_w(const float *__restrict__ dm_in, const float *__restrict__ m_n,
     issue(i0, 1);
     float4 dd[ARJ];        // d of the output voxels (plane s - 1)
     float vv[ARJ][3];      // dv of the output voxels
+    float gg[ARJ][3];      // (USEG) grad m^n of the output voxels
 #pragma unroll
     for (int jj = 0; jj < ARJ; ++jj) {
         dd[jj] = make_float4(0.f, 0.f, 0.f, 0.f);
         vv[jj][0] = vv[jj][1] = vv[jj][2] = 0.f;
+        gg[jj][0] = gg[jj][1] = gg[jj][2] = 0.f;
     }
     for (int s = i0 - 1; s <= i_end; ++s) {
         const int r = s - i0 + 1;
@@ -894,18 +927,23 @@ incstate_tile_w(const float *__restrict__ dm_in, const float *__restrict__ m_n,
         // the next output voxels' operands are loaded before this plane's work,
         // which then hides their latency
         float4 nd[ARJ];
-        float nv[ARJ][3];
+        float nv[ARJ][3], ng[ARJ][3];
 #pragma unroll
         for (int jj = 0; jj < ARJ; ++jj) {
             nd[jj] = dd[jj];
-            nv[jj][0] = vv[jj][0];
-            nv[jj][1] = vv[jj][1];
-            nv[jj][2] = vv[jj][2];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                nv[jj][a] = vv[jj][a];
+                ng[jj][a] = gg[jj][a];
+            }
             if (kin && jb + jj < g.N2 && s >= i0 && s < i_end) {
                 const long long nidx = (long long)s * plane + (long long)(jb + jj) * g.N3 + k;
-                nd[jj] = __ldg(d4 + nidx);
+                if (!(FIRST && USEG)) nd[jj] = __ldg(d4 + nidx);   // cell of dm^n (and m^n)
 #pragma unroll
-                for (int a = 0; a < 3; ++a) nv[jj][a] = __ldg(dv + a * g.V + nidx);
+                for (int a = 0; a < 3; ++a) {
+                    nv[jj][a] = __ldg(dv + a * g.V + nidx);
+                    if (USEG) ng[jj][a] = __ldg(Gn + a * g.V + nidx);
+                }
             }
         }
         const int o = s - 1;
@@ -923,7 +961,13 @@ incstate_tile_w(const float *__restrict__ dm_in, const float *__restrict__ m_n,
                     const uint32_t s0 = a0.lo < 0 ? (uint32_t)(r + 4) % IM : (uint32_t)(r + 5) % IM;
                     const uint32_t s1 = a0.lo < 0 ? (uint32_t)(r + 5) % IM : (uint32_t)r % IM;
                     float G[3];
-                    trilinear2<true, BW>(RM + s0 * IPL, RM + s1 * IPL, hj, hk, a0, a1, a2, G);
+                    if (USEG) {
+                        G[0] = gg[jj][0];
+                        G[1] = gg[jj][1];
+                        G[2] = gg[jj][2];
+                    } else {
+                        trilinear2<true, BW>(RM + s0 * IPL, RM + s1 * IPL, hj, hk, a0, a1, a2, G);
+                    }
                     float out = 0.f;
                     if (!FIRST)
                         out = trilinear2<false, BW>(RD + s0 * IPL, RD + s1 * IPL, hj, hk, a0, a1,
@@ -937,22 +981,24 @@ incstate_tile_w(const float *__restrict__ dm_in, const float *__restrict__ m_n,
 #pragma unroll
         for (int jj = 0; jj < ARJ; ++jj) {
             dd[jj] = nd[jj];
-            vv[jj][0] = nv[jj][0];
-            vv[jj][1] = nv[jj][1];
-            vv[jj][2] = nv[jj][2];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                vv[jj][a] = nv[jj][a];
+                gg[jj][a] = ng[jj][a];
+            }
         }
     }
 }
 
-template <bool FIRST, bool LAST>
+template <bool FIRST, bool LAST, bool USEG>
 __global__ void __launch_bounds__(MT, INC_BLOCKS)
 k_incstate_wide(const float *__restrict__ dm_in, const float *__restrict__ m_n,
                 const float4 *__restrict__ d4, const float *__restrict__ dv,
                 float *__restrict__ dm_out, float dt, float lam_scale, Grid3 g, int ntk,
-                long long W) {
+                long long W, const float *__restrict__ Gn) {
     for_segments(g.N1, ntk, W, [&](int kt, int jt, int i0, int len) {
-        incstate_tile_w<FIRST, LAST>(dm_in, m_n, d4, dv, dm_out, dt, lam_scale, g, len, kt * MK,
-                                     jt * AJ, i0);
+        incstate_tile_w<FIRST, LAST, USEG>(dm_in, m_n, d4, dv, dm_out, dt, lam_scale, g, len,
+                                           kt * MK, jt * AJ, i0, Gn);
     });
 }
 
@@ -989,14 +1035,22 @@ int adjoint_smem_attributes() {
     BLR_CK(cudaFuncSetAttribute(k_adjoint_bal<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
     BLR_CK(cudaFuncSetAttribute(k_adjoint_bal<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
     BLR_CK(cudaFuncSetAttribute(k_adjoint_bal<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
-    BLR_CK(cudaFuncSetAttribute(k_adjoint_wide<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM));
-    BLR_CK(cudaFuncSetAttribute(k_adjoint_wide<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM));
-    BLR_CK(cudaFuncSetAttribute(k_adjoint_wide<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM));
-    BLR_CK(cudaFuncSetAttribute(k_adjoint_wide<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM));
-    BLR_CK(cudaFuncSetAttribute(k_incstate_wide<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, incw_smem<true>()));
-    BLR_CK(cudaFuncSetAttribute(k_incstate_wide<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, incw_smem<true>()));
-    BLR_CK(cudaFuncSetAttribute(k_incstate_wide<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, incw_smem<false>()));
-    BLR_CK(cudaFuncSetAttribute(k_incstate_wide<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, incw_smem<false>()));
+    BLR_CK(cudaFuncSetAttribute(k_adjoint_wide<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM_G));
+    BLR_CK(cudaFuncSetAttribute(k_adjoint_wide<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_adjoint_wide<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM_G));
+    BLR_CK(cudaFuncSetAttribute(k_adjoint_wide<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_adjoint_wide<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM_G));
+    BLR_CK(cudaFuncSetAttribute(k_adjoint_wide<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_adjoint_wide<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM_G));
+    BLR_CK(cudaFuncSetAttribute(k_adjoint_wide<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_incstate_wide<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, incw_smem<true, true>()));
+    BLR_CK(cudaFuncSetAttribute(k_incstate_wide<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, incw_smem<true, false>()));
+    BLR_CK(cudaFuncSetAttribute(k_incstate_wide<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, incw_smem<true, true>()));
+    BLR_CK(cudaFuncSetAttribute(k_incstate_wide<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, incw_smem<true, false>()));
+    BLR_CK(cudaFuncSetAttribute(k_incstate_wide<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, incw_smem<false, true>()));
+    BLR_CK(cudaFuncSetAttribute(k_incstate_wide<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, incw_smem<false, false>()));
+    BLR_CK(cudaFuncSetAttribute(k_incstate_wide<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, incw_smem<false, true>()));
+    BLR_CK(cudaFuncSetAttribute(k_incstate_wide<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, incw_smem<false, false>()));
     done = true;
     return BLR_OK;
 }
@@ -1056,27 +1110,37 @@ BalGeom bal_geom(const blr_plan *P, int bps, int rows) {
     return b;
 }
 
-// One state step m_out = S m_in; LAST also writes lambda^nt and the image-term partials.
+// One state step m_out = S m_in; LAST also writes lambda^nt and the image-term
+// partials; Gout (nullable) receives grad m_in at the departure points.
 template <bool LAST>
 void launch_state(const blr_plan *P, const float *m_in, float *m_out, const float *I1, float *lam_out,
-                  float lam_scale, double *partials, cudaStream_t s) {
+                  float lam_scale, double *partials, float *Gout, cudaStream_t s) {
     if (P->bal_sweep) {
         const BalGeom b = bal_geom(P, P->bal_sweep, MJ);
         k_state_bal<LAST><<<b.G, MT, 0, s>>>(m_in, P->d, m_out, P->grid, I1, lam_out, lam_scale,
-                                              partials, b.ntk, b.W);
+                                              partials, b.ntk, b.W, Gout);
     } else {
         k_state_march<LAST><<<sweep_grid(P), MT, 0, s>>>(m_in, P->d, m_out, P->grid, P->chunk, I1,
-                                                          lam_out, lam_scale, partials);
+                                                          lam_out, lam_scale, partials, Gout);
     }
+}
+
+// grad m^n(x + d(x)) of step n when the plan keeps it, else nullptr.
+float *grad_slot(const blr_plan *P, int n) {
+    return P->Gm ? P->Gm + (size_t)3 * n * P->V : nullptr;
 }
 
 template <bool FIRST, bool WRITE_LAM>
 void launch_adjoint_t(const blr_plan *P, const float *lin, const float *mn, float *lout, float *b,
-                      cudaStream_t s) {
+                      const float *Gn, cudaStream_t s) {
     if (P->sweep_wide) {
         const BalGeom g = bal_geom(P, P->bal_adj ? P->bal_adj : ADJ_BLOCKS, AJ);
-        k_adjoint_wide<FIRST, WRITE_LAM><<<g.G, MT, ADJW_SMEM, s>>>(
-            lin, mn, P->d4, lout, b, P->dt, P->grid, g.ntk, g.W);
+        if (Gn)
+            k_adjoint_wide<FIRST, WRITE_LAM, true><<<g.G, MT, ADJW_SMEM_G, s>>>(
+                lin, mn, P->d4, lout, b, P->dt, P->grid, g.ntk, g.W, Gn);
+        else
+            k_adjoint_wide<FIRST, WRITE_LAM, false><<<g.G, MT, ADJW_SMEM, s>>>(
+                lin, mn, P->d4, lout, b, P->dt, P->grid, g.ntk, g.W, nullptr);
     } else if (P->bal_adj) {
         const BalGeom g = bal_geom(P, P->bal_adj, AJ);
         k_adjoint_bal<FIRST, WRITE_LAM><<<g.G, MT, ADJ_SMEM, s>>>(lin, mn, P->d, lout, b, P->dt,
@@ -1089,20 +1153,24 @@ void launch_adjoint_t(const blr_plan *P, const float *lin, const float *mn, floa
 
 // One adjoint step: lambda^n = S^T lambda^{n+1} (when wlam) and b (+)= dt lambda grad m^n.
 void launch_adjoint(const blr_plan *P, bool first, bool wlam, const float *lin, const float *mn,
-                    float *lout, float *b, cudaStream_t s) {
-    if (first && wlam) launch_adjoint_t<true, true>(P, lin, mn, lout, b, s);
-    else if (first) launch_adjoint_t<true, false>(P, lin, mn, lout, b, s);
-    else if (wlam) launch_adjoint_t<false, true>(P, lin, mn, lout, b, s);
-    else launch_adjoint_t<false, false>(P, lin, mn, lout, b, s);
+                    float *lout, float *b, const float *Gn, cudaStream_t s) {
+    if (first && wlam) launch_adjoint_t<true, true>(P, lin, mn, lout, b, Gn, s);
+    else if (first) launch_adjoint_t<true, false>(P, lin, mn, lout, b, Gn, s);
+    else if (wlam) launch_adjoint_t<false, true>(P, lin, mn, lout, b, Gn, s);
+    else launch_adjoint_t<false, false>(P, lin, mn, lout, b, Gn, s);
 }
 
 template <bool FIRST, bool LAST>
 void launch_incstate_t(const blr_plan *P, const float *din, const float *mn, float *dout,
-                       float lam_scale, cudaStream_t s, bool wide) {
+                       float lam_scale, const float *Gn, cudaStream_t s, bool wide) {
     if (wide && P->sweep_wide) {
         const BalGeom b = bal_geom(P, P->bal_inc ? P->bal_inc : INC_BLOCKS, AJ);
-        k_incstate_wide<FIRST, LAST><<<b.G, MT, incw_smem<FIRST>(), s>>>(
-            din, mn, P->d4, P->dv, dout, P->dt, lam_scale, P->grid, b.ntk, b.W);
+        if (Gn)
+            k_incstate_wide<FIRST, LAST, true><<<b.G, MT, incw_smem<FIRST, true>(), s>>>(
+                din, mn, P->d4, P->dv, dout, P->dt, lam_scale, P->grid, b.ntk, b.W, Gn);
+        else
+            k_incstate_wide<FIRST, LAST, false><<<b.G, MT, incw_smem<FIRST, false>(), s>>>(
+                din, mn, P->d4, P->dv, dout, P->dt, lam_scale, P->grid, b.ntk, b.W, nullptr);
     } else if (P->bal_sweep) {
         const BalGeom b = bal_geom(P, P->bal_sweep, MJ);
         k_incstate_bal<FIRST, LAST><<<b.G, MT, 0, s>>>(din, mn, P->d, P->dv, dout, P->dt, lam_scale,
@@ -1114,18 +1182,21 @@ void launch_incstate_t(const blr_plan *P, const float *din, const float *mn, flo
 }
 
 // One incremental-state step dm^{n+1} = S dm^n - dt grad m^n . dv (wide: whether
-// the wide-copy kernel may be used).
+// the wide-copy kernel may be used; Gn: grad m^n when the plan keeps it).
 void launch_incstate(const blr_plan *P, bool first, bool last, const float *din, const float *mn,
-                     float *dout, float lam_scale, cudaStream_t s, bool wide = true) {
-    if (first && last) launch_incstate_t<true, true>(P, din, mn, dout, lam_scale, s, wide);
-    else if (first) launch_incstate_t<true, false>(P, din, mn, dout, lam_scale, s, wide);
-    else if (last) launch_incstate_t<false, true>(P, din, mn, dout, lam_scale, s, wide);
-    else launch_incstate_t<false, false>(P, din, mn, dout, lam_scale, s, wide);
+                     float *dout, float lam_scale, const float *Gn, cudaStream_t s,
+                     bool wide = true) {
+    if (first && last) launch_incstate_t<true, true>(P, din, mn, dout, lam_scale, Gn, s, wide);
+    else if (first) launch_incstate_t<true, false>(P, din, mn, dout, lam_scale, Gn, s, wide);
+    else if (last) launch_incstate_t<false, true>(P, din, mn, dout, lam_scale, Gn, s, wide);
+    else launch_incstate_t<false, false>(P, din, mn, dout, lam_scale, Gn, s, wide);
 }
 
-// m^{n+1} from m^n in the slots given by state_slot (not the last step).
-int state_step(blr_plan *P, int n, cudaStream_t s) {
-    launch_state<false>(P, state_slot(P, n), state_slot(P, n + 1), nullptr, nullptr, 0.f, nullptr, s);
+// m^{n+1} from m^n in the slots given by state_slot (not the last step), with
+// grad m^n into Gout when given.
+int state_step(blr_plan *P, int n, float *Gout, cudaStream_t s) {
+    launch_state<false>(P, state_slot(P, n), state_slot(P, n + 1), nullptr, nullptr, 0.f, nullptr,
+                        Gout, s);
     BLR_CK_LAUNCH();
     return BLR_OK;
 }
@@ -1136,7 +1207,7 @@ int ensure_segment(blr_plan *P, int j, cudaStream_t s) {
     if (P->seg_valid == j) return BLR_OK;
     const int n0 = j * P->ck, n1 = n0 + P->ck < P->p.nt ? n0 + P->ck : P->p.nt;
     for (int n = n0; n < n1 - 1; ++n) {
-        int rc = state_step(P, n, s);
+        int rc = state_step(P, n, nullptr, s);
         if (rc) return rc;
     }
     P->seg_valid = j;
@@ -1149,11 +1220,11 @@ int sweep_state(blr_plan *P, cudaStream_t s) {
     const int nt = P->p.nt;
     const float lam_scale = (float)(-2.0 / (P->p.sigma * P->p.sigma));
     for (int n = 0; n < nt - 1; ++n) {
-        int rc = state_step(P, n, s);
+        int rc = state_step(P, n, grad_slot(P, n), s);
         if (rc) return rc;
     }
     launch_state<true>(P, state_slot(P, nt - 1), state_slot(P, nt), P->I1, P->lam[0], lam_scale,
-                       P->partials, s);
+                       P->partials, grad_slot(P, nt - 1), s);
     BLR_CK_LAUNCH();
     P->seg_valid = P->nseg - 1;   // the forward sweep leaves the last segment's states
     return BLR_OK;
@@ -1174,7 +1245,7 @@ int sweep_adjoint(blr_plan *P, float *b, float *lambda0, cudaStream_t s) {
             float *lout = (n == 0 && lambda0) ? lambda0 : P->lam[1 - cur];
             const bool first = (n == nt - 1);
             const bool wlam = (n > 0) || (lambda0 != nullptr);
-            launch_adjoint(P, first, wlam, lin, state_slot(P, n), lout, b, s);
+            launch_adjoint(P, first, wlam, lin, state_slot(P, n), lout, b, grad_slot(P, n), s);
             BLR_CK_LAUNCH();
             cur = 1 - cur;
         }
@@ -1194,7 +1265,8 @@ int sweep_incremental(blr_plan *P, cudaStream_t s) {
         for (int n = n0; n < n1; ++n) {
             const float *din = P->dm[cur];
             float *dout = (n == nt - 1) ? P->lam[0] : P->dm[1 - cur];
-            launch_incstate(P, n == 0, n == nt - 1, din, state_slot(P, n), dout, lam_scale, s);
+            launch_incstate(P, n == 0, n == nt - 1, din, state_slot(P, n), dout, lam_scale,
+                            grad_slot(P, n), s);
             BLR_CK_LAUNCH();
             cur = 1 - cur;
         }
@@ -1250,9 +1322,10 @@ namespace {
 // Kind 3 is the wide-copy incremental-state kernel, kind 2 the march kernel.
 int time_step(blr_plan *P, int kind, cudaStream_t s) {
     if (kind == 1)
-        launch_adjoint(P, false, true, P->lam[0], P->m, P->lam[1], P->b, s);
+        launch_adjoint(P, false, true, P->lam[0], P->m, P->lam[1], P->b, grad_slot(P, 0), s);
     else
-        launch_incstate(P, false, false, P->dm[0], P->m, P->dm[1], 1.f, s, kind == 3);
+        launch_incstate(P, false, false, P->dm[0], P->m, P->dm[1], 1.f,
+                        kind == 3 ? grad_slot(P, 0) : nullptr, s, kind == 3);
     BLR_CK_LAUNCH();
     return BLR_OK;
 }
