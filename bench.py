@@ -292,6 +292,23 @@ def measure_precision(precision, args, dev, I0g, I1g, flush, stream, dist, world
     e1.synchronize()
     hvp_ms = e0.elapsed_time(e1) / reps
 
+    # stage times at the same point: the truncated DFTs alone (blr_expand,
+    # blr_project); the incremental-state sweep is the rest of the HVP once the
+    # adjoint sweep (below) is taken out
+    fld = torch.empty((3,) + N, dtype=torch.float32, device=dev)
+    stage = {}
+    for name, fn in (("expand", lambda: plan.expand(dvt, fld)),
+                     ("project", lambda: plan.project(fld, hout))):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        stage[name + "_us"] = 1000.0 * e0.elapsed_time(e1) / reps
+
     # roofline of the dominant kernel (adjoint sweep step): blr_adjoint launches
     # exactly nt adjoint-step kernels and nothing else
     bforce = torch.empty((3,) + N, dtype=torch.float32, device=dev)
@@ -309,7 +326,10 @@ def measure_precision(precision, args, dev, I0g, I1g, flush, stream, dist, world
     adj_bytes = ADJ_BYTES(NT) * V / NT
     peak, peak_kind = peaks()
     achieved = adj_bytes / adj_launch_s / 1e9
-    roofline = {"kernel": "k_adjoint_march", "bound": "hbm", "achieved": achieved,
+    stage["adjoint_sweep_us"] = adj_launch_s * 1e6 * NT
+    stage["incremental_sweep_us"] = (1000.0 * hvp_ms - stage["expand_us"] - stage["project_us"]
+                                     - stage["adjoint_sweep_us"])
+    roofline = {"kernel": "k_adjoint_wide", "bound": "hbm", "achieved": achieved,
                 "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": f"{peak_kind} hbm_gbs (copy, burst; kernel timed alone)",
                 "algorithmic_bytes_per_launch": adj_bytes, "launch_us": adj_launch_s * 1e6,
@@ -318,7 +338,7 @@ def measure_precision(precision, args, dev, I0g, I1g, flush, stream, dist, world
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
                                   "interior launch at 128^3 (null once the kernel source changed)"}
     return dict(plan=plan, ms=ms, launches=launches, clocks=clocks, rep=rep, hvp_ms=hvp_ms,
-                roofline=roofline, dvt=dvt)
+                roofline=roofline, dvt=dvt, stage=stage)
 
 
 def main_ours(args):
@@ -367,7 +387,8 @@ def main_ours(args):
                                  "hvp_per_s": world * 1000.0 / r["hvp_ms"],
                                  "final_energy": r["rep"].energy,
                                  "pcg_iters": r["rep"].pcg_iters,
-                                 "adjoint_step_us": r["roofline"]["launch_us"]}
+                                 "adjoint_step_us": r["roofline"]["launch_us"],
+                                 "hvp_stage_us": r["stage"]}
                              for p, r in res.items()}}
     plan = head["plan"]
 

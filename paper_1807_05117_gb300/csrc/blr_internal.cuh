@@ -78,6 +78,9 @@ struct blr_plan {
     bool sweep_wide;    // adjoint and incremental state use the wide-copy kernels (N3 % 4 == 0)
     bool use_gm;        // Gm is kept (see Gm)
     int bal_inc;        // blocks per SM of the wide-copy incremental-state grid (sweep_autotune)
+    int adj_useg;       // the adjoint reads Gm (1) or interpolates it (0)      (sweep_autotune)
+    int inc_mode;       // incremental state: 0 wide-copy, 1 wide-copy reading Gm,
+                        // 2 gather reading Gm                                  (sweep_autotune)
     float *m;           // state slots (see state_slot): checkpoints, segment, final
     int ck;             // checkpoint interval k (nt when every state is kept)
     int nseg;           // segments ceil(nt / k)

@@ -1002,6 +1002,50 @@ k_incstate_wide(const float *__restrict__ dm_in, const float *__restrict__ m_n,
     });
 }
 
+// ---------------------------------------------------------------------------
+// Incremental state step, gather form (plans that keep grad m^n): one thread per
+// voxel and no shared memory; the eight corners of the cell of dm^n are read
+// straight from global memory (neighbouring threads share them through L1/L2),
+// d from d4, dv and grad m^n from their planar arrays.  Nothing waits at a
+// barrier, so the loads of many voxels overlap.  Block: 32 (x3) x 8 (x2) voxels
+// of one x1 plane.  Same arithmetic as incstate_tile.
+template <bool FIRST, bool LAST>
+__global__ void __launch_bounds__(MT)
+k_incstate_gather(const float *__restrict__ dm_in, const float4 *__restrict__ d4,
+                  const float *__restrict__ dv, const float *__restrict__ Gn,
+                  float *__restrict__ dm_out, float dt, float lam_scale, Grid3 g) {
+    const int k = blockIdx.x * MK + (threadIdx.x & 31);
+    const int j = blockIdx.y * MJ + (threadIdx.x >> 5);
+    const int i = blockIdx.z;
+    if (k >= g.N3 || j >= g.N2) return;
+    const long long plane = (long long)g.N2 * g.N3;
+    const long long idx = (long long)i * plane + (long long)j * g.N3 + k;
+    const float gdv = fmaf(__ldg(Gn + idx), __ldg(dv + idx),
+                           fmaf(__ldg(Gn + g.V + idx), __ldg(dv + g.V + idx),
+                                __ldg(Gn + 2 * g.V + idx) * __ldg(dv + 2 * g.V + idx)));
+    float out = 0.f;
+    if (!FIRST) {
+        const float4 q = __ldg(d4 + idx);
+        const AxisW a0 = axis_weights(q.x), a1 = axis_weights(q.y), a2 = axis_weights(q.z);
+        const long long p0 = (long long)wrap1(i + a0.lo, g.N1) * plane;
+        const long long p1 = (long long)wrap1(i + a0.lo + 1, g.N1) * plane;
+        const long long r0 = (long long)wrap1(j + a1.lo, g.N2) * g.N3;
+        const long long r1 = (long long)wrap1(j + a1.lo + 1, g.N2) * g.N3;
+        const int c0 = wrap1(k + a2.lo, g.N3), c1 = wrap1(k + a2.lo + 1, g.N3);
+        const float c000 = __ldg(dm_in + p0 + r0 + c0), c001 = __ldg(dm_in + p0 + r0 + c1);
+        const float c010 = __ldg(dm_in + p0 + r1 + c0), c011 = __ldg(dm_in + p0 + r1 + c1);
+        const float c100 = __ldg(dm_in + p1 + r0 + c0), c101 = __ldg(dm_in + p1 + r0 + c1);
+        const float c110 = __ldg(dm_in + p1 + r1 + c0), c111 = __ldg(dm_in + p1 + r1 + c1);
+        // the evaluation order of trilinear2
+        const float l00 = fmaf(a2.wl, c000, a2.wh * c001), l01 = fmaf(a2.wl, c010, a2.wh * c011);
+        const float l10 = fmaf(a2.wl, c100, a2.wh * c101), l11 = fmaf(a2.wl, c110, a2.wh * c111);
+        const float m0 = fmaf(a1.wl, l00, a1.wh * l01), m1 = fmaf(a1.wl, l10, a1.wh * l11);
+        out = fmaf(a0.wl, m0, a0.wh * m1);
+    }
+    out = fmaf(-dt, gdv, out);
+    dm_out[idx] = LAST ? lam_scale * out : out;
+}
+
 // d4 = (d0, d1, d2, 0) per voxel from the planar displacement.
 __global__ void k_pack_d4(const float *__restrict__ d, float4 *__restrict__ d4, long long V) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V;
@@ -1135,7 +1179,7 @@ void launch_adjoint_t(const blr_plan *P, const float *lin, const float *mn, floa
                       const float *Gn, cudaStream_t s) {
     if (P->sweep_wide) {
         const BalGeom g = bal_geom(P, P->bal_adj ? P->bal_adj : ADJ_BLOCKS, AJ);
-        if (Gn)
+        if (Gn && P->adj_useg)
             k_adjoint_wide<FIRST, WRITE_LAM, true><<<g.G, MT, ADJW_SMEM_G, s>>>(
                 lin, mn, P->d4, lout, b, P->dt, P->grid, g.ntk, g.W, Gn);
         else
@@ -1163,9 +1207,14 @@ void launch_adjoint(const blr_plan *P, bool first, bool wlam, const float *lin, 
 template <bool FIRST, bool LAST>
 void launch_incstate_t(const blr_plan *P, const float *din, const float *mn, float *dout,
                        float lam_scale, const float *Gn, cudaStream_t s, bool wide) {
-    if (wide && P->sweep_wide) {
+    if (wide && P->sweep_wide && Gn && P->inc_mode == 2) {
+        const dim3 grid((unsigned)ceil_div_ll(P->N3, MK), (unsigned)ceil_div_ll(P->N2, MJ),
+                        (unsigned)P->N1);
+        k_incstate_gather<FIRST, LAST><<<grid, MT, 0, s>>>(din, P->d4, P->dv, Gn, dout, P->dt,
+                                                           lam_scale, P->grid);
+    } else if (wide && P->sweep_wide) {
         const BalGeom b = bal_geom(P, P->bal_inc ? P->bal_inc : INC_BLOCKS, AJ);
-        if (Gn)
+        if (Gn && P->inc_mode == 1)
             k_incstate_wide<FIRST, LAST, true><<<b.G, MT, incw_smem<FIRST, true>(), s>>>(
                 din, mn, P->d4, P->dv, dout, P->dt, lam_scale, P->grid, b.ntk, b.W, Gn);
         else
@@ -1332,17 +1381,21 @@ int time_step(blr_plan *P, int kind, cudaStream_t s) {
 
 }  // namespace
 
-// Autotuner: for the adjoint and the incremental-state kernels, time an
-// interior step on the plan's own buffers for each candidate shape and keep the
-// fastest: chunked grids (the one-wave chunk of sweep_setup and 4, 8, 16, 32
-// planes) and balanced grids of 1 .. (blocks resident per SM) blocks per SM.
-// The best chunked chunk is kept either way (batched launches use it).
+// Autotuner: time one interior step of each candidate shape on the plan's own
+// buffers and keep the fastest.
+//   march kernels (state and incremental state; batched launches use their
+//   chunk): chunked grids (the one-wave chunk of sweep_setup and 4, 8, 16, 32
+//   planes) and balanced grids of 1 .. (blocks resident per SM) blocks per SM;
+//   adjoint: the wide-copy kernel with and without the kept gradient, on
+//   balanced grids (or the march kernel's shapes when N3 % 4 != 0);
+//   incremental state: the wide-copy kernel with and without the kept gradient
+//   on balanced grids, and the gather kernel.
 int sweep_autotune(blr_plan *P, cudaStream_t s) {
     cudaEvent_t e0, e1;
     BLR_CK(cudaEventCreate(&e0));
     BLR_CK(cudaEventCreate(&e1));
     int rc = BLR_OK;
-    auto time_shape = [&](int kind, float *out) {
+    auto time_shape = [&](int kind) {
         float tot = 0.f;
         for (int rep = 0; rep < 3 && !rc; ++rep) {
             if (cudaEventRecord(e0, s) != cudaSuccess) rc = BLR_ECUDA;
@@ -1354,56 +1407,77 @@ int sweep_autotune(blr_plan *P, cudaStream_t s) {
             if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = BLR_ECUDA;
             if (rep > 0) tot += ms;   // the first run warms up
         }
-        *out = tot;
+        return rc ? 1e30f : tot;
     };
-    for (int kind = 1; kind <= 2 && !rc; ++kind) {
+    // chunked and balanced shapes of a march kind (1 adjoint, 2 incremental state)
+    auto tune_march = [&](int kind) {
         int &bal = kind == 1 ? P->bal_adj : P->bal_sweep;
         bal = 0;
-        // the wide-copy adjoint runs on balanced grids only
-        const bool bal_only = kind == 1 && P->sweep_wide;
         const int heur = sweep_chunk(P, kind);
         const int cands[5] = {heur, 4, 8, 16, 32};
         float best = 1e30f;
         int best_ch = heur;
-        for (int c = 0; c < 5 && !rc && !bal_only; ++c) {
+        for (int c = 0; c < 5 && !rc; ++c) {
             const int ch = cands[c] < P->N1 ? cands[c] : P->N1;
             if (c > 0 && ch == heur) continue;
             sweep_set_chunk(P, kind, ch);
-            float t = 0.f;
-            time_shape(kind, &t);
+            const float t = time_shape(kind);
             if (t < best) {
                 best = t;
                 best_ch = ch;
             }
         }
         sweep_set_chunk(P, kind, best_ch);
-        int best_bal = bal_only ? sweep_blocks_per_sm(kind) : 0;
+        int best_bal = 0;
         for (int bps = 1; bps <= sweep_blocks_per_sm(kind) && !rc; ++bps) {
             bal = bps;
-            float t = 0.f;
-            time_shape(kind, &t);
+            const float t = time_shape(kind);
             if (t < best) {
                 best = t;
                 best_bal = bps;
             }
         }
         bal = best_bal;
-    }
-    // blocks per SM of the wide-copy incremental-state grid
+    };
+    P->adj_useg = 0;
+    P->inc_mode = 0;
     P->bal_inc = 0;
+    if (!P->sweep_wide) {
+        tune_march(1);
+    } else {
+        float best = 1e30f;
+        int best_u = 0, best_b = ADJ_BLOCKS;
+        for (int u = P->Gm ? 1 : 0; u >= 0 && !rc; --u)
+            for (int bps = 1; bps <= ADJ_BLOCKS && !rc; ++bps) {
+                P->adj_useg = u;
+                P->bal_adj = bps;
+                const float t = time_shape(1);
+                if (t < best) {
+                    best = t;
+                    best_u = u;
+                    best_b = bps;
+                }
+            }
+        P->adj_useg = best_u;
+        P->bal_adj = best_b;
+    }
+    if (!rc) tune_march(2);
     if (P->sweep_wide && !rc) {
         float best = 1e30f;
-        int best_bps = INC_BLOCKS;
-        for (int bps = 1; bps <= INC_BLOCKS && !rc; ++bps) {
-            P->bal_inc = bps;
-            float t = 0.f;
-            time_shape(3, &t);
-            if (t < best) {
-                best = t;
-                best_bps = bps;
+        int best_m = 0, best_b = INC_BLOCKS;
+        for (int mode = P->Gm ? 2 : 0; mode >= 0 && !rc; --mode)
+            for (int bps = 1; bps <= (mode == 2 ? 1 : INC_BLOCKS) && !rc; ++bps) {
+                P->inc_mode = mode;
+                P->bal_inc = bps;
+                const float t = time_shape(3);
+                if (t < best) {
+                    best = t;
+                    best_m = mode;
+                    best_b = bps;
+                }
             }
-        }
-        P->bal_inc = best_bps;
+        P->inc_mode = best_m;
+        P->bal_inc = best_b;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
