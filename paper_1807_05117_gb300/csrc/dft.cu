@@ -57,37 +57,67 @@ __global__ void k_regulariser(float *A, int N1, int N2, int N3, int B1, int B2, 
 }
 
 // ---------------------------------------------------------------------------
-// stage A: axis 3, band -> grid.  One thread per (row, x3); rows = 3*B1*B2.
-constexpr int EA_ROWS = 8;
-__global__ void __launch_bounds__(128)
+// stage A: axis 3, band -> grid.  A block owns XR rows (c, k1, k2) and XC x3
+// columns; the rows' coefficients and the E3 table for those columns are staged
+// in shared memory and each thread accumulates a 2 (rows) x 4 (x3, 32 apart)
+// register tile over k3 in order.
+constexpr int XR = 16, XC = 128;
+__global__ void __launch_bounds__(256)
 k_expand_axis3(const float *__restrict__ vt, const float *__restrict__ T3c,
                const float *__restrict__ T3s, float *__restrict__ out,
                int rows, int B2, int B3, int N3) {
-    extern __shared__ float sh[];   // EA_ROWS * B3 * 2
-    int row0 = blockIdx.x * EA_ROWS;
-    for (int i = threadIdx.x; i < EA_ROWS * B3 * 2; i += blockDim.x) {
-        int r = row0 + i / (2 * B3);
-        sh[i] = r < rows ? vt[(long long)row0 * B3 * 2 + i] : 0.f;
+    extern __shared__ float2 sh2[];
+    float2 *sc = sh2;                // [XR][B3] coefficients
+    float2 *st = sh2 + XR * B3;      // [B3][XC] (cos, sin)
+    const int r0 = blockIdx.x * XR, x0 = blockIdx.y * XC;
+    for (int i = threadIdx.x; i < XR * B3; i += 256) {
+        const int rr = i / B3, k3 = i - rr * B3, row = r0 + rr;
+        const long long o = ((long long)row * B3 + k3) * 2;
+        sc[i] = row < rows ? make_float2(vt[o], vt[o + 1]) : make_float2(0.f, 0.f);
+    }
+    for (int i = threadIdx.x; i < B3 * XC; i += 256) {
+        const int k3 = i / XC, x = x0 + (i - k3 * XC);
+        st[i] = x < N3 ? make_float2(__ldg(T3c + (long long)k3 * N3 + x), __ldg(T3s + (long long)k3 * N3 + x))
+                       : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    int x3 = blockIdx.y * blockDim.x + threadIdx.x;
-    if (x3 >= N3) return;
-    for (int r = 0; r < EA_ROWS; ++r) {
-        int row = row0 + r;
-        if (row >= rows) break;
-        float re = 0.f, im = 0.f;
-        for (int k3 = 0; k3 < B3; ++k3) {
-            float c = __ldg(T3c + (long long)k3 * N3 + x3);
-            float s = __ldg(T3s + (long long)k3 * N3 + x3);
-            float vr = sh[(r * B3 + k3) * 2], vi = sh[(r * B3 + k3) * 2 + 1];
-            re = fmaf(vr, c, fmaf(-vi, s, re));
-            im = fmaf(vr, s, fmaf(vi, c, im));
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float are[2][4], aim[2][4];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) are[r][q] = aim[r][q] = 0.f;
+    for (int k3 = 0; k3 < B3; ++k3) {
+        const float2 v[2] = {sc[(2 * w) * B3 + k3], sc[(2 * w + 1) * B3 + k3]};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 e = st[k3 * XC + lane + 32 * q];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {   // (vr + i vi)(c + i s)
+                are[r][q] = fmaf(v[r].x, e.x, fmaf(-v[r].y, e.y, are[r][q]));
+                aim[r][q] = fmaf(v[r].x, e.y, fmaf(v[r].y, e.x, aim[r][q]));
+            }
         }
-        int slab = row / B2, k2 = row - slab * B2;
-        out[((long long)(slab * 2 + 0) * B2 + k2) * N3 + x3] = re;
-        out[((long long)(slab * 2 + 1) * B2 + k2) * N3 + x3] = im;
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int row = r0 + 2 * w + r;
+        if (row >= rows) continue;
+        const int slab = row / B2, k2 = row - slab * B2;
+        float *ore = out + ((long long)(slab * 2 + 0) * B2 + k2) * N3;
+        float *oim = out + ((long long)(slab * 2 + 1) * B2 + k2) * N3;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int x = x0 + lane + 32 * q;
+            if (x < N3) {
+                ore[x] = are[r][q];
+                oim[x] = aim[r][q];
+            }
+        }
     }
 }
+
+size_t expand_axis3_smem(int B3) { return (size_t)(XR * B3 + B3 * XC) * sizeof(float2); }
 
 // ---------------------------------------------------------------------------
 // stage B (SIGN = +1, expand) and stage B' (SIGN = -1, project): per slab,
@@ -232,78 +262,76 @@ k_gemm_axis1(const float *__restrict__ A, int lda, const float *__restrict__ B,
 }
 
 // ---------------------------------------------------------------------------
-// stage A': axis 3, grid -> band.  Block: 8 rows (one per warp) x all k3;
-// x3 in chunks of 32.
-//   out[row][k3] = sum_x3 (c - i s)[k3][x3] P2[row][x3]  (+ A * vadd)
-constexpr int PA_ROWS = 8;
+// stage A': axis 3, grid -> band (+ A * vadd).  A block owns XR rows and every
+// k3; x3 runs in chunks of XC staged in shared memory together with the
+// conjugate table, transposed to [x3][k3] so that the lanes (one k3 each, two
+// when B3 > 32) read consecutive words.  Each thread accumulates 2 rows over x3
+// in order.
+constexpr int PXC = 128;
 __global__ void __launch_bounds__(256)
 k_project_axis3(const float *__restrict__ in, const float *__restrict__ T3c,
                 const float *__restrict__ T3s, float *__restrict__ out,
                 const float *__restrict__ Aw, const float *__restrict__ vadd,
                 int rows, int B2, int B3, int N3, int nb12) {
-    __shared__ float pre[PA_ROWS][33], pim[PA_ROWS][33];
-    __shared__ float tc[32][65], ts[32][65];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int row0 = blockIdx.x * PA_ROWS;
-    const int nk = (B3 + 31) / 32;     // k3 sub-blocks per lane (B3 <= 64)
-    constexpr int RW = PA_ROWS / 8;    // rows per warp
-    float are[RW][2], aim[RW][2];
+    extern __shared__ float2 sh2[];
+    const int B3p = B3 + 1;
+    float2 *sp = sh2;                // [XR][PXC] (re, im) of the rows
+    float2 *st = sh2 + XR * PXC;     // [PXC][B3p] (cos, sin)
+    const int r0 = blockIdx.x * XR;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nk = (B3 + 31) / 32;   // k3 per lane (B3 <= 64)
+    float are[2][2], aim[2][2];
 #pragma unroll
-    for (int r = 0; r < RW; ++r)
+    for (int r = 0; r < 2; ++r)
 #pragma unroll
         for (int t = 0; t < 2; ++t) are[r][t] = aim[r][t] = 0.f;
-    for (int x0 = 0; x0 < N3; x0 += 32) {
-        for (int i = tid; i < PA_ROWS * 32; i += 256) {
-            int rr = i >> 5, xx = i & 31;
-            int row = row0 + rr, gx = x0 + xx;
+    for (int x0 = 0; x0 < N3; x0 += PXC) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < XR * PXC; i += 256) {
+            const int rr = i / PXC, x = x0 + (i - rr * PXC), row = r0 + rr;
             float a = 0.f, b = 0.f;
-            if (row < rows && gx < N3) {
-                int slab = row / B2, k2 = row - slab * B2;
-                a = in[((long long)(slab * 2 + 0) * B2 + k2) * N3 + gx];
-                b = in[((long long)(slab * 2 + 1) * B2 + k2) * N3 + gx];
+            if (row < rows && x < N3) {
+                const int slab = row / B2, k2 = row - slab * B2;
+                a = in[((long long)(slab * 2 + 0) * B2 + k2) * N3 + x];
+                b = in[((long long)(slab * 2 + 1) * B2 + k2) * N3 + x];
             }
-            pre[rr][xx] = a;
-            pim[rr][xx] = b;
+            sp[i] = make_float2(a, b);
         }
-        for (int i = tid; i < 32 * 64; i += 256) {
-            int xx = i & 31, kk = i >> 5;
-            int gx = x0 + xx;
-            float c = 0.f, s = 0.f;
-            if (kk < B3 && gx < N3) {
-                c = T3c[(long long)kk * N3 + gx];
-                s = T3s[(long long)kk * N3 + gx];
-            }
-            tc[xx][kk] = c;
-            ts[xx][kk] = s;
+        for (int i = threadIdx.x; i < B3 * PXC; i += 256) {
+            const int k3 = i / PXC, xx = i - k3 * PXC, x = x0 + xx;
+            st[xx * B3p + k3] = x < N3 ? make_float2(__ldg(T3c + (long long)k3 * N3 + x),
+                                                     __ldg(T3s + (long long)k3 * N3 + x))
+                                       : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        for (int xx = 0; xx < 32; ++xx) {
+        const int xn = min(PXC, N3 - x0);
+        for (int xx = 0; xx < xn; ++xx) {
+            const float2 p[2] = {sp[(2 * w) * PXC + xx], sp[(2 * w + 1) * PXC + xx]};
 #pragma unroll
             for (int t = 0; t < 2; ++t) {
                 if (t >= nk) break;
-                float c = tc[xx][lane + 32 * t], s = ts[xx][lane + 32 * t];
+                // lanes past the last k3 read a valid entry; their sums are not stored
+                const float2 e = st[xx * B3p + min(lane + 32 * t, B3 - 1)];
 #pragma unroll
-                for (int r = 0; r < RW; ++r) {
-                    float pr = pre[warp * RW + r][xx], pi = pim[warp * RW + r][xx];
-                    are[r][t] = fmaf(c, pr, fmaf(s, pi, are[r][t]));
-                    aim[r][t] = fmaf(c, pi, fmaf(-s, pr, aim[r][t]));
+                for (int r = 0; r < 2; ++r) {   // (c - i s)(pr + i pi)
+                    are[r][t] = fmaf(e.x, p[r].x, fmaf(e.y, p[r].y, are[r][t]));
+                    aim[r][t] = fmaf(e.x, p[r].y, fmaf(-e.y, p[r].x, aim[r][t]));
                 }
             }
         }
-        __syncthreads();
     }
 #pragma unroll
-    for (int r = 0; r < RW; ++r) {
-        int row = row0 + warp * RW + r;
+    for (int r = 0; r < 2; ++r) {
+        const int row = r0 + 2 * w + r;
         if (row >= rows) continue;
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
-            int k3 = lane + 32 * t;
+            const int k3 = lane + 32 * t;
             if (t >= nk || k3 >= B3) continue;
-            long long o = ((long long)row * B3 + k3) * 2;
+            const long long o = ((long long)row * B3 + k3) * 2;
             float re = are[r][t], im = aim[r][t];
             if (vadd) {
-                float a = Aw[(long long)(row % nb12) * B3 + k3];
+                const float a = Aw[(long long)(row % nb12) * B3 + k3];
                 re = fmaf(a, vadd[o], re);
                 im = fmaf(a, vadd[o + 1], im);
             }
@@ -312,6 +340,8 @@ k_project_axis3(const float *__restrict__ in, const float *__restrict__ T3c,
         }
     }
 }
+
+size_t project_axis3_smem(int B3) { return (size_t)(XR * PXC + PXC * (B3 + 1)) * sizeof(float2); }
 
 }  // namespace
 
@@ -332,9 +362,10 @@ int dft_init_tables(blr_plan *P, cudaStream_t s) {
 int dft_expand(blr_plan *P, const float *vt, float *out, int mode, cudaStream_t s) {
     const int rows = 3 * P->B1 * P->B2;
     // stage A
-    dim3 ga((unsigned)ceil_div_ll(rows, EA_ROWS), (unsigned)ceil_div_ll(P->N3, 128));
-    k_expand_axis3<<<ga, 128, EA_ROWS * P->B3 * 2 * sizeof(float), s>>>(
-        vt, P->T3c, P->T3s, P->dft_small, rows, P->B2, P->B3, P->N3);
+    dim3 ga((unsigned)ceil_div_ll(rows, XR), (unsigned)ceil_div_ll(P->N3, XC));
+    const size_t sa = expand_axis3_smem(P->B3);
+    BLR_CK(cudaFuncSetAttribute(k_expand_axis3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa));
+    k_expand_axis3<<<ga, 256, sa, s>>>(vt, P->T3c, P->T3s, P->dft_small, rows, P->B2, P->B3, P->N3);
     BLR_CK_LAUNCH();
     // stage B
     if (P->tc_tab2_expand) {
@@ -392,7 +423,9 @@ int dft_project(blr_plan *P, const float *f, float *ft, const float *vadd, cudaS
     }
     // stage A'
     const int rows = 3 * P->B1 * P->B2;
-    k_project_axis3<<<(unsigned)ceil_div_ll(rows, PA_ROWS), 256, 0, s>>>(
+    const size_t sp = project_axis3_smem(P->B3);
+    BLR_CK(cudaFuncSetAttribute(k_project_axis3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp));
+    k_project_axis3<<<(unsigned)ceil_div_ll(rows, XR), 256, sp, s>>>(
         P->dft_small, P->T3c, P->T3s, ft, P->A, vadd, rows, P->B2, P->B3, P->N3, P->B1 * P->B2);
     BLR_CK_LAUNCH();
     return BLR_OK;

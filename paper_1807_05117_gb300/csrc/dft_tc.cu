@@ -152,7 +152,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 // t = blockIdx.x, blockIdx.x + gridDim.x, ...; with two staging buffers the next
 // tile's rows stream in (cp.async.bulk) while the current one is converted,
 // multiplied and written.
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TC_THREADS, 2)
 k_tc_axis1(TcArgs p, const __grid_constant__ CUtensorMap xmap) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -481,23 +481,33 @@ size_t tc_smem_bytes(int mtiles, int K, int Kpad, int nt, int nstage) {
            (alias ? 0 : epi) + 3 * 8 + 16;
 }
 
-// Column tile (256 .. 32) and staging depth: the largest tile whose shared
-// memory and TMEM fit and that still gives every SM a tile (when any does),
-// preferring two staging buffers (prefetch) over a larger tile.
+// Blocks of this kernel that fit on one SM with `smem` bytes of dynamic shared
+// memory and `cols` TMEM columns each (registers allow two).
+constexpr size_t TC_SMEM_SM = 228 * 1024, TC_SMEM_RESERVED = 1024;
+int tc_ctas_per_sm(size_t smem, int cols) {
+    return (2 * (smem + TC_SMEM_RESERVED) <= TC_SMEM_SM && 2 * cols <= 512) ? 2 : 1;
+}
+
+// Column tile (256 .. 32) and staging depth.  In order of preference: a shape
+// with two blocks per SM whose tiles fill both; a shape whose tiles give every
+// SM one; any shape that fits.  Within each, two staging buffers (prefetch)
+// before one, then the larger tile.
 bool tc_shape(int mtiles, int K, int Kpad, long long ncols, int nbatch, int sms, int *ntile,
               int *nstage, size_t *smem) {
-    for (int pass = 0; pass < 2; ++pass)
+    for (int pass = 0; pass < 3; ++pass)
         for (int ns = 2; ns >= 1; --ns)
             for (int nt = 256; nt >= 32; nt >>= 1) {
                 if (mtiles * nt > 512) continue;
-                if (pass == 0 && ceil_div_ll(ncols, nt) * nbatch < sms) continue;
                 const size_t sb = tc_smem_bytes(mtiles, K, Kpad, nt, ns);
-                if (sb <= TC_SMEM_MAX) {
-                    *ntile = nt;
-                    *nstage = ns;
-                    *smem = sb;
-                    return true;
-                }
+                if (sb > TC_SMEM_MAX) continue;
+                const long long tiles = ceil_div_ll(ncols, nt) * nbatch;
+                const int cps = tc_ctas_per_sm(sb, pow2_at_least(mtiles * nt));
+                if (pass == 0 && (cps < 2 || tiles < 2LL * sms)) continue;
+                if (pass == 1 && tiles < sms) continue;
+                *ntile = nt;
+                *nstage = ns;
+                *smem = sb;
+                return true;
             }
     return false;
 }
@@ -616,7 +626,8 @@ int tc_run(blr_plan *P, int kind, const float *X, float *D, float scale, int mod
     a.mode = mode;
     a.status = P->dstatus;
     BLR_CK(cudaFuncSetAttribute(k_tc_axis1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = a.tiles < sms ? a.tiles : sms;
+    const int slots = tc_ctas_per_sm(smem, a.tmem_cols) * sms;
+    const int grid = a.tiles < slots ? a.tiles : slots;
     k_tc_axis1<<<grid, TC_THREADS, smem, s>>>(a, xmap);
     BLR_CK_LAUNCH();
     return BLR_OK;
