@@ -488,22 +488,21 @@ int tc_ctas_per_sm(size_t smem, int cols) {
     return (2 * (smem + TC_SMEM_RESERVED) <= TC_SMEM_SM && 2 * cols <= 512) ? 2 : 1;
 }
 
-// Column tile (256 .. 32) and staging depth.  In order of preference: a shape
-// with two blocks per SM whose tiles fill both; a shape whose tiles give every
-// SM one; any shape that fits.  Within each, two staging buffers (prefetch)
-// before one, then the larger tile.
+// Column tile (256 .. 32) and staging depth: two staging buffers (the next
+// tile's load overlaps the current tile's work) before one, then the largest
+// tile that fits and still gives every SM a tile (else the largest that fits).
+// A shape whose shared memory and TMEM allow two blocks per SM gets a grid of
+// two blocks per SM (tc_run).
 bool tc_shape(int mtiles, int K, int Kpad, long long ncols, int nbatch, int sms, int *ntile,
               int *nstage, size_t *smem) {
-    for (int pass = 0; pass < 3; ++pass)
+    for (int pass = 0; pass < 2; ++pass)
         for (int ns = 2; ns >= 1; --ns)
             for (int nt = 256; nt >= 32; nt >>= 1) {
                 if (mtiles * nt > 512) continue;
                 const size_t sb = tc_smem_bytes(mtiles, K, Kpad, nt, ns);
                 if (sb > TC_SMEM_MAX) continue;
                 const long long tiles = ceil_div_ll(ncols, nt) * nbatch;
-                const int cps = tc_ctas_per_sm(sb, pow2_at_least(mtiles * nt));
-                if (pass == 0 && (cps < 2 || tiles < 2LL * sms)) continue;
-                if (pass == 1 && tiles < sms) continue;
+                if (pass == 0 && tiles < sms) continue;
                 *ntile = nt;
                 *nstage = ns;
                 *smem = sb;

@@ -910,39 +910,29 @@ incstate_tile_w(const float *__restrict__ dm_in, const float *__restrict__ m_n,
     };
     issue(i0 - 1, 0);
     issue(i0, 1);
-    float4 dd[ARJ];        // d of the output voxels (plane s - 1)
-    float vv[ARJ][3];      // dv of the output voxels
-    float gg[ARJ][3];      // (USEG) grad m^n of the output voxels
-#pragma unroll
-    for (int jj = 0; jj < ARJ; ++jj) {
-        dd[jj] = make_float4(0.f, 0.f, 0.f, 0.f);
-        vv[jj][0] = vv[jj][1] = vv[jj][2] = 0.f;
-        gg[jj][0] = gg[jj][1] = gg[jj][2] = 0.f;
-    }
-    for (int s = i0 - 1; s <= i_end; ++s) {
+    // Per-voxel operands of one plane: d, dv and (USEG) grad m^n of the thread's
+    // two voxels.  Two sets alternate (the plane loop is unrolled by two), so the
+    // operands of plane s are loaded into one set while plane s - 1 is computed
+    // from the other, with no register copy that would wait for the loads.
+    struct Ops {
+        float4 d[ARJ];
+        float v[ARJ][3], g[ARJ][3];
+    };
+    Ops A, B;
+    auto plane_step = [&](int s, const Ops &cur, Ops &nxt) {
         const int r = s - i0 + 1;
         cp_wait1();
         __syncthreads();
         issue(s + 2, r + 2);
-        // the next output voxels' operands are loaded before this plane's work,
-        // which then hides their latency
-        float4 nd[ARJ];
-        float nv[ARJ][3], ng[ARJ][3];
 #pragma unroll
         for (int jj = 0; jj < ARJ; ++jj) {
-            nd[jj] = dd[jj];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                nv[jj][a] = vv[jj][a];
-                ng[jj][a] = gg[jj][a];
-            }
             if (kin && jb + jj < g.N2 && s >= i0 && s < i_end) {
                 const long long nidx = (long long)s * plane + (long long)(jb + jj) * g.N3 + k;
-                if (!(FIRST && USEG)) nd[jj] = __ldg(d4 + nidx);   // cell of dm^n (and m^n)
+                if (!(FIRST && USEG)) nxt.d[jj] = __ldg(d4 + nidx);   // cell of dm^n (and m^n)
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    nv[jj][a] = __ldg(dv + a * g.V + nidx);
-                    if (USEG) ng[jj][a] = __ldg(Gn + a * g.V + nidx);
+                    nxt.v[jj][a] = __ldg(dv + a * g.V + nidx);
+                    if (USEG) nxt.g[jj][a] = __ldg(Gn + a * g.V + nidx);
                 }
             }
         }
@@ -954,17 +944,17 @@ incstate_tile_w(const float *__restrict__ dm_in, const float *__restrict__ m_n,
                 if (j < g.N2) {
                     const long long idx = (long long)o * plane + (long long)j * g.N3 + k;
                     const int hj = 1 + ARJ * w + jj;
-                    const AxisW a0 = axis_weights(dd[jj].x);
-                    const AxisW a1 = axis_weights(dd[jj].y);
-                    const AxisW a2 = axis_weights(dd[jj].z);
+                    const AxisW a0 = axis_weights(cur.d[jj].x);
+                    const AxisW a1 = axis_weights(cur.d[jj].y);
+                    const AxisW a2 = axis_weights(cur.d[jj].z);
                     // cell planes x1 - 1, x1 (a0.lo < 0) or x1, x1 + 1: ring positions r + 4, r + 5, r
                     const uint32_t s0 = a0.lo < 0 ? (uint32_t)(r + 4) % IM : (uint32_t)(r + 5) % IM;
                     const uint32_t s1 = a0.lo < 0 ? (uint32_t)(r + 5) % IM : (uint32_t)r % IM;
                     float G[3];
                     if (USEG) {
-                        G[0] = gg[jj][0];
-                        G[1] = gg[jj][1];
-                        G[2] = gg[jj][2];
+                        G[0] = cur.g[jj][0];
+                        G[1] = cur.g[jj][1];
+                        G[2] = cur.g[jj][2];
                     } else {
                         trilinear2<true, BW>(RM + s0 * IPL, RM + s1 * IPL, hj, hk, a0, a1, a2, G);
                     }
@@ -972,21 +962,19 @@ incstate_tile_w(const float *__restrict__ dm_in, const float *__restrict__ m_n,
                     if (!FIRST)
                         out = trilinear2<false, BW>(RD + s0 * IPL, RD + s1 * IPL, hj, hk, a0, a1,
                                                     a2, nullptr);
-                    const float gdv = fmaf(G[0], vv[jj][0], fmaf(G[1], vv[jj][1], G[2] * vv[jj][2]));
+                    const float gdv =
+                        fmaf(G[0], cur.v[jj][0], fmaf(G[1], cur.v[jj][1], G[2] * cur.v[jj][2]));
                     out = fmaf(-dt, gdv, out);
                     dm_out[idx] = LAST ? lam_scale * out : out;
                 }
             }
         }
-#pragma unroll
-        for (int jj = 0; jj < ARJ; ++jj) {
-            dd[jj] = nd[jj];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                vv[jj][a] = nv[jj][a];
-                gg[jj][a] = ng[jj][a];
-            }
-        }
+    };
+    // the first step (s = i0 - 1) computes nothing, so set A is read only after
+    // plane i0 has been loaded into it
+    for (int s = i0 - 1; s <= i_end; s += 2) {
+        plane_step(s, A, B);
+        if (s + 1 <= i_end) plane_step(s + 1, B, A);
     }
 }
 
