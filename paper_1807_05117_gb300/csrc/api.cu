@@ -85,6 +85,7 @@ size_t layout(blr_plan *P, char *base) {
     for (float **v : vecs) *v = a.take<float>(P->nfloat);
     P->dsc = a.take<double>(SC_COUNT);
     P->dstatus = a.take<int>(1);
+    P->pcg_live = a.take<int>(4);
     P->ticket = a.take<unsigned int>(1);
     P->partials = a.take<double>(P->npart);
     P->partials2 = a.take<double>(reduce_partials_needed());
@@ -140,37 +141,67 @@ int hessvec_here(blr_plan *P, const float *dvt, float *hdv, cudaStream_t s) {
     return dft_project(P, P->b, hdv, dvt, s);
 }
 
+// PCG (Eq. 55).  The stopping test runs on the device (k_pcg_update), so the
+// host queues iteration j + 1 before it looks at iteration j - 1's flag: the GPU
+// always has an iteration queued and no iteration waits for a host round trip.
+// When the solve stops, the one iteration queued past the stop does nothing
+// but a Hessian-vector product into scratch (its update and direction see the
+// flag).  Kernels, order and stopping rule are those of the loop written with a
+// host test after every update, so the iterates are identical.
 int pcg_run(blr_plan *P, const float *rhs, float *x, int maxit, double eta, int *iters,
             double *relres, int *n_hv, cudaStream_t s) {
     int rc = pcg_init(P, rhs, x, s);
     if (rc) return rc;
     if ((rc = fetch_scalars(P, s, nullptr))) return rc;
     const double rr0 = P->hsc[SC_RR0];
-    int it = 0;
-    double rel = rr0 > 0 ? 1.0 : 0.0;
-    rc = BLR_OK;
-    while (rr0 > 0 && it < maxit) {
-        if ((rc = hessvec_here(P, P->pv, P->q, s))) break;
-        if (n_hv) ++*n_hv;
-        if ((rc = vec_dot(P, P->pv, P->q, nullptr, P->dsc + SC_PQ, s))) break;
-        if ((rc = pcg_update(P, x, s))) break;
-        if ((rc = fetch_scalars(P, s, nullptr))) break;
-        if (!(P->hsc[SC_PQ] > 0)) {
-            rc = isfinite(P->hsc[SC_PQ]) ? BLR_ECURV : BLR_ENAN;
-            break;
-        }
-        ++it;
-        rel = sqrt(P->hsc[SC_RR] / rr0);
-        if (!isfinite(rel)) {
-            rc = BLR_ENAN;
-            break;
-        }
-        if (rel <= eta) break;
-        if ((rc = pcg_direction(P, s))) break;
+    if (!(rr0 > 0) || maxit <= 0) {
+        if (iters) *iters = 0;
+        if (relres) *relres = rr0 > 0 ? 1.0 : 0.0;
+        return BLR_OK;
     }
+    int *start = P->hlive + 8;   // running, no stop code, no updates
+    start[0] = 1;
+    start[1] = PCG_RUN;
+    start[2] = 0;
+    start[3] = 0;
+    BLR_CK(cudaMemcpyAsync(P->pcg_live, start, 4 * sizeof(int), cudaMemcpyHostToDevice, s));
+    cudaEvent_t ev[2];
+    BLR_CK(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    if (cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventDestroy(ev[0]);
+        return BLR_ECUDA;
+    }
+    for (int j = 0; j < maxit && !rc; ++j) {
+        if ((rc = hessvec_here(P, P->pv, P->q, s))) break;
+        if ((rc = vec_dot(P, P->pv, P->q, nullptr, P->dsc + SC_PQ, s))) break;
+        if ((rc = pcg_update(P, x, s, P->pcg_live, eta))) break;
+        if ((rc = pcg_direction(P, s, P->pcg_live))) break;
+        if (cudaMemcpyAsync(P->hlive + 4 * (j & 1), P->pcg_live, 4 * sizeof(int),
+                            cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaEventRecord(ev[j & 1], s) != cudaSuccess) {
+            rc = BLR_ECUDA;
+            break;
+        }
+        if (j >= 1) {
+            if (cudaEventSynchronize(ev[(j - 1) & 1]) != cudaSuccess) {
+                rc = BLR_ECUDA;
+                break;
+            }
+            if (P->hlive[4 * ((j - 1) & 1)] == 0) break;   // stopped by iteration j - 1
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (rc) return rc;
+    BLR_CK(cudaMemcpyAsync(P->hlive, P->pcg_live, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    if ((rc = fetch_scalars(P, s, nullptr))) return rc;   // also waits for the copy above
+    const int code = P->hlive[1], it = P->hlive[2];
+    if (n_hv) *n_hv += it + ((code == PCG_CURV || code == PCG_NAN_PQ) ? 1 : 0);
     if (iters) *iters = it;
-    if (relres) *relres = rel;
-    return rc;
+    if (relres) *relres = it > 0 ? P->hsc[SC_REL] : 1.0;
+    if (code == PCG_CURV) return BLR_ECURV;
+    if (code != PCG_RUN) return BLR_ENAN;
+    return BLR_OK;
 }
 
 int check_plan(blr_plan_t P) { return P ? BLR_OK : BLR_EINVAL; }
@@ -231,10 +262,17 @@ int plan_create(const blr_params *p, bool grad_cache, blr_plan **out) {
         delete P;
         return BLR_ENOMEM;
     }
+    if (cudaMallocHost(&P->hlive, 12 * sizeof(int)) != cudaSuccess) {
+        cudaFreeHost(P->hsc);
+        cudaFree(base);
+        delete P;
+        return BLR_ENOMEM;
+    }
     if (cudaMemset(base, 0, bytes) != cudaSuccess ||
         dft_init_tables(P, 0) != BLR_OK ||
         (p->precision == BLR_MIXED && tc_init_tables(P, 0) != BLR_OK) ||
         sweep_autotune(P, 0) != BLR_OK || cudaDeviceSynchronize() != cudaSuccess) {
+        cudaFreeHost(P->hlive);
         cudaFreeHost(P->hsc);
         cudaFree(base);
         delete P;
@@ -253,6 +291,7 @@ int blr_plan_destroy(blr_plan_t P) {
     cudaSetDevice(P->device);
     cudaError_t e1 = cudaFree(arena_base(P));
     cudaError_t e2 = cudaFreeHost(P->hsc);
+    if (cudaFreeHost(P->hlive) != cudaSuccess) e2 = cudaErrorInvalidValue;
     if (prev >= 0) cudaSetDevice(prev);
     delete P;
     return (e1 == cudaSuccess && e2 == cudaSuccess) ? BLR_OK : BLR_ECUDA;

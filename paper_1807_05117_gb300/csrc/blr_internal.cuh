@@ -32,6 +32,7 @@ enum {
     SC_E = 0, SC_EREG = 1, SC_EDATA = 2,       // energy of blr_state
     SC_RZ = 3, SC_PQ = 4, SC_RR = 5, SC_BETA = 6, SC_RR0 = 7,
     SC_GINF = 8, SC_DOT = 9, SC_ALPHA = 10,
+    SC_REL = 11,                               // ||r|| / ||r0|| after the last PCG update
     SC_COUNT = 16
 };
 
@@ -111,7 +112,9 @@ struct blr_plan {
 
     double *dsc;        // device scalars (SC_COUNT)
     double *hsc;        // pinned host mirror
+    int *hlive;         // pinned: two mirrors of pcg_live (4 ints each) and its start value
     int *dstatus;
+    int *pcg_live;      // device PCG control [running, stop code, updates] (single plans)
     double *partials;   // per-block partial sums
     double *partials2;  // second-level partials (energy)
     const int *active;  // batch member: device flag, 0 freezes PCG updates (else nullptr)
@@ -176,8 +179,13 @@ int energy_finalize(blr_plan *P, const float *vt, double *energy_out, int nblock
 int vec_dot(blr_plan *P, const float *a, const float *b, const float *w, double *out, cudaStream_t s);
 int vec_maxabs(blr_plan *P, const float *a, double *out, cudaStream_t s);
 int pcg_init(blr_plan *P, const float *rhs, float *x, cudaStream_t s);
-int pcg_update(blr_plan *P, float *x, cudaStream_t s);
-int pcg_direction(blr_plan *P, cudaStream_t s);
+// live: nullptr (batch members; the host decides) or P->pcg_live, in which case
+// the update itself decides to stop (curvature, NaN, ||r|| / ||r0|| <= eta) and
+// both kernels do nothing once it has.
+int pcg_update(blr_plan *P, float *x, cudaStream_t s, int *live = nullptr, double eta = 0.0);
+int pcg_direction(blr_plan *P, cudaStream_t s, const int *live = nullptr);
+// PCG stop codes in pcg_live[1]
+enum { PCG_RUN = 0, PCG_CURV = 1, PCG_NAN_PQ = 2, PCG_NAN_REL = 3 };
 // y = a + alpha * x
 int vec_axpy(blr_plan *P, float *y, const float *a, const float *x, double alpha, cudaStream_t s);
 int reduce_partials_needed();

@@ -178,15 +178,27 @@ k_pcg_init(const float *__restrict__ rhs, float *__restrict__ x, float *__restri
 }
 
 // alpha = rz / <p, q>; x += alpha p; r -= alpha q; rz' = <r, r/A>, rr = <r, r>;
-// beta = rz' / rz.
+// beta = rz' / rz.  With `live` (device [running, code, updates]) the kernel
+// also takes the stopping decision of the PCG loop: it does nothing once
+// stopped, stops without updating when <p, q> is not positive (or NaN), and
+// after an update stops when ||r|| / ||r0|| <= eta (or is NaN).
 __global__ void __launch_bounds__(RT)
 k_pcg_update(float *__restrict__ x, float *__restrict__ r, const float *__restrict__ p,
              const float *__restrict__ q, const float *__restrict__ A, long long n, long long nb,
              double *__restrict__ part, unsigned int *ticket, double *__restrict__ sc,
-             const int *active) {
+             const int *active, int *live, double eta) {
     __shared__ double red[RT / 32];
     if (active && *active == 0) return;   // batch member whose PCG has stopped
-    const double alpha_d = sc[SC_RZ] / sc[SC_PQ];
+    if (live && live[0] == 0) return;     // this plan's PCG has stopped
+    const double pq = sc[SC_PQ];
+    if (live && !(pq > 0.0)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            live[1] = isfinite(pq) ? PCG_CURV : PCG_NAN_PQ;
+            live[0] = 0;
+        }
+        return;
+    }
+    const double alpha_d = sc[SC_RZ] / pq;
     const float alpha = (float)alpha_d;
     double rz = 0.0, rr = 0.0;
     for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT) {
@@ -209,6 +221,17 @@ k_pcg_update(float *__restrict__ x, float *__restrict__ r, const float *__restri
             sc[SC_ALPHA] = alpha_d;
             sc[SC_RZ] = rz_new;
             sc[SC_RR] = rr_new;
+            if (live) {
+                const double rel = sqrt(rr_new / sc[SC_RR0]);
+                sc[SC_REL] = rel;
+                live[2] += 1;
+                if (!isfinite(rel)) {
+                    live[1] = PCG_NAN_REL;
+                    live[0] = 0;
+                } else if (rel <= eta) {
+                    live[0] = 0;
+                }
+            }
             *ticket = 0;
         }
     }
@@ -217,8 +240,10 @@ k_pcg_update(float *__restrict__ x, float *__restrict__ r, const float *__restri
 // p = r / A + beta p.
 __global__ void __launch_bounds__(RT)
 k_pcg_direction(float *__restrict__ p, const float *__restrict__ r, const float *__restrict__ A,
-                long long n, long long nb, const double *__restrict__ sc, const int *active) {
+                long long n, long long nb, const double *__restrict__ sc, const int *active,
+                const int *live) {
     if (active && *active == 0) return;
+    if (live && live[0] == 0) return;
     const float beta = (float)sc[SC_BETA];
     for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT)
         p[i] = fmaf(beta, p[i], r[i] / A[coef_index(i, nb)]);
@@ -268,16 +293,16 @@ int pcg_init(blr_plan *P, const float *rhs, float *x, cudaStream_t s) {
     return BLR_OK;
 }
 
-int pcg_update(blr_plan *P, float *x, cudaStream_t s) {
+int pcg_update(blr_plan *P, float *x, cudaStream_t s, int *live, double eta) {
     k_pcg_update<<<vec_blocks(P), RT, 0, s>>>(x, P->r, P->pv, P->q, P->A, P->nfloat, P->nb,
-                                              P->partials, P->ticket, P->dsc, P->active);
+                                              P->partials, P->ticket, P->dsc, P->active, live, eta);
     BLR_CK_LAUNCH();
     return BLR_OK;
 }
 
-int pcg_direction(blr_plan *P, cudaStream_t s) {
+int pcg_direction(blr_plan *P, cudaStream_t s, const int *live) {
     k_pcg_direction<<<vec_blocks(P), RT, 0, s>>>(P->pv, P->r, P->A, P->nfloat, P->nb, P->dsc,
-                                                 P->active);
+                                                 P->active, live);
     BLR_CK_LAUNCH();
     return BLR_OK;
 }

@@ -767,6 +767,54 @@ adjoint_tile_w(const float *__restrict__ lam_in, const float *__restrict__ m_n,
         __syncthreads();
         issue(s + 2, r + 2);
         if (kin) {
+            // the body force of plane s - 1 reads lambda^{n+1}, not lambda^n: it goes
+            // first, so the loads of plane s's b and grad m^n have the whole transpose
+            // to land
+            const int o = s - 1;
+            if (o >= i0) {
+                const float4 *Qo = R.Q + ((r + 3) & (BQ - 1)) * BPL;   // plane s - 1
+                const float *Lo = R.L + ((r + 3) & (BQ - 1)) * BPL;
+                const float *Ma = R.M + ((uint32_t)(r + 4) % BM) * BPL;          // plane s - 2
+                const float *Mb = R.M + ((uint32_t)(r + 5) % BM) * BPL;          // plane s - 1
+                const float *Mc = R.M + ((uint32_t)r % BM) * BPL;                // plane s
+#pragma unroll
+                for (int jj = 0; jj < ARJ; ++jj) {
+                    const int j = jb + jj;
+                    if (j < g.N2) {
+                        const int hj = 1 + ARJ * w + jj;
+                        float G[3];
+                        if (USEG) {
+                            G[0] = gg[jj][0];
+                            G[1] = gg[jj][1];
+                            G[2] = gg[jj][2];
+                        } else {
+                            const float4 q0 = Qo[hj * BW + hk];
+                            const AxisW a0 = axis_weights(q0.x);
+                            trilinear2<true, BW>(a0.lo < 0 ? Ma : Mb, a0.lo < 0 ? Mb : Mc, hj, hk,
+                                                 a0, axis_weights(q0.y), axis_weights(q0.z), G);
+                        }
+                        const float sl = dt * Lo[hj * BW + hk];
+                        const long long idx = (long long)o * plane + (long long)j * g.N3 + k;
+#pragma unroll
+                        for (int a = 0; a < 3; ++a)
+                            b[a * V + idx] = FIRST ? sl * G[a] : fmaf(sl, G[a], bb[jj][a]);
+                    }
+                }
+            }
+            if ((!FIRST || USEG) && s >= i0 && s < i_end) {
+#pragma unroll
+                for (int jj = 0; jj < ARJ; ++jj) {
+                    const int j = jb + jj;
+                    if (j < g.N2) {
+                        const long long nidx = (long long)s * plane + (long long)j * g.N3 + k;
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            if (!FIRST) bb[jj][a] = b[a * V + nidx];
+                            if (USEG) gg[jj][a] = __ldg(Gn + a * V + nidx);
+                        }
+                    }
+                }
+            }
             if (WRITE_LAM) {
                 const float4 *Q = R.Q + (r & (BQ - 1)) * BPL;
                 const float *L = R.L + (r & (BQ - 1)) * BPL;
@@ -800,50 +848,14 @@ adjoint_tile_w(const float *__restrict__ lam_in, const float *__restrict__ m_n,
                     }
                 }
             }
-            const int o = s - 1;
-            if (o >= i0) {
-                const float4 *Qo = R.Q + ((r + 3) & (BQ - 1)) * BPL;   // plane s - 1
-                const float *Lo = R.L + ((r + 3) & (BQ - 1)) * BPL;
-                const float *Ma = R.M + ((uint32_t)(r + 4) % BM) * BPL;          // plane s - 2
-                const float *Mb = R.M + ((uint32_t)(r + 5) % BM) * BPL;          // plane s - 1
-                const float *Mc = R.M + ((uint32_t)r % BM) * BPL;                // plane s
+            // lambda^n of plane s - 1 is complete once plane s has been scattered
+            if (WRITE_LAM && o >= i0) {
 #pragma unroll
                 for (int jj = 0; jj < ARJ; ++jj) {
                     const int j = jb + jj;
-                    if (j < g.N2) {
-                        const int hj = 1 + ARJ * w + jj;
-                        float G[3];
-                        if (USEG) {
-                            G[0] = gg[jj][0];
-                            G[1] = gg[jj][1];
-                            G[2] = gg[jj][2];
-                        } else {
-                            const float4 q0 = Qo[hj * BW + hk];
-                            const AxisW a0 = axis_weights(q0.x);
-                            trilinear2<true, BW>(a0.lo < 0 ? Ma : Mb, a0.lo < 0 ? Mb : Mc, hj, hk,
-                                                 a0, axis_weights(q0.y), axis_weights(q0.z), G);
-                        }
-                        const float sl = dt * Lo[hj * BW + hk];
-                        const long long idx = (long long)o * plane + (long long)j * g.N3 + k;
-#pragma unroll
-                        for (int a = 0; a < 3; ++a)
-                            b[a * V + idx] = FIRST ? sl * G[a] : fmaf(sl, G[a], bb[jj][a]);
-                        if (WRITE_LAM) lam_out[idx] = jj == 0 ? accA.x : accA.y;
-                    }
-                }
-            }
-            if ((!FIRST || USEG) && s >= i0 && s < i_end) {
-#pragma unroll
-                for (int jj = 0; jj < ARJ; ++jj) {
-                    const int j = jb + jj;
-                    if (j < g.N2) {
-                        const long long nidx = (long long)s * plane + (long long)j * g.N3 + k;
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            if (!FIRST) bb[jj][a] = b[a * V + nidx];
-                            if (USEG) gg[jj][a] = __ldg(Gn + a * V + nidx);
-                        }
-                    }
+                    if (j < g.N2)
+                        lam_out[(long long)o * plane + (long long)j * g.N3 + k] =
+                            jj == 0 ? accA.x : accA.y;
                 }
             }
         }
@@ -1370,7 +1382,7 @@ int time_step(blr_plan *P, int kind, cudaStream_t s) {
 }  // namespace
 
 // Autotuner: time one interior step of each candidate shape on the plan's own
-// buffers and keep the fastest.
+// buffers (best of five runs) and keep the fastest.
 //   march kernels (state and incremental state; batched launches use their
 //   chunk): chunked grids (the one-wave chunk of sweep_setup and 4, 8, 16, 32
 //   planes) and balanced grids of 1 .. (blocks resident per SM) blocks per SM;
@@ -1383,9 +1395,11 @@ int sweep_autotune(blr_plan *P, cudaStream_t s) {
     BLR_CK(cudaEventCreate(&e0));
     BLR_CK(cudaEventCreate(&e1));
     int rc = BLR_OK;
+    // the fastest of five timed runs after one warm-up run (the minimum is the
+    // least noisy estimate of a kernel's own time on a shared machine)
     auto time_shape = [&](int kind) {
-        float tot = 0.f;
-        for (int rep = 0; rep < 3 && !rc; ++rep) {
+        float best_ms = 1e30f;
+        for (int rep = 0; rep < 6 && !rc; ++rep) {
             if (cudaEventRecord(e0, s) != cudaSuccess) rc = BLR_ECUDA;
             if (!rc) rc = time_step(P, kind, s);
             if (!rc && (cudaEventRecord(e1, s) != cudaSuccess ||
@@ -1393,9 +1407,9 @@ int sweep_autotune(blr_plan *P, cudaStream_t s) {
                 rc = BLR_ECUDA;
             float ms = 0.f;
             if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = BLR_ECUDA;
-            if (rep > 0) tot += ms;   // the first run warms up
+            if (rep > 0 && ms < best_ms) best_ms = ms;
         }
-        return rc ? 1e30f : tot;
+        return rc ? 1e30f : best_ms;
     };
     // chunked and balanced shapes of a march kind (1 adjoint, 2 incremental state)
     auto tune_march = [&](int kind) {
