@@ -388,7 +388,8 @@ def main_ours(args):
                                  "final_energy": r["rep"].energy,
                                  "pcg_iters": r["rep"].pcg_iters,
                                  "adjoint_step_us": r["roofline"]["launch_us"],
-                                 "hvp_stage_us": r["stage"]}
+                                 "hvp_stage_us": r["stage"],
+                                 "autotuned": r["plan"].tuning()}
                              for p, r in res.items()}}
     plan = head["plan"]
 

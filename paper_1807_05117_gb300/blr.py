@@ -70,6 +70,7 @@ _SIGS = {
     "blr_newton": (_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                    ctypes.POINTER(blr_report), _P),
     "blr_status": (_P, _P),
+    "blr_plan_tuning": (_P, ctypes.POINTER(ctypes.c_int), ctypes.c_int),
     "blr_batch_create": (ctypes.POINTER(blr_params), ctypes.c_int, ctypes.POINTER(_P)),
     "blr_batch_destroy": (_P,),
     "blr_batch_set_images": (_P, ctypes.c_int, _P, _P, _P),
@@ -340,6 +341,16 @@ class Plan:
 
     def status(self, stream=None):
         return blr_status(self.handle, stream)
+
+    TUNING_KEYS = ("wide_sweeps", "grad_kept", "adjoint_blocks_per_sm", "adjoint_reads_grad",
+                   "incremental_form", "incremental_blocks_per_sm", "march_blocks_per_sm",
+                   "march_chunk", "adjoint_march_chunk")
+
+    def tuning(self) -> dict:
+        """The sweep shapes the autotuner chose (blr_plan_tuning)."""
+        vals = (ctypes.c_int * len(self.TUNING_KEYS))()
+        _check(_lib.blr_plan_tuning(_P(self.handle), vals, len(vals)), "blr_plan_tuning")
+        return dict(zip(self.TUNING_KEYS, [int(v) for v in vals]))
 
 
 def _ptr_array(tensors, **kw):

@@ -284,6 +284,14 @@ int plan_create(const blr_params *p, bool grad_cache, blr_plan **out) {
 
 extern "C" {
 
+int blr_plan_tuning(blr_plan_t P, int *vals, int n) {
+    if (!P || !vals) return BLR_EINVAL;
+    const int v[9] = {P->sweep_wide ? 1 : 0, P->Gm ? 1 : 0, P->bal_adj, P->adj_useg,
+                      P->inc_mode, P->bal_inc, P->bal_sweep, P->chunk, P->chunk_adj};
+    for (int i = 0; i < n && i < 9; ++i) vals[i] = v[i];
+    return BLR_OK;
+}
+
 int blr_plan_destroy(blr_plan_t P) {
     if (!P) return BLR_OK;
     int prev = -1;

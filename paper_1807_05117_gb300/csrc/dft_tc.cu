@@ -263,13 +263,15 @@ k_tc_axis1(TcArgs p, const __grid_constant__ CUtensorMap xmap) {
                 issue_tile(t, 0, 0u);   // the only buffer is free again
             }
             const uint32_t use = (p.nstage == 2) ? (uint32_t)(i >> 1) : (uint32_t)i;
-            ok = mbar_wait(bar_load0 + 8u * sb, use & 1u);
+            // one thread waits; the barrier below releases the others (no
+            // polling warps competing for issue slots)
+            ok = tid == 0 ? mbar_wait(bar_load0 + 8u * sb, use & 1u) : true;
             if (!ok) {
                 own_bar = bar_load0 + 8u * sb;
                 own_par = use & 1u;
             }
         } else {
-            if (i == 0) ok = mbar_wait(bar_load0, 0u);   // table
+            if (i == 0 && tid == 0) ok = mbar_wait(bar_load0, 0u);   // table
             for (int e = tid; e < p.K * p.ntile; e += TC_THREADS) {
                 const int k = e / p.ntile, r = e - k * p.ntile;
                 stage[e] = r < w ? __ldg(src + (long long)k * p.ncols + r) : 0.f;
@@ -321,12 +323,12 @@ k_tc_axis1(TcArgs p, const __grid_constant__ CUtensorMap xmap) {
                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                     bar_mma));
         }
-        ok = mbar_wait(bar_mma, (uint32_t)(i & 1));
-        asm volatile("tcgen05.fence::after_thread_sync;");
+        ok = tid == 0 ? mbar_wait(bar_mma, (uint32_t)(i & 1)) : true;
         if (__syncthreads_or(!ok)) {
             if (tid == 0) s_fail = 1;
             break;
         }
+        asm volatile("tcgen05.fence::after_thread_sync;");
         // epilogue: warp w reads TMEM lanes 32*(w%4).. (rows), columns of half w/4,
         // 32 x 32 blocks transposed through an XOR-swizzled buffer so that each
         // store instruction writes 128 contiguous bytes of one output row

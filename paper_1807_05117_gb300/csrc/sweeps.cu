@@ -1381,8 +1381,8 @@ int time_step(blr_plan *P, int kind, cudaStream_t s) {
 
 }  // namespace
 
-// Autotuner: time one interior step of each candidate shape on the plan's own
-// buffers (best of five runs) and keep the fastest.
+// Autotuner: time interior steps of each candidate shape on the plan's own
+// buffers and keep the fastest.
 //   march kernels (state and incremental state; batched launches use their
 //   chunk): chunked grids (the one-wave chunk of sweep_setup and 4, 8, 16, 32
 //   planes) and balanced grids of 1 .. (blocks resident per SM) blocks per SM;
@@ -1395,13 +1395,14 @@ int sweep_autotune(blr_plan *P, cudaStream_t s) {
     BLR_CK(cudaEventCreate(&e0));
     BLR_CK(cudaEventCreate(&e1));
     int rc = BLR_OK;
-    // the fastest of five timed runs after one warm-up run (the minimum is the
-    // least noisy estimate of a kernel's own time on a shared machine)
+    // the fastest of four timed runs of four back-to-back steps (as the sweeps
+    // run) after one warm-up run; the minimum is the least noisy estimate of a
+    // kernel's own time on a shared machine
     auto time_shape = [&](int kind) {
         float best_ms = 1e30f;
-        for (int rep = 0; rep < 6 && !rc; ++rep) {
+        for (int rep = 0; rep < 5 && !rc; ++rep) {
             if (cudaEventRecord(e0, s) != cudaSuccess) rc = BLR_ECUDA;
-            if (!rc) rc = time_step(P, kind, s);
+            for (int q = 0; q < 4 && !rc; ++q) rc = time_step(P, kind, s);
             if (!rc && (cudaEventRecord(e1, s) != cudaSuccess ||
                         cudaEventSynchronize(e1) != cudaSuccess))
                 rc = BLR_ECUDA;

@@ -62,3 +62,5 @@ def test_strerror_and_invalid_params(lib):
     assert lib.blr_plan_destroy(None) == blr.BLR_OK
     assert lib.blr_expand(None, None, None, None) == blr.BLR_EINVAL
     assert lib.blr_hessvec(None, None, None, None) == blr.BLR_EINVAL
+    vals = (ctypes.c_int * 9)()
+    assert lib.blr_plan_tuning(None, vals, 9) == blr.BLR_EINVAL
