@@ -24,6 +24,31 @@ extern unsigned long long g_blr_launches;
         BLR_CK(cudaGetLastError());                                       \
     } while (0)
 
+// Programmatic dependent launch.  launch_pdl lets the kernel start while the
+// previous kernel in the stream drains (block launch and any prologue that
+// reads nothing the previous kernel writes overlap its tail); every kernel
+// launched this way calls pdl_wait() before it touches such data, which returns
+// once the previous grid has completed and its writes are visible.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+#endif
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Device-latched conditions (bit flags in blr_plan::dstatus).
 enum { BLR_FLAG_CFL = 1, BLR_FLAG_NAN = 2, BLR_FLAG_TIMEOUT = 4 };
 

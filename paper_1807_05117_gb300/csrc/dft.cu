@@ -70,15 +70,16 @@ k_expand_axis3(const float *__restrict__ vt, const float *__restrict__ T3c,
     float2 *sc = sh2;                // [XR][B3] coefficients
     float2 *st = sh2 + XR * B3;      // [B3][XC] (cos, sin)
     const int r0 = blockIdx.x * XR, x0 = blockIdx.y * XC;
-    for (int i = threadIdx.x; i < XR * B3; i += 256) {
-        const int rr = i / B3, k3 = i - rr * B3, row = r0 + rr;
-        const long long o = ((long long)row * B3 + k3) * 2;
-        sc[i] = row < rows ? make_float2(vt[o], vt[o + 1]) : make_float2(0.f, 0.f);
-    }
+    pdl_wait();   // the tables may come from the previous kernel (allocation-free expand)
     for (int i = threadIdx.x; i < B3 * XC; i += 256) {
         const int k3 = i / XC, x = x0 + (i - k3 * XC);
         st[i] = x < N3 ? make_float2(__ldg(T3c + (long long)k3 * N3 + x), __ldg(T3s + (long long)k3 * N3 + x))
                        : make_float2(0.f, 0.f);
+    }
+    for (int i = threadIdx.x; i < XR * B3; i += 256) {
+        const int rr = i / B3, k3 = i - rr * B3, row = r0 + rr;
+        const long long o = ((long long)row * B3 + k3) * 2;
+        sc[i] = row < rows ? make_float2(vt[o], vt[o + 1]) : make_float2(0.f, 0.f);
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -280,6 +281,7 @@ k_project_axis3(const float *__restrict__ in, const float *__restrict__ T3c,
     const int r0 = blockIdx.x * XR;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nk = (B3 + 31) / 32;   // k3 per lane (B3 <= 64)
+    pdl_wait();
     float are[2][2], aim[2][2];
 #pragma unroll
     for (int r = 0; r < 2; ++r)
@@ -365,7 +367,8 @@ int dft_expand(blr_plan *P, const float *vt, float *out, int mode, cudaStream_t 
     dim3 ga((unsigned)ceil_div_ll(rows, XR), (unsigned)ceil_div_ll(P->N3, XC));
     const size_t sa = expand_axis3_smem(P->B3);
     BLR_CK(cudaFuncSetAttribute(k_expand_axis3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa));
-    k_expand_axis3<<<ga, 256, sa, s>>>(vt, P->T3c, P->T3s, P->dft_small, rows, P->B2, P->B3, P->N3);
+    launch_pdl(k_expand_axis3, ga, dim3(256), sa, s, vt, (const float *)P->T3c,
+               (const float *)P->T3s, P->dft_small, rows, P->B2, P->B3, P->N3);
     BLR_CK_LAUNCH();
     // stage B
     if (P->tc_tab2_expand) {
@@ -425,8 +428,9 @@ int dft_project(blr_plan *P, const float *f, float *ft, const float *vadd, cudaS
     const int rows = 3 * P->B1 * P->B2;
     const size_t sp = project_axis3_smem(P->B3);
     BLR_CK(cudaFuncSetAttribute(k_project_axis3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp));
-    k_project_axis3<<<(unsigned)ceil_div_ll(rows, XR), 256, sp, s>>>(
-        P->dft_small, P->T3c, P->T3s, ft, P->A, vadd, rows, P->B2, P->B3, P->N3, P->B1 * P->B2);
+    launch_pdl(k_project_axis3, dim3((unsigned)ceil_div_ll(rows, XR)), dim3(256), sp, s,
+               (const float *)P->dft_small, (const float *)P->T3c, (const float *)P->T3s, ft,
+               (const float *)P->A, vadd, rows, P->B2, P->B3, P->N3, P->B1 * P->B2);
     BLR_CK_LAUNCH();
     return BLR_OK;
 }

@@ -226,14 +226,17 @@ k_tc_axis1(TcArgs p, const __grid_constant__ CUtensorMap xmap) {
     };
 
     int first = blockIdx.x;
+    // the table is written once at plan creation (which synchronises the device),
+    // so it is fetched before the wait for the previous kernel in the stream
+    // (programmatic dependent launch); the field tiles after
+    if (warp == 0 && lane == 0) bulk_g2s(smem_u32(sA), p.tab, (uint32_t)all_tab, bar_load0);
+    pdl_wait();
     if (warp == 0) {
         if (p.bulk && first < p.tiles) {
-            if (lane == 0) bulk_g2s(smem_u32(sA), p.tab, (uint32_t)all_tab, bar_load0);
-            issue_tile(first, 0, (uint32_t)all_tab);
+            issue_tile(first, 0, (uint32_t)all_tab);   // arms bar_load0 for table + tile
         } else {
             if (lane == 0) mbar_expect_arrive(bar_load0, (uint32_t)all_tab);
             __syncwarp();
-            if (lane == 0) bulk_g2s(smem_u32(sA), p.tab, (uint32_t)all_tab, bar_load0);
         }
     }
 
@@ -629,7 +632,7 @@ int tc_run(blr_plan *P, int kind, const float *X, float *D, float scale, int mod
     BLR_CK(cudaFuncSetAttribute(k_tc_axis1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int slots = tc_ctas_per_sm(smem, a.tmem_cols) * sms;
     const int grid = a.tiles < slots ? a.tiles : slots;
-    k_tc_axis1<<<grid, TC_THREADS, smem, s>>>(a, xmap);
+    launch_pdl(k_tc_axis1, dim3(grid), dim3(TC_THREADS), smem, s, a, xmap);
     BLR_CK_LAUNCH();
     return BLR_OK;
 }

@@ -630,6 +630,7 @@ k_state_bal(const float *__restrict__ m_in, const float *__restrict__ d,
             float *__restrict__ m_out, Grid3 g, const float *__restrict__ I1,
             float *__restrict__ lam_out, float lam_scale, double *__restrict__ partials, int ntk,
             long long W, float *__restrict__ Gout) {
+    pdl_wait();
     for_segments(g.N1, ntk, W, [&](int kt, int jt, int i0, int len) {
         state_tile<LAST>(m_in, d, m_out, g, len, I1, lam_out, lam_scale, partials, kt * MK,
                          jt * MJ, i0, Gout);
@@ -870,6 +871,7 @@ __global__ void __launch_bounds__(MT, ADJ_BLOCKS)
 k_adjoint_wide(const float *__restrict__ lam_in, const float *__restrict__ m_n,
                const float4 *__restrict__ d4, float *__restrict__ lam_out, float *__restrict__ b,
                float dt, Grid3 g, int ntk, long long W, const float *__restrict__ Gn) {
+    pdl_wait();
     for_segments(g.N1, ntk, W, [&](int kt, int jt, int i0, int len) {
         adjoint_tile_w<FIRST, WRITE_LAM, USEG>(lam_in, m_n, d4, lam_out, b, dt, g, len, kt * MK,
                                                jt * AJ, i0, Gn);
@@ -996,6 +998,7 @@ k_incstate_wide(const float *__restrict__ dm_in, const float *__restrict__ m_n,
                 const float4 *__restrict__ d4, const float *__restrict__ dv,
                 float *__restrict__ dm_out, float dt, float lam_scale, Grid3 g, int ntk,
                 long long W, const float *__restrict__ Gn) {
+    pdl_wait();
     for_segments(g.N1, ntk, W, [&](int kt, int jt, int i0, int len) {
         incstate_tile_w<FIRST, LAST, USEG>(dm_in, m_n, d4, dv, dm_out, dt, lam_scale, g, len,
                                            kt * MK, jt * AJ, i0, Gn);
@@ -1014,6 +1017,7 @@ __global__ void __launch_bounds__(MT)
 k_incstate_gather(const float *__restrict__ dm_in, const float4 *__restrict__ d4,
                   const float *__restrict__ dv, const float *__restrict__ Gn,
                   float *__restrict__ dm_out, float dt, float lam_scale, Grid3 g) {
+    pdl_wait();
     const int k = blockIdx.x * MK + (threadIdx.x & 31);
     const int j = blockIdx.y * MJ + (threadIdx.x >> 5);
     const int i = blockIdx.z;
@@ -1161,8 +1165,8 @@ void launch_state(const blr_plan *P, const float *m_in, float *m_out, const floa
                   float lam_scale, double *partials, float *Gout, cudaStream_t s) {
     if (P->bal_sweep) {
         const BalGeom b = bal_geom(P, P->bal_sweep, MJ);
-        k_state_bal<LAST><<<b.G, MT, 0, s>>>(m_in, P->d, m_out, P->grid, I1, lam_out, lam_scale,
-                                              partials, b.ntk, b.W, Gout);
+        launch_pdl(k_state_bal<LAST>, dim3(b.G), dim3(MT), 0, s, m_in, P->d, m_out, P->grid, I1,
+                   lam_out, lam_scale, partials, b.ntk, b.W, Gout);
     } else {
         k_state_march<LAST><<<sweep_grid(P), MT, 0, s>>>(m_in, P->d, m_out, P->grid, P->chunk, I1,
                                                           lam_out, lam_scale, partials, Gout);
@@ -1180,11 +1184,11 @@ void launch_adjoint_t(const blr_plan *P, const float *lin, const float *mn, floa
     if (P->sweep_wide) {
         const BalGeom g = bal_geom(P, P->bal_adj ? P->bal_adj : ADJ_BLOCKS, AJ);
         if (Gn && P->adj_useg)
-            k_adjoint_wide<FIRST, WRITE_LAM, true><<<g.G, MT, ADJW_SMEM_G, s>>>(
-                lin, mn, P->d4, lout, b, P->dt, P->grid, g.ntk, g.W, Gn);
+            launch_pdl(k_adjoint_wide<FIRST, WRITE_LAM, true>, dim3(g.G), dim3(MT), ADJW_SMEM_G, s,
+                       lin, mn, P->d4, lout, b, P->dt, P->grid, g.ntk, g.W, Gn);
         else
-            k_adjoint_wide<FIRST, WRITE_LAM, false><<<g.G, MT, ADJW_SMEM, s>>>(
-                lin, mn, P->d4, lout, b, P->dt, P->grid, g.ntk, g.W, nullptr);
+            launch_pdl(k_adjoint_wide<FIRST, WRITE_LAM, false>, dim3(g.G), dim3(MT), ADJW_SMEM, s,
+                       lin, mn, P->d4, lout, b, P->dt, P->grid, g.ntk, g.W, (const float *)nullptr);
     } else if (P->bal_adj) {
         const BalGeom g = bal_geom(P, P->bal_adj, AJ);
         k_adjoint_bal<FIRST, WRITE_LAM><<<g.G, MT, ADJ_SMEM, s>>>(lin, mn, P->d, lout, b, P->dt,
@@ -1210,16 +1214,17 @@ void launch_incstate_t(const blr_plan *P, const float *din, const float *mn, flo
     if (wide && P->sweep_wide && Gn && P->inc_mode == 2) {
         const dim3 grid((unsigned)ceil_div_ll(P->N3, MK), (unsigned)ceil_div_ll(P->N2, MJ),
                         (unsigned)P->N1);
-        k_incstate_gather<FIRST, LAST><<<grid, MT, 0, s>>>(din, P->d4, P->dv, Gn, dout, P->dt,
-                                                           lam_scale, P->grid);
+        launch_pdl(k_incstate_gather<FIRST, LAST>, grid, dim3(MT), 0, s, din, P->d4, P->dv, Gn, dout,
+                   P->dt, lam_scale, P->grid);
     } else if (wide && P->sweep_wide) {
         const BalGeom b = bal_geom(P, P->bal_inc ? P->bal_inc : INC_BLOCKS, AJ);
         if (Gn && P->inc_mode == 1)
-            k_incstate_wide<FIRST, LAST, true><<<b.G, MT, incw_smem<FIRST, true>(), s>>>(
-                din, mn, P->d4, P->dv, dout, P->dt, lam_scale, P->grid, b.ntk, b.W, Gn);
+            launch_pdl(k_incstate_wide<FIRST, LAST, true>, dim3(b.G), dim3(MT), incw_smem<FIRST, true>(),
+                       s, din, mn, P->d4, P->dv, dout, P->dt, lam_scale, P->grid, b.ntk, b.W, Gn);
         else
-            k_incstate_wide<FIRST, LAST, false><<<b.G, MT, incw_smem<FIRST, false>(), s>>>(
-                din, mn, P->d4, P->dv, dout, P->dt, lam_scale, P->grid, b.ntk, b.W, nullptr);
+            launch_pdl(k_incstate_wide<FIRST, LAST, false>, dim3(b.G), dim3(MT),
+                       incw_smem<FIRST, false>(), s, din, mn, P->d4, P->dv, dout, P->dt, lam_scale,
+                       P->grid, b.ntk, b.W, (const float *)nullptr);
     } else if (P->bal_sweep) {
         const BalGeom b = bal_geom(P, P->bal_sweep, MJ);
         k_incstate_bal<FIRST, LAST><<<b.G, MT, 0, s>>>(din, mn, P->d, P->dv, dout, P->dt, lam_scale,
