@@ -130,6 +130,7 @@ __global__ void __launch_bounds__(256)
 k_axis2(const float *__restrict__ in, const float *__restrict__ T2c,
         const float *__restrict__ T2s, float *__restrict__ out,
         int in_rows, int out_rows, int N2, int N3) {
+    pdl_wait();
     __shared__ float sre[16][33], sim[16][33];
     __shared__ float sc[16][33], ss[16][33];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -200,6 +201,7 @@ __global__ void __launch_bounds__(256)
 k_gemm_axis1(const float *__restrict__ A, int lda, const float *__restrict__ B,
              long long strideB, float *__restrict__ C, long long strideC,
              int M, int K, long long Ncol, float scale, int *status) {
+    pdl_wait();
     __shared__ __align__(16) float As[16][64];
     __shared__ __align__(16) float Bs[16][128];
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
@@ -376,8 +378,9 @@ int dft_expand(blr_plan *P, const float *vt, float *out, int mode, cudaStream_t 
         if (rc) return rc;
     } else {
         dim3 gb((unsigned)ceil_div_ll(P->N3, 32), (unsigned)ceil_div_ll(P->N2, 32), 3u * P->B1);
-        k_axis2<+1><<<gb, 256, 0, s>>>(P->dft_small, P->T2c, P->T2s, P->dft_big, P->B2, P->N2,
-                                       P->N2, P->N3);
+        launch_pdl(k_axis2<+1>, gb, dim3(256), 0, s, (const float *)P->dft_small,
+                   (const float *)P->T2c, (const float *)P->T2s, P->dft_big, P->B2, P->N2, P->N2,
+                   P->N3);
         BLR_CK_LAUNCH();
     }
     // stage C
@@ -389,13 +392,13 @@ int dft_expand(blr_plan *P, const float *vt, float *out, int mode, cudaStream_t 
     const long long ncol = (long long)P->N2 * P->N3;
     dim3 gc((unsigned)ceil_div_ll(ncol, 128), (unsigned)ceil_div_ll(P->N1, 64), 3u);
     if (mode == 0)
-        k_gemm_axis1<true, 0><<<gc, 256, 0, s>>>(P->W1, P->N1, P->dft_big, 2LL * P->B1 * ncol,
-                                                 out, P->V, P->N1, 2 * P->B1, ncol, 1.f,
-                                                 P->dstatus);
+        launch_pdl(k_gemm_axis1<true, 0>, gc, dim3(256), 0, s, (const float *)P->W1, P->N1,
+                   (const float *)P->dft_big, 2LL * P->B1 * ncol, out, P->V, P->N1, 2 * P->B1, ncol,
+                   1.f, P->dstatus);
     else
-        k_gemm_axis1<true, 1><<<gc, 256, 0, s>>>(P->W1, P->N1, P->dft_big, 2LL * P->B1 * ncol,
-                                                 out, P->V, P->N1, 2 * P->B1, ncol, -P->dt,
-                                                 P->dstatus);
+        launch_pdl(k_gemm_axis1<true, 1>, gc, dim3(256), 0, s, (const float *)P->W1, P->N1,
+                   (const float *)P->dft_big, 2LL * P->B1 * ncol, out, P->V, P->N1, 2 * P->B1, ncol,
+                   -P->dt, P->dstatus);
     BLR_CK_LAUNCH();
     if (mode == 1 && out == P->d) return sweep_pack_d4(P, s);
     return BLR_OK;
@@ -409,9 +412,8 @@ int dft_project(blr_plan *P, const float *f, float *ft, const float *vadd, cudaS
         if (rc) return rc;
     } else {
         dim3 gc((unsigned)ceil_div_ll(ncol, 128), (unsigned)ceil_div_ll(2 * P->B1, 64), 3u);
-        k_gemm_axis1<false, 0><<<gc, 256, 0, s>>>(P->W1, P->N1, f, P->V, P->dft_big,
-                                                  2LL * P->B1 * ncol, 2 * P->B1, P->N1, ncol,
-                                                  1.f, P->dstatus);
+        launch_pdl(k_gemm_axis1<false, 0>, gc, dim3(256), 0, s, (const float *)P->W1, P->N1, f,
+                   P->V, P->dft_big, 2LL * P->B1 * ncol, 2 * P->B1, P->N1, ncol, 1.f, P->dstatus);
         BLR_CK_LAUNCH();
     }
     // stage B'
@@ -420,8 +422,9 @@ int dft_project(blr_plan *P, const float *f, float *ft, const float *vadd, cudaS
         if (rc) return rc;
     } else {
         dim3 gb((unsigned)ceil_div_ll(P->N3, 32), (unsigned)ceil_div_ll(P->B2, 32), 3u * P->B1);
-        k_axis2<-1><<<gb, 256, 0, s>>>(P->dft_big, P->T2c, P->T2s, P->dft_small, P->N2, P->B2,
-                                       P->N2, P->N3);
+        launch_pdl(k_axis2<-1>, gb, dim3(256), 0, s, (const float *)P->dft_big,
+                   (const float *)P->T2c, (const float *)P->T2s, P->dft_small, P->N2, P->B2, P->N2,
+                   P->N3);
         BLR_CK_LAUNCH();
     }
     // stage A'

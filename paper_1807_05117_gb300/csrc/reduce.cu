@@ -60,6 +60,7 @@ k_energy(const double *__restrict__ partials, int np, const float *__restrict__ 
          const float *__restrict__ A, long long nb, double inv_sigma2,
          double *__restrict__ part2, unsigned int *ticket, double *__restrict__ sc,
          double *__restrict__ out, int *status) {
+    pdl_wait();
     __shared__ double red[RT / 32];
     double sd = 0.0;
     for (int i = blockIdx.x * RT + threadIdx.x; i < np; i += gridDim.x * RT) sd += partials[i];
@@ -97,6 +98,7 @@ __global__ void __launch_bounds__(RT)
 k_dot(const float *__restrict__ a, const float *__restrict__ b, const float *__restrict__ w,
       long long n, long long nb, double *__restrict__ part, unsigned int *ticket,
       double *__restrict__ out) {
+    pdl_wait();
     __shared__ double red[RT / 32];
     double acc = 0.0;
     for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT) {
@@ -118,6 +120,7 @@ k_dot(const float *__restrict__ a, const float *__restrict__ b, const float *__r
 __global__ void __launch_bounds__(RT)
 k_maxabs(const float *__restrict__ a, long long n, double *__restrict__ part,
          unsigned int *ticket, double *__restrict__ out) {
+    pdl_wait();
     __shared__ float red[RT / 32];
     float m = 0.f;
     for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT)
@@ -151,6 +154,7 @@ __global__ void __launch_bounds__(RT)
 k_pcg_init(const float *__restrict__ rhs, float *__restrict__ x, float *__restrict__ r,
            float *__restrict__ p, const float *__restrict__ A, long long n, long long nb,
            double *__restrict__ part, unsigned int *ticket, double *__restrict__ sc) {
+    pdl_wait();
     __shared__ double red[RT / 32];
     double rz = 0.0, rr = 0.0;
     for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT) {
@@ -187,6 +191,7 @@ k_pcg_update(float *__restrict__ x, float *__restrict__ r, const float *__restri
              const float *__restrict__ q, const float *__restrict__ A, long long n, long long nb,
              double *__restrict__ part, unsigned int *ticket, double *__restrict__ sc,
              const int *active, int *live, double eta) {
+    pdl_wait();
     __shared__ double red[RT / 32];
     if (active && *active == 0) return;   // batch member whose PCG has stopped
     if (live && live[0] == 0) return;     // this plan's PCG has stopped
@@ -242,6 +247,7 @@ __global__ void __launch_bounds__(RT)
 k_pcg_direction(float *__restrict__ p, const float *__restrict__ r, const float *__restrict__ A,
                 long long n, long long nb, const double *__restrict__ sc, const int *active,
                 const int *live) {
+    pdl_wait();
     if (active && *active == 0) return;
     if (live && live[0] == 0) return;
     const float beta = (float)sc[SC_BETA];
@@ -253,6 +259,7 @@ k_pcg_direction(float *__restrict__ p, const float *__restrict__ r, const float 
 __global__ void __launch_bounds__(RT)
 k_axpy(float *__restrict__ y, const float *__restrict__ a, const float *__restrict__ x,
        float alpha, long long n) {
+    pdl_wait();
     for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT)
         y[i] = fmaf(alpha, x[i], a[i]);
 }
@@ -267,48 +274,51 @@ int vec_blocks(const blr_plan *P) {
 int reduce_partials_needed() { return 2 * RBLOCKS; }
 
 int energy_finalize(blr_plan *P, const float *vt, double *energy_out, int nblocks, cudaStream_t s) {
-    k_energy<<<vec_blocks(P), RT, 0, s>>>(P->partials, nblocks, vt, P->A, P->nb,
-                                          1.0 / (P->p.sigma * P->p.sigma), P->partials2,
-                                          P->ticket, P->dsc, energy_out, P->dstatus);
+    launch_pdl(k_energy, dim3(vec_blocks(P)), dim3(RT), 0, s, (const double *)P->partials, nblocks,
+               vt, (const float *)P->A, P->nb, 1.0 / (P->p.sigma * P->p.sigma), P->partials2,
+               P->ticket, P->dsc, energy_out, P->dstatus);
     BLR_CK_LAUNCH();
     return BLR_OK;
 }
 
 int vec_dot(blr_plan *P, const float *a, const float *b, const float *w, double *out, cudaStream_t s) {
-    k_dot<<<vec_blocks(P), RT, 0, s>>>(a, b, w, P->nfloat, P->nb, P->partials, P->ticket, out);
+    launch_pdl(k_dot, dim3(vec_blocks(P)), dim3(RT), 0, s, a, b, w, P->nfloat, P->nb, P->partials,
+               P->ticket, out);
     BLR_CK_LAUNCH();
     return BLR_OK;
 }
 
 int vec_maxabs(blr_plan *P, const float *a, double *out, cudaStream_t s) {
-    k_maxabs<<<vec_blocks(P), RT, 0, s>>>(a, P->nfloat, P->partials, P->ticket, out);
+    launch_pdl(k_maxabs, dim3(vec_blocks(P)), dim3(RT), 0, s, a, P->nfloat, P->partials, P->ticket,
+               out);
     BLR_CK_LAUNCH();
     return BLR_OK;
 }
 
 int pcg_init(blr_plan *P, const float *rhs, float *x, cudaStream_t s) {
-    k_pcg_init<<<vec_blocks(P), RT, 0, s>>>(rhs, x, P->r, P->pv, P->A, P->nfloat, P->nb,
-                                            P->partials, P->ticket, P->dsc);
+    launch_pdl(k_pcg_init, dim3(vec_blocks(P)), dim3(RT), 0, s, rhs, x, P->r, P->pv,
+               (const float *)P->A, P->nfloat, P->nb, P->partials, P->ticket, P->dsc);
     BLR_CK_LAUNCH();
     return BLR_OK;
 }
 
 int pcg_update(blr_plan *P, float *x, cudaStream_t s, int *live, double eta) {
-    k_pcg_update<<<vec_blocks(P), RT, 0, s>>>(x, P->r, P->pv, P->q, P->A, P->nfloat, P->nb,
-                                              P->partials, P->ticket, P->dsc, P->active, live, eta);
+    launch_pdl(k_pcg_update, dim3(vec_blocks(P)), dim3(RT), 0, s, x, P->r, (const float *)P->pv,
+               (const float *)P->q, (const float *)P->A, P->nfloat, P->nb, P->partials, P->ticket,
+               P->dsc, P->active, live, eta);
     BLR_CK_LAUNCH();
     return BLR_OK;
 }
 
 int pcg_direction(blr_plan *P, cudaStream_t s, const int *live) {
-    k_pcg_direction<<<vec_blocks(P), RT, 0, s>>>(P->pv, P->r, P->A, P->nfloat, P->nb, P->dsc,
-                                                 P->active, live);
+    launch_pdl(k_pcg_direction, dim3(vec_blocks(P)), dim3(RT), 0, s, P->pv, (const float *)P->r,
+               (const float *)P->A, P->nfloat, P->nb, (const double *)P->dsc, P->active, live);
     BLR_CK_LAUNCH();
     return BLR_OK;
 }
 
 int vec_axpy(blr_plan *P, float *y, const float *a, const float *x, double alpha, cudaStream_t s) {
-    k_axpy<<<vec_blocks(P), RT, 0, s>>>(y, a, x, (float)alpha, P->nfloat);
+    launch_pdl(k_axpy, dim3(vec_blocks(P)), dim3(RT), 0, s, y, a, x, (float)alpha, P->nfloat);
     BLR_CK_LAUNCH();
     return BLR_OK;
 }

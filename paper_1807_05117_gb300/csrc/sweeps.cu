@@ -1052,6 +1052,7 @@ k_incstate_gather(const float *__restrict__ dm_in, const float4 *__restrict__ d4
 
 // d4 = (d0, d1, d2, 0) per voxel from the planar displacement.
 __global__ void k_pack_d4(const float *__restrict__ d, float4 *__restrict__ d4, long long V) {
+    pdl_wait();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V;
          i += (long long)gridDim.x * blockDim.x)
         d4[i] = make_float4(__ldg(d + i), __ldg(d + V + i), __ldg(d + 2 * V + i), 0.f);
@@ -1495,7 +1496,8 @@ int sweep_autotune(blr_plan *P, cudaStream_t s) {
 int sweep_pack_d4(blr_plan *P, cudaStream_t s) {
     if (!P->d4) return BLR_OK;
     const long long blocks = ceil_div_ll(P->V, 256);
-    k_pack_d4<<<(unsigned)(blocks < 4LL * P->sms ? blocks : 4LL * P->sms), 256, 0, s>>>(P->d, P->d4, P->V);
+    launch_pdl(k_pack_d4, dim3((unsigned)(blocks < 4LL * P->sms ? blocks : 4LL * P->sms)), dim3(256), 0,
+               s, (const float *)P->d, P->d4, P->V);
     BLR_CK_LAUNCH();
     return BLR_OK;
 }
