@@ -64,10 +64,11 @@ ADJ_BYTES = lambda nt: ((36 + 44 + 48 * (nt - 2)) if nt > 1 else 32)
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one interior adjoint-step
-# launch (k_adjoint_march<false, true>) at 128^3 from an ncu capture, valid only
-# for the sweep source it was captured from (SHA-256 of csrc/sweeps.cu).
-ADJ_TRAFFIC = {"sweeps_sha256": "cb4726cd386c3c4ddca2f543af69fde54eb1a85562e887ca29347a31c5ed106e",
-               "bytes": 67481856 + 1691904}
+# launch (k_adjoint_wide<0, 1, 1>, kept state gradient) at 128^3 from an ncu
+# capture, valid only for the sweep source it was captured from (SHA-256 of
+# csrc/sweeps.cu).
+ADJ_TRAFFIC = {"sweeps_sha256": "b359739e9e03d80ae29ef71c871e63986b004d617d425f77ab498e4ac44589a1",
+               "bytes": 94975744 + 6430976}
 
 
 def adjoint_traffic():
