@@ -90,6 +90,13 @@ __device__ __forceinline__ void split8(const float *x, uint4 &hi, uint4 &lo) {
                     pack_bf16(l[6], l[7]));
 }
 
+// An FP32 staging slot, rounded up to 1024 bytes so every slot (a TMA
+// destination) and the swizzled tiles after them stay aligned.
+__host__ __device__ inline size_t tp_stage_bytes(int K, int nt) {
+    return ((size_t)K * nt * 4 + 1023) & ~(size_t)1023;
+}
+__host__ __device__ inline size_t tp_b_bytes(int Kpad, int nt) { return (size_t)nt * Kpad * 2; }
+
 struct TcArgs {
     const uint8_t *tab;      // [mtiles][hi|lo][128 x Kpad] BF16, swizzled
     int mtiles, M;           // M tiles of 128 rows; rows written (< M)
@@ -160,7 +167,7 @@ k_tc_axis1(TcArgs p, const __grid_constant__ CUtensorMap xmap) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const size_t tab_bytes = (size_t)TC_M * p.Kpad * 2;            // one hi or lo table tile
     const size_t all_tab = 2 * tab_bytes * p.mtiles;
-    const size_t stage_bytes = (size_t)p.K * p.ntile * 4;
+    const size_t stage_bytes = tp_stage_bytes(p.K, p.ntile);      // 1024-byte aligned slots
     const size_t b_bytes = (size_t)p.ntile * p.Kpad * 2;           // one hi or lo field tile
     uint8_t *sA = base;
     float *stage0 = reinterpret_cast<float *>(sA + all_tab);
@@ -212,7 +219,7 @@ k_tc_axis1(TcArgs p, const __grid_constant__ CUtensorMap xmap) {
         if (p.tma) {
             // the whole [K][ntile] box (columns past the end read as zeros)
             if (lane == 0) {
-                mbar_expect_arrive(bar, (uint32_t)stage_bytes + extra_bytes);
+                mbar_expect_arrive(bar, (uint32_t)(p.K * p.ntile * 4) + extra_bytes);   // the box
                 tma_load_2d(dst0, &xmap, (int)col0, (t / p.col_tiles) * p.K, bar);
             }
             __syncwarp();
@@ -387,6 +394,269 @@ k_tc_axis1(TcArgs p, const __grid_constant__ CUtensorMap xmap) {
                      "r"(p.tmem_cols));
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined, warp-specialised form of the same contraction.  Per CTA, tiles
+// t = blockIdx.x, blockIdx.x + gridDim.x, ... flow through double-buffered
+// stages, each hand-off on an mbarrier:
+//   warps 0-5 (192 threads): split the FP32 tile into BF16 hi / lo (swizzled
+//     K-major B operand); thread 0 also issues the TMA loads, two tiles ahead;
+//   warp 14, lane 0: issues the MMAs of a tile into one of two TMEM
+//     accumulators and commits them to the "B free" and "accumulator full"
+//     barriers;
+//   warps 6-13 (two per TMEM lane quadrant, each half of the 32-column
+//     chunks): epilogue, TMEM -> registers -> XOR-swizzled shared transpose ->
+//     coalesced global stores.
+// Each role is a chain of dependent loads, so it gets several warps per
+// scheduler to hide their latency.
+// So the split of tile i + 1, the MMAs of tile i and the epilogue of tile i - 1
+// overlap.  Slot s = i & 1 of every buffer is used by tiles i = s, s + 2, ...; the
+// u-th use (u = i >> 1) of a "full" barrier completes phase u, and a "free"
+// barrier's phase u - 1 must complete before slot s is refilled.  Every wait is
+// bounded: a wait that expires stops its role, the CTA waits (bounded) for its
+// copies in flight, frees TMEM and sets BLR_FLAG_TIMEOUT.
+constexpr int TP_CONV = 6, TP_EPI = 8;                  // converter / epilogue warps
+constexpr int TP_MMA_WARP = TP_CONV + TP_EPI;          // warp 14
+constexpr int TP_THREADS = (TP_MMA_WARP + 1) * 32;     // 480
+constexpr int TP_CT = TP_CONV * 32;                    // converter threads
+constexpr int TP_NBAR = 13;
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+}
+
+// Shared memory of the pipelined kernel (tc_pipe_smem on the host).
+
+// Epilogue of one CW-column chunk of a 32-row group: TMEM -> registers (scale,
+// and for the displacement clamp + flags) -> XOR-swizzled transpose -> stores of
+// 128 contiguous bytes per row.
+template <int CW>
+__device__ __forceinline__ void tp_epi_chunk(uint32_t ta, float *T, float *D, const TcArgs &p,
+                                             int row0, long long col0, int c, int w, int lane,
+                                             int &flags) {
+    uint32_t rv[CW];
+    if constexpr (CW == 32) tmem_ld32(ta, rv);
+    else tmem_ld16(ta, rv);
+#pragma unroll
+    for (int q = 0; q < CW; ++q) {
+        float v = __uint_as_float(rv[q]) * p.scale;
+        if (p.mode == 1) {
+            const bool valid = (row0 + lane < p.M) && (c + q < w);
+            if (valid && !(fabsf(v) < 1.f)) flags |= (v != v) ? BLR_FLAG_NAN : BLR_FLAG_CFL;
+            v = fminf(fmaxf(v, -1.f), 0.99999994f);
+        }
+        T[lane * 32 + (q ^ lane)] = v;
+    }
+    __syncwarp();
+    const bool col_ok = lane < CW && (c + lane) < w;
+#pragma unroll 8
+    for (int q = 0; q < 32; ++q) {
+        const int row = row0 + q;
+        if (row < p.M && col_ok) D[(long long)row * p.ncols + col0 + c + lane] = T[q * 32 + (lane ^ q)];
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(TP_THREADS, 1)
+k_tc_pipe(TcArgs p, const __grid_constant__ CUtensorMap xmap) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    uint8_t *base = smem_raw + (((raw + 1023) & ~1023u) - raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const size_t tab_bytes = (size_t)TC_M * p.Kpad * 2;       // one hi or lo table tile
+    const size_t all_tab = 2 * tab_bytes * p.mtiles;
+    const size_t stage_bytes = tp_stage_bytes(p.K, p.ntile);
+    const size_t b_bytes = tp_b_bytes(p.Kpad, p.ntile);        // one hi or lo field tile
+    uint8_t *sA = base;
+    uint8_t *sStage = sA + all_tab;                            // [2][K][ntile] FP32
+    uint8_t *sB = sStage + 2 * stage_bytes;                    // [2][hi|lo][ntile x Kpad]
+    float *sE = reinterpret_cast<float *>(sB + 4 * b_bytes);   // [4 warps][32 x 32]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sE + TP_EPI * 1024);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + TP_NBAR);
+    __shared__ int s_fail, s_issued;
+    const uint32_t b0 = smem_u32(bars);
+    // barriers: 0 table; 1+s stage full; 3+s stage free; 5+s B full; 7+s B free;
+    // 9+s accumulator full; 11+s accumulator free
+    auto BAR = [&](int i) { return b0 + 8u * (uint32_t)i; };
+    const int acc_cols = p.mtiles * p.ntile;
+    int n = 0;   // tiles of this CTA
+    for (int t = blockIdx.x; t < p.tiles; t += gridDim.x) ++n;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tslot)),
+                     "r"(p.tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        mbar_init(BAR(0), 1);
+        for (int sl = 0; sl < 2; ++sl) {
+            mbar_init(BAR(1 + sl), 1);
+            mbar_init(BAR(3 + sl), TP_CT);
+            mbar_init(BAR(5 + sl), TP_CT);
+            mbar_init(BAR(7 + sl), 1);
+            mbar_init(BAR(9 + sl), 1);
+            mbar_init(BAR(11 + sl), TP_EPI * 32);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        s_fail = 0;
+        s_issued = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tslot;
+    // the table is written once at plan creation (which synchronises the device),
+    // so it is fetched before the wait for the previous kernel in the stream
+    if (tid == 0) {
+        mbar_expect_arrive(BAR(0), (uint32_t)all_tab);
+        bulk_g2s(smem_u32(sA), p.tab, (uint32_t)all_tab, BAR(0));
+    }
+    pdl_wait();
+
+    auto tile_of = [&](int i) { return blockIdx.x + i * gridDim.x; };
+    auto issue = [&](int i) {   // thread 0: TMA load of tile i into slot i & 1
+        const int t = tile_of(i), sl = i & 1;
+        const int batch = t / p.col_tiles, ct = t - batch * p.col_tiles;
+        mbar_expect_arrive(BAR(1 + sl), (uint32_t)(p.K * p.ntile * 4));   // the box
+        tma_load_2d(smem_u32(sStage) + (uint32_t)(sl * stage_bytes), &xmap, ct * p.ntile,
+                    batch * p.K, BAR(1 + sl));
+        s_issued = i + 1;
+    };
+    bool ok = true;
+    if (warp < TP_CONV) {
+        // ---- split FP32 -> BF16 hi / lo (and the TMA producer in thread 0)
+        if (tid == 0)
+            for (int i = 0; i < n && i < 2; ++i) issue(i);
+        const int nkc = p.Kpad >> 3;
+        for (int i = 0; i < n && ok; ++i) {
+            const int sl = i & 1;
+            const uint32_t u = (uint32_t)(i >> 1);
+            ok = mbar_wait(BAR(1 + sl), u & 1u);
+            if (ok && i >= 2) ok = mbar_wait(BAR(7 + sl), (u - 1) & 1u);
+            if (!ok) break;
+            const int t = tile_of(i), ct = t % p.col_tiles;
+            const long long left = p.ncols - (long long)ct * p.ntile;
+            const int w = (int)(left < p.ntile ? left : p.ntile);
+            const float *stage = reinterpret_cast<const float *>(sStage + sl * stage_bytes);
+            uint8_t *sBh = sB + (size_t)(2 * sl) * b_bytes, *sBl = sBh + b_bytes;
+            for (int it = tid; it < p.ntile * nkc; it += TP_CT) {
+                const int r = it % p.ntile, kc = it / p.ntile;
+                float x[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int k = kc * 8 + q;
+                    x[q] = (k < p.K && r < w) ? stage[k * p.ntile + r] : 0.f;
+                }
+                uint4 hi, lo;
+                split8(x, hi, lo);
+                const uint32_t off = swz_chunk(r, kc, p.ntile);
+                *reinterpret_cast<uint4 *>(sBh + off) = hi;
+                *reinterpret_cast<uint4 *>(sBl + off) = lo;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(BAR(5 + sl));   // B full
+            mbar_arrive(BAR(3 + sl));   // stage free
+            if (tid == 0 && i + 2 < n) {
+                ok = mbar_wait(BAR(3 + sl), u & 1u);   // every converter has read the stage
+                if (ok) issue(i + 2);
+            }
+        }
+    } else if (warp < TP_MMA_WARP) {
+        // ---- epilogue: warp w reaches TMEM lanes 32 * (w % 4) .. + 31 (rows of the
+        // tile); the two warps of a quadrant take alternate 32-column chunks
+        const int lg = warp & 3;
+        const int half = ((warp - TP_CONV) >> 2) & 1;
+        float *T = sE + (warp - TP_CONV) * 1024;
+        const int cw = p.ntile < 32 ? 16 : 32;
+        int flags = 0;
+        for (int i = 0; i < n && ok; ++i) {
+            const int sl = i & 1;
+            const uint32_t u = (uint32_t)(i >> 1);
+            ok = mbar_wait(BAR(9 + sl), u & 1u);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const int t = tile_of(i), batch = t / p.col_tiles, ct = t - batch * p.col_tiles;
+            const long long col0 = (long long)ct * p.ntile;
+            const long long left = p.ncols - col0;
+            const int w = (int)(left < p.ntile ? left : p.ntile);
+            float *D = p.D + batch * p.dstride;
+            for (int mt = 0; mt < p.mtiles; ++mt) {
+                const int row0 = mt * TC_M + lg * 32;
+                for (int c = half * cw; c < p.ntile; c += 2 * cw) {
+                    const uint32_t ta = tmem + ((uint32_t)(lg * 32) << 16) +
+                                        (uint32_t)(sl * acc_cols + mt * p.ntile + c);
+                    if (cw == 32)
+                        tp_epi_chunk<32>(ta, T, D, p, row0, col0, c, w, lane, flags);
+                    else
+                        tp_epi_chunk<16>(ta, T, D, p, row0, col0, c, w, lane, flags);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            mbar_arrive(BAR(11 + sl));   // accumulator free
+        }
+        if (flags) atomicOr(p.status, flags);
+    } else if (lane == 0) {
+        // ---- MMA issue
+        const uint32_t idesc = umma_idesc(TC_M, p.ntile);
+        ok = mbar_wait(BAR(0), 0u);   // table
+        for (int i = 0; i < n && ok; ++i) {
+            const int sl = i & 1;
+            const uint32_t u = (uint32_t)(i >> 1);
+            ok = mbar_wait(BAR(5 + sl), u & 1u);
+            if (ok && i >= 2) ok = mbar_wait(BAR(11 + sl), (u - 1) & 1u);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t bh0 = smem_u32(sB + (size_t)(2 * sl) * b_bytes);
+            const uint32_t bl0 = bh0 + (uint32_t)b_bytes;
+            for (int mt = 0; mt < p.mtiles; ++mt) {
+                const uint32_t ah0 = smem_u32(sA + (size_t)(2 * mt) * tab_bytes);
+                const uint32_t al0 = ah0 + (uint32_t)tab_bytes;
+                const uint32_t d = tmem + (uint32_t)(sl * acc_cols + mt * p.ntile);
+                for (int j = 0; j < p.Kpad / 16; ++j) {
+                    const uint32_t oa = (uint32_t)((j >> 2) * TC_M * 128 + (j & 3) * 32);
+                    const uint32_t ob = (uint32_t)((j >> 2) * p.ntile * 128 + (j & 3) * 32);
+                    const uint64_t ah = umma_desc(ah0 + oa), al = umma_desc(al0 + oa);
+                    const uint64_t bh = umma_desc(bh0 + ob), bl = umma_desc(bl0 + ob);
+                    umma_bf16(d, ah, bh, idesc, j > 0);
+                    umma_bf16(d, ah, bl, idesc, 1u);
+                    umma_bf16(d, al, bh, idesc, 1u);
+                }
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    BAR(7 + sl)));   // B free
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    BAR(9 + sl)));   // accumulator full
+        }
+    }
+    if (!ok) s_fail = 1;
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (s_fail && tid == 0) {
+        // a wait expired: record it and give every TMA load issued a bounded
+        // time to land before the CTA leaves
+        atomicOr(p.status, BLR_FLAG_TIMEOUT);
+        for (int i = 0; i < s_issued; ++i) mbar_wait(BAR(1 + (i & 1)), (uint32_t)(i >> 1) & 1u);
+        mbar_wait(BAR(0), 0u);
+    }
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(p.tmem_cols));
+}
+
 // Table tiles, FP64 phases split into BF16 hi/lo, for stage kind
 //   0 axis-1 expand : row x1, k kappa = 2 j + re/im       W = cos | -sin (2 pi k_j x1 / N)
 //   1 axis-1 project: row kappa, k x1                       (the same values)
@@ -480,7 +750,7 @@ constexpr size_t TC_SMEM_MAX = 227 * 1024;
 // staging data are consumed before the MMAs, and the next tile's load is issued
 // only after the epilogue), so it costs nothing extra when it fits there.
 size_t tc_smem_bytes(int mtiles, int K, int Kpad, int nt, int nstage) {
-    const size_t stage = (size_t)nstage * K * nt * 4, epi = (size_t)TC_THREADS / 32 * 1024 * 4;
+    const size_t stage = (size_t)nstage * tp_stage_bytes(K, nt), epi = (size_t)TC_THREADS / 32 * 1024 * 4;
     const bool alias = nstage == 1 && stage >= epi;
     return 1024 + 2 * (size_t)TC_M * Kpad * 2 * mtiles + stage + 2 * (size_t)nt * Kpad * 2 +
            (alias ? 0 : epi) + 3 * 8 + 16;
@@ -513,6 +783,35 @@ bool tc_shape(int mtiles, int K, int Kpad, long long ncols, int nbatch, int sms,
                 *smem = sb;
                 return true;
             }
+    return false;
+}
+
+// Shared memory of the pipelined kernel: table, two FP32 stages, two hi/lo B
+// tiles, the epilogue buffers and the barriers (+ 1024 bytes of alignment slack).
+size_t tc_pipe_smem(int mtiles, int K, int Kpad, int nt) {
+    return 1024 + 2 * (size_t)TC_M * Kpad * 2 * mtiles + 2 * tp_stage_bytes(K, nt) +
+           4 * tp_b_bytes(Kpad, nt) + (size_t)TP_EPI * 1024 * 4 + TP_NBAR * 8 + 16;
+}
+
+// Column tile of the pipelined kernel (256 .. 16): the largest that fits with
+// at least two tiles per SM (so the stages of consecutive tiles overlap), else
+// one per SM, else any.  The field tile must be TMA-addressable (K <= 256 and
+// no wider than the field).
+bool tc_pipe_shape(int mtiles, int K, int Kpad, long long ncols, int nbatch, int sms, int *ntile,
+                   size_t *smem) {
+    if (K > 256) return false;
+    for (int pass = 0; pass < 3; ++pass)
+        for (int nt = 256; nt >= 16; nt >>= 1) {
+            if (2 * mtiles * nt > 512 || nt > ncols) continue;
+            const size_t sb = tc_pipe_smem(mtiles, K, Kpad, nt);
+            if (sb > TC_SMEM_MAX) continue;
+            const long long tiles = ceil_div_ll(ncols, nt) * nbatch;
+            if (pass == 0 && tiles < 2LL * sms) continue;
+            if (pass == 1 && tiles < sms) continue;
+            *ntile = nt;
+            *smem = sb;
+            return true;
+        }
     return false;
 }
 
@@ -592,7 +891,13 @@ int tc_run(blr_plan *P, int kind, const float *X, float *D, float scale, int mod
     a.Kpad = g.Kpad;
     size_t smem = 0;
     const int sms = plan_sms(P);
-    if (!tc_shape(a.mtiles, a.K, a.Kpad, g.ncols, g.nbatch, sms, &a.ntile, &a.nstage, &smem))
+    // the pipelined kernel when its shape fits and the field tiles can come by TMA
+    // (checked below), else the sequential one
+    const bool aligned = (g.ncols % 4 == 0) && ((uintptr_t)X % 16 == 0);
+    bool pipe = aligned && encode_tiled() &&
+                tc_pipe_shape(a.mtiles, a.K, a.Kpad, g.ncols, g.nbatch, sms, &a.ntile, &smem);
+    if (pipe) a.nstage = 2;
+    else if (!tc_shape(a.mtiles, a.K, a.Kpad, g.ncols, g.nbatch, sms, &a.ntile, &a.nstage, &smem))
         return BLR_EINVAL;
     uint8_t *tabs[4] = {P->tc_tab_expand, P->tc_tab_project, P->tc_tab2_expand, P->tc_tab2_project};
     a.tab = tabs[kind];
@@ -625,10 +930,25 @@ int tc_run(blr_plan *P, int kind, const float *X, float *D, float scale, int mod
                 a.tma = 1;
         }
     }
-    a.tmem_cols = pow2_at_least(a.mtiles * a.ntile);
+    if (pipe && !a.tma) {   // no tensor map after all: the sequential kernel
+        pipe = false;
+        if (!tc_shape(a.mtiles, a.K, a.Kpad, g.ncols, g.nbatch, sms, &a.ntile, &a.nstage, &smem))
+            return BLR_EINVAL;
+        a.col_tiles = (int)ceil_div_ll(a.ncols, a.ntile);
+        a.tiles = g.nbatch * a.col_tiles;
+    }
     a.scale = scale;
     a.mode = mode;
     a.status = P->dstatus;
+    if (pipe) {
+        a.tmem_cols = pow2_at_least(2 * a.mtiles * a.ntile);
+        BLR_CK(cudaFuncSetAttribute(k_tc_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int grid = a.tiles < sms ? a.tiles : sms;
+        launch_pdl(k_tc_pipe, dim3(grid), dim3(TP_THREADS), smem, s, a, xmap);
+        BLR_CK_LAUNCH();
+        return BLR_OK;
+    }
+    a.tmem_cols = pow2_at_least(a.mtiles * a.ntile);
     BLR_CK(cudaFuncSetAttribute(k_tc_axis1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int slots = tc_ctas_per_sm(smem, a.tmem_cols) * sms;
     const int grid = a.tiles < slots ? a.tiles : slots;
