@@ -374,7 +374,7 @@ def main_ours(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f32 fields; bf16 hi+lo split x3 products (fp32 accumulate) in the axis-1 DFT contractions"
+            "dtype": "f32 fields; bf16 hi+lo split x3 products (fp32 accumulate) in the axis-2 and axis-1 DFT contractions"
                      if args.precision == "mixed" else "f32",
             "data": "synthetic", "config": config(args.precision, world),
             "hvp_per_s": world * 1000.0 / head["hvp_ms"], "hvp_ms": head["hvp_ms"],
