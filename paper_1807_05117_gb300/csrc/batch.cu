@@ -39,6 +39,7 @@ struct Batch {
     unsigned long long pcg_launches = 0;      // kernel nodes per replay
     double *h_sc = nullptr;                   // pinned [npairs][SC_COUNT]
     int *h_flags = nullptr;                   // pinned [npairs]
+    bool wide = false;                        // every pair runs the wide-copy sweep tiles
 };
 
 Batch *as_batch(blr_batch_t b) { return reinterpret_cast<Batch *>(b); }
@@ -51,7 +52,7 @@ int fill_descriptors(Batch *B) {
         blr_plan *P = B->plans[p];
         int tiles[KINDS][3];
         for (int kind = 0; kind < KINDS; ++kind) {
-            sweep_tiles(P, kind, &tiles[kind][0], &tiles[kind][1], &tiles[kind][2]);
+            sweep_tiles(P, kind, B->wide, &tiles[kind][0], &tiles[kind][1], &tiles[kind][2]);
             long long *st = starts.data() + (size_t)kind * (np + 1);
             st[p + 1] = st[p] + (long long)tiles[kind][0] * tiles[kind][1] * tiles[kind][2];
         }
@@ -64,6 +65,7 @@ int fill_descriptors(Batch *B) {
             b.tj = tiles[kind][1];
             b.ti = tiles[kind][2];
             b.d = P->d;
+            b.d4 = P->d4;
             b.dt = P->dt;
             b.scale = lam_scale;
             b.active = B->d_active + p;
@@ -117,10 +119,10 @@ int launch_sweep(Batch *B, int kind, int n, cudaStream_t s) {
         f1 = n == 0;
         f2 = n == nt - 1;
     }
-    return sweep_batch_launch(kind, f1, f2, B->d_desc + ((size_t)kind * nt + n) * B->npairs,
+    return sweep_batch_launch(kind, f1, f2, B->wide, B->d_desc + ((size_t)kind * nt + n) * B->npairs,
                               B->d_starts + (size_t)kind * (B->npairs + 1), B->npairs,
                               B->d_counters + (size_t)kind * nt + n,
-                              sweep_blocks_per_sm(kind) * B->grid, s);
+                              sweep_blocks_per_sm(kind, B->wide) * B->grid, s);
 }
 
 int reset_counters(Batch *B, cudaStream_t s) {
@@ -362,6 +364,8 @@ int blr_batch_create(const blr_params *params, int npairs, blr_batch_t *out) {
     if (!rc && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, B->device) != cudaSuccess)
         rc = BLR_ECUDA;
     B->grid = sms > 0 ? sms : 148;   // SMs; persistent grids are blocks-per-SM multiples
+    B->wide = !rc;
+    for (int p = 0; p < npairs && !rc; ++p) B->wide = B->wide && B->plans[p]->sweep_wide;
     const int nside = npairs < 8 ? npairs : 8;
     if (!rc &&
         (cudaMalloc(&B->d_desc, sizeof(SweepPair) * KINDS * B->nt * npairs) != cudaSuccess ||

@@ -73,6 +73,7 @@ struct SweepPair {
     const float *in0;        // state: m^n | adjoint: lambda^{n+1} | incremental: dm^n
     const float *m;          // adjoint / incremental: m^n
     const float *d;          // displacement
+    const float4 *d4;        // its float4 copy (wide-copy tiles)
     const float *aux;        // state: I1 (last step) | incremental: dv
     float *out0;             // state: m^{n+1} | adjoint: lambda^n | incremental: dm^{n+1}
     float *out1;             // state: lambda^nt (last step) | adjoint: body force
@@ -189,12 +190,15 @@ long long sweep_blocks(const blr_plan *P);
 int sweep_state(blr_plan *P, cudaStream_t s);                  // m^1..m^nt, lambda^nt, partials
 int sweep_adjoint(blr_plan *P, float *b, float *lambda0, cudaStream_t s);
 int sweep_incremental(blr_plan *P, cudaStream_t s);            // dm -> dlambda^nt in lam[0]
-int sweep_batch_launch(int kind, bool f1, bool f2, const SweepPair *pairs, const long long *starts,
-                       int npairs, unsigned long long *counter, int grid, cudaStream_t s);
+// wide: the adjoint and incremental-state items use the wide-copy tiles (every
+// pair has N3 % 4 == 0); the incremental-state tiles are then AJ rows high.
+int sweep_batch_launch(int kind, bool f1, bool f2, bool wide, const SweepPair *pairs,
+                       const long long *starts, int npairs, unsigned long long *counter, int grid,
+                       cudaStream_t s);
 // kind: 0 state, 1 adjoint, 2 incremental state
-void sweep_tiles(const blr_plan *P, int kind, int *tk, int *tj, int *ti);
+void sweep_tiles(const blr_plan *P, int kind, bool wide, int *tk, int *tj, int *ti);
 int sweep_chunk(const blr_plan *P, int kind);
-int sweep_blocks_per_sm(int kind);
+int sweep_blocks_per_sm(int kind, bool wide = false);
 void sweep_set_chunk(blr_plan *P, int kind, int chunk);
 int sweep_autotune(blr_plan *P, cudaStream_t s);
 int sweep_pack_d4(blr_plan *P, cudaStream_t s);               // d4 from d (when P->d4)

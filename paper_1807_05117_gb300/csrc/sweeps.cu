@@ -521,50 +521,6 @@ k_incstate_march(const float *__restrict__ dm_in, const float *__restrict__ m_n,
                                blockIdx.y * MJ, blockIdx.z * CH);
 }
 
-// ---------------------------------------------------------------------------
-// Batched sweeps: one persistent launch runs the same time step of many
-// registration pairs.  Blocks pop (pair, tile) items from an atomic counter in
-// item order (items of pair p are starts[p] .. starts[p+1]-1); each item is a
-// full march tile of that pair, so the results equal the single-pair kernels'.
-template <int KIND, bool F1, bool F2>
-__global__ void __launch_bounds__(MT, KIND == 1 ? ADJ_BLOCKS : 4)
-k_sweep_batch(const SweepPair *__restrict__ pairs, const long long *__restrict__ starts,
-              int npairs, unsigned long long *counter) {
-    __shared__ long long s_item;
-    const long long total = starts[npairs];
-    while (true) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ull);
-        __syncthreads();
-        const long long item = s_item;
-        if (item >= total) break;
-        int lo = 0, hi = npairs - 1;          // last pair whose start <= item
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (starts[mid] <= item) lo = mid; else hi = mid - 1;
-        }
-        const SweepPair P = pairs[lo];   // by value: the tile bodies take plain values
-        if (P.active && *P.active == 0) continue;
-        const long long local = item - starts[lo];
-        const int kt = (int)(local % P.tk);
-        const int jt = (int)((local / P.tk) % P.tj);
-        const int it = (int)(local / ((long long)P.tk * P.tj));
-        const int k0 = kt * MK, j0 = jt * (KIND == 1 ? AJ : MJ), i0 = it * P.chunk;
-        if constexpr (KIND == 0)
-            state_tile<F1>(P.in0, P.d, P.out0, P.g, P.chunk, P.aux, P.out1, P.scale, P.partials,
-                           k0, j0, i0);
-        else if constexpr (KIND == 1)
-            adjoint_tile<F1, F2>(P.in0, P.m, P.d, P.out0, P.out1, P.dt, P.g, P.chunk, k0, j0, i0);
-        else
-            incstate_tile<F1, F2>(P.in0, P.m, P.d, P.aux, P.out0, P.dt, P.scale, P.g, P.chunk,
-                                  k0, j0, i0);
-        // Drain every copy group of this tile before the next tile refills the
-        // rings: without it the batched results differed from the one-tile
-        // kernels in the periodically wrapped x1 plane.
-        asm volatile("cp.async.wait_all;\n" ::: "memory");
-        __syncthreads();
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Balanced grids: the ncol * N1 (column tile, x1 plane) units of one step are
@@ -1058,6 +1014,60 @@ __global__ void k_pack_d4(const float *__restrict__ d, float4 *__restrict__ d4, 
         d4[i] = make_float4(__ldg(d + i), __ldg(d + V + i), __ldg(d + 2 * V + i), 0.f);
 }
 
+// ---------------------------------------------------------------------------
+// Batched sweeps: one persistent launch runs the same time step of many
+// registration pairs.  Blocks pop (pair, tile) items from an atomic counter in
+// item order (items of pair p are starts[p] .. starts[p+1]-1); each item is a
+// full march tile of that pair, so the results equal the single-pair kernels'.
+// WIDE: the adjoint and incremental-state items use the wide-copy tiles.
+template <int KIND, bool F1, bool F2, bool WIDE>
+__global__ void __launch_bounds__(MT, KIND == 1 ? ADJ_BLOCKS : (KIND == 2 && WIDE ? INC_BLOCKS : 4))
+k_sweep_batch(const SweepPair *__restrict__ pairs, const long long *__restrict__ starts,
+              int npairs, unsigned long long *counter) {
+    __shared__ long long s_item;
+    pdl_wait();
+    const long long total = starts[npairs];
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= total) break;
+        int lo = 0, hi = npairs - 1;          // last pair whose start <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (starts[mid] <= item) lo = mid; else hi = mid - 1;
+        }
+        const SweepPair P = pairs[lo];   // by value: the tile bodies take plain values
+        if (P.active && *P.active == 0) continue;
+        const long long local = item - starts[lo];
+        const int kt = (int)(local % P.tk);
+        const int jt = (int)((local / P.tk) % P.tj);
+        const int it = (int)(local / ((long long)P.tk * P.tj));
+        const int k0 = kt * MK, j0 = jt * ((KIND == 1 || (KIND == 2 && WIDE)) ? AJ : MJ);
+        const int i0 = it * P.chunk;
+        if constexpr (KIND == 0)
+            state_tile<F1>(P.in0, P.d, P.out0, P.g, P.chunk, P.aux, P.out1, P.scale, P.partials,
+                           k0, j0, i0);
+        else if constexpr (KIND == 1 && WIDE)
+            adjoint_tile_w<F1, F2, false>(P.in0, P.m, P.d4, P.out0, P.out1, P.dt, P.g, P.chunk, k0,
+                                          j0, i0, nullptr);
+        else if constexpr (KIND == 1)
+            adjoint_tile<F1, F2>(P.in0, P.m, P.d, P.out0, P.out1, P.dt, P.g, P.chunk, k0, j0, i0);
+        else if constexpr (WIDE)
+            incstate_tile_w<F1, F2, false>(P.in0, P.m, P.d4, P.aux, P.out0, P.dt, P.scale, P.g,
+                                           P.chunk, k0, j0, i0, nullptr);
+        else
+            incstate_tile<F1, F2>(P.in0, P.m, P.d, P.aux, P.out0, P.dt, P.scale, P.g, P.chunk,
+                                  k0, j0, i0);
+        // Drain every copy group of this tile before the next tile refills the
+        // rings: without it the batched results differed from the one-tile
+        // kernels in the periodically wrapped x1 plane.
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        __syncthreads();
+    }
+}
+
 dim3 sweep_grid(const blr_plan *P) {
     return dim3((unsigned)ceil_div_ll(P->N3, MK), (unsigned)ceil_div_ll(P->N2, MJ),
                 (unsigned)ceil_div_ll(P->N1, P->chunk));
@@ -1076,10 +1086,18 @@ int adjoint_smem_attributes() {
     BLR_CK(cudaFuncSetAttribute(k_adjoint_march<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
     BLR_CK(cudaFuncSetAttribute(k_adjoint_march<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
     BLR_CK(cudaFuncSetAttribute(k_adjoint_march<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
-    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
-    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
-    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
-    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<2, true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, incw_smem<true, false>()));
+    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<2, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, incw_smem<true, false>()));
+    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<2, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, incw_smem<false, false>()));
+    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<2, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, incw_smem<false, false>()));
     BLR_CK(cudaFuncSetAttribute(k_adjoint_bal<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
     BLR_CK(cudaFuncSetAttribute(k_adjoint_bal<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
     BLR_CK(cudaFuncSetAttribute(k_adjoint_bal<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
@@ -1332,29 +1350,47 @@ int sweep_incremental(blr_plan *P, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Batched launches and the tile-shape autotuner.
 
-int sweep_batch_launch(int kind, bool f1, bool f2, const SweepPair *pairs, const long long *starts,
-                       int npairs, unsigned long long *counter, int grid, cudaStream_t s) {
-#define BLR_BL(K, A, B) \
-    k_sweep_batch<K, A, B><<<grid, MT, (K) == 1 ? ADJ_SMEM : 0, s>>>(pairs, starts, npairs, counter)
+int sweep_batch_launch(int kind, bool f1, bool f2, bool wide, const SweepPair *pairs,
+                       const long long *starts, int npairs, unsigned long long *counter, int grid,
+                       cudaStream_t s) {
+#define BLR_BL(K, A, B, W, SM)                                                                   \
+    launch_pdl(k_sweep_batch<K, A, B, W>, dim3(grid), dim3(MT), (size_t)(SM), s, pairs, starts, \
+               npairs, counter)
     if (kind == 0) {
-        if (f1) BLR_BL(0, true, false); else BLR_BL(0, false, false);
+        if (f1) BLR_BL(0, true, false, false, 0); else BLR_BL(0, false, false, false, 0);
     } else if (kind == 1) {
-        if (f1 && f2) BLR_BL(1, true, true);
-        else if (f1) BLR_BL(1, true, false);
-        else if (f2) BLR_BL(1, false, true);
-        else BLR_BL(1, false, false);
+        if (wide) {
+            if (f1 && f2) BLR_BL(1, true, true, true, ADJW_SMEM);
+            else if (f1) BLR_BL(1, true, false, true, ADJW_SMEM);
+            else if (f2) BLR_BL(1, false, true, true, ADJW_SMEM);
+            else BLR_BL(1, false, false, true, ADJW_SMEM);
+        } else {
+            if (f1 && f2) BLR_BL(1, true, true, false, ADJ_SMEM);
+            else if (f1) BLR_BL(1, true, false, false, ADJ_SMEM);
+            else if (f2) BLR_BL(1, false, true, false, ADJ_SMEM);
+            else BLR_BL(1, false, false, false, ADJ_SMEM);
+        }
     } else {
-        if (f1 && f2) BLR_BL(2, true, true);
-        else if (f1) BLR_BL(2, true, false);
-        else if (f2) BLR_BL(2, false, true);
-        else BLR_BL(2, false, false);
+        if (wide) {
+            if (f1 && f2) BLR_BL(2, true, true, true, (incw_smem<true, false>()));
+            else if (f1) BLR_BL(2, true, false, true, (incw_smem<true, false>()));
+            else if (f2) BLR_BL(2, false, true, true, (incw_smem<false, false>()));
+            else BLR_BL(2, false, false, true, (incw_smem<false, false>()));
+        } else {
+            if (f1 && f2) BLR_BL(2, true, true, false, 0);
+            else if (f1) BLR_BL(2, true, false, false, 0);
+            else if (f2) BLR_BL(2, false, true, false, 0);
+            else BLR_BL(2, false, false, false, 0);
+        }
     }
 #undef BLR_BL
     BLR_CK_LAUNCH();
     return BLR_OK;
 }
 
-int sweep_blocks_per_sm(int kind) { return kind == 1 ? ADJ_BLOCKS : 4; }
+int sweep_blocks_per_sm(int kind, bool wide) {
+    return kind == 1 ? ADJ_BLOCKS : (kind == 2 && wide ? INC_BLOCKS : 4);
+}
 
 int sweep_chunk(const blr_plan *P, int kind) { return kind == 1 ? P->chunk_adj : P->chunk; }
 
@@ -1363,10 +1399,11 @@ void sweep_set_chunk(blr_plan *P, int kind, int chunk) {
     else P->chunk = chunk;
 }
 
-// Tiles of one pair for a sweep kind at its current chunk.
-void sweep_tiles(const blr_plan *P, int kind, int *tk, int *tj, int *ti) {
+// Tiles of one pair for a sweep kind at its current chunk (wide: the
+// incremental-state tiles are the wide-copy ones, AJ rows high).
+void sweep_tiles(const blr_plan *P, int kind, bool wide, int *tk, int *tj, int *ti) {
     *tk = (int)ceil_div_ll(P->N3, MK);
-    *tj = (int)ceil_div_ll(P->N2, kind == 1 ? AJ : MJ);
+    *tj = (int)ceil_div_ll(P->N2, (kind == 1 || (kind == 2 && wide)) ? AJ : MJ);
     *ti = (int)ceil_div_ll(P->N1, sweep_chunk(P, kind));
 }
 
