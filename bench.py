@@ -132,6 +132,31 @@ def run_oracle_subprocess(samples: int):
         os.unlink(path)
 
 
+# ----------------------------------------------------------------------------
+# replicas (N > 1 under torchrun): one independent pair per rank, max-over-ranks time
+# ----------------------------------------------------------------------------
+
+
+def pair_seed(rank: int) -> int:
+    """Seed of the phantom pair a rank registers (each rank its own pair)."""
+    return SEED + 1000 * rank
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest of a per-rank time over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, ms: float) -> float:
+    """Whole-job units per second: every rank completes one unit in `ms` (the slowest rank's time)."""
+    return world * 1000.0 / ms
+
+
 def registration_seconds(t_state, t_grad, t_hvp, n_state, n_grad, n_hvp):
     return n_state * t_state + n_grad * t_grad + n_hvp * t_hvp
 
@@ -273,11 +298,7 @@ def measure_precision(precision, args, dev, I0g, I1g, flush, stream, dist, world
     launches = blr.blr_kernel_launches() - launches0
     barrier()
     clocks = sampler.stop(int(os.environ.get("LOCAL_RANK", "0")))
-    ms = total_ms / max(args.steps, 1)
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(total_ms / max(args.steps, 1), dist, dev)
 
     # Gauss-Newton HVP/s at the final point of the last registration
     dvt = torch.from_numpy(synth.random_direction(BAND, SEED + 2).astype(np.complex64)).to(dev)
@@ -358,7 +379,7 @@ def main_ours(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
 
-    I0, I1, _ = synth.phantom_pair(N, SEED + 1000 * rank, max_disp=MAX_DISP)
+    I0, I1, _ = synth.phantom_pair(N, pair_seed(rank), max_disp=MAX_DISP)
     (I0f, _), (I1f, _) = synth.as_device_inputs(I0, I1)
     I0g, I1g = torch.from_numpy(I0f).to(dev), torch.from_numpy(I1f).to(dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
@@ -370,22 +391,22 @@ def main_ours(args):
     res = {p: measure_precision(p, args, dev, I0g, I1g, flush, stream, dist, world) for p in order}
     head = res[args.precision]
     rep = head["rep"]
-    line = {"metric": METRIC, "value": world * 1000.0 / head["ms"], "unit": "registrations/s",
+    line = {"metric": METRIC, "value": job_rate(world, head["ms"]), "unit": "registrations/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
             "dtype": "f32 fields; bf16 hi+lo split x3 products (fp32 accumulate) in the axis-2 and axis-1 DFT contractions"
                      if args.precision == "mixed" else "f32",
             "data": "synthetic", "config": config(args.precision, world),
-            "hvp_per_s": world * 1000.0 / head["hvp_ms"], "hvp_ms": head["hvp_ms"],
+            "hvp_per_s": job_rate(world, head["hvp_ms"]), "hvp_ms": head["hvp_ms"],
             "gpu_launches": int(head["launches"]), "roofline": head["roofline"],
             "clocks": head["clocks"],
             "report": {k: getattr(rep, k) for k in ("newton_iters", "pcg_iters", "n_state",
                                                      "n_hessvec", "n_halvings", "energy0",
                                                      "energy", "grad_inf_rel")},
-            "by_precision": {p: {"registrations_per_s": world * 1000.0 / r["ms"],
+            "by_precision": {p: {"registrations_per_s": job_rate(world, r["ms"]),
                                  "ms_per_registration": r["ms"],
-                                 "hvp_per_s": world * 1000.0 / r["hvp_ms"],
+                                 "hvp_per_s": job_rate(world, r["hvp_ms"]),
                                  "final_energy": r["rep"].energy,
                                  "pcg_iters": r["rep"].pcg_iters,
                                  "adjoint_step_us": r["roofline"]["launch_us"],
@@ -419,12 +440,8 @@ def main_ours(args):
             e1.record(stream)
             e1.synchronize()
             tot += e0.elapsed_time(e1)
-        e2e_ms = tot / max(args.steps, 1)
-        if dist is not None:
-            t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        line["e2e"] = {"value": world * 1000.0 / e2e_ms, "unit": "registrations/s",
+        e2e_ms = max_over_ranks(tot / max(args.steps, 1), dist, dev)
+        line["e2e"] = {"value": job_rate(world, e2e_ms), "unit": "registrations/s",
                        "ms_per_step": e2e_ms,
                        "h2d_bytes_per_step": 2 * I0f.nbytes + hvt.numel() * 8,
                        "d2h_bytes_per_step": hvt.numel() * 8}
