@@ -23,7 +23,12 @@ fields", arXiv 1807.05117):
 * Gauss-Newton Hessian-vector product H~dv~ = L~dv~ + pi(dlambda grad m) with
   the Gauss-Newton drops of Section 3.4 applied to Eq. 46;
 * PCG with preconditioner K~ and the reduced-space Newton update with a step
-  length (Section 3.4, Eqs. 54-55; Section 2.4, Eqs. 31-32).
+  length (Section 3.4, Eqs. 54-55; Section 2.4, Eqs. 31-32);
+* the incompressible form (Eq. 4 with gamma = 1, imposed in the band as in
+  Section 3.2): the velocity is restricted to divergence-free band fields by the
+  Fourier-diagonal Leray projector P(k) = I - kappa kappa^T / |kappa|^2,
+  kappa_d = 2 pi k_d / N_d; the energy is E(P v~), so the gradient is
+  P grad E(P v~) and the Hessian P H P.
 
 The paper states the continuous equations only (optimise-then-discretise).  The
 oracle fixes one discretisation and differentiates it exactly
@@ -70,8 +75,11 @@ class Params:
     n      -- grid (N1, N2, N3); array layout [N1][N2][N3], N3 fastest
     band   -- (B1, B2, B3), each even; centred frequencies -B/2 .. B/2-1
     nt     -- number of time steps (dt = 1/nt)
-    alpha, gamma, s -- L = (-alpha*Laplacian + gamma)^s, regulariser L^T L
+    alpha, gamma, s -- L = (-alpha*Laplacian + gamma)^s, regulariser L^T L;
+              s may be a half-integer (2s integer): s = 1/2 gives the H^1
+              regulariser alpha*omega + gamma of the incompressible experiments
     sigma  -- weight of the image term sigma^-2 ||m(1) - I1||^2 (Eq. 35)
+    incompressible -- restrict v~ to divergence-free band fields (Eq. 4, gamma = 1)
     """
 
     n: tuple
@@ -79,8 +87,9 @@ class Params:
     nt: int = 10
     alpha: float = 3.0
     gamma: float = 1.0
-    s: int = 2
+    s: float = 2
     sigma: float = 1.0
+    incompressible: bool = False
 
     @property
     def dt(self) -> float:
@@ -145,13 +154,40 @@ def laplacian_symbol(n, band) -> np.ndarray:
 
 def regulariser_weights(p: Params) -> np.ndarray:
     """A(k) = (alpha omega(k) + gamma)^(2s): symbol of L^T L, L = (-alpha Lap + gamma)^s.
-    The preconditioner K~ = (L^T L)^-1 is 1/A."""
-    return (p.alpha * laplacian_symbol(p.n, p.band) + p.gamma) ** (2 * p.s)
+    The preconditioner K~ = (L^T L)^-1 is 1/A.  2s must be an integer."""
+    q = int(round(2 * p.s))
+    if q != 2 * p.s or q < 0:
+        raise ValueError("2s must be a non-negative integer")
+    return (p.alpha * laplacian_symbol(p.n, p.band) + p.gamma) ** q
 
 
 def regulariser_energy(vt: np.ndarray, A: np.ndarray) -> float:
     """1/2 <L~ v~, v~>_{l2} for a stationary velocity (time integral over [0, 1])."""
     return 0.5 * float(np.sum(A[None] * np.abs(vt) ** 2))
+
+
+# ----------------------------------------------------------------------------
+# Incompressible form (Eq. 4 with gamma = 1, constraint taken in the band)
+# ----------------------------------------------------------------------------
+
+
+def leray_matrices(n, band) -> np.ndarray:
+    """(B1, B2, B3, 3, 3) real: P(k) = I - kappa kappa^T / |kappa|^2 with
+    kappa_d = 2 pi k_d / N_d, the wave vector of the Fourier mode k on the voxel
+    grid (h = 1); P(0) = I.  The divergence of the mode v~(k) e^{i kappa.x} is
+    i kappa.v~(k) e^{i kappa.x}, so P(k) v~(k) is the divergence-free part."""
+    kap = [2.0 * np.pi * band_frequencies(band[d]) / n[d] for d in range(3)]
+    K = np.stack(np.meshgrid(*kap, indexing="ij"), axis=-1)          # (B1, B2, B3, 3)
+    k2 = np.sum(K * K, axis=-1)
+    outer = K[..., :, None] * K[..., None, :]
+    safe = np.where(k2 > 0.0, k2, 1.0)
+    return np.eye(3) - np.where(k2[..., None, None] > 0.0, outer / safe[..., None, None], 0.0)
+
+
+def leray(vt: np.ndarray, n) -> np.ndarray:
+    """Apply P(k) to the three components of every band coefficient."""
+    Pk = leray_matrices(n, vt.shape[1:])
+    return np.einsum("abkcd,dabk->cabk", Pk, vt)
 
 
 # ----------------------------------------------------------------------------
@@ -242,6 +278,8 @@ class Point:
     def __init__(self, vt: np.ndarray, I0: np.ndarray, I1: np.ndarray, p: Params):
         self.p = p
         self.vt = np.asarray(vt, dtype=np.complex128)
+        if p.incompressible:
+            self.vt = leray(self.vt, p.n)       # the energy is evaluated at P v~
         self.I1 = np.asarray(I1, dtype=np.float64)
         self.A = regulariser_weights(p)
         self.d = displacement(self.vt, p)
@@ -274,11 +312,13 @@ class Point:
         return b, lam
 
     def gradient(self):
-        """g~ = A v~ + pi(b), final condition lambda^nt = -(2/sigma^2)(m^nt - I1).
-        Returns (g~, b, lambda^0)."""
+        """g~ = A v~ + pi(b), final condition lambda^nt = -(2/sigma^2)(m^nt - I1);
+        incompressible: P applied to that.  Returns (g~, b, lambda^0)."""
         lam_final = -(2.0 / self.p.sigma**2) * (self.m[-1] - self.I1)
         b, lam0 = self.adjoint_chain(lam_final)
         g = self.A[None] * self.vt + project(b, self.p.band)
+        if self.p.incompressible:
+            g = leray(g, self.p.n)
         return g, b, lam0
 
     def incremental_state(self, dvt: np.ndarray) -> np.ndarray:
@@ -296,12 +336,16 @@ class Point:
         -(2/sigma^2) dm^nt, dlambda^n = S^T dlambda^{n+1},
         db = dt sum dlambda^{n+1} G^n.  The Gauss-Newton drops of Section 3.4 remove
         the pi(lambda grad dm) term and the dJ term (all second derivatives of
-        the transport).  Returns (H dv~, dm^nt, db)."""
+        the transport).  Incompressible: P H P.  Returns (H dv~, dm^nt, db)."""
         dvt = np.asarray(dvt, dtype=np.complex128)
+        if self.p.incompressible:
+            dvt = leray(dvt, self.p.n)
         dm1 = self.incremental_state(dvt)
         dlam_final = -(2.0 / self.p.sigma**2) * dm1
         db, _ = self.adjoint_chain(dlam_final)
         h = self.A[None] * dvt + project(db, self.p.band)
+        if self.p.incompressible:
+            h = leray(h, self.p.n)
         return h, dm1, db
 
 

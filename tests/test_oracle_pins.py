@@ -166,19 +166,22 @@ def test_regulariser_symbol_is_stencil_eigenvalue():
     """A(k) = eigenvalue of (alpha(-Lap_h) + gamma) applied 2s times to the Fourier
     mode k, with Lap_h the periodic 7-point stencil (catches a wrong exponent,
     a missing 2 pi or a cos/sin mix-up)."""
-    p = O.Params(n=(10, 12, 8), band=(6, 8, 4), alpha=3.0, gamma=1.0, s=2)
-    A = O.regulariser_weights(p)
-    omega = O.laplacian_symbol(p.n, p.band)
-    x = np.indices(p.n)
-    for j in [(0, 0, 0), (1, 5, 2), (3, 4, 0), (5, 7, 3)]:
-        k = [j[d] - p.band[d] // 2 for d in range(3)]
-        mode = np.exp(2j * np.pi * sum(k[d] * x[d] / p.n[d] for d in range(3)))
-        lap = _neg_laplacian(mode)
-        assert np.max(np.abs(lap - omega[j] * mode)) < 1e-12
-        u = mode
-        for _ in range(2 * p.s):
-            u = p.alpha * _neg_laplacian(u) + p.gamma * u
-        assert np.max(np.abs(u - A[j] * mode)) < 1e-9 * A[j]
+    for s in (2, 0.5):     # s = 1/2: the H^1 regulariser alpha(-Lap) + gamma
+        p = O.Params(n=(10, 12, 8), band=(6, 8, 4), alpha=3.0, gamma=1.0, s=s)
+        A = O.regulariser_weights(p)
+        omega = O.laplacian_symbol(p.n, p.band)
+        x = np.indices(p.n)
+        for j in [(0, 0, 0), (1, 5, 2), (3, 4, 0), (5, 7, 3)]:
+            k = [j[d] - p.band[d] // 2 for d in range(3)]
+            mode = np.exp(2j * np.pi * sum(k[d] * x[d] / p.n[d] for d in range(3)))
+            lap = _neg_laplacian(mode)
+            assert np.max(np.abs(lap - omega[j] * mode)) < 1e-12
+            u = mode
+            for _ in range(int(2 * s)):
+                u = p.alpha * _neg_laplacian(u) + p.gamma * u
+            assert np.max(np.abs(u - A[j] * mode)) < 1e-9 * A[j]
+    with pytest.raises(ValueError):
+        O.regulariser_weights(O.Params(n=(8, 8, 8), band=(4, 4, 4), s=0.3))
 
 
 # ----------------------------------------------------------------------------
@@ -446,3 +449,155 @@ def test_newton_decreases_energy_and_gradient():
     assert rep.iterations >= 3
     assert all(b < a for a, b in zip(rep.energies, rep.energies[1:]))
     assert rep.grad_inf_rel < 0.5
+
+
+# ----------------------------------------------------------------------------
+# Incompressible form (Eq. 4 with gamma = 1, constraint in the band)
+# ----------------------------------------------------------------------------
+
+N_INC = (12, 10, 8)      # anisotropic, so a wave vector without the 1/N_d shows up
+B_INC = (6, 4, 6)
+
+
+def _band_field(vt, n, pts):
+    """The band-limited field Re sum_k v~(k) exp(2 pi i sum_d k_d x_d / N_d) at
+    arbitrary real points (P, 3), summed directly (not through the oracle)."""
+    B = vt.shape[1:]
+    ks = np.stack(np.meshgrid(*[np.arange(b) - b // 2 for b in B], indexing="ij"),
+                  axis=-1).reshape(-1, 3)
+    phase = np.exp(2j * np.pi * (pts / np.asarray(n, float)) @ ks.T)     # (P, K)
+    return (phase @ vt.reshape(3, -1).T).real                           # (P, 3)
+
+
+def _fd_jacobian(vt, n, pts, h=1e-5):
+    """(P, 3, 3): d f_c / d x_e by central differences of _band_field."""
+    J = np.zeros((len(pts), 3, 3))
+    for e in range(3):
+        step = np.zeros(3)
+        step[e] = h
+        J[:, :, e] = (_band_field(vt, n, pts + step) - _band_field(vt, n, pts - step)) / (2 * h)
+    return J
+
+
+def test_leray_field_is_divergence_free():
+    """The field of P v~ has zero divergence at off-grid points, by finite
+    differences of the directly summed trigonometric polynomial, while the field
+    of v~ does not (catches a wave vector without 1/N_d, a transposed axis, the
+    projector applied to the wrong index)."""
+    vt = synth.random_coefficients(B_INC, 81, bound=2.0)
+    pts = np.random.default_rng(82).uniform(0, 1, (64, 3)) * np.asarray(N_INC)
+    div_raw = np.trace(_fd_jacobian(vt, N_INC, pts), axis1=1, axis2=2)
+    div_inc = np.trace(_fd_jacobian(O.leray(vt, N_INC), N_INC, pts), axis1=1, axis2=2)
+    scale = np.max(np.abs(div_raw))
+    assert scale > 0.1
+    assert np.max(np.abs(div_inc)) < 1e-8 * scale
+
+
+def test_leray_is_orthogonal_helmholtz_split():
+    """v = P v + (v - P v): P is idempotent and self-adjoint in <.,.>, and the
+    removed part is a gradient field (zero curl by finite differences), the
+    L2-orthogonal complement of the divergence-free fields."""
+    v = synth.random_coefficients(B_INC, 83, bound=2.0)
+    w = synth.random_coefficients(B_INC, 84, bound=2.0)
+    Pv, Pw = O.leray(v, N_INC), O.leray(w, N_INC)
+    assert rel(O.leray(Pv, N_INC), Pv) < 1e-14
+    assert abs(O.inner(Pv, w) - O.inner(v, Pw)) < 1e-12 * np.linalg.norm(v) * np.linalg.norm(w)
+    assert abs(O.inner(v - Pv, Pw)) < 1e-12 * np.linalg.norm(v) * np.linalg.norm(w)
+    pts = np.random.default_rng(85).uniform(0, 1, (48, 3)) * np.asarray(N_INC)
+    J = _fd_jacobian(v - Pv, N_INC, pts)
+    curl = np.stack([J[:, 2, 1] - J[:, 1, 2], J[:, 0, 2] - J[:, 2, 0], J[:, 1, 0] - J[:, 0, 1]])
+    Jv = _fd_jacobian(v, N_INC, pts)
+    assert np.max(np.abs(curl)) < 1e-8 * np.max(np.abs(Jv))
+    # the zero frequency (a constant field) is divergence-free and kept
+    c = np.zeros((3,) + B_INC, complex)
+    c[(slice(None),) + tuple(b // 2 for b in B_INC)] = [1.0, -2.0, 0.5j]
+    assert rel(O.leray(c, N_INC), c) < 1e-15
+
+
+def test_incompressible_departure_jacobian_is_one_to_second_order():
+    """With a divergence-free velocity, det(I + grad d) of the step map
+    x -> x + d(x), d = -dt iota(P v~), differs from 1 only at second order in dt
+    (halving dt divides the deviation by 4), while a compressible velocity
+    deviates at first order (by 2): the Jacobians stay 1."""
+    vt = synth.random_coefficients(B_INC, 86, bound=2.0)
+    pts = np.random.default_rng(87).uniform(0, 1, (64, 3)) * np.asarray(N_INC)
+    dev = {}
+    for name, v in (("inc", O.leray(vt, N_INC)), ("comp", vt)):
+        G = _fd_jacobian(v, N_INC, pts)
+        for dt in (0.1, 0.05):
+            det = np.linalg.det(np.eye(3)[None] - dt * G)
+            dev[name, dt] = np.max(np.abs(det - 1.0))
+    assert 3.5 < dev["inc", 0.1] / dev["inc", 0.05] < 4.5
+    assert 1.5 < dev["comp", 0.1] / dev["comp", 0.05] < 2.5
+    assert dev["inc", 0.1] < 0.2 * dev["comp", 0.1]
+
+
+def _kink_free_inc(vt, dvt, eps, p):
+    lo = np.floor(O.displacement(O.leray(vt - eps * dvt, p.n), p))
+    hi = np.floor(O.displacement(O.leray(vt + eps * dvt, p.n), p))
+    return np.array_equal(lo, hi)
+
+
+def test_incompressible_gradient_matches_finite_differences():
+    """E(P v~) with the H^1 regulariser (s = 1/2): the gradient P grad E(P v~)
+    against central differences along unprojected random directions
+    (catches a projection missing on the input, the output or the regulariser)."""
+    p = O.Params(n=(12, 12, 10), band=(6, 4, 6), nt=6, s=0.5, incompressible=True)
+    I0, I1, _ = synth.blob_pair(p.n, 88, max_disp=2.0)
+    vt = synth.random_coefficients(p.band, 89, bound=2.5)
+    g, _, _ = O.Point(vt, I0, I1, p).gradient()
+    assert rel(O.leray(g, p.n), g) < 1e-14
+    eps = 1e-6
+    checked = 0
+    for s in range(24):
+        dvt = synth.random_direction(p.band, 900 + s)
+        if not _kink_free_inc(vt, dvt, eps, p):
+            continue
+        fd = (O.energy(vt + eps * dvt, I0, I1, p) - O.energy(vt - eps * dvt, I0, I1, p)) / (2 * eps)
+        dd = O.inner(g, dvt)
+        assert abs(fd - dd) <= 1e-6 * abs(dd), (s, fd, dd)
+        checked += 1
+        if checked == 8:
+            break
+    assert checked == 8
+
+
+def test_incompressible_gn_hessian():
+    """P H P: symmetric, positive on divergence-free directions, zero on gradient
+    fields, with range in the divergence-free fields; at zero residual it is the
+    central difference of the incompressible gradient."""
+    p = O.Params(n=(12, 10, 12), band=(4, 4, 6), nt=5, s=0.5, incompressible=True)
+    I0, _, _ = synth.blob_pair(p.n, 91, max_disp=2.0)
+    vt = synth.random_coefficients(p.band, 92, bound=2.0)
+    I1 = O.Point(vt, I0, I0, p).m[-1]
+    pt = O.Point(vt, I0, I1, p)
+    v = synth.random_direction(p.band, 93)
+    w = synth.random_direction(p.band, 94)
+    Hv, Hw = pt.gn_hessvec(v)[0], pt.gn_hessvec(w)[0]
+    a, b = O.inner(Hv, w), O.inner(v, Hw)
+    assert abs(a - b) <= 1e-10 * max(abs(a), abs(b))
+    assert O.inner(Hv, v) > 0.0
+    assert rel(O.leray(Hv, p.n), Hv) < 1e-14
+    grad_part = v - O.leray(v, p.n)
+    assert np.linalg.norm(pt.gn_hessvec(grad_part)[0]) < 1e-12 * np.linalg.norm(Hv)
+    eps = 1e-6
+    checked = 0
+    for s in range(6):
+        dvt = synth.random_direction(p.band, 950 + s)
+        if not _kink_free_inc(vt, dvt, eps, p):
+            continue
+        gp = O.Point(vt + eps * dvt, I0, I1, p).gradient()[0]
+        gm = O.Point(vt - eps * dvt, I0, I1, p).gradient()[0]
+        assert rel(pt.gn_hessvec(dvt)[0], (gp - gm) / (2 * eps)) < 1e-6
+        checked += 1
+    assert checked >= 2
+
+
+def test_incompressible_newton_stays_divergence_free():
+    p = O.Params(n=(16, 16, 16), band=(4, 4, 4), nt=5, s=0.5, incompressible=True)
+    I0, I1, _ = synth.blob_pair(p.n, 95, max_disp=2.0)
+    rep = O.newton(np.zeros((3,) + p.band, complex), I0, I1, p, max_newton=3, max_pcg=8,
+                   gtol=1e-6)
+    assert rep.iterations >= 2
+    assert all(b < a for a, b in zip(rep.energies, rep.energies[1:]))
+    assert rel(O.leray(rep.vt, p.n), rep.vt) < 1e-13
