@@ -22,6 +22,8 @@ fields", arXiv 1807.05117):
   Section 2.2);
 * Gauss-Newton Hessian-vector product H~dv~ = L~dv~ + pi(dlambda grad m) with
   the Gauss-Newton drops of Section 3.4 applied to Eq. 46;
+* the full Newton Hessian-vector product (Eqs. 44-46 without those drops):
+  the exact second derivative of the discrete energy;
 * PCG with preconditioner K~ and the reduced-space Newton update with a step
   length (Section 3.4, Eqs. 54-55; Section 2.4, Eqs. 31-32);
 * the incompressible form (Eq. 4 with gamma = 1, imposed in the band as in
@@ -211,6 +213,8 @@ class Stencil:
     S   -- (S m)(x) = trilinear value of m at x + d(x)
     D_a -- (D_a m)(x) = partial derivative along axis a of the trilinear
            polynomial of the cell used at x (right derivative on a node)
+    D2[(a, b)], a < b -- the mixed second partial d_a d_b of that polynomial
+           (its pure second partials are zero: it is linear along each axis)
     The cell on axis a is x_a + floor(d_a(x)) and the local coordinate is
     f_a = d_a - floor(d_a); corner o in {0,1}^3 has weight
     prod_a (f_a if o_a else 1 - f_a).
@@ -226,7 +230,9 @@ class Stencil:
         rows = np.arange(V)
         w = [[1.0 - f[a], f[a]] for a in range(3)]       # weight of corner bit o_a
         dw = [-1.0, 1.0]                                   # its derivative in p_a
+        pairs = ((0, 1), (0, 2), (1, 2))
         cols, vals, dvals = [], [], [[], [], []]
+        d2vals = {ab: [] for ab in pairs}
         for o in itertools.product((0, 1), repeat=3):
             idx = [(grid[a] + fl[a] + o[a]) % shape[a] for a in range(3)]
             cols.append(np.ravel_multi_index(idx, shape).ravel())
@@ -234,12 +240,17 @@ class Stencil:
             dvals[0].append((dw[o[0]] * w[1][o[1]] * w[2][o[2]]).ravel())
             dvals[1].append((w[0][o[0]] * dw[o[1]] * w[2][o[2]]).ravel())
             dvals[2].append((w[0][o[0]] * w[1][o[1]] * dw[o[2]]).ravel())
+            for a, b in pairs:
+                c3 = 3 - a - b
+                d2vals[a, b].append((dw[o[a]] * dw[o[b]] * w[c3][o[c3]]).ravel())
         r = np.tile(rows, 8)
         c = np.concatenate(cols)
         self.shape = shape
         self.S = sp.csr_matrix((np.concatenate(vals), (r, c)), shape=(V, V))
         self.D = [sp.csr_matrix((np.concatenate(dv), (r, c)), shape=(V, V))
                   for dv in dvals]
+        self.D2 = {ab: sp.csr_matrix((np.concatenate(d2vals[ab]), (r, c)), shape=(V, V))
+                   for ab in pairs}
 
     def apply(self, m: np.ndarray) -> np.ndarray:
         return (self.S @ m.ravel()).reshape(self.shape)
@@ -251,6 +262,21 @@ class Stencil:
         """(3, N1, N2, N3): exact gradient of the interpolant of m at x + d(x)."""
         mf = m.ravel()
         return np.stack([(Da @ mf).reshape(self.shape) for Da in self.D])
+
+    def hessian_times(self, m: np.ndarray, u: np.ndarray) -> np.ndarray:
+        """(3, ...): (Hess T[m](x + d(x))) u(x), the second derivatives of the
+        cell polynomial of m at the departure point applied to the vector field u."""
+        mf = m.ravel()
+        out = np.zeros((3,) + self.shape)
+        for (a, b), Dab in self.D2.items():
+            h = (Dab @ mf).reshape(self.shape)
+            out[a] += h * u[b]
+            out[b] += h * u[a]
+        return out
+
+    def gradient_transpose(self, q: np.ndarray) -> np.ndarray:
+        """sum_a D_a^T q_a for a vector field q: the transpose of m -> D m . q."""
+        return sum((self.D[a].T @ q[a].ravel()) for a in range(3)).reshape(self.shape)
 
 
 def state(I0: np.ndarray, st: Stencil, nt: int) -> list:
@@ -298,6 +324,17 @@ class Point:
         if self._G[n] is None:
             self._G[n] = self.stencil.gradient(self.m[n])
         return self._G[n]
+
+    def adjoint_states(self) -> list:
+        """[lambda^0, ..., lambda^nt] of the gradient's adjoint solve at this point."""
+        if getattr(self, "_lams", None) is None:
+            lam = -(2.0 / self.p.sigma**2) * (self.m[-1] - self.I1)
+            lams = [lam]
+            for _ in range(self.p.nt):
+                lam = self.stencil.apply_transpose(lam)
+                lams.append(lam)
+            self._lams = lams[::-1]
+        return self._lams
 
     def adjoint_chain(self, lam_final: np.ndarray):
         """lambda^n = S^T lambda^{n+1} (discrete adjoint equation, Eq. 8) and the
@@ -349,6 +386,41 @@ class Point:
         return h, dm1, db
 
 
+    def full_hessvec(self, dvt: np.ndarray):
+        """Exact Hessian of the discrete energy (Newton: Eqs. 44-46 without the
+        drops of Section 3.4), with dd = -dt iota(dv~):
+          dm^0 = 0, dm^{n+1} = S dm^n + G^n . dd             (incremental state)
+          dlambda^nt = -(2/sigma^2) dm^nt,
+          dlambda^n = S^T dlambda^{n+1} + sum_a D_a^T(dd_a lambda^{n+1})
+                      (the variation of S^T: the dJ term of the incremental adjoint)
+          db = dt sum_n [dlambda^{n+1} G^n
+                         + lambda^{n+1} (D dm^n + Hess T[m^n] dd)]
+                      (pi(lambda grad dm), and the move of the departure point
+                       inside its cell)
+          H dv~ = A dv~ + pi(db);  incompressible: P H P.
+        Returns (H dv~, dm^nt, db)."""
+        p, st = self.p, self.stencil
+        dvt = np.asarray(dvt, dtype=np.complex128)
+        if p.incompressible:
+            dvt = leray(dvt, p.n)
+        dd = -p.dt * expand(dvt, p.n)
+        dms = [np.zeros(tuple(p.n))]
+        for n in range(p.nt):
+            dms.append(st.apply(dms[-1]) + np.sum(self.grad_m(n) * dd, axis=0))
+        lams = self.adjoint_states()
+        dlam = -(2.0 / p.sigma**2) * dms[-1]
+        db = np.zeros((3,) + tuple(p.n))
+        for n in range(p.nt - 1, -1, -1):
+            lam1 = lams[n + 1]
+            dG = st.gradient(dms[n]) + st.hessian_times(self.m[n], dd)
+            db += p.dt * (dlam[None] * self.grad_m(n) + lam1[None] * dG)
+            dlam = st.apply_transpose(dlam) + st.gradient_transpose(dd * lam1[None])
+        h = self.A[None] * dvt + project(db, p.band)
+        if p.incompressible:
+            h = leray(h, p.n)
+        return h, dms[-1], db
+
+
 def energy(vt, I0, I1, p: Params) -> float:
     return Point(vt, I0, I1, p).energy
 
@@ -362,9 +434,14 @@ class NegativeCurvature(RuntimeError):
     pass
 
 
-def pcg(apply_H, rhs: np.ndarray, Minv: np.ndarray, eta: float, maxit: int):
+def pcg(apply_H, rhs: np.ndarray, Minv: np.ndarray, eta: float, maxit: int,
+        truncate: bool = False):
     """Preconditioned CG on H x = rhs from x = 0 with M^-1 = K~ (elementwise Minv).
     Stops when ||r_j|| <= eta ||r_0|| or after maxit iterations.
+    <p, Hp> <= 0 raises NegativeCurvature, or with truncate (the full Newton
+    Hessian, which can be indefinite away from a minimum, Section 3.4) ends the
+    solve: the iterate so far, or the first direction M^-1 rhs when no update
+    was made (truncated Newton-CG; both are descent directions for rhs = -g).
     Returns (x, iterations, ||r|| / ||r_0||)."""
     x = np.zeros_like(rhs)
     r = rhs.copy()
@@ -380,7 +457,9 @@ def pcg(apply_H, rhs: np.ndarray, Minv: np.ndarray, eta: float, maxit: int):
         q = apply_H(p)
         pq = inner(p, q)
         if pq <= 0.0:
-            raise NegativeCurvature(f"<p, Hp> = {pq}")
+            if not truncate:
+                raise NegativeCurvature(f"<p, Hp> = {pq}")
+            return (p.copy() if it == 0 else x), it, rel
         alpha = rz / pq
         x = x + alpha * p
         r = r - alpha * q
@@ -412,8 +491,9 @@ class NewtonReport:
 
 
 def newton(vt0, I0, I1, p: Params, max_newton=5, max_pcg=10, gtol=1e-2,
-           forcing=None, c1=1e-4, max_halvings=10) -> NewtonReport:
-    """Gauss-Newton-Krylov: p from PCG on H p = -g (preconditioner K~), then
+           forcing=None, c1=1e-4, max_halvings=10, hessian="gn") -> NewtonReport:
+    """Gauss-Newton-Krylov (hessian="gn") or Newton-Krylov (hessian="full",
+    truncated PCG): p from PCG on H p = -g (preconditioner K~), then
     v~ <- v~ + eps p with Armijo backtracking from eps = 1 (halving).
 
     The paper writes the update as v - eps dv with H dv = -g (Eqs. 54-55); read
@@ -435,8 +515,9 @@ def newton(vt0, I0, I1, p: Params, max_newton=5, max_pcg=10, gtol=1e-2,
         eta = (min(0.5, np.sqrt(np.sqrt(inner(g, g)) / g0_2)) if forcing is None
                else forcing)
         cur = pt
-        step, its, _ = pcg(lambda v: cur.gn_hessvec(v)[0], -g, 1.0 / cur.A[None],
-                           eta, max_pcg)
+        hv = cur.full_hessvec if hessian == "full" else cur.gn_hessvec
+        step, its, _ = pcg(lambda v: hv(v)[0], -g, 1.0 / cur.A[None], eta, max_pcg,
+                           truncate=(hessian == "full"))
         pcg_its.append(its)
         slope = inner(g, step)
         eps = 1.0

@@ -601,3 +601,109 @@ def test_incompressible_newton_stays_divergence_free():
     assert rep.iterations >= 2
     assert all(b < a for a, b in zip(rep.energies, rep.energies[1:]))
     assert rel(O.leray(rep.vt, p.n), rep.vt) < 1e-13
+
+
+# ----------------------------------------------------------------------------
+# Full Newton Hessian (Eqs. 44-46 without the drops of Section 3.4)
+# ----------------------------------------------------------------------------
+
+
+def test_full_hessian_is_fd_of_gradient():
+    """Away from a minimum (sigma = 0.5, large residual) the full Hessian equals
+    central differences of the gradient to 1e-7, while the Gauss-Newton one is
+    off by more than 1e-3.  Dropping any one of the three terms that the
+    Gauss-Newton step leaves out (pi(lambda grad dm), the variation of S^T, the
+    move of the departure point inside its cell) changes the result by more
+    than 1e-4, so each is checked."""
+    p = O.Params(n=(12, 12, 12), band=(4, 6, 4), nt=5, sigma=0.5)
+    I0, I1, _ = synth.blob_pair(p.n, 51, max_disp=2.0)
+    vt = synth.random_coefficients(p.band, 52, bound=2.0)
+    pt = O.Point(vt, I0, I1, p)
+    eps = 1e-6
+    checked = 0
+    for s in range(8):
+        dvt = synth.random_direction(p.band, 1600 + s)
+        if not _kink_free(vt, dvt, eps, p):
+            continue
+        gp = O.Point(vt + eps * dvt, I0, I1, p).gradient()[0]
+        gm = O.Point(vt - eps * dvt, I0, I1, p).gradient()[0]
+        fd = (gp - gm) / (2 * eps)
+        assert rel(pt.full_hessvec(dvt)[0], fd) < 1e-7
+        assert rel(pt.gn_hessvec(dvt)[0], fd) > 1e-3
+        checked += 1
+        if checked == 4:
+            break
+    assert checked == 4
+
+
+def test_full_hessian_symmetric_and_gauss_newton_at_zero_residual():
+    p = O.Params(n=(16, 16, 16), band=(6, 6, 6), nt=6, sigma=0.5)
+    I0, I1, _ = synth.blob_pair(p.n, 1611, max_disp=2.0)
+    vt = synth.random_coefficients(p.band, 1612, bound=2.5)
+    pt = O.Point(vt, I0, I1, p)
+    v = synth.random_direction(p.band, 1613)
+    w = synth.random_direction(p.band, 1614)
+    a, b = O.inner(pt.full_hessvec(v)[0], w), O.inner(v, pt.full_hessvec(w)[0])
+    assert abs(a - b) <= 1e-10 * max(abs(a), abs(b))
+    # zero residual: lambda = 0, so the extra terms vanish
+    pt0 = O.Point(vt, I0, pt.m[-1], p)
+    assert rel(pt0.full_hessvec(v)[0], pt0.gn_hessvec(v)[0]) < 1e-13
+
+
+def test_full_hessian_equals_dense_fd_hessian_bruteforce():
+    """8^3 grid, band 4^3 (384 real parameters): the dense Hessian from central
+    differences of the gradient, one parameter at a time, against the
+    Hessian-vector product on random directions."""
+    p = O.Params(n=(8, 8, 8), band=(4, 4, 4), nt=3, sigma=0.5)
+    I0, I1, _ = synth.blob_pair(p.n, 1621, max_disp=1.5)
+    for seed in range(1622, 1680):
+        vt = synth.random_coefficients(p.band, seed, bound=1.2)
+        d = O.displacement(vt, p)
+        if np.min(np.abs(d - np.round(d))) >= 1e-4:
+            break
+    else:
+        raise AssertionError("no kink-free point")
+    pt = O.Point(vt, I0, I1, p)
+    P = 2 * 3 * 64
+    eps = 1e-6
+    H = np.zeros((P, P))
+    for j in range(P):
+        e = np.zeros(P)
+        e[j] = eps
+        de = _from_theta(e, vt.shape)
+        gp = O.Point(vt + de, I0, I1, p).gradient()[0]
+        gm = O.Point(vt - de, I0, I1, p).gradient()[0]
+        H[:, j] = _theta((gp - gm) / (2 * eps))
+    assert np.max(np.abs(H - H.T)) < 1e-6 * np.max(np.abs(H))
+    for s in range(4):
+        v = synth.random_direction(p.band, 1690 + s)
+        assert rel(_theta(pt.full_hessvec(v)[0]), H @ _theta(v)) < 1e-7
+
+
+def test_truncated_pcg_on_an_indefinite_hessian():
+    """With a weak regulariser the full Hessian is indefinite away from the
+    minimum: plain PCG raises, truncated PCG stops at the non-positive curvature
+    with a descent direction; with no update made it returns M^-1 rhs."""
+    p = O.Params(n=(12, 12, 12), band=(4, 4, 4), nt=5, sigma=1.0, alpha=0.0, gamma=0.1, s=1)
+    I0, I1, _ = synth.blob_pair(p.n, 51, max_disp=2.0)
+    pt = O.Point(synth.random_coefficients(p.band, 52, bound=2.0), I0, I1, p)
+    g = pt.gradient()[0]
+    with pytest.raises(O.NegativeCurvature):
+        O.pcg(lambda v: pt.full_hessvec(v)[0], -g, 1.0 / pt.A[None], 1e-10, 60)
+    x, its, _ = O.pcg(lambda v: pt.full_hessvec(v)[0], -g, 1.0 / pt.A[None], 1e-10, 60,
+                      truncate=True)
+    assert 1 <= its < 60
+    assert O.inner(g, x) < 0.0
+    Minv = 1.0 / pt.A[None]
+    x0, its0, _ = O.pcg(lambda v: -v, -g, Minv, 1e-10, 5, truncate=True)
+    assert its0 == 0 and rel(x0, -Minv * g) == 0.0
+
+
+def test_full_newton_decreases_energy():
+    p = O.Params(n=(16, 16, 16), band=(4, 4, 4), nt=5)
+    I0, I1, _ = synth.blob_pair(p.n, 71, max_disp=2.0)
+    rep = O.newton(np.zeros((3,) + p.band, complex), I0, I1, p, max_newton=4, max_pcg=8,
+                   gtol=1e-6, hessian="full")
+    assert rep.iterations >= 3
+    assert all(b < a for a, b in zip(rep.energies, rep.energies[1:]))
+    assert rep.grad_inf_rel < 0.5
