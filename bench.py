@@ -65,17 +65,22 @@ ADJ_BYTES = lambda nt: ((36 + 44 + 48 * (nt - 2)) if nt > 1 else 32)
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one interior adjoint-step
 # launch (k_adjoint_wide<0, 1, 1>, kept state gradient) at 128^3 from an ncu
-# capture, valid only for the sweep source it was captured from (SHA-256 of
-# csrc/sweeps.cu).
-ADJ_TRAFFIC = {"sweeps_sha256": "b359739e9e03d80ae29ef71c871e63986b004d617d425f77ab498e4ac44589a1",
-               "bytes": 94975744 + 6430976}
+# capture (profiles/k_adjoint_wide_128cube.md), valid only while the device code
+# of csrc/sweeps.cu (the text above its host-side marker line) is the code the
+# capture was taken from: SHA-256 of that text.
+SWEEPS_HOST_MARKER = "// ==== host side: launch shapes, launchers, sweep orchestration, autotuner ===="
+ADJ_TRAFFIC = {"sweeps_device_sha256": "da203be71439a4a829777d7c74f291929c9c70d155a5a8398a658a9065644bb4",
+               "bytes": 95065856 + 5990912}
 
 
 def adjoint_traffic():
     path = os.path.join(ROOT, "paper_1807_05117_gb300", "csrc", "sweeps.cu")
-    with open(path, "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()
-    return ADJ_TRAFFIC["bytes"] if sha == ADJ_TRAFFIC["sweeps_sha256"] else None
+    with open(path, encoding="utf-8") as f:
+        text = f.read()
+    if SWEEPS_HOST_MARKER not in text:
+        return None
+    sha = hashlib.sha256(text.split(SWEEPS_HOST_MARKER)[0].encode("utf-8")).hexdigest()
+    return ADJ_TRAFFIC["bytes"] if sha == ADJ_TRAFFIC["sweeps_device_sha256"] else None
 
 
 def peaks():
@@ -363,6 +368,54 @@ def measure_precision(precision, args, dev, I0g, I1g, flush, stream, dist, world
                 roofline=roofline, dvt=dvt, stage=stage)
 
 
+def measure_form(precision, dev, I0g, I1g, flush, stream, reps=3, hvp_reps=50, **form):
+    """Registrations/s and HVP/s of a variant of the path (plan keyword
+    arguments `form`) on the benchmark pair, the same fixed work per registration."""
+    import numpy as np
+    import torch
+
+    from paper_1807_05117_gb300 import blr, synth
+
+    prec = blr.BLR_MIXED if precision == "mixed" else blr.BLR_FP32
+    plan = blr.Plan(N, BAND, NT, precision=prec, **form)
+    plan.set_images(I0g, I1g)
+    vt = torch.zeros((3,) + BAND, dtype=torch.complex64, device=dev)
+
+    def step():
+        vt.zero_()
+        return plan.newton(vt, NEWTON, PCG, 0.0, 0.0)
+
+    for _ in range(2):
+        step()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    tot = 0.0
+    for k in range(reps):
+        flush.fill_(k & 0xFF)
+        e0.record(stream)
+        rep = step()
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    dvt = torch.from_numpy(synth.random_direction(BAND, SEED + 2).astype(np.complex64)).to(dev)
+    hout = torch.empty_like(dvt)
+    for _ in range(3):
+        plan.hessvec(dvt, hout)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(hvp_reps):
+        plan.hessvec(dvt, hout)
+    e1.record(stream)
+    e1.synchronize()
+    hvp_ms = e0.elapsed_time(e1) / hvp_reps
+    plan.close()
+    return {"precision": precision, "registrations_per_s": 1000.0 * reps / tot,
+            "ms_per_registration": tot / reps, "hvp_per_s": 1000.0 / hvp_ms, "hvp_ms": hvp_ms,
+            "final_energy": rep.energy, "energy0": rep.energy0,
+            "newton_iters": rep.newton_iters, "pcg_iters": rep.pcg_iters,
+            "n_hessvec": rep.n_hessvec, "status": rep.status}
+
+
 def main_ours(args):
     import numpy as np
     import torch
@@ -414,6 +467,15 @@ def main_ours(args):
                                  "autotuned": r["plan"].tuning()}
                              for p, r in res.items()}}
     plan = head["plan"]
+
+    # the survey's adjacent forms, measured on the same pair and work
+    if not args.no_forms:
+        line["forms"] = {
+            "incompressible_h1": dict(
+                measure_form(args.precision, dev, I0g, I1g, flush, stream, s=0.5,
+                             incompressible=True),
+                regulariser="H1: A = alpha omega + gamma (s = 1/2)",
+                constraint="divergence-free band fields (Leray projector)")}
 
     # end to end through the C-ABI with pinned host buffers
     if not args.no_e2e:
@@ -622,6 +684,8 @@ def main():
     ap.add_argument("--hvp-reps", type=int, default=50)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the incompressible-form measurement")
     ap.add_argument("--adjoint-traffic", type=float, default=None,
                     help="dram bytes per adjoint-step launch from an ncu capture of this kernel")
     ap.add_argument("--workload", choices=["phantom128", "uneven64"], default="phantom128",

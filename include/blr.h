@@ -5,7 +5,7 @@
  * Method: Hernandez, "Newton-Krylov optimization in PDE-constrained
  * diffeomorphic registration parameterized in the space of band-limited vector
  * fields" (arXiv 1807.05117), state-equation variant, stationary velocity,
- * Gauss-Newton Hessian.
+ * Gauss-Newton Hessian; compressible or incompressible velocities.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -20,7 +20,8 @@
  * iota      iota(v~)_c(x) = Re sum_k v~_c(k) exp(2 pi i sum_d k_d x_d / N_d).
  * pi        pi(f)_c(k) = sum_x f_c(x) exp(-2 pi i sum_d k_d x_d / N_d) = iota^T
  *           under <a, b> = Re sum a conj(b).
- * A(k)      (alpha*omega(k) + gamma)^(2s), omega(k) = sum_d 2(1 - cos(2 pi k_d/N_d));
+ * A(k)      (alpha*omega(k) + gamma)^(2s), omega(k) = sum_d 2(1 - cos(2 pi k_d/N_d))
+ *           (2s an integer);
  *           the regulariser L~ of Eq. 34 with L = (-alpha Lap + gamma)^s, and
  *           the preconditioner K~ = 1/A (Sections 3.1, 3.4).
  * Transport nt steps, dt = 1/nt; d = -dt * iota(v~) is the per-step
@@ -76,13 +77,24 @@ typedef struct blr_params {
     int nt;          /* number of time steps, >= 1                          */
     double alpha;    /* L = (-alpha Lap + gamma)^s, alpha >= 0              */
     double gamma;    /* gamma > 0                                           */
-    int s;           /* s >= 0                                              */
+    double s;        /* s >= 0 with 2s an integer <= 64 (A = symbol^(2s)).  */
+                     /* s = 0.5 is the H^1 regulariser alpha(-Lap) + gamma   */
+                     /* of the incompressible experiments (Section 4)       */
     double sigma;    /* image term weight 1/sigma^2, sigma > 0              */
     int precision;   /* BLR_FP32 or BLR_MIXED                               */
     int ckpt_every;  /* 0: keep all nt+1 states.  k in 1..nt-1: keep only   */
                      /* m^0, m^k, m^2k, ... and m^nt; adjoint and HVP sweeps */
                      /* recompute each segment's states from its checkpoint  */
                      /* (same FP32 arithmetic, so results are bit-identical) */
+    int incompressible; /* 0: compressible velocities (Eq. 4, gamma = 0).    */
+                     /* 1: v~ restricted to divergence-free band fields      */
+                     /* (Eq. 4, gamma = 1, imposed in the band): every call  */
+                     /* that takes a velocity evaluates the energy at P v~,  */
+                     /* P the Leray projector P(k) = I - kappa kappa^T /     */
+                     /* |kappa|^2, kappa_d = 2 pi k_d / N_d (P(0) = I); the  */
+                     /* gradient is then P grad E(P v~) and the Hessian      */
+                     /* P H P.  blr_expand / blr_project / blr_adjoint stay  */
+                     /* the plain operators.  Batches reject it.             */
 } blr_params;
 
 /* Result of blr_newton (host struct filled by the library). */
@@ -207,7 +219,7 @@ int blr_newton(blr_plan_t plan, float *vt, int max_newton, int max_pcg,
 typedef struct blr_batch *blr_batch_t;
 
 /* params: host array of npairs descriptions.  BLR_EINVAL if they differ in nt,
- * request BLR_MIXED or checkpoints, or one is invalid. */
+ * request BLR_MIXED, checkpoints or the incompressible form, or one is invalid. */
 int blr_batch_create(const blr_params *params, int npairs, blr_batch_t *out);
 int blr_batch_destroy(blr_batch_t batch);
 

@@ -22,8 +22,9 @@ int validate(const blr_params *p) {
             return BLR_EINVAL;
     }
     if (p->band[2] > 64) return BLR_EINVAL;      // stage A' keeps <= 64 frequencies per lane pair
-    if (p->nt < 1 || !(p->sigma > 0) || !(p->gamma > 0) || !(p->alpha >= 0) || p->s < 0)
-        return BLR_EINVAL;
+    if (p->nt < 1 || !(p->sigma > 0) || !(p->gamma > 0) || !(p->alpha >= 0)) return BLR_EINVAL;
+    if (!(p->s >= 0 && p->s <= 32) || 2.0 * p->s != floor(2.0 * p->s)) return BLR_EINVAL;
+    if (p->incompressible != 0 && p->incompressible != 1) return BLR_EINVAL;
     if (p->precision != BLR_FP32 && p->precision != BLR_MIXED) return BLR_EINVAL;
     if (p->ckpt_every < 0) return BLR_EINVAL;
     long long V = (long long)p->n[0] * p->n[1] * p->n[2];
@@ -83,6 +84,7 @@ size_t layout(blr_plan *P, char *base) {
     }
     float **vecs[] = {&P->vt, &P->g, &P->r, &P->pv, &P->q, &P->x, &P->trial, &P->step, &P->vtmp};
     for (float **v : vecs) *v = a.take<float>(P->nfloat);
+    P->vproj = P->p.incompressible ? a.take<float>(P->nfloat) : nullptr;
     P->dsc = a.take<double>(SC_COUNT);
     P->dstatus = a.take<int>(1);
     P->pcg_live = a.take<int>(4);
@@ -115,10 +117,15 @@ int flags_to_status(int flags) {
 }
 
 // Forward solve at vt (device) -> current point; energy into dsc (and energy_out).
+// Incompressible plans keep P vt as the current velocity.
 int state_at(blr_plan *P, const float *vt, double *energy_out, cudaStream_t s) {
-    if (vt != P->vt)
+    int rc;
+    if (P->p.incompressible) {
+        if ((rc = vec_leray(P, P->vt, vt, s))) return rc;
+    } else if (vt != P->vt) {
         BLR_CK(cudaMemcpyAsync(P->vt, vt, P->nfloat * sizeof(float), cudaMemcpyDefault, s));
-    int rc = dft_expand(P, P->vt, P->d, 1, s);
+    }
+    rc = dft_expand(P, P->vt, P->d, 1, s);
     if (rc) return rc;
     if ((rc = sweep_state(P, s))) return rc;
     if ((rc = energy_finalize(P, P->vt, energy_out, (int)sweep_blocks(P), s))) return rc;
@@ -126,19 +133,26 @@ int state_at(blr_plan *P, const float *vt, double *energy_out, cudaStream_t s) {
     return BLR_OK;
 }
 
-// g = A v~ + pi(b) at the current point.
+// g = A v~ + pi(b) at the current point (incompressible: P applied to it).
 int gradient_here(blr_plan *P, float *g, cudaStream_t s) {
     int rc = sweep_adjoint(P, P->b, nullptr, s);
     if (rc) return rc;
-    return dft_project(P, P->b, g, P->vt, s);
+    if ((rc = dft_project(P, P->b, g, P->vt, s))) return rc;
+    return P->p.incompressible ? vec_leray(P, g, g, s) : BLR_OK;
 }
 
+// H dv~ = A dv~ + pi(db) (incompressible: P H P dv~).
 int hessvec_here(blr_plan *P, const float *dvt, float *hdv, cudaStream_t s) {
-    int rc = dft_expand(P, dvt, P->dv, 0, s);
-    if (rc) return rc;
+    int rc;
+    if (P->p.incompressible) {
+        if ((rc = vec_leray(P, P->vproj, dvt, s))) return rc;
+        dvt = P->vproj;
+    }
+    if ((rc = dft_expand(P, dvt, P->dv, 0, s))) return rc;
     if ((rc = sweep_incremental(P, s))) return rc;
     if ((rc = sweep_adjoint(P, P->b, nullptr, s))) return rc;
-    return dft_project(P, P->b, hdv, dvt, s);
+    if ((rc = dft_project(P, P->b, hdv, dvt, s))) return rc;
+    return P->p.incompressible ? vec_leray(P, hdv, hdv, s) : BLR_OK;
 }
 
 // PCG (Eq. 55).  The stopping test runs on the device (k_pcg_update), so the
@@ -379,6 +393,7 @@ int blr_newton(blr_plan_t P, float *vt, int max_newton, int max_pcg, double gtol
     int flags = 0, rc;
     BLR_CK(cudaMemsetAsync(P->dstatus, 0, sizeof(int), s));
     BLR_CK(cudaMemcpyAsync(P->vtmp, vt, vbytes, cudaMemcpyDefault, s));
+    if (P->p.incompressible && (rc = vec_leray(P, P->vtmp, P->vtmp, s))) return rc;
     if ((rc = state_at(P, P->vtmp, nullptr, s))) return rc;
     R.n_state = 1;
     if ((rc = gradient_here(P, P->g, s))) return rc;

@@ -135,6 +135,7 @@ struct blr_plan {
 
     // Krylov / Newton vectors (nfloat each)
     float *g, *r, *pv, *q, *x, *trial, *step, *vtmp;
+    float *vproj;       // incompressible plans: the projected HVP direction (else nullptr)
 
     double *dsc;        // device scalars (SC_COUNT)
     double *hsc;        // pinned host mirror
@@ -217,4 +218,6 @@ int pcg_direction(blr_plan *P, cudaStream_t s, const int *live = nullptr);
 enum { PCG_RUN = 0, PCG_CURV = 1, PCG_NAN_PQ = 2, PCG_NAN_REL = 3 };
 // y = a + alpha * x
 int vec_axpy(blr_plan *P, float *y, const float *a, const float *x, double alpha, cudaStream_t s);
+// out = P in, the Leray projector of the incompressible form (out may alias in)
+int vec_leray(blr_plan *P, float *out, const float *in, cudaStream_t s);
 int reduce_partials_needed();

@@ -39,9 +39,9 @@ __global__ void k_table_w1(float *W1, int N, int B) {
     W1[(2 * j + 1) * (long long)N + x] = (float)(-s);
 }
 
-// A(k) = (alpha omega(k) + gamma)^(2s), omega = sum_d 2(1 - cos(2 pi k_d / N_d)).
+// A(k) = (alpha omega(k) + gamma)^q, q = 2s, omega = sum_d 2(1 - cos(2 pi k_d / N_d)).
 __global__ void k_regulariser(float *A, int N1, int N2, int N3, int B1, int B2, int B3,
-                              double alpha, double gamma, int s) {
+                              double alpha, double gamma, int q) {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     long long nb = (long long)B1 * B2 * B3;
     if (idx >= nb) return;
@@ -52,7 +52,7 @@ __global__ void k_regulariser(float *A, int N1, int N2, int N3, int B1, int B2, 
                 2.0 * (1.0 - cospi(2.0 * (j2 - B2 / 2) / (double)N2)) +
                 2.0 * (1.0 - cospi(2.0 * (j3 - B3 / 2) / (double)N3));
     double base = alpha * om + gamma, a = 1.0;
-    for (int t = 0; t < 2 * s; ++t) a *= base;
+    for (int t = 0; t < q; ++t) a *= base;
     A[idx] = (float)a;
 }
 
@@ -358,7 +358,8 @@ int dft_init_tables(blr_plan *P, cudaStream_t s) {
     k_table_kx<<<(int)ceil_div_ll((long long)P->B3 * P->N3, T), T, 0, s>>>(P->T3c, P->T3s, P->N3, P->B3);
     BLR_CK_LAUNCH();
     k_regulariser<<<(int)ceil_div_ll(P->nb, T), T, 0, s>>>(
-        P->A, P->N1, P->N2, P->N3, P->B1, P->B2, P->B3, P->p.alpha, P->p.gamma, P->p.s);
+        P->A, P->N1, P->N2, P->N3, P->B1, P->B2, P->B3, P->p.alpha, P->p.gamma,
+        (int)(2.0 * P->p.s + 0.5));
     BLR_CK_LAUNCH();
     return BLR_OK;
 }

@@ -264,6 +264,38 @@ k_axpy(float *__restrict__ y, const float *__restrict__ a, const float *__restri
         y[i] = fmaf(alpha, x[i], a[i]);
 }
 
+// Leray projection of band coefficients (the incompressible form: Eq. 4 with
+// gamma = 1, imposed in the band): out(k) = P(k) in(k) with P(k) = I - kappa
+// kappa^T / |kappa|^2, kappa_d proportional to k_d / N_d (the common factor 2 pi
+// cancels), P(0) = I.  One thread per frequency, the three components' real and
+// imaginary parts projected alike (P is real).  out may alias in.
+__global__ void __launch_bounds__(RT)
+k_leray(float2 *out, const float2 *in, long long nb, int B1, int B2, int B3, int N1, int N2,
+        int N3) {
+    pdl_wait();
+    const float r1 = 1.0f / (float)N1, r2 = 1.0f / (float)N2, r3 = 1.0f / (float)N3;
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < nb; i += (long long)gridDim.x * RT) {
+        const int j3 = (int)(i % B3);
+        const int j2 = (int)((i / B3) % B2);
+        const int j1 = (int)(i / ((long long)B2 * B3));
+        const float k1 = (float)(j1 - B1 / 2) * r1, k2 = (float)(j2 - B2 / 2) * r2,
+                    k3 = (float)(j3 - B3 / 2) * r3;
+        const float kk = k1 * k1 + k2 * k2 + k3 * k3;
+        float2 a = in[i], b = in[nb + i], c = in[2 * nb + i];
+        if (kk > 0.0f) {
+            const float inv = 1.0f / kk;
+            const float wr = (k1 * a.x + k2 * b.x + k3 * c.x) * inv;
+            const float wi = (k1 * a.y + k2 * b.y + k3 * c.y) * inv;
+            a.x -= k1 * wr; a.y -= k1 * wi;
+            b.x -= k2 * wr; b.y -= k2 * wi;
+            c.x -= k3 * wr; c.y -= k3 * wi;
+        }
+        out[i] = a;
+        out[nb + i] = b;
+        out[2 * nb + i] = c;
+    }
+}
+
 int vec_blocks(const blr_plan *P) {
     long long b = ceil_div_ll(P->nfloat, RT);
     return (int)(b < RBLOCKS ? (b < 1 ? 1 : b) : RBLOCKS);
@@ -319,6 +351,16 @@ int pcg_direction(blr_plan *P, cudaStream_t s, const int *live) {
 
 int vec_axpy(blr_plan *P, float *y, const float *a, const float *x, double alpha, cudaStream_t s) {
     launch_pdl(k_axpy, dim3(vec_blocks(P)), dim3(RT), 0, s, y, a, x, (float)alpha, P->nfloat);
+    BLR_CK_LAUNCH();
+    return BLR_OK;
+}
+
+int vec_leray(blr_plan *P, float *out, const float *in, cudaStream_t s) {
+    long long b = ceil_div_ll(P->nb, RT);
+    const int blocks = (int)(b < RBLOCKS ? (b < 1 ? 1 : b) : RBLOCKS);
+    launch_pdl(k_leray, dim3(blocks), dim3(RT), 0, s, reinterpret_cast<float2 *>(out),
+               reinterpret_cast<const float2 *>(in), P->nb, P->B1, P->B2, P->B3, P->N1, P->N2,
+               P->N3);
     BLR_CK_LAUNCH();
     return BLR_OK;
 }

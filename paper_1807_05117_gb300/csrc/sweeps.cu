@@ -1068,6 +1068,8 @@ k_sweep_batch(const SweepPair *__restrict__ pairs, const long long *__restrict__
     }
 }
 
+// ==== host side: launch shapes, launchers, sweep orchestration, autotuner ====
+
 dim3 sweep_grid(const blr_plan *P) {
     return dim3((unsigned)ceil_div_ll(P->N3, MK), (unsigned)ceil_div_ll(P->N2, MJ),
                 (unsigned)ceil_div_ll(P->N1, P->chunk));

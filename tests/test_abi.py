@@ -48,6 +48,8 @@ def test_strerror_and_invalid_params(lib):
         dict(n=(16, 16, 16), band=(4, 4, 4), nt=0),   # no time step
         dict(n=(16, 16, 16), band=(4, 4, 4), sigma=0.0),
         dict(n=(0, 16, 16), band=(4, 4, 4)),
+        dict(n=(16, 16, 16), band=(4, 4, 4), s=0.3),  # 2s not an integer
+        dict(n=(16, 16, 16), band=(4, 4, 4), s=-0.5),
     ]
     for kw in bad:
         p = blr.make_params(**{"nt": 4, **kw})
@@ -58,9 +60,43 @@ def test_strerror_and_invalid_params(lib):
     p.ckpt_every = -1
     h = ctypes.c_void_p()
     assert lib.blr_plan_create(ctypes.byref(p), ctypes.byref(h)) == blr.BLR_EINVAL
+    p = blr.make_params((16, 16, 16), (4, 4, 4))
+    p.incompressible = 2
+    assert lib.blr_plan_create(ctypes.byref(p), ctypes.byref(h)) == blr.BLR_EINVAL
+    # batches take neither the incompressible form nor mixed precision
+    for kw in (dict(incompressible=True), dict(precision=blr.BLR_MIXED)):
+        arr = (blr.blr_params * 2)(blr.make_params((16, 16, 16), (4, 4, 4), nt=4),
+                                   blr.make_params((16, 16, 16), (4, 4, 4), nt=4, **kw))
+        assert lib.blr_batch_create(arr, 2, ctypes.byref(h)) == blr.BLR_EINVAL
+        assert not h.value
     # NULL plan handles are rejected, destroy(NULL) is a no-op
     assert lib.blr_plan_destroy(None) == blr.BLR_OK
     assert lib.blr_expand(None, None, None, None) == blr.BLR_EINVAL
     assert lib.blr_hessvec(None, None, None, None) == blr.BLR_EINVAL
     vals = (ctypes.c_int * 9)()
     assert lib.blr_plan_tuning(None, vals, 9) == blr.BLR_EINVAL
+
+
+def test_params_struct_layout_matches_header(tmp_path):
+    """The ctypes mirror of blr_params has the size and field offsets that a C
+    compiler gives the header's struct (a host C program prints them)."""
+    import shutil
+    import subprocess
+    from paper_1807_05117_gb300 import blr
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [f for f, _ in blr.blr_params._fields_]
+    prog = tmp_path / "layout.c"
+    prog.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "blr.h"\nint main(void) {\n'
+        '  printf("%zu\\n", sizeof(blr_params));\n'
+        + "".join(f'  printf("%zu\\n", offsetof(blr_params, {f}));\n' for f in fields)
+        + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)],
+                   check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    want = [ctypes.sizeof(blr.blr_params)] + [getattr(blr.blr_params, f).offset for f in fields]
+    assert got == want
