@@ -475,7 +475,10 @@ def main_ours(args):
                 measure_form(args.precision, dev, I0g, I1g, flush, stream, s=0.5,
                              incompressible=True),
                 regulariser="H1: A = alpha omega + gamma (s = 1/2)",
-                constraint="divergence-free band fields (Leray projector)")}
+                constraint="divergence-free band fields (Leray projector)"),
+            "full_newton": dict(
+                measure_form(args.precision, dev, I0g, I1g, flush, stream, hessian=1),
+                hessian="full: exact second derivative of the discrete energy, truncated PCG")}
 
     # end to end through the C-ABI with pinned host buffers
     if not args.no_e2e:
@@ -642,8 +645,9 @@ def main_batch(args):
     return 0
 
 
-def probe(precision="fp32"):
-    """A few launches of every hot-path kernel at the benchmark size, for ncu."""
+def probe(precision="fp32", hessian=0):
+    """A few launches of every hot-path kernel at the benchmark size, for ncu
+    (hessian=1: the full Newton Hessian's kernels as well)."""
     import numpy as np
     import torch
 
@@ -655,7 +659,7 @@ def probe(precision="fp32"):
     dvt = synth.random_direction(BAND, SEED + 2)
     (a, _), (b, _), (c, _), (d, _) = synth.as_device_inputs(I0, I1, vt, dvt)
     prec = blr.BLR_MIXED if precision == "mixed" else blr.BLR_FP32
-    with blr.Plan(N, BAND, NT, precision=prec) as plan:
+    with blr.Plan(N, BAND, NT, precision=prec, hessian=hessian) as plan:
         plan.set_images(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev))
         g = torch.empty((3,) + BAND, dtype=torch.complex64, device=dev)
         plan.gradient(torch.from_numpy(c).to(dev), g)
@@ -685,13 +689,15 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
-                    help="skip the incompressible-form measurement")
+                    help="skip the incompressible and full-Newton measurements")
     ap.add_argument("--adjoint-traffic", type=float, default=None,
                     help="dram bytes per adjoint-step launch from an ncu capture of this kernel")
     ap.add_argument("--workload", choices=["phantom128", "uneven64"], default="phantom128",
                     help="phantom128: the 128^3 registration (default); uneven64: the batching form")
     ap.add_argument("--probe", action="store_true",
                     help="short run for profilers: one gradient, 3 HVPs, 2 adjoint solves")
+    ap.add_argument("--probe-hessian", type=int, default=0, choices=[0, 1],
+                    help="with --probe: 1 probes a full-Newton plan")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--samples", type=int, default=1, help=argparse.SUPPRESS)
     args = ap.parse_args()
@@ -699,7 +705,7 @@ def main():
         oracle_sample(args.oracle_sample, args.samples)
         return 0
     if args.probe:
-        return probe(args.precision)
+        return probe(args.precision, args.probe_hessian)
     if args.impl == "reference":
         return main_reference(args)
     if args.workload == "uneven64":

@@ -5,7 +5,8 @@
  * Method: Hernandez, "Newton-Krylov optimization in PDE-constrained
  * diffeomorphic registration parameterized in the space of band-limited vector
  * fields" (arXiv 1807.05117), state-equation variant, stationary velocity,
- * Gauss-Newton Hessian; compressible or incompressible velocities.
+ * Gauss-Newton or full Newton Hessian; compressible or incompressible
+ * velocities.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -62,6 +63,11 @@ extern "C" {
 #define BLR_ECURV    (-7)  /* PCG met <p, Hp> <= 0                          */
 #define BLR_ETIMEOUT (-8)  /* a bounded device wait expired (tensor cores)  */
 
+/* Hessian used by blr_hessvec, blr_pcg and blr_newton. */
+#define BLR_GAUSS_NEWTON 0 /* Eq. 46 with the Gauss-Newton drops of Section 3.4 */
+#define BLR_NEWTON       1 /* the full Hessian of the discrete energy (Eqs. 44-46, */
+                           /* no drops); may be indefinite away from a minimum  */
+
 /* Precision of the truncated-DFT contractions (the transport is always FP32). */
 #define BLR_FP32   0       /* FP32 FMA contractions                         */
 #define BLR_MIXED  1       /* BF16 hi+lo split operands on tensor cores,     */
@@ -95,6 +101,9 @@ typedef struct blr_params {
                      /* gradient is then P grad E(P v~) and the Hessian      */
                      /* P H P.  blr_expand / blr_project / blr_adjoint stay  */
                      /* the plain operators.  Batches reject it.             */
+    int hessian;     /* BLR_GAUSS_NEWTON or BLR_NEWTON.  BLR_NEWTON keeps   */
+                     /* every adjoint and incremental state (2 nt V floats  */
+                     /* more), so it takes no checkpoints; batches reject it */
 } blr_params;
 
 /* Result of blr_newton (host struct filled by the library). */
@@ -152,6 +161,8 @@ int blr_state(blr_plan_t plan, const float *vt, float *m1, double *energy,
 /* Adjoint solve (Eq. 8 with lambda(1) = -(2/sigma^2)(m(1) - I1)) at the current
  * point, and the body force b = dt sum_n lambda^{n+1} grad m^n(x + d), the
  * discrete lambda grad m of Eq. 38.  Needs a prior blr_state (BLR_ESTATE).
+ * Repeatable: the plan keeps lambda^nt of the current point apart from the
+ * buffers that blr_hessvec uses.
  * b      : device, 3*V floats, written.
  * lambda0: device, V floats, receives lambda^0; may be NULL. */
 int blr_adjoint(blr_plan_t plan, float *b, float *lambda0, blr_stream_t stream);
@@ -170,12 +181,20 @@ int blr_gradient(blr_plan_t plan, const float *vt, float *g, double *energy,
  * g: device, 2*3*B1*B2*B3 floats (written).  Needs a prior blr_state (BLR_ESTATE). */
 int blr_gradient_at_state(blr_plan_t plan, float *g, blr_stream_t stream);
 
-/* Gauss-Newton Hessian-vector product at the current point (Section 3.2,
- * Eqs. 44-46 with the Gauss-Newton drops of Section 3.4):
+/* Hessian-vector product at the current point (Section 3.2, Eqs. 44-46).
+ * BLR_GAUSS_NEWTON (the drops of Section 3.4):
  *   H~ dv~ = A dv~ + pi(db), incremental state dm^0 = 0,
  *   dm^{n+1} = S dm^n - dt grad m^n(x+d) . iota(dv~), dlambda^nt =
  *   -(2/sigma^2) dm^nt, dlambda^n = S^T dlambda^{n+1},
  *   db = dt sum_n dlambda^{n+1} grad m^n(x + d).
+ * BLR_NEWTON (the exact Hessian of the discrete energy), with dd = -dt iota(dv~)
+ * and lambda^n the gradient's adjoint states at the current point:
+ *   dlambda^n = S^T dlambda^{n+1} + sum_a D_a^T (dd_a lambda^{n+1}),
+ *   db = dt sum_n [dlambda^{n+1} grad m^n(x+d)
+ *                  + lambda^{n+1} (grad dm^n(x+d) + Hess m^n(x+d) dd)],
+ *   D_a and Hess the first and second derivatives of the trilinear cell
+ *   polynomial at the departure point (the adjoint states are computed on the
+ *   first call after a forward solve when blr_gradient has not done so).
  * dvt: device input, hdv: device output, 2*3*B1*B2*B3 floats each.
  * Needs a prior blr_state / blr_gradient (BLR_ESTATE). */
 int blr_hessvec(blr_plan_t plan, const float *dvt, float *hdv,
@@ -187,7 +206,8 @@ int blr_hessvec(blr_plan_t plan, const float *dvt, float *hdv,
  * maxit iterations.  Synchronises the stream once per iteration.
  * rhs, x: device, 2*3*B1*B2*B3 floats (x written).
  * iters, relres: host, may be NULL (iterations run, final ||r||/||r_0||).
- * Returns BLR_ECURV if <p, Hp> <= 0. */
+ * Returns BLR_ECURV if <p, Hp> <= 0 (x then holds the iterate before that
+ * direction). */
 int blr_pcg(blr_plan_t plan, const float *rhs, float *x, int maxit, double eta,
             int *iters, double *relres, blr_stream_t stream);
 
@@ -198,6 +218,9 @@ int blr_pcg(blr_plan_t plan, const float *rhs, float *x, int maxit, double eta,
  * rejected).  The paper's "v - eps dv" is read as this descent step.
  * PCG tolerance: eta = forcing if forcing >= 0, else
  * min(0.5, sqrt(||g|| / ||g_0||)).  Stops when ||g||_inf / ||g_0||_inf < gtol.
+ * With BLR_NEWTON the solve is truncated at non-positive curvature: p is the
+ * PCG iterate before that direction, or K~(-g) when it is the first (truncated
+ * Newton-CG; both are descent directions).
  * vt : host or device, 2*3*B1*B2*B3 floats, in: initial velocity, out: result.
  * rep: host, may be NULL.  Synchronous. */
 int blr_newton(blr_plan_t plan, float *vt, int max_newton, int max_pcg,

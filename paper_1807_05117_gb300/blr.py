@@ -30,13 +30,16 @@ BLR_ETIMEOUT = -8
 
 BLR_FP32 = 0
 BLR_MIXED = 1
+BLR_GAUSS_NEWTON = 0
+BLR_NEWTON = 1
 
 
 class blr_params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("band", ctypes.c_int * 3), ("nt", ctypes.c_int),
                 ("alpha", ctypes.c_double), ("gamma", ctypes.c_double), ("s", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("precision", ctypes.c_int),
-                ("ckpt_every", ctypes.c_int), ("incompressible", ctypes.c_int)]
+                ("ckpt_every", ctypes.c_int), ("incompressible", ctypes.c_int),
+                ("hessian", ctypes.c_int)]
 
 
 class blr_report(ctypes.Structure):
@@ -144,7 +147,7 @@ def _ptr(t, *, device_only=True, dtype=None, numel=None, optional=False, name="t
 
 
 def make_params(n, band, nt=10, alpha=3.0, gamma=1.0, s=2, sigma=1.0, precision=BLR_FP32,
-                ckpt_every=0, incompressible=False):
+                ckpt_every=0, incompressible=False, hessian=BLR_GAUSS_NEWTON):
     p = blr_params()
     p.n[:] = [int(v) for v in n]
     p.band[:] = [int(v) for v in band]
@@ -153,6 +156,7 @@ def make_params(n, band, nt=10, alpha=3.0, gamma=1.0, s=2, sigma=1.0, precision=
     p.precision = int(precision)
     p.ckpt_every = int(ckpt_every)
     p.incompressible = 1 if incompressible else 0
+    p.hessian = int(hessian)
     return p
 
 
@@ -279,9 +283,10 @@ class Plan:
     """Owning handle: ``with Plan(n, band, nt) as P: P.gradient(vt, g)``."""
 
     def __init__(self, n, band, nt=10, alpha=3.0, gamma=1.0, s=2, sigma=1.0,
-                 precision=BLR_FP32, ckpt_every=0, incompressible=False):
+                 precision=BLR_FP32, ckpt_every=0, incompressible=False,
+                 hessian=BLR_GAUSS_NEWTON):
         self.params = make_params(n, band, nt, alpha, gamma, s, sigma, precision, ckpt_every,
-                                  incompressible)
+                                  incompressible, hessian)
         self.n = tuple(int(v) for v in n)
         self.band = tuple(int(v) for v in band)
         self.nt = int(nt)

@@ -25,6 +25,9 @@ int validate(const blr_params *p) {
     if (p->nt < 1 || !(p->sigma > 0) || !(p->gamma > 0) || !(p->alpha >= 0)) return BLR_EINVAL;
     if (!(p->s >= 0 && p->s <= 32) || 2.0 * p->s != floor(2.0 * p->s)) return BLR_EINVAL;
     if (p->incompressible != 0 && p->incompressible != 1) return BLR_EINVAL;
+    if (p->hessian != BLR_GAUSS_NEWTON && p->hessian != BLR_NEWTON) return BLR_EINVAL;
+    // the full Hessian keeps every adjoint and incremental state: no checkpoints
+    if (p->hessian == BLR_NEWTON && p->ckpt_every > 0 && p->ckpt_every < p->nt) return BLR_EINVAL;
     if (p->precision != BLR_FP32 && p->precision != BLR_MIXED) return BLR_EINVAL;
     if (p->ckpt_every < 0) return BLR_EINVAL;
     long long V = (long long)p->n[0] * p->n[1] * p->n[2];
@@ -56,6 +59,18 @@ size_t layout(blr_plan *P, char *base) {
     P->d4 = P->sweep_wide ? a.take<float4>(V) : nullptr;
     P->lam[0] = a.take<float>(V);
     P->lam[1] = a.take<float>(V);
+    if (P->p.hessian == BLR_NEWTON) {
+        const int nt = P->p.nt;
+        P->lam_all = a.take<float>((size_t)nt * V);
+        P->lam_nt = P->lam_all + (size_t)(nt - 1) * V;
+        P->dm_all = nt > 1 ? a.take<float>((size_t)(nt - 1) * V) : nullptr;
+        P->nt_kap = a.take<float>((size_t)8 * V);
+        P->nt_lob = a.take<uint8_t>(V);
+    } else {
+        P->lam_all = P->dm_all = P->nt_kap = nullptr;
+        P->nt_lob = nullptr;
+        P->lam_nt = a.take<float>(V);
+    }
     P->Gm = P->use_gm ? a.take<float>((size_t)3 * P->p.nt * V) : nullptr;
     P->b = a.take<float>(3 * V);
     P->dv = a.take<float>(3 * V);
@@ -125,6 +140,7 @@ int state_at(blr_plan *P, const float *vt, double *energy_out, cudaStream_t s) {
     } else if (vt != P->vt) {
         BLR_CK(cudaMemcpyAsync(P->vt, vt, P->nfloat * sizeof(float), cudaMemcpyDefault, s));
     }
+    P->have_lams = false;
     rc = dft_expand(P, P->vt, P->d, 1, s);
     if (rc) return rc;
     if ((rc = sweep_state(P, s))) return rc;
@@ -135,22 +151,28 @@ int state_at(blr_plan *P, const float *vt, double *energy_out, cudaStream_t s) {
 
 // g = A v~ + pi(b) at the current point (incompressible: P applied to it).
 int gradient_here(blr_plan *P, float *g, cudaStream_t s) {
-    int rc = sweep_adjoint(P, P->b, nullptr, s);
+    int rc = sweep_adjoint(P, P->b, nullptr, P->lam_nt, s);
     if (rc) return rc;
     if ((rc = dft_project(P, P->b, g, P->vt, s))) return rc;
     return P->p.incompressible ? vec_leray(P, g, g, s) : BLR_OK;
 }
 
-// H dv~ = A dv~ + pi(db) (incompressible: P H P dv~).
+// H dv~ = A dv~ + pi(db) (incompressible: P H P dv~).  Gauss-Newton, or the full
+// Hessian, which needs the gradient's adjoint states (computed here when the
+// current point has none yet).
 int hessvec_here(blr_plan *P, const float *dvt, float *hdv, cudaStream_t s) {
     int rc;
+    const bool full = P->p.hessian == BLR_NEWTON;
+    if (full && !P->have_lams && (rc = sweep_adjoint(P, P->b, nullptr, P->lam_nt, s))) return rc;
     if (P->p.incompressible) {
         if ((rc = vec_leray(P, P->vproj, dvt, s))) return rc;
         dvt = P->vproj;
     }
     if ((rc = dft_expand(P, dvt, P->dv, 0, s))) return rc;
     if ((rc = sweep_incremental(P, s))) return rc;
-    if ((rc = sweep_adjoint(P, P->b, nullptr, s))) return rc;
+    if (full && (rc = newton_prep(P, s))) return rc;
+    rc = full ? sweep_adjoint_newton(P, P->b, s) : sweep_adjoint(P, P->b, nullptr, P->lam[0], s);
+    if (rc) return rc;
     if ((rc = dft_project(P, P->b, hdv, dvt, s))) return rc;
     return P->p.incompressible ? vec_leray(P, hdv, hdv, s) : BLR_OK;
 }
@@ -162,8 +184,12 @@ int hessvec_here(blr_plan *P, const float *dvt, float *hdv, cudaStream_t s) {
 // but a Hessian-vector product into scratch (its update and direction see the
 // flag).  Kernels, order and stopping rule are those of the loop written with a
 // host test after every update, so the iterates are identical.
+// truncate: non-positive curvature ends the solve with the iterate so far (or the
+// first direction K~ rhs when no update was made) instead of BLR_ECURV: the
+// truncated Newton-CG rule for the full Hessian, which can be indefinite away
+// from a minimum (Section 3.4).
 int pcg_run(blr_plan *P, const float *rhs, float *x, int maxit, double eta, int *iters,
-            double *relres, int *n_hv, cudaStream_t s) {
+            double *relres, int *n_hv, cudaStream_t s, bool truncate = false) {
     int rc = pcg_init(P, rhs, x, s);
     if (rc) return rc;
     if ((rc = fetch_scalars(P, s, nullptr))) return rc;
@@ -213,6 +239,11 @@ int pcg_run(blr_plan *P, const float *rhs, float *x, int maxit, double eta, int 
     if (n_hv) *n_hv += it + ((code == PCG_CURV || code == PCG_NAN_PQ) ? 1 : 0);
     if (iters) *iters = it;
     if (relres) *relres = it > 0 ? P->hsc[SC_REL] : 1.0;
+    if (code == PCG_CURV && truncate) {
+        if (it == 0)   // p_0 = K~ rhs, untouched since the stop
+            BLR_CK(cudaMemcpyAsync(x, P->pv, P->nfloat * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        return BLR_OK;
+    }
     if (code == PCG_CURV) return BLR_ECURV;
     if (code != PCG_RUN) return BLR_ENAN;
     return BLR_OK;
@@ -353,7 +384,7 @@ int blr_state(blr_plan_t P, const float *vt, float *m1, double *energy, blr_stre
 int blr_adjoint(blr_plan_t P, float *b, float *lambda0, blr_stream_t stream) {
     if (check_plan(P) || !b) return BLR_EINVAL;
     if (!P->have_state) return BLR_ESTATE;
-    return sweep_adjoint(P, b, lambda0, (cudaStream_t)stream);
+    return sweep_adjoint(P, b, lambda0, P->lam_nt, (cudaStream_t)stream);
 }
 
 int blr_gradient(blr_plan_t P, const float *vt, float *g, double *energy, blr_stream_t stream) {
@@ -413,7 +444,8 @@ int blr_newton(blr_plan_t P, float *vt, int max_newton, int max_pcg, double gtol
         if ((rc = vec_axpy(P, P->trial, P->g, P->g, -2.0, s))) break;
         int its = 0;
         double relres = 0;
-        rc = pcg_run(P, P->trial, P->step, max_pcg, eta, &its, &relres, &R.n_hessvec, s);
+        rc = pcg_run(P, P->trial, P->step, max_pcg, eta, &its, &relres, &R.n_hessvec, s,
+                     P->p.hessian == BLR_NEWTON);
         R.pcg_iters += its;
         if (rc) break;
         if ((rc = vec_dot(P, P->g, P->step, nullptr, P->dsc + SC_DOT, s))) break;

@@ -113,7 +113,16 @@ struct blr_plan {
     int nseg;           // segments ceil(nt / k)
     int seg_valid;      // segment whose interior states the segment buffer holds
     bool have_state;
+    bool have_lams;     // lam_all holds the adjoint states of the current point
     float *lam[2];      // V each (adjoint / incremental adjoint ping-pong)
+    float *lam_nt;      // V: lambda^nt of the current point (written by the state sweep)
+    float *lam_all;     // full Newton Hessian: [nt][V], slot k-1 = lambda^k (k = 1..nt; the
+                        // last slot is lam_nt), else nullptr
+    float *dm_all;      // full Newton Hessian: [nt-1][V], slot k-1 = dm^k of the last
+                        // incremental state (k = 1..nt-1), else nullptr
+    float *nt_kap;      // full Newton Hessian: [8][V] corner weights of the variation of
+                        // S^T for the current direction (newton.cu), else nullptr
+    uint8_t *nt_lob;    // full Newton Hessian: [V] cell-start bits, else nullptr
     float *Gm;          // [nt][3][V] grad of the trilinear cell of m^n at x + d(x) (written by
                         // the state sweep, read by the adjoint and incremental sweeps), or
                         // nullptr (checkpointed plans and batch members compute it on the fly)
@@ -189,7 +198,13 @@ int tc_axis2(blr_plan *P, int project, const float *X, float *D, cudaStream_t s)
 int sweep_setup(blr_plan *P);
 long long sweep_blocks(const blr_plan *P);
 int sweep_state(blr_plan *P, cudaStream_t s);                  // m^1..m^nt, lambda^nt, partials
-int sweep_adjoint(blr_plan *P, float *b, float *lambda0, cudaStream_t s);
+// Adjoint sweep from lambda^nt = lam_final: b = dt sum_n lambda^{n+1} grad m^n,
+// lambda^0 into lambda0 (nullable).  The gradient's solve (lam_final == P->lam_nt)
+// also keeps every lambda^n in lam_all when the plan has it.
+int sweep_adjoint(blr_plan *P, float *b, float *lambda0, const float *lam_final, cudaStream_t s);
+// The full Newton incremental adjoint: as sweep_adjoint from dlambda^nt in lam[0], with
+// the second-order terms of newton.cu after every step (needs lam_all and dm_all).
+int sweep_adjoint_newton(blr_plan *P, float *b, cudaStream_t s);
 int sweep_incremental(blr_plan *P, cudaStream_t s);            // dm -> dlambda^nt in lam[0]
 // wide: the adjoint and incremental-state items use the wide-copy tiles (every
 // pair has N3 % 4 == 0); the incremental-state tiles are then AJ rows high.
@@ -203,6 +218,13 @@ int sweep_blocks_per_sm(int kind, bool wide = false);
 void sweep_set_chunk(blr_plan *P, int kind, int chunk);
 int sweep_autotune(blr_plan *P, cudaStream_t s);
 int sweep_pack_d4(blr_plan *P, cudaStream_t s);               // d4 from d (when P->d4)
+
+// newton.cu: step n's second-order terms of the full Newton Hessian (b += ..., and
+// dlam += the variation of S^T when transpose_term); dmn = dm^n or nullptr (n = 0).
+int newton_terms(blr_plan *P, bool transpose_term, const float *lam1, const float *mn,
+                 const float *dmn, float *dlam, float *b, cudaStream_t s);
+// newton.cu: the step-invariant weights of those terms for the direction in P->dv.
+int newton_prep(blr_plan *P, cudaStream_t s);
 
 // reduce.cu
 int energy_finalize(blr_plan *P, const float *vt, double *energy_out, int nblocks, cudaStream_t s);

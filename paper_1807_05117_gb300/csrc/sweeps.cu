@@ -1298,32 +1298,64 @@ int sweep_state(blr_plan *P, cudaStream_t s) {
         int rc = state_step(P, n, grad_slot(P, n), s);
         if (rc) return rc;
     }
-    launch_state<true>(P, state_slot(P, nt - 1), state_slot(P, nt), P->I1, P->lam[0], lam_scale,
+    launch_state<true>(P, state_slot(P, nt - 1), state_slot(P, nt), P->I1, P->lam_nt, lam_scale,
                        P->partials, grad_slot(P, nt - 1), s);
     BLR_CK_LAUNCH();
     P->seg_valid = P->nseg - 1;   // the forward sweep leaves the last segment's states
     return BLR_OK;
 }
 
-// lambda^nt must be in lam[0].  Writes the body force into b (3V) and, when
-// lambda0 != nullptr, lambda^0 into lambda0.  Segments are visited backwards,
-// each recomputed from its checkpoint when needed.
-int sweep_adjoint(blr_plan *P, float *b, float *lambda0, cudaStream_t s) {
+// Writes the body force into b (3V) and, when lambda0 != nullptr, lambda^0 into
+// lambda0, starting from lambda^nt in lam_final (which is never written).
+// Segments are visited backwards, each recomputed from its checkpoint when
+// needed.  The gradient's solve of a full-Newton plan writes every lambda^n into
+// lam_all instead of the ping-pong pair.
+int sweep_adjoint(blr_plan *P, float *b, float *lambda0, const float *lam_final, cudaStream_t s) {
     const int nt = P->p.nt;
+    const bool keep = P->lam_all && lam_final == P->lam_nt;
     int cur = 0;
     for (int j = P->nseg - 1; j >= 0; --j) {
         int rc = ensure_segment(P, j, s);
         if (rc) return rc;
         const int n0 = j * P->ck, n1 = n0 + P->ck < nt ? n0 + P->ck : nt;
         for (int n = n1 - 1; n >= n0; --n) {
-            const float *lin = P->lam[cur];
-            float *lout = (n == 0 && lambda0) ? lambda0 : P->lam[1 - cur];
+            const float *lin;
+            float *lout;
+            if (keep) {
+                lin = P->lam_all + (size_t)n * P->V;   // lambda^{n+1}
+                lout = n == 0 ? lambda0 : P->lam_all + (size_t)(n - 1) * P->V;
+            } else {
+                lin = (n == nt - 1) ? lam_final : P->lam[cur];
+                lout = (n == 0 && lambda0) ? lambda0 : P->lam[1 - cur];
+            }
             const bool first = (n == nt - 1);
             const bool wlam = (n > 0) || (lambda0 != nullptr);
             launch_adjoint(P, first, wlam, lin, state_slot(P, n), lout, b, grad_slot(P, n), s);
             BLR_CK_LAUNCH();
             cur = 1 - cur;
         }
+    }
+    if (keep) P->have_lams = true;
+    return BLR_OK;
+}
+
+// Full Newton incremental adjoint: dlambda^n = S^T dlambda^{n+1} + the variation of
+// S^T applied to lambda^{n+1}; db = dt sum_n [dlambda^{n+1} grad m^n + lambda^{n+1}
+// (D dm^n + Hess T[m^n] dd)].  dlambda^nt in lam[0], lambda^k in lam_all, dm^k in
+// dm_all (every state kept: full-Newton plans do not checkpoint).
+int sweep_adjoint_newton(blr_plan *P, float *b, cudaStream_t s) {
+    const int nt = P->p.nt;
+    int cur = 0;
+    for (int n = nt - 1; n >= 0; --n) {
+        const float *lin = P->lam[cur];
+        float *lout = n > 0 ? P->lam[1 - cur] : nullptr;
+        const float *mn = state_slot(P, n);
+        launch_adjoint(P, n == nt - 1, n > 0, lin, mn, lout, b, grad_slot(P, n), s);
+        BLR_CK_LAUNCH();
+        const float *dmn = n > 0 ? P->dm_all + (size_t)(n - 1) * P->V : nullptr;
+        int rc = newton_terms(P, n > 0, P->lam_all + (size_t)n * P->V, mn, dmn, lout, b, s);
+        if (rc) return rc;
+        cur = 1 - cur;
     }
     return BLR_OK;
 }
@@ -1340,6 +1372,10 @@ int sweep_incremental(blr_plan *P, cudaStream_t s) {
         for (int n = n0; n < n1; ++n) {
             const float *din = P->dm[cur];
             float *dout = (n == nt - 1) ? P->lam[0] : P->dm[1 - cur];
+            if (P->dm_all) {   // full Newton: keep dm^{n+1} for the adjoint's terms
+                din = n > 0 ? P->dm_all + (size_t)(n - 1) * P->V : P->dm[0];
+                if (n < nt - 1) dout = P->dm_all + (size_t)n * P->V;
+            }
             launch_incstate(P, n == 0, n == nt - 1, din, state_slot(P, n), dout, lam_scale,
                             grad_slot(P, n), s);
             BLR_CK_LAUNCH();
