@@ -26,6 +26,10 @@ fields", arXiv 1807.05117):
   the exact second derivative of the discrete energy;
 * PCG with preconditioner K~ and the reduced-space Newton update with a step
   length (Section 3.4, Eqs. 54-55; Section 2.4, Eqs. 31-32);
+* the non-stationary parameterisation (one band-limited velocity v~^n per time
+  step, the time-varying v~_t of Section 3.2 and of the NSt. experiments): the
+  regulariser is the time integral 1/2 dt sum_n <L~ v~^n, v~^n>, and the
+  gradient and Hessian are taken per step;
 * the incompressible form (Eq. 4 with gamma = 1, imposed in the band as in
   Section 3.2): the velocity is restricted to divergence-free band fields by the
   Fourier-diagonal Leray projector P(k) = I - kappa kappa^T / |kappa|^2,
@@ -82,6 +86,8 @@ class Params:
               regulariser alpha*omega + gamma of the incompressible experiments
     sigma  -- weight of the image term sigma^-2 ||m(1) - I1||^2 (Eq. 35)
     incompressible -- restrict v~ to divergence-free band fields (Eq. 4, gamma = 1)
+    stationary -- one velocity for all steps, coefficients (3, B1, B2, B3); else one
+              per step, (nt, 3, B1, B2, B3), step n transported by v~^n
     """
 
     n: tuple
@@ -92,6 +98,7 @@ class Params:
     s: float = 2
     sigma: float = 1.0
     incompressible: bool = False
+    stationary: bool = True
 
     @property
     def dt(self) -> float:
@@ -281,10 +288,20 @@ class Stencil:
 
 def state(I0: np.ndarray, st: Stencil, nt: int) -> list:
     """m^0 = I0, m^{n+1} = S m^n, n = 0 .. nt-1.  Returns [m^0, ..., m^nt]."""
+    return state_steps(I0, [st] * nt)
+
+
+def state_steps(I0: np.ndarray, stencils: list) -> list:
+    """m^0 = I0, m^{n+1} = S^n m^n with the step's own stencil.  Returns [m^0, ..., m^nt]."""
     m = [np.asarray(I0, dtype=np.float64)]
-    for _ in range(nt):
+    for st in stencils:
         m.append(st.apply(m[-1]))
     return m
+
+
+def per_step(f, x: np.ndarray, p: Params) -> np.ndarray:
+    """f applied to the coefficients of each step (the whole array when stationary)."""
+    return f(x) if p.stationary else np.stack([f(x[n]) for n in range(p.nt)])
 
 
 def data_energy(m1: np.ndarray, I1: np.ndarray, p: Params) -> float:
@@ -304,68 +321,91 @@ class Point:
     def __init__(self, vt: np.ndarray, I0: np.ndarray, I1: np.ndarray, p: Params):
         self.p = p
         self.vt = np.asarray(vt, dtype=np.complex128)
-        if p.incompressible:
-            self.vt = leray(self.vt, p.n)       # the energy is evaluated at P v~
+        want = (3,) + tuple(p.band) if p.stationary else (p.nt, 3) + tuple(p.band)
+        if self.vt.shape != want:
+            raise ValueError(f"coefficients of shape {self.vt.shape}, expected {want}")
+        if p.incompressible:      # the energy is evaluated at P v~
+            self.vt = per_step(lambda v: leray(v, p.n), self.vt, p)
         self.I1 = np.asarray(I1, dtype=np.float64)
         self.A = regulariser_weights(p)
-        self.d = displacement(self.vt, p)
+        self.d = per_step(lambda v: displacement(v, p), self.vt, p)
         self.cfl = cfl_number(self.d)
-        self.stencil = Stencil(self.d)
-        self.m = state(I0, self.stencil, p.nt)
-        self.energy_reg = regulariser_energy(self.vt, self.A)
+        if p.stationary:
+            self.stencils = [Stencil(self.d)] * p.nt
+        else:
+            self.stencils = [Stencil(self.d[n]) for n in range(p.nt)]
+        self.stencil = self.stencils[0]
+        self.m = state_steps(I0, self.stencils)
+        # 1/2 int_0^1 <L~ v~_t, v~_t> dt: dt sum over the steps when v~ varies
+        self.energy_reg = regulariser_energy(self.vt, self.A) * (1.0 if p.stationary else p.dt)
         self.energy_data = data_energy(self.m[-1], self.I1, p)
         self.energy = self.energy_reg + self.energy_data
         self._G = None
 
     def grad_m(self, n: int) -> np.ndarray:
-        """G^n = gradient of the interpolant of m^n at the departure points."""
+        """G^n = gradient of the interpolant of m^n at the departure points of step n."""
         if self._G is None:
             self._G = [None] * self.p.nt
         if self._G[n] is None:
-            self._G[n] = self.stencil.gradient(self.m[n])
+            self._G[n] = self.stencils[n].gradient(self.m[n])
         return self._G[n]
+
+    def _assemble(self, v: np.ndarray, b: np.ndarray) -> np.ndarray:
+        """A v~ + pi(b) (stationary), or dt A v~^n + pi(b^n) per step; then P."""
+        p = self.p
+        if p.stationary:
+            out = self.A[None] * v + project(b, p.band)
+        else:
+            out = np.stack([p.dt * self.A[None] * v[n] + project(b[n], p.band)
+                            for n in range(p.nt)])
+        if p.incompressible:
+            out = per_step(lambda x: leray(x, p.n), out, p)
+        return out
 
     def adjoint_states(self) -> list:
         """[lambda^0, ..., lambda^nt] of the gradient's adjoint solve at this point."""
         if getattr(self, "_lams", None) is None:
             lam = -(2.0 / self.p.sigma**2) * (self.m[-1] - self.I1)
             lams = [lam]
-            for _ in range(self.p.nt):
-                lam = self.stencil.apply_transpose(lam)
+            for n in range(self.p.nt - 1, -1, -1):
+                lam = self.stencils[n].apply_transpose(lam)
                 lams.append(lam)
             self._lams = lams[::-1]
         return self._lams
 
     def adjoint_chain(self, lam_final: np.ndarray):
         """lambda^n = S^T lambda^{n+1} (discrete adjoint equation, Eq. 8) and the
-        body force b = dt sum_{n<nt} lambda^{n+1} G^n (the lambda grad m of Eq. 38).
+        body force b = dt sum_{n<nt} lambda^{n+1} G^n (the lambda grad m of Eq. 38);
+        non-stationary: one body force per step, b^n = dt lambda^{n+1} G^n.
         Returns (b, lambda^0)."""
         p = self.p
         lam = lam_final
-        b = np.zeros((3,) + tuple(p.n))
+        b = np.zeros((3,) + tuple(p.n)) if p.stationary else np.zeros((p.nt, 3) + tuple(p.n))
         for n in range(p.nt - 1, -1, -1):
-            b += p.dt * lam[None] * self.grad_m(n)
-            lam = self.stencil.apply_transpose(lam)
+            if p.stationary:
+                b += p.dt * lam[None] * self.grad_m(n)
+            else:
+                b[n] = p.dt * lam[None] * self.grad_m(n)
+            lam = self.stencils[n].apply_transpose(lam)
         return b, lam
 
     def gradient(self):
         """g~ = A v~ + pi(b), final condition lambda^nt = -(2/sigma^2)(m^nt - I1);
-        incompressible: P applied to that.  Returns (g~, b, lambda^0)."""
+        non-stationary: g~^n = dt A v~^n + pi(b^n), the derivative in each step's
+        coefficients; incompressible: P applied to that.  Returns (g~, b, lambda^0)."""
         lam_final = -(2.0 / self.p.sigma**2) * (self.m[-1] - self.I1)
         b, lam0 = self.adjoint_chain(lam_final)
-        g = self.A[None] * self.vt + project(b, self.p.band)
-        if self.p.incompressible:
-            g = leray(g, self.p.n)
-        return g, b, lam0
+        return self._assemble(self.vt, b), b, lam0
 
     def incremental_state(self, dvt: np.ndarray) -> np.ndarray:
-        """dm^0 = 0, dm^{n+1} = S dm^n - dt G^n . iota(dv~)  (linearised Eq. 36).
+        """dm^0 = 0, dm^{n+1} = S dm^n - dt G^n . iota(dv~^n)  (linearised Eq. 36).
         Returns dm^nt."""
         p = self.p
-        dv = expand(dvt, p.n)
+        dv = per_step(lambda v: expand(v, p.n), dvt, p)
         dm = np.zeros(tuple(p.n))
         for n in range(p.nt):
-            dm = self.stencil.apply(dm) - p.dt * np.sum(self.grad_m(n) * dv, axis=0)
+            dvn = dv if p.stationary else dv[n]
+            dm = self.stencils[n].apply(dm) - p.dt * np.sum(self.grad_m(n) * dvn, axis=0)
         return dm
 
     def gn_hessvec(self, dvt: np.ndarray):
@@ -374,16 +414,14 @@ class Point:
         db = dt sum dlambda^{n+1} G^n.  The Gauss-Newton drops of Section 3.4 remove
         the pi(lambda grad dm) term and the dJ term (all second derivatives of
         the transport).  Incompressible: P H P.  Returns (H dv~, dm^nt, db)."""
+        p = self.p
         dvt = np.asarray(dvt, dtype=np.complex128)
-        if self.p.incompressible:
-            dvt = leray(dvt, self.p.n)
+        if p.incompressible:
+            dvt = per_step(lambda v: leray(v, p.n), dvt, p)
         dm1 = self.incremental_state(dvt)
-        dlam_final = -(2.0 / self.p.sigma**2) * dm1
+        dlam_final = -(2.0 / p.sigma**2) * dm1
         db, _ = self.adjoint_chain(dlam_final)
-        h = self.A[None] * dvt + project(db, self.p.band)
-        if self.p.incompressible:
-            h = leray(h, self.p.n)
-        return h, dm1, db
+        return self._assemble(dvt, db), dm1, db
 
 
     def full_hessvec(self, dvt: np.ndarray):
@@ -398,8 +436,10 @@ class Point:
                       (pi(lambda grad dm), and the move of the departure point
                        inside its cell)
           H dv~ = A dv~ + pi(db);  incompressible: P H P.
-        Returns (H dv~, dm^nt, db)."""
+        Stationary velocities only.  Returns (H dv~, dm^nt, db)."""
         p, st = self.p, self.stencil
+        if not p.stationary:
+            raise NotImplementedError("the full Hessian is built for stationary velocities")
         dvt = np.asarray(dvt, dtype=np.complex128)
         if p.incompressible:
             dvt = leray(dvt, p.n)

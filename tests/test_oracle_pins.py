@@ -707,3 +707,107 @@ def test_full_newton_decreases_energy():
     assert rep.iterations >= 3
     assert all(b < a for a, b in zip(rep.energies, rep.energies[1:]))
     assert rep.grad_inf_rel < 0.5
+
+
+# ----------------------------------------------------------------------------
+# Non-stationary velocity (one band-limited velocity per time step)
+# ----------------------------------------------------------------------------
+
+
+def test_nonstationary_constant_in_time_reduces_to_stationary():
+    """With v~^n = v~ for every step the energy is the stationary one, and the
+    per-step gradients and HVPs (constant direction) sum to the stationary
+    gradient and HVP (catches a missing dt in the regulariser, a step index off
+    by one in the body force or the incremental state)."""
+    ps = O.Params(n=(12, 10, 14), band=(4, 4, 6), nt=5, sigma=0.7)
+    pn = O.Params(n=ps.n, band=ps.band, nt=ps.nt, sigma=ps.sigma, stationary=False)
+    I0, I1, _ = synth.blob_pair(ps.n, 1701, max_disp=2.0)
+    vt = synth.random_coefficients(ps.band, 1702, bound=2.5)
+    dvt = synth.random_direction(ps.band, 1703)
+    a = O.Point(vt, I0, I1, ps)
+    b = O.Point(np.stack([vt] * ps.nt), I0, I1, pn)
+    assert abs(a.energy - b.energy) < 1e-12 * a.energy
+    assert rel(b.gradient()[0].sum(axis=0), a.gradient()[0]) < 1e-12
+    assert rel(b.gn_hessvec(np.stack([dvt] * ps.nt))[0].sum(axis=0), a.gn_hessvec(dvt)[0]) < 1e-12
+
+
+def test_nonstationary_single_step_velocity_is_exact_shift():
+    """Only step 1 moves, by a constant displacement of (1, -1, 0) voxels (a hair
+    inside the cell): m^1 = I0, and m^2 = m^nt is I0 shifted by exactly that
+    vector (catches steps taken in the wrong order or with another step's
+    velocity)."""
+    n, band, nt = (8, 6, 10), (4, 4, 4), 4
+    p = O.Params(n=n, band=band, nt=nt, stationary=False)
+    I0 = np.random.default_rng(1704).normal(size=n)
+    vt = np.zeros((nt, 3) + band, complex)
+    centre = tuple(b // 2 for b in band)
+    shift = (1, -1, 0)
+    for c in range(3):
+        vt[(1, c) + centre] = -shift[c] / p.dt * 0.999999999999   # d = shift (just inside the cell)
+    pt = O.Point(vt, I0, I0, p)
+    want = np.roll(I0, shift=[-s for s in shift], axis=(0, 1, 2))
+    assert np.max(np.abs(pt.m[1] - I0)) == 0.0
+    assert np.max(np.abs(pt.m[2] - want)) < 1e-9
+    assert np.max(np.abs(pt.m[-1] - want)) < 1e-9
+
+
+def _kink_free_nst(vt, dvt, eps, p):
+    lo = np.floor(O.per_step(lambda v: O.displacement(v, p), vt - eps * dvt, p))
+    hi = np.floor(O.per_step(lambda v: O.displacement(v, p), vt + eps * dvt, p))
+    return np.array_equal(lo, hi)
+
+
+def test_nonstationary_gradient_matches_finite_differences():
+    p = O.Params(n=(12, 12, 12), band=(4, 6, 4), nt=4, stationary=False)
+    I0, I1, _ = synth.blob_pair(p.n, 1705, max_disp=2.0)
+    vt = np.stack([synth.random_coefficients(p.band, 1710 + n, bound=2.5) for n in range(p.nt)])
+    g = O.Point(vt, I0, I1, p).gradient()[0]
+    eps = 1e-6
+    checked = 0
+    for s in range(24):
+        dvt = np.stack([synth.random_direction(p.band, 1800 + 10 * s + n) for n in range(p.nt)])
+        if not _kink_free_nst(vt, dvt, eps, p):
+            continue
+        fd = (O.energy(vt + eps * dvt, I0, I1, p) - O.energy(vt - eps * dvt, I0, I1, p)) / (2 * eps)
+        dd = O.inner(g, dvt)
+        assert abs(fd - dd) <= 1e-6 * abs(dd), (s, fd, dd)
+        checked += 1
+        if checked == 8:
+            break
+    assert checked == 8
+
+
+def test_nonstationary_gn_hessian():
+    """Symmetric, positive, and the FD of the gradient at zero residual."""
+    p = O.Params(n=(12, 10, 12), band=(4, 4, 6), nt=4, stationary=False)
+    I0, _, _ = synth.blob_pair(p.n, 1720, max_disp=2.0)
+    vt = np.stack([synth.random_coefficients(p.band, 1721 + n, bound=2.0) for n in range(p.nt)])
+    I1 = O.Point(vt, I0, I0, p).m[-1]
+    pt = O.Point(vt, I0, I1, p)
+    v = np.stack([synth.random_direction(p.band, 1730 + n) for n in range(p.nt)])
+    w = np.stack([synth.random_direction(p.band, 1740 + n) for n in range(p.nt)])
+    Hv, Hw = pt.gn_hessvec(v)[0], pt.gn_hessvec(w)[0]
+    a, b = O.inner(Hv, w), O.inner(v, Hw)
+    assert abs(a - b) <= 1e-10 * max(abs(a), abs(b))
+    assert O.inner(Hv, v) > 0.0
+    eps = 1e-6
+    checked = 0
+    for s in range(6):
+        dvt = np.stack([synth.random_direction(p.band, 1750 + 10 * s + n) for n in range(p.nt)])
+        if not _kink_free_nst(vt, dvt, eps, p):
+            continue
+        gp = O.Point(vt + eps * dvt, I0, I1, p).gradient()[0]
+        gm = O.Point(vt - eps * dvt, I0, I1, p).gradient()[0]
+        assert rel(pt.gn_hessvec(dvt)[0], (gp - gm) / (2 * eps)) < 1e-6
+        checked += 1
+    assert checked >= 2
+
+
+def test_nonstationary_newton_decreases_energy():
+    p = O.Params(n=(16, 16, 16), band=(4, 4, 4), nt=4, stationary=False)
+    I0, I1, _ = synth.blob_pair(p.n, 71, max_disp=2.0)
+    rep = O.newton(np.zeros((p.nt, 3) + p.band, complex), I0, I1, p, max_newton=4,
+                   max_pcg=8, gtol=1e-6)
+    assert rep.iterations >= 3
+    assert all(b < a for a, b in zip(rep.energies, rep.energies[1:]))
+    assert rep.grad_inf_rel < 0.5
