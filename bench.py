@@ -379,7 +379,8 @@ def measure_form(precision, dev, I0g, I1g, flush, stream, reps=3, hvp_reps=50, *
     prec = blr.BLR_MIXED if precision == "mixed" else blr.BLR_FP32
     plan = blr.Plan(N, BAND, NT, precision=prec, **form)
     plan.set_images(I0g, I1g)
-    vt = torch.zeros((3,) + BAND, dtype=torch.complex64, device=dev)
+    steps = NT if form.get("nonstationary") else 1     # velocities in the parameter vector
+    vt = torch.zeros((steps, 3) + BAND, dtype=torch.complex64, device=dev)
 
     def step():
         vt.zero_()
@@ -397,7 +398,8 @@ def measure_form(precision, dev, I0g, I1g, flush, stream, reps=3, hvp_reps=50, *
         e1.record(stream)
         e1.synchronize()
         tot += e0.elapsed_time(e1)
-    dvt = torch.from_numpy(synth.random_direction(BAND, SEED + 2).astype(np.complex64)).to(dev)
+    dvt = torch.from_numpy(np.stack([synth.random_direction(BAND, SEED + 2 + n)
+                                     for n in range(steps)]).astype(np.complex64)).to(dev)
     hout = torch.empty_like(dvt)
     for _ in range(3):
         plan.hessvec(dvt, hout)
@@ -478,7 +480,10 @@ def main_ours(args):
                 constraint="divergence-free band fields (Leray projector)"),
             "full_newton": dict(
                 measure_form(args.precision, dev, I0g, I1g, flush, stream, hessian=1),
-                hessian="full: exact second derivative of the discrete energy, truncated PCG")}
+                hessian="full: exact second derivative of the discrete energy, truncated PCG"),
+            "nonstationary": dict(
+                measure_form(args.precision, dev, I0g, I1g, flush, stream, nonstationary=True),
+                velocity="one band-limited velocity per time step (10 x 3 x 32^3 coefficients)")}
 
     # end to end through the C-ABI with pinned host buffers
     if not args.no_e2e:
@@ -689,7 +694,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
-                    help="skip the incompressible and full-Newton measurements")
+                    help="skip the incompressible, full-Newton and non-stationary measurements")
     ap.add_argument("--adjoint-traffic", type=float, default=None,
                     help="dram bytes per adjoint-step launch from an ncu capture of this kernel")
     ap.add_argument("--workload", choices=["phantom128", "uneven64"], default="phantom128",

@@ -4,9 +4,9 @@
  *
  * Method: Hernandez, "Newton-Krylov optimization in PDE-constrained
  * diffeomorphic registration parameterized in the space of band-limited vector
- * fields" (arXiv 1807.05117), state-equation variant, stationary velocity,
- * Gauss-Newton or full Newton Hessian; compressible or incompressible
- * velocities.
+ * fields" (arXiv 1807.05117), state-equation variant, stationary or
+ * non-stationary velocity, Gauss-Newton or full Newton Hessian; compressible
+ * or incompressible velocities.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -104,6 +104,16 @@ typedef struct blr_params {
     int hessian;     /* BLR_GAUSS_NEWTON or BLR_NEWTON.  BLR_NEWTON keeps   */
                      /* every adjoint and incremental state (2 nt V floats  */
                      /* more), so it takes no checkpoints; batches reject it */
+    int nonstationary; /* 0: one velocity v~ for all steps.  1: one per time */
+                     /* step, v~^n transporting step n (the time-varying    */
+                     /* v~_t of Section 3.2): every velocity, gradient, HVP, */
+                     /* PCG and Newton array is then [nt][3][B1][B2][B3]    */
+                     /* (nt times 2*3*B1*B2*B3 floats), the regulariser is  */
+                     /* 1/2 dt sum_n <A v~^n, v~^n> and the gradient is     */
+                     /* g^n = dt A v~^n + pi(b^n), b^n = dt lambda^{n+1}    */
+                     /* grad m^n(x + d^n).  blr_adjoint then writes nt * 3V */
+                     /* floats (b^n per step).  Gauss-Newton only; batches  */
+                     /* reject it.                                          */
 } blr_params;
 
 /* Result of blr_newton (host struct filled by the library). */
@@ -242,7 +252,8 @@ int blr_newton(blr_plan_t plan, float *vt, int max_newton, int max_pcg,
 typedef struct blr_batch *blr_batch_t;
 
 /* params: host array of npairs descriptions.  BLR_EINVAL if they differ in nt,
- * request BLR_MIXED, checkpoints or the incompressible form, or one is invalid. */
+ * request BLR_MIXED, checkpoints, the incompressible form, the full Hessian or
+ * non-stationary velocities, or one is invalid. */
 int blr_batch_create(const blr_params *params, int npairs, blr_batch_t *out);
 int blr_batch_destroy(blr_batch_t batch);
 

@@ -39,7 +39,7 @@ class blr_params(ctypes.Structure):
                 ("alpha", ctypes.c_double), ("gamma", ctypes.c_double), ("s", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("precision", ctypes.c_int),
                 ("ckpt_every", ctypes.c_int), ("incompressible", ctypes.c_int),
-                ("hessian", ctypes.c_int)]
+                ("hessian", ctypes.c_int), ("nonstationary", ctypes.c_int)]
 
 
 class blr_report(ctypes.Structure):
@@ -147,7 +147,8 @@ def _ptr(t, *, device_only=True, dtype=None, numel=None, optional=False, name="t
 
 
 def make_params(n, band, nt=10, alpha=3.0, gamma=1.0, s=2, sigma=1.0, precision=BLR_FP32,
-                ckpt_every=0, incompressible=False, hessian=BLR_GAUSS_NEWTON):
+                ckpt_every=0, incompressible=False, hessian=BLR_GAUSS_NEWTON,
+                nonstationary=False):
     p = blr_params()
     p.n[:] = [int(v) for v in n]
     p.band[:] = [int(v) for v in band]
@@ -157,6 +158,7 @@ def make_params(n, band, nt=10, alpha=3.0, gamma=1.0, s=2, sigma=1.0, precision=
     p.ckpt_every = int(ckpt_every)
     p.incompressible = 1 if incompressible else 0
     p.hessian = int(hessian)
+    p.nonstationary = 1 if nonstationary else 0
     return p
 
 
@@ -284,9 +286,9 @@ class Plan:
 
     def __init__(self, n, band, nt=10, alpha=3.0, gamma=1.0, s=2, sigma=1.0,
                  precision=BLR_FP32, ckpt_every=0, incompressible=False,
-                 hessian=BLR_GAUSS_NEWTON):
+                 hessian=BLR_GAUSS_NEWTON, nonstationary=False):
         self.params = make_params(n, band, nt, alpha, gamma, s, sigma, precision, ckpt_every,
-                                  incompressible, hessian)
+                                  incompressible, hessian, nonstationary)
         self.n = tuple(int(v) for v in n)
         self.band = tuple(int(v) for v in band)
         self.nt = int(nt)

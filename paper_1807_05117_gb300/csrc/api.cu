@@ -26,6 +26,9 @@ int validate(const blr_params *p) {
     if (!(p->s >= 0 && p->s <= 32) || 2.0 * p->s != floor(2.0 * p->s)) return BLR_EINVAL;
     if (p->incompressible != 0 && p->incompressible != 1) return BLR_EINVAL;
     if (p->hessian != BLR_GAUSS_NEWTON && p->hessian != BLR_NEWTON) return BLR_EINVAL;
+    if (p->nonstationary != 0 && p->nonstationary != 1) return BLR_EINVAL;
+    // the full Hessian is built for stationary velocities
+    if (p->nonstationary && p->hessian == BLR_NEWTON) return BLR_EINVAL;
     // the full Hessian keeps every adjoint and incremental state: no checkpoints
     if (p->hessian == BLR_NEWTON && p->ckpt_every > 0 && p->ckpt_every < p->nt) return BLR_EINVAL;
     if (p->precision != BLR_FP32 && p->precision != BLR_MIXED) return BLR_EINVAL;
@@ -55,8 +58,8 @@ size_t layout(blr_plan *P, char *base) {
     P->m = a.take<float>((size_t)(P->nseg + P->ck) * V);
     P->I0 = P->m;                        // m^0 = I0 lives in the first slot
     P->I1 = a.take<float>(V);
-    P->d = a.take<float>(3 * V);
-    P->d4 = P->sweep_wide ? a.take<float4>(V) : nullptr;
+    P->d = P->d_base = a.take<float>((size_t)3 * P->nvel * V);
+    P->d4 = P->d4_base = P->sweep_wide ? a.take<float4>((size_t)P->nvel * V) : nullptr;
     P->lam[0] = a.take<float>(V);
     P->lam[1] = a.take<float>(V);
     if (P->p.hessian == BLR_NEWTON) {
@@ -141,8 +144,10 @@ int state_at(blr_plan *P, const float *vt, double *energy_out, cudaStream_t s) {
         BLR_CK(cudaMemcpyAsync(P->vt, vt, P->nfloat * sizeof(float), cudaMemcpyDefault, s));
     }
     P->have_lams = false;
-    rc = dft_expand(P, P->vt, P->d, 1, s);
-    if (rc) return rc;
+    for (int n = 0; n < P->nvel; ++n) {   // every step's displacement (one when stationary)
+        use_step(P, n);
+        if ((rc = dft_expand(P, P->vt + (size_t)n * P->nf1, P->d, 1, s))) return rc;
+    }
     if ((rc = sweep_state(P, s))) return rc;
     if ((rc = energy_finalize(P, P->vt, energy_out, (int)sweep_blocks(P), s))) return rc;
     P->have_state = true;
@@ -150,10 +155,15 @@ int state_at(blr_plan *P, const float *vt, double *energy_out, cudaStream_t s) {
 }
 
 // g = A v~ + pi(b) at the current point (incompressible: P applied to it).
+// Non-stationary: g^n = dt A v~^n + pi(b^n) per step.
 int gradient_here(blr_plan *P, float *g, cudaStream_t s) {
-    int rc = sweep_adjoint(P, P->b, nullptr, P->lam_nt, s);
-    if (rc) return rc;
-    if ((rc = dft_project(P, P->b, g, P->vt, s))) return rc;
+    int rc;
+    if (P->nvel > 1) {
+        if ((rc = sweep_adjoint_steps(P, P->lam_nt, g, P->vt, nullptr, nullptr, s))) return rc;
+    } else {
+        if ((rc = sweep_adjoint(P, P->b, nullptr, P->lam_nt, s))) return rc;
+        if ((rc = dft_project(P, P->b, g, P->vt, s))) return rc;
+    }
     return P->p.incompressible ? vec_leray(P, g, g, s) : BLR_OK;
 }
 
@@ -167,6 +177,11 @@ int hessvec_here(blr_plan *P, const float *dvt, float *hdv, cudaStream_t s) {
     if (P->p.incompressible) {
         if ((rc = vec_leray(P, P->vproj, dvt, s))) return rc;
         dvt = P->vproj;
+    }
+    if (P->nvel > 1) {   // non-stationary: each step expands its own direction
+        if ((rc = sweep_incremental(P, s, dvt))) return rc;
+        if ((rc = sweep_adjoint_steps(P, P->lam[0], hdv, dvt, nullptr, nullptr, s))) return rc;
+        return P->p.incompressible ? vec_leray(P, hdv, hdv, s) : BLR_OK;
     }
     if ((rc = dft_expand(P, dvt, P->dv, 0, s))) return rc;
     if ((rc = sweep_incremental(P, s))) return rc;
@@ -275,7 +290,9 @@ int plan_create(const blr_params *p, bool grad_cache, blr_plan **out) {
     P->B3 = p->band[2];
     P->V = (long long)P->N1 * P->N2 * P->N3;
     P->nb = (long long)P->B1 * P->B2 * P->B3;
-    P->nfloat = 6 * P->nb;
+    P->nf1 = 6 * P->nb;
+    P->nvel = p->nonstationary ? p->nt : 1;
+    P->nfloat = P->nvel * P->nf1;
     P->dt = (float)(1.0 / p->nt);
     P->ck = (p->ckpt_every > 0 && p->ckpt_every < p->nt) ? p->ckpt_every : p->nt;
     P->nseg = (int)ceil_div_ll(p->nt, P->ck);
@@ -384,6 +401,8 @@ int blr_state(blr_plan_t P, const float *vt, float *m1, double *energy, blr_stre
 int blr_adjoint(blr_plan_t P, float *b, float *lambda0, blr_stream_t stream) {
     if (check_plan(P) || !b) return BLR_EINVAL;
     if (!P->have_state) return BLR_ESTATE;
+    if (P->nvel > 1)   // one body force per step: b holds nt * 3V floats
+        return sweep_adjoint_steps(P, P->lam_nt, nullptr, nullptr, b, lambda0, (cudaStream_t)stream);
     return sweep_adjoint(P, b, lambda0, P->lam_nt, (cudaStream_t)stream);
 }
 

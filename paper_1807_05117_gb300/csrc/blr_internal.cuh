@@ -87,7 +87,9 @@ struct blr_plan {
     int N1, N2, N3, B1, B2, B3;
     long long V;       // voxels
     long long nb;      // B1*B2*B3
-    long long nfloat;  // floats in one coefficient array: 2*3*nb
+    long long nf1;     // floats in one velocity's coefficients: 2*3*nb
+    int nvel;          // velocities in the parameter vector: 1, or nt (non-stationary)
+    long long nfloat;  // floats in one parameter vector: nvel * nf1
     float dt;
     int device;
     int chunk;          // x1 planes per state / incremental-state sweep block
@@ -99,9 +101,12 @@ struct blr_plan {
     Grid3 grid;
 
     float *I0, *I1;
-    float *vt;          // current point (2*3*nb)
-    float *d;           // 3V displacement -dt*iota(vt), clamped to [-1, 1)
+    float *vt;          // current point (nfloat)
+    float *d;           // 3V displacement -dt*iota(vt), clamped to [-1, 1) (non-stationary:
+                        // the step that use_step selected)
     float4 *d4;         // V (d0, d1, d2, 0) copy of d for the wide-copy sweeps, or nullptr
+    float *d_base;      // [nvel][3V] every step's displacement
+    float4 *d4_base;    // [nvel][V] their float4 copies, or nullptr
     bool sweep_wide;    // adjoint and incremental state use the wide-copy kernels (N3 % 4 == 0)
     bool use_gm;        // Gm is kept (see Gm)
     int bal_inc;        // blocks per SM of the wide-copy incremental-state grid (sweep_autotune)
@@ -171,6 +176,15 @@ inline float *state_slot(const blr_plan *P, int n) {
     return P->m + slot * P->V;
 }
 
+// Point d / d4 at the displacement of step n (a no-op for stationary plans: every
+// step has the one displacement).  The launchers read P->d / P->d4 when they
+// launch, so each step's kernels see their own step's field.
+inline void use_step(blr_plan *P, int n) {
+    if (P->nvel <= 1) return;
+    P->d = P->d_base + (size_t)3 * n * P->V;
+    if (P->d4_base) P->d4 = P->d4_base + (size_t)n * P->V;
+}
+
 // Plan creation (api.cu); grad_cache: keep the per-step state gradients Gm
 // when every state is stored (batch members run their own sweeps and skip it).
 int plan_create(const blr_params *p, bool grad_cache, blr_plan **out);
@@ -181,8 +195,9 @@ int plan_create(const blr_params *p, bool grad_cache, blr_plan **out);
 int dft_init_tables(blr_plan *P, cudaStream_t s);
 // iota into out (3V). mode 0: out = v; mode 1: out = clamp(-dt*v) + CFL/NaN flags.
 int dft_expand(blr_plan *P, const float *vt, float *out, int mode, cudaStream_t s);
-// pi(f) (+ A * vadd when vadd != nullptr) into ft.
-int dft_project(blr_plan *P, const float *f, float *ft, const float *vadd, cudaStream_t s);
+// pi(f) (+ areg A * vadd when vadd != nullptr) into ft.
+int dft_project(blr_plan *P, const float *f, float *ft, const float *vadd, cudaStream_t s,
+                float areg = 1.0f);
 
 // dft_tc.cu (BLR_MIXED)
 // stage kinds: 0 / 1 axis-1 expand / project, 2 / 3 axis-2 expand / project
@@ -205,7 +220,13 @@ int sweep_adjoint(blr_plan *P, float *b, float *lambda0, const float *lam_final,
 // The full Newton incremental adjoint: as sweep_adjoint from dlambda^nt in lam[0], with
 // the second-order terms of newton.cu after every step (needs lam_all and dm_all).
 int sweep_adjoint_newton(blr_plan *P, float *b, cudaStream_t s);
-int sweep_incremental(blr_plan *P, cudaStream_t s);            // dm -> dlambda^nt in lam[0]
+// dm -> dlambda^nt in lam[0]; dvt_steps (non-stationary plans): the direction's
+// coefficients, expanded into P->dv before each step.
+int sweep_incremental(blr_plan *P, cudaStream_t s, const float *dvt_steps = nullptr);
+// Non-stationary adjoint: per step n, b^n = dt lambda^{n+1} grad m^n (into b_steps +
+// 3nV when given, else P->b) and, when gout is given, gout^n = pi(b^n) + dt A vadd^n.
+int sweep_adjoint_steps(blr_plan *P, const float *lam_final, float *gout, const float *vadd,
+                        float *b_steps, float *lambda0, cudaStream_t s);
 // wide: the adjoint and incremental-state items use the wide-copy tiles (every
 // pair has N3 % 4 == 0); the incremental-state tiles are then AJ rows high.
 int sweep_batch_launch(int kind, bool f1, bool f2, bool wide, const SweepPair *pairs,

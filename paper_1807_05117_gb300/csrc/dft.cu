@@ -274,7 +274,7 @@ constexpr int PXC = 128;
 __global__ void __launch_bounds__(256)
 k_project_axis3(const float *__restrict__ in, const float *__restrict__ T3c,
                 const float *__restrict__ T3s, float *__restrict__ out,
-                const float *__restrict__ Aw, const float *__restrict__ vadd,
+                const float *__restrict__ Aw, const float *__restrict__ vadd, float areg,
                 int rows, int B2, int B3, int N3, int nb12) {
     extern __shared__ float2 sh2[];
     const int B3p = B3 + 1;
@@ -335,7 +335,7 @@ k_project_axis3(const float *__restrict__ in, const float *__restrict__ T3c,
             const long long o = ((long long)row * B3 + k3) * 2;
             float re = are[r][t], im = aim[r][t];
             if (vadd) {
-                const float a = Aw[(long long)(row % nb12) * B3 + k3];
+                const float a = areg * Aw[(long long)(row % nb12) * B3 + k3];
                 re = fmaf(a, vadd[o], re);
                 im = fmaf(a, vadd[o + 1], im);
             }
@@ -405,7 +405,8 @@ int dft_expand(blr_plan *P, const float *vt, float *out, int mode, cudaStream_t 
     return BLR_OK;
 }
 
-int dft_project(blr_plan *P, const float *f, float *ft, const float *vadd, cudaStream_t s) {
+int dft_project(blr_plan *P, const float *f, float *ft, const float *vadd, cudaStream_t s,
+                float areg) {
     const long long ncol = (long long)P->N2 * P->N3;
     // stage C'
     if (P->p.precision == BLR_MIXED) {
@@ -434,7 +435,7 @@ int dft_project(blr_plan *P, const float *f, float *ft, const float *vadd, cudaS
     BLR_CK(cudaFuncSetAttribute(k_project_axis3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp));
     launch_pdl(k_project_axis3, dim3((unsigned)ceil_div_ll(rows, XR)), dim3(256), sp, s,
                (const float *)P->dft_small, (const float *)P->T3c, (const float *)P->T3s, ft,
-               (const float *)P->A, vadd, rows, P->B2, P->B3, P->N3, P->B1 * P->B2);
+               (const float *)P->A, vadd, areg, rows, P->B2, P->B3, P->N3, P->B1 * P->B2);
     BLR_CK_LAUNCH();
     return BLR_OK;
 }

@@ -73,7 +73,8 @@ extern "C" int blr_expand_noalloc(const int n[3], const int band[3], const float
     P.B3 = band[2];
     P.V = (long long)N1 * N2 * N3;
     P.nb = (long long)B1 * B2 * B3;
-    P.nfloat = 6 * P.nb;
+    P.nf1 = P.nfloat = 6 * P.nb;
+    P.nvel = 1;
     P.p.alpha = 0.0;   // the regulariser table is filled but unused by iota
     P.p.gamma = 1.0;
     P.p.s = 0;

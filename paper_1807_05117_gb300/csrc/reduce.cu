@@ -28,7 +28,7 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 // Band index of float i of an interleaved complex [3][B1][B2][B3] array.
 __device__ __forceinline__ long long coef_index(long long i, long long nb) {
     const long long c = i >> 1;
-    return c < nb ? c : (c < 2 * nb ? c - nb : c - 2 * nb);
+    return c < nb ? c : (c < 2 * nb ? c - nb : (c < 3 * nb ? c - 2 * nb : c % nb));
 }
 
 // Returns true in every thread of the last block to arrive.
@@ -57,7 +57,7 @@ __device__ __forceinline__ double ordered_sum(const double *part, int count, int
 // block partials in block order.
 __global__ void __launch_bounds__(RT)
 k_energy(const double *__restrict__ partials, int np, const float *__restrict__ vt,
-         const float *__restrict__ A, long long nb, double inv_sigma2,
+         const float *__restrict__ A, long long nb, int nvel, double wreg, double inv_sigma2,
          double *__restrict__ part2, unsigned int *ticket, double *__restrict__ sc,
          double *__restrict__ out, int *status) {
     pdl_wait();
@@ -67,9 +67,9 @@ k_energy(const double *__restrict__ partials, int np, const float *__restrict__ 
     sd = block_sum<RT>(sd, red);
     if (threadIdx.x == 0) part2[2 * blockIdx.x] = sd;
     double sr = 0.0;
-    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < 3 * nb;
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < 3 * nb * nvel;
          i += (long long)gridDim.x * RT) {
-        const long long kk = i < nb ? i : (i < 2 * nb ? i - nb : i - 2 * nb);
+        const long long kk = coef_index(2 * i, nb);
         const double re = vt[2 * i], im = vt[2 * i + 1];
         sr += (double)A[kk] * (re * re + im * im);
     }
@@ -80,7 +80,7 @@ k_energy(const double *__restrict__ partials, int np, const float *__restrict__ 
     const double srt = ordered_sum(part2, gridDim.x, 2, 1, red);
     if (threadIdx.x == 0) {
         *ticket = 0;
-        const double edata = sdt * inv_sigma2, ereg = 0.5 * srt, e = ereg + edata;
+        const double edata = sdt * inv_sigma2, ereg = 0.5 * wreg * srt, e = ereg + edata;
         sc[SC_E] = e;
         sc[SC_EREG] = ereg;
         sc[SC_EDATA] = edata;
@@ -307,7 +307,8 @@ int reduce_partials_needed() { return 2 * RBLOCKS; }
 
 int energy_finalize(blr_plan *P, const float *vt, double *energy_out, int nblocks, cudaStream_t s) {
     launch_pdl(k_energy, dim3(vec_blocks(P)), dim3(RT), 0, s, (const double *)P->partials, nblocks,
-               vt, (const float *)P->A, P->nb, 1.0 / (P->p.sigma * P->p.sigma), P->partials2,
+               vt, (const float *)P->A, P->nb, P->nvel, P->nvel > 1 ? 1.0 / P->p.nt : 1.0,
+               1.0 / (P->p.sigma * P->p.sigma), P->partials2,
                P->ticket, P->dsc, energy_out, P->dstatus);
     BLR_CK_LAUNCH();
     return BLR_OK;
@@ -358,9 +359,12 @@ int vec_axpy(blr_plan *P, float *y, const float *a, const float *x, double alpha
 int vec_leray(blr_plan *P, float *out, const float *in, cudaStream_t s) {
     long long b = ceil_div_ll(P->nb, RT);
     const int blocks = (int)(b < RBLOCKS ? (b < 1 ? 1 : b) : RBLOCKS);
-    launch_pdl(k_leray, dim3(blocks), dim3(RT), 0, s, reinterpret_cast<float2 *>(out),
-               reinterpret_cast<const float2 *>(in), P->nb, P->B1, P->B2, P->B3, P->N1, P->N2,
-               P->N3);
-    BLR_CK_LAUNCH();
+    for (int v = 0; v < P->nvel; ++v) {   // one launch per velocity of the parameter vector
+        launch_pdl(k_leray, dim3(blocks), dim3(RT), 0, s,
+                   reinterpret_cast<float2 *>(out + (size_t)v * P->nf1),
+                   reinterpret_cast<const float2 *>(in + (size_t)v * P->nf1), P->nb, P->B1, P->B2,
+                   P->B3, P->N1, P->N2, P->N3);
+        BLR_CK_LAUNCH();
+    }
     return BLR_OK;
 }

@@ -1270,6 +1270,7 @@ void launch_incstate(const blr_plan *P, bool first, bool last, const float *din,
 // m^{n+1} from m^n in the slots given by state_slot (not the last step), with
 // grad m^n into Gout when given.
 int state_step(blr_plan *P, int n, float *Gout, cudaStream_t s) {
+    use_step(P, n);
     launch_state<false>(P, state_slot(P, n), state_slot(P, n + 1), nullptr, nullptr, 0.f, nullptr,
                         Gout, s);
     BLR_CK_LAUNCH();
@@ -1298,6 +1299,7 @@ int sweep_state(blr_plan *P, cudaStream_t s) {
         int rc = state_step(P, n, grad_slot(P, n), s);
         if (rc) return rc;
     }
+    use_step(P, nt - 1);
     launch_state<true>(P, state_slot(P, nt - 1), state_slot(P, nt), P->I1, P->lam_nt, lam_scale,
                        P->partials, grad_slot(P, nt - 1), s);
     BLR_CK_LAUNCH();
@@ -1330,6 +1332,7 @@ int sweep_adjoint(blr_plan *P, float *b, float *lambda0, const float *lam_final,
             }
             const bool first = (n == nt - 1);
             const bool wlam = (n > 0) || (lambda0 != nullptr);
+            use_step(P, n);
             launch_adjoint(P, first, wlam, lin, state_slot(P, n), lout, b, grad_slot(P, n), s);
             BLR_CK_LAUNCH();
             cur = 1 - cur;
@@ -1360,8 +1363,35 @@ int sweep_adjoint_newton(blr_plan *P, float *b, cudaStream_t s) {
     return BLR_OK;
 }
 
+// Non-stationary adjoint sweep: the body force is not summed over the steps, each
+// step's b^n is projected (or stored) on its own.
+int sweep_adjoint_steps(blr_plan *P, const float *lam_final, float *gout, const float *vadd,
+                        float *b_steps, float *lambda0, cudaStream_t s) {
+    const int nt = P->p.nt;
+    int cur = 0;
+    for (int j = P->nseg - 1; j >= 0; --j) {
+        int rc = ensure_segment(P, j, s);
+        if (rc) return rc;
+        const int n0 = j * P->ck, n1 = n0 + P->ck < nt ? n0 + P->ck : nt;
+        for (int n = n1 - 1; n >= n0; --n) {
+            const float *lin = (n == nt - 1) ? lam_final : P->lam[cur];
+            float *lout = (n == 0 && lambda0) ? lambda0 : P->lam[1 - cur];
+            const bool wlam = (n > 0) || (lambda0 != nullptr);
+            float *bn = b_steps ? b_steps + (size_t)3 * n * P->V : P->b;
+            use_step(P, n);
+            launch_adjoint(P, true, wlam, lin, state_slot(P, n), lout, bn, grad_slot(P, n), s);
+            BLR_CK_LAUNCH();
+            if (gout && (rc = dft_project(P, bn, gout + (size_t)n * P->nf1,
+                                          vadd + (size_t)n * P->nf1, s, P->dt)))
+                return rc;
+            cur = 1 - cur;
+        }
+    }
+    return BLR_OK;
+}
+
 // Incremental state from dv = iota(dv~) (in P->dv); leaves dlambda^nt in lam[0].
-int sweep_incremental(blr_plan *P, cudaStream_t s) {
+int sweep_incremental(blr_plan *P, cudaStream_t s, const float *dvt_steps) {
     const int nt = P->p.nt;
     const float lam_scale = (float)(-2.0 / (P->p.sigma * P->p.sigma));
     int cur = 0;
@@ -1376,6 +1406,9 @@ int sweep_incremental(blr_plan *P, cudaStream_t s) {
                 din = n > 0 ? P->dm_all + (size_t)(n - 1) * P->V : P->dm[0];
                 if (n < nt - 1) dout = P->dm_all + (size_t)n * P->V;
             }
+            if (dvt_steps && (rc = dft_expand(P, dvt_steps + (size_t)n * P->nf1, P->dv, 0, s)))
+                return rc;
+            use_step(P, n);
             launch_incstate(P, n == 0, n == nt - 1, din, state_slot(P, n), dout, lam_scale,
                             grad_slot(P, n), s);
             BLR_CK_LAUNCH();

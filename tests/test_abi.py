@@ -66,12 +66,18 @@ def test_strerror_and_invalid_params(lib):
     p = blr.make_params((16, 16, 16), (4, 4, 4))
     p.hessian = 2
     assert lib.blr_plan_create(ctypes.byref(p), ctypes.byref(h)) == blr.BLR_EINVAL
+    # the full Hessian is built for stationary velocities
+    p = blr.make_params((16, 16, 16), (4, 4, 4), nonstationary=True, hessian=blr.BLR_NEWTON)
+    assert lib.blr_plan_create(ctypes.byref(p), ctypes.byref(h)) == blr.BLR_EINVAL
+    p = blr.make_params((16, 16, 16), (4, 4, 4))
+    p.nonstationary = 2
+    assert lib.blr_plan_create(ctypes.byref(p), ctypes.byref(h)) == blr.BLR_EINVAL
     # the full Hessian keeps every state: no checkpoints
     p = blr.make_params((16, 16, 16), (4, 4, 4), nt=4, ckpt_every=2, hessian=blr.BLR_NEWTON)
     assert lib.blr_plan_create(ctypes.byref(p), ctypes.byref(h)) == blr.BLR_EINVAL
     # batches take neither the incompressible form, mixed precision nor the full Hessian
     for kw in (dict(incompressible=True), dict(precision=blr.BLR_MIXED),
-               dict(hessian=blr.BLR_NEWTON)):
+               dict(hessian=blr.BLR_NEWTON), dict(nonstationary=True)):
         arr = (blr.blr_params * 2)(blr.make_params((16, 16, 16), (4, 4, 4), nt=4),
                                    blr.make_params((16, 16, 16), (4, 4, 4), nt=4, **kw))
         assert lib.blr_batch_create(arr, 2, ctypes.byref(h)) == blr.BLR_EINVAL
