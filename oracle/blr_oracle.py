@@ -30,6 +30,12 @@ fields", arXiv 1807.05117):
   step, the time-varying v~_t of Section 3.2 and of the NSt. experiments): the
   regulariser is the time integral 1/2 dt sum_n <L~ v~^n, v~^n>, and the
   gradient and Hessian are taken per step;
+* the deformation-state-equation variant (Section 2.3, Eqs. 16-18; its
+  band-limited form in Section 3.3): the deformation phi = id + u is transported,
+  u^0 = 0, u^{n+1} = S u^n + d, and the template is warped once,
+  m(1) = T[I0](x + u^nt); the adjoint rho (a vector field) starts from
+  rho^nt = lambda(1) grad T[I0](x + u^nt) and runs backwards with S^T; the body
+  force is dt sum_n (rho^{n+1} + D u^n^T rho^{n+1}) (Gauss-Newton Hessian only);
 * the incompressible form (Eq. 4 with gamma = 1, imposed in the band as in
   Section 3.2): the velocity is restricted to divergence-free band fields by the
   Fourier-diagonal Leray projector P(k) = I - kappa kappa^T / |kappa|^2,
@@ -88,6 +94,8 @@ class Params:
     incompressible -- restrict v~ to divergence-free band fields (Eq. 4, gamma = 1)
     stationary -- one velocity for all steps, coefficients (3, B1, B2, B3); else one
               per step, (nt, 3, B1, B2, B3), step n transported by v~^n
+    state  -- "image" (the state equation) or "deformation" (the deformation state
+              equation: u = phi - id is transported, I0 warped once at the end)
     """
 
     n: tuple
@@ -99,6 +107,7 @@ class Params:
     sigma: float = 1.0
     incompressible: bool = False
     stationary: bool = True
+    state: str = "image"
 
     @property
     def dt(self) -> float:
@@ -461,8 +470,102 @@ class Point:
         return h, dms[-1], db
 
 
+class DeformationPoint:
+    """The deformation-state-equation variant at one velocity (Section 2.3,
+    Eqs. 16-18, with the band-limited velocity of Section 3.3), discretised on
+    the same semi-Lagrangian step S as the image variant:
+      u^0 = 0, u^{n+1} = S u^n + d            (phi^{n+1}(x) = phi^n(x + d(x)))
+      m(1) = T[I0](x + u^nt)                  (trilinear, any displacement, periodic)
+      E = 1/2 <A v~, v~> + sigma^-2 ||m(1) - I1||^2.
+    Stationary velocity, Gauss-Newton Hessian."""
+
+    def __init__(self, vt: np.ndarray, I0: np.ndarray, I1: np.ndarray, p: Params):
+        if not p.stationary:
+            raise NotImplementedError("the deformation variant takes a stationary velocity")
+        self.p = p
+        self.vt = np.asarray(vt, dtype=np.complex128)
+        if p.incompressible:
+            self.vt = leray(self.vt, p.n)
+        self.I0 = np.asarray(I0, dtype=np.float64)
+        self.I1 = np.asarray(I1, dtype=np.float64)
+        self.A = regulariser_weights(p)
+        self.d = displacement(self.vt, p)
+        self.cfl = cfl_number(self.d)
+        self.stencil = Stencil(self.d)
+        u = [np.zeros((3,) + tuple(p.n))]
+        for _ in range(p.nt):
+            u.append(np.stack([self.stencil.apply(u[-1][c]) for c in range(3)]) + self.d)
+        self.u = u
+        self.warp = Stencil(u[-1])              # T[.](x + u^nt): general displacement
+        self.m1 = self.warp.apply(self.I0)
+        self.grad_warp = self.warp.gradient(self.I0)   # grad T[I0](x + u^nt)
+        self.energy_reg = regulariser_energy(self.vt, self.A)
+        self.energy_data = data_energy(self.m1, self.I1, p)
+        self.energy = self.energy_reg + self.energy_data
+        self._Du = {}
+
+    def grad_u(self, n: int) -> np.ndarray:
+        """(3 components c, 3 axes a, ...): D_a u_c^n at the departure points."""
+        if n not in self._Du:
+            self._Du[n] = np.stack([self.stencil.gradient(self.u[n][c]) for c in range(3)])
+        return self._Du[n]
+
+    def _body_force(self, rho_final: np.ndarray) -> np.ndarray:
+        """rho^n = S^T rho^{n+1} per component and b_a = dt sum_n (rho_a^{n+1} +
+        sum_c rho_c^{n+1} D_a u_c^n), the derivative of u^{n+1} = S u^n + d in d."""
+        p = self.p
+        rho = rho_final
+        b = np.zeros((3,) + tuple(p.n))
+        for n in range(p.nt - 1, -1, -1):
+            b += p.dt * (rho + np.einsum("c...,ca...->a...", rho, self.grad_u(n)))
+            rho = np.stack([self.stencil.apply_transpose(rho[c]) for c in range(3)])
+        return b
+
+    def gradient(self):
+        """g~ = A v~ + pi(b) with rho^nt = lambda(1) grad T[I0](x + u^nt),
+        lambda(1) = -(2/sigma^2)(m(1) - I1).  Returns (g~, b)."""
+        lam = -(2.0 / self.p.sigma**2) * (self.m1 - self.I1)
+        b = self._body_force(lam[None] * self.grad_warp)
+        g = self.A[None] * self.vt + project(b, self.p.band)
+        if self.p.incompressible:
+            g = leray(g, self.p.n)
+        return g, b
+
+    def incremental_state(self, dvt: np.ndarray) -> np.ndarray:
+        """du^0 = 0, du^{n+1} = S du^n + (D u^n) dd + dd, dd = -dt iota(dv~);
+        returns dm(1) = grad T[I0](x + u^nt) . du^nt."""
+        p = self.p
+        dd = -p.dt * expand(dvt, p.n)
+        du = np.zeros((3,) + tuple(p.n))
+        for n in range(p.nt):
+            Sdu = np.stack([self.stencil.apply(du[c]) for c in range(3)])
+            du = Sdu + np.einsum("ca...,a...->c...", self.grad_u(n), dd) + dd
+        return np.sum(self.grad_warp * du, axis=0)
+
+    def gn_hessvec(self, dvt: np.ndarray):
+        """A dv~ + pi(db): drho^nt = dlambda(1) grad T[I0](x + u^nt) with
+        dlambda(1) = -(2/sigma^2) dm(1); the Gauss-Newton drops of Section 3.4
+        remove lambda(1) d(grad m(1)), the D du^T rho term and the variation of
+        S^T.  Returns (H dv~, dm(1))."""
+        dvt = np.asarray(dvt, dtype=np.complex128)
+        if self.p.incompressible:
+            dvt = leray(dvt, self.p.n)
+        dm1 = self.incremental_state(dvt)
+        dlam = -(2.0 / self.p.sigma**2) * dm1
+        db = self._body_force(dlam[None] * self.grad_warp)
+        h = self.A[None] * dvt + project(db, self.p.band)
+        if self.p.incompressible:
+            h = leray(h, self.p.n)
+        return h, dm1
+
+
+def make_point(vt, I0, I1, p: Params):
+    """The point of the chosen state equation (Point or DeformationPoint)."""
+    return DeformationPoint(vt, I0, I1, p) if p.state == "deformation" else Point(vt, I0, I1, p)
+
+
 def energy(vt, I0, I1, p: Params) -> float:
-    return Point(vt, I0, I1, p).energy
+    return make_point(vt, I0, I1, p).energy
 
 
 # ----------------------------------------------------------------------------
@@ -541,8 +644,8 @@ def newton(vt0, I0, I1, p: Params, max_newton=5, max_pcg=10, gtol=1e-2,
     forcing=None uses eta = min(0.5, sqrt(||g|| / ||g0||)); a number fixes eta.
     Stops when ||g||_inf / ||g0||_inf < gtol, after max_newton updates, or when
     the line search fails."""
-    pt = Point(vt0, I0, I1, p)
-    g, _, _ = pt.gradient()
+    pt = make_point(vt0, I0, I1, p)
+    g = pt.gradient()[0]
     g0_inf = max_abs(g)
     g0_2 = np.sqrt(inner(g, g))
     energies = [pt.energy]
@@ -563,7 +666,7 @@ def newton(vt0, I0, I1, p: Params, max_newton=5, max_pcg=10, gtol=1e-2,
         eps = 1.0
         accepted = None
         for _ in range(max_halvings + 1):
-            trial = Point(pt.vt + eps * step, I0, I1, p)
+            trial = make_point(pt.vt + eps * step, I0, I1, p)
             if trial.cfl < 1.0 and trial.energy <= pt.energy + c1 * eps * slope:
                 accepted = trial
                 break
@@ -572,7 +675,7 @@ def newton(vt0, I0, I1, p: Params, max_newton=5, max_pcg=10, gtol=1e-2,
             break
         steps.append(eps)
         pt = accepted
-        g, _, _ = pt.gradient()
+        g = pt.gradient()[0]
         energies.append(pt.energy)
     rel = max_abs(g) / g0_inf if g0_inf > 0 else 0.0
     return NewtonReport(len(steps), pcg_its, energies, steps, rel, pt.vt)

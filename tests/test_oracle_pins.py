@@ -811,3 +811,120 @@ def test_nonstationary_newton_decreases_energy():
     assert rep.iterations >= 3
     assert all(b < a for a, b in zip(rep.energies, rep.energies[1:]))
     assert rep.grad_inf_rel < 0.5
+
+
+# ----------------------------------------------------------------------------
+# Deformation-state-equation variant (Section 2.3, Eqs. 16-18)
+# ----------------------------------------------------------------------------
+
+
+def _kink_free_def(vt, dvt, eps, p):
+    """No cell change in the step stencil nor in the final warp between v -+ eps dv."""
+    a = O.DeformationPoint(vt - eps * dvt, np.zeros(p.n), np.zeros(p.n), p)
+    b = O.DeformationPoint(vt + eps * dvt, np.zeros(p.n), np.zeros(p.n), p)
+    return (np.array_equal(np.floor(a.d), np.floor(b.d)) and
+            np.array_equal(np.floor(a.u[-1]), np.floor(b.u[-1])))
+
+
+def test_deformation_constant_velocity_is_exact_shift():
+    """A constant velocity moving 1 voxel per step (a hair less) along axes 0
+    and 2: u^nt = nt d, and m(1) is I0 shifted by nt voxels on those axes,
+    as in the image variant (catches a missing + d in the deformation step or a
+    wrong warp)."""
+    n, band, nt = (10, 8, 12), (4, 4, 4), 3
+    I0 = np.random.default_rng(1901).normal(size=n)
+    vt = np.zeros((3,) + band, complex)
+    centre = tuple(b // 2 for b in band)
+    vt[(0,) + centre] = -0.999999999999 * nt     # d_0 = 0.999999999999
+    vt[(2,) + centre] = 0.999999999999 * nt      # d_2 = -0.999999999999
+    for state in ("deformation", "image"):
+        p = O.Params(n=n, band=band, nt=nt, state=state)
+        pt = O.make_point(vt, I0, I0, p)
+        m1 = pt.m1 if state == "deformation" else pt.m[-1]
+        want = np.roll(I0, shift=(-nt, 0, nt), axis=(0, 1, 2))
+        assert np.max(np.abs(m1 - want)) < 1e-9, state
+    assert np.max(np.abs(pt.energy_reg)) > 0
+
+
+def test_deformation_gradient_matches_finite_differences():
+    p = O.Params(n=(12, 12, 12), band=(4, 6, 4), nt=5, state="deformation")
+    I0, I1, _ = synth.blob_pair(p.n, 1911, max_disp=2.0)
+    vt = synth.random_coefficients(p.band, 1912, bound=2.5)
+    g = O.DeformationPoint(vt, I0, I1, p).gradient()[0]
+    eps = 1e-6
+    checked = 0
+    for s in range(24):
+        dvt = synth.random_direction(p.band, 1920 + s)
+        if not _kink_free_def(vt, dvt, eps, p):
+            continue
+        fd = (O.energy(vt + eps * dvt, I0, I1, p) - O.energy(vt - eps * dvt, I0, I1, p)) / (2 * eps)
+        dd = O.inner(g, dvt)
+        assert abs(fd - dd) <= 1e-6 * abs(dd), (s, fd, dd)
+        checked += 1
+        if checked == 8:
+            break
+    assert checked == 8
+
+
+def test_deformation_gn_hessian():
+    """Symmetric, positive, the FD of the gradient at zero residual, and A +
+    (2/sigma^2) J^T J with J = dm(1)/dtheta from central differences (8^3, 384
+    parameters)."""
+    p = O.Params(n=(12, 10, 12), band=(4, 4, 6), nt=4, state="deformation")
+    I0, _, _ = synth.blob_pair(p.n, 1931, max_disp=2.0)
+    vt = synth.random_coefficients(p.band, 1932, bound=2.0)
+    I1 = O.DeformationPoint(vt, I0, I0, p).m1
+    pt = O.DeformationPoint(vt, I0, I1, p)
+    v = synth.random_direction(p.band, 1933)
+    w = synth.random_direction(p.band, 1934)
+    Hv, Hw = pt.gn_hessvec(v)[0], pt.gn_hessvec(w)[0]
+    a, b = O.inner(Hv, w), O.inner(v, Hw)
+    assert abs(a - b) <= 1e-10 * max(abs(a), abs(b))
+    assert O.inner(Hv, v) > 0.0
+    eps = 1e-6
+    checked = 0
+    for s in range(6):
+        dvt = synth.random_direction(p.band, 1940 + s)
+        if not _kink_free_def(vt, dvt, eps, p):
+            continue
+        gp = O.DeformationPoint(vt + eps * dvt, I0, I1, p).gradient()[0]
+        gm = O.DeformationPoint(vt - eps * dvt, I0, I1, p).gradient()[0]
+        assert rel(pt.gn_hessvec(dvt)[0], (gp - gm) / (2 * eps)) < 1e-6
+        checked += 1
+    assert checked >= 2
+
+    q = O.Params(n=(8, 8, 8), band=(4, 4, 4), nt=3, sigma=0.7, state="deformation")
+    J0, J1, _ = synth.blob_pair(q.n, 1951, max_disp=1.5)
+    # a point whose step and final displacements keep >= 1e-5 voxel from every
+    # cell boundary: a 1e-6 change of one coefficient moves them by less
+    for seed in range(1952, 2300):
+        vq = synth.random_coefficients(q.band, seed, bound=1.2)
+        dq = O.DeformationPoint(vq, J0, J1, q)
+        if (np.min(np.abs(dq.d - np.round(dq.d))) >= 1e-5 and
+                np.min(np.abs(dq.u[-1] - np.round(dq.u[-1]))) >= 1e-5):
+            break
+    else:
+        raise AssertionError("no kink-free point")
+    P = 2 * 3 * 64
+    J = np.zeros((int(np.prod(q.n)), P))
+    for j in range(P):
+        e = np.zeros(P)
+        e[j] = 1e-6
+        de = _from_theta(e, vq.shape)
+        J[:, j] = ((O.DeformationPoint(vq + de, J0, J1, q).m1 -
+                    O.DeformationPoint(vq - de, J0, J1, q).m1) / 2e-6).ravel()
+    A = O.regulariser_weights(q)
+    H = np.diag(np.concatenate([np.tile(A.ravel(), 3)] * 2)) + (2.0 / q.sigma**2) * J.T @ J
+    for s in range(3):
+        v = synth.random_direction(q.band, 2020 + s)
+        assert rel(_theta(dq.gn_hessvec(v)[0]), H @ _theta(v)) < 1e-7
+
+
+def test_deformation_newton_decreases_energy():
+    p = O.Params(n=(16, 16, 16), band=(4, 4, 4), nt=5, state="deformation")
+    I0, I1, _ = synth.blob_pair(p.n, 71, max_disp=2.0)
+    rep = O.newton(np.zeros((3,) + p.band, complex), I0, I1, p, max_newton=4, max_pcg=8,
+                   gtol=1e-6)
+    assert rep.iterations >= 3
+    assert all(b < a for a, b in zip(rep.energies, rep.energies[1:]))
+    assert rep.grad_inf_rel < 0.5
