@@ -483,7 +483,10 @@ def main_ours(args):
                 hessian="full: exact second derivative of the discrete energy, truncated PCG"),
             "nonstationary": dict(
                 measure_form(args.precision, dev, I0g, I1g, flush, stream, nonstationary=True),
-                velocity="one band-limited velocity per time step (10 x 3 x 32^3 coefficients)")}
+                velocity="one band-limited velocity per time step (10 x 3 x 32^3 coefficients)"),
+            "deformation_state": dict(
+                measure_form(args.precision, dev, I0g, I1g, flush, stream, state_equation=1),
+                state="deformation phi = id + u transported, I0 warped once (Gauss-Newton)")}
 
     # end to end through the C-ABI with pinned host buffers
     if not args.no_e2e:
@@ -694,7 +697,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
-                    help="skip the incompressible, full-Newton and non-stationary measurements")
+                    help="skip the measurements of the adjacent forms")
     ap.add_argument("--adjoint-traffic", type=float, default=None,
                     help="dram bytes per adjoint-step launch from an ncu capture of this kernel")
     ap.add_argument("--workload", choices=["phantom128", "uneven64"], default="phantom128",

@@ -4,9 +4,10 @@
  *
  * Method: Hernandez, "Newton-Krylov optimization in PDE-constrained
  * diffeomorphic registration parameterized in the space of band-limited vector
- * fields" (arXiv 1807.05117), state-equation variant, stationary or
- * non-stationary velocity, Gauss-Newton or full Newton Hessian; compressible
- * or incompressible velocities.
+ * fields" (arXiv 1807.05117): the state-equation variant (stationary or
+ * non-stationary velocity, Gauss-Newton or full Newton Hessian) and the
+ * deformation-state-equation variant (Gauss-Newton); compressible or
+ * incompressible velocities.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -68,6 +69,11 @@ extern "C" {
 #define BLR_NEWTON       1 /* the full Hessian of the discrete energy (Eqs. 44-46, */
                            /* no drops); may be indefinite away from a minimum  */
 
+/* State equation of the constraint (Section 2.2 or 2.3). */
+#define BLR_STATE_IMAGE       0 /* d_t m + grad m . v = 0, m(0) = I0 (Eq. 5)     */
+#define BLR_STATE_DEFORMATION 1 /* d_t phi + D phi . v = 0, phi(0) = id, and    */
+                                /* m(1) = I0 o phi(1) (Eqs. 16-18)             */
+
 /* Precision of the truncated-DFT contractions (the transport is always FP32). */
 #define BLR_FP32   0       /* FP32 FMA contractions                         */
 #define BLR_MIXED  1       /* BF16 hi+lo split operands on tensor cores,     */
@@ -114,6 +120,16 @@ typedef struct blr_params {
                      /* grad m^n(x + d^n).  blr_adjoint then writes nt * 3V */
                      /* floats (b^n per step).  Gauss-Newton only; batches  */
                      /* reject it.                                          */
+    int state_equation; /* BLR_STATE_IMAGE, or BLR_STATE_DEFORMATION: the    */
+                     /* deformation u = phi - id is transported on the same  */
+                     /* step, u^{n+1} = S u^n + d, and I0 is warped once,    */
+                     /* m(1) = T[I0](x + u^nt) (trilinear, any displacement, */
+                     /* periodic).  The adjoint is the vector rho, from       */
+                     /* rho^nt = lambda(1) grad T[I0](x + u^nt); the body     */
+                     /* force is dt sum_n (rho^{n+1} + sum_c rho_c^{n+1}      */
+                     /* grad u^n_c(x + d)).  Stationary velocity, Gauss-Newton, */
+                     /* no checkpoints; blr_adjoint takes no lambda0; batches */
+                     /* reject it.  Keeps 3 (nt + 1) V floats of u^n.        */
 } blr_params;
 
 /* Result of blr_newton (host struct filled by the library). */
@@ -173,8 +189,9 @@ int blr_state(blr_plan_t plan, const float *vt, float *m1, double *energy,
  * discrete lambda grad m of Eq. 38.  Needs a prior blr_state (BLR_ESTATE).
  * Repeatable: the plan keeps lambda^nt of the current point apart from the
  * buffers that blr_hessvec uses.
- * b      : device, 3*V floats, written.
- * lambda0: device, V floats, receives lambda^0; may be NULL. */
+ * b      : device, 3*V floats, written (non-stationary plans: nt * 3V, b^n).
+ * lambda0: device, V floats, receives lambda^0; may be NULL (must be NULL for
+ *          the deformation state equation, whose adjoint is a vector). */
 int blr_adjoint(blr_plan_t plan, float *b, float *lambda0, blr_stream_t stream);
 
 /* Reduced gradient (Section 3.2, Eq. 38): g~ = A v~ + pi(b), i.e. blr_state +
@@ -252,8 +269,9 @@ int blr_newton(blr_plan_t plan, float *vt, int max_newton, int max_pcg,
 typedef struct blr_batch *blr_batch_t;
 
 /* params: host array of npairs descriptions.  BLR_EINVAL if they differ in nt,
- * request BLR_MIXED, checkpoints, the incompressible form, the full Hessian or
- * non-stationary velocities, or one is invalid. */
+ * request BLR_MIXED, checkpoints, the incompressible form, the full Hessian,
+ * non-stationary velocities or the deformation state equation, or one is
+ * invalid. */
 int blr_batch_create(const blr_params *params, int npairs, blr_batch_t *out);
 int blr_batch_destroy(blr_batch_t batch);
 

@@ -32,6 +32,8 @@ BLR_FP32 = 0
 BLR_MIXED = 1
 BLR_GAUSS_NEWTON = 0
 BLR_NEWTON = 1
+BLR_STATE_IMAGE = 0
+BLR_STATE_DEFORMATION = 1
 
 
 class blr_params(ctypes.Structure):
@@ -39,7 +41,8 @@ class blr_params(ctypes.Structure):
                 ("alpha", ctypes.c_double), ("gamma", ctypes.c_double), ("s", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("precision", ctypes.c_int),
                 ("ckpt_every", ctypes.c_int), ("incompressible", ctypes.c_int),
-                ("hessian", ctypes.c_int), ("nonstationary", ctypes.c_int)]
+                ("hessian", ctypes.c_int), ("nonstationary", ctypes.c_int),
+                ("state_equation", ctypes.c_int)]
 
 
 class blr_report(ctypes.Structure):
@@ -148,7 +151,7 @@ def _ptr(t, *, device_only=True, dtype=None, numel=None, optional=False, name="t
 
 def make_params(n, band, nt=10, alpha=3.0, gamma=1.0, s=2, sigma=1.0, precision=BLR_FP32,
                 ckpt_every=0, incompressible=False, hessian=BLR_GAUSS_NEWTON,
-                nonstationary=False):
+                nonstationary=False, state_equation=BLR_STATE_IMAGE):
     p = blr_params()
     p.n[:] = [int(v) for v in n]
     p.band[:] = [int(v) for v in band]
@@ -159,6 +162,7 @@ def make_params(n, band, nt=10, alpha=3.0, gamma=1.0, s=2, sigma=1.0, precision=
     p.incompressible = 1 if incompressible else 0
     p.hessian = int(hessian)
     p.nonstationary = 1 if nonstationary else 0
+    p.state_equation = int(state_equation)
     return p
 
 
@@ -286,9 +290,10 @@ class Plan:
 
     def __init__(self, n, band, nt=10, alpha=3.0, gamma=1.0, s=2, sigma=1.0,
                  precision=BLR_FP32, ckpt_every=0, incompressible=False,
-                 hessian=BLR_GAUSS_NEWTON, nonstationary=False):
+                 hessian=BLR_GAUSS_NEWTON, nonstationary=False,
+                 state_equation=BLR_STATE_IMAGE):
         self.params = make_params(n, band, nt, alpha, gamma, s, sigma, precision, ckpt_every,
-                                  incompressible, hessian, nonstationary)
+                                  incompressible, hessian, nonstationary, state_equation)
         self.n = tuple(int(v) for v in n)
         self.band = tuple(int(v) for v in band)
         self.nt = int(nt)

@@ -29,6 +29,13 @@ int validate(const blr_params *p) {
     if (p->nonstationary != 0 && p->nonstationary != 1) return BLR_EINVAL;
     // the full Hessian is built for stationary velocities
     if (p->nonstationary && p->hessian == BLR_NEWTON) return BLR_EINVAL;
+    if (p->state_equation != BLR_STATE_IMAGE && p->state_equation != BLR_STATE_DEFORMATION)
+        return BLR_EINVAL;
+    // the deformation variant: stationary velocity, Gauss-Newton, every state kept
+    if (p->state_equation == BLR_STATE_DEFORMATION &&
+        (p->nonstationary || p->hessian != BLR_GAUSS_NEWTON ||
+         (p->ckpt_every > 0 && p->ckpt_every < p->nt)))
+        return BLR_EINVAL;
     // the full Hessian keeps every adjoint and incremental state: no checkpoints
     if (p->hessian == BLR_NEWTON && p->ckpt_every > 0 && p->ckpt_every < p->nt) return BLR_EINVAL;
     if (p->precision != BLR_FP32 && p->precision != BLR_MIXED) return BLR_EINVAL;
@@ -73,6 +80,17 @@ size_t layout(blr_plan *P, char *base) {
         P->lam_all = P->dm_all = P->nt_kap = nullptr;
         P->nt_lob = nullptr;
         P->lam_nt = a.take<float>(V);
+    }
+    if (P->p.state_equation == BLR_STATE_DEFORMATION) {
+        P->U = a.take<float>((size_t)3 * (P->p.nt + 1) * V);
+        P->rho_nt = a.take<float>(3 * V);
+        P->rho[0] = a.take<float>(3 * V);
+        P->rho[1] = a.take<float>(3 * V);
+        P->du[0] = a.take<float>(3 * V);
+        P->du[1] = a.take<float>(3 * V);
+        P->Gw = a.take<float>(3 * V);
+    } else {
+        P->U = P->rho_nt = P->rho[0] = P->rho[1] = P->du[0] = P->du[1] = P->Gw = nullptr;
     }
     P->Gm = P->use_gm ? a.take<float>((size_t)3 * P->p.nt * V) : nullptr;
     P->b = a.take<float>(3 * V);
@@ -148,8 +166,13 @@ int state_at(blr_plan *P, const float *vt, double *energy_out, cudaStream_t s) {
         use_step(P, n);
         if ((rc = dft_expand(P, P->vt + (size_t)n * P->nf1, P->d, 1, s))) return rc;
     }
-    if ((rc = sweep_state(P, s))) return rc;
-    if ((rc = energy_finalize(P, P->vt, energy_out, (int)sweep_blocks(P), s))) return rc;
+    if (P->p.state_equation == BLR_STATE_DEFORMATION) {
+        if ((rc = sweep_state_def(P, s))) return rc;
+        if ((rc = energy_finalize(P, P->vt, energy_out, def_final_blocks(P), s))) return rc;
+    } else {
+        if ((rc = sweep_state(P, s))) return rc;
+        if ((rc = energy_finalize(P, P->vt, energy_out, (int)sweep_blocks(P), s))) return rc;
+    }
     P->have_state = true;
     return BLR_OK;
 }
@@ -160,6 +183,9 @@ int gradient_here(blr_plan *P, float *g, cudaStream_t s) {
     int rc;
     if (P->nvel > 1) {
         if ((rc = sweep_adjoint_steps(P, P->lam_nt, g, P->vt, nullptr, nullptr, s))) return rc;
+    } else if (P->p.state_equation == BLR_STATE_DEFORMATION) {
+        if ((rc = sweep_adjoint_def(P, P->rho_nt, P->b, s))) return rc;
+        if ((rc = dft_project(P, P->b, g, P->vt, s))) return rc;
     } else {
         if ((rc = sweep_adjoint(P, P->b, nullptr, P->lam_nt, s))) return rc;
         if ((rc = dft_project(P, P->b, g, P->vt, s))) return rc;
@@ -177,6 +203,13 @@ int hessvec_here(blr_plan *P, const float *dvt, float *hdv, cudaStream_t s) {
     if (P->p.incompressible) {
         if ((rc = vec_leray(P, P->vproj, dvt, s))) return rc;
         dvt = P->vproj;
+    }
+    if (P->p.state_equation == BLR_STATE_DEFORMATION) {
+        if ((rc = dft_expand(P, dvt, P->dv, 0, s))) return rc;
+        if ((rc = sweep_incremental_def(P, s))) return rc;
+        if ((rc = sweep_adjoint_def(P, P->rho[0], P->b, s))) return rc;
+        if ((rc = dft_project(P, P->b, hdv, dvt, s))) return rc;
+        return P->p.incompressible ? vec_leray(P, hdv, hdv, s) : BLR_OK;
     }
     if (P->nvel > 1) {   // non-stationary: each step expands its own direction
         if ((rc = sweep_incremental(P, s, dvt))) return rc;
@@ -307,7 +340,8 @@ int plan_create(const blr_params *p, bool grad_cache, blr_plan **out) {
         delete P;
         return BLR_EINVAL;
     }
-    P->use_gm = grad_cache && P->sweep_wide && P->ck == p->nt;
+    P->use_gm = grad_cache && P->sweep_wide && P->ck == p->nt &&
+                p->state_equation == BLR_STATE_IMAGE;
     long long nsweep = sweep_blocks(P);
     long long nred = reduce_partials_needed();
     P->npart = (int)(nsweep > nred ? nsweep : nred);
@@ -401,6 +435,8 @@ int blr_state(blr_plan_t P, const float *vt, float *m1, double *energy, blr_stre
 int blr_adjoint(blr_plan_t P, float *b, float *lambda0, blr_stream_t stream) {
     if (check_plan(P) || !b) return BLR_EINVAL;
     if (!P->have_state) return BLR_ESTATE;
+    if (P->p.state_equation == BLR_STATE_DEFORMATION)   // rho is a vector: no lambda^0
+        return lambda0 ? BLR_EINVAL : sweep_adjoint_def(P, P->rho_nt, b, (cudaStream_t)stream);
     if (P->nvel > 1)   // one body force per step: b holds nt * 3V floats
         return sweep_adjoint_steps(P, P->lam_nt, nullptr, nullptr, b, lambda0, (cudaStream_t)stream);
     return sweep_adjoint(P, b, lambda0, P->lam_nt, (cudaStream_t)stream);

@@ -348,7 +348,8 @@ int blr_batch_create(const blr_params *params, int npairs, blr_batch_t *out) {
     for (int p = 0; p < npairs; ++p)
         if (params[p].nt != params[0].nt || params[p].ckpt_every != 0 ||
             params[p].precision != BLR_FP32 || params[p].incompressible != 0 ||
-            params[p].hessian != BLR_GAUSS_NEWTON || params[p].nonstationary != 0)
+            params[p].hessian != BLR_GAUSS_NEWTON || params[p].nonstationary != 0 ||
+            params[p].state_equation != BLR_STATE_IMAGE)
             return BLR_EINVAL;
     Batch *B = new (std::nothrow) Batch();
     if (!B) return BLR_ENOMEM;

@@ -125,6 +125,12 @@ struct blr_plan {
                         // last slot is lam_nt), else nullptr
     float *dm_all;      // full Newton Hessian: [nt-1][V], slot k-1 = dm^k of the last
                         // incremental state (k = 1..nt-1), else nullptr
+    // deformation state equation (else nullptr)
+    float *U;           // [nt+1][3][V] u^n = phi^n - id (u^0 = 0)
+    float *rho_nt;      // 3V rho^nt of the current point
+    float *rho[2];      // 3V each: adjoint / incremental adjoint ping-pong
+    float *du[2];       // 3V each: incremental deformation ping-pong
+    float *Gw;          // 3V grad T[I0](x + u^nt)
     float *nt_kap;      // full Newton Hessian: [8][V] corner weights of the variation of
                         // S^T for the current direction (newton.cu), else nullptr
     uint8_t *nt_lob;    // full Newton Hessian: [V] cell-start bits, else nullptr
@@ -167,6 +173,10 @@ __host__ __device__ inline long long ceil_div_ll(long long a, long long b) { ret
 
 // Storage of m^n.  Slots: checkpoints C_j = m^{j k} (j < nseg), then the k-1
 // interior states of one segment, then m^nt.  With k = nt this is m^n in slot n.
+inline float *def_u(const blr_plan *P, int n, int c) {   // u^n_c (deformation variant)
+    return P->U + ((size_t)3 * n + c) * P->V;
+}
+
 inline float *state_slot(const blr_plan *P, int n) {
     const int k = P->ck;
     long long slot;
@@ -246,6 +256,20 @@ int newton_terms(blr_plan *P, bool transpose_term, const float *lam1, const floa
                  const float *dmn, float *dlam, float *b, cudaStream_t s);
 // newton.cu: the step-invariant weights of those terms for the direction in P->dv.
 int newton_prep(blr_plan *P, cudaStream_t s);
+
+// deform.cu: y = a + alpha x over n floats; the final warp (mode 0: m(1) into the
+// last state slot, Gw, rho^nt = lambda(1) Gw and the energy partials; mode 1:
+// drho^nt from du^nt) and its fixed block count.
+int field_axpy(blr_plan *P, float *y, const float *a, const float *x, float alpha, long long n,
+               cudaStream_t s);
+int def_final(blr_plan *P, int mode, const float *u, const float *du, float *rho, cudaStream_t s);
+int def_final_blocks(const blr_plan *P);
+// sweeps.cu: the deformation variant's forward solve (u^1..u^nt, m(1), rho^nt,
+// energy partials), incremental state (du^nt and drho^nt into rho[0]) and adjoint
+// (body force b from rho_final).
+int sweep_state_def(blr_plan *P, cudaStream_t s);
+int sweep_incremental_def(blr_plan *P, cudaStream_t s);
+int sweep_adjoint_def(blr_plan *P, const float *rho_final, float *b, cudaStream_t s);
 
 // reduce.cu
 int energy_finalize(blr_plan *P, const float *vt, double *energy_out, int nblocks, cudaStream_t s);

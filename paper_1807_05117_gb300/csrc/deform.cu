@@ -1,0 +1,155 @@
+// Kernels of the deformation-state-equation variant (Section 2.3, Eqs. 16-18,
+// with the band-limited velocity of Section 3.3).  The deformation phi = id + u
+// is transported on the semi-Lagrangian step of the image variant,
+//   u^0 = 0,  u^{n+1}_c = S u^n_c + d_c,
+// by the scalar sweep kernels (one launch per component) and k_field_axpy for
+// the + d; the template is warped once at the end, m(1) = T[I0](x + u^nt), by
+// k_def_final, which also starts the vector adjoint,
+//   rho^nt = lambda(1) grad T[I0](x + u^nt),  lambda(1) = -(2/sigma^2)(m(1) - I1),
+// and in the Gauss-Newton product its increment drho^nt = dlambda(1) grad T[I0]
+// with dlambda(1) = -(2/sigma^2) grad T[I0] . du^nt.  The host orchestration
+// (sweep_state_def and the other two) is in sweeps.cu.
+#include "blr_internal.cuh"
+
+namespace {
+
+constexpr int DT = 256;
+
+__device__ __forceinline__ int wrapn(int s, int N) {
+    const int r = s % N;
+    return r < 0 ? r + N : r;
+}
+
+// y = a + alpha x over n floats.
+__global__ void __launch_bounds__(DT)
+k_field_axpy(float *__restrict__ y, const float *__restrict__ a, const float *__restrict__ x,
+             float alpha, long long n) {
+    pdl_wait();
+    for (long long i = blockIdx.x * (long long)DT + threadIdx.x; i < n; i += (long long)gridDim.x * DT)
+        y[i] = fmaf(alpha, x[i], a[i]);
+}
+
+// Trilinear value and gradient of f at x + u (any displacement; the cell on axis
+// a starts at x_a + floor(u_a); periodic wrap).
+__device__ __forceinline__ void warp_point(const float *__restrict__ f, int i, int j, int k,
+                                           float u0, float u1, float u2, const Grid3 &g,
+                                           float *val, float grad[3]) {
+    const float l0 = floorf(u0), l1 = floorf(u1), l2 = floorf(u2);
+    const float f0 = u0 - l0, f1 = u1 - l1, f2 = u2 - l2;
+    const long long plane = (long long)g.N2 * g.N3;
+    const long long p[2] = {(long long)wrapn(i + (int)l0, g.N1) * plane,
+                            (long long)wrapn(i + (int)l0 + 1, g.N1) * plane};
+    const long long r[2] = {(long long)wrapn(j + (int)l1, g.N2) * g.N3,
+                            (long long)wrapn(j + (int)l1 + 1, g.N2) * g.N3};
+    const int q[2] = {wrapn(k + (int)l2, g.N3), wrapn(k + (int)l2 + 1, g.N3)};
+    float c[2][2][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) c[a][b][e] = __ldg(f + p[a] + r[b] + q[e]);
+    const float w0[2] = {1.f - f0, f0}, w1[2] = {1.f - f1, f1}, w2[2] = {1.f - f2, f2};
+    float v = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const float lin = fmaf(w2[0], c[a][b][0], w2[1] * c[a][b][1]);   // along x3
+            v = fmaf(w0[a] * w1[b], lin, v);
+            g2 = fmaf(w0[a] * w1[b], c[a][b][1] - c[a][b][0], g2);
+            g0 = fmaf(a ? w1[b] : -w1[b], lin, g0);
+            g1 = fmaf(b ? w0[a] : -w0[a], lin, g1);
+        }
+    *val = v;
+    grad[0] = g0;
+    grad[1] = g1;
+    grad[2] = g2;
+}
+
+// MODE 0: m1 = T[I0](x + u), Gw = grad T[I0](x + u), rho = lam_scale (m1 - I1) Gw,
+//         one FP64 partial sum of (m1 - I1)^2 per block (fixed grid: deterministic).
+// MODE 1: drho = lam_scale (Gw . du) Gw from the kept Gw.
+template <int MODE>
+__global__ void __launch_bounds__(DT)
+k_def_final(const float *__restrict__ I0, const float *__restrict__ I1,
+            const float *__restrict__ u, const float *__restrict__ du, float *__restrict__ m1,
+            float *__restrict__ Gw, float *__restrict__ rho, float lam_scale,
+            double *__restrict__ partials, Grid3 g) {
+    pdl_wait();
+    __shared__ double red[DT / 32];
+    const long long V = g.V;
+    const long long plane = (long long)g.N2 * g.N3;
+    double acc = 0.0;
+    for (long long x = blockIdx.x * (long long)DT + threadIdx.x; x < V; x += (long long)gridDim.x * DT) {
+        if constexpr (MODE == 0) {
+            const int i = (int)(x / plane);
+            const long long rem = x - (long long)i * plane;
+            const int j = (int)(rem / g.N3), k = (int)(rem - (long long)j * g.N3);
+            float v, gr[3];
+            warp_point(I0, i, j, k, __ldg(u + x), __ldg(u + V + x), __ldg(u + 2 * V + x), g, &v, gr);
+            const float res = v - __ldg(I1 + x);
+            const float lam = lam_scale * res;
+            m1[x] = v;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                Gw[a * V + x] = gr[a];
+                rho[a * V + x] = lam * gr[a];
+            }
+            acc += (double)res * (double)res;
+        } else {
+            const float g0 = __ldg(Gw + x), g1 = __ldg(Gw + V + x), g2 = __ldg(Gw + 2 * V + x);
+            const float dm = fmaf(g0, __ldg(du + x), fmaf(g1, __ldg(du + V + x), g2 * __ldg(du + 2 * V + x)));
+            const float dl = lam_scale * dm;
+            rho[x] = dl * g0;
+            rho[V + x] = dl * g1;
+            rho[2 * V + x] = dl * g2;
+        }
+    }
+    if constexpr (MODE == 0) {
+        // fixed-order block tree
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < DT / 32; ++w) t += red[w];
+            partials[blockIdx.x] = t;
+        }
+    }
+}
+
+int field_blocks(const blr_plan *P, long long n) {
+    long long b = ceil_div_ll(n, DT);
+    const long long cap = (long long)P->sms * 8;
+    return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
+}
+
+}  // namespace
+
+int field_axpy(blr_plan *P, float *y, const float *a, const float *x, float alpha, long long n,
+               cudaStream_t s) {
+    launch_pdl(k_field_axpy, dim3(field_blocks(P, n)), dim3(DT), 0, s, y, a, x, alpha, n);
+    BLR_CK_LAUNCH();
+    return BLR_OK;
+}
+
+int def_final_blocks(const blr_plan *P) {
+    long long b = ceil_div_ll(P->V, DT);
+    return (int)(b < P->npart ? b : P->npart);
+}
+
+int def_final(blr_plan *P, int mode, const float *u, const float *du, float *rho, cudaStream_t s) {
+    const float lam_scale = (float)(-2.0 / (P->p.sigma * P->p.sigma));
+    const int blocks = def_final_blocks(P);
+    if (mode == 0)
+        launch_pdl(k_def_final<0>, dim3(blocks), dim3(DT), 0, s, (const float *)P->I0,
+                   (const float *)P->I1, u, (const float *)nullptr, state_slot(P, P->p.nt), P->Gw,
+                   rho, lam_scale, P->partials, P->grid);
+    else
+        launch_pdl(k_def_final<1>, dim3(blocks), dim3(DT), 0, s, (const float *)P->I0,
+                   (const float *)P->I1, (const float *)nullptr, du, (float *)nullptr, P->Gw, rho,
+                   lam_scale, (double *)nullptr, P->grid);
+    BLR_CK_LAUNCH();
+    return BLR_OK;
+}

@@ -1419,6 +1419,63 @@ int sweep_incremental(blr_plan *P, cudaStream_t s, const float *dvt_steps) {
 }
 
 // ---------------------------------------------------------------------------
+// Deformation state equation: the scalar step kernels applied to each component
+// of u = phi - id (no kept gradients: every launch reads its own u^n_c).
+
+int sweep_state_def(blr_plan *P, cudaStream_t s) {
+    const int nt = P->p.nt;
+    const long long V3 = 3 * P->V;
+    for (int n = 0; n < nt; ++n) {
+        for (int c = 0; c < 3; ++c) {   // S u^n_c
+            launch_state<false>(P, def_u(P, n, c), def_u(P, n + 1, c), nullptr, nullptr, 0.f,
+                                nullptr, nullptr, s);
+            BLR_CK_LAUNCH();
+        }
+        int rc = field_axpy(P, def_u(P, n + 1, 0), def_u(P, n + 1, 0), P->d, 1.f, V3, s);   // + d
+        if (rc) return rc;
+    }
+    return def_final(P, 0, def_u(P, nt, 0), nullptr, P->rho_nt, s);
+}
+
+// du^{n+1}_c = S du^n_c - dt grad u^n_c(x + d) . dv - dt dv_c; drho^nt into rho[0].
+int sweep_incremental_def(blr_plan *P, cudaStream_t s) {
+    const int nt = P->p.nt;
+    const long long V3 = 3 * P->V;
+    int cur = 0;
+    for (int n = 0; n < nt; ++n) {
+        for (int c = 0; c < 3; ++c) {
+            launch_incstate(P, n == 0, false, P->du[cur] + c * P->V, def_u(P, n, c),
+                            P->du[1 - cur] + c * P->V, 1.f, nullptr, s);
+            BLR_CK_LAUNCH();
+        }
+        int rc = field_axpy(P, P->du[1 - cur], P->du[1 - cur], P->dv, -P->dt, V3, s);
+        if (rc) return rc;
+        cur = 1 - cur;
+    }
+    return def_final(P, 1, nullptr, P->du[cur], P->rho[0], s);
+}
+
+// rho^n_c = S^T rho^{n+1}_c; b = dt sum_n (sum_c rho^{n+1}_c grad u^n_c(x + d) + rho^{n+1}).
+int sweep_adjoint_def(blr_plan *P, const float *rho_final, float *b, cudaStream_t s) {
+    const int nt = P->p.nt;
+    const long long V3 = 3 * P->V;
+    int cur = 0;
+    for (int n = nt - 1; n >= 0; --n) {
+        const float *rin = (n == nt - 1) ? rho_final : P->rho[cur];
+        float *rout = P->rho[1 - cur];
+        for (int c = 0; c < 3; ++c) {
+            launch_adjoint(P, n == nt - 1 && c == 0, n > 0, rin + c * P->V, def_u(P, n, c),
+                           n > 0 ? rout + c * P->V : nullptr, b, nullptr, s);
+            BLR_CK_LAUNCH();
+        }
+        int rc = field_axpy(P, b, b, rin, P->dt, V3, s);
+        if (rc) return rc;
+        cur = 1 - cur;
+    }
+    return BLR_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Batched launches and the tile-shape autotuner.
 
 int sweep_batch_launch(int kind, bool f1, bool f2, bool wide, const SweepPair *pairs,

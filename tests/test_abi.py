@@ -72,12 +72,21 @@ def test_strerror_and_invalid_params(lib):
     p = blr.make_params((16, 16, 16), (4, 4, 4))
     p.nonstationary = 2
     assert lib.blr_plan_create(ctypes.byref(p), ctypes.byref(h)) == blr.BLR_EINVAL
+    # the deformation state equation: stationary, Gauss-Newton, no checkpoints
+    for kw in (dict(nonstationary=True), dict(hessian=blr.BLR_NEWTON), dict(nt=4, ckpt_every=2)):
+        p = blr.make_params((16, 16, 16), (4, 4, 4),
+                            **{"state_equation": blr.BLR_STATE_DEFORMATION, **kw})
+        assert lib.blr_plan_create(ctypes.byref(p), ctypes.byref(h)) == blr.BLR_EINVAL
+    p = blr.make_params((16, 16, 16), (4, 4, 4))
+    p.state_equation = 2
+    assert lib.blr_plan_create(ctypes.byref(p), ctypes.byref(h)) == blr.BLR_EINVAL
     # the full Hessian keeps every state: no checkpoints
     p = blr.make_params((16, 16, 16), (4, 4, 4), nt=4, ckpt_every=2, hessian=blr.BLR_NEWTON)
     assert lib.blr_plan_create(ctypes.byref(p), ctypes.byref(h)) == blr.BLR_EINVAL
     # batches take neither the incompressible form, mixed precision nor the full Hessian
     for kw in (dict(incompressible=True), dict(precision=blr.BLR_MIXED),
-               dict(hessian=blr.BLR_NEWTON), dict(nonstationary=True)):
+               dict(hessian=blr.BLR_NEWTON), dict(nonstationary=True),
+               dict(state_equation=blr.BLR_STATE_DEFORMATION)):
         arr = (blr.blr_params * 2)(blr.make_params((16, 16, 16), (4, 4, 4), nt=4),
                                    blr.make_params((16, 16, 16), (4, 4, 4), nt=4, **kw))
         assert lib.blr_batch_create(arr, 2, ctypes.byref(h)) == blr.BLR_EINVAL
