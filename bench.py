@@ -74,6 +74,11 @@ ADJ_TRAFFIC = {"sweeps_device_sha256": "da203be71439a4a829777d7c74f291929c9c70d1
 
 
 def adjoint_traffic():
+    """The captured traffic while the sweep device code is that of the capture,
+    else None.  ncu's default cache control flushes the caches before the
+    launch, so the figure is the launch's cold-cache traffic; the L2 window the
+    autotuner may put over the displacement copy changes the live traffic, not
+    the kernel."""
     path = os.path.join(ROOT, "paper_1807_05117_gb300", "csrc", "sweeps.cu")
     with open(path, encoding="utf-8") as f:
         text = f.read()
@@ -363,7 +368,9 @@ def measure_precision(precision, args, dev, I0g, I1g, flush, stream, dist, world
                 "traffic": (args.adjoint_traffic if args.adjoint_traffic is not None
                             else adjoint_traffic()),
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
-                                  "interior launch at 128^3 (null once the kernel source changed)"}
+                                  "interior launch at 128^3, caches flushed by ncu (null once "
+                                  "the kernel source changed)",
+                "l2_persist_d4": plan.tuning()["l2_persist_d4"]}
     return dict(plan=plan, ms=ms, launches=launches, clocks=clocks, rep=rep, hvp_ms=hvp_ms,
                 roofline=roofline, dvt=dvt, stage=stage)
 
@@ -680,6 +687,7 @@ def probe(precision="fp32", hessian=0):
             plan.adjoint(bf)
         torch.cuda.synchronize()
         assert plan.status() == blr.BLR_OK
+        print("probe tuning", json.dumps(plan.tuning()))
     print("probe ok", float(np.abs(h.cpu().numpy()).max()))
     return 0
 

@@ -331,13 +331,14 @@ int blr_expand_noalloc(const int n[3], const int band[3], const float *vt, float
 unsigned long long blr_kernel_launches(void);
 
 /* Diagnostic (no counterpart in the paper): the sweep shapes the plan's
- * autotuner chose at creation.  vals: host, n ints; the first min(n, 9) are
+ * autotuner chose at creation.  vals: host, n ints; the first min(n, 10) are
  * written, in this order: wide-copy sweeps (0/1), state gradients kept (0/1),
  * adjoint blocks per SM, adjoint reads the kept gradient (0/1), incremental
  * state form (0 wide-copy, 1 wide-copy reading the kept gradient, 2 gather),
  * its blocks per SM, march-kernel blocks per SM (0: chunked grid), march x1
- * chunk, adjoint march x1 chunk.  Returns BLR_EINVAL for a NULL plan or
- * vals. */
+ * chunk, adjoint march x1 chunk, displacement copy kept in persisting L2
+ * lines (0/1; when 1, plan creation raised the context's persisting-L2
+ * set-aside to hold it).  Returns BLR_EINVAL for a NULL plan or vals. */
 int blr_plan_tuning(blr_plan_t plan, int *vals, int n);
 
 /* Human-readable text for a status code (static storage). */

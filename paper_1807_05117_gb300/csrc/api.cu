@@ -342,6 +342,33 @@ int plan_create(const blr_params *p, bool grad_cache, blr_plan **out) {
     }
     P->use_gm = grad_cache && P->sweep_wide && P->ck == p->nt &&
                 p->state_equation == BLR_STATE_IMAGE;
+    // L2 persistence for the displacement copy d4 (the autotuner decides whether the
+    // sweeps use it): the window covers one step's d4, and the context's
+    // persisting set-aside is raised to hold it when the device allows
+    P->l2_persist = 0;
+    P->l2_win_bytes = 0;
+    P->l2_hit = 0.f;
+    if (P->sweep_wide) {
+        int max_persist = 0, max_window = 0;
+        if (cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, P->device) ==
+                cudaSuccess &&
+            cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, P->device) ==
+                cudaSuccess &&
+            max_persist > 0 && max_window > 0) {
+            size_t win = (size_t)P->V * sizeof(float4);
+            if (win > (size_t)max_window) win = (size_t)max_window;
+            size_t aside = win < (size_t)max_persist ? win : (size_t)max_persist;
+            size_t cur = 0;
+            if (cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) == cudaSuccess &&
+                (cur >= aside || cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, aside) ==
+                                     cudaSuccess)) {
+                P->l2_win_bytes = win;
+                P->l2_hit = (float)((double)(cur > aside ? cur : aside) / (double)win);
+                if (P->l2_hit > 1.f) P->l2_hit = 1.f;
+            }
+        }
+        cudaGetLastError();
+    }
     long long nsweep = sweep_blocks(P);
     long long nred = reduce_partials_needed();
     P->npart = (int)(nsweep > nred ? nsweep : nred);
@@ -382,9 +409,10 @@ extern "C" {
 
 int blr_plan_tuning(blr_plan_t P, int *vals, int n) {
     if (!P || !vals) return BLR_EINVAL;
-    const int v[9] = {P->sweep_wide ? 1 : 0, P->Gm ? 1 : 0, P->bal_adj, P->adj_useg,
-                      P->inc_mode, P->bal_inc, P->bal_sweep, P->chunk, P->chunk_adj};
-    for (int i = 0; i < n && i < 9; ++i) vals[i] = v[i];
+    const int v[10] = {P->sweep_wide ? 1 : 0, P->Gm ? 1 : 0, P->bal_adj, P->adj_useg,
+                       P->inc_mode, P->bal_inc, P->bal_sweep, P->chunk, P->chunk_adj,
+                       P->l2_persist};
+    for (int i = 0; i < n && i < 10; ++i) vals[i] = v[i];
     return BLR_OK;
 }
 
@@ -393,6 +421,7 @@ int blr_plan_destroy(blr_plan_t P) {
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(P->device);
+    if (P->l2_persist) cudaCtxResetPersistingL2Cache();   // release this plan's lines
     cudaError_t e1 = cudaFree(arena_base(P));
     cudaError_t e2 = cudaFreeHost(P->hsc);
     if (cudaFreeHost(P->hlive) != cudaSuccess) e2 = cudaErrorInvalidValue;

@@ -49,6 +49,29 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
+// launch_pdl with an L2 access-policy window (win may be nullptr: plain launch_pdl).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl_l2(const cudaAccessPolicyWindow *win, void (*kernel)(KArgs...),
+                                 dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                 Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (win) {
+        attr[1].id = cudaLaunchAttributeAccessPolicyWindow;
+        attr[1].val.accessPolicyWindow = *win;
+        cfg.numAttrs = 2;
+    }
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Device-latched conditions (bit flags in blr_plan::dstatus).
 enum { BLR_FLAG_CFL = 1, BLR_FLAG_NAN = 2, BLR_FLAG_TIMEOUT = 4 };
 
@@ -98,6 +121,9 @@ struct blr_plan {
                         // blocks per SM, or 0 for the chunked grid
     int bal_adj;        // the same for the adjoint sweep (both chosen by sweep_autotune)
     int sms;            // multiprocessors of the plan's device
+    int l2_persist;     // the wide sweeps keep d4 in persisting L2 lines (sweep_autotune)
+    size_t l2_win_bytes;  // access-policy window over d4 (0: not available on this device)
+    float l2_hit;       // its hit ratio (set-aside / window)
     Grid3 grid;
 
     float *I0, *I1;

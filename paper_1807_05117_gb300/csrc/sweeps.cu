@@ -1199,17 +1199,33 @@ float *grad_slot(const blr_plan *P, int n) {
     return P->Gm ? P->Gm + (size_t)3 * n * P->V : nullptr;
 }
 
+// The displacement copy d4 is read by every step of the adjoint and incremental
+// sweeps.  When the autotuner finds it faster, those launches carry an
+// access-policy window that keeps d4 in persisting L2 lines between steps.
+const cudaAccessPolicyWindow *d4_window(const blr_plan *P, cudaAccessPolicyWindow *w) {
+    if (!P->l2_persist || !P->d4 || !P->l2_win_bytes) return nullptr;
+    w->base_ptr = (void *)P->d4;
+    w->num_bytes = P->l2_win_bytes;
+    w->hitRatio = P->l2_hit;
+    w->hitProp = cudaAccessPropertyPersisting;
+    w->missProp = cudaAccessPropertyStreaming;
+    return w;
+}
+
 template <bool FIRST, bool WRITE_LAM>
 void launch_adjoint_t(const blr_plan *P, const float *lin, const float *mn, float *lout, float *b,
                       const float *Gn, cudaStream_t s) {
     if (P->sweep_wide) {
         const BalGeom g = bal_geom(P, P->bal_adj ? P->bal_adj : ADJ_BLOCKS, AJ);
+        cudaAccessPolicyWindow w;
+        const cudaAccessPolicyWindow *win = d4_window(P, &w);
         if (Gn && P->adj_useg)
-            launch_pdl(k_adjoint_wide<FIRST, WRITE_LAM, true>, dim3(g.G), dim3(MT), ADJW_SMEM_G, s,
-                       lin, mn, P->d4, lout, b, P->dt, P->grid, g.ntk, g.W, Gn);
+            launch_pdl_l2(win, k_adjoint_wide<FIRST, WRITE_LAM, true>, dim3(g.G), dim3(MT),
+                          ADJW_SMEM_G, s, lin, mn, P->d4, lout, b, P->dt, P->grid, g.ntk, g.W, Gn);
         else
-            launch_pdl(k_adjoint_wide<FIRST, WRITE_LAM, false>, dim3(g.G), dim3(MT), ADJW_SMEM, s,
-                       lin, mn, P->d4, lout, b, P->dt, P->grid, g.ntk, g.W, (const float *)nullptr);
+            launch_pdl_l2(win, k_adjoint_wide<FIRST, WRITE_LAM, false>, dim3(g.G), dim3(MT),
+                          ADJW_SMEM, s, lin, mn, P->d4, lout, b, P->dt, P->grid, g.ntk, g.W,
+                          (const float *)nullptr);
     } else if (P->bal_adj) {
         const BalGeom g = bal_geom(P, P->bal_adj, AJ);
         k_adjoint_bal<FIRST, WRITE_LAM><<<g.G, MT, ADJ_SMEM, s>>>(lin, mn, P->d, lout, b, P->dt,
@@ -1232,20 +1248,23 @@ void launch_adjoint(const blr_plan *P, bool first, bool wlam, const float *lin, 
 template <bool FIRST, bool LAST>
 void launch_incstate_t(const blr_plan *P, const float *din, const float *mn, float *dout,
                        float lam_scale, const float *Gn, cudaStream_t s, bool wide) {
+    cudaAccessPolicyWindow w;
+    const cudaAccessPolicyWindow *win = d4_window(P, &w);
     if (wide && P->sweep_wide && Gn && P->inc_mode == 2) {
         const dim3 grid((unsigned)ceil_div_ll(P->N3, MK), (unsigned)ceil_div_ll(P->N2, MJ),
                         (unsigned)P->N1);
-        launch_pdl(k_incstate_gather<FIRST, LAST>, grid, dim3(MT), 0, s, din, P->d4, P->dv, Gn, dout,
-                   P->dt, lam_scale, P->grid);
+        launch_pdl_l2(win, k_incstate_gather<FIRST, LAST>, grid, dim3(MT), 0, s, din, P->d4, P->dv,
+                      Gn, dout, P->dt, lam_scale, P->grid);
     } else if (wide && P->sweep_wide) {
         const BalGeom b = bal_geom(P, P->bal_inc ? P->bal_inc : INC_BLOCKS, AJ);
         if (Gn && P->inc_mode == 1)
-            launch_pdl(k_incstate_wide<FIRST, LAST, true>, dim3(b.G), dim3(MT), incw_smem<FIRST, true>(),
-                       s, din, mn, P->d4, P->dv, dout, P->dt, lam_scale, P->grid, b.ntk, b.W, Gn);
+            launch_pdl_l2(win, k_incstate_wide<FIRST, LAST, true>, dim3(b.G), dim3(MT),
+                          incw_smem<FIRST, true>(), s, din, mn, P->d4, P->dv, dout, P->dt,
+                          lam_scale, P->grid, b.ntk, b.W, Gn);
         else
-            launch_pdl(k_incstate_wide<FIRST, LAST, false>, dim3(b.G), dim3(MT),
-                       incw_smem<FIRST, false>(), s, din, mn, P->d4, P->dv, dout, P->dt, lam_scale,
-                       P->grid, b.ntk, b.W, (const float *)nullptr);
+            launch_pdl_l2(win, k_incstate_wide<FIRST, LAST, false>, dim3(b.G), dim3(MT),
+                          incw_smem<FIRST, false>(), s, din, mn, P->d4, P->dv, dout, P->dt,
+                          lam_scale, P->grid, b.ntk, b.W, (const float *)nullptr);
     } else if (P->bal_sweep) {
         const BalGeom b = bal_geom(P, P->bal_sweep, MJ);
         k_incstate_bal<FIRST, LAST><<<b.G, MT, 0, s>>>(din, mn, P->d, P->dv, dout, P->dt, lam_scale,
@@ -1652,6 +1671,20 @@ int sweep_autotune(blr_plan *P, cudaStream_t s) {
             }
         P->inc_mode = best_m;
         P->bal_inc = best_b;
+    }
+    // d4 in persisting L2 lines, or not: one adjoint and one incremental-state
+    // step with the chosen shapes, timed both ways (lines released in between)
+    P->l2_persist = 0;
+    if (P->sweep_wide && P->l2_win_bytes && !rc) {
+        float t[2] = {0.f, 0.f};
+        for (int on = 0; on < 2 && !rc; ++on) {
+            P->l2_persist = on;
+            if (cudaCtxResetPersistingL2Cache() != cudaSuccess) rc = BLR_ECUDA;
+            if (!rc) t[on] = time_shape(1);
+            if (!rc) t[on] += time_shape(3);
+        }
+        P->l2_persist = (!rc && t[1] < t[0]) ? 1 : 0;
+        if (!P->l2_persist && cudaCtxResetPersistingL2Cache() != cudaSuccess) rc = BLR_ECUDA;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
