@@ -477,7 +477,8 @@ def main_ours(args):
                              for p, r in res.items()}}
     plan = head["plan"]
 
-    # the survey's adjacent forms, measured on the same pair and work
+    # the adjacent forms of the method (full Newton Hessian, deformation state
+    # equation, non-stationary and incompressible velocities), same pair and work
     if not args.no_forms:
         line["forms"] = {
             "incompressible_h1": dict(
