@@ -6,7 +6,9 @@ the library's adjoint kernel chain (``blr_gradient_at_state``: adjoint sweeps wi
 the body force, projection pi and the regulariser term of Eq. 38), so
 ``E.backward()`` leaves dE/dv~ in ``vt.grad``.  With a plan created with
 ``ckpt_every=k`` the forward keeps only every k-th state and the backward
-recomputes each segment from its checkpoint.
+recomputes each segment from its checkpoint.  Any plan form works (the
+incompressible, non-stationary and deformation-state variants): the backward
+is the plan's own gradient at its current point.
 
 Gradients of complex coefficients follow PyTorch's convention for a real loss:
 grad = dE/d(Re v~) + i dE/d(Im v~), which is exactly g~ of Eq. 38 under the inner
@@ -22,7 +24,9 @@ class RegistrationEnergy(torch.autograd.Function):
     @staticmethod
     def forward(ctx, vt, plan):
         if vt.dtype != torch.complex64 or not vt.is_cuda:
-            raise ValueError("vt must be a complex64 CUDA tensor of shape (3, B1, B2, B3)")
+            raise ValueError("vt must be a complex64 CUDA tensor of the plan's coefficient "
+                             "shape: (3, B1, B2, B3), or (nt, 3, B1, B2, B3) for a "
+                             "non-stationary plan")
         vt = vt.contiguous()
         energy = torch.empty(3, dtype=torch.float64, device=vt.device)
         plan.state(vt, energy=energy)
