@@ -928,3 +928,39 @@ def test_deformation_newton_decreases_energy():
     assert rep.iterations >= 3
     assert all(b < a for a, b in zip(rep.energies, rep.energies[1:]))
     assert rep.grad_inf_rel < 0.5
+
+
+def test_form_combinations_match_finite_differences():
+    """The forms compose: the incompressible H^1 form with non-stationary
+    velocities and with the deformation state equation, each gradient against
+    central differences of its own energy (4 directions)."""
+    cases = [
+        O.Params(n=(12, 10, 12), band=(4, 4, 6), nt=3, s=0.5, incompressible=True,
+                 stationary=False),
+        O.Params(n=(12, 10, 12), band=(4, 4, 6), nt=4, s=0.5, incompressible=True,
+                 state="deformation"),
+    ]
+    for k, p in enumerate(cases):
+        I0, I1, _ = synth.blob_pair(p.n, 2101 + k, max_disp=2.0)
+        shape = ((p.nt,) if not p.stationary else ()) + (3,) + p.band
+        rng = np.random.default_rng(2110 + k)
+        vt = (rng.normal(size=shape) + 1j * rng.normal(size=shape)) * 0.3
+        g = O.make_point(vt, I0, I1, p).gradient()[0]
+        eps = 1e-6
+        checked = 0
+        for s in range(12):
+            dvt = rng.normal(size=shape) + 1j * rng.normal(size=shape)
+            a = O.make_point(vt - eps * dvt, I0, I1, p)
+            b = O.make_point(vt + eps * dvt, I0, I1, p)
+            cells = [(np.floor(a.d), np.floor(b.d))]
+            if p.state == "deformation":
+                cells.append((np.floor(a.u[-1]), np.floor(b.u[-1])))
+            if not all(np.array_equal(x, y) for x, y in cells):
+                continue
+            fd = (b.energy - a.energy) / (2 * eps)
+            dd = O.inner(g, dvt)
+            assert abs(fd - dd) <= 1e-6 * abs(dd), (k, s, fd, dd)
+            checked += 1
+            if checked == 4:
+                break
+        assert checked == 4, k
