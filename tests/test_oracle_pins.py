@@ -964,3 +964,34 @@ def test_form_combinations_match_finite_differences():
             if checked == 4:
                 break
         assert checked == 4, k
+
+
+def test_nonstationary_gn_hessian_equals_dense_jacobian_bruteforce():
+    """8^3 grid, band 4^3, two steps (768 real parameters): H = dt A (per step) +
+    (2/sigma^2) J^T J with J = dm^nt/dtheta from central differences of the
+    state, against the per-step incremental state / adjoint chain."""
+    p = O.Params(n=(8, 8, 8), band=(4, 4, 4), nt=2, sigma=0.7, stationary=False)
+    I0, I1, _ = synth.blob_pair(p.n, 2201, max_disp=1.5)
+    for seed in range(2202, 2400):
+        vt = np.stack([synth.random_coefficients(p.band, seed + 500 * n, bound=1.2)
+                       for n in range(p.nt)])
+        d = O.per_step(lambda v: O.displacement(v, p), vt, p)
+        if np.min(np.abs(d - np.round(d))) >= 1e-5:
+            break
+    else:
+        raise AssertionError("no kink-free point")
+    pt = O.Point(vt, I0, I1, p)
+    P = 2 * p.nt * 3 * 64
+    J = np.zeros((int(np.prod(p.n)), P))
+    for j in range(P):
+        e = np.zeros(P)
+        e[j] = 1e-6
+        de = _from_theta(e, vt.shape)
+        J[:, j] = ((O.Point(vt + de, I0, I1, p).m[-1] - O.Point(vt - de, I0, I1, p).m[-1])
+                   / 2e-6).ravel()
+    A = O.regulariser_weights(p)
+    Ad = np.concatenate([np.tile(p.dt * A.ravel(), 3 * p.nt)] * 2)
+    H = np.diag(Ad) + (2.0 / p.sigma**2) * J.T @ J
+    for s in range(3):
+        v = np.stack([synth.random_direction(p.band, 2450 + 10 * s + n) for n in range(p.nt)])
+        assert rel(_theta(pt.gn_hessvec(v)[0]), H @ _theta(v)) < 1e-7
