@@ -35,7 +35,8 @@ fields", arXiv 1807.05117):
   u^0 = 0, u^{n+1} = S u^n + d, and the template is warped once,
   m(1) = T[I0](x + u^nt); the adjoint rho (a vector field) starts from
   rho^nt = lambda(1) grad T[I0](x + u^nt) and runs backwards with S^T; the body
-  force is dt sum_n (rho^{n+1} + D u^n^T rho^{n+1}) (Gauss-Newton Hessian only);
+  force is dt sum_n (rho^{n+1} + D u^n^T rho^{n+1}); Gauss-Newton and full
+  Newton Hessians;
 * the incompressible form (Eq. 4 with gamma = 1, imposed in the band as in
   Section 3.2): the velocity is restricted to divergence-free band fields by the
   Fourier-diagonal Leray projector P(k) = I - kappa kappa^T / |kappa|^2,
@@ -477,7 +478,7 @@ class DeformationPoint:
       u^0 = 0, u^{n+1} = S u^n + d            (phi^{n+1}(x) = phi^n(x + d(x)))
       m(1) = T[I0](x + u^nt)                  (trilinear, any displacement, periodic)
       E = 1/2 <A v~, v~> + sigma^-2 ||m(1) - I1||^2.
-    Stationary velocity, Gauss-Newton Hessian."""
+    Stationary velocity; Gauss-Newton and full Newton Hessians."""
 
     def __init__(self, vt: np.ndarray, I0: np.ndarray, I1: np.ndarray, p: Params):
         if not p.stationary:
@@ -556,6 +557,50 @@ class DeformationPoint:
         h = self.A[None] * dvt + project(db, self.p.band)
         if self.p.incompressible:
             h = leray(h, self.p.n)
+        return h, dm1
+
+
+    def full_hessvec(self, dvt: np.ndarray):
+        """Exact Hessian of the discrete energy of this variant (Eqs. 19-21 of
+        Section 2.3 without the drops of Section 3.4), with dd = -dt iota(dv~):
+          du as in incremental_state;
+          drho^nt = dlambda(1) Gw + lambda(1) Hess T[I0](x + u^nt) du^nt,
+          drho^n_c = S^T drho^{n+1}_c + sum_a D_a^T (dd_a rho^{n+1}_c),
+          db_a = dt sum_n (drho_a^{n+1} + sum_c [drho_c^{n+1} D_a u_c^n
+                 + rho_c^{n+1} (D_a du_c^n + (Hess T[u_c^n] dd)_a)]).
+        Incompressible: P H P.  Returns (H dv~, dm(1))."""
+        p, st = self.p, self.stencil
+        dvt = np.asarray(dvt, dtype=np.complex128)
+        if p.incompressible:
+            dvt = leray(dvt, p.n)
+        dd = -p.dt * expand(dvt, p.n)
+        dus = [np.zeros((3,) + tuple(p.n))]
+        for n in range(p.nt):
+            Sdu = np.stack([st.apply(dus[-1][c]) for c in range(3)])
+            dus.append(Sdu + np.einsum("ca...,a...->c...", self.grad_u(n), dd) + dd)
+        lam = -(2.0 / p.sigma**2) * (self.m1 - self.I1)
+        dm1 = np.sum(self.grad_warp * dus[-1], axis=0)
+        dlam = -(2.0 / p.sigma**2) * dm1
+        rho = lam[None] * self.grad_warp
+        drho = dlam[None] * self.grad_warp + lam[None] * self.warp.hessian_times(self.I0, dus[-1])
+        rhos = [rho]
+        for n in range(p.nt - 1, 0, -1):      # rho^n for n = nt-1 .. 1
+            rho = np.stack([st.apply_transpose(rho[c]) for c in range(3)])
+            rhos.append(rho)
+        rhos = rhos[::-1]                     # rhos[n - 1] = rho^n, n = 1 .. nt
+        db = np.zeros((3,) + tuple(p.n))
+        for n in range(p.nt - 1, -1, -1):
+            rho1 = rhos[n]
+            Du = self.grad_u(n)
+            dDu = np.stack([st.gradient(dus[n][c]) + st.hessian_times(self.u[n][c], dd)
+                            for c in range(3)])
+            db += p.dt * (drho + np.einsum("c...,ca...->a...", drho, Du)
+                          + np.einsum("c...,ca...->a...", rho1, dDu))
+            drho = np.stack([st.apply_transpose(drho[c]) + st.gradient_transpose(dd * rho1[c][None])
+                             for c in range(3)])
+        h = self.A[None] * dvt + project(db, p.band)
+        if p.incompressible:
+            h = leray(h, p.n)
         return h, dm1
 
 

@@ -995,3 +995,41 @@ def test_nonstationary_gn_hessian_equals_dense_jacobian_bruteforce():
     for s in range(3):
         v = np.stack([synth.random_direction(p.band, 2450 + 10 * s + n) for n in range(p.nt)])
         assert rel(_theta(pt.gn_hessvec(v)[0]), H @ _theta(v)) < 1e-7
+
+
+def test_deformation_full_hessian():
+    """The deformation variant's full Newton Hessian: central differences of the
+    gradient to 1e-7 away from a minimum (Gauss-Newton off by more than 1e-3),
+    symmetric, equal to Gauss-Newton at zero residual, and a full Newton run
+    decreases the energy."""
+    p = O.Params(n=(12, 12, 12), band=(4, 6, 4), nt=5, sigma=0.5, state="deformation")
+    I0, I1, _ = synth.blob_pair(p.n, 2301, max_disp=2.0)
+    vt = synth.random_coefficients(p.band, 2302, bound=2.0)
+    pt = O.DeformationPoint(vt, I0, I1, p)
+    eps = 1e-6
+    checked = 0
+    for s in range(12):
+        dvt = synth.random_direction(p.band, 2310 + s)
+        if not _kink_free_def(vt, dvt, eps, p):
+            continue
+        gp = O.DeformationPoint(vt + eps * dvt, I0, I1, p).gradient()[0]
+        gm = O.DeformationPoint(vt - eps * dvt, I0, I1, p).gradient()[0]
+        fd = (gp - gm) / (2 * eps)
+        assert rel(pt.full_hessvec(dvt)[0], fd) < 1e-7
+        assert rel(pt.gn_hessvec(dvt)[0], fd) > 1e-3
+        checked += 1
+        if checked == 3:
+            break
+    assert checked == 3
+    v = synth.random_direction(p.band, 2330)
+    w = synth.random_direction(p.band, 2331)
+    a, b = O.inner(pt.full_hessvec(v)[0], w), O.inner(v, pt.full_hessvec(w)[0])
+    assert abs(a - b) <= 1e-10 * max(abs(a), abs(b))
+    pt0 = O.DeformationPoint(vt, I0, pt.m1, p)
+    assert rel(pt0.full_hessvec(v)[0], pt0.gn_hessvec(v)[0]) < 1e-13
+    q = O.Params(n=(16, 16, 16), band=(4, 4, 4), nt=5, state="deformation")
+    J0, J1, _ = synth.blob_pair(q.n, 71, max_disp=2.0)
+    rep = O.newton(np.zeros((3,) + q.band, complex), J0, J1, q, max_newton=3, max_pcg=8,
+                   gtol=1e-6, hessian="full")
+    assert rep.iterations >= 2
+    assert all(y < x for x, y in zip(rep.energies, rep.energies[1:]))
