@@ -122,3 +122,20 @@ def test_params_struct_layout_matches_header(tmp_path):
                                           text=True).stdout.split()]
     want = [ctypes.sizeof(blr.blr_params)] + [getattr(blr.blr_params, f).offset for f in fields]
     assert got == want
+
+
+def test_header_compiles_as_c_and_cpp(tmp_path):
+    """include/blr.h is plain C (C99) and C++ with the extern "C" guard: both
+    compilers accept a translation unit that takes the address of every entry
+    point the header declares."""
+    import shutil
+    import subprocess
+    names = _declared()
+    body = "".join(f"  (void)&{n};\n" for n in names)
+    for cc, ext, std in ((shutil.which("gcc"), "c", "-std=c99"), (shutil.which("g++"), "cpp", "-std=c++17")):
+        if cc is None:
+            continue
+        src_file = tmp_path / f"uses.{ext}"
+        src_file.write_text('#include "blr.h"\nvoid uses(void) {\n' + body + "}\n")
+        subprocess.run([cc, std, "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), "-c",
+                        str(src_file), "-o", str(tmp_path / f"uses_{ext}.o")], check=True)
