@@ -84,7 +84,7 @@ typedef struct blr_plan *blr_plan_t;
 
 /* Problem description (Section 3.2, Eq. 35 and the constants of L). */
 typedef struct blr_params {
-    int n[3];        /* grid N1, N2, N3 (each >= 1)                         */
+    int n[3];        /* grid N1, N2, N3 (each >= 1; N1 <= 65535; V <= 2^31) */
     int band[3];     /* B1, B2, B3 (each even, 2 <= B_d <= N_d)             */
     int nt;          /* number of time steps, >= 1                          */
     double alpha;    /* L = (-alpha Lap + gamma)^s, alpha >= 0              */

@@ -42,6 +42,7 @@ int validate(const blr_params *p) {
     if (p->ckpt_every < 0) return BLR_EINVAL;
     long long V = (long long)p->n[0] * p->n[1] * p->n[2];
     if (V > (1LL << 31)) return BLR_EINVAL;
+    if (p->n[0] > 65535) return BLR_EINVAL;   // one grid row of blocks per x1 plane
     return BLR_OK;
 }
 

@@ -50,6 +50,7 @@ def test_strerror_and_invalid_params(lib):
         dict(n=(0, 16, 16), band=(4, 4, 4)),
         dict(n=(16, 16, 16), band=(4, 4, 4), s=0.3),  # 2s not an integer
         dict(n=(16, 16, 16), band=(4, 4, 4), s=-0.5),
+        dict(n=(65536, 2, 2), band=(4, 2, 2)),           # x1 planes past the grid limit
     ]
     for kw in bad:
         p = blr.make_params(**{"nt": 4, **kw})
