@@ -679,7 +679,8 @@ class NewtonReport:
 
 
 def newton(vt0, I0, I1, p: Params, max_newton=5, max_pcg=10, gtol=1e-2,
-           forcing=None, c1=1e-4, max_halvings=10, hessian="gn") -> NewtonReport:
+           forcing=None, c1=1e-4, max_halvings=10, hessian="gn",
+           point=None) -> NewtonReport:
     """Gauss-Newton-Krylov (hessian="gn") or Newton-Krylov (hessian="full",
     truncated PCG): p from PCG on H p = -g (preconditioner K~), then
     v~ <- v~ + eps p with Armijo backtracking from eps = 1 (halving).
@@ -688,8 +689,16 @@ def newton(vt0, I0, I1, p: Params, max_newton=5, max_pcg=10, gtol=1e-2,
     literally that is an ascent step, so the descent direction p = dv is added.
     forcing=None uses eta = min(0.5, sqrt(||g|| / ||g0||)); a number fixes eta.
     Stops when ||g||_inf / ||g0||_inf < gtol, after max_newton updates, or when
-    the line search fails."""
-    pt = make_point(vt0, I0, I1, p)
+    the line search fails.
+
+    point: the objective, a callable vt -> an object with .vt, .energy, .cfl,
+    .A (the preconditioner is 1 / A), .gradient() and .gn_hessvec(v) /
+    .full_hessvec(v) (first element of each result used).  None is the
+    registration energy of the chosen state equation (make_point); the pins
+    pass closed-form objectives to check the iteration itself."""
+    if point is None:
+        point = lambda v: make_point(v, I0, I1, p)  # noqa: E731
+    pt = point(vt0)
     g = pt.gradient()[0]
     g0_inf = max_abs(g)
     g0_2 = np.sqrt(inner(g, g))
@@ -711,7 +720,7 @@ def newton(vt0, I0, I1, p: Params, max_newton=5, max_pcg=10, gtol=1e-2,
         eps = 1.0
         accepted = None
         for _ in range(max_halvings + 1):
-            trial = make_point(pt.vt + eps * step, I0, I1, p)
+            trial = point(pt.vt + eps * step)
             if trial.cfl < 1.0 and trial.energy <= pt.energy + c1 * eps * slope:
                 accepted = trial
                 break

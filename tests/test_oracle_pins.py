@@ -451,6 +451,190 @@ def test_newton_decreases_energy_and_gradient():
     assert rep.grad_inf_rel < 0.5
 
 
+# Closed-form objectives for the Newton iteration itself (Section 3.4, Eqs. 54-55
+# read as v~ <- v~ + eps p with H p = -g).  The parameter space is complex arrays
+# with <a, b> = Re sum a conj(b), i.e. the real vector (Re x, Im x).
+
+
+class _DiagObjective:
+    """E(x) = sum_i phi(Re x_i) + phi(Im x_i) for a scalar function phi with
+    derivatives dphi, ddphi: gradient and Hessian are elementwise.  The
+    preconditioner 1 / A is per frequency, shared by the three components: A is
+    component 0's Hessian diagonal (exact where only component 0 moves) unless
+    `A` is given."""
+
+    def __init__(self, x, phi, dphi, ddphi, A=None):
+        self.vt = x
+        self.energy = float(np.sum(phi(x.real)) + np.sum(phi(x.imag)))
+        self._g = dphi(x.real) + 1j * dphi(x.imag)
+        self._hr, self._hi = ddphi(x.real), ddphi(x.imag)
+        self.A = self._hr[0] if A is None else A
+        self.cfl = 0.0
+
+    def gradient(self):
+        return self._g, None, None
+
+    def gn_hessvec(self, v):
+        return self._hr * v.real + 1j * (self._hi * v.imag), None
+
+
+class _Quadratic:
+    """E(x) = 1/2 <x, q x> - <c, x>, q > 0 real elementwise; the preconditioner
+    is 1 / A (A per frequency: q[0] when q is the same for every component)."""
+
+    def __init__(self, x, q, c, A):
+        self.vt = x
+        self.energy = 0.5 * O.inner(x, q * x) - O.inner(c, x)
+        self._g = q * x - c
+        self._q = q
+        self.A = A
+        self.cfl = 0.0
+
+    def gradient(self):
+        return self._g, None, None
+
+    def gn_hessvec(self, v):
+        return self._q * v, None
+
+
+def _quadratic(q, c, A=None):
+    return lambda x: _Quadratic(x, q, c, q[0] if A is None else A)
+
+
+def test_newton_takes_the_exact_newton_step_on_a_quadratic():
+    """With the exact preconditioner PCG solves H p = -g in one iteration, the
+    full step eps = 1 passes Armijo and lands on the minimiser q^-1 c, where the
+    gradient vanishes (catches v - eps p, a wrong PCG start, a missing step)."""
+    rng = np.random.default_rng(3)
+    shape = (3, 2, 2, 2)
+    q = np.broadcast_to(rng.uniform(0.5, 4.0, size=shape[1:]), shape).copy()
+    c = rng.normal(size=shape) + 1j * rng.normal(size=shape)
+    rep = O.newton(np.zeros(shape, complex), None, None, None, max_newton=3, max_pcg=5,
+                   gtol=1e-12, point=_quadratic(q, c))
+    assert rep.iterations == 1 and rep.steps == [1.0] and rep.pcg_iterations == [1]
+    assert rel(rep.vt, c / q) < 1e-14
+    assert abs(rep.energies[1] - (-0.5 * O.inner(c, c / q))) < 1e-12 * abs(rep.energies[1])
+
+
+def _huber():
+    return (lambda t: np.sqrt(1 + t * t), lambda t: t / np.sqrt(1 + t * t),
+            lambda t: (1 + t * t) ** -1.5)
+
+
+def test_newton_backtracking_halves_to_the_first_armijo_step():
+    """phi(t) = sqrt(1 + t^2): the Newton step from t is -t(1 + t^2).  From t = 2
+    it goes to -8 (eps = 1) and -3 (eps = 1/2), both uphill, and eps = 1/4 gives
+    t = -1/2.  From there full steps are taken and t -> -t^3 (catches a missing
+    halving, a wrong halving factor, a step that is not re-based on the accepted
+    point)."""
+    phi, dphi, ddphi = _huber()
+    x0 = np.zeros((3, 2, 2, 2), complex)
+    x0[0, 0, 1, 0] = 2.0
+    rep = O.newton(x0, None, None, None, max_newton=3, max_pcg=5, gtol=0.0,
+                   point=lambda x: _DiagObjective(x, phi, dphi, ddphi))
+    assert rep.steps == [0.25, 1.0, 1.0]
+    want = [2.0, -0.5, 0.125, -0.125 ** 3]
+    E = [float(np.sum(phi(np.array([t])))) + (2 * x0.size - 1) for t in want]
+    assert np.allclose(rep.energies, E, rtol=0, atol=1e-14)
+    assert rep.vt.shape == x0.shape
+    assert abs(rep.vt[0, 0, 1, 0] - want[-1]) < 1e-15
+
+
+@pytest.mark.parametrize("ratio,eps", [(1.25e-4, 1.0), (0.8e-4, 0.5)])
+def test_newton_armijo_constant_is_1e_4(ratio, eps):
+    """From t0 = 1 - delta the full Newton step lands on -(1 - delta)^3, a small
+    decrease.  delta is chosen (bisection on the closed form) so that the
+    decrease is `ratio` times |eps <g, p>| at eps = 1: with c1 = 1e-4 the full step
+    is accepted at ratio 1.25e-4 and rejected at 0.8e-4 (then eps = 1/2 passes).
+    A constant outside [0.8e-4, 1.25e-4) fails one of the two cases."""
+    phi, dphi, ddphi = _huber()
+
+    def decrease_ratio(d):
+        t0 = 1.0 - d
+        p = -t0 * (1 + t0 * t0)
+        return (phi(t0) - phi(t0 + p)) / abs(dphi(t0) * p)
+
+    lo, hi = 1e-9, 1e-2          # decrease_ratio is increasing in delta on this range
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if decrease_ratio(mid) < ratio:
+            lo = mid
+        else:
+            hi = mid
+    t0 = 1.0 - 0.5 * (lo + hi)
+    x0 = np.zeros((3, 2, 2, 2), complex)
+    x0[0, 1, 1, 1] = t0   # component 0: the preconditioner is exact there
+    rep = O.newton(x0, None, None, None, max_newton=1, max_pcg=5, gtol=0.0,
+                   point=lambda x: _DiagObjective(x, phi, dphi, ddphi))
+    assert rep.steps == [eps]
+
+
+def test_newton_forcing_term_matches_scipy_cg_iteration_counts():
+    """Without a preconditioner (A = 1) PCG is plain CG; per Newton step its
+    iteration count must be that of scipy's CG on the same system with
+    rtol = eta, eta = min(0.5, sqrt(||g|| / ||g0||)) (catches a forcing term in
+    the inf-norm, without the square root, or measured against the wrong norm)."""
+    from scipy.sparse.linalg import cg
+    rng = np.random.default_rng(11)
+    shape = (3, 4, 4, 4)
+    q = rng.uniform(1.0, 300.0, size=shape)
+    c = rng.normal(size=shape) + 1j * rng.normal(size=shape)
+    rep = O.newton(np.zeros(shape, complex), None, None, None, max_newton=3, max_pcg=200,
+                   gtol=0.0, point=_quadratic(q, c, A=np.ones(shape[1:])))
+    assert rep.steps == [1.0, 1.0, 1.0]   # CG iterates satisfy Armijo at eps = 1
+    Q = np.concatenate([q.ravel(), q.ravel()])
+    x = np.zeros(2 * q.size)
+    b = np.concatenate([c.real.ravel(), c.imag.ravel()])
+    g0 = np.linalg.norm(Q * x - b)
+    for its in rep.pcg_iterations:
+        g = Q * x - b
+        eta = min(0.5, math.sqrt(np.linalg.norm(g) / g0))
+        count = []
+        p, _ = cg(np.diag(Q), -g, rtol=eta, atol=0.0, maxiter=200,
+                  callback=lambda _x: count.append(1))
+        assert its == len(count)
+        x = x + p
+    assert rel(np.concatenate([rep.vt.real.ravel(), rep.vt.imag.ravel()]), x) < 1e-10
+
+
+def test_newton_line_search_log_on_a_registration():
+    """On a registration: every accepted eps satisfies the Armijo inequality with
+    c1 = 1e-4 against the base point's energy and slope <g, p>, and every trial
+    before it (eps' = 2 eps, 4 eps, ... from 1) did not."""
+    p = O.Params(n=(12, 12, 12), band=(4, 4, 4), nt=4)
+    I0, I1, _ = synth.blob_pair(p.n, 72, max_disp=2.5)
+    log = []
+
+    def point(v):
+        pt = O.make_point(v, I0, I1, p)
+        log.append(pt)
+        return pt
+
+    rep = O.newton(np.zeros((3,) + p.band, complex), None, None, None, max_newton=4,
+                   max_pcg=6, gtol=0.0, point=point)
+    assert rep.iterations >= 3
+    i = 0
+    base = log[0]
+    for eps in rep.steps:
+        step = None
+        trials = [1.0]
+        while trials[-1] > eps:
+            trials.append(trials[-1] * 0.5)
+        g = base.gradient()[0]
+        for k, e in enumerate(trials):
+            i += 1
+            t = log[i]
+            if step is None:
+                step = (t.vt - base.vt) / e
+            assert rel(t.vt, base.vt + e * step) < 1e-13
+            bound = base.energy + 1e-4 * e * O.inner(g, step)
+            if k == len(trials) - 1:
+                assert t.energy <= bound
+            else:
+                assert not (t.cfl < 1.0 and t.energy <= bound)
+        base = log[i]
+
+
 # ----------------------------------------------------------------------------
 # Incompressible form (Eq. 4 with gamma = 1, constraint in the band)
 # ----------------------------------------------------------------------------
