@@ -316,7 +316,10 @@ int blr_status(blr_plan_t plan, blr_stream_t stream);
  *   BLR_EINVAL before anything runs (a 128^3 grid with a 32^3 band fits).
  * Set-up: the first call on each device, with that device current, looks up
  *   the array's device address (cudaGetSymbolAddress); make that first call
- *   before any stream capture.
+ *   before any stream capture.  The look-up is repeated when the device's
+ *   context has changed since (after cudaDeviceReset the library's device code
+ *   is loaded again and the array may have moved), so make the first call after
+ *   a reset before any capture too.
  * Sharing: every call on a device uses the same array.  Calls whose work
  *   overlaps on the GPU (other streams, other host threads) race and corrupt
  *   each other's results: order them on one stream.  Each call writes every

@@ -23,10 +23,13 @@ import torch
 class RegistrationEnergy(torch.autograd.Function):
     @staticmethod
     def forward(ctx, vt, plan):
-        if vt.dtype != torch.complex64 or not vt.is_cuda:
-            raise ValueError("vt must be a complex64 CUDA tensor of the plan's coefficient "
-                             "shape: (3, B1, B2, B3), or (nt, 3, B1, B2, B3) for a "
-                             "non-stationary plan")
+        want = (3,) + tuple(plan.band)
+        if plan.params.nonstationary:
+            want = (plan.nt,) + want
+        if vt.dtype != torch.complex64 or not vt.is_cuda or tuple(vt.shape) != want:
+            raise ValueError(f"vt must be a complex64 CUDA tensor of the plan's coefficient "
+                             f"shape {want} ((3, B1, B2, B3), or (nt, 3, B1, B2, B3) for a "
+                             f"non-stationary plan); got {tuple(vt.shape)} {vt.dtype} on {vt.device}")
         vt = vt.contiguous()
         energy = torch.empty(3, dtype=torch.float64, device=vt.device)
         plan.state(vt, energy=energy)

@@ -133,20 +133,62 @@ def _stream(stream):
     return _P(stream.cuda_stream)
 
 
-def _ptr(t, *, device_only=True, dtype=None, numel=None, optional=False, name="tensor"):
+def _ptr(t, *, device_only=True, dtype=None, numel=None, optional=False, name="tensor",
+         device=None):
+    """Data pointer of `t` after checking what the C entry point cannot: element
+    count (numel), dtype, contiguity, and for device pointers that the tensor is
+    on the CUDA device `device` (an index; None skips the check)."""
     if t is None:
         if optional:
             return None
         raise ValueError(f"{name} is required")
-    if device_only and not t.is_cuda:
-        raise ValueError(f"{name} must be a CUDA tensor")
-    if not t.is_contiguous():
-        raise ValueError(f"{name} must be contiguous")
     if dtype is not None and t.dtype != dtype:
         raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
     if numel is not None and t.numel() != numel:
         raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if device_only and not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if device is not None and t.is_cuda and t.device.index != device:
+        raise ValueError(f"{name} is on {t.device}, the call runs on cuda:{device}")
     return _P(t.data_ptr())
+
+
+@dataclass(frozen=True)
+class _Shape:
+    """Element counts of one plan's arrays (complex64 counts for coefficients)."""
+    V: int          # voxels
+    coef: int       # one velocity's coefficients: 3 B1 B2 B3
+    nvel: int       # velocities in a parameter vector (nt when non-stationary)
+    device: int     # CUDA device the plan was created on
+    deformation: bool
+
+    @property
+    def param(self):
+        return self.nvel * self.coef
+
+
+_SHAPES: dict = {}
+
+
+def _shape_of(params: blr_params, device: int) -> _Shape:
+    n, b = list(params.n), list(params.band)
+    return _Shape(V=n[0] * n[1] * n[2], coef=3 * b[0] * b[1] * b[2],
+                  nvel=int(params.nt) if params.nonstationary else 1, device=int(device),
+                  deformation=params.state_equation == BLR_STATE_DEFORMATION)
+
+
+def _shape(plan) -> _Shape:
+    try:
+        return _SHAPES[int(plan)]
+    except (KeyError, TypeError):
+        raise ValueError("not a live plan handle of this binding") from None
+
+
+def _current_device() -> int:
+    import torch
+    return torch.cuda.current_device()
 
 
 def make_params(n, band, nt=10, alpha=3.0, gamma=1.0, s=2, sigma=1.0, precision=BLR_FP32,
@@ -172,87 +214,124 @@ def make_params(n, band, nt=10, alpha=3.0, gamma=1.0, s=2, sigma=1.0, precision=
 def blr_plan_create(params: blr_params) -> int:
     h = _P()
     _check(_lib.blr_plan_create(ctypes.byref(params), ctypes.byref(h)), "blr_plan_create")
+    _SHAPES[h.value] = _shape_of(params, _current_device())
     return h.value
 
 
 def blr_plan_destroy(plan: int):
+    _SHAPES.pop(int(plan), None)
     _check(_lib.blr_plan_destroy(_P(plan)), "blr_plan_destroy")
 
 
 def blr_set_images(plan, I0, I1, stream=None):
     import torch
-    _check(_lib.blr_set_images(_P(plan), _ptr(I0, device_only=False, dtype=torch.float32, name="I0"),
-                               _ptr(I1, device_only=False, dtype=torch.float32, name="I1"),
+    sh = _shape(plan)
+    kw = dict(device_only=False, dtype=torch.float32, numel=sh.V, device=sh.device)
+    _check(_lib.blr_set_images(_P(plan), _ptr(I0, name="I0", **kw), _ptr(I1, name="I1", **kw),
                                _stream(stream)), "blr_set_images")
 
 
 def blr_expand(plan, vt, v, stream=None):
     import torch
-    _check(_lib.blr_expand(_P(plan), _ptr(vt, dtype=torch.complex64, name="vt"),
-                           _ptr(v, dtype=torch.float32, name="v"), _stream(stream)), "blr_expand")
+    sh = _shape(plan)
+    _check(_lib.blr_expand(_P(plan),
+                           _ptr(vt, dtype=torch.complex64, numel=sh.coef, name="vt", device=sh.device),
+                           _ptr(v, dtype=torch.float32, numel=3 * sh.V, name="v", device=sh.device),
+                           _stream(stream)), "blr_expand")
 
 
 def blr_expand_noalloc(n, band, vt, v, stream=None):
     """iota without a plan and without allocating (see include/blr.h): the
-    library's fixed device scratch array holds the tables and intermediates."""
+    library's fixed device scratch array holds the tables and intermediates.
+    vt and v must be on the current device (the call runs there)."""
     import torch
-    cn = (ctypes.c_int * 3)(*[int(x) for x in n])
-    cb = (ctypes.c_int * 3)(*[int(x) for x in band])
-    _check(_lib.blr_expand_noalloc(cn, cb, _ptr(vt, dtype=torch.complex64, name="vt"),
-                                   _ptr(v, dtype=torch.float32, name="v"), _stream(stream)),
-           "blr_expand_noalloc")
+    n, band = [int(x) for x in n], [int(x) for x in band]
+    if len(n) != 3 or len(band) != 3:
+        raise ValueError("n and band take three entries each")
+    dev = _current_device()
+    cn = (ctypes.c_int * 3)(*n)
+    cb = (ctypes.c_int * 3)(*band)
+    coef = 3 * band[0] * band[1] * band[2]
+    V = n[0] * n[1] * n[2]
+    _check(_lib.blr_expand_noalloc(cn, cb,
+                                   _ptr(vt, dtype=torch.complex64, numel=coef, name="vt", device=dev),
+                                   _ptr(v, dtype=torch.float32, numel=3 * V, name="v", device=dev),
+                                   _stream(stream)), "blr_expand_noalloc")
 
 
 def blr_project(plan, f, ft, stream=None):
     import torch
-    _check(_lib.blr_project(_P(plan), _ptr(f, dtype=torch.float32, name="f"),
-                            _ptr(ft, dtype=torch.complex64, name="ft"), _stream(stream)),
-           "blr_project")
+    sh = _shape(plan)
+    _check(_lib.blr_project(_P(plan),
+                            _ptr(f, dtype=torch.float32, numel=3 * sh.V, name="f", device=sh.device),
+                            _ptr(ft, dtype=torch.complex64, numel=sh.coef, name="ft", device=sh.device),
+                            _stream(stream)), "blr_project")
 
 
 def blr_state(plan, vt, m1=None, energy=None, stream=None):
     import torch
-    _check(_lib.blr_state(_P(plan), _ptr(vt, dtype=torch.complex64, name="vt"),
-                          _ptr(m1, dtype=torch.float32, optional=True, name="m1"),
-                          _ptr(energy, dtype=torch.float64, numel=3, optional=True, name="energy"),
+    sh = _shape(plan)
+    _check(_lib.blr_state(_P(plan),
+                          _ptr(vt, dtype=torch.complex64, numel=sh.param, name="vt", device=sh.device),
+                          _ptr(m1, dtype=torch.float32, numel=sh.V, optional=True, name="m1",
+                               device=sh.device),
+                          _ptr(energy, dtype=torch.float64, numel=3, optional=True, name="energy",
+                               device=sh.device),
                           _stream(stream)), "blr_state")
 
 
 def blr_adjoint(plan, b, lambda0=None, stream=None):
     import torch
-    _check(_lib.blr_adjoint(_P(plan), _ptr(b, dtype=torch.float32, name="b"),
-                            _ptr(lambda0, dtype=torch.float32, optional=True, name="lambda0"),
+    sh = _shape(plan)
+    _check(_lib.blr_adjoint(_P(plan),
+                            _ptr(b, dtype=torch.float32, numel=3 * sh.nvel * sh.V, name="b",
+                                 device=sh.device),
+                            _ptr(lambda0, dtype=torch.float32, numel=sh.V, optional=True,
+                                 name="lambda0", device=sh.device),
                             _stream(stream)), "blr_adjoint")
 
 
 def blr_gradient(plan, vt, g, energy=None, stream=None):
     import torch
-    _check(_lib.blr_gradient(_P(plan), _ptr(vt, dtype=torch.complex64, name="vt"),
-                             _ptr(g, dtype=torch.complex64, name="g"),
-                             _ptr(energy, dtype=torch.float64, numel=3, optional=True, name="energy"),
+    sh = _shape(plan)
+    _check(_lib.blr_gradient(_P(plan),
+                             _ptr(vt, dtype=torch.complex64, numel=sh.param, name="vt",
+                                  device=sh.device),
+                             _ptr(g, dtype=torch.complex64, numel=sh.param, name="g", device=sh.device),
+                             _ptr(energy, dtype=torch.float64, numel=3, optional=True, name="energy",
+                                  device=sh.device),
                              _stream(stream)), "blr_gradient")
 
 
 def blr_gradient_at_state(plan, g, stream=None):
     import torch
-    _check(_lib.blr_gradient_at_state(_P(plan), _ptr(g, dtype=torch.complex64, name="g"),
-                                      _stream(stream)), "blr_gradient_at_state")
+    sh = _shape(plan)
+    _check(_lib.blr_gradient_at_state(
+        _P(plan), _ptr(g, dtype=torch.complex64, numel=sh.param, name="g", device=sh.device),
+        _stream(stream)), "blr_gradient_at_state")
 
 
 def blr_hessvec(plan, dvt, hdv, stream=None):
     import torch
-    _check(_lib.blr_hessvec(_P(plan), _ptr(dvt, dtype=torch.complex64, name="dvt"),
-                            _ptr(hdv, dtype=torch.complex64, name="hdv"), _stream(stream)),
-           "blr_hessvec")
+    sh = _shape(plan)
+    _check(_lib.blr_hessvec(_P(plan),
+                            _ptr(dvt, dtype=torch.complex64, numel=sh.param, name="dvt",
+                                 device=sh.device),
+                            _ptr(hdv, dtype=torch.complex64, numel=sh.param, name="hdv",
+                                 device=sh.device),
+                            _stream(stream)), "blr_hessvec")
 
 
 def blr_pcg(plan, rhs, x, maxit, eta, stream=None):
     import torch
+    sh = _shape(plan)
     it = ctypes.c_int(0)
     rel = ctypes.c_double(0.0)
-    _check(_lib.blr_pcg(_P(plan), _ptr(rhs, dtype=torch.complex64, name="rhs"),
-                        _ptr(x, dtype=torch.complex64, name="x"), int(maxit), float(eta),
-                        ctypes.byref(it), ctypes.byref(rel), _stream(stream)), "blr_pcg")
+    _check(_lib.blr_pcg(_P(plan),
+                        _ptr(rhs, dtype=torch.complex64, numel=sh.param, name="rhs", device=sh.device),
+                        _ptr(x, dtype=torch.complex64, numel=sh.param, name="x", device=sh.device),
+                        int(maxit), float(eta), ctypes.byref(it), ctypes.byref(rel),
+                        _stream(stream)), "blr_pcg")
     return it.value, rel.value
 
 
@@ -272,8 +351,10 @@ class Report:
 def blr_newton(plan, vt, max_newton, max_pcg, gtol, forcing=-1.0, stream=None,
                raise_on_error=True) -> Report:
     import torch
+    sh = _shape(plan)
     rep = blr_report()
-    rc = _lib.blr_newton(_P(plan), _ptr(vt, device_only=False, dtype=torch.complex64, name="vt"),
+    rc = _lib.blr_newton(_P(plan), _ptr(vt, device_only=False, dtype=torch.complex64,
+                                        numel=sh.param, name="vt", device=sh.device),
                          int(max_newton), int(max_pcg), float(gtol), float(forcing),
                          ctypes.byref(rep), _stream(stream))
     if raise_on_error:
@@ -367,10 +448,14 @@ class Plan:
         return dict(zip(self.TUNING_KEYS, [int(v) for v in vals]))
 
 
-def _ptr_array(tensors, **kw):
+def _ptr_array(tensors, shapes, numel, **kw):
+    """Pointers of one tensor per pair, each checked against its pair's shape
+    (numel(shape) elements, on the pair's device)."""
+    if len(tensors) != len(shapes):
+        raise ValueError(f"{len(tensors)} tensors for {len(shapes)} pairs")
     arr = (_P * len(tensors))()
-    for i, t in enumerate(tensors):
-        arr[i] = _ptr(t, **kw)
+    for i, (t, sh) in enumerate(zip(tensors, shapes)):
+        arr[i] = _ptr(t, numel=numel(sh), device=sh.device, name=f"pair {i}", **kw)
     return arr
 
 
@@ -383,6 +468,7 @@ class Batch:
         params = [sh if isinstance(sh, blr_params) else
                   make_params(sh[0], sh[1], nt, alpha, gamma, s, sigma) for sh in shapes]
         self.npairs = len(params)
+        self._pair = [_shape_of(p, _current_device()) for p in params]
         self.shapes = [(tuple(p.n), tuple(p.band)) for p in params]
         arr = (blr_params * self.npairs)(*params)
         h = _P()
@@ -408,28 +494,36 @@ class Batch:
 
     def set_images(self, pair, I0, I1, stream=None):
         import torch
-        _check(_lib.blr_batch_set_images(_P(self.handle), int(pair),
-                                         _ptr(I0, device_only=False, dtype=torch.float32, name="I0"),
-                                         _ptr(I1, device_only=False, dtype=torch.float32, name="I1"),
-                                         _stream(stream)), "blr_batch_set_images")
+        if not 0 <= int(pair) < self.npairs:
+            raise ValueError(f"pair {pair} out of range 0..{self.npairs - 1}")
+        sh = self._pair[int(pair)]
+        kw = dict(device_only=False, dtype=torch.float32, numel=sh.V, device=sh.device)
+        _check(_lib.blr_batch_set_images(_P(self.handle), int(pair), _ptr(I0, name="I0", **kw),
+                                         _ptr(I1, name="I1", **kw), _stream(stream)),
+               "blr_batch_set_images")
 
     def gradient(self, vts, gs, stream=None):
         import torch
-        _check(_lib.blr_batch_gradient(_P(self.handle), _ptr_array(vts, dtype=torch.complex64),
-                                       _ptr_array(gs, dtype=torch.complex64), _stream(stream)),
-               "blr_batch_gradient")
+        coef = lambda sh: sh.coef  # noqa: E731
+        _check(_lib.blr_batch_gradient(_P(self.handle),
+                                       _ptr_array(vts, self._pair, coef, dtype=torch.complex64),
+                                       _ptr_array(gs, self._pair, coef, dtype=torch.complex64),
+                                       _stream(stream)), "blr_batch_gradient")
 
     def hessvec(self, dvts, hdvs, stream=None):
         import torch
-        _check(_lib.blr_batch_hessvec(_P(self.handle), _ptr_array(dvts, dtype=torch.complex64),
-                                      _ptr_array(hdvs, dtype=torch.complex64), _stream(stream)),
-               "blr_batch_hessvec")
+        coef = lambda sh: sh.coef  # noqa: E731
+        _check(_lib.blr_batch_hessvec(_P(self.handle),
+                                      _ptr_array(dvts, self._pair, coef, dtype=torch.complex64),
+                                      _ptr_array(hdvs, self._pair, coef, dtype=torch.complex64),
+                                      _stream(stream)), "blr_batch_hessvec")
 
     def newton(self, vts, max_newton, max_pcg, gtol, forcing=-1.0, stream=None):
         import torch
         reps = (blr_report * self.npairs)()
         _check(_lib.blr_batch_newton(_P(self.handle),
-                                     _ptr_array(vts, device_only=False, dtype=torch.complex64),
+                                     _ptr_array(vts, self._pair, lambda sh: sh.coef,
+                                                device_only=False, dtype=torch.complex64),
                                      int(max_newton), int(max_pcg), float(gtol), float(forcing),
                                      reps, _stream(stream)), "blr_batch_newton")
         return [Report(*[getattr(r, f) for f, _ in blr_report._fields_]) for r in reps]

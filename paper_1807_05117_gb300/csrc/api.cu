@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 
 #include "blr_internal.cuh"
@@ -14,6 +15,58 @@
 unsigned long long g_blr_launches = 0;
 
 namespace {
+
+// The context's persisting-L2 set-aside is a per-process limit shared with every
+// other library in the process.  Plans that may keep their displacement copy in
+// persisting lines raise it; the first of them records the limit as it was, and
+// the last one destroyed releases the persisting lines (only if some plan used
+// them) and puts the old limit back.
+struct L2Share {
+    int plans = 0;        // live plans counted here
+    bool raised = false;  // a plan raised the limit above `prev`
+    bool used = false;    // a plan kept lines in the set-aside
+    size_t prev = 0;      // the limit before the first counted plan
+};
+constexpr int kL2Devices = 64;
+std::mutex g_l2_mu;
+L2Share g_l2[kL2Devices];
+
+// Raise the set-aside to `aside` bytes for plan P (its device current).
+bool l2_acquire(blr_plan *P, size_t aside) {
+    if (P->device < 0 || P->device >= kL2Devices) return false;
+    std::lock_guard<std::mutex> lock(g_l2_mu);
+    L2Share &u = g_l2[P->device];
+    size_t cur = 0;
+    if (cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) != cudaSuccess) return false;
+    if (u.plans == 0) {
+        u.prev = cur;
+        u.raised = false;
+        u.used = false;
+    }
+    if (cur < aside) {
+        if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, aside) != cudaSuccess) return false;
+        u.raised = true;
+        cur = aside;
+    }
+    ++u.plans;
+    P->l2_counted = 1;
+    P->l2_hit = (float)((double)cur / (double)P->l2_win_bytes);
+    if (P->l2_hit > 1.f) P->l2_hit = 1.f;
+    return true;
+}
+
+// Plan P is going away (its device current).
+void l2_release(blr_plan *P) {
+    if (!P->l2_counted) return;
+    std::lock_guard<std::mutex> lock(g_l2_mu);
+    L2Share &u = g_l2[P->device];
+    if (P->l2_persist) u.used = true;
+    if (--u.plans > 0) return;
+    if (u.used) cudaCtxResetPersistingL2Cache();
+    if (u.raised) cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, u.prev);
+    cudaGetLastError();
+    u = L2Share();
+}
 
 int validate(const blr_params *p) {
     if (!p) return BLR_EINVAL;
@@ -349,6 +402,7 @@ int plan_create(const blr_params *p, bool grad_cache, blr_plan **out) {
     P->l2_persist = 0;
     P->l2_win_bytes = 0;
     P->l2_hit = 0.f;
+    P->l2_counted = 0;
     if (P->sweep_wide) {
         int max_persist = 0, max_window = 0;
         if (cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, P->device) ==
@@ -359,14 +413,8 @@ int plan_create(const blr_params *p, bool grad_cache, blr_plan **out) {
             size_t win = (size_t)P->V * sizeof(float4);
             if (win > (size_t)max_window) win = (size_t)max_window;
             size_t aside = win < (size_t)max_persist ? win : (size_t)max_persist;
-            size_t cur = 0;
-            if (cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) == cudaSuccess &&
-                (cur >= aside || cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, aside) ==
-                                     cudaSuccess)) {
-                P->l2_win_bytes = win;
-                P->l2_hit = (float)((double)(cur > aside ? cur : aside) / (double)win);
-                if (P->l2_hit > 1.f) P->l2_hit = 1.f;
-            }
+            P->l2_win_bytes = win;
+            if (!l2_acquire(P, aside)) P->l2_win_bytes = 0;
         }
         cudaGetLastError();
     }
@@ -377,18 +425,21 @@ int plan_create(const blr_params *p, bool grad_cache, blr_plan **out) {
     char *base = nullptr;
     if (cudaMalloc(&base, bytes) != cudaSuccess) {
         cudaGetLastError();
+        l2_release(P);
         delete P;
         return BLR_ENOMEM;
     }
     layout(P, base);
     if (cudaMallocHost(&P->hsc, (SC_COUNT + 1) * sizeof(double)) != cudaSuccess) {
         cudaFree(base);
+        l2_release(P);
         delete P;
         return BLR_ENOMEM;
     }
     if (cudaMallocHost(&P->hlive, 12 * sizeof(int)) != cudaSuccess) {
         cudaFreeHost(P->hsc);
         cudaFree(base);
+        l2_release(P);
         delete P;
         return BLR_ENOMEM;
     }
@@ -399,6 +450,7 @@ int plan_create(const blr_params *p, bool grad_cache, blr_plan **out) {
         cudaFreeHost(P->hlive);
         cudaFreeHost(P->hsc);
         cudaFree(base);
+        l2_release(P);
         delete P;
         return BLR_ECUDA;
     }
@@ -422,8 +474,8 @@ int blr_plan_destroy(blr_plan_t P) {
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(P->device);
-    if (P->l2_persist) cudaCtxResetPersistingL2Cache();   // release this plan's lines
     cudaError_t e1 = cudaFree(arena_base(P));
+    l2_release(P);   // the last such plan releases the lines and restores the limit
     cudaError_t e2 = cudaFreeHost(P->hsc);
     if (cudaFreeHost(P->hlive) != cudaSuccess) e2 = cudaErrorInvalidValue;
     if (prev >= 0) cudaSetDevice(prev);

@@ -123,6 +123,7 @@ struct blr_plan {
     int sms;            // multiprocessors of the plan's device
     int l2_persist;     // the wide sweeps keep d4 in persisting L2 lines (sweep_autotune)
     size_t l2_win_bytes;  // access-policy window over d4 (0: not available on this device)
+    int l2_counted;     // counted among the plans that rely on the raised persisting-L2 limit
     float l2_hit;       // its hit ratio (set-aside / window)
     Grid3 grid;
 

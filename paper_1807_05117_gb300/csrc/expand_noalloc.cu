@@ -10,7 +10,9 @@
 //
 // The kernels and launchers are the ones blr_expand uses (dft.cu); only the
 // storage differs.
-#include <atomic>
+#include <cuda.h>
+
+#include <mutex>
 
 #include "blr_internal.cuh"
 
@@ -22,24 +24,71 @@ static __device__ __align__(256) float g_noalloc_scratch[BLR_NOALLOC_SCRATCH_FLO
 namespace {
 
 constexpr int kMaxDevices = 256;
-// Device address of g_noalloc_scratch per device ordinal (host code may not use
-// the symbol itself as a device pointer: in host code it names a host-side
-// stand-in).
-std::atomic<float *> g_scratch_addr[kMaxDevices];
+
+// Device address of g_noalloc_scratch per device ordinal, looked up once per
+// device and context (host code may not use the symbol itself as a device
+// pointer: in host code it names a host-side stand-in).  The context's unique
+// id is kept beside it: after the device's primary context is torn down and
+// re-created (cudaDeviceReset), the module is loaded again and the array may
+// live elsewhere, so a new id repeats the look-up.
+struct ScratchAddr {
+    float *addr = nullptr;
+    unsigned long long ctx = 0;
+};
+std::mutex g_scratch_mu;
+ScratchAddr g_scratch_addr[kMaxDevices];
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// Unique id of the calling thread's current context, or 0 when no context is
+// current or the driver offers no way to ask (the caller then looks the
+// address up again).
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) ==
+                cudaSuccess &&
+            qa == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) ==
+                cudaSuccess &&
+            qb == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<CtxGetCurrentFn>(a);
+            get_id = reinterpret_cast<CtxGetIdFn>(b);
+        }
+        cudaGetLastError();
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&ctx) == CUDA_SUCCESS && ctx &&
+        get_id(ctx, &id) == CUDA_SUCCESS)
+        return id;
+    return 0;
+}
 
 int scratch_on_current_device(float **out) {
     int dev = -1;
     BLR_CK(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return BLR_EINVAL;
-    float *p = g_scratch_addr[dev].load(std::memory_order_acquire);
-    if (!p) {
+    // id 0: no context is current on this thread yet (or the driver cannot say);
+    // the look-up below makes the device's primary context current
+    const unsigned long long ctx = current_context_id();
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    ScratchAddr &e = g_scratch_addr[dev];
+    if (!e.addr || ctx == 0 || ctx != e.ctx) {
         void *addr = nullptr;
-        if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || !addr)
+        if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || !addr) {
+            cudaGetLastError();
             return BLR_ECUDA;
-        p = static_cast<float *>(addr);
-        g_scratch_addr[dev].store(p, std::memory_order_release);
+        }
+        e.addr = static_cast<float *>(addr);
+        e.ctx = current_context_id();
     }
-    *out = p;
+    *out = e.addr;
     return BLR_OK;
 }
 

@@ -140,3 +140,36 @@ def test_header_compiles_as_c_and_cpp(tmp_path):
         src_file.write_text('#include "blr.h"\nvoid uses(void) {\n' + body + "}\n")
         subprocess.run([cc, std, "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), "-c",
                         str(src_file), "-o", str(tmp_path / f"uses_{ext}.o")], check=True)
+
+
+def test_binding_checks_sizes_and_devices_before_calling(lib):  # noqa: ARG001 (builds the library)
+    """The C entry points take bare pointers, so the binding checks element
+    counts (from the plan's grid and band), dtypes and devices first: a wrongly
+    sized tensor raises ValueError and never reaches the library."""
+    import torch
+
+    from paper_1807_05117_gb300 import blr
+    sh = blr._shape_of(blr.make_params((8, 6, 4), (4, 2, 4), nt=3, nonstationary=True), 0)
+    assert (sh.V, sh.coef, sh.nvel, sh.param) == (192, 96, 3, 288)
+    fake = 0x1234
+    blr._SHAPES[fake] = sh
+    try:
+        good = torch.zeros(192 * 3, dtype=torch.float32)
+        with pytest.raises(ValueError, match="elements"):
+            blr.blr_expand(fake, torch.zeros(95, dtype=torch.complex64), good)
+        with pytest.raises(ValueError, match="elements"):
+            blr.blr_project(fake, good[:-1], torch.zeros(96, dtype=torch.complex64))
+        with pytest.raises(ValueError, match="complex64"):
+            blr.blr_gradient(fake, torch.zeros(288, dtype=torch.complex128),
+                             torch.zeros(288, dtype=torch.complex64))
+        with pytest.raises(ValueError, match="elements"):   # one velocity, not nt
+            blr.blr_hessvec(fake, torch.zeros(96, dtype=torch.complex64),
+                            torch.zeros(96, dtype=torch.complex64))
+        with pytest.raises(ValueError, match="elements"):   # nt body forces
+            blr.blr_adjoint(fake, good)
+        with pytest.raises(ValueError, match="CUDA tensor"):  # right size, host memory
+            blr.blr_project(fake, good, torch.zeros(96, dtype=torch.complex64))
+    finally:
+        del blr._SHAPES[fake]
+    with pytest.raises(ValueError, match="live plan"):
+        blr.blr_expand(fake, torch.zeros(96, dtype=torch.complex64), good)

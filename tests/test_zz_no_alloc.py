@@ -48,12 +48,17 @@ def test_expand_noalloc_matches_plan_expand_on_two_calls_in_a_row():
 
 
 def test_expand_noalloc_rejects_sizes_beyond_the_array():
+    """Correctly sized tensors, so that the library itself (not the binding's
+    size check) rejects the problem: too large for the fixed array, or an odd band."""
     from paper_1807_05117_gb300 import blr
+    for n, band in (((192, 224, 192), (48, 48, 48)), ((16, 16, 16), (5, 4, 4))):
+        vt = torch.zeros((3,) + band, dtype=torch.complex64, device="cuda")
+        v = torch.zeros((3,) + n, dtype=torch.float32, device="cuda")
+        with pytest.raises(blr.BlrError) as ei:
+            blr.blr_expand_noalloc(n, band, vt, v)
+        assert ei.value.code == blr.BLR_EINVAL
+    # a wrongly sized output is caught by the binding before any call
     vt = torch.zeros((3, 4, 4, 4), dtype=torch.complex64, device="cuda")
-    v = torch.zeros(4, dtype=torch.float32, device="cuda")
-    with pytest.raises(blr.BlrError) as ei:
-        blr.blr_expand_noalloc((192, 224, 192), (48, 48, 48), vt, v)
-    assert ei.value.code == blr.BLR_EINVAL
-    with pytest.raises(blr.BlrError) as ei:
-        blr.blr_expand_noalloc((16, 16, 16), (5, 4, 4), vt, v)
-    assert ei.value.code == blr.BLR_EINVAL
+    with pytest.raises(ValueError):
+        blr.blr_expand_noalloc((16, 16, 16), (4, 4, 4), vt,
+                               torch.zeros(4, dtype=torch.float32, device="cuda"))
