@@ -65,7 +65,7 @@ ADJ_BYTES = lambda nt: ((36 + 44 + 48 * (nt - 2)) if nt > 1 else 32)
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one interior adjoint-step
 # launch (k_adjoint_wide<0, 1, 1>, kept state gradient) at 128^3 from an ncu
-# capture (profiles/k_adjoint_wide_128cube.md), valid only while the device code
+# capture of that launch, valid only while the device code
 # of csrc/sweeps.cu (the text above its host-side marker line) is the code the
 # capture was taken from: SHA-256 of that text.
 SWEEPS_HOST_MARKER = "// ==== host side: launch shapes, launchers, sweep orchestration, autotuner ===="

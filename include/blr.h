@@ -344,6 +344,16 @@ unsigned long long blr_kernel_launches(void);
  * set-aside to hold it).  Returns BLR_EINVAL for a NULL plan or vals. */
 int blr_plan_tuning(blr_plan_t plan, int *vals, int n);
 
+/* Test hook (no counterpart in the paper): while `on` is non-zero, every launch
+ * of the pipelined tensor-core DFT kernel (BLR_MIXED plans) first waits about
+ * 1 ms on a barrier that nothing arrives at, before it issues any copy or MMA.
+ * The wait expires, the launch frees its tensor memory, writes no output and
+ * latches BLR_ETIMEOUT (returned by blr_status / blr_newton), exactly as when a
+ * real bounded wait of the kernel runs out.  It exists so that the timeout path
+ * can be tested without a fault; the waits that guard copies or MMAs in flight
+ * are never shortened.  Process-wide; returns BLR_OK. */
+int blr_test_expire_waits(int on);
+
 /* Human-readable text for a status code (static storage). */
 const char *blr_strerror(int code);
 

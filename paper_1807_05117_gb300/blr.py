@@ -76,6 +76,7 @@ _SIGS = {
     "blr_newton": (_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                    ctypes.POINTER(blr_report), _P),
     "blr_status": (_P, _P),
+    "blr_test_expire_waits": (ctypes.c_int,),
     "blr_plan_tuning": (_P, ctypes.POINTER(ctypes.c_int), ctypes.c_int),
     "blr_batch_create": (ctypes.POINTER(blr_params), ctypes.c_int, ctypes.POINTER(_P)),
     "blr_batch_destroy": (_P,),
@@ -364,6 +365,11 @@ def blr_newton(plan, vt, max_newton, max_pcg, gtol, forcing=-1.0, stream=None,
 
 def blr_status(plan, stream=None) -> int:
     return int(_lib.blr_status(_P(plan), _stream(stream)))
+
+
+def blr_test_expire_waits(on: bool):
+    """Test hook: tensor-core DFT launches time out on purpose (include/blr.h)."""
+    _check(_lib.blr_test_expire_waits(1 if on else 0), "blr_test_expire_waits")
 
 
 class Plan:

@@ -559,16 +559,26 @@ int blr_newton(blr_plan_t P, float *vt, int max_newton, int max_pcg, double gtol
     memset(&R, 0, sizeof(R));
     const size_t vbytes = P->nfloat * sizeof(float);
     int flags = 0, rc;
-    BLR_CK(cudaMemsetAsync(P->dstatus, 0, sizeof(int), s));
-    BLR_CK(cudaMemcpyAsync(P->vtmp, vt, vbytes, cudaMemcpyDefault, s));
-    if (P->p.incompressible && (rc = vec_leray(P, P->vtmp, P->vtmp, s))) return rc;
-    if ((rc = state_at(P, P->vtmp, nullptr, s))) return rc;
+    // a failure before the first update still reports (status, counts)
+    auto fail = [&](int code) {
+        R.status = code;
+        if (rep) *rep = R;
+        return code;
+    };
+    if (cudaMemsetAsync(P->dstatus, 0, sizeof(int), s) != cudaSuccess ||
+        cudaMemcpyAsync(P->vtmp, vt, vbytes, cudaMemcpyDefault, s) != cudaSuccess)
+        return fail(BLR_ECUDA);
+    if (P->p.incompressible && (rc = vec_leray(P, P->vtmp, P->vtmp, s))) return fail(rc);
+    if ((rc = state_at(P, P->vtmp, nullptr, s))) return fail(rc);
     R.n_state = 1;
-    if ((rc = gradient_here(P, P->g, s))) return rc;
-    if ((rc = vec_maxabs(P, P->g, P->dsc + SC_GINF, s))) return rc;
-    if ((rc = vec_dot(P, P->g, P->g, nullptr, P->dsc + SC_DOT, s))) return rc;
-    if ((rc = fetch_scalars(P, s, &flags))) return rc;
-    if ((rc = flags_to_status(flags))) return rc;
+    if ((rc = gradient_here(P, P->g, s))) return fail(rc);
+    if ((rc = vec_maxabs(P, P->g, P->dsc + SC_GINF, s))) return fail(rc);
+    if ((rc = vec_dot(P, P->g, P->g, nullptr, P->dsc + SC_DOT, s))) return fail(rc);
+    if ((rc = fetch_scalars(P, s, &flags))) return fail(rc);
+    if ((rc = flags_to_status(flags))) {
+        R.energy0 = R.energy = P->hsc[SC_E];
+        return fail(rc);
+    }
     double E = P->hsc[SC_E];
     const double g0inf = P->hsc[SC_GINF], g0n = sqrt(P->hsc[SC_DOT]);
     double ginf = g0inf, gn = g0n;
@@ -611,7 +621,10 @@ int blr_newton(blr_plan_t P, float *vt, int max_newton, int max_pcg, double gtol
             ++R.n_state;
             break;
         }
-        BLR_CK(cudaMemcpyAsync(P->vtmp, P->trial, vbytes, cudaMemcpyDeviceToDevice, s));
+        if (cudaMemcpyAsync(P->vtmp, P->trial, vbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+            rc = BLR_ECUDA;
+            break;
+        }
         ++R.newton_iters;
         if ((rc = gradient_here(P, P->g, s))) break;
         if ((rc = vec_maxabs(P, P->g, P->dsc + SC_GINF, s))) break;
@@ -620,8 +633,9 @@ int blr_newton(blr_plan_t P, float *vt, int max_newton, int max_pcg, double gtol
         ginf = P->hsc[SC_GINF];
         gn = sqrt(P->hsc[SC_DOT]);
     }
-    BLR_CK(cudaMemcpyAsync(vt, P->vtmp, vbytes, cudaMemcpyDefault, s));
-    BLR_CK(cudaStreamSynchronize(s));
+    if ((cudaMemcpyAsync(vt, P->vtmp, vbytes, cudaMemcpyDefault, s) != cudaSuccess ||
+         cudaStreamSynchronize(s) != cudaSuccess) && !rc)
+        rc = BLR_ECUDA;
     R.energy = E;
     R.grad_inf_rel = g0inf > 0 ? ginf / g0inf : 0.0;
     R.status = rc;

@@ -17,6 +17,8 @@
 #include <string.h>
 #include <cuda_bf16.h>
 
+#include <atomic>
+
 #include "blr_internal.cuh"
 
 namespace {
@@ -115,6 +117,8 @@ struct TcArgs {
     float scale;
     int mode;                // 0 store scale*acc; 1 displacement (clamp + flags)
     int *status;
+    int probe;               // test hook (blr_test_expire_waits): a bounded wait that
+                             // expires before anything is issued (k_tc_pipe)
 };
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, int count) {
@@ -139,8 +143,10 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
-// Bounded wait for the phase of the given parity; false after ~2 s.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait for the phase of the given parity; false after `cycles` SM clocks
+// (default ~2 s).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          long long cycles = 4000000000LL) {
     uint32_t done = 0;
     const long long t0 = clock64();
     while (true) {
@@ -151,9 +157,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
             : "r"(bar), "r"(parity)
             : "memory");
         if (done) return true;
-        if (clock64() - t0 > 4000000000LL) return false;
+        if (clock64() - t0 > cycles) return false;
     }
 }
+
+// Length of the test hook's wait (about 1 ms at 2 GHz).
+constexpr long long TC_PROBE_CYCLES = 2000000LL;
 
 // Persistent: each CTA loads the table once, then walks column tiles
 // t = blockIdx.x, blockIdx.x + gridDim.x, ...; with two staging buffers the next
@@ -418,7 +427,7 @@ constexpr int TP_CONV = 6, TP_EPI = 8;                  // converter / epilogue 
 constexpr int TP_MMA_WARP = TP_CONV + TP_EPI;          // warp 14
 constexpr int TP_THREADS = (TP_MMA_WARP + 1) * 32;     // 480
 constexpr int TP_CT = TP_CONV * 32;                    // converter threads
-constexpr int TP_NBAR = 13;
+constexpr int TP_NBAR = 14;   // the last one: the test hook's, never arrived at
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -483,10 +492,10 @@ k_tc_pipe(TcArgs p, const __grid_constant__ CUtensorMap xmap) {
     float *sE = reinterpret_cast<float *>(sB + 4 * b_bytes);   // [4 warps][32 x 32]
     uint64_t *bars = reinterpret_cast<uint64_t *>(sE + TP_EPI * 1024);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + TP_NBAR);
-    __shared__ int s_fail, s_issued;
+    __shared__ int s_fail, s_issued, s_table;
     const uint32_t b0 = smem_u32(bars);
     // barriers: 0 table; 1+s stage full; 3+s stage free; 5+s B full; 7+s B free;
-    // 9+s accumulator full; 11+s accumulator free
+    // 9+s accumulator full; 11+s accumulator free; 13 test hook
     auto BAR = [&](int i) { return b0 + 8u * (uint32_t)i; };
     const int acc_cols = p.mtiles * p.ntile;
     int n = 0;   // tiles of this CTA
@@ -508,19 +517,30 @@ k_tc_pipe(TcArgs p, const __grid_constant__ CUtensorMap xmap) {
             mbar_init(BAR(9 + sl), 1);
             mbar_init(BAR(11 + sl), TP_EPI * 32);
         }
+        mbar_init(BAR(13), 1);
         asm volatile("fence.mbarrier_init.release.cluster;");
         s_fail = 0;
         s_issued = 0;
+        s_table = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tslot;
+    // Test hook: a bounded wait on a barrier nothing arrives at, taken while no
+    // copy and no MMA has been issued, so that its expiry leaves nothing in flight.
+    // The CTA then takes the timeout path below (no roles run, TMEM freed).
+    if (p.probe) {
+        const bool expired = tid == 0 ? !mbar_wait(BAR(13), 0u, TC_PROBE_CYCLES) : false;
+        if (__syncthreads_or(expired)) n = 0;
+        if (tid == 0 && expired) s_fail = 1;
+    }
     // the table is written once at plan creation (which synchronises the device),
     // so it is fetched before the wait for the previous kernel in the stream
-    if (tid == 0) {
+    if (tid == 0 && n > 0) {
         mbar_expect_arrive(BAR(0), (uint32_t)all_tab);
         bulk_g2s(smem_u32(sA), p.tab, (uint32_t)all_tab, BAR(0));
+        s_table = 1;
     }
     pdl_wait();
 
@@ -606,7 +626,7 @@ k_tc_pipe(TcArgs p, const __grid_constant__ CUtensorMap xmap) {
             mbar_arrive(BAR(11 + sl));   // accumulator free
         }
         if (flags) atomicOr(p.status, flags);
-    } else if (lane == 0) {
+    } else if (lane == 0 && n > 0) {
         // ---- MMA issue
         const uint32_t idesc = umma_idesc(TC_M, p.ntile);
         ok = mbar_wait(BAR(0), 0u);   // table
@@ -649,7 +669,7 @@ k_tc_pipe(TcArgs p, const __grid_constant__ CUtensorMap xmap) {
         // time to land before the CTA leaves
         atomicOr(p.status, BLR_FLAG_TIMEOUT);
         for (int i = 0; i < s_issued; ++i) mbar_wait(BAR(1 + (i & 1)), (uint32_t)(i >> 1) & 1u);
-        mbar_wait(BAR(0), 0u);
+        if (s_table) mbar_wait(BAR(0), 0u);
     }
     __syncthreads();
     if (warp == 0)
@@ -845,6 +865,10 @@ TcGeom tc_geometry(const blr_plan *P, int kind) {
 
 int plan_sms(const blr_plan *P) { return P->sms > 0 ? P->sms : 148; }
 
+// blr_test_expire_waits: the pipelined kernel's test hook, for every launch
+// while set.
+std::atomic<int> g_tc_probe{0};
+
 bool tc_kind_ok(const blr_plan *P, int kind) {
     const TcGeom g = tc_geometry(P, kind);
     int nt, ns;
@@ -940,6 +964,7 @@ int tc_run(blr_plan *P, int kind, const float *X, float *D, float scale, int mod
     a.scale = scale;
     a.mode = mode;
     a.status = P->dstatus;
+    a.probe = g_tc_probe.load(std::memory_order_relaxed);
     if (pipe) {
         a.tmem_cols = pow2_at_least(2 * a.mtiles * a.ntile);
         BLR_CK(cudaFuncSetAttribute(k_tc_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -966,4 +991,9 @@ int tc_axis1(blr_plan *P, int project, const float *X, float *D, float scale, in
 
 int tc_axis2(blr_plan *P, int project, const float *X, float *D, cudaStream_t s) {
     return tc_run(P, project ? 3 : 2, X, D, 1.f, 0, s);
+}
+
+extern "C" int blr_test_expire_waits(int on) {
+    g_tc_probe.store(on ? 1 : 0, std::memory_order_relaxed);
+    return BLR_OK;
 }

@@ -4,7 +4,8 @@ CUDA graph, autotuned tile length).  Each pair's arithmetic equals a single
 plan's, so gradients, Hessian-vector products and whole registrations must be
 bit-identical to per-pair calls: on six small pairs, and on the 64-pair
 workload (grids 64^3 to 160x192x160, bands 16^3 to 32^3) with one pair of every
-grid size rerun alone."""
+grid size rerun alone.  Batched pairs are also compared with the FP64 oracle
+directly (gradient, HVP and a short registration)."""
 
 import os
 
@@ -120,3 +121,76 @@ def test_uneven_batch_of_64_pairs():
         assert torch.equal(vb[i], vs)
         pl.close()
     batch.close()
+
+
+# --- batched pairs against the FP64 oracle ------------------------------------
+# Shapes of the many-pair workload (the largest grid with band 24^3, 96^3 with
+# band 16^3, 64^3 with band 32^3 and 128^3 with band 24^3): the batched gradient
+# and Gauss-Newton HVP of each pair within the FP32 bounds of the single-plan
+# parity tests (relative L2 1e-4), so a fault shared by the batched and the
+# single-plan code (tile tails of these grids, their bands) cannot pass.
+
+# coefficient bounds give 0.56-0.64 voxel per step (both cell choices, all 27
+# transpose neighbours)
+ORACLE_PAIRS = [((160, 192, 160), (24, 24, 24), 95.0), ((96, 96, 96), (16, 16, 16), 62.0),
+                ((64, 64, 64), (32, 32, 32), 120.0), ((128, 128, 128), (24, 24, 24), 100.0)]
+
+
+@pytest.mark.slow
+def test_batched_pairs_match_the_oracle():
+    from oracle import blr_oracle as O
+    from paper_1807_05117_gb300 import blr
+    nt = 10
+    data = []
+    for i, (n, band, bound) in enumerate(ORACLE_PAIRS):
+        I0, I1, _ = synth.phantom_pair(n, 5100 + i, max_disp=5.0)
+        vt = synth.random_coefficients(band, 5200 + i, bound=bound)
+        dv = synth.random_direction(band, 5300 + i)
+        data.append(synth.as_device_inputs(I0, I1, vt, dv))
+    batch = blr.Batch([(n, band) for n, band, _ in ORACLE_PAIRS], nt)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    for i, ((I0f, _), (I1f, _), _, _) in enumerate(data):
+        batch.set_images(i, dev(I0f), dev(I1f))
+    vts = [dev(d[2][0]) for d in data]
+    dvs = [dev(d[3][0]) for d in data]
+    gb = [torch.empty_like(v) for v in vts]
+    hb = [torch.empty_like(v) for v in vts]
+    batch.gradient(vts, gb)
+    batch.hessvec(dvs, hb)
+    torch.cuda.synchronize()
+    batch.close()
+    for (n, band, _), d, g, h in zip(ORACLE_PAIRS, data, gb, hb):
+        (_, I0d), (_, I1d), (_, vtd), (_, dvd) = d
+        pt = O.Point(vtd, I0d, I1d, O.Params(n, band, nt))
+        assert pt.cfl < 1.0
+        g_ref = pt.gradient()[0]
+        h_ref = pt.gn_hessvec(dvd)[0]
+        eg = np.linalg.norm(g.cpu().numpy() - g_ref) / np.linalg.norm(g_ref)
+        eh = np.linalg.norm(h.cpu().numpy() - h_ref) / np.linalg.norm(h_ref)
+        assert eg <= 1e-4 and eh <= 1e-4, (n, band, eg, eh)
+
+
+def test_batched_newton_matches_the_oracle():
+    """Two small uneven pairs (16^3 / band 4^3, 24x20x16 / band 6^3), 3 Newton
+    updates each: Newton counts equal, final energy within 1e-3, PCG totals
+    within +-1 per update (the single-plan registration bars)."""
+    from oracle import blr_oracle as O
+    from paper_1807_05117_gb300 import blr
+    shapes, nt = [((16, 16, 16), (4, 4, 4)), ((24, 20, 16), (6, 6, 6))], 4
+    batch = blr.Batch(shapes, nt)
+    refs, vts = [], []
+    for i, (n, band) in enumerate(shapes):
+        I0, I1, _ = synth.blob_pair(n, 5400 + i, max_disp=2.0)
+        (I0f, I0d), (I1f, I1d) = synth.as_device_inputs(I0, I1)
+        batch.set_images(i, torch.from_numpy(I0f).cuda(), torch.from_numpy(I1f).cuda())
+        vts.append(torch.zeros((3,) + band, dtype=torch.complex64, device="cuda"))
+        refs.append(O.newton(np.zeros((3,) + band, complex), I0d, I1d, O.Params(n, band, nt),
+                             max_newton=3, max_pcg=6, gtol=1e-6))
+    reps = batch.newton(vts, 3, 6, 1e-6)
+    batch.close()
+    for r, ref in zip(reps, refs):
+        assert r.status == blr.BLR_OK
+        assert r.newton_iters == ref.iterations
+        assert abs(r.energy0 - ref.energies[0]) <= 1e-5 * ref.energies[0]
+        assert abs(r.energy - ref.energies[-1]) <= 1e-3 * ref.energies[-1]
+        assert abs(r.pcg_iters - sum(ref.pcg_iterations)) <= ref.iterations
