@@ -480,7 +480,11 @@ class DeformationPoint:
       E = 1/2 <A v~, v~> + sigma^-2 ||m(1) - I1||^2.
     Stationary velocity; Gauss-Newton and full Newton Hessians."""
 
-    def __init__(self, vt: np.ndarray, I0: np.ndarray, I1: np.ndarray, p: Params):
+    def __init__(self, vt: np.ndarray, I0: np.ndarray, I1: np.ndarray, p: Params,
+                 displacement_factor=None):
+        """displacement_factor: None, or an array multiplying the displacement
+        elementwise (the tests' probes of how the results respond to a small
+        relative change of d)."""
         if not p.stationary:
             raise NotImplementedError("the deformation variant takes a stationary velocity")
         self.p = p
@@ -491,6 +495,8 @@ class DeformationPoint:
         self.I1 = np.asarray(I1, dtype=np.float64)
         self.A = regulariser_weights(p)
         self.d = displacement(self.vt, p)
+        if displacement_factor is not None:
+            self.d = self.d * displacement_factor
         self.cfl = cfl_number(self.d)
         self.stencil = Stencil(self.d)
         u = [np.zeros((3,) + tuple(p.n))]

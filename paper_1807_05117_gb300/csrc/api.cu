@@ -159,7 +159,14 @@ size_t layout(blr_plan *P, char *base) {
     P->A = a.take<float>(P->nb);
     P->dft_big = a.take<float>((size_t)3 * P->B1 * P->N2 * P->N3 * 2);
     P->dft_small = a.take<float>((size_t)3 * P->B1 * P->B2 * P->N3 * 2);
-    if (P->p.precision == BLR_MIXED) {
+    for (int k = 0; k < 4; ++k) P->fz_tab[k] = nullptr;
+    P->fz_buf = nullptr;
+    if (P->p.precision == BLR_MIXED && fz_supported(P)) {
+        for (int k = 0; k < 4; ++k) P->fz_tab[k] = a.take<uint8_t>(fz_table_bytes(P, k));
+        P->fz_buf = a.take<float>(fz_buffer_floats(P));
+        P->tc_tab_expand = P->tc_tab_project = nullptr;
+        P->tc_tab2_expand = P->tc_tab2_project = nullptr;
+    } else if (P->p.precision == BLR_MIXED) {
         P->tc_tab_expand = a.take<uint8_t>(tc_table_bytes(P, 0));
         P->tc_tab_project = a.take<uint8_t>(tc_table_bytes(P, 1));
         if (tc_axis2_supported(P)) {
@@ -390,7 +397,7 @@ int plan_create(const blr_params *p, bool grad_cache, blr_plan **out) {
         return BLR_ECUDA;
     }
     sweep_setup(P);   // SM count and sweep shapes (the tensor-core tile shapes use the SM count)
-    if (p->precision == BLR_MIXED && !tc_supported(P)) {
+    if (p->precision == BLR_MIXED && !fz_supported(P) && !tc_supported(P)) {
         delete P;
         return BLR_EINVAL;
     }
@@ -446,6 +453,7 @@ int plan_create(const blr_params *p, bool grad_cache, blr_plan **out) {
     if (cudaMemset(base, 0, bytes) != cudaSuccess ||
         dft_init_tables(P, 0) != BLR_OK ||
         (p->precision == BLR_MIXED && tc_init_tables(P, 0) != BLR_OK) ||
+        (P->fz_tab[0] && fz_init_tables(P, 0) != BLR_OK) ||
         sweep_autotune(P, 0) != BLR_OK || cudaDeviceSynchronize() != cudaSuccess) {
         cudaFreeHost(P->hlive);
         cudaFreeHost(P->hsc);

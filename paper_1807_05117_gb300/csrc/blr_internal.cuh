@@ -179,6 +179,9 @@ struct blr_plan {
     uint8_t *tc_tab_project;
     uint8_t *tc_tab2_expand;   // BLR_MIXED axis-2 stages, or nullptr (SIMT axis 2)
     uint8_t *tc_tab2_project;
+    uint8_t *fz_tab[4];        // BLR_MIXED fused transforms (dft_fused.cu), or nullptr:
+                               // then the stages above are not used
+    float *fz_buf;             // their band-sized intermediate
 
     // Krylov / Newton vectors (nfloat each)
     float *g, *r, *pv, *q, *x, *trial, *step, *vtmp;
@@ -245,6 +248,16 @@ int tc_init_tables(blr_plan *P, cudaStream_t s);
 int tc_axis1(blr_plan *P, int project, const float *X, float *D, float scale, int mode,
              cudaStream_t s);
 int tc_axis2(blr_plan *P, int project, const float *X, float *D, cudaStream_t s);
+
+// dft_fused.cu (BLR_MIXED): iota and pi as a band-sized axis-1 stage plus one
+// tensor-core kernel over (component, x1 plane, x2 tile) units
+bool fz_supported(const blr_plan *P);
+size_t fz_table_bytes(const blr_plan *P, int kind);
+size_t fz_buffer_floats(const blr_plan *P);
+int fz_init_tables(blr_plan *P, cudaStream_t s);
+int fz_expand(blr_plan *P, const float *vt, float *out, float scale, int mode, cudaStream_t s);
+int fz_project(blr_plan *P, const float *f, float *ft, const float *vadd, float areg,
+               cudaStream_t s);
 
 // sweeps.cu
 int sweep_setup(blr_plan *P);

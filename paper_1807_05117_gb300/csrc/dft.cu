@@ -365,6 +365,11 @@ int dft_init_tables(blr_plan *P, cudaStream_t s) {
 }
 
 int dft_expand(blr_plan *P, const float *vt, float *out, int mode, cudaStream_t s) {
+    if (P->fz_tab[0]) {   // mixed precision, fused tensor-core transform
+        int rc = fz_expand(P, vt, out, mode == 0 ? 1.f : -P->dt, mode, s);
+        if (rc || mode == 0 || out != P->d) return rc;
+        return sweep_pack_d4(P, s);
+    }
     const int rows = 3 * P->B1 * P->B2;
     // stage A
     dim3 ga((unsigned)ceil_div_ll(rows, XR), (unsigned)ceil_div_ll(P->N3, XC));
@@ -407,6 +412,7 @@ int dft_expand(blr_plan *P, const float *vt, float *out, int mode, cudaStream_t 
 
 int dft_project(blr_plan *P, const float *f, float *ft, const float *vadd, cudaStream_t s,
                 float areg) {
+    if (P->fz_tab[0]) return fz_project(P, f, ft, vadd, areg, s);
     const long long ncol = (long long)P->N2 * P->N3;
     // stage C'
     if (P->p.precision == BLR_MIXED) {

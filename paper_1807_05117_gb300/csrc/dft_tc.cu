@@ -20,77 +20,13 @@
 #include <atomic>
 
 #include "blr_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace {
 
 constexpr int TC_THREADS = 256;
 constexpr int TC_M = 128;
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// Byte offset of the 16-byte chunk (row r, k-chunk kc = k/8) in a K-major,
-// 128-byte-swizzled BF16 tile with `rows` rows: 64-element K atoms stacked
-// along K, 8-row groups of 1024 bytes, chunk index XOR-ed with the row.
-__host__ __device__ __forceinline__ uint32_t swz_chunk(int r, int kc, int rows) {
-    return (uint32_t)((kc >> 3) * rows * 128 + (r >> 3) * 1024 + (r & 7) * 128 +
-                      (((kc & 7) ^ (r & 7)) << 4));
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (stride byte offset), descriptor version 1.
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
-    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-
-// Instruction descriptor for kind::f16: FP32 accumulator, BF16 A and B, both
-// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-__host__ __device__ constexpr uint32_t umma_idesc(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-           ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void umma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                          uint32_t accumulate) {
-    asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t *r) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;");
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<uint32_t *>(&h);
-}
-
-// Split 8 floats into BF16 hi and lo halves, each packed into a uint4.
-__device__ __forceinline__ void split8(const float *x, uint4 &hi, uint4 &lo) {
-    float h[8], l[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        h[i] = __bfloat162float(__float2bfloat16_rn(x[i]));
-        l[i] = x[i] - h[i];
-    }
-    hi = make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]),
-                    pack_bf16(h[6], h[7]));
-    lo = make_uint4(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]), pack_bf16(l[4], l[5]),
-                    pack_bf16(l[6], l[7]));
-}
 
 // An FP32 staging slot, rounded up to 1024 bytes so every slot (a TMA
 // destination) and the swizzled tiles after them stay aligned.
@@ -121,48 +57,6 @@ struct TcArgs {
                              // expires before anything is issued (k_tc_pipe)
 };
 
-__device__ __forceinline__ void mbar_init(uint32_t bar, int count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_arrive(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-}
-// One 2-D tile of the tensor map (x = column, y = row) into shared memory.
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
-                                            uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-
-// Bounded wait for the phase of the given parity; false after `cycles` SM clocks
-// (default ~2 s).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
-                                          long long cycles = 4000000000LL) {
-    uint32_t done = 0;
-    const long long t0 = clock64();
-    while (true) {
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            "selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if (clock64() - t0 > cycles) return false;
-    }
-}
-
-// Length of the test hook's wait (about 1 ms at 2 GHz).
-constexpr long long TC_PROBE_CYCLES = 2000000LL;
 
 // Persistent: each CTA loads the table once, then walks column tiles
 // t = blockIdx.x, blockIdx.x + gridDim.x, ...; with two staging buffers the next
@@ -429,20 +323,6 @@ constexpr int TP_THREADS = (TP_MMA_WARP + 1) * 32;     // 480
 constexpr int TP_CT = TP_CONV * 32;                    // converter threads
 constexpr int TP_NBAR = 14;   // the last one: the test hook's, never arrived at
 
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-        "%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;");
-}
 
 // Shared memory of the pipelined kernel (tc_pipe_smem on the host).
 
@@ -865,10 +745,6 @@ TcGeom tc_geometry(const blr_plan *P, int kind) {
 
 int plan_sms(const blr_plan *P) { return P->sms > 0 ? P->sms : 148; }
 
-// blr_test_expire_waits: the pipelined kernel's test hook, for every launch
-// while set.
-std::atomic<int> g_tc_probe{0};
-
 bool tc_kind_ok(const blr_plan *P, int kind) {
     const TcGeom g = tc_geometry(P, kind);
     int nt, ns;
@@ -877,6 +753,10 @@ bool tc_kind_ok(const blr_plan *P, int kind) {
 }
 
 }  // namespace
+
+// blr_test_expire_waits: the tensor-core kernels' test hook (k_tc_pipe here, k_fx
+// and k_fp in dft_fused.cu), for every launch while set.
+std::atomic<int> g_tc_probe{0};
 
 size_t tc_table_bytes(const blr_plan *P, int kind) {
     const TcGeom g = tc_geometry(P, kind);

@@ -7,7 +7,7 @@ inputs.  Tolerances (relative L2):
               5e-4 on the gradient, the HVP and the PCG iterates;
 a full registration's final energy within 1e-3 with PCG iteration counts within
 +-1 per Newton step.  Cases: ragged tiles, a grid smaller than one tile, one
-time step, the 32^3 blob registration, the 128^3 phantom (band 32^3) and the
+time step, two x2 tiles of the fused transforms, the 32^3 blob registration, the 128^3 phantom (band 32^3) and the
 192x224x192 phantom with band 48^3 (gradient and HVP against the oracle in both
 precisions; a 10-step registration mixed against FP32)."""
 
@@ -78,6 +78,9 @@ CASES = {
     "tiny": dict(n=(3, 5, 7), band=(2, 2, 4), nt=3, seed=202, bound=3.0),
     # a single time step: first and last sweep steps coincide
     "nt1": dict(n=(16, 12, 20), band=(4, 4, 4), nt=1, seed=303, bound=2.0, sigma=0.5),
+    # more than 128 x2 rows: two x2 tiles in the fused tensor-core transforms, the
+    # second one partly filled
+    "twotile": dict(n=(6, 140, 20), band=(4, 6, 8), nt=3, seed=404, bound=7.0),
 }
 
 
