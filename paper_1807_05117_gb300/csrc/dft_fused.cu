@@ -39,7 +39,6 @@
 
 namespace {
 
-constexpr int FZ_THREADS = 256;   // 8 warps
 constexpr int FZ_M = 128;         // rows of every MMA (x2 tile, or (j3, re|im) padded)
 constexpr int PZ_MAX_SMEM = 227 * 1024;
 
@@ -71,36 +70,62 @@ FzGeom fz_geometry(const blr_plan *P) {
 // bytes of one hi or lo BF16 operand tile of `rows` x `k`
 __host__ __device__ inline size_t tile_bytes(int rows, int k) { return (size_t)rows * k * 2; }
 
-// Shared memory: tables, then the operand region (expand: B operand of GEMM 2,
-// then A operand of GEMM 3, then the epilogue transposes, one after the other in
-// the same bytes), then three barriers and the TMEM slot.
-size_t fx_smem(const FzGeom &g) {
-    const size_t t2 = 2 * tile_bytes(FZ_M, g.K2e), t3 = 2 * tile_bytes(g.N3e, g.K3e);
-    size_t r = 2 * tile_bytes(g.N2e, g.K2e);
-    r = r > 2 * tile_bytes(FZ_M, g.K3e) ? r : 2 * tile_bytes(FZ_M, g.K3e);
-    r = r > (size_t)(FZ_THREADS / 32) * 4096 ? r : (size_t)(FZ_THREADS / 32) * 4096;
-    return 1024 + t2 + t3 + r + 4 * 8 + 16;
-}
-
-// project: tables, the A operand region (field tile, then the transposed Q3),
-// and the FP32 staging of Q3 (then of GEMM 2's result).
-inline int qpitch(const FzGeom &g) { return g.N3p + 4; }
-inline int epitch(const FzGeom &g) { return g.N2p + 1; }
-size_t fp_smem(const FzGeom &g) {
-    const size_t t3 = 2 * tile_bytes(g.N3p, g.K3p), t2 = 2 * tile_bytes(g.N2p, FZ_M);
-    const size_t ka = g.K3p > FZ_M ? g.K3p : FZ_M;
-    const size_t a = 2 * tile_bytes(FZ_M, (int)ka);
-    size_t q = (size_t)FZ_M * qpitch(g) * 4;
-    const size_t e = (size_t)FZ_M * epitch(g) * 4;
-    q = q > e ? q : e;
-    return 1024 + t3 + t2 + a + q + 4 * 8 + 16;
-}
-
 int pow2_cols(int v) {
     int p = 32;
     while (p < v) p <<= 1;
     return p;
 }
+
+size_t up1k(size_t v) { return (v + 1023) & ~(size_t)1023; }
+
+// Launch shape of a fused kernel: G warpgroups of 128 threads, each with `gbytes`
+// of operand buffer and `gcols` TMEM columns, after `fixed` bytes of tables.
+struct FzShape {
+    int G, gcols, tmem_cols;
+    size_t gbytes, smem;
+};
+
+// G: the most warpgroups that fit (shared memory, 512 TMEM columns), at most 4 and
+// at most the units a CTA gets when every SM has one (gmax, 0: no cap).
+FzShape fz_shape(size_t fixed, size_t gbytes, int gcols, size_t tail, int gmax = 0) {
+    FzShape sh;
+    sh.gbytes = up1k(gbytes);
+    sh.gcols = gcols;
+    sh.G = 4;
+    while (sh.G > 0 && (fixed + sh.G * sh.gbytes + tail > (size_t)PZ_MAX_SMEM || sh.G * gcols > 512))
+        --sh.G;
+    if (gmax > 0 && sh.G > gmax) sh.G = gmax;
+    sh.tmem_cols = pow2_cols(sh.G * gcols);
+    sh.smem = fixed + sh.G * sh.gbytes + tail;
+    return sh;
+}
+
+// expand: tables T2e (A of GEMM 2) and T3e (B of GEMM 3); per warpgroup the B
+// operand of GEMM 2, then the A operand of GEMM 3, then four epilogue transposes,
+// one after the other in the same bytes; D3 reuses the TMEM columns of D2.
+FzShape fx_shape(const FzGeom &g, int B2, int B3, int gmax = 0) {
+    const size_t fixed = 1024 + 2 * tile_bytes(FZ_M, g.K2e) + 2 * tile_bytes(g.N3e, g.K3e);
+    size_t r = 2 * tile_bytes(g.N2e, g.K2e) + (size_t)B2 * B3 * 8;   // + the P1 slab
+    r = r > 2 * tile_bytes(FZ_M, g.K3e) ? r : 2 * tile_bytes(FZ_M, g.K3e);
+    r = r > 4 * 4096 ? r : 4 * 4096;
+    const int cols = pow2_cols(g.N2e > g.N3e ? g.N2e : g.N3e);
+    return fz_shape(fixed, r, cols, 8 * (2 + 2 * 4) + 16, gmax);
+}
+
+// project: tables T3p (A of GEMM 3', N3p rows, plus the rows the MMA reads past
+// them) and T2p; per warpgroup a field chunk, then the A operand of GEMM 2' (N3p
+// rows), then the FP32 staging of its result; D2t reuses the columns of D3t.
+FzShape fp_shape(const FzGeom &g, int gmax = 0) {
+    const size_t slack = (size_t)(FZ_M - g.N3p) * 128;
+    const size_t fixed = 1024 + 2 * tile_bytes(g.N3p, g.K3p) + slack + 2 * tile_bytes(g.N2p, FZ_M);
+    size_t r = 2 * tile_bytes(FZ_M, 64);
+    r = r > 2 * tile_bytes(g.N3p, FZ_M) ? r : 2 * tile_bytes(g.N3p, FZ_M);
+    const size_t e = (size_t)g.N3p * (g.N2p + 1) * 4;
+    r = r > e ? r : e;
+    const int cols = pow2_cols(FZ_M > g.N2p ? FZ_M : g.N2p);
+    return fz_shape(fixed, r, cols, slack + 8 * (2 + 4) + 16, gmax);
+}
+
 
 // ---------------------------------------------------------------------------
 // Tables.  kind 0: expand GEMM 2 A operand, per x2 tile, rows x2, k = (C | S)(j2);
@@ -180,99 +205,171 @@ __device__ __forceinline__ void store_chunk(uint8_t *hi_tile, size_t tb, uint32_
 }
 
 // ---------------------------------------------------------------------------
-// k_ex1: P1[c][x1][j2 j3] = sum_j1 v~[c][j1][j2 j3] (cos + i sin)(2 pi k_j1 x1 / N1),
-// cos / sin from W1 (rows 2j = cos, 2j+1 = -sin).  A block owns 8 planes x1 and
-// 256 columns (j2, j3); each thread sums over j1 in order.
-constexpr int EX1_XB = 8;
+// k_ex1: P1[c][x1][col] = sum_j1 (cos + i sin)(2 pi k_j1 x1 / N1) v~[c][j1][col], col = (j2, j3),
+// a complex GEMM [N1 x B1] x [B1 x B2 B3] per component (cos / sin from W1, rows
+// 2j = cos, 2j+1 = -sin).  A block computes a 32 (x1) x 64 (col) tile; j1 runs in
+// chunks of 32 staged in shared memory, summed in order.  Thread (ty, tx) owns x1
+// rows 2 ty, 2 ty + 1 and columns tx + 16 q (q < 4): stores are coalesced.
+constexpr int EX_TX = 32, EX_TC = 64, EX_TK = 32;
+constexpr int EX_NE = EX_TK * EX_TX / 256, EX_NV = EX_TK * EX_TC / 256;   // loads per thread
 __global__ void __launch_bounds__(256)
 k_ex1(const float2 *__restrict__ vt, const float *__restrict__ W1, float2 *__restrict__ P1,
       int N1, int B1, int nb23) {
-    extern __shared__ float2 sE[];   // [B1][EX1_XB]
-    const int nxb = (N1 + EX1_XB - 1) / EX1_XB;
-    const int c = blockIdx.y / nxb, x1b = (blockIdx.y % nxb) * EX1_XB;
-    for (int i = threadIdx.x; i < B1 * EX1_XB; i += blockDim.x) {
-        const int j = i / EX1_XB, x1 = x1b + (i % EX1_XB);
-        sE[i] = x1 < N1 ? make_float2(W1[(2LL * j) * N1 + x1], -W1[(2LL * j + 1) * N1 + x1])
+    __shared__ float2 sE[EX_TK][EX_TX + 1];   // [j1][x1]
+    __shared__ float2 sV[EX_TK][EX_TC];       // [j1][col]
+    const int c = blockIdx.z, x0 = blockIdx.y * EX_TX, c0 = blockIdx.x * EX_TC;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    float2 acc[2][4];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[r][q] = make_float2(0.f, 0.f);
+    // chunk k0's operands into registers (every load issued before any is used)
+    float2 re[EX_NE], rv[EX_NV];
+    auto load_e = [&](int k0) {
+#pragma unroll
+        for (int s = 0; s < EX_NE; ++s) {
+            const int i = tid + 256 * s, kk = i / EX_TX, j = k0 + kk, x1 = x0 + i % EX_TX;
+            re[s] = (j < B1 && x1 < N1)
+                        ? make_float2(W1[(2LL * j) * N1 + x1], -W1[(2LL * j + 1) * N1 + x1])
                         : make_float2(0.f, 0.f);
-    }
+        }
+    };
+    auto load_v = [&](int k0) {
+#pragma unroll
+        for (int s = 0; s < EX_NV; ++s) {
+            const int i = tid + 256 * s, kk = i / EX_TC, j = k0 + kk, col = c0 + i % EX_TC;
+            rv[s] = (j < B1 && col < nb23) ? vt[((long long)c * B1 + j) * nb23 + col]
+                                           : make_float2(0.f, 0.f);
+        }
+    };
+    load_e(0);
     pdl_wait();   // v~ may come from the previous kernel
-    __syncthreads();
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
-    if (col >= nb23) return;
-    float2 acc[EX1_XB];
-#pragma unroll
-    for (int q = 0; q < EX1_XB; ++q) acc[q] = make_float2(0.f, 0.f);
-    const float2 *src = vt + (long long)c * B1 * nb23 + col;
-    for (int j = 0; j < B1; ++j) {
-        const float2 v = src[(long long)j * nb23];
-#pragma unroll
-        for (int q = 0; q < EX1_XB; ++q) {
-            const float2 e = sE[j * EX1_XB + q];
-            acc[q].x = fmaf(v.x, e.x, fmaf(-v.y, e.y, acc[q].x));
-            acc[q].y = fmaf(v.x, e.y, fmaf(v.y, e.x, acc[q].y));
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < EX1_XB; ++q)
-        if (x1b + q < N1) P1[((long long)c * N1 + x1b + q) * nb23 + col] = acc[q];
-}
-
-// ---------------------------------------------------------------------------
-// k_p1: pi(f)_c(j1, j2 j3) = sum_x1 sum_t Q2[c][x1][t][j2 j3] (cos - i sin)(2 pi k_j1 x1/N1)
-// (+ areg A(j) vadd).  A block owns 4 frequencies j1 and 128 columns; x1 is
-// summed in order, table pieces of 256 planes staged in shared memory.
-constexpr int P1_JB = 4, P1_XC = 256;
-__global__ void __launch_bounds__(128)
-k_p1(const float2 *__restrict__ Q2, const float *__restrict__ W1, float2 *__restrict__ ft,
-     const float *__restrict__ Aw, const float2 *__restrict__ vadd, float areg, int N1, int B1,
-     int MT, int nb23) {
-    __shared__ float2 sE[P1_XC * P1_JB];   // [x1][jj]
-    const int njb = (B1 + P1_JB - 1) / P1_JB;
-    const int c = blockIdx.y / njb, j1b = (blockIdx.y % njb) * P1_JB;
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
-    float2 acc[P1_JB];
-#pragma unroll
-    for (int q = 0; q < P1_JB; ++q) acc[q] = make_float2(0.f, 0.f);
-    bool waited = false;
-    for (int x0 = 0; x0 < N1; x0 += P1_XC) {
-        const int xn = min(P1_XC, N1 - x0);
+    load_v(0);
+    for (int k0 = 0; k0 < B1; k0 += EX_TK) {
         __syncthreads();
-        for (int i = threadIdx.x; i < xn * P1_JB; i += blockDim.x) {
-            const int xx = i / P1_JB, j = j1b + i % P1_JB, x1 = x0 + xx;
-            sE[i] = j < B1 ? make_float2(W1[(2LL * j) * N1 + x1], W1[(2LL * j + 1) * N1 + x1])
-                           : make_float2(0.f, 0.f);   // (cos, -sin)
+#pragma unroll
+        for (int s = 0; s < EX_NE; ++s) {
+            const int i = tid + 256 * s;
+            sE[i / EX_TX][i % EX_TX] = re[s];
         }
-        if (!waited) {
-            pdl_wait();   // Q2 comes from the previous kernel
-            waited = true;
+#pragma unroll
+        for (int s = 0; s < EX_NV; ++s) {
+            const int i = tid + 256 * s;
+            sV[i / EX_TC][i % EX_TC] = rv[s];
         }
         __syncthreads();
-        if (col < nb23) {
-            const float2 *src = Q2 + ((long long)c * N1 + x0) * MT * nb23 + col;
-            for (int xx = 0; xx < xn; ++xx) {
-                float2 q = src[(long long)xx * MT * nb23];
-                for (int t = 1; t < MT; ++t) {
-                    const float2 r = src[((long long)xx * MT + t) * nb23];
-                    q.x += r.x;
-                    q.y += r.y;
-                }
+        if (k0 + EX_TK < B1) {   // the next chunk's loads fly during this chunk's sums
+            load_e(k0 + EX_TK);
+            load_v(k0 + EX_TK);
+        }
+#pragma unroll 8
+        for (int kk = 0; kk < EX_TK; ++kk) {
+            const float2 e0 = sE[kk][2 * ty], e1 = sE[kk][2 * ty + 1];
 #pragma unroll
-                for (int jj = 0; jj < P1_JB; ++jj) {   // (qr + i qi)(cos - i sin)
-                    const float2 e = sE[xx * P1_JB + jj];
-                    acc[jj].x = fmaf(q.x, e.x, fmaf(-q.y, e.y, acc[jj].x));
-                    acc[jj].y = fmaf(q.y, e.x, fmaf(q.x, e.y, acc[jj].y));
-                }
+            for (int q = 0; q < 4; ++q) {
+                const float2 v = sV[kk][tx + 16 * q];
+                acc[0][q].x = fmaf(e0.x, v.x, fmaf(-e0.y, v.y, acc[0][q].x));
+                acc[0][q].y = fmaf(e0.x, v.y, fmaf(e0.y, v.x, acc[0][q].y));
+                acc[1][q].x = fmaf(e1.x, v.x, fmaf(-e1.y, v.y, acc[1][q].x));
+                acc[1][q].y = fmaf(e1.x, v.y, fmaf(e1.y, v.x, acc[1][q].y));
             }
         }
     }
-    if (!waited) pdl_wait();
-    if (col >= nb23) return;
 #pragma unroll
-    for (int jj = 0; jj < P1_JB; ++jj) {
-        const int j = j1b + jj;
-        if (j >= B1) continue;
+    for (int r = 0; r < 2; ++r) {
+        const int x1 = x0 + 2 * ty + r;
+        if (x1 >= N1) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int col = c0 + tx + 16 * q;
+            if (col < nb23) P1[((long long)c * N1 + x1) * nb23 + col] = acc[r][q];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_p1: pi(f)_c(j1, col) = sum_x1 (cos - i sin)(2 pi k_j1 x1 / N1) sum_t Q2[c][x1][t][col]
+// (+ areg A(j) vadd), a complex GEMM [B1 x N1] x [N1 x B2 B3] per component.  A
+// block computes a 16 (j1) x 32 (col) tile; x1 runs in chunks of 32 staged in
+// shared memory (the x2-tile partial sums added while staging), summed in order.
+// Thread (ty, tx) owns frequency j1 = ty and columns tx, tx + 16.
+constexpr int P1_TJ = 16, P1_TC = 32, P1_TK = 32;
+constexpr int P1_NE = P1_TK * P1_TJ / 256, P1_NQ = P1_TK * P1_TC / 256;   // loads per thread
+__global__ void __launch_bounds__(256)
+k_p1(const float2 *__restrict__ Q2, const float *__restrict__ W1, float2 *__restrict__ ft,
+     const float *__restrict__ Aw, const float2 *__restrict__ vadd, float areg, int N1, int B1,
+     int MT, int nb23) {
+    __shared__ float2 sE[P1_TK][P1_TJ + 1];   // [x1][j1]: (cos, -sin)
+    __shared__ float2 sQ[P1_TK][P1_TC];       // [x1][col]
+    const int c = blockIdx.z, j0 = blockIdx.y * P1_TJ, c0 = blockIdx.x * P1_TC;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    float2 acc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    float2 re[P1_NE], rq[P1_NQ];
+    auto load_e = [&](int k0) {
+#pragma unroll
+        for (int s = 0; s < P1_NE; ++s) {
+            const int i = tid + 256 * s, x1 = k0 + i / P1_TJ, j = j0 + i % P1_TJ;
+            re[s] = (j < B1 && x1 < N1) ? make_float2(W1[(2LL * j) * N1 + x1], W1[(2LL * j + 1) * N1 + x1])
+                                        : make_float2(0.f, 0.f);
+        }
+    };
+    auto load_q = [&](int k0) {   // the x2-tile partial sums, added in tile order
+#pragma unroll
+        for (int s = 0; s < P1_NQ; ++s) {
+            const int i = tid + 256 * s, x1 = k0 + i / P1_TC, col = c0 + i % P1_TC;
+            float2 q = make_float2(0.f, 0.f);
+            if (x1 < N1 && col < nb23) {
+                const float2 *src = Q2 + ((long long)c * N1 + x1) * MT * nb23 + col;
+                q = src[0];
+                for (int t = 1; t < MT; ++t) {
+                    const float2 r = src[(long long)t * nb23];
+                    q.x += r.x;
+                    q.y += r.y;
+                }
+            }
+            rq[s] = q;
+        }
+    };
+    load_e(0);
+    pdl_wait();   // Q2 comes from the previous kernel
+    load_q(0);
+    for (int k0 = 0; k0 < N1; k0 += P1_TK) {
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < P1_NE; ++s) {
+            const int i = tid + 256 * s;
+            sE[i / P1_TJ][i % P1_TJ] = re[s];
+        }
+#pragma unroll
+        for (int s = 0; s < P1_NQ; ++s) {
+            const int i = tid + 256 * s;
+            sQ[i / P1_TC][i % P1_TC] = rq[s];
+        }
+        __syncthreads();
+        if (k0 + P1_TK < N1) {
+            load_e(k0 + P1_TK);
+            load_q(k0 + P1_TK);
+        }
+#pragma unroll 8
+        for (int kk = 0; kk < P1_TK; ++kk) {
+            const float2 e = sE[kk][ty];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {   // (qr + i qi)(cos - i sin)
+                const float2 v = sQ[kk][tx + 16 * q];
+                acc[q].x = fmaf(v.x, e.x, fmaf(-v.y, e.y, acc[q].x));
+                acc[q].y = fmaf(v.y, e.x, fmaf(v.x, e.y, acc[q].y));
+            }
+        }
+    }
+    const int j = j0 + ty;
+    if (j >= B1) return;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int col = c0 + tx + 16 * q;
+        if (col >= nb23) continue;
         const long long o = ((long long)c * B1 + j) * nb23 + col;
-        float2 r = acc[jj];
+        float2 r = acc[q];
         if (vadd) {
             const float a = areg * Aw[(long long)j * nb23 + col];
             const float2 v = vadd[o];
@@ -284,6 +381,30 @@ k_p1(const float2 *__restrict__ Q2, const float *__restrict__ W1, float2 *__rest
 }
 
 // ---------------------------------------------------------------------------
+// Both tensor-core kernels run one CTA per SM with G independent warpgroups of
+// 128 threads.  The DFT tables are loaded once per CTA and shared; each
+// warpgroup owns an operand buffer in shared memory, a range of tensor-memory
+// columns, an mbarrier for its MMAs and a named barrier, and walks its own units
+// one after the other, so the units of the G warpgroups overlap.  Warp w of a
+// warpgroup reaches TMEM lanes 32 w .. 32 w + 31.
+
+__device__ __forceinline__ void group_sync(int g) {
+    asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory");
+}
+
+// The group's MMAs are complete (thread 0 of the group waits, bounded; the
+// group learns the outcome through shared memory after the named barrier).
+__device__ __forceinline__ bool group_wait(int g, int gt, uint32_t bar, uint32_t phase,
+                                           volatile int *s_ok) {
+    if (gt == 0) s_ok[g] = mbar_wait(bar, phase) ? 1 : 0;
+    group_sync(g);
+    const bool ok = s_ok[g] != 0;
+    group_sync(g);   // everyone has read the flag before it is written again
+    return ok;
+}
+
+constexpr int FZ_G_MAX = 4;
+
 struct FxArgs {
     const uint8_t *tab2;   // [MT][hi|lo][128 x K2e]
     const uint8_t *tab3;   // [hi|lo][N3e x K3e]
@@ -291,7 +412,9 @@ struct FxArgs {
     float *out;            // [3][N1][N2][N3]
     int N1, N2, N3, B2, B3, MT;
     int K2e, N2e, K3e, N3e;
-    int units;             // 3 N1 MT
+    int G;                 // warpgroups per CTA
+    size_t gbytes;         // operand buffer of a warpgroup
+    int gcols;             // TMEM columns of a warpgroup
     int tmem_cols;
     float scale;
     int mode;              // 0: store scale * v; 1: displacement (clamp, CFL / NaN flags)
@@ -327,25 +450,28 @@ __device__ __forceinline__ void fz_epi_chunk(uint32_t ta, float *T, float *dst_r
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(FZ_THREADS, 2)
+__global__ void __launch_bounds__(FZ_G_MAX * 128, 1)
 k_fx(FxArgs p) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     uint8_t *base = smem_raw + (((raw + 1023) & ~1023u) - raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = tid >> 7, gt = tid & 127, gw = warp & 3;
     const size_t tb2 = tile_bytes(FZ_M, p.K2e), tb3 = tile_bytes(p.N3e, p.K3e);
     const size_t tbB = tile_bytes(p.N2e, p.K2e), tbA = tile_bytes(FZ_M, p.K3e);
     uint8_t *sT2 = base;
     uint8_t *sT3 = sT2 + 2 * tb2;
-    uint8_t *sR = sT3 + 2 * tb3;   // B operand of GEMM 2 / A operand of GEMM 3 / epilogue
-    size_t rb = 2 * tbB > 2 * tbA ? 2 * tbB : 2 * tbA;
-    if (rb < (size_t)(FZ_THREADS / 32) * 4096) rb = (size_t)(FZ_THREADS / 32) * 4096;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sR + rb);   // table, mma, probe
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 4);
+    uint8_t *sG = sT3 + 2 * tb3;                    // G operand buffers
+    uint8_t *buf = sG + (size_t)g * p.gbytes;       // this warpgroup's
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sG + (size_t)p.G * p.gbytes);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 + 2 * FZ_G_MAX);
     __shared__ int s_fail, s_table;
-    const uint32_t bar_tab = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]),
-                   bar_probe = smem_u32(&bars[2]);
+    __shared__ int s_ok[FZ_G_MAX], s_ld[FZ_G_MAX];
+    const uint32_t bar_tab = smem_u32(&bars[0]), bar_probe = smem_u32(&bars[1]);
+    const uint32_t bar_mma = smem_u32(&bars[2 + g]), bar_ld = smem_u32(&bars[2 + FZ_G_MAX + g]);
     const int mt = blockIdx.x % p.MT;   // the grid is a multiple of MT: one x2 tile per CTA
+    const size_t p1_bytes = (size_t)p.B2 * p.B3 * 8;
+    const float2 *sP1 = reinterpret_cast<const float2 *>(buf + 2 * tbB);   // the unit's P1 slab
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -355,8 +481,12 @@ k_fx(FxArgs p) {
     }
     if (tid == 0) {
         mbar_init(bar_tab, 1);
-        mbar_init(bar_mma, 1);
         mbar_init(bar_probe, 1);
+        for (int q = 0; q < p.G; ++q) {
+            mbar_init(smem_u32(&bars[2 + q]), 1);
+            mbar_init(smem_u32(&bars[2 + FZ_G_MAX + q]), 1);
+            s_ld[q] = 0;
+        }
         asm volatile("fence.mbarrier_init.release.cluster;");
         s_fail = 0;
         s_table = 0;
@@ -365,7 +495,7 @@ k_fx(FxArgs p) {
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tslot;
-    bool run = (int)blockIdx.x < p.units;
+    bool run = true;
     if (p.probe) {   // test hook: a wait that expires while nothing is in flight
         const bool expired = tid == 0 ? !mbar_wait(bar_probe, 0u, TC_PROBE_CYCLES) : false;
         if (__syncthreads_or(expired)) run = false;
@@ -390,16 +520,32 @@ k_fx(FxArgs p) {
     const int nb23 = p.B2 * p.B3;
     const uint32_t idesc2 = umma_idesc(FZ_M, p.N2e), idesc3 = umma_idesc(FZ_M, p.N3e);
     const long long V = (long long)p.N1 * p.N2 * p.N3;
-    uint32_t phase = 0;
+    const uint32_t tg = tmem + (uint32_t)(g * p.gcols);   // this warpgroup's columns
+    const int units = 3 * p.N1;                          // per x2 tile
+    const int lanes = (int)(gridDim.x / p.MT) * p.G;
+    uint32_t phase = 0, ld_phase = 0;
     int flags = 0;
-    for (int u = blockIdx.x; run && u < p.units; u += gridDim.x) {
-        const int rest = u / p.MT, c = rest / p.N1, x1 = rest - c * p.N1;
-        const float2 *src = p.P1 + ((long long)c * p.N1 + x1) * nb23;
+    for (int u = (int)(blockIdx.x / p.MT) * p.G + g; run && u < units; u += lanes) {
+        const int c = u / p.N1, x1 = u - c * p.N1;
+        // the unit's P1 slab (contiguous, B2 B3 complex) by one bulk copy
+        if (gt == 0) {
+            mbar_expect_arrive(bar_ld, (uint32_t)p1_bytes);
+            bulk_g2s(smem_u32(sP1), p.P1 + ((long long)c * p.N1 + x1) * nb23, (uint32_t)p1_bytes, bar_ld);
+            s_ld[g] = 1 + (int)ld_phase;   // in flight, with the parity of its phase
+        }
+        bool ok = group_wait(g, gt, bar_ld, ld_phase, s_ok);
+        ld_phase ^= 1u;
+        if (!ok) {
+            if (gt == 0) s_fail = 1;
+            break;
+        }
+        if (gt == 0) s_ld[g] = 0;
+        const float2 *src = sP1;
         // B operand of GEMM 2, [n = (re | im)(j3)][k = (C | S)(j2)]:
         //   (C, re) P1re  (C, im) P1im  (S, re) -P1im  (S, im) P1re
         {
             const int nkc = p.K2e >> 3;
-            for (int it = tid; it < p.N2e * nkc; it += FZ_THREADS) {
+            for (int it = gt; it < p.N2e * nkc; it += 128) {
                 const int n = it % p.N2e, kc = it / p.N2e;
                 float x[8];
                 const bool im = n >= p.B3;
@@ -415,64 +561,64 @@ k_fx(FxArgs p) {
                     }
                     x[q] = v;
                 }
-                store_chunk(sR, tbB, swz_chunk(n, kc, p.N2e), x);
+                store_chunk(buf, tbB, swz_chunk(n, kc, p.N2e), x);
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
+        group_sync(g);
         asm volatile("tcgen05.fence::after_thread_sync;");
-        if (tid == 0) {
-            mma_split(tmem, smem_u32(sT2), smem_u32(sT2) + (uint32_t)tb2, FZ_M, smem_u32(sR),
-                      smem_u32(sR) + (uint32_t)tbB, p.N2e, p.K2e, idesc2);
+        if (gt == 0) {
+            mma_split(tg, smem_u32(sT2), smem_u32(sT2) + (uint32_t)tb2, FZ_M, smem_u32(buf),
+                      smem_u32(buf) + (uint32_t)tbB, p.N2e, p.K2e, idesc2);
             mma_commit(bar_mma);
         }
-        bool ok = tid == 0 ? mbar_wait(bar_mma, phase) : true;
+        ok = group_wait(g, gt, bar_mma, phase, s_ok);
         phase ^= 1u;
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) s_fail = 1;
+        if (!ok) {
+            if (gt == 0) s_fail = 1;
             break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        // D2 rows (TMEM lane = x2 row) -> A operand of GEMM 3, [x2][k = (re | im)(j3)]
-        if (warp < 4) {
-            const int r = warp * 32 + lane;
-            const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        // D2 rows (TMEM lane = x2 row) -> A operand of GEMM 3, [x2][k = (re | im)(j3)],
+        // in the same buffer (GEMM 2 has read its B operand)
+        {
+            const int r = gw * 32 + lane;
+            const uint32_t trow = tg + ((uint32_t)(gw * 32) << 16);
             for (int c0 = 0; c0 < p.N2e; c0 += 16) {
                 uint32_t rv[16];
                 tmem_ld16(trow + (uint32_t)c0, rv);
-                store_chunk(sR, tbA, swz_chunk(r, c0 >> 3, FZ_M), reinterpret_cast<const float *>(rv));
-                store_chunk(sR, tbA, swz_chunk(r, (c0 >> 3) + 1, FZ_M),
+                store_chunk(buf, tbA, swz_chunk(r, c0 >> 3, FZ_M), reinterpret_cast<const float *>(rv));
+                store_chunk(buf, tbA, swz_chunk(r, (c0 >> 3) + 1, FZ_M),
                             reinterpret_cast<const float *>(rv) + 8);
             }
             const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            for (int kc = p.N2e >> 3; kc < (p.K3e >> 3); ++kc) store_chunk(sR, tbA, swz_chunk(r, kc, FZ_M), z);
+            for (int kc = p.N2e >> 3; kc < (p.K3e >> 3); ++kc) store_chunk(buf, tbA, swz_chunk(r, kc, FZ_M), z);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
+        group_sync(g);
         asm volatile("tcgen05.fence::after_thread_sync;");
-        if (tid == 0) {
-            mma_split(tmem + (uint32_t)p.N2e, smem_u32(sR), smem_u32(sR) + (uint32_t)tbA, FZ_M,
-                      smem_u32(sT3), smem_u32(sT3) + (uint32_t)tb3, p.N3e, p.K3e, idesc3);
+        if (gt == 0) {   // D3 overwrites the columns of D2, which have been read
+            mma_split(tg, smem_u32(buf), smem_u32(buf) + (uint32_t)tbA, FZ_M, smem_u32(sT3),
+                      smem_u32(sT3) + (uint32_t)tb3, p.N3e, p.K3e, idesc3);
             mma_commit(bar_mma);
         }
-        ok = tid == 0 ? mbar_wait(bar_mma, phase) : true;
+        ok = group_wait(g, gt, bar_mma, phase, s_ok);
         phase ^= 1u;
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) s_fail = 1;
+        if (!ok) {
+            if (gt == 0) s_fail = 1;
             break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. (x2 rows), the two warps of
-        // a quadrant alternate 32-column chunks (x3)
+        // epilogue: warp gw of the group stores x2 rows 32 gw .. of the tile, all
+        // x3 columns in chunks of 32 (transposes in the group's buffer)
         {
-            const int lg = warp & 3, half = warp >> 2;
-            float *T = reinterpret_cast<float *>(sR) + warp * 1024;
-            const int row0 = mt * FZ_M + lg * 32;
+            float *T = reinterpret_cast<float *>(buf) + gw * 1024;
+            const int row0 = mt * FZ_M + gw * 32;
             float *dst = p.out + c * V + (long long)x1 * p.N2 * p.N3;
-            const uint32_t tq = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)p.N2e;
-            for (int c0 = half * 32; c0 < p.N3e; c0 += 64) {
+            const uint32_t tq = tg + ((uint32_t)(gw * 32) << 16);
+            for (int c0 = 0; c0 < p.N3e; c0 += 32) {
                 if (c0 + 32 <= p.N3e)
                     fz_epi_chunk<32>(tq + (uint32_t)c0, T, dst, row0, p.N2, p.N3, c0, p.N3, p.scale,
                                      p.mode, lane, flags);
@@ -482,14 +628,17 @@ k_fx(FxArgs p) {
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
+        group_sync(g);
     }
     if (flags) atomicOr(p.status, flags);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (s_fail && tid == 0) {
+        // a wait expired: give the copies still in flight a bounded time to land
         atomicOr(p.status, BLR_FLAG_TIMEOUT);
         if (s_table) mbar_wait(bar_tab, 0u);
+        for (int q = 0; q < p.G; ++q)
+            if (s_ld[q]) mbar_wait(smem_u32(&bars[2 + FZ_G_MAX + q]), (uint32_t)(s_ld[q] - 1));
     }
     __syncthreads();
     if (warp == 0)
@@ -498,40 +647,50 @@ k_fx(FxArgs p) {
 }
 
 // ---------------------------------------------------------------------------
+// Project.  GEMM 3' is computed transposed, D3t[n][x2] = sum_x3 T3p[n][x3] f[x2][x3]
+// (A = the table, B = the field tile, x3 in chunks of 64), so that tensor-memory
+// lane n holds row n of the next GEMM's A operand Q3t[n][x2] without a transpose.
+// Only the N3p meaningful rows of the table and of Q3t are stored: the MMA's rows
+// N3p .. 127 read whatever follows in shared memory and land in accumulator rows
+// that are never read.
 struct FpArgs {
-    const uint8_t *tab3;   // [hi|lo][N3p x K3p]
+    const uint8_t *tab3;   // [hi|lo][N3p x K3p]  (A operand, N3p rows stored)
     const uint8_t *tab2;   // [MT][hi|lo][N2p x 128]
     const float *f;        // [3][N1][N2][N3]
     float2 *Q2;            // [3][N1][MT][B2 B3]
     int N1, N2, N3, B2, B3, MT;
     int K3p, N3p, N2p;
-    int units;
+    int G;
+    size_t gbytes;
+    int gcols;
     int tmem_cols;
     int vec4;              // rows of f are 16-byte aligned (N3 % 4 == 0, aligned base)
     int *status;
     int probe;
 };
 
-__global__ void __launch_bounds__(FZ_THREADS, 1)
+constexpr int FP_KC = 64;   // x3 per field chunk (one 128-byte swizzle atom)
+
+__global__ void __launch_bounds__(FZ_G_MAX * 128, 1)
 k_fp(FpArgs p) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     uint8_t *base = smem_raw + (((raw + 1023) & ~1023u) - raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = tid >> 7, gt = tid & 127, gw = warp & 3;
     const size_t tb3 = tile_bytes(p.N3p, p.K3p), tb2 = tile_bytes(p.N2p, FZ_M);
-    const int ka = p.K3p > FZ_M ? p.K3p : FZ_M;
-    const size_t tbA = tile_bytes(FZ_M, p.K3p), tbA2 = tile_bytes(FZ_M, FZ_M);
+    const size_t tbF = tile_bytes(FZ_M, FP_KC), tbQ = tile_bytes(p.N3p, FZ_M);
+    const size_t slack = (size_t)(FZ_M - p.N3p) * 128;   // rows read past N3p
     uint8_t *sT3 = base;
-    uint8_t *sT2 = sT3 + 2 * tb3;
-    uint8_t *sA = sT2 + 2 * tb2;                  // field tile, then the transposed Q3
-    float *sQ = reinterpret_cast<float *>(sA + 2 * tile_bytes(FZ_M, ka));
-    const int qp = p.N3p + 4, ep = p.N2p + 1;
-    const size_t qbytes = (size_t)FZ_M * (qp > ep ? qp : ep) * 4;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(sQ) + qbytes);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 4);
+    uint8_t *sT2 = sT3 + 2 * tb3 + slack;
+    uint8_t *sG = sT2 + 2 * tb2;
+    uint8_t *buf = sG + (size_t)g * p.gbytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sG + (size_t)p.G * p.gbytes + slack);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 + FZ_G_MAX);
     __shared__ int s_fail, s_table;
-    const uint32_t bar_tab = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]),
-                   bar_probe = smem_u32(&bars[2]);
+    __shared__ int s_ok[FZ_G_MAX];
+    const uint32_t bar_tab = smem_u32(&bars[0]), bar_probe = smem_u32(&bars[1]);
+    const uint32_t bar_mma = smem_u32(&bars[2 + g]);
     const int mt = blockIdx.x % p.MT;
 
     if (warp == 0) {
@@ -542,8 +701,8 @@ k_fp(FpArgs p) {
     }
     if (tid == 0) {
         mbar_init(bar_tab, 1);
-        mbar_init(bar_mma, 1);
         mbar_init(bar_probe, 1);
+        for (int q = 0; q < p.G; ++q) mbar_init(smem_u32(&bars[2 + q]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;");
         s_fail = 0;
         s_table = 0;
@@ -552,7 +711,7 @@ k_fp(FpArgs p) {
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tslot;
-    bool run = (int)blockIdx.x < p.units;
+    bool run = true;
     if (p.probe) {
         const bool expired = tid == 0 ? !mbar_wait(bar_probe, 0u, TC_PROBE_CYCLES) : false;
         if (__syncthreads_or(expired)) run = false;
@@ -573,127 +732,131 @@ k_fp(FpArgs p) {
         }
     }
     const int nb23 = p.B2 * p.B3;
-    const uint32_t idesc3 = umma_idesc(FZ_M, p.N3p), idesc2 = umma_idesc(FZ_M, p.N2p);
+    const uint32_t idesc3 = umma_idesc(FZ_M, FZ_M), idesc2 = umma_idesc(FZ_M, p.N2p);
     const long long V = (long long)p.N1 * p.N2 * p.N3;
     const int rows = min(FZ_M, p.N2 - mt * FZ_M);   // x2 rows of this CTA's tile
+    const uint32_t tg = tmem + (uint32_t)(g * p.gcols);
+    const int units = 3 * p.N1;
+    const int lanes = (int)(gridDim.x / p.MT) * p.G;
+    const int nchunk = p.K3p / FP_KC;
+    const int ep = p.N2p + 1;
     uint32_t phase = 0;
-    for (int u = blockIdx.x; run && u < p.units; u += gridDim.x) {
-        const int rest = u / p.MT, c = rest / p.N1, x1 = rest - c * p.N1;
+    for (int u = (int)(blockIdx.x / p.MT) * p.G + g; run && u < units; u += lanes) {
+        const int c = u / p.N1, x1 = u - c * p.N1;
         const float *src = p.f + c * V + ((long long)x1 * p.N2 + (long long)mt * FZ_M) * p.N3;
-        // field tile -> A operand of GEMM 3', [x2][k = x3]: each thread loads all its
-        // chunks first (many loads in flight), then splits and stores them
-        {
-            const int nkc = p.K3p >> 3, total = FZ_M * nkc;
-            constexpr int PER = 8;
-            for (int base_it = 0; base_it < total; base_it += FZ_THREADS * PER) {
-                float x[PER][8];
+        bool ok = true;
+        // field chunks -> B operand of GEMM 3', [x2][k = x3 in the chunk].  Each
+        // thread holds its 8 pieces of 8 values of one chunk in registers: the
+        // next chunk's loads are issued before the wait for this chunk's MMAs.
+        constexpr int PER = FZ_M * (FP_KC / 8) / 128;   // 8 per thread
+        float x[PER][8];
+        auto load_chunk = [&](int ch) {
 #pragma unroll
-                for (int s = 0; s < PER; ++s) {
-                    const int it = base_it + s * FZ_THREADS + tid;
-                    const int r = it / nkc, kc = it - r * nkc, k0 = kc * 8;
-                    const bool live = it < total && r < rows;
-                    if (live && p.vec4 && k0 + 8 <= p.N3) {
-                        const float4 a = __ldg(reinterpret_cast<const float4 *>(src + (long long)r * p.N3 + k0));
-                        const float4 b = __ldg(reinterpret_cast<const float4 *>(src + (long long)r * p.N3 + k0 + 4));
-                        x[s][0] = a.x; x[s][1] = a.y; x[s][2] = a.z; x[s][3] = a.w;
-                        x[s][4] = b.x; x[s][5] = b.y; x[s][6] = b.z; x[s][7] = b.w;
-                    } else {
+            for (int s = 0; s < PER; ++s) {
+                const int it = s * 128 + gt, r = it >> 3, kc = it & 7;
+                const int k0 = ch * FP_KC + kc * 8;
+                const bool live = r < rows;
+                if (live && p.vec4 && k0 + 8 <= p.N3) {
+                    const float4 a = __ldg(reinterpret_cast<const float4 *>(src + (long long)r * p.N3 + k0));
+                    const float4 b = __ldg(reinterpret_cast<const float4 *>(src + (long long)r * p.N3 + k0 + 4));
+                    x[s][0] = a.x; x[s][1] = a.y; x[s][2] = a.z; x[s][3] = a.w;
+                    x[s][4] = b.x; x[s][5] = b.y; x[s][6] = b.z; x[s][7] = b.w;
+                } else {
 #pragma unroll
-                        for (int q = 0; q < 8; ++q)
-                            x[s][q] = (live && k0 + q < p.N3) ? __ldg(src + (long long)r * p.N3 + k0 + q) : 0.f;
-                    }
+                    for (int q = 0; q < 8; ++q)
+                        x[s][q] = (live && k0 + q < p.N3) ? __ldg(src + (long long)r * p.N3 + k0 + q) : 0.f;
                 }
+            }
+        };
+        load_chunk(0);
+        for (int ch = 0; ch < nchunk && ok; ++ch) {
 #pragma unroll
-                for (int s = 0; s < PER; ++s) {
-                    const int it = base_it + s * FZ_THREADS + tid;
-                    if (it < total) {
-                        const int r = it / nkc, kc = it - r * nkc;
-                        store_chunk(sA, tbA, swz_chunk(r, kc, FZ_M), x[s]);
-                    }
+            for (int s = 0; s < PER; ++s) {
+                const int it = s * 128 + gt;
+                store_chunk(buf, tbF, swz_chunk(it >> 3, it & 7, FZ_M), x[s]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            group_sync(g);
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (ch + 1 < nchunk) load_chunk(ch + 1);
+            if (gt == 0) {
+                // A: atom ch of the table (N3p rows per atom), B: the field chunk
+                const uint32_t a0 = smem_u32(sT3) + (uint32_t)(ch * p.N3p * 128);
+                for (int j = 0; j < FP_KC / 16; ++j) {
+                    const uint32_t o = (uint32_t)(j * 32);
+                    const uint64_t ah = umma_desc(a0 + o), al = umma_desc(a0 + (uint32_t)tb3 + o);
+                    const uint64_t bh = umma_desc(smem_u32(buf) + o), bl = umma_desc(smem_u32(buf) + (uint32_t)tbF + o);
+                    umma_bf16(tg, ah, bh, idesc3, (ch > 0 || j > 0) ? 1u : 0u);
+                    umma_bf16(tg, ah, bl, idesc3, 1u);
+                    umma_bf16(tg, al, bh, idesc3, 1u);
+                }
+                mma_commit(bar_mma);
+            }
+            ok = group_wait(g, gt, bar_mma, phase, s_ok);
+            phase ^= 1u;
+        }
+        if (!ok) {
+            if (gt == 0) s_fail = 1;
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        // D3t row n (TMEM lane n) -> A operand of GEMM 2', [n][k = x2 in tile]
+        if (gw * 32 < p.N3p) {
+            const int n = gw * 32 + lane;
+            const uint32_t trow = tg + ((uint32_t)(gw * 32) << 16);
+            for (int c0 = 0; c0 < FZ_M; c0 += 32) {
+                uint32_t rv[32];
+                tmem_ld32(trow + (uint32_t)c0, rv);
+                if (n < p.N3p) {
+#pragma unroll
+                    for (int h = 0; h < 4; ++h)
+                        store_chunk(buf, tbQ, swz_chunk(n, (c0 >> 3) + h, p.N3p),
+                                    reinterpret_cast<const float *>(rv) + 8 * h);
                 }
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
+        group_sync(g);
         asm volatile("tcgen05.fence::after_thread_sync;");
-        if (tid == 0) {
-            mma_split(tmem, smem_u32(sA), smem_u32(sA) + (uint32_t)tbA, FZ_M, smem_u32(sT3),
-                      smem_u32(sT3) + (uint32_t)tb3, p.N3p, p.K3p, idesc3);
+        if (gt == 0) {   // D2t overwrites the first columns of D3t, which have been read
+            mma_split(tg, smem_u32(buf), smem_u32(buf) + (uint32_t)tbQ, p.N3p, smem_u32(sT2),
+                      smem_u32(sT2) + (uint32_t)tb2, p.N2p, FZ_M, idesc2);
             mma_commit(bar_mma);
         }
-        bool ok = tid == 0 ? mbar_wait(bar_mma, phase) : true;
+        ok = group_wait(g, gt, bar_mma, phase, s_ok);
         phase ^= 1u;
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) s_fail = 1;
+        if (!ok) {
+            if (gt == 0) s_fail = 1;
             break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        // Q3 rows (TMEM lane = x2) -> FP32 staging [x2][n]
-        if (warp < 4) {
-            const int r = warp * 32 + lane;
-            const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-            for (int c0 = 0; c0 < p.N3p; c0 += 16) {
-                uint32_t rv[16];
-                tmem_ld16(trow + (uint32_t)c0, rv);
-                float4 *d = reinterpret_cast<float4 *>(sQ + (size_t)r * qp + c0);
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    d[q] = make_float4(__uint_as_float(rv[4 * q]), __uint_as_float(rv[4 * q + 1]),
-                                       __uint_as_float(rv[4 * q + 2]), __uint_as_float(rv[4 * q + 3]));
-            }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        // transposed Q3 -> A operand of GEMM 2', [m = (re | im)(j3)][k = x2 in tile];
-        // rows m >= N3p keep stale values: their products land in rows that are
-        // never read
-        for (int it = tid; it < p.N3p * (FZ_M / 8); it += FZ_THREADS) {
-            const int m = it % p.N3p, kc = it / p.N3p;
-            float x[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) x[q] = sQ[(size_t)(kc * 8 + q) * qp + m];
-            store_chunk(sA, tbA2, swz_chunk(m, kc, FZ_M), x);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (tid == 0) {
-            mma_split(tmem + (uint32_t)p.N3p, smem_u32(sA), smem_u32(sA) + (uint32_t)tbA2, FZ_M,
-                      smem_u32(sT2), smem_u32(sT2) + (uint32_t)tb2, p.N2p, FZ_M, idesc2);
-            mma_commit(bar_mma);
-        }
-        ok = tid == 0 ? mbar_wait(bar_mma, phase) : true;
-        phase ^= 1u;
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) s_fail = 1;
-            break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        // GEMM 2' rows m < 2 B3 -> FP32 staging [m][n] (odd pitch: column reads below)
-        if (warp < 4) {
-            const int m = warp * 32 + lane;
-            const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)p.N3p;
+        // D2t rows m < 2 B3 -> FP32 staging [m][n] in the group's buffer (odd pitch:
+        // column reads below)
+        float *sE = reinterpret_cast<float *>(buf);
+        if (gw * 32 < 2 * p.B3) {
+            const int m = gw * 32 + lane;
+            const uint32_t trow = tg + ((uint32_t)(gw * 32) << 16);
             for (int c0 = 0; c0 < p.N2p; c0 += 16) {
                 uint32_t rv[16];
                 tmem_ld16(trow + (uint32_t)c0, rv);
                 if (m < 2 * p.B3) {
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) sQ[(size_t)m * ep + c0 + q] = __uint_as_float(rv[q]);
+                    for (int q = 0; q < 16; ++q) sE[(size_t)m * ep + c0 + q] = __uint_as_float(rv[q]);
                 }
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
+        group_sync(g);
         // Q2[j2][j3] = (C re + S im, C im - S re) combinations of the four blocks
         float2 *dst = p.Q2 + (((long long)c * p.N1 + x1) * p.MT + mt) * nb23;
-        for (int e = tid; e < nb23; e += FZ_THREADS) {
+        for (int e = gt; e < nb23; e += 128) {
             const int j2 = e / p.B3, j3 = e - j2 * p.B3;
-            const float *re = sQ + (size_t)j3 * ep, *im = sQ + (size_t)(p.B3 + j3) * ep;
+            const float *re = sE + (size_t)j3 * ep, *im = sE + (size_t)(p.B3 + j3) * ep;
             dst[e] = make_float2(re[j2] + im[p.B2 + j2], im[j2] - re[p.B2 + j2]);
         }
-        __syncthreads();
+        group_sync(g);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -707,19 +870,23 @@ k_fp(FpArgs p) {
                      "r"(p.tmem_cols));
 }
 
-// CTAs of a fused kernel per SM from its shared memory and TMEM columns.
-int fz_ctas_per_sm(size_t smem, int cols) {
-    constexpr size_t SM_SMEM = 228 * 1024, RESERVED = 1024;
-    int k = 1;
-    while ((size_t)(k + 1) * (smem + RESERVED) <= SM_SMEM && (k + 1) * cols <= 512 && k < 2) ++k;
-    return k;
+// CTAs per x2 tile when every SM holds one CTA, and the warpgroups that spreads
+// a tile's units over: units are (component, x1 plane), per x2 tile.
+int fz_ctas_per_tile(const blr_plan *P, int MT) {
+    const int sms = P->sms > 0 ? P->sms : 148;
+    return sms / MT > 1 ? sms / MT : 1;
 }
-
-int fz_grid(const blr_plan *P, int units, int per_sm, int MT) {
-    int grid = per_sm * (P->sms > 0 ? P->sms : 148);
-    if (grid > units) grid = units;
-    grid = grid / MT * MT;
-    return grid < MT ? MT : grid;
+int fz_gmax(const blr_plan *P, int MT) {
+    const int per = fz_ctas_per_tile(P, MT), units = 3 * P->N1;
+    return (units + per - 1) / per;
+}
+// Grid of a fused kernel: at most one CTA per SM, a multiple of MT, and no CTA
+// without units.
+int fz_grid(const blr_plan *P, int G, int MT) {
+    int per = fz_ctas_per_tile(P, MT);
+    const int need = (3 * P->N1 + G - 1) / G;
+    if (per > need) per = need;
+    return per * MT;
 }
 
 }  // namespace
@@ -732,8 +899,7 @@ extern std::atomic<int> g_tc_probe;   // dft_tc.cu (blr_test_expire_waits)
 bool fz_supported(const blr_plan *P) {
     const FzGeom g = fz_geometry(P);
     if (P->N3 > 256 || P->B2 > 128 || 2 * P->B3 > FZ_M) return false;
-    if (g.N2e + g.N3e > 512 || g.N3p + g.N2p > 512) return false;
-    return fx_smem(g) <= PZ_MAX_SMEM && fp_smem(g) <= PZ_MAX_SMEM;
+    return fx_shape(g, P->B2, P->B3).G >= 1 && fp_shape(g).G >= 1;
 }
 
 size_t fz_table_bytes(const blr_plan *P, int kind) {
@@ -770,11 +936,11 @@ int fz_expand(blr_plan *P, const float *vt, float *out, float scale, int mode, c
     const FzGeom g = fz_geometry(P);
     const int nb23 = P->B2 * P->B3;
     float2 *P1 = reinterpret_cast<float2 *>(P->fz_buf);
-    const int nxb = (P->N1 + EX1_XB - 1) / EX1_XB;
-    launch_pdl(k_ex1, dim3((unsigned)((nb23 + 255) / 256), (unsigned)(3 * nxb)), dim3(256),
-               (size_t)P->B1 * EX1_XB * sizeof(float2), s, reinterpret_cast<const float2 *>(vt),
-               (const float *)P->W1, P1, P->N1, P->B1, nb23);
+    launch_pdl(k_ex1, dim3((unsigned)((nb23 + EX_TC - 1) / EX_TC), (unsigned)((P->N1 + EX_TX - 1) / EX_TX), 3u),
+               dim3(256), 0, s, reinterpret_cast<const float2 *>(vt), (const float *)P->W1, P1,
+               P->N1, P->B1, nb23);
     BLR_CK_LAUNCH();
+    const FzShape sh = fx_shape(g, P->B2, P->B3, fz_gmax(P, g.MT));
     FxArgs a;
     a.tab2 = P->fz_tab[0];
     a.tab3 = P->fz_tab[1];
@@ -790,16 +956,16 @@ int fz_expand(blr_plan *P, const float *vt, float *out, float scale, int mode, c
     a.N2e = g.N2e;
     a.K3e = g.K3e;
     a.N3e = g.N3e;
-    a.units = 3 * P->N1 * g.MT;
-    a.tmem_cols = pow2_cols(g.N2e + g.N3e);
+    a.G = sh.G;
+    a.gbytes = sh.gbytes;
+    a.gcols = sh.gcols;
+    a.tmem_cols = sh.tmem_cols;
     a.scale = scale;
     a.mode = mode;
     a.status = P->dstatus;
     a.probe = g_tc_probe.load(std::memory_order_relaxed);
-    const size_t smem = fx_smem(g);
-    BLR_CK(cudaFuncSetAttribute(k_fx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = fz_grid(P, a.units, fz_ctas_per_sm(smem, a.tmem_cols), g.MT);
-    launch_pdl(k_fx, dim3(grid), dim3(FZ_THREADS), smem, s, a);
+    BLR_CK(cudaFuncSetAttribute(k_fx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem));
+    launch_pdl(k_fx, dim3(fz_grid(P, sh.G, g.MT)), dim3(128 * sh.G), sh.smem, s, a);
     BLR_CK_LAUNCH();
     return BLR_OK;
 }
@@ -809,6 +975,7 @@ int fz_project(blr_plan *P, const float *f, float *ft, const float *vadd, float 
     const FzGeom g = fz_geometry(P);
     const int nb23 = P->B2 * P->B3;
     float2 *Q2 = reinterpret_cast<float2 *>(P->fz_buf);
+    const FzShape sh = fp_shape(g, fz_gmax(P, g.MT));
     FpArgs a;
     a.tab3 = P->fz_tab[2];
     a.tab2 = P->fz_tab[3];
@@ -823,18 +990,18 @@ int fz_project(blr_plan *P, const float *f, float *ft, const float *vadd, float 
     a.K3p = g.K3p;
     a.N3p = g.N3p;
     a.N2p = g.N2p;
-    a.units = 3 * P->N1 * g.MT;
-    a.tmem_cols = pow2_cols(g.N3p + g.N2p);
+    a.G = sh.G;
+    a.gbytes = sh.gbytes;
+    a.gcols = sh.gcols;
+    a.tmem_cols = sh.tmem_cols;
     a.vec4 = (P->N3 % 4 == 0) && ((uintptr_t)f % 16 == 0);
     a.status = P->dstatus;
     a.probe = g_tc_probe.load(std::memory_order_relaxed);
-    const size_t smem = fp_smem(g);
-    BLR_CK(cudaFuncSetAttribute(k_fp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = fz_grid(P, a.units, fz_ctas_per_sm(smem, a.tmem_cols), g.MT);
-    launch_pdl(k_fp, dim3(grid), dim3(FZ_THREADS), smem, s, a);
+    BLR_CK(cudaFuncSetAttribute(k_fp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem));
+    launch_pdl(k_fp, dim3(fz_grid(P, sh.G, g.MT)), dim3(128 * sh.G), sh.smem, s, a);
     BLR_CK_LAUNCH();
-    const int njb = (P->B1 + P1_JB - 1) / P1_JB;
-    launch_pdl(k_p1, dim3((unsigned)((nb23 + 127) / 128), (unsigned)(3 * njb)), dim3(128), 0, s,
+    launch_pdl(k_p1, dim3((unsigned)((nb23 + P1_TC - 1) / P1_TC), (unsigned)((P->B1 + P1_TJ - 1) / P1_TJ), 3u),
+               dim3(256), 0, s,
                (const float2 *)Q2, (const float *)P->W1, reinterpret_cast<float2 *>(ft),
                (const float *)P->A, reinterpret_cast<const float2 *>(vadd), areg, P->N1, P->B1,
                g.MT, nb23);
