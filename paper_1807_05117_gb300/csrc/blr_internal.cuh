@@ -31,6 +31,13 @@ extern unsigned long long g_blr_launches;
 // once the previous grid has completed and its writes are visible.
 #ifdef __CUDACC__
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the next kernel of the stream launch before this one has finished (it
+// still waits for this grid's completion in its pdl_wait).  The next grid
+// launches only once every block of this grid has executed the trigger or
+// exited, so no block of this grid is still waiting for room on an SM.
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 #endif
 
 template <typename... KArgs, typename... Args>

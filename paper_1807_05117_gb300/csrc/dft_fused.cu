@@ -219,6 +219,7 @@ k_ex1(const float2 *__restrict__ vt, const float *__restrict__ W1, float2 *__res
     __shared__ float2 sV[EX_TK][EX_TC];       // [j1][col]
     const int c = blockIdx.z, x0 = blockIdx.y * EX_TX, c0 = blockIdx.x * EX_TC;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    pdl_trigger();   // k_fx may launch and fetch its tables meanwhile
     float2 acc[2][4];
 #pragma unroll
     for (int r = 0; r < 2; ++r)
