@@ -78,6 +78,7 @@ _SIGS = {
     "blr_status": (_P, _P),
     "blr_test_expire_waits": (ctypes.c_int,),
     "blr_plan_tuning": (_P, ctypes.POINTER(ctypes.c_int), ctypes.c_int),
+    "blr_plan_set_tuning": (_P, ctypes.POINTER(ctypes.c_int), ctypes.c_int),
     "blr_batch_create": (ctypes.POINTER(blr_params), ctypes.c_int, ctypes.POINTER(_P)),
     "blr_batch_destroy": (_P,),
     "blr_batch_set_images": (_P, ctypes.c_int, _P, _P, _P),
@@ -445,13 +446,23 @@ class Plan:
 
     TUNING_KEYS = ("wide_sweeps", "grad_kept", "adjoint_blocks_per_sm", "adjoint_reads_grad",
                    "incremental_form", "incremental_blocks_per_sm", "march_blocks_per_sm",
-                   "march_chunk", "adjoint_march_chunk", "l2_persist_d4")
+                   "march_chunk", "adjoint_march_chunk", "l2_persist_d4", "adjoint_two_step")
 
     def tuning(self) -> dict:
         """The sweep shapes the autotuner chose (blr_plan_tuning)."""
         vals = (ctypes.c_int * len(self.TUNING_KEYS))()
         _check(_lib.blr_plan_tuning(_P(self.handle), vals, len(vals)), "blr_plan_tuning")
         return dict(zip(self.TUNING_KEYS, [int(v) for v in vals]))
+
+    def set_tuning(self, **changes):
+        """Override sweep shapes (blr_plan_set_tuning): keys of tuning()."""
+        cur = self.tuning()
+        for k, v in changes.items():
+            if k not in cur:
+                raise ValueError(f"unknown tuning key {k}")
+            cur[k] = int(v)
+        vals = (ctypes.c_int * len(self.TUNING_KEYS))(*[cur[k] for k in self.TUNING_KEYS])
+        _check(_lib.blr_plan_set_tuning(_P(self.handle), vals, len(vals)), "blr_plan_set_tuning")
 
 
 def _ptr_array(tensors, shapes, numel, **kw):

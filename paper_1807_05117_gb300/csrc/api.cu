@@ -470,10 +470,37 @@ extern "C" {
 
 int blr_plan_tuning(blr_plan_t P, int *vals, int n) {
     if (!P || !vals) return BLR_EINVAL;
-    const int v[10] = {P->sweep_wide ? 1 : 0, P->Gm ? 1 : 0, P->bal_adj, P->adj_useg,
+    const int v[11] = {P->sweep_wide ? 1 : 0, P->Gm ? 1 : 0, P->bal_adj, P->adj_useg,
                        P->inc_mode, P->bal_inc, P->bal_sweep, P->chunk, P->chunk_adj,
-                       P->l2_persist};
-    for (int i = 0; i < n && i < 10; ++i) vals[i] = v[i];
+                       P->l2_persist, P->adj2};
+    for (int i = 0; i < n && i < 11; ++i) vals[i] = v[i];
+    return BLR_OK;
+}
+
+int blr_plan_set_tuning(blr_plan_t P, const int *vals, int n) {
+    if (!P || !vals || n < 11) return BLR_EINVAL;
+    // the first two entries describe the plan's buffers and must be unchanged
+    if (vals[0] != (P->sweep_wide ? 1 : 0) || vals[1] != (P->Gm ? 1 : 0)) return BLR_EINVAL;
+    const int bal_adj = vals[2], useg = vals[3], inc = vals[4], bal_inc = vals[5];
+    const int bal_sweep = vals[6], chunk = vals[7], chunk_adj = vals[8], l2 = vals[9], adj2 = vals[10];
+    const bool gm = P->Gm != nullptr;
+    if (bal_adj < 0 || bal_adj > 4 || (P->sweep_wide && bal_adj < 1)) return BLR_EINVAL;
+    if ((useg != 0 && useg != 1) || (useg && !gm)) return BLR_EINVAL;
+    if (inc < 0 || inc > 2 || (inc > 0 && !gm)) return BLR_EINVAL;
+    if (bal_inc < 0 || bal_inc > 4 || bal_sweep < 0 || bal_sweep > 4) return BLR_EINVAL;
+    if (chunk < 1 || chunk > P->N1 || chunk_adj < 1 || chunk_adj > P->N1) return BLR_EINVAL;
+    if ((l2 != 0 && l2 != 1) || (l2 && !P->l2_win_bytes)) return BLR_EINVAL;
+    if (adj2 < 0 || adj2 > 2 || (adj2 && (!gm || !P->d4 || P->nvel != 1))) return BLR_EINVAL;
+    if (cudaDeviceSynchronize() != cudaSuccess) return BLR_ECUDA;
+    P->bal_adj = bal_adj;
+    P->adj_useg = useg;
+    P->inc_mode = inc;
+    P->bal_inc = bal_inc;
+    P->bal_sweep = bal_sweep;
+    sweep_set_chunk(P, 2, chunk);
+    sweep_set_chunk(P, 1, chunk_adj);
+    P->l2_persist = l2;
+    P->adj2 = adj2;
     return BLR_OK;
 }
 

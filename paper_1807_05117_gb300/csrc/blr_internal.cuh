@@ -145,6 +145,9 @@ struct blr_plan {
     bool use_gm;        // Gm is kept (see Gm)
     int bal_inc;        // blocks per SM of the wide-copy incremental-state grid (sweep_autotune)
     int adj_useg;       // the adjoint reads Gm (1) or interpolates it (0)      (sweep_autotune)
+    int adj2;           // two adjoint steps per launch on a balanced grid of adj2 blocks
+                        // per SM (plans that keep Gm), or 0: one step per launch
+                        //                                                      (sweep_autotune)
     int inc_mode;       // incremental state: 0 wide-copy, 1 wide-copy reading Gm,
                         // 2 gather reading Gm                                  (sweep_autotune)
     float *m;           // state slots (see state_slot): checkpoints, segment, final

@@ -1068,6 +1068,214 @@ k_sweep_batch(const SweepPair *__restrict__ pairs, const long long *__restrict__
     }
 }
 
+// ---------------------------------------------------------------------------
+// Two adjoint steps per launch (temporal blocking), for plans that keep the
+// state gradients: from lambda^{n+1},
+//   step n:     lambda^n     = S^T lambda^{n+1},  b += dt lambda^{n+1} grad m^n
+//   step n - 1: lambda^{n-1} = S^T lambda^n,      b += dt lambda^n grad m^{n-1}
+// with lambda^n kept in shared memory and the body force read and written once
+// for both steps.  A block's core is 28 (x3) x 16 (x2) voxels; step n is computed
+// on the core and a one-voxel halo (30 x 18, the sources of step n - 1's gather),
+// step n - 1 on the same positions (the halo's results are not stored).  Thread
+// (w, lane) owns region rows 2w, 2w + 1 and column lane (x3 = k0 - 1 + lane,
+// lanes 30 and 31 only copy).  Source plane s of step n is scattered at march
+// index s, source plane s - 1 of step n - 1 at the same index, so lambda^{n-1}
+// and the body force of plane s - 2 are final then.  Both gathers accumulate
+// their terms in the order of the one-step kernel (source planes in order, then
+// rows and columns), and the body force takes the same two FMAs in the same
+// order, so the results equal two one-step launches bit for bit.
+constexpr int A2K = 28, A2J = 16;              // core x3 columns, x2 rows
+constexpr int A2W = 9;                         // warps: region rows 2w, 2w + 1
+constexpr int A2T = A2W * 32;                  // threads per block
+constexpr int A2RR = A2J + 2;                  // region rows: x2 = j0 - 1 .. j0 + 16
+constexpr int A2RC = 32;                       // lambda^n ring row (30 used)
+constexpr int A2IR = A2J + 4;                  // input rows: x2 = j0 - 2 .. j0 + 17
+constexpr int A2QC = 32;                       // d4 input columns: x3 = k0 - 2 .. k0 + 29
+constexpr int A2LC = 36;                       // lambda input columns: x3 = k0 - 4 .. k0 + 31
+constexpr int A2LG = A2LC / 4;                 // 16-byte groups of a lambda row
+constexpr int A2NQ = 4, A2NL = 6, A2NM = 3;    // ring slots: d4, lambda^{n+1}, lambda^n
+constexpr int A2Q_PL = A2IR * A2QC;            // float4 per d4 plane
+constexpr int A2L_PL = A2IR * A2LC;            // floats per lambda^{n+1} plane
+constexpr int A2M_PL = A2RR * A2RC;            // floats per lambda^n plane
+constexpr int A2QCP = (A2Q_PL + A2T - 1) / A2T;   // d4 copies per thread
+constexpr int A2LCP = A2IR * A2LG;             // lambda copies per plane (one per thread)
+constexpr int ADJ2_SMEM = A2NQ * A2Q_PL * 16 + A2NL * A2L_PL * 4 + A2NM * A2M_PL * 4;
+constexpr int ADJ2_BLOCKS = 2;                 // resident blocks per SM at most
+static_assert(A2LCP <= A2T, "one lambda copy per thread at most");
+
+// The scatter of one source plane into three target planes (A: s - 1, B: s,
+// C: s + 1) for the thread's two rows: `src(sr, dk)` gives the source value at
+// relative row sr (0 .. 3) and column offset dk, q its displacement (d0, d1, d2).
+template <typename SRC, typename QF>
+__device__ __forceinline__ void scatter_plane(SRC &&src, QF &&qf, float2 &accA, float2 &accB,
+                                              float2 &accC) {
+#pragma unroll
+    for (int sr = 0; sr < 4; ++sr) {
+#pragma unroll
+        for (int dk = -1; dk <= 1; ++dk) {
+            const float4 q = qf(sr, dk);
+            const float wl = src(sr, dk) * hat_e(-dk, q.z);
+            const float xa = fmaxf(-q.x, 0.f), xb = 1.f - fabsf(q.x), xc = fmaxf(q.x, 0.f);
+            if (sr == 0) {
+                const float wt = wl * hat_e(1, q.y);
+                accA.x = fmaf(wt, xa, accA.x);
+                accB.x = fmaf(wt, xb, accB.x);
+                accC.x = fmaf(wt, xc, accC.x);
+            } else if (sr == 3) {
+                const float wt = wl * hat_e(-1, q.y);
+                accA.y = fmaf(wt, xa, accA.y);
+                accB.y = fmaf(wt, xb, accB.y);
+                accC.y = fmaf(wt, xc, accC.y);
+            } else {
+                const float2 wt = __fmul2_rn(make_float2(wl, wl),
+                                             make_float2(hat_e(1 - sr, q.y), hat_e(2 - sr, q.y)));
+                accA = __ffma2_rn(wt, make_float2(xa, xa), accA);
+                accB = __ffma2_rn(wt, make_float2(xb, xb), accB);
+                accC = __ffma2_rn(wt, make_float2(xc, xc), accC);
+            }
+        }
+    }
+}
+
+template <bool FIRST, bool WRITE_LAM>
+__device__ __forceinline__ void
+adjoint2_tile(const float *__restrict__ lam_in, const float4 *__restrict__ d4,
+              float *__restrict__ lam_out, float *__restrict__ b, float dt, const Grid3 g, int CH,
+              int k0, int j0, int i0, const float *__restrict__ G1, const float *__restrict__ G2) {
+    extern __shared__ __align__(16) unsigned char blr_dyn_smem[];
+    float4 *Q = reinterpret_cast<float4 *>(blr_dyn_smem);
+    float *L = reinterpret_cast<float *>(blr_dyn_smem + A2NQ * A2Q_PL * 16);
+    float *M = L + A2NL * A2L_PL;
+    const int i_end = min(i0 + CH, g.N1);
+    const long long plane = (long long)g.N2 * g.N3, V = g.V;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int r0 = 2 * w;
+    const bool act = lane < A2K + 2;
+    const int x3 = k0 - 1 + lane;
+    const bool colcore = lane >= 1 && lane <= A2K && x3 < g.N3;
+    // this thread's copies: d4 positions tid + A2T i, lambda group tid
+    int offq[A2QCP];
+#pragma unroll
+    for (int i = 0; i < A2QCP; ++i) {
+        const int c = tid + A2T * i;
+        offq[i] = c < A2Q_PL ? wrapi(j0 - 2 + c / A2QC, g.N2) * g.N3 + wrapi(k0 - 2 + c % A2QC, g.N3) : 0;
+    }
+    const bool cl = tid < A2LCP;
+    const int offl = cl ? wrapi(j0 - 2 + tid / A2LG, g.N2) * g.N3 + wrapi(k0 - 4 + 4 * (tid % A2LG), g.N3) : 0;
+    const uint32_t q0s = smem_u32(Q) + (uint32_t)tid * 16u;
+    const uint32_t l0s = smem_u32(L) + (uint32_t)tid * 16u;
+    const int sb = i0 - 2;
+    auto issue = [&](int sp, int r) {   // input plane sp into ring position r (one commit group)
+        if (sp <= i_end + 1) {
+            const long long pb = (long long)wrapi(sp, g.N1) * plane;
+            const uint32_t qs = q0s + (uint32_t)(r & (A2NQ - 1)) * (A2Q_PL * 16);
+#pragma unroll
+            for (int i = 0; i < A2QCP; ++i)
+                if (tid + A2T * i < A2Q_PL) cp16(qs + (uint32_t)(A2T * i) * 16u, d4 + pb + offq[i]);
+            if (cl) cp16(l0s + (uint32_t)(r % A2NL) * (A2L_PL * 4), lam_in + pb + offl);
+        }
+        cp_commit();
+    };
+    issue(sb, 0);
+    issue(sb + 1, 1);
+    float2 a1A = make_float2(0.f, 0.f), a1B = a1A, a1C = a1A;   // lambda^n: planes s-1, s, s+1
+    float2 a2A = a1A, a2B = a1A, a2C = a1A;                     // lambda^{n-1}: planes s-2, s-1, s
+    float bb[2][3], g1[2][3], g2[2][3];   // b, grad m^n, grad m^{n-1} of the next output plane
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) bb[jj][a] = g1[jj][a] = g2[jj][a] = 0.f;
+    for (int s = sb; s <= i_end + 1; ++s) {
+        const int r = s - sb;
+        cp_wait1();
+        __syncthreads();
+        issue(s + 2, r + 2);
+        if (act) {
+            // step n: scatter lambda^{n+1} of source plane s
+            const float4 *Qs = Q + (r & (A2NQ - 1)) * A2Q_PL;
+            const float *Ls = L + (r % A2NL) * A2L_PL;
+            scatter_plane([&](int sr, int dk) { return Ls[(r0 + sr) * A2LC + lane + 3 + dk]; },
+                          [&](int sr, int dk) { return Qs[(r0 + sr) * A2QC + lane + 1 + dk]; },
+                          a1A, a1B, a1C);
+            // lambda^n of plane s - 1 is complete: into its ring slot
+            if (s >= i0) {
+                float *Mw = M + ((r - 1) % A2NM) * A2M_PL;
+                Mw[r0 * A2RC + lane] = a1A.x;
+                Mw[(r0 + 1) * A2RC + lane] = a1A.y;
+            }
+        }
+        a1A = a1B;
+        a1B = a1C;
+        a1C = make_float2(0.f, 0.f);
+        __syncthreads();
+        if (WRITE_LAM && act && s >= i0) {
+            // step n - 1: scatter lambda^n of source plane s - 1 (rows and columns past
+            // the region are clamped: only halo results, which are not stored, use them)
+            const float4 *Qp = Q + ((r - 1) & (A2NQ - 1)) * A2Q_PL;
+            const float *Mp = M + ((r - 1) % A2NM) * A2M_PL;
+            scatter_plane(
+                [&](int sr, int dk) {
+                    const int mr = min(max(r0 - 1 + sr, 0), A2RR - 1);
+                    return Mp[mr * A2RC + max(lane + dk, 0)];
+                },
+                [&](int sr, int dk) { return Qp[(r0 + sr) * A2QC + lane + 1 + dk]; }, a2A, a2B, a2C);
+        }
+        // plane o = s - 2: lambda^{n-1} final, and the body force of both steps
+        const int o = s - 2;
+        if (act && o >= i0 && o < i_end) {
+            const float *Lo = L + ((r - 2) % A2NL) * A2L_PL;
+            const float *Mo = M + ((r - 2) % A2NM) * A2M_PL;
+#pragma unroll
+            for (int jj = 0; jj < 2; ++jj) {
+                const int rr = r0 + jj, x2 = j0 - 1 + rr;
+                if (rr >= 1 && rr <= A2J && x2 < g.N2 && colcore) {
+                    const long long idx = (long long)o * plane + (long long)x2 * g.N3 + x3;
+                    const float sl1 = dt * Lo[(rr + 1) * A2LC + lane + 3];
+                    const float sl2 = dt * Mo[rr * A2RC + lane];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const float v = FIRST ? sl1 * g1[jj][a] : fmaf(sl1, g1[jj][a], bb[jj][a]);
+                        b[a * V + idx] = fmaf(sl2, g2[jj][a], v);
+                    }
+                    if (WRITE_LAM) lam_out[idx] = jj == 0 ? a2A.x : a2A.y;
+                }
+            }
+        }
+        a2A = a2B;
+        a2B = a2C;
+        a2C = make_float2(0.f, 0.f);
+        // operands of the next output plane, s - 1
+        const int on = s - 1;
+        if (act && on >= i0 && on < i_end) {
+#pragma unroll
+            for (int jj = 0; jj < 2; ++jj) {
+                const int rr = r0 + jj, x2 = j0 - 1 + rr;
+                if (rr >= 1 && rr <= A2J && x2 < g.N2 && colcore) {
+                    const long long nidx = (long long)on * plane + (long long)x2 * g.N3 + x3;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        if (!FIRST) bb[jj][a] = b[a * V + nidx];
+                        g1[jj][a] = __ldg(G1 + a * V + nidx);
+                        g2[jj][a] = __ldg(G2 + a * V + nidx);
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <bool FIRST, bool WRITE_LAM>
+__global__ void __launch_bounds__(A2T, 2)
+k_adjoint2(const float *__restrict__ lam_in, const float4 *__restrict__ d4,
+           float *__restrict__ lam_out, float *__restrict__ b, float dt, Grid3 g, int ntk,
+           long long W, const float *__restrict__ G1, const float *__restrict__ G2) {
+    pdl_wait();
+    for_segments(g.N1, ntk, W, [&](int kt, int jt, int i0, int len) {
+        adjoint2_tile<FIRST, WRITE_LAM>(lam_in, d4, lam_out, b, dt, g, len, kt * A2K, jt * A2J, i0,
+                                        G1, G2);
+    });
+}
+
 // ==== host side: launch shapes, launchers, sweep orchestration, autotuner ====
 
 dim3 sweep_grid(const blr_plan *P) {
@@ -1084,6 +1292,10 @@ dim3 adjoint_grid(const blr_plan *P) {
 int adjoint_smem_attributes() {
     static bool done = false;
     if (done) return BLR_OK;
+    BLR_CK(cudaFuncSetAttribute(k_adjoint2<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ2_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_adjoint2<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ2_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_adjoint2<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ2_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_adjoint2<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ2_SMEM));
     BLR_CK(cudaFuncSetAttribute(k_adjoint_march<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
     BLR_CK(cudaFuncSetAttribute(k_adjoint_march<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
     BLR_CK(cudaFuncSetAttribute(k_adjoint_march<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
@@ -1236,6 +1448,28 @@ void launch_adjoint_t(const blr_plan *P, const float *lin, const float *mn, floa
     }
 }
 
+// Two adjoint steps n, n - 1 (k_adjoint2): lambda^{n-1} from lambda^{n+1} (when wlam),
+// b (+)= dt (lambda^{n+1} grad m^n + lambda^n grad m^{n-1}); G1, G2 = grad m^n, m^{n-1}.
+template <bool FIRST, bool WRITE_LAM>
+void launch_adjoint2_t(const blr_plan *P, const float *lin, float *lout, float *b, const float *G1,
+                       const float *G2, cudaStream_t s) {
+    const int ntk = (int)ceil_div_ll(P->N3, A2K);
+    const long long W = (long long)ntk * ceil_div_ll(P->N2, A2J) * P->N1;
+    long long G = (long long)P->adj2 * P->sms;
+    if (G > W) G = W;
+    cudaAccessPolicyWindow w;
+    launch_pdl_l2(d4_window(P, &w), k_adjoint2<FIRST, WRITE_LAM>, dim3((unsigned)G), dim3(A2T),
+                  ADJ2_SMEM, s, lin, (const float4 *)P->d4, lout, b, P->dt, P->grid, ntk, W, G1, G2);
+}
+
+void launch_adjoint2(const blr_plan *P, bool first, bool wlam, const float *lin, float *lout,
+                     float *b, const float *G1, const float *G2, cudaStream_t s) {
+    if (first && wlam) launch_adjoint2_t<true, true>(P, lin, lout, b, G1, G2, s);
+    else if (first) launch_adjoint2_t<true, false>(P, lin, lout, b, G1, G2, s);
+    else if (wlam) launch_adjoint2_t<false, true>(P, lin, lout, b, G1, G2, s);
+    else launch_adjoint2_t<false, false>(P, lin, lout, b, G1, G2, s);
+}
+
 // One adjoint step: lambda^n = S^T lambda^{n+1} (when wlam) and b (+)= dt lambda grad m^n.
 void launch_adjoint(const blr_plan *P, bool first, bool wlam, const float *lin, const float *mn,
                     float *lout, float *b, const float *Gn, cudaStream_t s) {
@@ -1335,6 +1569,25 @@ int sweep_adjoint(blr_plan *P, float *b, float *lambda0, const float *lam_final,
     const int nt = P->p.nt;
     const bool keep = P->lam_all && lam_final == P->lam_nt;
     int cur = 0;
+    if (P->adj2 && !keep && P->Gm && P->nvel == 1 && P->d4) {
+        // two steps per launch from the top, the last step alone when nt is odd
+        int n = nt - 1;
+        for (; n >= 1; n -= 2) {
+            const float *lin = (n == nt - 1) ? lam_final : P->lam[cur];
+            float *lout = (n - 1 == 0 && lambda0) ? lambda0 : P->lam[1 - cur];
+            const bool wlam = (n - 1 > 0) || (lambda0 != nullptr);
+            launch_adjoint2(P, n == nt - 1, wlam, lin, lout, b, grad_slot(P, n), grad_slot(P, n - 1), s);
+            BLR_CK_LAUNCH();
+            cur = 1 - cur;
+        }
+        if (n == 0) {
+            const float *lin = (nt == 1) ? lam_final : P->lam[cur];
+            launch_adjoint(P, nt == 1, lambda0 != nullptr, lin, state_slot(P, 0), lambda0, b,
+                           grad_slot(P, 0), s);
+            BLR_CK_LAUNCH();
+        }
+        return BLR_OK;
+    }
     for (int j = P->nseg - 1; j >= 0; --j) {
         int rc = ensure_segment(P, j, s);
         if (rc) return rc;
@@ -1562,6 +1815,9 @@ namespace {
 int time_step(blr_plan *P, int kind, cudaStream_t s) {
     if (kind == 1)
         launch_adjoint(P, false, true, P->lam[0], P->m, P->lam[1], P->b, grad_slot(P, 0), s);
+    else if (kind == 4)   // two adjoint steps in one launch
+        launch_adjoint2(P, false, true, P->lam[0], P->lam[1], P->b, grad_slot(P, 0),
+                        grad_slot(P, P->p.nt > 1 ? 1 : 0), s);
     else
         launch_incstate(P, false, false, P->dm[0], P->m, P->dm[1], 1.f,
                         kind == 3 ? grad_slot(P, 0) : nullptr, s, kind == 3);
@@ -1653,6 +1909,21 @@ int sweep_autotune(blr_plan *P, cudaStream_t s) {
             }
         P->adj_useg = best_u;
         P->bal_adj = best_b;
+        // two steps per launch: k_adjoint2 covers two steps, so it is compared with
+        // two launches of the best one-step shape
+        P->adj2 = 0;
+        if (P->Gm && P->nvel == 1 && P->p.nt > 1 && !rc) {
+            int best2 = 0;
+            for (int bps = 1; bps <= ADJ2_BLOCKS && !rc; ++bps) {
+                P->adj2 = bps;
+                const float t = 0.5f * time_shape(4);
+                if (t < best) {
+                    best = t;
+                    best2 = bps;
+                }
+            }
+            P->adj2 = best2;
+        }
     }
     if (!rc) tune_march(2);
     if (P->sweep_wide && !rc) {
