@@ -69,8 +69,8 @@ ADJ_BYTES = lambda nt: ((36 + 44 + 48 * (nt - 2)) if nt > 1 else 32)
 # of csrc/sweeps.cu (the text above its host-side marker line) is the code the
 # capture was taken from: SHA-256 of that text.
 SWEEPS_HOST_MARKER = "// ==== host side: launch shapes, launchers, sweep orchestration, autotuner ===="
-ADJ_TRAFFIC = {"sweeps_device_sha256": "da203be71439a4a829777d7c74f291929c9c70d155a5a8398a658a9065644bb4",
-               "bytes": 95065856 + 5990912}
+ADJ_TRAFFIC = {"sweeps_device_sha256": "36f427b1b307c5be9ac1f990d63b1f4e494775dc8fe769fc8cdabefeab99143f",
+               "bytes": 95279616 + 2032896}
 
 
 def adjoint_traffic():
@@ -102,17 +102,31 @@ def peaks():
 # ----------------------------------------------------------------------------
 
 
-def oracle_sample(out_path: str, samples: int):
+# the precision form's sample point (192x224x192, band 48^3, 10 steps, 8-voxel warp)
+N3C, B3C, SEED3, BOUND3 = (192, 224, 192), (48, 48, 48), 3001, 200.0
+
+
+def oracle_sample(out_path: str, samples: int, kind: str = "phantom128"):
+    """FP64 oracle timings in this (single-threaded) process.  phantom128: one
+    forward solve, gradient and Gauss-Newton HVP at 128^3 per sample;
+    precision192: the gradient and HVP of the precision form's sample point."""
     import numpy as np
 
     from oracle import blr_oracle as O
     from paper_1807_05117_gb300 import synth
 
-    I0, I1, _ = synth.phantom_pair(N, SEED, max_disp=MAX_DISP)
-    vt = synth.random_coefficients(BAND, SEED + 1, SAMPLE_BOUND)
-    dvt = synth.random_direction(BAND, SEED + 2)
+    if kind == "precision192":
+        I0, I1, _ = synth.phantom_pair(N3C, SEED3, max_disp=8.0)
+        vt = synth.random_coefficients(B3C, SEED3 + 1, BOUND3)
+        dvt = synth.random_direction(B3C, SEED3 + 2)
+        n, band = N3C, B3C
+    else:
+        I0, I1, _ = synth.phantom_pair(N, SEED, max_disp=MAX_DISP)
+        vt = synth.random_coefficients(BAND, SEED + 1, SAMPLE_BOUND)
+        dvt = synth.random_direction(BAND, SEED + 2)
+        n, band = N, BAND
     (_, I0d), (_, I1d), (_, vtd), (_, dvd) = synth.as_device_inputs(I0, I1, vt, dvt)
-    p = O.Params(N, BAND, NT)
+    p = O.Params(n, band, NT)
     times = []
     for _ in range(samples):
         t0 = time.perf_counter()
@@ -126,20 +140,53 @@ def oracle_sample(out_path: str, samples: int):
     np.savez(out_path, times=np.array(times), g=g, h=h, energy=pt.energy)
 
 
-def run_oracle_subprocess(samples: int):
-    import numpy as np
-    env = dict(os.environ)
-    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[k] = "1"
-    fd, path = tempfile.mkstemp(suffix=".npz")
-    os.close(fd)
-    try:
-        subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", path,
-                        "--samples", str(samples)], check=True, env=env, cwd=ROOT)
-        with np.load(path) as z:
-            return {k: z[k] for k in z.files}
-    finally:
-        os.unlink(path)
+def host_cores() -> int:
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+class OracleJobs:
+    """Oracle samples in fresh single-threaded interpreter processes (started with
+    fork + exec, so they share nothing with this process's CUDA context)."""
+
+    def __init__(self):
+        self.jobs = []
+
+    def start(self, samples: int, kind: str = "phantom128"):
+        import tempfile as tf
+        env = dict(os.environ)
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[k] = "1"
+        fd, path = tf.mkstemp(suffix=".npz")
+        os.close(fd)
+        proc = subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-sample", path,
+                                 "--samples", str(samples), "--oracle-kind", kind], env=env, cwd=ROOT)
+        self.jobs.append((proc, path))
+        return len(self.jobs) - 1
+
+    def result(self, i: int):
+        import numpy as np
+        proc, path = self.jobs[i]
+        if proc.wait() != 0:
+            raise RuntimeError(f"oracle sample process failed ({proc.returncode})")
+        try:
+            with np.load(path) as z:
+                return {k: z[k] for k in z.files}
+        finally:
+            os.unlink(path)
+
+
+def run_oracle_subprocess(samples: int, kind: str = "phantom128"):
+    jobs = OracleJobs()
+    return jobs.result(jobs.start(samples, kind))
+
+
+def run_oracle_parallel(nproc: int, samples: int):
+    """nproc concurrent single-threaded oracle processes of `samples` 128^3 samples
+    each (one process per host core): the throughput of the FP64 oracle on all
+    cores.  Returns the per-process results."""
+    jobs = OracleJobs()
+    ids = [jobs.start(samples) for _ in range(nproc)]
+    return [jobs.result(i) for i in ids]
 
 
 # ----------------------------------------------------------------------------
@@ -192,20 +239,25 @@ def main_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    res = run_oracle_subprocess(args.warmup + args.steps)
-    t = res["times"][args.warmup:]
-    per = [registration_seconds(a, b, c, **NOMINAL_COUNTS) for a, b, c in t]
-    s_per_reg = sum(per) / len(per)
-    value = 1.0 / s_per_reg
-    sample = (f"per step: one FP64 forward solve, gradient and Gauss-Newton HVP at 128^3 "
-              f"(band 32^3, nt 10), scaled by the registration's nominal counts "
-              f"{NOMINAL_COUNTS}; oracle wall time {sum(sum(x) for x in t) / len(t):.2f} s per sample")
+    cores = host_cores()
+    res = run_oracle_parallel(cores, args.warmup + args.steps)
+    # step k: every process's k-th sample, concurrently; the step's throughput is the
+    # sum over the processes of one registration per (scaled) sample time
+    per_step = []
+    for k in range(args.warmup, args.warmup + args.steps):
+        per_step.append(sum(1.0 / registration_seconds(*r["times"][k], **NOMINAL_COUNTS) for r in res))
+    value = sum(per_step) / len(per_step)
+    wall = sum(sum(r["times"][args.warmup:].sum(axis=1)) for r in res) / len(res) / args.steps
+    sample = (f"per step: on each of {cores} host cores at once, one single-threaded FP64 forward "
+              f"solve, gradient and Gauss-Newton HVP at 128^3 (band 32^3, nt 10), each scaled to a "
+              f"registration by the nominal counts {NOMINAL_COUNTS}; {wall:.2f} s of oracle time per "
+              f"sample")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "registrations/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * s_per_reg, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config("f64 oracle", 1),
-            "cpu_baseline": {"value": value, "unit": "registrations/s", "cores": 1,
+            "cpu_baseline": {"value": value, "unit": "registrations/s", "cores": cores,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "registrations/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -434,6 +486,15 @@ def main_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    # the FP64 oracle (CPU baseline and the reference values of the HVP errors) runs
+    # in its own processes on the host cores, before any GPU work, so that it
+    # neither competes with the timed GPU runs for host time nor shares their process
+    oracle = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        oracle = {"single": run_oracle_subprocess(1)}
+        oracle["all"] = run_oracle_parallel(host_cores(), 1)
+        if not args.no_configs:
+            oracle["precision192"] = run_oracle_subprocess(1, "precision192")
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -528,17 +589,25 @@ def main_ours(args):
                        "d2h_bytes_per_step": hvt.numel() * 8}
 
     # FP64 oracle on the host cores (rank 0, one GPU only) and the HVP errors
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out = run_oracle_subprocess(1)
+    if oracle is not None:
+        out = oracle["single"]
         ts, tg, th = out["times"][0]
         counts = dict(n_state=rep.n_state, n_grad=rep.newton_iters + 1, n_hvp=rep.n_hessvec)
         sec = registration_seconds(ts, tg, th, **counts)
+        cores = len(oracle["all"])
+        allv = sum(1.0 / registration_seconds(*r["times"][0], **counts) for r in oracle["all"])
+        allh = sum(1.0 / r["times"][0][2] for r in oracle["all"])
         line["cpu_baseline"] = {
-            "value": 1.0 / sec, "unit": "registrations/s", "cores": 1, "kind": "oracle",
-            "hvp_per_s": 1.0 / th,
-            "sample": (f"one FP64 forward solve ({ts:.2f} s), gradient ({tg:.2f} s) and "
-                       f"Gauss-Newton HVP ({th:.2f} s) at 128^3, single thread, scaled by "
-                       f"this run's operation counts {counts}")}
+            "value": allv, "unit": "registrations/s", "cores": cores, "kind": "oracle",
+            "hvp_per_s": allh,
+            "sample": (f"on each of {cores} host cores at once, one single-threaded FP64 forward "
+                       f"solve, gradient and Gauss-Newton HVP at 128^3, each scaled to a "
+                       f"registration by this run's operation counts {counts}; value and "
+                       f"hvp_per_s are summed over the cores"),
+            "single_thread": {
+                "value": 1.0 / sec, "unit": "registrations/s", "cores": 1, "hvp_per_s": 1.0 / th,
+                "sample": (f"one FP64 forward solve ({ts:.2f} s), gradient ({tg:.2f} s) and "
+                           f"Gauss-Newton HVP ({th:.2f} s) at 128^3 on one core alone")}}
         # the sample point on the GPU, for the errors against the FP64 oracle
         vt_s = synth.random_coefficients(BAND, SEED + 1, SAMPLE_BOUND)
         I0s, I1s, _ = synth.phantom_pair(N, SEED, max_disp=MAX_DISP)
@@ -557,10 +626,17 @@ def main_ours(args):
             line["by_precision"][p]["grad_rel_err_vs_fp64"] = eg
         line["hvp_rel_err"] = line["by_precision"][args.precision]["hvp_rel_err_vs_fp64"]
 
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     for r in res.values():
         r["plan"].close()
+    # the precision, batching and differentiation forms' configurations (one GPU)
+    if rank == 0 and world == 1 and not args.no_configs:
+        line["configs"] = {
+            "precision_form": measure_precision_form(
+                dev, flush, stream, oracle.get("precision192") if oracle else None),
+            "batching_form": batch_measure(1, 1, dev, flush, stream, one_by_one=False),
+            "differentiation_form": measure_differentiation_form(dev, flush, stream)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -570,8 +646,11 @@ def main_ours(args):
 UNEVEN_PAIRS, UNEVEN_SEED = 64, 4
 
 
-def main_batch(args):
-    """The batching form on the 64-pair workload (FP32, 10 time steps)."""
+def batch_measure(steps, warmup, dev, flush, stream, one_by_one=True):
+    """The batching form on the 64-pair workload (FP32, 10 time steps): one step =
+    a fixed-work registration (10 Newton x 20 PCG) of every pair through
+    blr_batch_newton; with one_by_one, the same registrations through single plans
+    are timed beside it."""
     import multiprocessing as mp
 
     import torch
@@ -582,10 +661,6 @@ def main_batch(args):
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
         imgs = pool.starmap(synth.phantom_pair_f32,
                             [(p["n"], p["seed"], p["max_disp"]) for p in pairs])
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(0)
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     t0 = time.perf_counter()
     batch = blr.Batch([(p["n"], p["band"]) for p in pairs], NT)
     create_s = time.perf_counter() - t0
@@ -601,69 +676,236 @@ def main_batch(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
 
-    def timed(fn, steps):
+    def timed(fn, n):
         tot = 0.0
         out = None
-        for k in range(steps):
+        for k in range(n):
             flush.fill_(k & 0xFF)
             e0.record(stream)
             out = fn()
             e1.record(stream)
             e1.synchronize()
             tot += e0.elapsed_time(e1)
-        return tot / max(steps, 1), out
+        return tot / max(n, 1), out
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     sampler = ClockSampler()
     sampler.start()
     l0 = blr.blr_kernel_launches()
-    ms, reps = timed(step, args.steps)
+    ms, reps = timed(step, steps)
     launches = blr.blr_kernel_launches() - l0
     clocks = sampler.stop(0)
-
-    # the same registrations one pair at a time through single plans
-    plans = []
-    for i, p in enumerate(pairs):
-        pl = blr.Plan(p["n"], p["band"], NT)
-        pl.set_images(torch.from_numpy(imgs[i][0]).to(dev), torch.from_numpy(imgs[i][1]).to(dev))
-        plans.append(pl)
-
-    def serial():
-        for pl, v in zip(plans, vts):
-            v.zero_()
-            pl.newton(v, NEWTON, PCG, 0.0, 0.0)
-
-    serial()
-    ms_serial, _ = timed(serial, max(1, min(args.steps, 2)))
-    for pl in plans:
-        pl.close()
     voxels = sum(p["n"][0] * p["n"][1] * p["n"][2] for p in pairs)
+    # stepwise algorithmic bytes of the registrations' operators (survey per-unit figures):
+    # HVP (24 + 84 nt) V, gradient (32 + 68 nt) V, extra forward solve (20 nt + 12) V
+    nbytes = 0
+    for p, r in zip(pairs, reps):
+        V = p["n"][0] * p["n"][1] * p["n"][2]
+        ngrad = r.newton_iters + 1
+        nbytes += V * (r.n_hessvec * (24 + 84 * NT) + ngrad * (32 + 68 * NT)
+                       + (r.n_state - ngrad) * (20 * NT + 12))
+    peak, peak_kind = peaks()
+    achieved = nbytes / (ms / 1e3) / 1e9
     grids = sorted({tuple(p["n"]) for p in pairs})
-    line = {"metric": "registrations/s, 64 uneven pairs (batching form)",
-            "value": UNEVEN_PAIRS * 1000.0 / ms, "unit": "registrations/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+    out = {"metric": "registrations/s, 64 uneven pairs (batching form)",
+           "value": UNEVEN_PAIRS * 1000.0 / ms, "unit": "registrations/s", "ms_per_step": ms,
+           "steps": steps, "warmup": warmup,
+           "workload": (f"{UNEVEN_PAIRS} phantom pairs, grids {grids}, bands 16^3/24^3/32^3, 3-8 "
+                        "voxel warps, 10 time steps, 10 Newton x 20 PCG (fixed work) per pair, FP32"),
+           "voxels_total": voxels, "gpu_launches": int(launches), "clocks": clocks,
+           "batch_create_s": create_s,
+           "gvoxel_steps_per_s": voxels * NT * (NEWTON * PCG) / (ms / 1000.0) / 1e9,
+           "status": sorted({r.status for r in reps}),
+           "roofline": {"kernel": "all operators of the registrations (stepwise algorithmic bytes)",
+                        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "peak_source": f"{peak_kind} hbm_gbs",
+                        "algorithmic_bytes_per_step": nbytes}}
+    if one_by_one:
+        plans = []
+        for i, p in enumerate(pairs):
+            pl = blr.Plan(p["n"], p["band"], NT)
+            pl.set_images(torch.from_numpy(imgs[i][0]).to(dev), torch.from_numpy(imgs[i][1]).to(dev))
+            plans.append(pl)
+
+        def serial():
+            for pl, v in zip(plans, vts):
+                v.zero_()
+                pl.newton(v, NEWTON, PCG, 0.0, 0.0)
+
+        serial()
+        ms_serial, _ = timed(serial, max(1, min(steps, 2)))
+        for pl in plans:
+            pl.close()
+        out["one_by_one"] = {"value": UNEVEN_PAIRS * 1000.0 / ms_serial, "unit": "registrations/s",
+                             "ms_per_step": ms_serial}
+    batch.close()
+    return out
+
+
+def main_batch(args):
+    """The batching form on the 64-pair workload (FP32, 10 time steps)."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    r = batch_measure(args.steps, args.warmup, dev, flush, torch.cuda.current_stream())
+    line = {"metric": r.pop("metric"), "value": r.pop("value"), "unit": r.pop("unit"), "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r.pop("ms_per_step"),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": (f"{UNEVEN_PAIRS} phantom pairs, grids {grids}, bands "
-                                    "16^3/24^3/32^3, 3-8 voxel warps, 10 time steps, "
-                                    "10 Newton x 20 PCG (fixed work) per pair"),
-                       "voxels_total": voxels, "l2": "flushed between timed steps"},
-            "gpu_launches": int(launches), "clocks": clocks,
-            "batch_create_s": create_s,
-            "one_by_one": {"value": UNEVEN_PAIRS * 1000.0 / ms_serial,
-                           "unit": "registrations/s", "ms_per_step": ms_serial},
-            "gvoxel_steps_per_s": voxels * NT * (NEWTON * PCG) / (ms / 1000.0) / 1e9,
-            "status": sorted({r.status for r in reps})}
+            "config": {"workload": r.pop("workload"), "voxels_total": r.pop("voxels_total"),
+                       "l2": "flushed between timed steps"}}
+    line.update(r)
     print(json.dumps(line), flush=True)
-    batch.close()
     return 0
 
 
-def probe(precision="fp32", hessian=0):
+def measure_precision_form(dev, flush, stream, ref, reps=2, hvp_reps=20):
+    """The precision form's configuration (192x224x192, band 48^3, 10 steps, 8-voxel
+    phantom warp): fixed-work registrations and Gauss-Newton HVPs in both
+    precisions, each HVP's error against the FP64 oracle at the sample point."""
+    import numpy as np
+    import torch
+
+    from paper_1807_05117_gb300 import blr, synth
+
+    I0, I1, _ = synth.phantom_pair(N3C, SEED3, max_disp=8.0)
+    vt = synth.random_coefficients(B3C, SEED3 + 1, BOUND3)
+    dvt = synth.random_direction(B3C, SEED3 + 2)
+    (I0f, _), (I1f, _), (vtf, _), (dvf, _) = synth.as_device_inputs(I0, I1, vt, dvt)
+    I0g, I1g = torch.from_numpy(I0f).to(dev), torch.from_numpy(I1f).to(dev)
+    vtg, dvg = torch.from_numpy(vtf).to(dev), torch.from_numpy(dvf).to(dev)
+    V = N3C[0] * N3C[1] * N3C[2]
+    peak, peak_kind = peaks()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    out = {"workload": ("192x224x192 phantom pair (the paper's 180x210x180 brains padded), band "
+                        "48^3, 10 time steps, 8-voxel warp, 10 Newton x 20 PCG (fixed work)"),
+           "grid": list(N3C), "band": list(B3C), "nt": NT}
+    for precision in ("mixed", "fp32"):
+        plan = blr.Plan(N3C, B3C, NT, precision=blr.BLR_MIXED if precision == "mixed" else blr.BLR_FP32)
+        plan.set_images(I0g, I1g)
+        v = torch.zeros((3,) + B3C, dtype=torch.complex64, device=dev)
+
+        def step():
+            v.zero_()
+            return plan.newton(v, NEWTON, PCG, 0.0, 0.0)
+
+        step()
+        tot = 0.0
+        for k in range(reps):
+            flush.fill_(k & 0xFF)
+            e0.record(stream)
+            rep = step()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        ms = tot / reps
+        g = torch.empty_like(vtg)
+        h = torch.empty_like(vtg)
+        plan.gradient(vtg, g)
+        for _ in range(3):
+            plan.hessvec(dvg, h)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(hvp_reps):
+            plan.hessvec(dvg, h)
+        e1.record(stream)
+        e1.synchronize()
+        hvp_ms = e0.elapsed_time(e1) / hvp_reps
+        nbytes = (24 + 84 * NT) * V
+        achieved = nbytes / (hvp_ms / 1e3) / 1e9
+        d = {"registrations_per_s": 1000.0 / ms, "ms_per_registration": ms,
+             "hvp_per_s": 1000.0 / hvp_ms, "hvp_ms": hvp_ms, "energy0": rep.energy0,
+             "final_energy": rep.energy, "pcg_iters": rep.pcg_iters, "status": rep.status,
+             "autotuned": plan.tuning(),
+             "roofline": {"kernel": "whole Gauss-Newton HVP (stepwise algorithmic bytes)",
+                          "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                          "frac": achieved / peak, "traffic": None,
+                          "peak_source": f"{peak_kind} hbm_gbs",
+                          "algorithmic_bytes_per_hvp": nbytes}}
+        if ref is not None:
+            d["hvp_rel_err_vs_fp64"] = float(np.linalg.norm(h.cpu().numpy() - ref["h"]) / np.linalg.norm(ref["h"]))
+            d["grad_rel_err_vs_fp64"] = float(np.linalg.norm(g.cpu().numpy() - ref["g"]) / np.linalg.norm(ref["g"]))
+        out[precision] = d
+        plan.close()
+    out["mixed_over_fp32"] = {"hvp": out["mixed"]["hvp_per_s"] / out["fp32"]["hvp_per_s"],
+                              "registration": out["mixed"]["registrations_per_s"] / out["fp32"]["registrations_per_s"]}
+    return out
+
+
+N5, B5, NT5, CK5 = (256, 256, 256), (32, 32, 32), 20, 4
+
+
+def measure_differentiation_form(dev, flush, stream, reps=3):
+    """The differentiation form's configuration: the registration energy as a
+    torch.autograd.Function on a 256^3 FP32 phantom pair (band 32^3, 20 steps,
+    the state checkpointed every 4 steps); one step = forward + backward (the
+    adjoint kernel chain with segment recomputation)."""
+    import numpy as np
+    import torch
+
+    from paper_1807_05117_gb300 import blr, synth
+    from paper_1807_05117_gb300.autograd import registration_energy
+
+    I0, I1, _ = synth.phantom_pair(N5, 5001, max_disp=6.0)
+    vt = synth.random_coefficients(B5, 5002, 240.0)
+    (I0f, _), (I1f, _), (vtf, _) = synth.as_device_inputs(I0, I1, vt)
+    plan = blr.Plan(N5, B5, NT5, ckpt_every=CK5)
+    plan.set_images(torch.from_numpy(I0f).to(dev), torch.from_numpy(I1f).to(dev))
+    v = torch.from_numpy(vtf).to(dev).requires_grad_(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def step():
+        v.grad = None
+        E = registration_energy(v, plan)
+        E.backward()
+        return E
+
+    step()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for k in range(reps):
+        flush.fill_(k & 0xFF)
+        e0.record(stream)
+        E = step()
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    ms = tot / reps
+    status = plan.status()
+    V = N5[0] * N5[1] * N5[2]
+    nseg = -(-NT5 // CK5)
+    # forward (displacement 12 + 20 per step), the backward's recomputation of the
+    # non-checkpoint states, the adjoint (48 per step), the projection (12)
+    nbytes = (12 + 20 * NT5 + 20 * (NT5 - nseg) + 48 * NT5 + 12) * V
+    peak, peak_kind = peaks()
+    achieved = nbytes / (ms / 1e3) / 1e9
+    out = {"workload": ("256^3 phantom pair, band 32^3, 20 time steps, state checkpointed every "
+                        "4 steps (recomputed per segment in backward), FP32; one step = "
+                        "registration_energy forward + backward"),
+           "gradients_per_s": 1000.0 / ms, "ms_per_gradient": ms, "energy": float(E),
+           "grad_norm": float(torch.linalg.vector_norm(v.grad)), "status": status,
+           "roofline": {"kernel": "forward + checkpointed backward (stepwise algorithmic bytes)",
+                        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "peak_source": f"{peak_kind} hbm_gbs",
+                        "algorithmic_bytes_per_gradient": nbytes}}
+    plan.close()
+    del I0, I1, np
+    return out
+
+
+def probe(precision="fp32", hessian=0, tuning=None):
     """A few launches of every hot-path kernel at the benchmark size, for ncu
-    (hessian=1: the full Newton Hessian's kernels as well)."""
+    (hessian=1: the full Newton Hessian's kernels as well).  tuning: sweep shapes
+    (a dict of Plan.tuning() keys) that replace the autotuner's choice, e.g. the
+    choice of a run without the profiler, whose interception of every launch
+    distorts the autotuner's timings."""
     import numpy as np
     import torch
 
@@ -677,6 +919,12 @@ def probe(precision="fp32", hessian=0):
     prec = blr.BLR_MIXED if precision == "mixed" else blr.BLR_FP32
     with blr.Plan(N, BAND, NT, precision=prec, hessian=hessian) as plan:
         plan.set_images(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev))
+        if tuning:
+            plan.set_tuning(**{k: v for k, v in tuning.items() if k not in ("wide_sweeps", "grad_kept")})
+        torch.cuda.synchronize()
+        # the launches of the hot path (not the plan's autotuner): an NVTX range
+        # that profilers can select (ncu --nvtx --nvtx-include "probe/")
+        torch.cuda.nvtx.range_push("probe")
         g = torch.empty((3,) + BAND, dtype=torch.complex64, device=dev)
         plan.gradient(torch.from_numpy(c).to(dev), g)
         h = torch.empty_like(g)
@@ -687,6 +935,7 @@ def probe(precision="fp32", hessian=0):
         for _ in range(2):
             plan.adjoint(bf)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         assert plan.status() == blr.BLR_OK
         print("probe tuning", json.dumps(plan.tuning()))
     print("probe ok", float(np.abs(h.cpu().numpy()).max()))
@@ -715,14 +964,21 @@ def main():
                     help="short run for profilers: one gradient, 3 HVPs, 2 adjoint solves")
     ap.add_argument("--probe-hessian", type=int, default=0, choices=[0, 1],
                     help="with --probe: 1 probes a full-Newton plan")
+    ap.add_argument("--probe-tuning", default=None,
+                    help="with --probe: JSON of sweep shapes (Plan.tuning() keys) to use instead of "
+                         "the autotuner's choice")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the precision, batching and differentiation forms' configurations")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--samples", type=int, default=1, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-kind", default="phantom128", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_sample:
-        oracle_sample(args.oracle_sample, args.samples)
+        oracle_sample(args.oracle_sample, args.samples, args.oracle_kind)
         return 0
     if args.probe:
-        return probe(args.precision, args.probe_hessian)
+        return probe(args.precision, args.probe_hessian,
+                     json.loads(args.probe_tuning) if args.probe_tuning else None)
     if args.impl == "reference":
         return main_reference(args)
     if args.workload == "uneven64":

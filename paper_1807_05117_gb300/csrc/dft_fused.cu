@@ -207,10 +207,11 @@ __device__ __forceinline__ void store_chunk(uint8_t *hi_tile, size_t tb, uint32_
 // ---------------------------------------------------------------------------
 // k_ex1: P1[c][x1][col] = sum_j1 (cos + i sin)(2 pi k_j1 x1 / N1) v~[c][j1][col], col = (j2, j3),
 // a complex GEMM [N1 x B1] x [B1 x B2 B3] per component (cos / sin from W1, rows
-// 2j = cos, 2j+1 = -sin).  A block computes a 32 (x1) x 64 (col) tile; j1 runs in
-// chunks of 32 staged in shared memory, summed in order.  Thread (ty, tx) owns x1
-// rows 2 ty, 2 ty + 1 and columns tx + 16 q (q < 4): stores are coalesced.
-constexpr int EX_TX = 32, EX_TC = 64, EX_TK = 32;
+// 2j = cos, 2j+1 = -sin).  A block computes a 16 (x1) x 64 (col) tile; j1 runs in
+// chunks of 32 staged in shared memory (the next chunk's loads in flight during
+// this chunk's sums), summed in order.  Thread (ty, tx) owns x1 row ty and
+// columns tx + 16 q (q < 4): stores are coalesced.
+constexpr int EX_TX = 16, EX_TC = 64, EX_TK = 32;
 constexpr int EX_NE = EX_TK * EX_TX / 256, EX_NV = EX_TK * EX_TC / 256;   // loads per thread
 __global__ void __launch_bounds__(256)
 k_ex1(const float2 *__restrict__ vt, const float *__restrict__ W1, float2 *__restrict__ P1,
@@ -220,11 +221,9 @@ k_ex1(const float2 *__restrict__ vt, const float *__restrict__ W1, float2 *__res
     const int c = blockIdx.z, x0 = blockIdx.y * EX_TX, c0 = blockIdx.x * EX_TC;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     pdl_trigger();   // k_fx may launch and fetch its tables meanwhile
-    float2 acc[2][4];
+    float2 acc[4];
 #pragma unroll
-    for (int r = 0; r < 2; ++r)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[r][q] = make_float2(0.f, 0.f);
+    for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
     // chunk k0's operands into registers (every load issued before any is used)
     float2 re[EX_NE], rv[EX_NV];
     auto load_e = [&](int k0) {
@@ -266,36 +265,32 @@ k_ex1(const float2 *__restrict__ vt, const float *__restrict__ W1, float2 *__res
         }
 #pragma unroll 8
         for (int kk = 0; kk < EX_TK; ++kk) {
-            const float2 e0 = sE[kk][2 * ty], e1 = sE[kk][2 * ty + 1];
+            const float2 e = sE[kk][ty];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const float2 v = sV[kk][tx + 16 * q];
-                acc[0][q].x = fmaf(e0.x, v.x, fmaf(-e0.y, v.y, acc[0][q].x));
-                acc[0][q].y = fmaf(e0.x, v.y, fmaf(e0.y, v.x, acc[0][q].y));
-                acc[1][q].x = fmaf(e1.x, v.x, fmaf(-e1.y, v.y, acc[1][q].x));
-                acc[1][q].y = fmaf(e1.x, v.y, fmaf(e1.y, v.x, acc[1][q].y));
+                acc[q].x = fmaf(e.x, v.x, fmaf(-e.y, v.y, acc[q].x));
+                acc[q].y = fmaf(e.x, v.y, fmaf(e.y, v.x, acc[q].y));
             }
         }
     }
+    const int x1 = x0 + ty;
+    if (x1 >= N1) return;
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int x1 = x0 + 2 * ty + r;
-        if (x1 >= N1) continue;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int col = c0 + tx + 16 * q;
-            if (col < nb23) P1[((long long)c * N1 + x1) * nb23 + col] = acc[r][q];
-        }
+    for (int q = 0; q < 4; ++q) {
+        const int col = c0 + tx + 16 * q;
+        if (col < nb23) P1[((long long)c * N1 + x1) * nb23 + col] = acc[q];
     }
 }
 
 // ---------------------------------------------------------------------------
 // k_p1: pi(f)_c(j1, col) = sum_x1 (cos - i sin)(2 pi k_j1 x1 / N1) sum_t Q2[c][x1][t][col]
 // (+ areg A(j) vadd), a complex GEMM [B1 x N1] x [N1 x B2 B3] per component.  A
-// block computes a 16 (j1) x 32 (col) tile; x1 runs in chunks of 32 staged in
-// shared memory (the x2-tile partial sums added while staging), summed in order.
-// Thread (ty, tx) owns frequency j1 = ty and columns tx, tx + 16.
-constexpr int P1_TJ = 16, P1_TC = 32, P1_TK = 32;
+// block computes an 8 (j1) x 32 (col) tile; x1 runs in chunks of 32 staged in
+// shared memory (the x2-tile partial sums added while staging; the next chunk's
+// loads in flight during this chunk's sums), summed in order.  Thread (ty, tx)
+// owns frequency j1 = ty and column tx.
+constexpr int P1_TJ = 8, P1_TC = 32, P1_TK = 32;
 constexpr int P1_NE = P1_TK * P1_TJ / 256, P1_NQ = P1_TK * P1_TC / 256;   // loads per thread
 __global__ void __launch_bounds__(256)
 k_p1(const float2 *__restrict__ Q2, const float *__restrict__ W1, float2 *__restrict__ ft,
@@ -304,8 +299,8 @@ k_p1(const float2 *__restrict__ Q2, const float *__restrict__ W1, float2 *__rest
     __shared__ float2 sE[P1_TK][P1_TJ + 1];   // [x1][j1]: (cos, -sin)
     __shared__ float2 sQ[P1_TK][P1_TC];       // [x1][col]
     const int c = blockIdx.z, j0 = blockIdx.y * P1_TJ, c0 = blockIdx.x * P1_TC;
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    float2 acc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    float2 acc = make_float2(0.f, 0.f);
     float2 re[P1_NE], rq[P1_NQ];
     auto load_e = [&](int k0) {
 #pragma unroll
@@ -353,32 +348,23 @@ k_p1(const float2 *__restrict__ Q2, const float *__restrict__ W1, float2 *__rest
             load_q(k0 + P1_TK);
         }
 #pragma unroll 8
-        for (int kk = 0; kk < P1_TK; ++kk) {
-            const float2 e = sE[kk][ty];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {   // (qr + i qi)(cos - i sin)
-                const float2 v = sQ[kk][tx + 16 * q];
-                acc[q].x = fmaf(v.x, e.x, fmaf(-v.y, e.y, acc[q].x));
-                acc[q].y = fmaf(v.y, e.x, fmaf(v.x, e.y, acc[q].y));
-            }
+        for (int kk = 0; kk < P1_TK; ++kk) {   // (qr + i qi)(cos - i sin)
+            const float2 e = sE[kk][ty], v = sQ[kk][tx];
+            acc.x = fmaf(v.x, e.x, fmaf(-v.y, e.y, acc.x));
+            acc.y = fmaf(v.y, e.x, fmaf(v.x, e.y, acc.y));
         }
     }
-    const int j = j0 + ty;
-    if (j >= B1) return;
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const int col = c0 + tx + 16 * q;
-        if (col >= nb23) continue;
-        const long long o = ((long long)c * B1 + j) * nb23 + col;
-        float2 r = acc[q];
-        if (vadd) {
-            const float a = areg * Aw[(long long)j * nb23 + col];
-            const float2 v = vadd[o];
-            r.x = fmaf(a, v.x, r.x);
-            r.y = fmaf(a, v.y, r.y);
-        }
-        ft[o] = r;
+    const int j = j0 + ty, col = c0 + tx;
+    if (j >= B1 || col >= nb23) return;
+    const long long o = ((long long)c * B1 + j) * nb23 + col;
+    float2 r = acc;
+    if (vadd) {
+        const float a = areg * Aw[(long long)j * nb23 + col];
+        const float2 v = vadd[o];
+        r.x = fmaf(a, v.x, r.x);
+        r.y = fmaf(a, v.y, r.y);
     }
+    ft[o] = r;
 }
 
 // ---------------------------------------------------------------------------
