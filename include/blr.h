@@ -6,8 +6,8 @@
  * diffeomorphic registration parameterized in the space of band-limited vector
  * fields" (arXiv 1807.05117): the state-equation variant (stationary or
  * non-stationary velocity, Gauss-Newton or full Newton Hessian) and the
- * deformation-state-equation variant (Gauss-Newton); compressible or
- * incompressible velocities.
+ * deformation-state-equation variant (stationary, Gauss-Newton or full
+ * Newton Hessian); compressible or incompressible velocities.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -109,7 +109,8 @@ typedef struct blr_params {
                      /* the plain operators.  Batches reject it.             */
     int hessian;     /* BLR_GAUSS_NEWTON or BLR_NEWTON.  BLR_NEWTON keeps   */
                      /* every adjoint and incremental state (2 nt V floats  */
-                     /* more), so it takes no checkpoints; batches reject it */
+                     /* more; 6 nt V for the deformation state equation),   */
+                     /* so it takes no checkpoints; batches reject it       */
     int nonstationary; /* 0: one velocity v~ for all steps.  1: one per time */
                      /* step, v~^n transporting step n (the time-varying    */
                      /* v~_t of Section 3.2): every velocity, gradient, HVP, */
@@ -127,9 +128,10 @@ typedef struct blr_params {
                      /* periodic).  The adjoint is the vector rho, from       */
                      /* rho^nt = lambda(1) grad T[I0](x + u^nt); the body     */
                      /* force is dt sum_n (rho^{n+1} + sum_c rho_c^{n+1}      */
-                     /* grad u^n_c(x + d)).  Stationary velocity, Gauss-Newton, */
-                     /* no checkpoints; blr_adjoint takes no lambda0; batches */
-                     /* reject it.  Keeps 3 (nt + 1) V floats of u^n.        */
+                     /* grad u^n_c(x + d)).  Stationary velocity, no         */
+                     /* checkpoints; either Hessian; blr_adjoint takes no    */
+                     /* lambda0; batches reject it.  Keeps 3 (nt + 1) V      */
+                     /* floats of u^n.                                      */
 } blr_params;
 
 /* Result of blr_newton (host struct filled by the library). */
@@ -222,6 +224,12 @@ int blr_gradient_at_state(blr_plan_t plan, float *g, blr_stream_t stream);
  *   D_a and Hess the first and second derivatives of the trilinear cell
  *   polynomial at the departure point (the adjoint states are computed on the
  *   first call after a forward solve when blr_gradient has not done so).
+ * BLR_NEWTON with BLR_STATE_DEFORMATION (Eqs. 19-21 without the drops), with the
+ *   gradient's adjoint states rho^n and du^n the incremental deformation:
+ *   drho^nt = dlambda(1) grad T[I0](x+u^nt) + lambda(1) Hess T[I0](x+u^nt) du^nt,
+ *   drho^n_c = S^T drho^{n+1}_c + sum_a D_a^T (dd_a rho^{n+1}_c),
+ *   db_a = dt sum_n (drho_a^{n+1} + sum_c [drho_c^{n+1} D_a u_c^n
+ *          + rho_c^{n+1} (D_a du_c^n + (Hess T[u_c^n] dd)_a)]).
  * dvt: device input, hdv: device output, 2*3*B1*B2*B3 floats each.
  * Needs a prior blr_state / blr_gradient (BLR_ESTATE). */
 int blr_hessvec(blr_plan_t plan, const float *dvt, float *hdv,

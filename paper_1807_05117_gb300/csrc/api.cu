@@ -84,10 +84,9 @@ int validate(const blr_params *p) {
     if (p->nonstationary && p->hessian == BLR_NEWTON) return BLR_EINVAL;
     if (p->state_equation != BLR_STATE_IMAGE && p->state_equation != BLR_STATE_DEFORMATION)
         return BLR_EINVAL;
-    // the deformation variant: stationary velocity, Gauss-Newton, every state kept
+    // the deformation variant: stationary velocity, every state kept
     if (p->state_equation == BLR_STATE_DEFORMATION &&
-        (p->nonstationary || p->hessian != BLR_GAUSS_NEWTON ||
-         (p->ckpt_every > 0 && p->ckpt_every < p->nt)))
+        (p->nonstationary || (p->ckpt_every > 0 && p->ckpt_every < p->nt)))
         return BLR_EINVAL;
     // the full Hessian keeps every adjoint and incremental state: no checkpoints
     if (p->hessian == BLR_NEWTON && p->ckpt_every > 0 && p->ckpt_every < p->nt) return BLR_EINVAL;
@@ -123,11 +122,20 @@ size_t layout(blr_plan *P, char *base) {
     P->d4 = P->d4_base = P->sweep_wide ? a.take<float4>((size_t)P->nvel * V) : nullptr;
     P->lam[0] = a.take<float>(V);
     P->lam[1] = a.take<float>(V);
+    const bool def = P->p.state_equation == BLR_STATE_DEFORMATION;
+    P->rho_all = P->du_all = nullptr;
     if (P->p.hessian == BLR_NEWTON) {
         const int nt = P->p.nt;
-        P->lam_all = a.take<float>((size_t)nt * V);
-        P->lam_nt = P->lam_all + (size_t)(nt - 1) * V;
-        P->dm_all = nt > 1 ? a.take<float>((size_t)(nt - 1) * V) : nullptr;
+        if (def) {   // the vector adjoint and incremental states instead of lambda, dm
+            P->lam_all = P->dm_all = nullptr;
+            P->lam_nt = a.take<float>(V);
+            P->rho_all = a.take<float>((size_t)3 * nt * V);
+            P->du_all = nt > 1 ? a.take<float>((size_t)3 * (nt - 1) * V) : nullptr;
+        } else {
+            P->lam_all = a.take<float>((size_t)nt * V);
+            P->lam_nt = P->lam_all + (size_t)(nt - 1) * V;
+            P->dm_all = nt > 1 ? a.take<float>((size_t)(nt - 1) * V) : nullptr;
+        }
         P->nt_kap = a.take<float>((size_t)8 * V);
         P->nt_lob = a.take<uint8_t>(V);
     } else {
@@ -135,9 +143,9 @@ size_t layout(blr_plan *P, char *base) {
         P->nt_lob = nullptr;
         P->lam_nt = a.take<float>(V);
     }
-    if (P->p.state_equation == BLR_STATE_DEFORMATION) {
+    if (def) {
         P->U = a.take<float>((size_t)3 * (P->p.nt + 1) * V);
-        P->rho_nt = a.take<float>(3 * V);
+        P->rho_nt = P->rho_all ? P->rho_all + (size_t)3 * (P->p.nt - 1) * V : a.take<float>(3 * V);
         P->rho[0] = a.take<float>(3 * V);
         P->rho[1] = a.take<float>(3 * V);
         P->du[0] = a.take<float>(3 * V);
@@ -260,15 +268,20 @@ int gradient_here(blr_plan *P, float *g, cudaStream_t s) {
 int hessvec_here(blr_plan *P, const float *dvt, float *hdv, cudaStream_t s) {
     int rc;
     const bool full = P->p.hessian == BLR_NEWTON;
-    if (full && !P->have_lams && (rc = sweep_adjoint(P, P->b, nullptr, P->lam_nt, s))) return rc;
+    if (full && !P->have_lams && P->p.state_equation == BLR_STATE_IMAGE &&
+        (rc = sweep_adjoint(P, P->b, nullptr, P->lam_nt, s)))
+        return rc;
     if (P->p.incompressible) {
         if ((rc = vec_leray(P, P->vproj, dvt, s))) return rc;
         dvt = P->vproj;
     }
     if (P->p.state_equation == BLR_STATE_DEFORMATION) {
+        if (full && !P->have_lams && (rc = sweep_adjoint_def(P, P->rho_nt, P->b, s))) return rc;
         if ((rc = dft_expand(P, dvt, P->dv, 0, s))) return rc;
         if ((rc = sweep_incremental_def(P, s))) return rc;
-        if ((rc = sweep_adjoint_def(P, P->rho[0], P->b, s))) return rc;
+        if (full && (rc = newton_prep(P, s))) return rc;
+        rc = full ? sweep_adjoint_def_newton(P, P->b, s) : sweep_adjoint_def(P, P->rho[0], P->b, s);
+        if (rc) return rc;
         if ((rc = dft_project(P, P->b, hdv, dvt, s))) return rc;
         return P->p.incompressible ? vec_leray(P, hdv, hdv, s) : BLR_OK;
     }

@@ -168,6 +168,10 @@ struct blr_plan {
     float *rho[2];      // 3V each: adjoint / incremental adjoint ping-pong
     float *du[2];       // 3V each: incremental deformation ping-pong
     float *Gw;          // 3V grad T[I0](x + u^nt)
+    float *rho_all;     // full Newton Hessian: [nt][3][V], slot k-1 = rho^k (k = 1..nt; the
+                        // last slot is rho_nt), else nullptr
+    float *du_all;      // full Newton Hessian: [nt-1][3][V], slot k-1 = du^k of the last
+                        // incremental state (k = 1..nt-1), else nullptr
     float *nt_kap;      // full Newton Hessian: [8][V] corner weights of the variation of
                         // S^T for the current direction (newton.cu), else nullptr
     uint8_t *nt_lob;    // full Newton Hessian: [V] cell-start bits, else nullptr
@@ -313,6 +317,9 @@ int newton_prep(blr_plan *P, cudaStream_t s);
 int field_axpy(blr_plan *P, float *y, const float *a, const float *x, float alpha, long long n,
                cudaStream_t s);
 int def_final(blr_plan *P, int mode, const float *u, const float *du, float *rho, cudaStream_t s);
+// deform.cu: the full Newton Hessian's start of the incremental adjoint,
+// drho^nt = dlambda(1) grad T[I0](x + u^nt) + lambda(1) Hess T[I0](x + u^nt) du^nt.
+int def_final_newton(blr_plan *P, const float *du, float *rho, cudaStream_t s);
 int def_final_blocks(const blr_plan *P);
 // sweeps.cu: the deformation variant's forward solve (u^1..u^nt, m(1), rho^nt,
 // energy partials), incremental state (du^nt and drho^nt into rho[0]) and adjoint
@@ -320,6 +327,10 @@ int def_final_blocks(const blr_plan *P);
 int sweep_state_def(blr_plan *P, cudaStream_t s);
 int sweep_incremental_def(blr_plan *P, cudaStream_t s);
 int sweep_adjoint_def(blr_plan *P, const float *rho_final, float *b, cudaStream_t s);
+// The deformation variant's full Newton incremental adjoint: as sweep_adjoint_def from
+// drho^nt in rho[0], with the second-order terms of newton.cu per component after every
+// step (needs rho_all, du_all and newton_prep's weights).
+int sweep_adjoint_def_newton(blr_plan *P, float *b, cudaStream_t s);
 
 // reduce.cu
 int energy_finalize(blr_plan *P, const float *vt, double *energy_out, int nblocks, cudaStream_t s);

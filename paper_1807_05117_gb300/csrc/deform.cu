@@ -67,9 +67,44 @@ __device__ __forceinline__ void warp_point(const float *__restrict__ f, int i, i
     grad[2] = g2;
 }
 
+// Mixed second derivatives of the trilinear cell of f at x + u (the diagonal ones
+// are zero) applied to the vector w: out_a = sum_b (d_a d_b T[f](x + u)) w_b.
+__device__ __forceinline__ void warp_hess_times(const float *__restrict__ f, int i, int j, int k,
+                                                float u0, float u1, float u2, const Grid3 &g,
+                                                const float w[3], float out[3]) {
+    const float l0 = floorf(u0), l1 = floorf(u1), l2 = floorf(u2);
+    const float f0 = u0 - l0, f1 = u1 - l1, f2 = u2 - l2;
+    const long long plane = (long long)g.N2 * g.N3;
+    const long long p[2] = {(long long)wrapn(i + (int)l0, g.N1) * plane,
+                            (long long)wrapn(i + (int)l0 + 1, g.N1) * plane};
+    const long long r[2] = {(long long)wrapn(j + (int)l1, g.N2) * g.N3,
+                            (long long)wrapn(j + (int)l1 + 1, g.N2) * g.N3};
+    const int q[2] = {wrapn(k + (int)l2, g.N3), wrapn(k + (int)l2 + 1, g.N3)};
+    float c[2][2][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) c[a][b][e] = __ldg(f + p[a] + r[b] + q[e]);
+    const float w0[2] = {1.f - f0, f0}, w1[2] = {1.f - f1, f1}, w2[2] = {1.f - f2, f2};
+    float h01 = 0.f, h02 = 0.f, h12 = 0.f;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        h01 = fmaf(w2[t], (c[1][1][t] - c[1][0][t]) - (c[0][1][t] - c[0][0][t]), h01);
+        h02 = fmaf(w1[t], (c[1][t][1] - c[1][t][0]) - (c[0][t][1] - c[0][t][0]), h02);
+        h12 = fmaf(w0[t], (c[t][1][1] - c[t][1][0]) - (c[t][0][1] - c[t][0][0]), h12);
+    }
+    out[0] = fmaf(h01, w[1], h02 * w[2]);
+    out[1] = fmaf(h01, w[0], h12 * w[2]);
+    out[2] = fmaf(h02, w[0], h12 * w[1]);
+}
+
 // MODE 0: m1 = T[I0](x + u), Gw = grad T[I0](x + u), rho = lam_scale (m1 - I1) Gw,
 //         one FP64 partial sum of (m1 - I1)^2 per block (fixed grid: deterministic).
 // MODE 1: drho = lam_scale (Gw . du) Gw from the kept Gw.
+// MODE 2: MODE 1 + lam_scale (m1 - I1) Hess T[I0](x + u) du, the full Newton
+//         Hessian's term of the final warp (m1: the kept m(1)).
 template <int MODE>
 __global__ void __launch_bounds__(DT)
 k_def_final(const float *__restrict__ I0, const float *__restrict__ I1,
@@ -99,11 +134,25 @@ k_def_final(const float *__restrict__ I0, const float *__restrict__ I1,
             acc += (double)res * (double)res;
         } else {
             const float g0 = __ldg(Gw + x), g1 = __ldg(Gw + V + x), g2 = __ldg(Gw + 2 * V + x);
-            const float dm = fmaf(g0, __ldg(du + x), fmaf(g1, __ldg(du + V + x), g2 * __ldg(du + 2 * V + x)));
+            const float w[3] = {__ldg(du + x), __ldg(du + V + x), __ldg(du + 2 * V + x)};
+            const float dm = fmaf(g0, w[0], fmaf(g1, w[1], g2 * w[2]));
             const float dl = lam_scale * dm;
-            rho[x] = dl * g0;
-            rho[V + x] = dl * g1;
-            rho[2 * V + x] = dl * g2;
+            float r0 = dl * g0, r1 = dl * g1, r2 = dl * g2;
+            if constexpr (MODE == 2) {
+                const int i = (int)(x / plane);
+                const long long rem = x - (long long)i * plane;
+                const int j = (int)(rem / g.N3), k = (int)(rem - (long long)j * g.N3);
+                float hw[3];
+                warp_hess_times(I0, i, j, k, __ldg(u + x), __ldg(u + V + x), __ldg(u + 2 * V + x), g,
+                                w, hw);
+                const float lam = lam_scale * (__ldg(m1 + x) - __ldg(I1 + x));
+                r0 = fmaf(lam, hw[0], r0);
+                r1 = fmaf(lam, hw[1], r1);
+                r2 = fmaf(lam, hw[2], r2);
+            }
+            rho[x] = r0;
+            rho[V + x] = r1;
+            rho[2 * V + x] = r2;
         }
     }
     if constexpr (MODE == 0) {
@@ -137,6 +186,15 @@ int field_axpy(blr_plan *P, float *y, const float *a, const float *x, float alph
 int def_final_blocks(const blr_plan *P) {
     long long b = ceil_div_ll(P->V, DT);
     return (int)(b < P->npart ? b : P->npart);
+}
+
+int def_final_newton(blr_plan *P, const float *du, float *rho, cudaStream_t s) {
+    const float lam_scale = (float)(-2.0 / (P->p.sigma * P->p.sigma));
+    launch_pdl(k_def_final<2>, dim3(def_final_blocks(P)), dim3(DT), 0, s, (const float *)P->I0,
+               (const float *)P->I1, (const float *)def_u(P, P->p.nt, 0), du,
+               state_slot(P, P->p.nt), P->Gw, rho, lam_scale, (double *)nullptr, P->grid);
+    BLR_CK_LAUNCH();
+    return BLR_OK;
 }
 
 int def_final(blr_plan *P, int mode, const float *u, const float *du, float *rho, cudaStream_t s) {

@@ -1710,35 +1710,92 @@ int sweep_state_def(blr_plan *P, cudaStream_t s) {
 }
 
 // du^{n+1}_c = S du^n_c - dt grad u^n_c(x + d) . dv - dt dv_c; drho^nt into rho[0].
+// Full Newton plans keep du^1 .. du^{nt-1} in du_all and start the incremental
+// adjoint with the Hessian term of the final warp.
 int sweep_incremental_def(blr_plan *P, cudaStream_t s) {
     const int nt = P->p.nt;
     const long long V3 = 3 * P->V;
+    const bool keep = P->du_all != nullptr;
     int cur = 0;
+    const float *last = nullptr;
     for (int n = 0; n < nt; ++n) {
+        const float *din;
+        float *dout;
+        if (keep) {
+            din = n == 0 ? P->du[0] : P->du_all + (size_t)(n - 1) * V3;
+            dout = n + 1 < nt ? P->du_all + (size_t)n * V3 : P->du[1];
+        } else {
+            din = P->du[cur];
+            dout = P->du[1 - cur];
+        }
         for (int c = 0; c < 3; ++c) {
-            launch_incstate(P, n == 0, false, P->du[cur] + c * P->V, def_u(P, n, c),
-                            P->du[1 - cur] + c * P->V, 1.f, nullptr, s);
+            launch_incstate(P, n == 0, false, din + c * P->V, def_u(P, n, c), dout + c * P->V, 1.f,
+                            nullptr, s);
             BLR_CK_LAUNCH();
         }
-        int rc = field_axpy(P, P->du[1 - cur], P->du[1 - cur], P->dv, -P->dt, V3, s);
+        int rc = field_axpy(P, dout, dout, P->dv, -P->dt, V3, s);
         if (rc) return rc;
         cur = 1 - cur;
+        last = dout;
     }
-    return def_final(P, 1, nullptr, P->du[cur], P->rho[0], s);
+    if (P->p.hessian == BLR_NEWTON) return def_final_newton(P, last, P->rho[0], s);
+    return def_final(P, 1, nullptr, last, P->rho[0], s);
 }
 
 // rho^n_c = S^T rho^{n+1}_c; b = dt sum_n (sum_c rho^{n+1}_c grad u^n_c(x + d) + rho^{n+1}).
+// The gradient's solve of a full Newton plan (rho_final == rho_nt) keeps every
+// rho^n in rho_all.
 int sweep_adjoint_def(blr_plan *P, const float *rho_final, float *b, cudaStream_t s) {
     const int nt = P->p.nt;
     const long long V3 = 3 * P->V;
+    const bool keep = P->rho_all && rho_final == P->rho_nt;
     int cur = 0;
     for (int n = nt - 1; n >= 0; --n) {
-        const float *rin = (n == nt - 1) ? rho_final : P->rho[cur];
-        float *rout = P->rho[1 - cur];
+        const float *rin;
+        float *rout;
+        if (keep) {
+            rin = P->rho_all + (size_t)n * V3;                       // rho^{n+1}
+            rout = n > 0 ? P->rho_all + (size_t)(n - 1) * V3 : nullptr;
+        } else {
+            rin = (n == nt - 1) ? rho_final : P->rho[cur];
+            rout = P->rho[1 - cur];
+        }
         for (int c = 0; c < 3; ++c) {
             launch_adjoint(P, n == nt - 1 && c == 0, n > 0, rin + c * P->V, def_u(P, n, c),
                            n > 0 ? rout + c * P->V : nullptr, b, nullptr, s);
             BLR_CK_LAUNCH();
+        }
+        int rc = field_axpy(P, b, b, rin, P->dt, V3, s);
+        if (rc) return rc;
+        cur = 1 - cur;
+    }
+    if (keep) P->have_lams = true;
+    return BLR_OK;
+}
+
+// The deformation variant's full Newton incremental adjoint from drho^nt in rho[0]:
+// per step n and component c, the Gauss-Newton step (drho^n_c = S^T drho^{n+1}_c,
+// b += dt drho^{n+1}_c grad u^n_c) and then the second-order terms of newton.cu with
+// (lambda, m, dm, dlambda) = (rho_c^{n+1}, u^n_c, du^n_c, drho^n_c):
+//   b += dt rho^{n+1}_c (D du^n_c + Hess T[u^n_c] dd),  drho^n_c += sum_a D_a^T (dd_a rho^{n+1}_c);
+// then b += dt drho^{n+1}.
+int sweep_adjoint_def_newton(blr_plan *P, float *b, cudaStream_t s) {
+    const int nt = P->p.nt;
+    const long long V3 = 3 * P->V;
+    int cur = 0;
+    for (int n = nt - 1; n >= 0; --n) {
+        const float *rin = P->rho[cur];
+        float *rout = n > 0 ? P->rho[1 - cur] : nullptr;
+        const float *rho1 = P->rho_all + (size_t)n * V3;                          // rho^{n+1}
+        const float *dun = n > 0 ? P->du_all + (size_t)(n - 1) * V3 : nullptr;      // du^n
+        for (int c = 0; c < 3; ++c) {
+            launch_adjoint(P, n == nt - 1 && c == 0, n > 0, rin + c * P->V, def_u(P, n, c),
+                           rout ? rout + c * P->V : nullptr, b, nullptr, s);
+            BLR_CK_LAUNCH();
+            int rc = newton_terms(P, n > 0, rho1 + c * P->V, def_u(P, n, c),
+                                  dun ? dun + c * P->V : nullptr, rout ? rout + c * P->V : nullptr,
+                                  b, s);
+            if (rc) return rc;
         }
         int rc = field_axpy(P, b, b, rin, P->dt, V3, s);
         if (rc) return rc;
