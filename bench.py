@@ -555,7 +555,12 @@ def main_ours(args):
                 velocity="one band-limited velocity per time step (10 x 3 x 32^3 coefficients)"),
             "deformation_state": dict(
                 measure_form(args.precision, dev, I0g, I1g, flush, stream, state_equation=1),
-                state="deformation phi = id + u transported, I0 warped once (Gauss-Newton)")}
+                state="deformation phi = id + u transported, I0 warped once (Gauss-Newton)"),
+            "deformation_full_newton": dict(
+                measure_form(args.precision, dev, I0g, I1g, flush, stream, state_equation=1,
+                             hessian=1),
+                state="deformation phi = id + u transported, I0 warped once",
+                hessian="full: exact second derivative of the discrete energy, truncated PCG")}
 
     # end to end through the C-ABI with pinned host buffers
     if not args.no_e2e:
