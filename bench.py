@@ -720,7 +720,7 @@ def batch_measure(steps, warmup, dev, flush, stream, one_by_one=True):
            "workload": (f"{UNEVEN_PAIRS} phantom pairs, grids {grids}, bands 16^3/24^3/32^3, 3-8 "
                         "voxel warps, 10 time steps, 10 Newton x 20 PCG (fixed work) per pair, FP32"),
            "voxels_total": voxels, "gpu_launches": int(launches), "clocks": clocks,
-           "batch_create_s": create_s,
+           "batch_create_s": create_s, "tuning": batch.tuning(),
            "gvoxel_steps_per_s": voxels * NT * (NEWTON * PCG) / (ms / 1000.0) / 1e9,
            "status": sorted({r.status for r in reps}),
            "roofline": {"kernel": "all operators of the registrations (stepwise algorithmic bytes)",

@@ -81,6 +81,8 @@ _SIGS = {
     "blr_plan_set_tuning": (_P, ctypes.POINTER(ctypes.c_int), ctypes.c_int),
     "blr_batch_create": (ctypes.POINTER(blr_params), ctypes.c_int, ctypes.POINTER(_P)),
     "blr_batch_destroy": (_P,),
+    "blr_batch_tuning": (_P, ctypes.POINTER(ctypes.c_int), ctypes.c_int),
+    "blr_batch_set_tuning": (_P, ctypes.POINTER(ctypes.c_int), ctypes.c_int),
     "blr_batch_set_images": (_P, ctypes.c_int, _P, _P, _P),
     "blr_batch_gradient": (_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _P),
     "blr_batch_hessvec": (_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _P),
@@ -508,6 +510,27 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+    TUNING_KEYS = ("kept_gradients", "use_kept_gradients", "adjoint_chunk", "state_chunk",
+                   "solo_min_voxels", "solo_pairs")
+
+    def tuning(self) -> dict:
+        """The batch's sweep choices (blr_batch_tuning)."""
+        vals = (ctypes.c_int * len(self.TUNING_KEYS))()
+        _check(_lib.blr_batch_tuning(_P(self.handle), vals, len(vals)), "blr_batch_tuning")
+        return dict(zip(self.TUNING_KEYS, [int(v) for v in vals]))
+
+    def set_tuning(self, **changes):
+        """Override the sweep choices (blr_batch_set_tuning): keys of tuning() but
+        the last (solo_pairs follows from solo_min_voxels)."""
+        cur = self.tuning()
+        for k, v in changes.items():
+            if k not in cur or k == "solo_pairs":
+                raise ValueError(f"unknown or read-only tuning key {k}")
+            cur[k] = int(v)
+        keys = self.TUNING_KEYS[:5]
+        vals = (ctypes.c_int * len(keys))(*[cur[k] for k in keys])
+        _check(_lib.blr_batch_set_tuning(_P(self.handle), vals, len(vals)), "blr_batch_set_tuning")
 
     def set_images(self, pair, I0, I1, stream=None):
         import torch

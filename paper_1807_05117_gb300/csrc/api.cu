@@ -221,6 +221,8 @@ int flags_to_status(int flags) {
     return BLR_OK;
 }
 
+}  // namespace
+
 // Forward solve at vt (device) -> current point; energy into dsc (and energy_out).
 // Incompressible plans keep P vt as the current velocity.
 int state_at(blr_plan *P, const float *vt, double *energy_out, cudaStream_t s) {
@@ -298,6 +300,8 @@ int hessvec_here(blr_plan *P, const float *dvt, float *hdv, cudaStream_t s) {
     if ((rc = dft_project(P, P->b, hdv, dvt, s))) return rc;
     return P->p.incompressible ? vec_leray(P, hdv, hdv, s) : BLR_OK;
 }
+
+namespace {
 
 // PCG (Eq. 55).  The stopping test runs on the device (k_pcg_update), so the
 // host queues iteration j + 1 before it looks at iteration j - 1's flag: the GPU

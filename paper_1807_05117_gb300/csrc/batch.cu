@@ -8,8 +8,14 @@
 // * One PCG iteration of all pairs (HVP, <p, Hp>, update, new direction) is
 //   captured once as a CUDA graph and replayed; per-pair device flags freeze
 //   pairs whose PCG has converged.
-// * The x1 chunk of the sweep tiles is chosen by timing candidate shapes on the
-//   batch itself (batch_autotune).
+// * The x1 chunk of the sweep tiles, and whether the batched sweeps keep the
+//   state gradients, are chosen by timing candidates on the batch itself
+//   (batch_autotune).
+// * A pair whose grid fills the GPU by itself ("solo", at least solo_min voxels)
+//   skips the work queue: it runs its own plan's autotuned kernels (balanced
+//   grids, the two-step adjoint, the gather form of the incremental state), one
+//   pair after the other on the batch stream, and its PCG iteration is a graph
+//   of its own, replayed while the pair is active.
 // Each pair's arithmetic is exactly that of a single plan, so batched results
 // are bit-identical to running the pairs one by one.
 #include <string.h>
@@ -40,6 +46,15 @@ struct Batch {
     double *h_sc = nullptr;                   // pinned [npairs][SC_COUNT]
     int *h_flags = nullptr;                   // pinned [npairs]
     bool wide = false;                        // every pair runs the wide-copy sweep tiles
+    bool gm = false;                          // every pair keeps its state gradients
+    bool useg = false;                        // the batched sweeps write / read them (autotuned)
+    std::vector<int> own_chunk[3];            // [kind][pair]: each plan's own x1 chunk
+    int chunk_choice[3] = {0, 0, 0};          // [kind]: 0 = own chunks, else planes for all
+    long long solo_min = 1LL << 21;           // voxels from which a pair runs solo (0: none)
+    std::vector<char> solo;                   // [pair]
+    int nbatched = 0;                         // pairs in the work queue
+    std::vector<cudaGraphExec_t> solo_exec;   // [pair]: PCG iteration of a solo pair
+    std::vector<unsigned long long> solo_launches;
 };
 
 Batch *as_batch(blr_batch_t b) { return reinterpret_cast<Batch *>(b); }
@@ -54,7 +69,8 @@ int fill_descriptors(Batch *B) {
         for (int kind = 0; kind < KINDS; ++kind) {
             sweep_tiles(P, kind, B->wide, &tiles[kind][0], &tiles[kind][1], &tiles[kind][2]);
             long long *st = starts.data() + (size_t)kind * (np + 1);
-            st[p + 1] = st[p] + (long long)tiles[kind][0] * tiles[kind][1] * tiles[kind][2];
+            st[p + 1] = st[p] + (B->solo[p] ? 0LL
+                                            : (long long)tiles[kind][0] * tiles[kind][1] * tiles[kind][2]);
         }
         const float lam_scale = (float)(-2.0 / (P->p.sigma * P->p.sigma));
         auto base_for = [&](int kind) {
@@ -76,6 +92,7 @@ int fill_descriptors(Batch *B) {
             SweepPair st = base_for(0);
             st.in0 = state_slot(P, n);
             st.out0 = state_slot(P, n + 1);
+            st.Gout = B->useg ? grad_slot(P, n) : nullptr;
             if (n == nt - 1) {
                 st.aux = P->I1;
                 st.out1 = P->lam[0];
@@ -89,6 +106,7 @@ int fill_descriptors(Batch *B) {
             ad.m = state_slot(P, n);
             ad.out0 = P->lam[1 - ca];
             ad.out1 = P->b;
+            ad.G = B->useg ? grad_slot(P, n) : nullptr;
             h[((size_t)1 * nt + n) * np + p] = ad;
             // incremental state step n: dm ping-pong, dlambda^nt into lam[0]
             SweepPair in = base_for(2);
@@ -97,9 +115,12 @@ int fill_descriptors(Batch *B) {
             in.m = state_slot(P, n);
             in.aux = P->dv;
             in.out0 = (n == nt - 1) ? P->lam[0] : P->dm[1 - ci];
+            in.G = B->useg ? grad_slot(P, n) : nullptr;
             h[((size_t)2 * nt + n) * np + p] = in;
         }
     }
+    B->nbatched = 0;
+    for (int p = 0; p < np; ++p) B->nbatched += B->solo[p] ? 0 : 1;
     BLR_CK(cudaMemcpy(B->d_desc, h.data(), h.size() * sizeof(SweepPair), cudaMemcpyHostToDevice));
     BLR_CK(cudaMemcpy(B->d_starts, starts.data(), starts.size() * sizeof(long long),
                       cudaMemcpyHostToDevice));
@@ -107,6 +128,7 @@ int fill_descriptors(Batch *B) {
 }
 
 int launch_sweep(Batch *B, int kind, int n, cudaStream_t s) {
+    if (B->nbatched == 0) return BLR_OK;   // every pair runs solo
     const int nt = B->nt;
     bool f1, f2;
     if (kind == 0) {
@@ -119,7 +141,7 @@ int launch_sweep(Batch *B, int kind, int n, cudaStream_t s) {
         f1 = n == 0;
         f2 = n == nt - 1;
     }
-    return sweep_batch_launch(kind, f1, f2, B->wide, B->d_desc + ((size_t)kind * nt + n) * B->npairs,
+    return sweep_batch_launch(kind, f1, f2, B->wide, B->useg, B->d_desc + ((size_t)kind * nt + n) * B->npairs,
                               B->d_starts + (size_t)kind * (B->npairs + 1), B->npairs,
                               B->d_counters + (size_t)kind * nt + n,
                               sweep_blocks_per_sm(kind, B->wide) * B->grid, s);
@@ -165,7 +187,7 @@ int batch_state(Batch *B, const std::vector<int> &sel, const std::vector<const f
     int rc;
     if ((rc = upload_active(B, sel)) || (rc = reset_counters(B, B->s)) || (rc = fork(B))) return rc;
     for (int p = 0; p < B->npairs; ++p) {
-        if (!sel[p]) continue;
+        if (!sel[p] || B->solo[p]) continue;
         blr_plan *P = B->plans[p];
         cudaStream_t t = lane_of(B, p);
         if (vt[p] != P->vt)
@@ -177,13 +199,16 @@ int batch_state(Batch *B, const std::vector<int> &sel, const std::vector<const f
         if ((rc = launch_sweep(B, 0, n, B->s))) return rc;
     if ((rc = fork(B))) return rc;
     for (int p = 0; p < B->npairs; ++p) {
-        if (!sel[p]) continue;
+        if (!sel[p] || B->solo[p]) continue;
         blr_plan *P = B->plans[p];
         if ((rc = energy_finalize(P, P->vt, nullptr, (int)sweep_blocks(P), lane_of(B, p)))) return rc;
         P->have_state = true;
         P->seg_valid = 0;
     }
-    return join(B);
+    if ((rc = join(B))) return rc;
+    for (int p = 0; p < B->npairs; ++p)
+        if (sel[p] && B->solo[p] && (rc = state_at(B->plans[p], vt[p], nullptr, B->s))) return rc;
+    return BLR_OK;
 }
 
 // Gradients of the selected pairs at their current points into g[p].
@@ -194,20 +219,25 @@ int batch_gradient_here(Batch *B, const std::vector<int> &sel, const std::vector
         if ((rc = launch_sweep(B, 1, n, B->s))) return rc;
     if ((rc = fork(B))) return rc;
     for (int p = 0; p < B->npairs; ++p) {
-        if (!sel[p]) continue;
+        if (!sel[p] || B->solo[p]) continue;
         blr_plan *P = B->plans[p];
         if ((rc = dft_project(P, P->b, g[p], P->vt, lane_of(B, p)))) return rc;
     }
-    return join(B);
+    if ((rc = join(B))) return rc;
+    for (int p = 0; p < B->npairs; ++p)
+        if (sel[p] && B->solo[p] && (rc = gradient_here(B->plans[p], g[p], B->s))) return rc;
+    return BLR_OK;
 }
 
-// Gauss-Newton HVPs of all pairs (flags decide which pairs' sweeps run).
+// Gauss-Newton HVPs of all pairs (flags decide which queued pairs' sweeps run);
+// with_solo: the solo pairs' products too.
 int batch_hessvec_all(Batch *B, const std::vector<const float *> &dvt,
-                      const std::vector<float *> &hdv) {
+                      const std::vector<float *> &hdv, bool with_solo) {
     int rc;
     if ((rc = reset_counters(B, B->s)) || (rc = fork(B))) return rc;
     for (int p = 0; p < B->npairs; ++p)
-        if ((rc = dft_expand(B->plans[p], dvt[p], B->plans[p]->dv, 0, lane_of(B, p)))) return rc;
+        if (!B->solo[p] && (rc = dft_expand(B->plans[p], dvt[p], B->plans[p]->dv, 0, lane_of(B, p))))
+            return rc;
     if ((rc = join(B))) return rc;
     for (int n = 0; n < B->nt; ++n)
         if ((rc = launch_sweep(B, 2, n, B->s))) return rc;
@@ -215,32 +245,22 @@ int batch_hessvec_all(Batch *B, const std::vector<const float *> &dvt,
         if ((rc = launch_sweep(B, 1, n, B->s))) return rc;
     if ((rc = fork(B))) return rc;
     for (int p = 0; p < B->npairs; ++p)
-        if ((rc = dft_project(B->plans[p], B->plans[p]->b, hdv[p], dvt[p], lane_of(B, p)))) return rc;
-    return join(B);
+        if (!B->solo[p] &&
+            (rc = dft_project(B->plans[p], B->plans[p]->b, hdv[p], dvt[p], lane_of(B, p))))
+            return rc;
+    if ((rc = join(B))) return rc;
+    for (int p = 0; p < B->npairs && with_solo; ++p)
+        if (B->solo[p] && (rc = hessvec_here(B->plans[p], dvt[p], hdv[p], B->s))) return rc;
+    return BLR_OK;
 }
 
-// One PCG iteration of every pair (HVP, <p, q>, update of x = step, r and the
-// next direction), captured once as a graph.
-int capture_pcg(Batch *B) {
-    if (B->pcg_exec) return BLR_OK;
-    std::vector<const float *> in(B->npairs);
-    std::vector<float *> out(B->npairs);
-    for (int p = 0; p < B->npairs; ++p) {
-        in[p] = B->plans[p]->pv;
-        out[p] = B->plans[p]->q;
-    }
+// Capture what `body` queues on the batch stream as a graph (instantiated into
+// *exec; *launches: kernel nodes per replay).
+template <typename F>
+int capture_graph(Batch *B, F &&body, cudaGraphExec_t *exec, unsigned long long *launches) {
     const unsigned long long l0 = blr_kernel_launches();
     BLR_CK(cudaStreamBeginCapture(B->s, cudaStreamCaptureModeThreadLocal));
-    int rc = batch_hessvec_all(B, in, out);
-    if (!rc) rc = fork(B);
-    for (int p = 0; p < B->npairs && !rc; ++p) {
-        blr_plan *P = B->plans[p];
-        cudaStream_t t = lane_of(B, p);
-        if ((rc = vec_dot(P, P->pv, P->q, nullptr, P->dsc + SC_PQ, t))) break;
-        if ((rc = pcg_update(P, P->step, t))) break;
-        rc = pcg_direction(P, t);
-    }
-    if (!rc) rc = join(B);
+    int rc = body();
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(B->s, &graph);
     if (rc) {
@@ -248,10 +268,59 @@ int capture_pcg(Batch *B) {
         return rc;
     }
     if (e != cudaSuccess) return BLR_ECUDA;
-    B->pcg_launches = blr_kernel_launches() - l0;
-    e = cudaGraphInstantiate(&B->pcg_exec, graph, 0);
+    *launches = blr_kernel_launches() - l0;
+    e = cudaGraphInstantiate(exec, graph, 0);
     cudaGraphDestroy(graph);
     return e == cudaSuccess ? BLR_OK : BLR_ECUDA;
+}
+
+void drop_graphs(Batch *B) {
+    if (B->pcg_exec) cudaGraphExecDestroy(B->pcg_exec);
+    B->pcg_exec = nullptr;
+    for (cudaGraphExec_t &g : B->solo_exec) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+}
+
+// One PCG iteration (HVP, <p, q>, update of x = step, r and the next direction)
+// captured once as graphs: one for every queued pair, one per solo pair.
+int capture_pcg(Batch *B) {
+    int rc = BLR_OK;
+    if (B->nbatched > 0 && !B->pcg_exec) {
+        std::vector<const float *> in(B->npairs);
+        std::vector<float *> out(B->npairs);
+        for (int p = 0; p < B->npairs; ++p) {
+            in[p] = B->plans[p]->pv;
+            out[p] = B->plans[p]->q;
+        }
+        rc = capture_graph(B, [&]() {
+            int r = batch_hessvec_all(B, in, out, false);
+            if (!r) r = fork(B);
+            for (int p = 0; p < B->npairs && !r; ++p) {
+                if (B->solo[p]) continue;
+                blr_plan *P = B->plans[p];
+                cudaStream_t t = lane_of(B, p);
+                if ((r = vec_dot(P, P->pv, P->q, nullptr, P->dsc + SC_PQ, t))) break;
+                if ((r = pcg_update(P, P->step, t))) break;
+                r = pcg_direction(P, t);
+            }
+            if (!r) r = join(B);
+            return r;
+        }, &B->pcg_exec, &B->pcg_launches);
+    }
+    for (int p = 0; p < B->npairs && !rc; ++p) {
+        if (!B->solo[p] || B->solo_exec[p]) continue;
+        blr_plan *P = B->plans[p];
+        rc = capture_graph(B, [&]() {
+            int r = hessvec_here(P, P->pv, P->q, B->s);
+            if (!r) r = vec_dot(P, P->pv, P->q, nullptr, P->dsc + SC_PQ, B->s);
+            if (!r) r = pcg_update(P, P->step, B->s);
+            if (!r) r = pcg_direction(P, B->s);
+            return r;
+        }, &B->solo_exec[p], &B->solo_launches[p]);
+    }
+    return rc;
 }
 
 int fetch_all(Batch *B, bool flags) {
@@ -270,51 +339,71 @@ int fetch_all(Batch *B, bool flags) {
 
 double sc(Batch *B, int p, int slot) { return B->h_sc[(size_t)p * SC_COUNT + slot]; }
 
+// x1 chunk of every pair for a sweep kind (1 adjoint, 2 incremental and state):
+// each plan's own (0) or `planes` for all pairs (at most N1).
+void apply_chunk(Batch *B, int kind, int planes) {
+    for (int p = 0; p < B->npairs; ++p) {
+        blr_plan *P = B->plans[p];
+        sweep_set_chunk(P, kind, planes ? (planes < P->N1 ? planes : P->N1) : B->own_chunk[kind][p]);
+    }
+    B->chunk_choice[kind] = planes;
+}
+
 // For the adjoint and the incremental-state sweeps, time one interior batched
 // step for candidate x1 chunks (each plan's own autotuned chunk, or 4, 8, 16, 32
 // planes for every pair) and keep the best; the state sweep shares the
-// incremental-state chunk.
+// incremental-state chunk.  When every pair keeps its state gradients, both
+// kinds are tuned with and without reading them, and the faster sum is kept.
+// Only the queued pairs take part (solo pairs have no items).
 int batch_autotune(Batch *B) {
     const int cands[5] = {0, 4, 8, 16, 32};   // 0: each plan's own chunk
+    for (int kind = 1; kind <= 2; ++kind) {
+        B->own_chunk[kind].resize(B->npairs);
+        for (int p = 0; p < B->npairs; ++p) B->own_chunk[kind][p] = sweep_chunk(B->plans[p], kind);
+    }
+    int rc = fill_descriptors(B);
+    if (rc || B->nbatched == 0) return rc;
     cudaEvent_t e0, e1;
     BLR_CK(cudaEventCreate(&e0));
     BLR_CK(cudaEventCreate(&e1));
     std::vector<int> all(B->npairs, 1);
-    int rc = upload_active(B, all);
+    rc = upload_active(B, all);
     const int n = B->nt > 2 ? 1 : 0;
-    for (int kind = 1; kind <= 2 && !rc; ++kind) {
-        std::vector<int> own(B->npairs);
-        for (int p = 0; p < B->npairs; ++p) own[p] = sweep_chunk(B->plans[p], kind);
-        auto apply = [&](int c) {
-            for (int p = 0; p < B->npairs; ++p) {
-                blr_plan *P = B->plans[p];
-                sweep_set_chunk(P, kind, cands[c] ? (cands[c] < P->N1 ? cands[c] : P->N1) : own[p]);
+    const int nu = B->gm ? 2 : 1;
+    float total[2] = {0.f, 0.f};
+    int best_c[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    for (int u = 0; u < nu && !rc; ++u) {
+        B->useg = u == 1;
+        for (int kind = 1; kind <= 2 && !rc; ++kind) {
+            float best = 1e30f;
+            for (int c = 0; c < 5 && !rc; ++c) {
+                apply_chunk(B, kind, cands[c]);
+                if ((rc = fill_descriptors(B))) break;
+                float tot = 0.f;
+                for (int rep = 0; rep < 3 && !rc; ++rep) {
+                    if ((rc = reset_counters(B, B->s))) break;
+                    if (cudaEventRecord(e0, B->s) != cudaSuccess) rc = BLR_ECUDA;
+                    if (!rc) rc = launch_sweep(B, kind, n, B->s);
+                    if (!rc && (cudaEventRecord(e1, B->s) != cudaSuccess ||
+                                cudaEventSynchronize(e1) != cudaSuccess))
+                        rc = BLR_ECUDA;
+                    float ms = 0.f;
+                    if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = BLR_ECUDA;
+                    if (rep) tot += ms;
+                }
+                if (tot < best) {
+                    best = tot;
+                    best_c[u][kind] = cands[c];
+                }
             }
-        };
-        float best = 1e30f;
-        int best_c = 0;
-        for (int c = 0; c < 5 && !rc; ++c) {
-            apply(c);
-            if ((rc = fill_descriptors(B))) break;
-            float tot = 0.f;
-            for (int rep = 0; rep < 3 && !rc; ++rep) {
-                if ((rc = reset_counters(B, B->s))) break;
-                if (cudaEventRecord(e0, B->s) != cudaSuccess) rc = BLR_ECUDA;
-                if (!rc) rc = launch_sweep(B, kind, n, B->s);
-                if (!rc && (cudaEventRecord(e1, B->s) != cudaSuccess ||
-                            cudaEventSynchronize(e1) != cudaSuccess))
-                    rc = BLR_ECUDA;
-                float ms = 0.f;
-                if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = BLR_ECUDA;
-                if (rep) tot += ms;
-            }
-            if (tot < best) {
-                best = tot;
-                best_c = c;
-            }
+            apply_chunk(B, kind, best_c[u][kind]);
+            total[u] += best;
         }
-        apply(best_c);
     }
+    const int u = (nu == 2 && total[1] < total[0]) ? 1 : 0;
+    B->useg = u == 1;
+    apply_chunk(B, 1, best_c[u][1]);
+    apply_chunk(B, 2, best_c[u][2]);
     if (!rc) rc = fill_descriptors(B);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -323,7 +412,7 @@ int batch_autotune(Batch *B) {
 
 void free_batch(Batch *B) {
     if (!B) return;
-    if (B->pcg_exec) cudaGraphExecDestroy(B->pcg_exec);
+    drop_graphs(B);
     for (cudaStream_t t : B->side) cudaStreamDestroy(t);
     for (cudaEvent_t e : B->ev_join) cudaEventDestroy(e);
     if (B->ev_fork) cudaEventDestroy(B->ev_fork);
@@ -358,8 +447,11 @@ int blr_batch_create(const blr_params *params, int npairs, blr_batch_t *out) {
     int rc = BLR_OK;
     if (cudaGetDevice(&B->device) != cudaSuccess) rc = BLR_ECUDA;
     for (int p = 0; p < npairs && !rc; ++p) {
+        // kept state gradients (3 nt V floats) when they fit, else the pair
+        // interpolates grad m^n in every adjoint and incremental-state step
         blr_plan_t P = nullptr;
-        rc = plan_create(&params[p], false, &P);
+        rc = plan_create(&params[p], true, &P);
+        if (rc == BLR_ENOMEM) rc = plan_create(&params[p], false, &P);
         if (!rc) B->plans.push_back(P);
     }
     int sms = 0;
@@ -368,6 +460,13 @@ int blr_batch_create(const blr_params *params, int npairs, blr_batch_t *out) {
     B->grid = sms > 0 ? sms : 148;   // SMs; persistent grids are blocks-per-SM multiples
     B->wide = !rc;
     for (int p = 0; p < npairs && !rc; ++p) B->wide = B->wide && B->plans[p]->sweep_wide;
+    B->gm = B->wide;
+    for (int p = 0; p < npairs && !rc; ++p) B->gm = B->gm && B->plans[p]->Gm != nullptr;
+    B->solo.assign(npairs, 0);
+    for (int p = 0; p < npairs && !rc; ++p)
+        B->solo[p] = B->solo_min > 0 && B->plans[p]->V >= B->solo_min;
+    B->solo_exec.assign(npairs, nullptr);
+    B->solo_launches.assign(npairs, 0);
     const int nside = npairs < 8 ? npairs : 8;
     if (!rc &&
         (cudaMalloc(&B->d_desc, sizeof(SweepPair) * KINDS * B->nt * npairs) != cudaSuccess ||
@@ -409,6 +508,43 @@ int blr_batch_destroy(blr_batch_t b) {
     return BLR_OK;
 }
 
+int blr_batch_tuning(blr_batch_t b, int *vals, int n) {
+    Batch *B = as_batch(b);
+    if (!B || !vals || n < 0) return BLR_EINVAL;
+    int nsolo = 0;
+    for (char c : B->solo) nsolo += c;
+    const long long smin = B->solo_min < 0x7fffffffLL ? B->solo_min : 0x7fffffffLL;
+    const int v[6] = {B->gm ? 1 : 0, B->useg ? 1 : 0, B->chunk_choice[1], B->chunk_choice[2],
+                      (int)smin, nsolo};
+    for (int i = 0; i < n && i < 6; ++i) vals[i] = v[i];
+    return BLR_OK;
+}
+
+int blr_batch_set_tuning(blr_batch_t b, const int *vals, int n) {
+    Batch *B = as_batch(b);
+    if (!B || !vals || n < 5) return BLR_EINVAL;
+    if (vals[0] != (B->gm ? 1 : 0) || vals[1] < 0 || vals[1] > vals[0] || vals[4] < 0) return BLR_EINVAL;
+    for (int k = 2; k < 4; ++k)
+        if (vals[k] != 0 && (vals[k] < 2 || vals[k] > 1024)) return BLR_EINVAL;
+    BLR_CK(cudaDeviceSynchronize());
+    drop_graphs(B);   // the captured iterations hold the old launches
+    bool moved = (vals[1] != 0) != B->useg;
+    B->useg = vals[1] != 0;
+    B->solo_min = vals[4];
+    for (int p = 0; p < B->npairs; ++p) {
+        const char solo = B->solo_min > 0 && B->plans[p]->V >= B->solo_min;
+        moved = moved || solo != B->solo[p];
+        B->solo[p] = solo;
+    }
+    // the current points' kept gradients and final adjoint states were written
+    // (or not) for the old path: every pair needs a new forward solve
+    if (moved)
+        for (blr_plan_t P : B->plans) P->have_state = false;
+    apply_chunk(B, 1, vals[2]);
+    apply_chunk(B, 2, vals[3]);
+    return fill_descriptors(B);
+}
+
 int blr_batch_set_images(blr_batch_t b, int pair, const float *I0, const float *I1,
                          blr_stream_t stream) {
     Batch *B = as_batch(b);
@@ -439,7 +575,7 @@ int blr_batch_hessvec(blr_batch_t b, const float *const *dvt, float *const *hdv,
     std::vector<int> all(B->npairs, 1);
     int rc = upload_active(B, all);
     if (!rc) rc = batch_hessvec_all(B, std::vector<const float *>(dvt, dvt + B->npairs),
-                                    std::vector<float *>(hdv, hdv + B->npairs));
+                                    std::vector<float *>(hdv, hdv + B->npairs), true);
     BLR_CK(cudaStreamSynchronize(B->s));
     return rc;
 }
@@ -513,8 +649,17 @@ int blr_batch_newton(blr_batch_t b, float *const *vt, int max_newton, int max_pc
             for (int p = 0; p < np; ++p) on |= pcg_on[p];
             if (!on) break;
             if ((rc = upload_active(B, pcg_on))) return rc;
-            BLR_CK(cudaGraphLaunch(B->pcg_exec, B->s));
-            __atomic_fetch_add(&g_blr_launches, B->pcg_launches, __ATOMIC_RELAXED);
+            bool queued = false;
+            for (int p = 0; p < np; ++p) queued = queued || (pcg_on[p] && !B->solo[p]);
+            if (queued) {
+                BLR_CK(cudaGraphLaunch(B->pcg_exec, B->s));
+                __atomic_fetch_add(&g_blr_launches, B->pcg_launches, __ATOMIC_RELAXED);
+            }
+            for (int p = 0; p < np; ++p) {
+                if (!pcg_on[p] || !B->solo[p]) continue;
+                BLR_CK(cudaGraphLaunch(B->solo_exec[p], B->s));
+                __atomic_fetch_add(&g_blr_launches, B->solo_launches[p], __ATOMIC_RELAXED);
+            }
             if ((rc = fetch_all(B, false))) return rc;
             for (int p = 0; p < np; ++p) {
                 if (!pcg_on[p]) continue;

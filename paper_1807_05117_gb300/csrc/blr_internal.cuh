@@ -110,6 +110,8 @@ struct SweepPair {
     double *partials;        // state (last step): image-term sums per 32-voxel row segment
     float dt, scale;         // time step; lambda scale -2/sigma^2
     const int *active;       // nullptr or a device flag: 0 skips the pair
+    const float *G;          // adjoint / incremental (kept gradients): grad m^n(x + d(x))
+    float *Gout;             // state (kept gradients): where grad m^n(x + d(x)) is written
 };
 
 struct blr_plan {
@@ -293,7 +295,7 @@ int sweep_adjoint_steps(blr_plan *P, const float *lam_final, float *gout, const 
                         float *b_steps, float *lambda0, cudaStream_t s);
 // wide: the adjoint and incremental-state items use the wide-copy tiles (every
 // pair has N3 % 4 == 0); the incremental-state tiles are then AJ rows high.
-int sweep_batch_launch(int kind, bool f1, bool f2, bool wide, const SweepPair *pairs,
+int sweep_batch_launch(int kind, bool f1, bool f2, bool wide, bool useg, const SweepPair *pairs,
                        const long long *starts, int npairs, unsigned long long *counter, int grid,
                        cudaStream_t s);
 // kind: 0 state, 1 adjoint, 2 incremental state
@@ -301,6 +303,7 @@ void sweep_tiles(const blr_plan *P, int kind, bool wide, int *tk, int *tj, int *
 int sweep_chunk(const blr_plan *P, int kind);
 int sweep_blocks_per_sm(int kind, bool wide = false);
 void sweep_set_chunk(blr_plan *P, int kind, int chunk);
+float *grad_slot(const blr_plan *P, int n);   // kept grad m^n, or nullptr
 int sweep_autotune(blr_plan *P, cudaStream_t s);
 int sweep_pack_d4(blr_plan *P, cudaStream_t s);               // d4 from d (when P->d4)
 
@@ -334,6 +337,11 @@ int sweep_adjoint_def_newton(blr_plan *P, float *b, cudaStream_t s);
 
 // reduce.cu
 int energy_finalize(blr_plan *P, const float *vt, double *energy_out, int nblocks, cudaStream_t s);
+// A plan's forward solve at vt (device), gradient and Gauss-Newton / full HVP at
+// its current point, on stream s (api.cu; the batch runs its solo pairs through them).
+int state_at(blr_plan *P, const float *vt, double *energy_out, cudaStream_t s);
+int gradient_here(blr_plan *P, float *g, cudaStream_t s);
+int hessvec_here(blr_plan *P, const float *dvt, float *hdv, cudaStream_t s);
 int vec_dot(blr_plan *P, const float *a, const float *b, const float *w, double *out, cudaStream_t s);
 int vec_maxabs(blr_plan *P, const float *a, double *out, cudaStream_t s);
 int pcg_init(blr_plan *P, const float *rhs, float *x, cudaStream_t s);

@@ -1020,7 +1020,9 @@ __global__ void k_pack_d4(const float *__restrict__ d, float4 *__restrict__ d4, 
 // item order (items of pair p are starts[p] .. starts[p+1]-1); each item is a
 // full march tile of that pair, so the results equal the single-pair kernels'.
 // WIDE: the adjoint and incremental-state items use the wide-copy tiles.
-template <int KIND, bool F1, bool F2, bool WIDE>
+// USEG (with WIDE): those tiles read the kept state gradients P.G instead of
+// interpolating grad m^n; the state items write them whenever P.Gout is set.
+template <int KIND, bool F1, bool F2, bool WIDE, bool USEG>
 __global__ void __launch_bounds__(MT, KIND == 1 ? ADJ_BLOCKS : (KIND == 2 && WIDE ? INC_BLOCKS : 4))
 k_sweep_batch(const SweepPair *__restrict__ pairs, const long long *__restrict__ starts,
               int npairs, unsigned long long *counter) {
@@ -1048,15 +1050,15 @@ k_sweep_batch(const SweepPair *__restrict__ pairs, const long long *__restrict__
         const int i0 = it * P.chunk;
         if constexpr (KIND == 0)
             state_tile<F1>(P.in0, P.d, P.out0, P.g, P.chunk, P.aux, P.out1, P.scale, P.partials,
-                           k0, j0, i0);
+                           k0, j0, i0, P.Gout);
         else if constexpr (KIND == 1 && WIDE)
-            adjoint_tile_w<F1, F2, false>(P.in0, P.m, P.d4, P.out0, P.out1, P.dt, P.g, P.chunk, k0,
-                                          j0, i0, nullptr);
+            adjoint_tile_w<F1, F2, USEG>(P.in0, P.m, P.d4, P.out0, P.out1, P.dt, P.g, P.chunk, k0,
+                                         j0, i0, USEG ? P.G : nullptr);
         else if constexpr (KIND == 1)
             adjoint_tile<F1, F2>(P.in0, P.m, P.d, P.out0, P.out1, P.dt, P.g, P.chunk, k0, j0, i0);
         else if constexpr (WIDE)
-            incstate_tile_w<F1, F2, false>(P.in0, P.m, P.d4, P.aux, P.out0, P.dt, P.scale, P.g,
-                                           P.chunk, k0, j0, i0, nullptr);
+            incstate_tile_w<F1, F2, USEG>(P.in0, P.m, P.d4, P.aux, P.out0, P.dt, P.scale, P.g,
+                                          P.chunk, k0, j0, i0, USEG ? P.G : nullptr);
         else
             incstate_tile<F1, F2>(P.in0, P.m, P.d, P.aux, P.out0, P.dt, P.scale, P.g, P.chunk,
                                   k0, j0, i0);
@@ -1288,6 +1290,22 @@ dim3 adjoint_grid(const blr_plan *P) {
                 (unsigned)ceil_div_ll(P->N1, P->chunk_adj));
 }
 
+// Dynamic shared memory of a batched sweep instantiation.
+template <int K, bool A, bool W, bool G>
+constexpr int batch_smem() {
+    return K == 1 ? (W ? (G ? ADJW_SMEM_G : ADJW_SMEM) : ADJ_SMEM)
+                  : (K == 2 && W ? incw_smem<A, G>() : 0);
+}
+
+template <int K, bool W, bool G>
+int batch_smem_attributes() {
+    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<K, true, true, W, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, batch_smem<K, true, W, G>()));
+    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<K, true, false, W, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, batch_smem<K, true, W, G>()));
+    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<K, false, true, W, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, batch_smem<K, false, W, G>()));
+    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<K, false, false, W, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, batch_smem<K, false, W, G>()));
+    return BLR_OK;
+}
+
 // The adjoint kernels' shared memory exceeds the default 48 KB window.
 int adjoint_smem_attributes() {
     static bool done = false;
@@ -1300,18 +1318,12 @@ int adjoint_smem_attributes() {
     BLR_CK(cudaFuncSetAttribute(k_adjoint_march<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
     BLR_CK(cudaFuncSetAttribute(k_adjoint_march<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
     BLR_CK(cudaFuncSetAttribute(k_adjoint_march<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
-    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
-    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM));
-    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<2, true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, incw_smem<true, false>()));
-    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
-    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM));
-    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<2, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, incw_smem<true, false>()));
-    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
-    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM));
-    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<2, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, incw_smem<false, false>()));
-    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
-    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<1, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM));
-    BLR_CK(cudaFuncSetAttribute(k_sweep_batch<2, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, incw_smem<false, false>()));
+    {
+        const int rc = batch_smem_attributes<1, false, false>() | batch_smem_attributes<1, true, false>() |
+                       batch_smem_attributes<1, true, true>() | batch_smem_attributes<2, true, false>() |
+                       batch_smem_attributes<2, true, true>();
+        if (rc) return BLR_ECUDA;
+    }
     BLR_CK(cudaFuncSetAttribute(k_adjoint_bal<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
     BLR_CK(cudaFuncSetAttribute(k_adjoint_bal<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
     BLR_CK(cudaFuncSetAttribute(k_adjoint_bal<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
@@ -1406,10 +1418,14 @@ void launch_state(const blr_plan *P, const float *m_in, float *m_out, const floa
     }
 }
 
+}  // namespace
+
 // grad m^n(x + d(x)) of step n when the plan keeps it, else nullptr.
 float *grad_slot(const blr_plan *P, int n) {
     return P->Gm ? P->Gm + (size_t)3 * n * P->V : nullptr;
 }
+
+namespace {
 
 // The displacement copy d4 is read by every step of the adjoint and incremental
 // sweeps.  When the autotuner finds it faster, those launches carry an
@@ -1807,40 +1823,38 @@ int sweep_adjoint_def_newton(blr_plan *P, float *b, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Batched launches and the tile-shape autotuner.
 
-int sweep_batch_launch(int kind, bool f1, bool f2, bool wide, const SweepPair *pairs,
+template <int K, bool W, bool G>
+void batch_dispatch(bool f1, bool f2, const SweepPair *pairs, const long long *starts, int npairs,
+                    unsigned long long *counter, int grid, cudaStream_t s) {
+#define BLR_BL(A, B)                                                                            \
+    launch_pdl(k_sweep_batch<K, A, B, W, G>, dim3(grid), dim3(MT),                              \
+               (size_t)batch_smem<K, A, W, G>(), s, pairs, starts, npairs, counter)
+    if (f1 && f2) BLR_BL(true, true);
+    else if (f1) BLR_BL(true, false);
+    else if (f2) BLR_BL(false, true);
+    else BLR_BL(false, false);
+#undef BLR_BL
+}
+
+int sweep_batch_launch(int kind, bool f1, bool f2, bool wide, bool useg, const SweepPair *pairs,
                        const long long *starts, int npairs, unsigned long long *counter, int grid,
                        cudaStream_t s) {
-#define BLR_BL(K, A, B, W, SM)                                                                   \
-    launch_pdl(k_sweep_batch<K, A, B, W>, dim3(grid), dim3(MT), (size_t)(SM), s, pairs, starts, \
-               npairs, counter)
+    if (useg && !wide) return BLR_EINVAL;   // kept gradients are read by the wide-copy tiles only
     if (kind == 0) {
-        if (f1) BLR_BL(0, true, false, false, 0); else BLR_BL(0, false, false, false, 0);
+        // the state items write the kept gradients through P.Gout: one instantiation
+        if (f1) launch_pdl(k_sweep_batch<0, true, false, false, false>, dim3(grid), dim3(MT),
+                           (size_t)0, s, pairs, starts, npairs, counter);
+        else launch_pdl(k_sweep_batch<0, false, false, false, false>, dim3(grid), dim3(MT),
+                        (size_t)0, s, pairs, starts, npairs, counter);
     } else if (kind == 1) {
-        if (wide) {
-            if (f1 && f2) BLR_BL(1, true, true, true, ADJW_SMEM);
-            else if (f1) BLR_BL(1, true, false, true, ADJW_SMEM);
-            else if (f2) BLR_BL(1, false, true, true, ADJW_SMEM);
-            else BLR_BL(1, false, false, true, ADJW_SMEM);
-        } else {
-            if (f1 && f2) BLR_BL(1, true, true, false, ADJ_SMEM);
-            else if (f1) BLR_BL(1, true, false, false, ADJ_SMEM);
-            else if (f2) BLR_BL(1, false, true, false, ADJ_SMEM);
-            else BLR_BL(1, false, false, false, ADJ_SMEM);
-        }
+        if (useg) batch_dispatch<1, true, true>(f1, f2, pairs, starts, npairs, counter, grid, s);
+        else if (wide) batch_dispatch<1, true, false>(f1, f2, pairs, starts, npairs, counter, grid, s);
+        else batch_dispatch<1, false, false>(f1, f2, pairs, starts, npairs, counter, grid, s);
     } else {
-        if (wide) {
-            if (f1 && f2) BLR_BL(2, true, true, true, (incw_smem<true, false>()));
-            else if (f1) BLR_BL(2, true, false, true, (incw_smem<true, false>()));
-            else if (f2) BLR_BL(2, false, true, true, (incw_smem<false, false>()));
-            else BLR_BL(2, false, false, true, (incw_smem<false, false>()));
-        } else {
-            if (f1 && f2) BLR_BL(2, true, true, false, 0);
-            else if (f1) BLR_BL(2, true, false, false, 0);
-            else if (f2) BLR_BL(2, false, true, false, 0);
-            else BLR_BL(2, false, false, false, 0);
-        }
+        if (useg) batch_dispatch<2, true, true>(f1, f2, pairs, starts, npairs, counter, grid, s);
+        else if (wide) batch_dispatch<2, true, false>(f1, f2, pairs, starts, npairs, counter, grid, s);
+        else batch_dispatch<2, false, false>(f1, f2, pairs, starts, npairs, counter, grid, s);
     }
-#undef BLR_BL
     BLR_CK_LAUNCH();
     return BLR_OK;
 }

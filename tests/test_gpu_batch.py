@@ -77,6 +77,65 @@ def test_batched_newton_equals_single_plans(setup, forcing):
         assert r.energy < r.energy0
 
 
+def _compare_with_single_plans(blr, pairs, batch, plans):
+    gb = [torch.empty_like(p["vt"]) for p in pairs]
+    batch.gradient([p["vt"] for p in pairs], gb)
+    hb = [torch.empty_like(p["vt"]) for p in pairs]
+    batch.hessvec([p["dv"] for p in pairs], hb)
+    vb = [torch.zeros_like(p["vt"]) for p in pairs]
+    reps = batch.newton(vb, 2, 5, 1e-6, 0.0)
+    for p, pl, g, h, v, r in zip(pairs, plans, gb, hb, vb, reps):
+        gs, hs = torch.empty_like(g), torch.empty_like(h)
+        pl.gradient(p["vt"], gs)
+        pl.hessvec(p["dv"], hs)
+        assert torch.equal(g, gs)
+        assert torch.equal(h, hs)
+        vs = torch.zeros_like(v)
+        rs = pl.newton(vs, 2, 5, 1e-6, 0.0)
+        assert r.status == rs.status == blr.BLR_OK
+        assert (r.newton_iters, r.pcg_iters, r.n_halvings) == \
+            (rs.newton_iters, rs.pcg_iters, rs.n_halvings)
+        assert r.energy == rs.energy
+        assert torch.equal(v, vs)
+
+
+@pytest.mark.parametrize("useg", [1, 0], ids=["kept-gradients", "interpolated-gradients"])
+def test_both_gradient_choices_equal_single_plans(setup, useg):
+    """Batched sweeps that read the kept state gradients and ones that
+    interpolate grad m^n give the single plans' results bit for bit."""
+    blr, pairs, batch, plans = setup
+    tun = batch.tuning()
+    assert tun["kept_gradients"] == 1
+    batch.set_tuning(use_kept_gradients=useg)
+    assert batch.tuning()["use_kept_gradients"] == useg
+    try:
+        if useg != tun["use_kept_gradients"]:
+            with pytest.raises(blr.BlrError):   # the change dropped the current points
+                batch.hessvec([p["dv"] for p in pairs], [torch.empty_like(p["vt"]) for p in pairs])
+        _compare_with_single_plans(blr, pairs, batch, plans)
+    finally:
+        batch.set_tuning(use_kept_gradients=tun["use_kept_gradients"])
+    with pytest.raises(blr.BlrError):
+        batch.set_tuning(kept_gradients=0)
+
+
+@pytest.mark.parametrize("solo_min", [30000, 1], ids=["three-solo", "all-solo"])
+def test_solo_pairs_equal_single_plans(setup, solo_min):
+    """Pairs that run solo (their own plans' tuned kernels, their own PCG graphs)
+    beside queued pairs, and a batch of solo pairs only, give the single plans'
+    results bit for bit."""
+    blr, pairs, batch, plans = setup
+    tun = batch.tuning()
+    batch.set_tuning(solo_min_voxels=solo_min)
+    want = sum(1 for p in pairs if p["n"][0] * p["n"][1] * p["n"][2] >= solo_min)
+    assert batch.tuning()["solo_pairs"] == want
+    try:
+        _compare_with_single_plans(blr, pairs, batch, plans)
+    finally:
+        batch.set_tuning(solo_min_voxels=tun["solo_min_voxels"])
+    assert batch.tuning()["solo_pairs"] == tun["solo_pairs"]
+
+
 def test_batch_rejects_mixed_shapes_of_time(setup):
     blr = setup[0]
     with pytest.raises(blr.BlrError) as ei:
