@@ -164,6 +164,12 @@ size_t layout(blr_plan *P, char *base) {
     P->T2s = a.take<float>((size_t)P->B2 * P->N2);
     P->T3c = a.take<float>((size_t)P->B3 * P->N3);
     P->T3s = a.take<float>((size_t)P->B3 * P->N3);
+    P->T2e = P->T2p = P->W1t = nullptr;
+    if (P->p.precision == BLR_FP32) {
+        P->W1t = a.take<float>((size_t)2 * P->B1 * P->N1);
+        P->T2e = a.take<float>((size_t)4 * P->B2 * P->N2);
+        P->T2p = a.take<float>((size_t)4 * P->B2 * P->N2);
+    }
     P->A = a.take<float>(P->nb);
     P->dft_big = a.take<float>((size_t)3 * P->B1 * P->N2 * P->N3 * 2);
     P->dft_small = a.take<float>((size_t)3 * P->B1 * P->B2 * P->N3 * 2);
@@ -468,7 +474,7 @@ int plan_create(const blr_params *p, bool grad_cache, blr_plan **out) {
         return BLR_ENOMEM;
     }
     if (cudaMemset(base, 0, bytes) != cudaSuccess ||
-        dft_init_tables(P, 0) != BLR_OK ||
+        dft_init_tables(P, 0) != BLR_OK || dft_autotune(P, 0) != BLR_OK ||
         (p->precision == BLR_MIXED && tc_init_tables(P, 0) != BLR_OK) ||
         (P->fz_tab[0] && fz_init_tables(P, 0) != BLR_OK) ||
         sweep_autotune(P, 0) != BLR_OK || cudaDeviceSynchronize() != cudaSuccess) {

@@ -187,6 +187,10 @@ struct blr_plan {
     // truncated-DFT tables and intermediates
     float *W1;          // [2*B1][N1]: row 2j = cos, row 2j+1 = -sin (2 pi k_j x / N1)
     float *T2c, *T2s;   // [B2][N2]
+    float *W1t;         // FP32 project axis-1 stage: W1 transposed, [N1][2 B1] (or nullptr)
+    int gemm_tile[4];   // FP32 GEMM stages' register tile (0: modelled choice; dft_autotune)
+    float *T2e, *T2p;   // FP32 axis-2 stages as real GEMMs, A operand [k][m] (or nullptr):
+                        // expand [2 B2][2 N2] = [[C, S], [-S, C]]^T-ordered, project [2 N2][2 B2]
     float *T3c, *T3s;   // [B3][N3]
     float *A;           // [B1][B2][B3] regulariser weights
     float *dft_big;     // 3*B1*N2*N3*2 floats
@@ -249,6 +253,7 @@ int plan_create(const blr_params *p, bool grad_cache, blr_plan **out);
 
 // dft.cu
 int dft_init_tables(blr_plan *P, cudaStream_t s);
+int dft_autotune(blr_plan *P, cudaStream_t s);
 // iota into out (3V). mode 0: out = v; mode 1: out = clamp(-dt*v) + CFL/NaN flags.
 int dft_expand(blr_plan *P, const float *vt, float *out, int mode, cudaStream_t s);
 // pi(f) (+ areg A * vadd when vadd != nullptr) into ft.

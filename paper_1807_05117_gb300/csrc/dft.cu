@@ -7,6 +7,8 @@
 //   stage C (axis 1): v[c,x1,x2,x3]  = sum_{k1,re/im} W1[(k1,re/im), x1] A2[...] real GEMM
 // pi = iota^T runs the transposed stages in reverse order (C', B', A').
 // Intermediates are planar: [slab = c*B1 + k1][re|im][row][x3].
+#include <algorithm>
+
 #include "blr_internal.cuh"
 
 namespace {
@@ -28,8 +30,9 @@ __global__ void k_table_kx(float *C, float *S, int N, int B) {
     S[idx] = (float)s;
 }
 
-// W1[2j][x] = cos, W1[2j+1][x] = -sin: the real form of the complex axis-1 sum.
-__global__ void k_table_w1(float *W1, int N, int B) {
+// W1[2j][x] = cos, W1[2j+1][x] = -sin: the real form of the complex axis-1 sum
+// (and, when W1t is given, its transpose W1t[x][2j + (0|1)]).
+__global__ void k_table_w1(float *W1, float *W1t, int N, int B) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= B * N) return;
     int j = idx / N, x = idx - j * N;
@@ -37,6 +40,33 @@ __global__ void k_table_w1(float *W1, int N, int B) {
     phase_cs(j - B / 2, x, N, &c, &s);
     W1[(2 * j) * (long long)N + x] = (float)c;
     W1[(2 * j + 1) * (long long)N + x] = (float)(-s);
+    if (W1t) {
+        W1t[(long long)x * 2 * B + 2 * j] = (float)c;
+        W1t[(long long)x * 2 * B + 2 * j + 1] = (float)(-s);
+    }
+}
+
+// The axis-2 stages' A operands in [k][m] order (see k_sgemm): expand
+// T2e[(ki, k2)][(mi, x2)] and project T2p[(ki, x2)][(mi, k2)], each entry C, S or
+// -S of the phase (k2 - B/2) x2.
+__global__ void k_table_axis2(float *T2e, float *T2p, int N, int B) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= B * N) return;
+    const int j = idx / N, x = idx - j * N;
+    double c, s;
+    phase_cs(j - B / 2, x, N, &c, &s);
+    const float C = (float)c, S = (float)s;
+    const long long M2e = 2LL * N, M2p = 2LL * B;
+    // expand: out (mi, x2) from in (ki, k2): [[C, -S], [S, C]]
+    T2e[(long long)j * M2e + x] = C;                 // ki 0, mi 0
+    T2e[(long long)j * M2e + N + x] = S;             // ki 0, mi 1
+    T2e[(long long)(B + j) * M2e + x] = -S;          // ki 1, mi 0
+    T2e[(long long)(B + j) * M2e + N + x] = C;       // ki 1, mi 1
+    // project: out (mi, k2) from in (ki, x2): [[C, S], [-S, C]]
+    T2p[(long long)x * M2p + j] = C;                 // ki 0, mi 0
+    T2p[(long long)x * M2p + B + j] = -S;            // ki 0, mi 1
+    T2p[(long long)(N + x) * M2p + j] = S;           // ki 1, mi 0
+    T2p[(long long)(N + x) * M2p + B + j] = C;       // ki 1, mi 1
 }
 
 // A(k) = (alpha omega(k) + gamma)^q, q = 2s, omega = sum_d 2(1 - cos(2 pi k_d / N_d)).
@@ -121,147 +151,278 @@ k_expand_axis3(const float *__restrict__ vt, const float *__restrict__ T3c,
 size_t expand_axis3_smem(int B3) { return (size_t)(XR * B3 + B3 * XC) * sizeof(float2); }
 
 // ---------------------------------------------------------------------------
-// stage B (SIGN = +1, expand) and stage B' (SIGN = -1, project): per slab,
-//   out[r][x3] = sum_s (T2c[?] + i SIGN T2s[?]) in[s][x3]
-// expand : r = x2, s = k2, table index [k2][x2]; in rows = B2, out rows = N2
-// project: r = k2, s = x2, table index [k2][x2]; in rows = N2, out rows = B2
-template <int SIGN>
-__global__ void __launch_bounds__(256)
-k_axis2(const float *__restrict__ in, const float *__restrict__ T2c,
-        const float *__restrict__ T2s, float *__restrict__ out,
-        int in_rows, int out_rows, int N2, int N3) {
-    pdl_wait();
-    __shared__ float sre[16][33], sim[16][33];
-    __shared__ float sc[16][33], ss[16][33];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int x3 = blockIdx.x * 32 + tx;
-    const int rb = blockIdx.y * 32;
-    const long long slab = blockIdx.z;
-    const float *inre = in + slab * 2 * (long long)in_rows * N3;
-    const float *inim = inre + (long long)in_rows * N3;
-    float are[4] = {0.f, 0.f, 0.f, 0.f}, aim[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int s0 = 0; s0 < in_rows; s0 += 16) {
-        for (int i = threadIdx.x; i < 512; i += 256) {
-            int ss_ = i >> 5, xx = i & 31;
-            int sidx = s0 + ss_;
-            int gx3 = blockIdx.x * 32 + xx;
-            int gr = rb + xx;
-            bool ok = sidx < in_rows;
-            sre[ss_][xx] = (ok && gx3 < N3) ? inre[(long long)sidx * N3 + gx3] : 0.f;
-            sim[ss_][xx] = (ok && gx3 < N3) ? inim[(long long)sidx * N3 + gx3] : 0.f;
-            float c = 0.f, s = 0.f;
-            if (ok && gr < out_rows) {
-                // table [k2][x2]
-                long long t = (SIGN > 0) ? (long long)sidx * N2 + gr : (long long)gr * N2 + sidx;
-                c = T2c[t];
-                s = T2s[t];
-            }
-            sc[ss_][xx] = c;
-            ss[ss_][xx] = s;
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int q = 0; q < 16; ++q) {
-            float vr = sre[q][tx], vi = sim[q][tx];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                float c = sc[q][ty * 4 + r], s = ss[q][ty * 4 + r];
-                if (SIGN > 0) {   // (c + i s)(vr + i vi)
-                    are[r] = fmaf(c, vr, fmaf(-s, vi, are[r]));
-                    aim[r] = fmaf(s, vr, fmaf(c, vi, aim[r]));
-                } else {          // (c - i s)(vr + i vi)
-                    are[r] = fmaf(c, vr, fmaf(s, vi, are[r]));
-                    aim[r] = fmaf(c, vi, fmaf(-s, vr, aim[r]));
-                }
-            }
-        }
-        __syncthreads();
+// Stages B, B', C and C' are real GEMMs batched over z,
+//   C_z[m][n] = scale * sum_k A(m, k) B_z[k][n],   B_z = B + z strideB ([K][N]),
+// run by one FP32 kernel; only the A operand differs:
+//   AK_KM  A(m, k) = A[k lda + m]    stage C  (A = W1 [2B1][N1]: m = x1, k = (k1, re|im))
+//   AK_MK  A(m, k) = A[m lda + k]    stage C' (A = W1: m = (k1, re|im), k = x1)
+//   AK_E2  stage B  on a planar slab [re|im][k2][x3] -> [re|im][x2][x3]:
+//          m = (re|im, x2), k = (re|im, k2), A = [[C, -S], [S, C]]  (C + i S)(re + i im)
+//   AK_P2  stage B' on a planar slab [re|im][x2][x3] -> [re|im][k2][x3]:
+//          m = (re|im, k2), k = (re|im, x2), A = [[C, S], [-S, C]]  (C - i S)(re + i im)
+// with C = T2c[k2][x2], S = T2s[k2][x2].  Tiles of (16 TM) x (16 TN) outputs,
+// 256 threads as 16 x 16, each thread a TM x TN register tile (rows tm*4 + i + 64 h,
+// columns tn*4 + j + 64 h'); k in chunks of 16 through two shared-memory buffers,
+// the next chunk's loads in flight (registers) during this chunk's products.  The
+// sum over k runs in order.  MODE 1 stores the clamped displacement and latches
+// the CFL / NaN flags.
+enum { AK_KM = 0, AK_MK = 1, AK_E2 = 2, AK_P2 = 3 };
+
+struct GemmArgs {
+    const float *A;
+    int lda;
+    const float *Tc, *Ts;   // AK_E2 / AK_P2
+    int N2, B2;
+    const float *B;
+    long long strideB;
+    float *C;
+    long long strideC;
+    int M, K;
+    long long N;
+    float scale;
+    int *status;
+};
+
+template <int AK>
+__device__ __forceinline__ float a_elem(const GemmArgs &p, int m, int k) {
+    if (m >= p.M || k >= p.K) return 0.f;
+    if (AK == AK_KM) return __ldg(p.A + (long long)k * p.lda + m);
+    if (AK == AK_MK) return __ldg(p.A + (long long)m * p.lda + k);
+    if (AK == AK_E2) {
+        const int mi = m >= p.N2, ki = k >= p.B2;
+        const long long t = (long long)(k - ki * p.B2) * p.N2 + (m - mi * p.N2);
+        return mi == ki ? __ldg(p.Tc + t) : (mi ? __ldg(p.Ts + t) : -__ldg(p.Ts + t));
     }
-    if (x3 >= N3) return;
-    float *ore = out + slab * 2 * (long long)out_rows * N3;
-    float *oim = ore + (long long)out_rows * N3;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        int row = rb + ty * 4 + r;
-        if (row < out_rows) {
-            ore[(long long)row * N3 + x3] = are[r];
-            oim[(long long)row * N3 + x3] = aim[r];
-        }
-    }
+    const int mi = m >= p.B2, ki = k >= p.N2;
+    const long long t = (long long)(m - mi * p.B2) * p.N2 + (k - ki * p.N2);
+    return mi == ki ? __ldg(p.Tc + t) : (mi ? -__ldg(p.Ts + t) : __ldg(p.Ts + t));
 }
 
-// ---------------------------------------------------------------------------
-// stage C / C': C[M][Ncol] = sum_k A(m, k) B[k][Ncol], batched over components.
-// A_TRANS: A(m, k) = A[k*lda + m] (expand, A = W1 [2B1][N1], m = x1, k = (k1,re/im))
-// else   : A(m, k) = A[m*lda + k] (project, m = (k1,re/im), k = x1)
-// MODE 0 stores scale*acc; MODE 1 stores the clamped displacement and latches
-// the CFL / NaN flags.
-template <bool A_TRANS, int MODE>
-__global__ void __launch_bounds__(256)
-k_gemm_axis1(const float *__restrict__ A, int lda, const float *__restrict__ B,
-             long long strideB, float *__restrict__ C, long long strideC,
-             int M, int K, long long Ncol, float scale, int *status) {
+constexpr int GK = 16;   // k per chunk
+
+template <int AK, int MODE, int TM, int TN>
+__global__ void __launch_bounds__(256, 2)
+k_sgemm(GemmArgs p) {
+    constexpr int BM = 16 * TM, BN = 16 * TN;
+    __shared__ __align__(16) float As[2][GK][BM];
+    __shared__ __align__(16) float Bs[2][GK][BN];
+    const int tid = threadIdx.x, tn = tid & 15, tm = tid >> 4;
+    const int m0 = blockIdx.y * BM;
+    const long long n0 = (long long)blockIdx.x * BN;
+    const float *Bz = p.B + blockIdx.z * p.strideB;
+    const bool vec = (p.N & 3) == 0;
+    float ra[TM];
+    float4 rb[TN / 4];
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            const int e = tid + 256 * i;
+            ra[i] = a_elem<AK>(p, m0 + e % BM, k0 + e / BM);
+        }
+#pragma unroll
+        for (int i = 0; i < TN / 4; ++i) {
+            const int e = tid + 256 * i, kk = e / (BN / 4), k = k0 + kk;
+            const long long n = n0 + 4 * (e % (BN / 4));
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k < p.K) {
+                const float *src = Bz + (long long)k * p.N + n;
+                if (vec && n + 3 < p.N) {
+                    v = __ldg(reinterpret_cast<const float4 *>(src));
+                } else {
+                    if (n < p.N) v.x = __ldg(src);
+                    if (n + 1 < p.N) v.y = __ldg(src + 1);
+                    if (n + 2 < p.N) v.z = __ldg(src + 2);
+                    if (n + 3 < p.N) v.w = __ldg(src + 3);
+                }
+            }
+            rb[i] = v;
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            const int e = tid + 256 * i;
+            As[buf][e / BM][e % BM] = ra[i];
+        }
+#pragma unroll
+        for (int i = 0; i < TN / 4; ++i) {
+            const int e = tid + 256 * i;
+            *reinterpret_cast<float4 *>(&Bs[buf][e / (BN / 4)][4 * (e % (BN / 4))]) = rb[i];
+        }
+    };
+    float acc[TM][TN];
+#pragma unroll
+    for (int r = 0; r < TM; ++r)
+#pragma unroll
+        for (int c = 0; c < TN; ++c) acc[r][c] = 0.f;
     pdl_wait();
-    __shared__ __align__(16) float As[16][64];
-    __shared__ __align__(16) float Bs[16][128];
-    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-    const int m0 = blockIdx.y * 64;
-    const long long c0 = (long long)blockIdx.x * 128;
-    B += blockIdx.z * strideB;
-    C += blockIdx.z * strideC;
-    float acc[8][4];
+    load(0);
+    store(0);
+    __syncthreads();
+    for (int k0 = 0, cur = 0; k0 < p.K; k0 += GK, cur ^= 1) {
+        const bool more = k0 + GK < p.K;
+        if (more) load(k0 + GK);
 #pragma unroll
-    for (int r = 0; r < 8; ++r)
+        for (int kk = 0; kk < GK; ++kk) {
+            float a[TM], b[TN];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[r][j] = 0.f;
-    for (int k0 = 0; k0 < K; k0 += 16) {
-        for (int i = tid; i < 16 * 64; i += 256) {
-            int kk = i >> 6, mm = i & 63;
-            int gm = m0 + mm, gk = k0 + kk;
-            float a = 0.f;
-            if (gm < M && gk < K) a = A_TRANS ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk];
-            As[kk][mm] = a;
+            for (int h = 0; h < TM / 4; ++h) {
+                const float4 v = *reinterpret_cast<const float4 *>(&As[cur][kk][64 * h + tm * 4]);
+                a[4 * h] = v.x;
+                a[4 * h + 1] = v.y;
+                a[4 * h + 2] = v.z;
+                a[4 * h + 3] = v.w;
+            }
+#pragma unroll
+            for (int h = 0; h < TN / 4; ++h) {
+                const float4 v = *reinterpret_cast<const float4 *>(&Bs[cur][kk][64 * h + tn * 4]);
+                b[4 * h] = v.x;
+                b[4 * h + 1] = v.y;
+                b[4 * h + 2] = v.z;
+                b[4 * h + 3] = v.w;
+            }
+#pragma unroll
+            for (int r = 0; r < TM; ++r)
+#pragma unroll
+                for (int c = 0; c < TN; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
         }
-        for (int i = tid; i < 16 * 128; i += 256) {
-            int kk = i >> 7, cc = i & 127;
-            int gk = k0 + kk;
-            long long gc = c0 + cc;
-            Bs[kk][cc] = (gk < K && gc < Ncol) ? B[(long long)gk * Ncol + gc] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            float4 a0 = *reinterpret_cast<const float4 *>(&As[kk][ty * 8]);
-            float4 a1 = *reinterpret_cast<const float4 *>(&As[kk][ty * 8 + 4]);
-            float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            float b[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 32 * j];
-#pragma unroll
-            for (int r = 0; r < 8; ++r)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[r][j] = fmaf(a[r], b[j], acc[r][j]);
-        }
+        if (more) store(cur ^ 1);
         __syncthreads();
     }
+    float *Cz = p.C + blockIdx.z * p.strideC;
     int flags = 0;
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        int gm = m0 + ty * 8 + r;
-        if (gm >= M) continue;
+    for (int r = 0; r < TM; ++r) {
+        const int m = m0 + 64 * (r / 4) + tm * 4 + (r & 3);
+        if (m >= p.M) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            long long gc = c0 + tx + 32 * j;
-            if (gc >= Ncol) continue;
-            float v = acc[r][j] * scale;
-            if (MODE == 1) {
-                if (!(fabsf(v) < 1.f)) flags |= (v != v) ? BLR_FLAG_NAN : BLR_FLAG_CFL;
-                v = fminf(fmaxf(v, -1.f), 0.99999994f);
+        for (int h = 0; h < TN / 4; ++h) {
+            const long long n = n0 + 64 * h + tn * 4;
+            float v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float x = acc[r][4 * h + j] * p.scale;
+                if (MODE == 1) {
+                    if (n + j < p.N && !(fabsf(x) < 1.f)) flags |= (x != x) ? BLR_FLAG_NAN : BLR_FLAG_CFL;
+                    x = fminf(fmaxf(x, -1.f), 0.99999994f);
+                }
+                v[j] = x;
             }
-            C[(long long)gm * Ncol + gc] = v;
+            float *dst = Cz + (long long)m * p.N + n;
+            if (vec && n + 3 < p.N) {
+                *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (n + j < p.N) dst[j] = v[j];
+            }
         }
     }
-    if (MODE == 1 && flags) atomicOr(status, flags);
+    if (MODE == 1 && flags) atomicOr(p.status, flags);
+}
+
+// Launch k_sgemm with the largest register tile that still gives every SM two
+// blocks (or the smallest tile when even that does not).
+constexpr int SG_CANDS = 4;
+
+template <int AK, int MODE>
+int launch_sgemm(const GemmArgs &p, int batch, int sms, cudaStream_t s, int forced = 0) {
+    // modelled time: waves of resident blocks x a block's padded tile over the
+    // register tile's relative FMA rate (smem operand traffic per FMA)
+    const int tms[4] = {8, 8, 4, 4}, tns[4] = {8, 4, 8, 4}, res[4] = {2, 2, 2, 3};
+    const double rate[4] = {1.0, 0.75, 0.75, 0.55};
+    int pick = 0;
+    double best = 1e300;
+    for (int c = 0; c < 4; ++c) {
+        const long long bm = 16LL * tms[c], bn = 16LL * tns[c];
+        const long long blocks = ceil_div_ll(p.N, bn) * ceil_div_ll(p.M, bm) * batch;
+        const long long waves = ceil_div_ll(blocks, (long long)res[c] * sms);
+        const long long share = std::min<long long>(res[c], ceil_div_ll(blocks, sms));
+        const double t = (double)waves * (double)(bm * bn) * share / rate[c];
+        if (t < best * 0.999) {
+            best = t;
+            pick = c;
+        }
+    }
+    if (forced >= 1 && forced <= SG_CANDS) pick = forced - 1;
+    const int TMc = tms[pick], TNc = tns[pick];
+    const dim3 grid((unsigned)ceil_div_ll(p.N, 16LL * TNc), (unsigned)ceil_div_ll(p.M, 16LL * TMc),
+                    (unsigned)batch);
+    if (TMc == 8 && TNc == 8) launch_pdl(k_sgemm<AK, MODE, 8, 8>, grid, dim3(256), 0, s, p);
+    else if (TMc == 8) launch_pdl(k_sgemm<AK, MODE, 8, 4>, grid, dim3(256), 0, s, p);
+    else if (TNc == 8) launch_pdl(k_sgemm<AK, MODE, 4, 8>, grid, dim3(256), 0, s, p);
+    else launch_pdl(k_sgemm<AK, MODE, 4, 4>, grid, dim3(256), 0, s, p);
+    BLR_CK_LAUNCH();
+    return BLR_OK;
+}
+
+int device_sms(const blr_plan *P) {
+    if (P->sms > 0) return P->sms;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        sms = 148;
+    return sms;
+}
+
+// The four GEMM stages of the FP32 transforms: 0 B (expand, axis 2), 1 C (expand,
+// axis 1), 2 C' (project, axis 1), 3 B' (project, axis 2).  `in` / `out` are the
+// stage's B operand and result; mode 1 (stage C only) stores the displacement.
+int launch_stage(const blr_plan *P, int stage, const float *in, float *out, float scale, int mode,
+                 cudaStream_t s) {
+    const long long ncol = (long long)P->N2 * P->N3;
+    const int sms = device_sms(P), forced = P->gemm_tile[stage];
+    GemmArgs g{};
+    g.Tc = P->T2c;
+    g.Ts = P->T2s;
+    g.N2 = P->N2;
+    g.B2 = P->B2;
+    g.B = in;
+    g.C = out;
+    g.scale = scale;
+    g.status = P->dstatus;
+    switch (stage) {
+        case 0:
+            g.A = P->T2e;
+            g.lda = 2 * P->N2;
+            g.strideB = 2LL * P->B2 * P->N3;
+            g.strideC = 2LL * P->N2 * P->N3;
+            g.M = 2 * P->N2;
+            g.K = 2 * P->B2;
+            g.N = P->N3;
+            return P->T2e ? launch_sgemm<AK_KM, 0>(g, 3 * P->B1, sms, s, forced)
+                          : launch_sgemm<AK_E2, 0>(g, 3 * P->B1, sms, s, forced);
+        case 1:
+            g.A = P->W1;
+            g.lda = P->N1;
+            g.strideB = 2LL * P->B1 * ncol;
+            g.strideC = P->V;
+            g.M = P->N1;
+            g.K = 2 * P->B1;
+            g.N = ncol;
+            return mode == 0 ? launch_sgemm<AK_KM, 0>(g, 3, sms, s, forced)
+                             : launch_sgemm<AK_KM, 1>(g, 3, sms, s, forced);
+        case 2:
+            g.A = P->W1t ? P->W1t : P->W1;
+            g.lda = P->W1t ? 2 * P->B1 : P->N1;
+            g.strideB = P->V;
+            g.strideC = 2LL * P->B1 * ncol;
+            g.M = 2 * P->B1;
+            g.K = P->N1;
+            g.N = ncol;
+            return P->W1t ? launch_sgemm<AK_KM, 0>(g, 3, sms, s, forced)
+                          : launch_sgemm<AK_MK, 0>(g, 3, sms, s, forced);
+        default:
+            g.A = P->T2p;
+            g.lda = 2 * P->B2;
+            g.strideB = 2LL * P->N2 * P->N3;
+            g.strideC = 2LL * P->B2 * P->N3;
+            g.M = 2 * P->B2;
+            g.K = 2 * P->N2;
+            g.N = P->N3;
+            return P->T2p ? launch_sgemm<AK_KM, 0>(g, 3 * P->B1, sms, s, forced)
+                          : launch_sgemm<AK_P2, 0>(g, 3 * P->B1, sms, s, forced);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -351,12 +512,17 @@ size_t project_axis3_smem(int B3) { return (size_t)(XR * PXC + PXC * (B3 + 1)) *
 
 int dft_init_tables(blr_plan *P, cudaStream_t s) {
     const int T = 256;
-    k_table_w1<<<(int)ceil_div_ll((long long)P->B1 * P->N1, T), T, 0, s>>>(P->W1, P->N1, P->B1);
+    k_table_w1<<<(int)ceil_div_ll((long long)P->B1 * P->N1, T), T, 0, s>>>(P->W1, P->W1t, P->N1, P->B1);
     BLR_CK_LAUNCH();
     k_table_kx<<<(int)ceil_div_ll((long long)P->B2 * P->N2, T), T, 0, s>>>(P->T2c, P->T2s, P->N2, P->B2);
     BLR_CK_LAUNCH();
     k_table_kx<<<(int)ceil_div_ll((long long)P->B3 * P->N3, T), T, 0, s>>>(P->T3c, P->T3s, P->N3, P->B3);
     BLR_CK_LAUNCH();
+    if (P->T2e && P->T2p) {
+        k_table_axis2<<<(int)ceil_div_ll((long long)P->B2 * P->N2, T), T, 0, s>>>(P->T2e, P->T2p,
+                                                                                 P->N2, P->B2);
+        BLR_CK_LAUNCH();
+    }
     k_regulariser<<<(int)ceil_div_ll(P->nb, T), T, 0, s>>>(
         P->A, P->N1, P->N2, P->N3, P->B1, P->B2, P->B3, P->p.alpha, P->p.gamma,
         (int)(2.0 * P->p.s + 0.5));
@@ -383,11 +549,8 @@ int dft_expand(blr_plan *P, const float *vt, float *out, int mode, cudaStream_t 
         int rc = tc_axis2(P, 0, P->dft_small, P->dft_big, s);
         if (rc) return rc;
     } else {
-        dim3 gb((unsigned)ceil_div_ll(P->N3, 32), (unsigned)ceil_div_ll(P->N2, 32), 3u * P->B1);
-        launch_pdl(k_axis2<+1>, gb, dim3(256), 0, s, (const float *)P->dft_small,
-                   (const float *)P->T2c, (const float *)P->T2s, P->dft_big, P->B2, P->N2, P->N2,
-                   P->N3);
-        BLR_CK_LAUNCH();
+        int rc = launch_stage(P, 0, P->dft_small, P->dft_big, 1.f, 0, s);
+        if (rc) return rc;
     }
     // stage C
     if (P->p.precision == BLR_MIXED) {
@@ -395,17 +558,8 @@ int dft_expand(blr_plan *P, const float *vt, float *out, int mode, cudaStream_t 
         if (rc || mode == 0 || out != P->d) return rc;
         return sweep_pack_d4(P, s);
     }
-    const long long ncol = (long long)P->N2 * P->N3;
-    dim3 gc((unsigned)ceil_div_ll(ncol, 128), (unsigned)ceil_div_ll(P->N1, 64), 3u);
-    if (mode == 0)
-        launch_pdl(k_gemm_axis1<true, 0>, gc, dim3(256), 0, s, (const float *)P->W1, P->N1,
-                   (const float *)P->dft_big, 2LL * P->B1 * ncol, out, P->V, P->N1, 2 * P->B1, ncol,
-                   1.f, P->dstatus);
-    else
-        launch_pdl(k_gemm_axis1<true, 1>, gc, dim3(256), 0, s, (const float *)P->W1, P->N1,
-                   (const float *)P->dft_big, 2LL * P->B1 * ncol, out, P->V, P->N1, 2 * P->B1, ncol,
-                   -P->dt, P->dstatus);
-    BLR_CK_LAUNCH();
+    const int rc = launch_stage(P, 1, P->dft_big, out, mode == 0 ? 1.f : -P->dt, mode, s);
+    if (rc) return rc;
     if (mode == 1 && out == P->d) return sweep_pack_d4(P, s);
     return BLR_OK;
 }
@@ -413,27 +567,21 @@ int dft_expand(blr_plan *P, const float *vt, float *out, int mode, cudaStream_t 
 int dft_project(blr_plan *P, const float *f, float *ft, const float *vadd, cudaStream_t s,
                 float areg) {
     if (P->fz_tab[0]) return fz_project(P, f, ft, vadd, areg, s);
-    const long long ncol = (long long)P->N2 * P->N3;
     // stage C'
     if (P->p.precision == BLR_MIXED) {
         int rc = tc_axis1(P, 1, f, P->dft_big, 1.f, 0, s);
         if (rc) return rc;
     } else {
-        dim3 gc((unsigned)ceil_div_ll(ncol, 128), (unsigned)ceil_div_ll(2 * P->B1, 64), 3u);
-        launch_pdl(k_gemm_axis1<false, 0>, gc, dim3(256), 0, s, (const float *)P->W1, P->N1, f,
-                   P->V, P->dft_big, 2LL * P->B1 * ncol, 2 * P->B1, P->N1, ncol, 1.f, P->dstatus);
-        BLR_CK_LAUNCH();
+        int rc = launch_stage(P, 2, f, P->dft_big, 1.f, 0, s);
+        if (rc) return rc;
     }
     // stage B'
     if (P->tc_tab2_project) {
         int rc = tc_axis2(P, 1, P->dft_big, P->dft_small, s);
         if (rc) return rc;
     } else {
-        dim3 gb((unsigned)ceil_div_ll(P->N3, 32), (unsigned)ceil_div_ll(P->B2, 32), 3u * P->B1);
-        launch_pdl(k_axis2<-1>, gb, dim3(256), 0, s, (const float *)P->dft_big,
-                   (const float *)P->T2c, (const float *)P->T2s, P->dft_small, P->N2, P->B2, P->N2,
-                   P->N3);
-        BLR_CK_LAUNCH();
+        int rc = launch_stage(P, 3, P->dft_big, P->dft_small, 1.f, 0, s);
+        if (rc) return rc;
     }
     // stage A'
     const int rows = 3 * P->B1 * P->B2;
@@ -444,4 +592,42 @@ int dft_project(blr_plan *P, const float *f, float *ft, const float *vadd, cudaS
                (const float *)P->A, vadd, areg, rows, P->B2, P->B3, P->N3, P->B1 * P->B2);
     BLR_CK_LAUNCH();
     return BLR_OK;
+}
+
+// Tile shapes of the FP32 GEMM stages, chosen by timing each candidate on the
+// plan's own buffers (at creation, while they hold nothing).
+int dft_autotune(blr_plan *P, cudaStream_t s) {
+    for (int st = 0; st < 4; ++st) P->gemm_tile[st] = 0;
+    if (!P->T2e || !P->T2p || !P->W1t) return BLR_OK;   // FP32 plans only
+    cudaEvent_t e0, e1;
+    BLR_CK(cudaEventCreate(&e0));
+    BLR_CK(cudaEventCreate(&e1));
+    const float *ins[4] = {P->dft_small, P->dft_big, P->dv, P->dft_big};
+    float *outs[4] = {P->dft_big, P->dv, P->dft_big, P->dft_small};
+    int rc = BLR_OK;
+    for (int st = 0; st < 4 && !rc; ++st) {
+        float best = 1e30f;
+        int pick = 0;
+        for (int c = 1; c <= SG_CANDS && !rc; ++c) {
+            P->gemm_tile[st] = c;
+            float tot = 0.f;
+            for (int rep = 0; rep < 4 && !rc; ++rep) {
+                if (cudaEventRecord(e0, s) != cudaSuccess) rc = BLR_ECUDA;
+                if (!rc) rc = launch_stage(P, st, ins[st], outs[st], 1.f, 0, s);
+                if (!rc && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+                    rc = BLR_ECUDA;
+                float ms = 0.f;
+                if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = BLR_ECUDA;
+                if (rep) tot += ms;
+            }
+            if (tot < best) {
+                best = tot;
+                pick = c;
+            }
+        }
+        P->gemm_tile[st] = pick;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
 }
