@@ -364,7 +364,7 @@ int blr_expand_noalloc(const int n[3], const int band[3], const float *vt, float
 unsigned long long blr_kernel_launches(void);
 
 /* Diagnostic (no counterpart in the paper): the sweep shapes the plan's
- * autotuner chose at creation.  vals: host, n ints; the first min(n, 11) are
+ * autotuner chose at creation.  vals: host, n ints; the first min(n, 12) are
  * written, in this order: wide-copy sweeps (0/1), state gradients kept (0/1),
  * adjoint blocks per SM, adjoint reads the kept gradient (0/1), incremental
  * state form (0 wide-copy, 1 wide-copy reading the kept gradient, 2 gather),
@@ -372,8 +372,10 @@ unsigned long long blr_kernel_launches(void);
  * chunk, adjoint march x1 chunk, displacement copy kept in persisting L2
  * lines (0/1; when 1, plan creation raised the context's persisting-L2
  * set-aside to hold it), two adjoint steps per launch (blocks per SM of that
- * kernel's grid, or 0 for one step per launch).  Returns BLR_EINVAL for a
- * NULL plan or vals. */
+ * kernel's grid, or 0 for one step per launch), split adjoint solve (0/1: the
+ * steps transport lambda alone into kept adjoint states, (nt - 1) V floats,
+ * and one pass sums the body force of all steps, bit-identical to the per-step
+ * sums).  Returns BLR_EINVAL for a NULL plan or vals. */
 int blr_plan_tuning(blr_plan_t plan, int *vals, int n);
 
 /* Test hook (no counterpart in the paper): while `on` is non-zero, every launch
@@ -387,12 +389,14 @@ int blr_plan_tuning(blr_plan_t plan, int *vals, int n);
 int blr_test_expire_waits(int on);
 
 /* Diagnostic (no counterpart in the paper): set the sweep shapes, in the order
- * and meaning of blr_plan_tuning (n >= 11 values; the first two must be the
- * plan's own), instead of the autotuner's choice, e.g. to reproduce a
+ * and meaning of blr_plan_tuning (n >= 11 values, a 12th sets the split
+ * adjoint solve; the first two must be the plan's own), instead of the
+ * autotuner's choice, e.g. to reproduce a
  * configuration.  Every shape computes the same results bit for bit.
  * Synchronises the device.  BLR_EINVAL for a value out of range or a shape the
  * plan's buffers do not support (a kept-gradient form without kept gradients,
- * the persisting-L2 window where the device has none). */
+ * the persisting-L2 window where the device has none, the split adjoint
+ * without its kept adjoint states or together with two steps per launch). */
 int blr_plan_set_tuning(blr_plan_t plan, const int *vals, int n);
 
 /* Human-readable text for a status code (static storage). */

@@ -448,7 +448,8 @@ class Plan:
 
     TUNING_KEYS = ("wide_sweeps", "grad_kept", "adjoint_blocks_per_sm", "adjoint_reads_grad",
                    "incremental_form", "incremental_blocks_per_sm", "march_blocks_per_sm",
-                   "march_chunk", "adjoint_march_chunk", "l2_persist_d4", "adjoint_two_step")
+                   "march_chunk", "adjoint_march_chunk", "l2_persist_d4", "adjoint_two_step",
+                   "adjoint_split")
 
     def tuning(self) -> dict:
         """The sweep shapes the autotuner chose (blr_plan_tuning)."""

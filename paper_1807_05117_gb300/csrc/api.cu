@@ -155,6 +155,9 @@ size_t layout(blr_plan *P, char *base) {
         P->U = P->rho_nt = P->rho[0] = P->rho[1] = P->du[0] = P->du[1] = P->Gw = nullptr;
     }
     P->Gm = P->use_gm ? a.take<float>((size_t)3 * P->p.nt * V) : nullptr;
+    P->lam_keep = (P->use_gm && P->nvel == 1 && P->p.nt > 1 && P->p.hessian != BLR_NEWTON)
+                      ? a.take<float>((size_t)(P->p.nt - 1) * V)
+                      : nullptr;
     P->b = a.take<float>(3 * V);
     P->dv = a.take<float>(3 * V);
     P->dm[0] = a.take<float>(V);
@@ -493,10 +496,10 @@ extern "C" {
 
 int blr_plan_tuning(blr_plan_t P, int *vals, int n) {
     if (!P || !vals) return BLR_EINVAL;
-    const int v[11] = {P->sweep_wide ? 1 : 0, P->Gm ? 1 : 0, P->bal_adj, P->adj_useg,
+    const int v[12] = {P->sweep_wide ? 1 : 0, P->Gm ? 1 : 0, P->bal_adj, P->adj_useg,
                        P->inc_mode, P->bal_inc, P->bal_sweep, P->chunk, P->chunk_adj,
-                       P->l2_persist, P->adj2};
-    for (int i = 0; i < n && i < 11; ++i) vals[i] = v[i];
+                       P->l2_persist, P->adj2, P->adj_split};
+    for (int i = 0; i < n && i < 12; ++i) vals[i] = v[i];
     return BLR_OK;
 }
 
@@ -514,6 +517,8 @@ int blr_plan_set_tuning(blr_plan_t P, const int *vals, int n) {
     if (chunk < 1 || chunk > P->N1 || chunk_adj < 1 || chunk_adj > P->N1) return BLR_EINVAL;
     if ((l2 != 0 && l2 != 1) || (l2 && !P->l2_win_bytes)) return BLR_EINVAL;
     if (adj2 < 0 || adj2 > 2 || (adj2 && (!gm || !P->d4 || P->nvel != 1))) return BLR_EINVAL;
+    const int split = n >= 12 ? vals[11] : P->adj_split;
+    if ((split != 0 && split != 1) || (split && (!P->lam_keep || !P->d4 || adj2))) return BLR_EINVAL;
     if (cudaDeviceSynchronize() != cudaSuccess) return BLR_ECUDA;
     P->bal_adj = bal_adj;
     P->adj_useg = useg;
@@ -524,6 +529,7 @@ int blr_plan_set_tuning(blr_plan_t P, const int *vals, int n) {
     sweep_set_chunk(P, 1, chunk_adj);
     P->l2_persist = l2;
     P->adj2 = adj2;
+    P->adj_split = split;
     return BLR_OK;
 }
 

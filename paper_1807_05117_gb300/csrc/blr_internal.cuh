@@ -147,6 +147,9 @@ struct blr_plan {
     bool use_gm;        // Gm is kept (see Gm)
     int bal_inc;        // blocks per SM of the wide-copy incremental-state grid (sweep_autotune)
     int adj_useg;       // the adjoint reads Gm (1) or interpolates it (0)      (sweep_autotune)
+    int adj_split;      // adjoint solve as transport steps + one body-force pass (sweep_autotune)
+    int bal_tr;         // blocks per SM of the transport-only grid (0: ADJ_BLOCKS)
+    float *lam_keep;    // lambda^1 .. lambda^{nt-1} of the split adjoint solve, or nullptr
     int adj2;           // two adjoint steps per launch on a balanced grid of adj2 blocks
                         // per SM (plans that keep Gm), or 0: one step per launch
                         //                                                      (sweep_autotune)

@@ -669,7 +669,9 @@ __device__ __forceinline__ AdjWRings adjw_rings() {
 
 // USEG: grad m^n(x + d(x)) is read from Gn ([3][V], written by the state sweep)
 // instead of being interpolated from an m^n ring (which is then not kept).
-template <bool FIRST, bool WRITE_LAM, bool USEG>
+// BODY false: the transport lambda^n = S^T lambda^{n+1} alone (no body force, no
+// m^n ring; the body force is summed over the steps afterwards, k_body_force).
+template <bool FIRST, bool WRITE_LAM, bool USEG, bool BODY = true>
 __device__ __forceinline__ void
 adjoint_tile_w(const float *__restrict__ lam_in, const float *__restrict__ m_n,
                const float4 *__restrict__ d4, float *__restrict__ lam_out, float *__restrict__ b,
@@ -691,7 +693,7 @@ adjoint_tile_w(const float *__restrict__ lam_in, const float *__restrict__ m_n,
         const int c = tid + MT * i;
         offq[i] = c < BPL ? win_off(g, j0, k0, c / BW, c % BW) : 0;
     }
-    const bool cl = tid < ASC, cm = !USEG && tid >= AM0;
+    const bool cl = tid < ASC, cm = BODY && !USEG && tid >= AM0;
     const int offl = cl ? win_off(g, j0, k0, tid / BG, 4 * (tid % BG)) : 0;
     const int offm = cm ? win_off(g, j0, k0, (tid - AM0) / BG, 4 * ((tid - AM0) % BG)) : 0;
     const uint32_t q0s = smem_u32(R.Q) + (uint32_t)tid * 16u;
@@ -728,7 +730,7 @@ adjoint_tile_w(const float *__restrict__ lam_in, const float *__restrict__ m_n,
             // first, so the loads of plane s's b and grad m^n have the whole transpose
             // to land
             const int o = s - 1;
-            if (o >= i0) {
+            if (BODY && o >= i0) {
                 const float4 *Qo = R.Q + ((r + 3) & (BQ - 1)) * BPL;   // plane s - 1
                 const float *Lo = R.L + ((r + 3) & (BQ - 1)) * BPL;
                 const float *Ma = R.M + ((uint32_t)(r + 4) % BM) * BPL;          // plane s - 2
@@ -758,7 +760,7 @@ adjoint_tile_w(const float *__restrict__ lam_in, const float *__restrict__ m_n,
                     }
                 }
             }
-            if ((!FIRST || USEG) && s >= i0 && s < i_end) {
+            if (BODY && (!FIRST || USEG) && s >= i0 && s < i_end) {
 #pragma unroll
                 for (int jj = 0; jj < ARJ; ++jj) {
                     const int j = jb + jj;
@@ -832,6 +834,70 @@ k_adjoint_wide(const float *__restrict__ lam_in, const float *__restrict__ m_n,
         adjoint_tile_w<FIRST, WRITE_LAM, USEG>(lam_in, m_n, d4, lam_out, b, dt, g, len, kt * MK,
                                                jt * AJ, i0, Gn);
     });
+}
+
+// The adjoint transport alone, lambda^n = S^T lambda^{n+1} (wide-copy tiles).
+__global__ void __launch_bounds__(MT, ADJ_BLOCKS)
+k_adjoint_transport(const float *__restrict__ lam_in, const float4 *__restrict__ d4,
+                    float *__restrict__ lam_out, Grid3 g, int ntk, long long W) {
+    pdl_wait();
+    for_segments(g.N1, ntk, W, [&](int kt, int jt, int i0, int len) {
+        adjoint_tile_w<false, true, true, false>(lam_in, nullptr, d4, lam_out, nullptr, 0.f, g, len,
+                                                 kt * MK, jt * AJ, i0, nullptr);
+    });
+}
+
+// Body force of a whole adjoint solve from its kept adjoint states,
+//   b_a(x) = sum_{n = nt-1 .. 0} dt lambda^{n+1}(x) grad_a m^n(x + d(x)),
+// summed from n = nt - 1 down with the products and fused multiply-adds of the
+// per-step kernels (so the result is theirs bit for bit).  lambda^nt is lam_final;
+// lambda^k (1 <= k < nt) is lam_keep[k - 1]; Gm[n] the kept state gradients.
+// Four voxels per thread (V % 4 == 0) or one.
+template <bool VEC>
+__global__ void __launch_bounds__(256)
+k_body_force(const float *__restrict__ lam_final, const float *__restrict__ lam_keep,
+             const float *__restrict__ Gm, float *__restrict__ b, float dt, int nt, long long V) {
+    pdl_wait();
+    constexpr int W4 = VEC ? 4 : 1;
+    const long long units = V / W4;
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < units;
+         u += (long long)gridDim.x * blockDim.x) {
+        const long long x = u * W4;
+        float acc[3][W4];
+#pragma unroll 2
+        for (int n = nt - 1; n >= 0; --n) {
+            const float *lp = n == nt - 1 ? lam_final : lam_keep + (size_t)n * V;
+            const float *G = Gm + (size_t)3 * n * V;
+            float lam[W4], gv[3][W4];
+            if constexpr (VEC) {
+                const float4 l4 = __ldg(reinterpret_cast<const float4 *>(lp + x));
+                lam[0] = l4.x; lam[1] = l4.y; lam[2] = l4.z; lam[3] = l4.w;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const float4 g4 = __ldg(reinterpret_cast<const float4 *>(G + a * V + x));
+                    gv[a][0] = g4.x; gv[a][1] = g4.y; gv[a][2] = g4.z; gv[a][3] = g4.w;
+                }
+            } else {
+                lam[0] = __ldg(lp + x);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) gv[a][0] = __ldg(G + a * V + x);
+            }
+#pragma unroll
+            for (int q = 0; q < W4; ++q) {
+                const float sl = dt * lam[q];
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    acc[a][q] = n == nt - 1 ? sl * gv[a][q] : fmaf(sl, gv[a][q], acc[a][q]);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if constexpr (VEC)
+                *reinterpret_cast<float4 *>(b + a * V + x) = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+            else
+                b[a * V + x] = acc[a][0];
+        }
+    }
 }
 
 // Incremental state: a block covers 32 (x3) x AJ (x2) voxels, each thread two
@@ -1328,6 +1394,7 @@ int adjoint_smem_attributes() {
     BLR_CK(cudaFuncSetAttribute(k_adjoint_bal<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
     BLR_CK(cudaFuncSetAttribute(k_adjoint_bal<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
     BLR_CK(cudaFuncSetAttribute(k_adjoint_bal<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_adjoint_transport, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM_G));
     BLR_CK(cudaFuncSetAttribute(k_adjoint_wide<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM_G));
     BLR_CK(cudaFuncSetAttribute(k_adjoint_wide<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM));
     BLR_CK(cudaFuncSetAttribute(k_adjoint_wide<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM_G));
@@ -1495,6 +1562,28 @@ void launch_adjoint(const blr_plan *P, bool first, bool wlam, const float *lin, 
     else launch_adjoint_t<false, false>(P, lin, mn, lout, b, Gn, s);
 }
 
+// lambda^n = S^T lambda^{n+1} alone (the split adjoint solve)
+void launch_transport(const blr_plan *P, const float *lin, float *lout, cudaStream_t s) {
+    const BalGeom g = bal_geom(P, P->bal_tr ? P->bal_tr : ADJ_BLOCKS, AJ);
+    cudaAccessPolicyWindow w;
+    const cudaAccessPolicyWindow *win = d4_window(P, &w);
+    launch_pdl_l2(win, k_adjoint_transport, dim3(g.G), dim3(MT), ADJW_SMEM_G, s, lin,
+                  (const float4 *)P->d4, lout, P->grid, g.ntk, g.W);
+}
+
+void launch_body_force(const blr_plan *P, const float *lam_final, float *b, cudaStream_t s) {
+    const bool vec = (P->V & 3) == 0;
+    const long long units = vec ? P->V / 4 : P->V;
+    long long blocks = ceil_div_ll(units, 256);
+    if (blocks > 8LL * P->sms) blocks = 8LL * P->sms;
+    if (vec)
+        launch_pdl(k_body_force<true>, dim3((unsigned)blocks), dim3(256), 0, s, lam_final,
+                   (const float *)P->lam_keep, (const float *)P->Gm, b, P->dt, P->p.nt, P->V);
+    else
+        launch_pdl(k_body_force<false>, dim3((unsigned)blocks), dim3(256), 0, s, lam_final,
+                   (const float *)P->lam_keep, (const float *)P->Gm, b, P->dt, P->p.nt, P->V);
+}
+
 template <bool FIRST, bool LAST>
 void launch_incstate_t(const blr_plan *P, const float *din, const float *mn, float *dout,
                        float lam_scale, const float *Gn, cudaStream_t s, bool wide) {
@@ -1585,6 +1674,19 @@ int sweep_adjoint(blr_plan *P, float *b, float *lambda0, const float *lam_final,
     const int nt = P->p.nt;
     const bool keep = P->lam_all && lam_final == P->lam_nt;
     int cur = 0;
+    if (P->adj_split && !keep && P->lam_keep && P->Gm && P->nvel == 1 && P->d4) {
+        // transport steps into the kept states (lambda^0 only when asked for), then
+        // the body force of all steps in one pass
+        for (int n = nt - 1; n >= (lambda0 ? 0 : 1); --n) {
+            const float *lin = n == nt - 1 ? lam_final : P->lam_keep + (size_t)n * P->V;
+            float *lout = n == 0 ? lambda0 : P->lam_keep + (size_t)(n - 1) * P->V;
+            launch_transport(P, lin, lout, s);
+            BLR_CK_LAUNCH();
+        }
+        launch_body_force(P, lam_final, b, s);
+        BLR_CK_LAUNCH();
+        return BLR_OK;
+    }
     if (P->adj2 && !keep && P->Gm && P->nvel == 1 && P->d4) {
         // two steps per launch from the top, the last step alone when nt is odd
         int n = nt - 1;
@@ -1889,6 +1991,10 @@ int time_step(blr_plan *P, int kind, cudaStream_t s) {
     else if (kind == 4)   // two adjoint steps in one launch
         launch_adjoint2(P, false, true, P->lam[0], P->lam[1], P->b, grad_slot(P, 0),
                         grad_slot(P, P->p.nt > 1 ? 1 : 0), s);
+    else if (kind == 5)   // the transport alone
+        launch_transport(P, P->lam[0], P->lam[1], s);
+    else if (kind == 6)   // the body force of a whole solve
+        launch_body_force(P, P->lam[0], P->b, s);
     else
         launch_incstate(P, false, false, P->dm[0], P->m, P->dm[1], 1.f,
                         kind == 3 ? grad_slot(P, 0) : nullptr, s, kind == 3);
@@ -1994,6 +2100,25 @@ int sweep_autotune(blr_plan *P, cudaStream_t s) {
                 }
             }
             P->adj2 = best2;
+        }
+        // the split solve: transport steps plus one body-force pass per solve (a
+        // pass covers nt steps), against the best per-step form
+        P->adj_split = 0;
+        if (P->lam_keep && P->Gm && P->nvel == 1 && P->p.nt > 1 && !rc) {
+            const int save2 = P->adj2;
+            P->adj2 = 0;
+            int best_b2 = 0;
+            for (int bps = 1; bps <= ADJ_BLOCKS && !rc; ++bps) {
+                P->bal_tr = bps;
+                const float t = time_shape(5) + time_shape(6) / (float)P->p.nt;
+                if (t < best) {
+                    best = t;
+                    best_b2 = bps;
+                }
+            }
+            P->bal_tr = best_b2;
+            if (best_b2) P->adj_split = 1;
+            else P->adj2 = save2;
         }
     }
     if (!rc) tune_march(2);

@@ -1,8 +1,10 @@
 """Sweep kernels chosen by the autotuner compute the same results bit for bit.
 
 The adjoint sweep runs one time step per launch, or two (temporal blocking:
-lambda^n kept in shared memory, the body force of both steps written once).
-blr_plan_set_tuning forces either form on the same plan; the gradient (Eq. 38),
+lambda^n kept in shared memory, the body force of both steps written once), or
+is split (the steps transport lambda alone into kept adjoint states, one pass
+then sums the body force of every step).  blr_plan_set_tuning forces each form
+on the same plan; the gradient (Eq. 38),
 the Gauss-Newton HVP (Eq. 46), and blr_adjoint's body force and lambda^0 must be
 identical, for odd and even numbers of steps (an odd count ends with one
 single step) and for ragged tiles."""
@@ -39,7 +41,7 @@ def _run(plan, vt, dv, n, band, lambda0):
 
 @pytest.mark.parametrize("name", sorted(CASES))
 @pytest.mark.parametrize("precision", ["fp32", "mixed"])
-def test_two_step_adjoint_equals_one_step(name, precision):
+def test_adjoint_forms_are_bit_identical(name, precision):
     from paper_1807_05117_gb300 import blr
     c = CASES[name]
     n, band, nt = c["n"], c["band"], c["nt"]
@@ -52,19 +54,20 @@ def test_two_step_adjoint_equals_one_step(name, precision):
     plan.set_images(dev(I0f), dev(I1f))
     assert plan.tuning()["grad_kept"] == 1
     out = {}
-    for adj2 in (0, 1, 2):
-        if adj2 and nt < 2:
+    for adj2, split in ((0, 0), (1, 0), (2, 0), (0, 1)):
+        if (adj2 or split) and nt < 2:
             continue
-        plan.set_tuning(adjoint_two_step=adj2)
-        assert plan.tuning()["adjoint_two_step"] == adj2
+        plan.set_tuning(adjoint_two_step=adj2, adjoint_split=split)
+        tun = plan.tuning()
+        assert (tun["adjoint_two_step"], tun["adjoint_split"]) == (adj2, split)
         for lambda0 in (False, True):
-            out[(adj2, lambda0)] = _run(plan, dev(vtf), dev(dvf), n, band, lambda0)
+            out[(adj2, split, lambda0)] = _run(plan, dev(vtf), dev(dvf), n, band, lambda0)
     assert plan.status() == blr.BLR_OK
-    for (adj2, lambda0), res in out.items():
-        ref = out[(0, lambda0)]
+    for (adj2, split, lambda0), res in out.items():
+        ref = out[(0, 0, lambda0)]
         for a, r in zip(res, ref):
             if r is not None:
-                assert torch.equal(a, r), (adj2, lambda0)
+                assert torch.equal(a, r), (adj2, split, lambda0)
 
 
 def test_set_tuning_rejects_shapes_the_plan_cannot_run():
@@ -72,7 +75,7 @@ def test_set_tuning_rejects_shapes_the_plan_cannot_run():
     plan = blr.Plan((16, 16, 16), (4, 4, 4), 4, ckpt_every=2)   # checkpoints: no kept gradients
     assert plan.tuning()["grad_kept"] == 0
     for bad in (dict(adjoint_two_step=1), dict(incremental_form=2), dict(adjoint_reads_grad=1),
-                dict(march_chunk=0), dict(grad_kept=1)):
+                dict(march_chunk=0), dict(grad_kept=1), dict(adjoint_split=1)):
         with pytest.raises(blr.BlrError) as ei:
             plan.set_tuning(**bad)
         assert ei.value.code == blr.BLR_EINVAL
