@@ -69,8 +69,8 @@ ADJ_BYTES = lambda nt: ((36 + 44 + 48 * (nt - 2)) if nt > 1 else 32)
 # of csrc/sweeps.cu (the text above its host-side marker line) is the code the
 # capture was taken from: SHA-256 of that text.
 SWEEPS_HOST_MARKER = "// ==== host side: launch shapes, launchers, sweep orchestration, autotuner ===="
-ADJ_TRAFFIC = {"sweeps_device_sha256": "36f427b1b307c5be9ac1f990d63b1f4e494775dc8fe769fc8cdabefeab99143f",
-               "bytes": 95279616 + 2032896}
+ADJ_TRAFFIC = {"sweeps_device_sha256": "c561ef93da9b9b6ad56a04ac73561ad36c6ab5af3b32723f5071039374e49ddd",
+               "bytes": 94933760 + 2162688}
 
 
 def adjoint_traffic():

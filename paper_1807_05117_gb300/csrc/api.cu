@@ -167,8 +167,9 @@ size_t layout(blr_plan *P, char *base) {
     P->T2s = a.take<float>((size_t)P->B2 * P->N2);
     P->T3c = a.take<float>((size_t)P->B3 * P->N3);
     P->T3s = a.take<float>((size_t)P->B3 * P->N3);
-    P->T2e = P->T2p = P->W1t = nullptr;
+    P->T2e = P->T2p = P->W1t = P->T3e = nullptr;
     if (P->p.precision == BLR_FP32) {
+        P->T3e = a.take<float>((size_t)4 * P->B3 * P->N3);
         P->W1t = a.take<float>((size_t)2 * P->B1 * P->N1);
         P->T2e = a.take<float>((size_t)4 * P->B2 * P->N2);
         P->T2p = a.take<float>((size_t)4 * P->B2 * P->N2);

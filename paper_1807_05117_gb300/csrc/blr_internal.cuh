@@ -191,7 +191,8 @@ struct blr_plan {
     float *W1;          // [2*B1][N1]: row 2j = cos, row 2j+1 = -sin (2 pi k_j x / N1)
     float *T2c, *T2s;   // [B2][N2]
     float *W1t;         // FP32 project axis-1 stage: W1 transposed, [N1][2 B1] (or nullptr)
-    int gemm_tile[4];   // FP32 GEMM stages' register tile (0: modelled choice; dft_autotune)
+    int gemm_tile[5];   // FP32 GEMM stages' register tile (0: modelled choice; dft_autotune)
+    float *T3e;         // FP32 expand axis-3 stage's B operand [2 B3][2 N3] (or nullptr)
     float *T2e, *T2p;   // FP32 axis-2 stages as real GEMMs, A operand [k][m] (or nullptr):
                         // expand [2 B2][2 N2] = [[C, S], [-S, C]]^T-ordered, project [2 N2][2 B2]
     float *T3c, *T3s;   // [B3][N3]

@@ -69,6 +69,23 @@ __global__ void k_table_axis2(float *T2e, float *T2p, int N, int B) {
     T2p[(long long)(N + x) * M2p + B + j] = C;       // ki 1, mi 1
 }
 
+// The expand axis-3 stage's B operand T3e[(k3, ri')][(ri, x3)], entries C, S or
+// -S of the phase (k3 - B/2) x3.
+__global__ void k_table_axis3(float *T3e, int N, int B) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= B * N) return;
+    const int j = idx / N, x = idx - j * N;
+    double c, s;
+    phase_cs(j - B / 2, x, N, &c, &s);
+    const float C = (float)c, S = (float)s;
+    const long long ne = 2LL * N;
+    // expand: (vr + i vi)(C + i S): re = vr C - vi S, im = vr S + vi C
+    T3e[(2LL * j) * ne + x] = C;
+    T3e[(2LL * j) * ne + N + x] = S;
+    T3e[(2LL * j + 1) * ne + x] = -S;
+    T3e[(2LL * j + 1) * ne + N + x] = C;
+}
+
 // A(k) = (alpha omega(k) + gamma)^q, q = 2s, omega = sum_d 2(1 - cos(2 pi k_d / N_d)).
 __global__ void k_regulariser(float *A, int N1, int N2, int N3, int B1, int B2, int B3,
                               double alpha, double gamma, int q) {
@@ -151,16 +168,19 @@ k_expand_axis3(const float *__restrict__ vt, const float *__restrict__ T3c,
 size_t expand_axis3_smem(int B3) { return (size_t)(XR * B3 + B3 * XC) * sizeof(float2); }
 
 // ---------------------------------------------------------------------------
-// Stages B, B', C and C' are real GEMMs batched over z,
+// Stages A, B, B', C and C' are real GEMMs batched over z,
 //   C_z[m][n] = scale * sum_k A(m, k) B_z[k][n],   B_z = B + z strideB ([K][N]),
-// run by one FP32 kernel; only the A operand differs:
+// run by one FP32 kernel; the A operand and the output mapping differ:
 //   AK_KM  A(m, k) = A[k lda + m]    stage C  (A = W1 [2B1][N1]: m = x1, k = (k1, re|im))
 //   AK_MK  A(m, k) = A[m lda + k]    stage C' (A = W1: m = (k1, re|im), k = x1)
 //   AK_E2  stage B  on a planar slab [re|im][k2][x3] -> [re|im][x2][x3]:
 //          m = (re|im, x2), k = (re|im, k2), A = [[C, -S], [S, C]]  (C + i S)(re + i im)
 //   AK_P2  stage B' on a planar slab [re|im][x2][x3] -> [re|im][k2][x3]:
 //          m = (re|im, k2), k = (re|im, x2), A = [[C, S], [-S, C]]  (C - i S)(re + i im)
-// with C = T2c[k2][x2], S = T2s[k2][x2].  Tiles of (16 TM) x (16 TN) outputs,
+// with C = T2c[k2][x2], S = T2s[k2][x2].  Stage A takes AK_MK (A = v~ as
+// [(c, k1, k2)][(k3, re|im)], B = T3e [(k3, re|im)][(re|im, x3)]) and writes
+// its rows to the planar layout (EPI 1).  Row-major A operands (AK_MK) are
+// fetched k-fastest, the others m-fastest, so that every fetch is coalesced.  Tiles of (16 TM) x (16 TN) outputs,
 // 256 threads as 16 x 16, each thread a TM x TN register tile (rows tm*4 + i + 64 h,
 // columns tn*4 + j + 64 h'); k in chunks of 16 through two shared-memory buffers,
 // the next chunk's loads in flight (registers) during this chunk's products.  The
@@ -181,6 +201,7 @@ struct GemmArgs {
     long long N;
     float scale;
     int *status;
+    int pN3, pB2;             // planar rows (EPI 1): x3 extent, k2 rows per slab
 };
 
 template <int AK>
@@ -200,11 +221,12 @@ __device__ __forceinline__ float a_elem(const GemmArgs &p, int m, int k) {
 
 constexpr int GK = 16;   // k per chunk
 
-template <int AK, int MODE, int TM, int TN>
+template <int AK, int MODE, int TM, int TN, int EPI = 0>
 __global__ void __launch_bounds__(256, 2)
 k_sgemm(GemmArgs p) {
-    constexpr int BM = 16 * TM, BN = 16 * TN;
-    __shared__ __align__(16) float As[2][GK][BM];
+    constexpr int BM = 16 * TM, BN = 16 * TN, AP = BM + 4;   // padded A rows
+    constexpr bool KFAST = AK == AK_MK;
+    __shared__ __align__(16) float As[2][GK][AP];
     __shared__ __align__(16) float Bs[2][GK][BN];
     const int tid = threadIdx.x, tn = tid & 15, tm = tid >> 4;
     const int m0 = blockIdx.y * BM;
@@ -217,7 +239,8 @@ k_sgemm(GemmArgs p) {
 #pragma unroll
         for (int i = 0; i < TM; ++i) {
             const int e = tid + 256 * i;
-            ra[i] = a_elem<AK>(p, m0 + e % BM, k0 + e / BM);
+            const int mm = KFAST ? e / GK : e % BM, kk = KFAST ? e % GK : e / BM;
+            ra[i] = a_elem<AK>(p, m0 + mm, k0 + kk);
         }
 #pragma unroll
         for (int i = 0; i < TN / 4; ++i) {
@@ -242,7 +265,8 @@ k_sgemm(GemmArgs p) {
 #pragma unroll
         for (int i = 0; i < TM; ++i) {
             const int e = tid + 256 * i;
-            As[buf][e / BM][e % BM] = ra[i];
+            const int mm = KFAST ? e / GK : e % BM, kk = KFAST ? e % GK : e / BM;
+            As[buf][kk][mm] = ra[i];
         }
 #pragma unroll
         for (int i = 0; i < TN / 4; ++i) {
@@ -308,8 +332,27 @@ k_sgemm(GemmArgs p) {
                 }
                 v[j] = x;
             }
-            float *dst = Cz + (long long)m * p.N + n;
-            if (vec && n + 3 < p.N) {
+            float *dst;
+            bool vst = vec && n + 3 < p.N;
+            if (EPI == 1) {   // row m = (slab, k2), column n = (re|im, x3) of the planar layout
+                const int slab = m / p.pB2, k2 = m - slab * p.pB2;
+                const int ri = n >= p.pN3;
+                dst = Cz + ((long long)(slab * 2 + ri) * p.pB2 + k2) * p.pN3 + (n - ri * p.pN3);
+                vst = vst && (p.pN3 & 3) == 0;
+                if (!vst) {   // the four columns may straddle the re | im halves
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const long long nj = n + j;
+                        if (nj >= p.N) continue;
+                        const int rj = nj >= p.pN3;
+                        Cz[((long long)(slab * 2 + rj) * p.pB2 + k2) * p.pN3 + (nj - rj * p.pN3)] = v[j];
+                    }
+                    continue;
+                }
+            } else {
+                dst = Cz + (long long)m * p.N + n;
+            }
+            if (vst) {
                 *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], v[2], v[3]);
             } else {
 #pragma unroll
@@ -325,7 +368,7 @@ k_sgemm(GemmArgs p) {
 // blocks (or the smallest tile when even that does not).
 constexpr int SG_CANDS = 4;
 
-template <int AK, int MODE>
+template <int AK, int MODE, int EPI = 0>
 int launch_sgemm(const GemmArgs &p, int batch, int sms, cudaStream_t s, int forced = 0) {
     // modelled time: waves of resident blocks x a block's padded tile over the
     // register tile's relative FMA rate (smem operand traffic per FMA)
@@ -348,10 +391,10 @@ int launch_sgemm(const GemmArgs &p, int batch, int sms, cudaStream_t s, int forc
     const int TMc = tms[pick], TNc = tns[pick];
     const dim3 grid((unsigned)ceil_div_ll(p.N, 16LL * TNc), (unsigned)ceil_div_ll(p.M, 16LL * TMc),
                     (unsigned)batch);
-    if (TMc == 8 && TNc == 8) launch_pdl(k_sgemm<AK, MODE, 8, 8>, grid, dim3(256), 0, s, p);
-    else if (TMc == 8) launch_pdl(k_sgemm<AK, MODE, 8, 4>, grid, dim3(256), 0, s, p);
-    else if (TNc == 8) launch_pdl(k_sgemm<AK, MODE, 4, 8>, grid, dim3(256), 0, s, p);
-    else launch_pdl(k_sgemm<AK, MODE, 4, 4>, grid, dim3(256), 0, s, p);
+    if (TMc == 8 && TNc == 8) launch_pdl(k_sgemm<AK, MODE, 8, 8, EPI>, grid, dim3(256), 0, s, p);
+    else if (TMc == 8) launch_pdl(k_sgemm<AK, MODE, 8, 4, EPI>, grid, dim3(256), 0, s, p);
+    else if (TNc == 8) launch_pdl(k_sgemm<AK, MODE, 4, 8, EPI>, grid, dim3(256), 0, s, p);
+    else launch_pdl(k_sgemm<AK, MODE, 4, 4, EPI>, grid, dim3(256), 0, s, p);
     BLR_CK_LAUNCH();
     return BLR_OK;
 }
@@ -365,9 +408,10 @@ int device_sms(const blr_plan *P) {
     return sms;
 }
 
-// The four GEMM stages of the FP32 transforms: 0 B (expand, axis 2), 1 C (expand,
-// axis 1), 2 C' (project, axis 1), 3 B' (project, axis 2).  `in` / `out` are the
-// stage's B operand and result; mode 1 (stage C only) stores the displacement.
+// The GEMM stages of the FP32 transforms: 0 B (expand, axis 2), 1 C (expand,
+// axis 1), 2 C' (project, axis 1), 3 B' (project, axis 2), 4 A (expand, axis 3).
+// `in` / `out` are the stage's data operand and result; mode 1 (stage C only)
+// stores the displacement.
 int launch_stage(const blr_plan *P, int stage, const float *in, float *out, float scale, int mode,
                  cudaStream_t s) {
     const long long ncol = (long long)P->N2 * P->N3;
@@ -412,6 +456,17 @@ int launch_stage(const blr_plan *P, int stage, const float *in, float *out, floa
             g.N = ncol;
             return P->W1t ? launch_sgemm<AK_KM, 0>(g, 3, sms, s, forced)
                           : launch_sgemm<AK_MK, 0>(g, 3, sms, s, forced);
+        case 4:
+            g.A = in;
+            g.lda = 2 * P->B3;
+            g.B = P->T3e;
+            g.strideB = 0;
+            g.pN3 = P->N3;
+            g.pB2 = P->B2;
+            g.M = 3 * P->B1 * P->B2;
+            g.K = 2 * P->B3;
+            g.N = 2LL * P->N3;
+            return launch_sgemm<AK_MK, 0, 1>(g, 1, sms, s, forced);
         default:
             g.A = P->T2p;
             g.lda = 2 * P->B2;
@@ -518,6 +573,11 @@ int dft_init_tables(blr_plan *P, cudaStream_t s) {
     BLR_CK_LAUNCH();
     k_table_kx<<<(int)ceil_div_ll((long long)P->B3 * P->N3, T), T, 0, s>>>(P->T3c, P->T3s, P->N3, P->B3);
     BLR_CK_LAUNCH();
+    if (P->T3e) {
+        k_table_axis3<<<(int)ceil_div_ll((long long)P->B3 * P->N3, T), T, 0, s>>>(P->T3e, P->N3,
+                                                                                 P->B3);
+        BLR_CK_LAUNCH();
+    }
     if (P->T2e && P->T2p) {
         k_table_axis2<<<(int)ceil_div_ll((long long)P->B2 * P->N2, T), T, 0, s>>>(P->T2e, P->T2p,
                                                                                  P->N2, P->B2);
@@ -538,12 +598,17 @@ int dft_expand(blr_plan *P, const float *vt, float *out, int mode, cudaStream_t 
     }
     const int rows = 3 * P->B1 * P->B2;
     // stage A
-    dim3 ga((unsigned)ceil_div_ll(rows, XR), (unsigned)ceil_div_ll(P->N3, XC));
-    const size_t sa = expand_axis3_smem(P->B3);
-    BLR_CK(cudaFuncSetAttribute(k_expand_axis3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa));
-    launch_pdl(k_expand_axis3, ga, dim3(256), sa, s, vt, (const float *)P->T3c,
-               (const float *)P->T3s, P->dft_small, rows, P->B2, P->B3, P->N3);
-    BLR_CK_LAUNCH();
+    if (P->T3e) {
+        int rc = launch_stage(P, 4, vt, P->dft_small, 1.f, 0, s);
+        if (rc) return rc;
+    } else {
+        dim3 ga((unsigned)ceil_div_ll(rows, XR), (unsigned)ceil_div_ll(P->N3, XC));
+        const size_t sa = expand_axis3_smem(P->B3);
+        BLR_CK(cudaFuncSetAttribute(k_expand_axis3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa));
+        launch_pdl(k_expand_axis3, ga, dim3(256), sa, s, vt, (const float *)P->T3c,
+                   (const float *)P->T3s, P->dft_small, rows, P->B2, P->B3, P->N3);
+        BLR_CK_LAUNCH();
+    }
     // stage B
     if (P->tc_tab2_expand) {
         int rc = tc_axis2(P, 0, P->dft_small, P->dft_big, s);
@@ -597,15 +662,15 @@ int dft_project(blr_plan *P, const float *f, float *ft, const float *vadd, cudaS
 // Tile shapes of the FP32 GEMM stages, chosen by timing each candidate on the
 // plan's own buffers (at creation, while they hold nothing).
 int dft_autotune(blr_plan *P, cudaStream_t s) {
-    for (int st = 0; st < 4; ++st) P->gemm_tile[st] = 0;
-    if (!P->T2e || !P->T2p || !P->W1t) return BLR_OK;   // FP32 plans only
+    for (int st = 0; st < 5; ++st) P->gemm_tile[st] = 0;
+    if (!P->T2e || !P->T2p || !P->W1t || !P->T3e) return BLR_OK;   // FP32 plans only
     cudaEvent_t e0, e1;
     BLR_CK(cudaEventCreate(&e0));
     BLR_CK(cudaEventCreate(&e1));
-    const float *ins[4] = {P->dft_small, P->dft_big, P->dv, P->dft_big};
-    float *outs[4] = {P->dft_big, P->dv, P->dft_big, P->dft_small};
+    const float *ins[5] = {P->dft_small, P->dft_big, P->dv, P->dft_big, P->vt};
+    float *outs[5] = {P->dft_big, P->dv, P->dft_big, P->dft_small, P->dft_small};
     int rc = BLR_OK;
-    for (int st = 0; st < 4 && !rc; ++st) {
+    for (int st = 0; st < 5 && !rc; ++st) {
         float best = 1e30f;
         int pick = 0;
         for (int c = 1; c <= SG_CANDS && !rc; ++c) {
