@@ -154,9 +154,15 @@ size_t layout(blr_plan *P, char *base) {
     } else {
         P->U = P->rho_nt = P->rho[0] = P->rho[1] = P->du[0] = P->du[1] = P->Gw = nullptr;
     }
-    P->Gm = P->use_gm ? a.take<float>((size_t)3 * P->p.nt * V) : nullptr;
-    P->lam_keep = (P->use_gm && P->nvel == 1 && P->p.nt > 1 && P->p.hessian != BLR_NEWTON)
+    // kept state gradients: [nt][3][V] (image), [nt][3 components][3][V] (deformation)
+    const size_t gm_fields = P->p.state_equation == BLR_STATE_DEFORMATION ? 9 : 3;
+    P->Gm = P->use_gm ? a.take<float>(gm_fields * P->p.nt * V) : nullptr;
+    P->lam_keep = (P->use_gm && P->nvel == 1 && P->p.nt > 1 && P->p.hessian != BLR_NEWTON &&
+                   P->p.state_equation == BLR_STATE_IMAGE)
                       ? a.take<float>((size_t)(P->p.nt - 1) * V)
+                      : nullptr;
+    P->rho_keep = (P->use_gm && P->p.nt > 1 && P->p.state_equation == BLR_STATE_DEFORMATION)
+                      ? a.take<float>((size_t)3 * (P->p.nt - 1) * V)
                       : nullptr;
     P->b = a.take<float>(3 * V);
     P->dv = a.take<float>(3 * V);
@@ -429,7 +435,8 @@ int plan_create(const blr_params *p, bool grad_cache, blr_plan **out) {
         return BLR_EINVAL;
     }
     P->use_gm = grad_cache && P->sweep_wide && P->ck == p->nt &&
-                p->state_equation == BLR_STATE_IMAGE;
+                (p->state_equation == BLR_STATE_IMAGE ||
+                 (p->hessian == BLR_GAUSS_NEWTON && !p->nonstationary));
     // L2 persistence for the displacement copy d4 (the autotuner decides whether the
     // sweeps use it): the window covers one step's d4, and the context's
     // persisting set-aside is raised to hold it when the device allows
@@ -519,7 +526,8 @@ int blr_plan_set_tuning(blr_plan_t P, const int *vals, int n) {
     if ((l2 != 0 && l2 != 1) || (l2 && !P->l2_win_bytes)) return BLR_EINVAL;
     if (adj2 < 0 || adj2 > 2 || (adj2 && (!gm || !P->d4 || P->nvel != 1))) return BLR_EINVAL;
     const int split = n >= 12 ? vals[11] : P->adj_split;
-    if ((split != 0 && split != 1) || (split && (!P->lam_keep || !P->d4 || adj2))) return BLR_EINVAL;
+    if ((split != 0 && split != 1) || (split && ((!P->lam_keep && !P->rho_keep) || !P->d4 || adj2)))
+        return BLR_EINVAL;
     if (cudaDeviceSynchronize() != cudaSuccess) return BLR_ECUDA;
     P->bal_adj = bal_adj;
     P->adj_useg = useg;

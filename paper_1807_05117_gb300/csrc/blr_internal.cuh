@@ -150,6 +150,7 @@ struct blr_plan {
     int adj_split;      // adjoint solve as transport steps + one body-force pass (sweep_autotune)
     int bal_tr;         // blocks per SM of the transport-only grid (0: ADJ_BLOCKS)
     float *lam_keep;    // lambda^1 .. lambda^{nt-1} of the split adjoint solve, or nullptr
+    float *rho_keep;    // rho^1 .. rho^{nt-1} ([3][V] each) of the deformation variant's split solve
     int adj2;           // two adjoint steps per launch on a balanced grid of adj2 blocks
                         // per SM (plans that keep Gm), or 0: one step per launch
                         //                                                      (sweep_autotune)
@@ -313,6 +314,7 @@ int sweep_chunk(const blr_plan *P, int kind);
 int sweep_blocks_per_sm(int kind, bool wide = false);
 void sweep_set_chunk(blr_plan *P, int kind, int chunk);
 float *grad_slot(const blr_plan *P, int n);   // kept grad m^n, or nullptr
+float *def_grad_slot(const blr_plan *P, int n, int c);   // kept grad u^n_c, or nullptr
 int sweep_autotune(blr_plan *P, cudaStream_t s);
 int sweep_pack_d4(blr_plan *P, cudaStream_t s);               // d4 from d (when P->d4)
 

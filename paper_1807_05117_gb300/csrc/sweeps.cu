@@ -836,14 +836,146 @@ k_adjoint_wide(const float *__restrict__ lam_in, const float *__restrict__ m_n,
     });
 }
 
-// The adjoint transport alone, lambda^n = S^T lambda^{n+1} (wide-copy tiles).
+// The adjoint transport alone, lambda^n_f = S^T lambda^{n+1}_f, for NF fields at
+// stride V that share the displacement (NF = 3: the deformation variant's
+// components): the d4 ring and each source position's hat weights serve all the
+// fields.  The gather of each field is that of adjoint_tile_w (same operations,
+// same order), so the results equal its transport bit for bit.
+template <int NF>
+__device__ __forceinline__ void
+transport_tile(const float *__restrict__ lam_in, const float4 *__restrict__ d4,
+               float *__restrict__ lam_out, const Grid3 g, int CH, int k0, int j0, int i0) {
+    extern __shared__ __align__(16) unsigned char blr_dyn_smem[];
+    float4 *const RQ = reinterpret_cast<float4 *>(blr_dyn_smem);
+    float *const RL = reinterpret_cast<float *>(blr_dyn_smem + BQ * BPL * 16);   // [NF][BQ][BPL]
+    constexpr int NLC = (NF * ASC + MT - 1) / MT;   // lambda copies per thread
+    const int i_end = min(i0 + CH, g.N1);
+    const long long plane = (long long)g.N2 * g.N3;
+    const long long V = g.V;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int k = k0 + lane;
+    const int jb = j0 + ARJ * w;
+    const bool kin = k < g.N3;
+    const int hk = BHK + lane;
+    int offq[AQC];
+#pragma unroll
+    for (int i = 0; i < AQC; ++i) {
+        const int c = tid + MT * i;
+        offq[i] = c < BPL ? win_off(g, j0, k0, c / BW, c % BW) : 0;
+    }
+    // lambda copy u of this thread: field e / ASC, 16-byte group e % ASC
+    long long offl[NLC];
+    uint32_t dstl[NLC];
+    bool okl[NLC];
+#pragma unroll
+    for (int u = 0; u < NLC; ++u) {
+        const int e = tid + MT * u;
+        okl[u] = e < NF * ASC;
+        const int f = okl[u] ? e / ASC : 0, gi = okl[u] ? e % ASC : 0;
+        offl[u] = (long long)f * V + win_off(g, j0, k0, gi / BG, 4 * (gi % BG));
+        dstl[u] = smem_u32(RL) + (uint32_t)(f * BQ * BPL * 4) + (uint32_t)gi * 16u;
+    }
+    const uint32_t q0s = smem_u32(RQ) + (uint32_t)tid * 16u;
+    auto issue = [&](int sp, int r) {   // plane sp into ring position r (one commit group)
+        if (sp <= i_end) {
+            const long long pb = (long long)wrap1(sp, g.N1) * plane;
+            const uint32_t qs = q0s + (uint32_t)(r & (BQ - 1)) * (BPL * 16);
+#pragma unroll
+            for (int i = 0; i < AQC; ++i)
+                if (tid + MT * i < BPL) cp16(qs + (uint32_t)(MT * i) * 16u, d4 + pb + offq[i]);
+#pragma unroll
+            for (int u = 0; u < NLC; ++u)
+                if (okl[u]) cp16(dstl[u] + (uint32_t)(r & (BQ - 1)) * (BPL * 4), lam_in + pb + offl[u]);
+        }
+        cp_commit();
+    };
+    issue(i0 - 1, 0);
+    issue(i0, 1);
+    float2 accA[NF], accB[NF], accC[NF];   // rows (jb, jb + 1) of output planes s - 1, s, s + 1
+#pragma unroll
+    for (int f = 0; f < NF; ++f) accA[f] = accB[f] = accC[f] = make_float2(0.f, 0.f);
+    for (int s = i0 - 1; s <= i_end; ++s) {
+        const int r = s - i0 + 1;
+        cp_wait1();
+        __syncthreads();
+        issue(s + 2, r + 2);
+        if (kin) {
+            const int o = s - 1;
+            const float4 *Q = RQ + (r & (BQ - 1)) * BPL;
+#pragma unroll
+            for (int sr = 0; sr < ARJ + 2; ++sr) {        // source halo row ARJ w + sr
+#pragma unroll
+                for (int dk = -1; dk <= 1; ++dk) {
+                    const int pos = (ARJ * w + sr) * BW + hk + dk;
+                    const float4 q = Q[pos];
+                    const float hz = hat_e(-dk, q.z);
+                    const float xa = fmaxf(-q.x, 0.f), xb = 1.f - fabsf(q.x), xc = fmaxf(q.x, 0.f);
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        const float wl = RL[(f * BQ + (r & (BQ - 1))) * BPL + pos] * hz;
+                        // target rows jb (source row offset sr - 1) and jb + 1 (sr - 2)
+                        if (sr == 0) {
+                            const float wt = wl * hat_e(1, q.y);
+                            accA[f].x = fmaf(wt, xa, accA[f].x);
+                            accB[f].x = fmaf(wt, xb, accB[f].x);
+                            accC[f].x = fmaf(wt, xc, accC[f].x);
+                        } else if (sr == ARJ + 1) {
+                            const float wt = wl * hat_e(-1, q.y);
+                            accA[f].y = fmaf(wt, xa, accA[f].y);
+                            accB[f].y = fmaf(wt, xb, accB[f].y);
+                            accC[f].y = fmaf(wt, xc, accC[f].y);
+                        } else {
+                            const float2 wt = __fmul2_rn(make_float2(wl, wl),
+                                                         make_float2(hat_e(1 - sr, q.y),
+                                                                     hat_e(2 - sr, q.y)));
+                            accA[f] = __ffma2_rn(wt, make_float2(xa, xa), accA[f]);
+                            accB[f] = __ffma2_rn(wt, make_float2(xb, xb), accB[f]);
+                            accC[f] = __ffma2_rn(wt, make_float2(xc, xc), accC[f]);
+                        }
+                    }
+                }
+            }
+            // lambda^n of plane s - 1 is complete once plane s has been scattered
+            if (o >= i0) {
+#pragma unroll
+                for (int f = 0; f < NF; ++f)
+#pragma unroll
+                    for (int jj = 0; jj < ARJ; ++jj) {
+                        const int j = jb + jj;
+                        if (j < g.N2)
+                            lam_out[(long long)f * V + (long long)o * plane + (long long)j * g.N3 + k] =
+                                jj == 0 ? accA[f].x : accA[f].y;
+                    }
+            }
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            accA[f] = accB[f];
+            accB[f] = accC[f];
+            accC[f] = make_float2(0.f, 0.f);
+        }
+    }
+}
+
+constexpr int TR1_SMEM = BQ * BPL * 16 + BQ * BPL * 4;
+constexpr int TR3_SMEM = BQ * BPL * 16 + 3 * BQ * BPL * 4;
+constexpr int TR3_BLOCKS = 2;   // resident blocks per SM (shared memory)
+
 __global__ void __launch_bounds__(MT, ADJ_BLOCKS)
 k_adjoint_transport(const float *__restrict__ lam_in, const float4 *__restrict__ d4,
                     float *__restrict__ lam_out, Grid3 g, int ntk, long long W) {
     pdl_wait();
     for_segments(g.N1, ntk, W, [&](int kt, int jt, int i0, int len) {
-        adjoint_tile_w<false, true, true, false>(lam_in, nullptr, d4, lam_out, nullptr, 0.f, g, len,
-                                                 kt * MK, jt * AJ, i0, nullptr);
+        transport_tile<1>(lam_in, d4, lam_out, g, len, kt * MK, jt * AJ, i0);
+    });
+}
+
+__global__ void __launch_bounds__(MT, TR3_BLOCKS)
+k_adjoint_transport3(const float *__restrict__ lam_in, const float4 *__restrict__ d4,
+                     float *__restrict__ lam_out, Grid3 g, int ntk, long long W) {
+    pdl_wait();
+    for_segments(g.N1, ntk, W, [&](int kt, int jt, int i0, int len) {
+        transport_tile<3>(lam_in, d4, lam_out, g, len, kt * MK, jt * AJ, i0);
     });
 }
 
@@ -897,6 +1029,41 @@ k_body_force(const float *__restrict__ lam_final, const float *__restrict__ lam_
             else
                 b[a * V + x] = acc[a][0];
         }
+    }
+}
+
+// The deformation variant's body force from its kept adjoint states: for
+// n = nt-1 .. 0, b += dt rho^{n+1}_c grad u^n_c(x + d) for c = 0, 1, 2 and then
+// b_a += dt rho^{n+1}_a, with the operations and order of the per-step kernels
+// and k_field_axpy (bit-identical).  rho^nt is rho_final ([3][V]), rho^k is
+// rho_keep[k - 1]; Gm[n][c] holds grad u^n_c.
+__global__ void __launch_bounds__(256)
+k_body_force_def(const float *__restrict__ rho_final, const float *__restrict__ rho_keep,
+                 const float *__restrict__ Gm, float *__restrict__ b, float dt, int nt, long long V) {
+    pdl_wait();
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < V;
+         x += (long long)gridDim.x * blockDim.x) {
+        float acc[3] = {0.f, 0.f, 0.f};
+        for (int n = nt - 1; n >= 0; --n) {
+            const float *rp = n == nt - 1 ? rho_final : rho_keep + (size_t)3 * n * V;
+            float rho[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) rho[c] = __ldg(rp + c * V + x);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float *G = Gm + ((size_t)3 * n + c) * 3 * V;
+                const float sl = dt * rho[c];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const float gv = __ldg(G + a * V + x);
+                    acc[a] = (n == nt - 1 && c == 0) ? sl * gv : fmaf(sl, gv, acc[a]);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc[a] = fmaf(dt, rho[a], acc[a]);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) b[a * V + x] = acc[a];
     }
 }
 
@@ -1070,6 +1237,62 @@ k_incstate_gather(const float *__restrict__ dm_in, const float4 *__restrict__ d4
     }
     out = fmaf(-dt, gdv, out);
     dm_out[idx] = LAST ? lam_scale * out : out;
+}
+
+// The deformation variant's incremental step for all three components at once,
+//   du^{n+1}_c = S du^n_c - dt grad u^n_c(x + d) . dv - dt dv_c,
+// with the operations of k_incstate_gather (per component) followed by the
+// - dt dv_c of k_field_axpy: bit-identical to those launches, with d4, dv and the
+// cell weights read once.  du is [3][V]; Gn is grad u^n_c for c = 0..2, [3][3][V].
+template <bool FIRST>
+__global__ void __launch_bounds__(MT)
+k_incstate_gather3(const float *__restrict__ du_in, const float4 *__restrict__ d4,
+                   const float *__restrict__ dv, const float *__restrict__ Gn,
+                   float *__restrict__ du_out, float dt, Grid3 g) {
+    pdl_wait();
+    const int k = blockIdx.x * MK + (threadIdx.x & 31);
+    const int j = blockIdx.y * MJ + (threadIdx.x >> 5);
+    const int i = blockIdx.z;
+    if (k >= g.N3 || j >= g.N2) return;
+    const long long plane = (long long)g.N2 * g.N3;
+    const long long idx = (long long)i * plane + (long long)j * g.N3 + k;
+    const float dv0 = __ldg(dv + idx), dv1 = __ldg(dv + g.V + idx), dv2 = __ldg(dv + 2 * g.V + idx);
+    AxisW a0{}, a1{}, a2{};
+    long long p0 = 0, p1 = 0, r0 = 0, r1 = 0;
+    int c0 = 0, c1 = 0;
+    if (!FIRST) {
+        const float4 q = __ldg(d4 + idx);
+        a0 = axis_weights(q.x);
+        a1 = axis_weights(q.y);
+        a2 = axis_weights(q.z);
+        p0 = (long long)wrap1(i + a0.lo, g.N1) * plane;
+        p1 = (long long)wrap1(i + a0.lo + 1, g.N1) * plane;
+        r0 = (long long)wrap1(j + a1.lo, g.N2) * g.N3;
+        r1 = (long long)wrap1(j + a1.lo + 1, g.N2) * g.N3;
+        c0 = wrap1(k + a2.lo, g.N3);
+        c1 = wrap1(k + a2.lo + 1, g.N3);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float *G = Gn + (long long)c * 3 * g.V;
+        const float gdv = fmaf(__ldg(G + idx), dv0,
+                               fmaf(__ldg(G + g.V + idx), dv1, __ldg(G + 2 * g.V + idx) * dv2));
+        float out = 0.f;
+        if (!FIRST) {
+            const float *f = du_in + (long long)c * g.V;
+            const float c000 = __ldg(f + p0 + r0 + c0), c001 = __ldg(f + p0 + r0 + c1);
+            const float c010 = __ldg(f + p0 + r1 + c0), c011 = __ldg(f + p0 + r1 + c1);
+            const float c100 = __ldg(f + p1 + r0 + c0), c101 = __ldg(f + p1 + r0 + c1);
+            const float c110 = __ldg(f + p1 + r1 + c0), c111 = __ldg(f + p1 + r1 + c1);
+            const float l00 = fmaf(a2.wl, c000, a2.wh * c001), l01 = fmaf(a2.wl, c010, a2.wh * c011);
+            const float l10 = fmaf(a2.wl, c100, a2.wh * c101), l11 = fmaf(a2.wl, c110, a2.wh * c111);
+            const float m0 = fmaf(a1.wl, l00, a1.wh * l01), m1 = fmaf(a1.wl, l10, a1.wh * l11);
+            out = fmaf(a0.wl, m0, a0.wh * m1);
+        }
+        out = fmaf(-dt, gdv, out);
+        const float dvc = c == 0 ? dv0 : (c == 1 ? dv1 : dv2);
+        du_out[(long long)c * g.V + idx] = fmaf(-dt, dvc, out);
+    }
 }
 
 // d4 = (d0, d1, d2, 0) per voxel from the planar displacement.
@@ -1394,7 +1617,8 @@ int adjoint_smem_attributes() {
     BLR_CK(cudaFuncSetAttribute(k_adjoint_bal<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
     BLR_CK(cudaFuncSetAttribute(k_adjoint_bal<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
     BLR_CK(cudaFuncSetAttribute(k_adjoint_bal<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM));
-    BLR_CK(cudaFuncSetAttribute(k_adjoint_transport, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM_G));
+    BLR_CK(cudaFuncSetAttribute(k_adjoint_transport, cudaFuncAttributeMaxDynamicSharedMemorySize, TR1_SMEM));
+    BLR_CK(cudaFuncSetAttribute(k_adjoint_transport3, cudaFuncAttributeMaxDynamicSharedMemorySize, TR3_SMEM));
     BLR_CK(cudaFuncSetAttribute(k_adjoint_wide<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM_G));
     BLR_CK(cudaFuncSetAttribute(k_adjoint_wide<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM));
     BLR_CK(cudaFuncSetAttribute(k_adjoint_wide<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJW_SMEM_G));
@@ -1492,6 +1716,11 @@ float *grad_slot(const blr_plan *P, int n) {
     return P->Gm ? P->Gm + (size_t)3 * n * P->V : nullptr;
 }
 
+// The deformation variant's grad u^n_c(x + d(x)) when kept, else nullptr.
+float *def_grad_slot(const blr_plan *P, int n, int c) {
+    return P->Gm ? P->Gm + ((size_t)3 * n + c) * 3 * P->V : nullptr;
+}
+
 namespace {
 
 // The displacement copy d4 is read by every step of the adjoint and incremental
@@ -1567,7 +1796,17 @@ void launch_transport(const blr_plan *P, const float *lin, float *lout, cudaStre
     const BalGeom g = bal_geom(P, P->bal_tr ? P->bal_tr : ADJ_BLOCKS, AJ);
     cudaAccessPolicyWindow w;
     const cudaAccessPolicyWindow *win = d4_window(P, &w);
-    launch_pdl_l2(win, k_adjoint_transport, dim3(g.G), dim3(MT), ADJW_SMEM_G, s, lin,
+    launch_pdl_l2(win, k_adjoint_transport, dim3(g.G), dim3(MT), TR1_SMEM, s, lin,
+                  (const float4 *)P->d4, lout, P->grid, g.ntk, g.W);
+}
+
+// The three fields at stride V at once (the deformation variant's components).
+void launch_transport3(const blr_plan *P, const float *lin, float *lout, cudaStream_t s) {
+    const int bps = P->bal_tr ? (P->bal_tr < TR3_BLOCKS ? P->bal_tr : TR3_BLOCKS) : TR3_BLOCKS;
+    const BalGeom g = bal_geom(P, bps, AJ);
+    cudaAccessPolicyWindow w;
+    const cudaAccessPolicyWindow *win = d4_window(P, &w);
+    launch_pdl_l2(win, k_adjoint_transport3, dim3(g.G), dim3(MT), TR3_SMEM, s, lin,
                   (const float4 *)P->d4, lout, P->grid, g.ntk, g.W);
 }
 
@@ -1582,6 +1821,13 @@ void launch_body_force(const blr_plan *P, const float *lam_final, float *b, cuda
     else
         launch_pdl(k_body_force<false>, dim3((unsigned)blocks), dim3(256), 0, s, lam_final,
                    (const float *)P->lam_keep, (const float *)P->Gm, b, P->dt, P->p.nt, P->V);
+}
+
+void launch_body_force_def(const blr_plan *P, const float *rho_final, float *b, cudaStream_t s) {
+    long long blocks = ceil_div_ll(P->V, 256);
+    if (blocks > 8LL * P->sms) blocks = 8LL * P->sms;
+    launch_pdl(k_body_force_def, dim3((unsigned)blocks), dim3(256), 0, s, rho_final,
+               (const float *)P->rho_keep, (const float *)P->Gm, b, P->dt, P->p.nt, P->V);
 }
 
 template <bool FIRST, bool LAST>
@@ -1816,9 +2062,9 @@ int sweep_state_def(blr_plan *P, cudaStream_t s) {
     const int nt = P->p.nt;
     const long long V3 = 3 * P->V;
     for (int n = 0; n < nt; ++n) {
-        for (int c = 0; c < 3; ++c) {   // S u^n_c
+        for (int c = 0; c < 3; ++c) {   // S u^n_c (and grad u^n_c(x + d) when kept)
             launch_state<false>(P, def_u(P, n, c), def_u(P, n + 1, c), nullptr, nullptr, 0.f,
-                                nullptr, nullptr, s);
+                                nullptr, def_grad_slot(P, n, c), s);
             BLR_CK_LAUNCH();
         }
         int rc = field_axpy(P, def_u(P, n + 1, 0), def_u(P, n + 1, 0), P->d, 1.f, V3, s);   // + d
@@ -1846,13 +2092,29 @@ int sweep_incremental_def(blr_plan *P, cudaStream_t s) {
             din = P->du[cur];
             dout = P->du[1 - cur];
         }
-        for (int c = 0; c < 3; ++c) {
-            launch_incstate(P, n == 0, false, din + c * P->V, def_u(P, n, c), dout + c * P->V, 1.f,
-                            nullptr, s);
+        if (P->Gm && P->d4 && P->inc_mode == 2) {   // the three components in one gather
+            cudaAccessPolicyWindow w;
+            const cudaAccessPolicyWindow *win = d4_window(P, &w);
+            const dim3 grid((unsigned)ceil_div_ll(P->N3, MK), (unsigned)ceil_div_ll(P->N2, MJ),
+                            (unsigned)P->N1);
+            if (n == 0)
+                launch_pdl_l2(win, k_incstate_gather3<true>, grid, dim3(MT), 0, s, din,
+                              (const float4 *)P->d4, (const float *)P->dv,
+                              (const float *)def_grad_slot(P, n, 0), dout, P->dt, P->grid);
+            else
+                launch_pdl_l2(win, k_incstate_gather3<false>, grid, dim3(MT), 0, s, din,
+                              (const float4 *)P->d4, (const float *)P->dv,
+                              (const float *)def_grad_slot(P, n, 0), dout, P->dt, P->grid);
             BLR_CK_LAUNCH();
+        } else {
+            for (int c = 0; c < 3; ++c) {
+                launch_incstate(P, n == 0, false, din + c * P->V, def_u(P, n, c), dout + c * P->V,
+                                1.f, def_grad_slot(P, n, c), s);
+                BLR_CK_LAUNCH();
+            }
+            int rc = field_axpy(P, dout, dout, P->dv, -P->dt, V3, s);
+            if (rc) return rc;
         }
-        int rc = field_axpy(P, dout, dout, P->dv, -P->dt, V3, s);
-        if (rc) return rc;
         cur = 1 - cur;
         last = dout;
     }
@@ -1867,6 +2129,19 @@ int sweep_adjoint_def(blr_plan *P, const float *rho_final, float *b, cudaStream_
     const int nt = P->p.nt;
     const long long V3 = 3 * P->V;
     const bool keep = P->rho_all && rho_final == P->rho_nt;
+    if (P->adj_split && !keep && P->rho_keep && P->Gm && P->d4) {
+        // transport steps of the three components into the kept states (rho^0 is
+        // not needed), then the body force of all steps in one pass
+        for (int n = nt - 1; n >= 1; --n) {
+            const float *rin = n == nt - 1 ? rho_final : P->rho_keep + (size_t)n * V3;
+            float *rout = P->rho_keep + (size_t)(n - 1) * V3;
+            launch_transport3(P, rin, rout, s);
+            BLR_CK_LAUNCH();
+        }
+        launch_body_force_def(P, rho_final, b, s);
+        BLR_CK_LAUNCH();
+        return BLR_OK;
+    }
     int cur = 0;
     for (int n = nt - 1; n >= 0; --n) {
         const float *rin;
@@ -1880,7 +2155,7 @@ int sweep_adjoint_def(blr_plan *P, const float *rho_final, float *b, cudaStream_
         }
         for (int c = 0; c < 3; ++c) {
             launch_adjoint(P, n == nt - 1 && c == 0, n > 0, rin + c * P->V, def_u(P, n, c),
-                           n > 0 ? rout + c * P->V : nullptr, b, nullptr, s);
+                           n > 0 ? rout + c * P->V : nullptr, b, def_grad_slot(P, n, c), s);
             BLR_CK_LAUNCH();
         }
         int rc = field_axpy(P, b, b, rin, P->dt, V3, s);
@@ -1995,6 +2270,8 @@ int time_step(blr_plan *P, int kind, cudaStream_t s) {
         launch_transport(P, P->lam[0], P->lam[1], s);
     else if (kind == 6)   // the body force of a whole solve
         launch_body_force(P, P->lam[0], P->b, s);
+    else if (kind == 7)   // three transports at once (lambda / b used as [3][V] scratch)
+        launch_transport3(P, P->b, P->dv, s);
     else
         launch_incstate(P, false, false, P->dm[0], P->m, P->dm[1], 1.f,
                         kind == 3 ? grad_slot(P, 0) : nullptr, s, kind == 3);
@@ -2119,6 +2396,23 @@ int sweep_autotune(blr_plan *P, cudaStream_t s) {
             P->bal_tr = best_b2;
             if (best_b2) P->adj_split = 1;
             else P->adj2 = save2;
+        }
+        // the deformation variant: three transports per step share one body-force
+        // pass that also absorbs the per-step b += dt rho, so the split form is
+        // taken; only its grid is tuned
+        if (P->rho_keep && P->Gm && !rc) {
+            float best_t = 1e30f;
+            for (int bps = 1; bps <= TR3_BLOCKS && !rc; ++bps) {
+                P->bal_tr = bps;
+                const float t = time_shape(7);
+                if (t < best_t) {
+                    best_t = t;
+                    best_b = bps;
+                }
+            }
+            P->bal_tr = best_b;
+            P->adj_split = 1;
+            P->adj2 = 0;
         }
     }
     if (!rc) tune_march(2);

@@ -121,6 +121,39 @@ def test_pcg_iterates_parity(case):
     assert rel(x.cpu().numpy(), x_ref) <= case["tol"]["grad"]
 
 
+def test_sweep_forms_are_bit_identical(case, blr):
+    """Kept state gradients grad u^n_c (read by the adjoint and incremental sweeps)
+    against interpolated ones, the gather and march incremental forms, and the
+    split adjoint solve (transport steps, then one body-force pass) against the
+    per-step one: gradient, Gauss-Newton HVP and blr_adjoint's body force equal
+    bit for bit."""
+    plan = case["plan"]
+    tun = plan.tuning()
+    assert tun["grad_kept"] == 1
+    splits = (0, 1) if plan.nt > 1 else (0,)
+    out = {}
+    try:
+        for split in splits:
+            for useg in (0, 1):
+                for inc in (0, 2):
+                    plan.set_tuning(adjoint_split=split, adjoint_reads_grad=useg,
+                                    incremental_form=inc, adjoint_two_step=0)
+                    g, h = _coef(case["band"]), _coef(case["band"])
+                    plan.gradient(_dev(case["vtf"]), g)
+                    plan.hessvec(_dev(case["dvf"]), h)
+                    b = torch.zeros((3,) + case["n"], dtype=torch.float32, device="cuda")
+                    plan.adjoint(b)
+                    out[(split, useg, inc)] = (g, h, b)
+    finally:
+        plan.set_tuning(**{k: tun[k] for k in ("adjoint_split", "adjoint_reads_grad",
+                                               "incremental_form", "adjoint_two_step")})
+    assert plan.status() == blr.BLR_OK
+    ref = out[(0, 0, 0)]
+    for key, res in out.items():
+        for a, r in zip(res, ref):
+            assert torch.equal(a, r), key
+
+
 def test_gradient_repeats_after_hessvec_and_adjoint_arguments(blr):
     n, band, nt = (24, 20, 36), (6, 4, 8), 4
     I0, I1, _ = synth.blob_pair(n, 241, max_disp=2.0)
