@@ -101,11 +101,12 @@ FzShape fz_shape(size_t fixed, size_t gbytes, int gcols, size_t tail, int gmax =
 }
 
 // expand: tables T2e (A of GEMM 2) and T3e (B of GEMM 3); per warpgroup the B
-// operand of GEMM 2, then the A operand of GEMM 3, then four epilogue transposes,
-// one after the other in the same bytes; D3 reuses the TMEM columns of D2.
-FzShape fx_shape(const FzGeom &g, int B2, int B3, int gmax = 0) {
+// operand of GEMM 2 (with the unit's P1 slab, or a 1/parts share of it, beside
+// it), then the A operand of GEMM 3, then four epilogue transposes, one after
+// the other in the same bytes; D3 reuses the TMEM columns of D2.
+FzShape fx_shape(const FzGeom &g, int B2, int B3, int gmax = 0, int parts = 1) {
     const size_t fixed = 1024 + 2 * tile_bytes(FZ_M, g.K2e) + 2 * tile_bytes(g.N3e, g.K3e);
-    size_t r = 2 * tile_bytes(g.N2e, g.K2e) + (size_t)B2 * B3 * 8;   // + the P1 slab
+    size_t r = 2 * tile_bytes(g.N2e, g.K2e) + (size_t)B2 * B3 * 8 / parts;   // + the P1 slab
     r = r > 2 * tile_bytes(FZ_M, g.K3e) ? r : 2 * tile_bytes(FZ_M, g.K3e);
     r = r > 4 * 4096 ? r : 4 * 4096;
     const int cols = pow2_cols(g.N2e > g.N3e ? g.N2e : g.N3e);
@@ -407,6 +408,7 @@ struct FxArgs {
     int mode;              // 0: store scale * v; 1: displacement (clamp, CFL / NaN flags)
     int *status;
     int probe;
+    int parts;             // the P1 slab is fetched in `parts` slices of B2 / parts j2 rows
 };
 
 // TMEM -> (scale, clamp) -> XOR-swizzled 32 x 32 transpose -> rows of 128 bytes.
@@ -457,8 +459,9 @@ k_fx(FxArgs p) {
     const uint32_t bar_tab = smem_u32(&bars[0]), bar_probe = smem_u32(&bars[1]);
     const uint32_t bar_mma = smem_u32(&bars[2 + g]), bar_ld = smem_u32(&bars[2 + FZ_G_MAX + g]);
     const int mt = blockIdx.x % p.MT;   // the grid is a multiple of MT: one x2 tile per CTA
-    const size_t p1_bytes = (size_t)p.B2 * p.B3 * 8;
-    const float2 *sP1 = reinterpret_cast<const float2 *>(buf + 2 * tbB);   // the unit's P1 slab
+    const int jn = p.B2 / p.parts;                       // j2 rows of a slab slice
+    const size_t p1_bytes = (size_t)jn * p.B3 * 8;
+    const float2 *sP1 = reinterpret_cast<const float2 *>(buf + 2 * tbB);   // the slab slice
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -514,42 +517,56 @@ k_fx(FxArgs p) {
     int flags = 0;
     for (int u = (int)(blockIdx.x / p.MT) * p.G + g; run && u < units; u += lanes) {
         const int c = u / p.N1, x1 = u - c * p.N1;
-        // the unit's P1 slab (contiguous, B2 B3 complex) by one bulk copy
-        if (gt == 0) {
-            mbar_expect_arrive(bar_ld, (uint32_t)p1_bytes);
-            bulk_g2s(smem_u32(sP1), p.P1 + ((long long)c * p.N1 + x1) * nb23, (uint32_t)p1_bytes, bar_ld);
-            s_ld[g] = 1 + (int)ld_phase;   // in flight, with the parity of its phase
-        }
-        bool ok = group_wait(g, gt, bar_ld, ld_phase, s_ok);
-        ld_phase ^= 1u;
-        if (!ok) {
-            if (gt == 0) s_fail = 1;
-            break;
-        }
-        if (gt == 0) s_ld[g] = 0;
-        const float2 *src = sP1;
-        // B operand of GEMM 2, [n = (re | im)(j3)][k = (C | S)(j2)]:
-        //   (C, re) P1re  (C, im) P1im  (S, re) -P1im  (S, im) P1re
-        {
+        // the unit's P1 slab (contiguous, B2 B3 complex) by bulk copies, one per
+        // slice of jn j2 rows; each slice's chunks of the GEMM 2 B operand are
+        // built before the next slice overwrites it
+        bool ok = true;
+        for (int part = 0; part < p.parts && ok; ++part) {
+            const int jlo = part * jn;
+            if (part > 0) {   // every thread has read the previous slice
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                group_sync(g);
+            }
+            if (gt == 0) {
+                mbar_expect_arrive(bar_ld, (uint32_t)p1_bytes);
+                bulk_g2s(smem_u32(sP1), p.P1 + ((long long)c * p.N1 + x1) * nb23 + (long long)jlo * p.B3,
+                         (uint32_t)p1_bytes, bar_ld);
+                s_ld[g] = 1 + (int)ld_phase;   // in flight, with the parity of its phase
+            }
+            ok = group_wait(g, gt, bar_ld, ld_phase, s_ok);
+            ld_phase ^= 1u;
+            if (!ok) break;
+            if (gt == 0) s_ld[g] = 0;
+            const float2 *src = sP1;
+            // B operand of GEMM 2, [n = (re | im)(j3)][k = (C | S)(j2)]:
+            //   (C, re) P1re  (C, im) P1im  (S, re) -P1im  (S, im) P1re
+            // (the chunks of this slice's j2 rows; the zero padding with the last)
             const int nkc = p.K2e >> 3;
             for (int it = gt; it < p.N2e * nkc; it += 128) {
                 const int n = it % p.N2e, kc = it / p.N2e;
+                const int k0 = kc * 8;
+                const int j2c = k0 < p.B2 ? k0 : (k0 < 2 * p.B2 ? k0 - p.B2 : -1);
+                if ((j2c < 0 ? p.parts - 1 : j2c / jn) != part) continue;
                 float x[8];
                 const bool im = n >= p.B3;
                 const int j3 = im ? n - p.B3 : n;
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
-                    const int k = kc * 8 + q;
+                    const int k = k0 + q;
                     float v = 0.f;
                     if (n < 2 * p.B3 && k < 2 * p.B2) {
                         const bool sp = k >= p.B2;
-                        const float2 w = src[(sp ? k - p.B2 : k) * p.B3 + j3];
+                        const float2 w = src[((sp ? k - p.B2 : k) - jlo) * p.B3 + j3];
                         v = sp ? (im ? w.x : -w.y) : (im ? w.y : w.x);
                     }
                     x[q] = v;
                 }
                 store_chunk(buf, tbB, swz_chunk(n, kc, p.N2e), x);
             }
+        }
+        if (!ok) {
+            if (gt == 0) s_fail = 1;
+            break;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");
@@ -857,6 +874,15 @@ k_fp(FpArgs p) {
                      "r"(p.tmem_cols));
 }
 
+// Slices of the expand's P1 slab: 1 when the whole slab fits beside one
+// warpgroup's operands, 2 (halves of j2, each a whole number of 8-column
+// chunks) when only half does, 0 when neither fits.
+int fx_parts(const FzGeom &g, int B2, int B3) {
+    if (fx_shape(g, B2, B3, 0, 1).G >= 1) return 1;
+    if (B2 % 16 == 0 && fx_shape(g, B2, B3, 0, 2).G >= 1) return 2;
+    return 0;
+}
+
 // CTAs per x2 tile when every SM holds one CTA, and the warpgroups that spreads
 // a tile's units over: units are (component, x1 plane), per x2 tile.
 int fz_ctas_per_tile(const blr_plan *P, int MT) {
@@ -886,7 +912,7 @@ extern std::atomic<int> g_tc_probe;   // dft_tc.cu (blr_test_expire_waits)
 bool fz_supported(const blr_plan *P) {
     const FzGeom g = fz_geometry(P);
     if (P->N3 > 256 || P->B2 > 128 || 2 * P->B3 > FZ_M) return false;
-    return fx_shape(g, P->B2, P->B3).G >= 1 && fp_shape(g).G >= 1;
+    return fx_parts(g, P->B2, P->B3) >= 1 && fp_shape(g).G >= 1;
 }
 
 size_t fz_table_bytes(const blr_plan *P, int kind) {
@@ -927,8 +953,10 @@ int fz_expand(blr_plan *P, const float *vt, float *out, float scale, int mode, c
                dim3(256), 0, s, reinterpret_cast<const float2 *>(vt), (const float *)P->W1, P1,
                P->N1, P->B1, nb23);
     BLR_CK_LAUNCH();
-    const FzShape sh = fx_shape(g, P->B2, P->B3, fz_gmax(P, g.MT));
+    const int parts = fx_parts(g, P->B2, P->B3);
+    const FzShape sh = fx_shape(g, P->B2, P->B3, fz_gmax(P, g.MT), parts);
     FxArgs a;
+    a.parts = parts;
     a.tab2 = P->fz_tab[0];
     a.tab3 = P->fz_tab[1];
     a.P1 = P1;

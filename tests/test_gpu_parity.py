@@ -81,6 +81,9 @@ CASES = {
     # more than 128 x2 rows: two x2 tiles in the fused tensor-core transforms, the
     # second one partly filled
     "twotile": dict(n=(6, 140, 20), band=(4, 6, 8), nt=3, seed=404, bound=7.0),
+    # x3 tables of 192 columns and band 48 x 48 in (x2, x3): the mixed expand
+    # fetches each band slab in two halves (the grid of the precision form)
+    "slabhalves": dict(n=(10, 52, 192), band=(4, 48, 48), nt=3, seed=505, bound=18.0),
 }
 
 
