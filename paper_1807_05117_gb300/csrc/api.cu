@@ -185,9 +185,14 @@ size_t layout(blr_plan *P, char *base) {
     P->dft_small = a.take<float>((size_t)3 * P->B1 * P->B2 * P->N3 * 2);
     for (int k = 0; k < 4; ++k) P->fz_tab[k] = nullptr;
     P->fz_buf = nullptr;
+    P->dv_all = P->b_all = nullptr;
     if (P->p.precision == BLR_MIXED && fz_supported(P)) {
         for (int k = 0; k < 4; ++k) P->fz_tab[k] = a.take<uint8_t>(fz_table_bytes(P, k));
         P->fz_buf = a.take<float>(fz_buffer_floats(P));
+        if (P->nvel > 1) {   // every step's velocity in one fused transform
+            P->dv_all = a.take<float>((size_t)3 * P->nvel * V);
+            P->b_all = a.take<float>((size_t)3 * P->nvel * V);
+        }
         P->tc_tab_expand = P->tc_tab_project = nullptr;
         P->tc_tab2_expand = P->tc_tab2_project = nullptr;
     } else if (P->p.precision == BLR_MIXED) {
@@ -249,9 +254,17 @@ int state_at(blr_plan *P, const float *vt, double *energy_out, cudaStream_t s) {
         BLR_CK(cudaMemcpyAsync(P->vt, vt, P->nfloat * sizeof(float), cudaMemcpyDefault, s));
     }
     P->have_lams = false;
-    for (int n = 0; n < P->nvel; ++n) {   // every step's displacement (one when stationary)
-        use_step(P, n);
-        if ((rc = dft_expand(P, P->vt + (size_t)n * P->nf1, P->d, 1, s))) return rc;
+    if (P->nvel > 1 && P->fz_tab[0]) {   // every step's displacement in one fused transform
+        if ((rc = fz_expand(P, P->vt, P->d_base, -P->dt, 1, s, 3 * P->nvel))) return rc;
+        for (int n = 0; n < P->nvel; ++n) {
+            use_step(P, n);
+            if ((rc = sweep_pack_d4(P, s))) return rc;
+        }
+    } else {
+        for (int n = 0; n < P->nvel; ++n) {   // every step's displacement (one when stationary)
+            use_step(P, n);
+            if ((rc = dft_expand(P, P->vt + (size_t)n * P->nf1, P->d, 1, s))) return rc;
+        }
     }
     if (P->p.state_equation == BLR_STATE_DEFORMATION) {
         if ((rc = sweep_state_def(P, s))) return rc;

@@ -151,6 +151,8 @@ struct blr_plan {
     int bal_tr;         // blocks per SM of the transport-only grid (0: ADJ_BLOCKS)
     float *lam_keep;    // lambda^1 .. lambda^{nt-1} of the split adjoint solve, or nullptr
     float *rho_keep;    // rho^1 .. rho^{nt-1} ([3][V] each) of the deformation variant's split solve
+    float *dv_all;      // non-stationary, fused transforms: every step's expanded direction [nt][3][V]
+    float *b_all;       // non-stationary, fused transforms: every step's body force [nt][3][V]
     int adj2;           // two adjoint steps per launch on a balanced grid of adj2 blocks
                         // per SM (plans that keep Gm), or 0: one step per launch
                         //                                                      (sweep_autotune)
@@ -281,9 +283,10 @@ bool fz_supported(const blr_plan *P);
 size_t fz_table_bytes(const blr_plan *P, int kind);
 size_t fz_buffer_floats(const blr_plan *P);
 int fz_init_tables(blr_plan *P, cudaStream_t s);
-int fz_expand(blr_plan *P, const float *vt, float *out, float scale, int mode, cudaStream_t s);
+int fz_expand(blr_plan *P, const float *vt, float *out, float scale, int mode, cudaStream_t s,
+              int nc = 3);
 int fz_project(blr_plan *P, const float *f, float *ft, const float *vadd, float areg,
-               cudaStream_t s);
+               cudaStream_t s, int nc = 3);
 
 // sweeps.cu
 int sweep_setup(blr_plan *P);

@@ -409,6 +409,8 @@ struct FxArgs {
     int *status;
     int probe;
     int parts;             // the P1 slab is fetched in `parts` slices of B2 / parts j2 rows
+    int NC;                // fields: 3 per velocity (the steps' velocities of a
+                           // non-stationary plan are transformed in one launch)
 };
 
 // TMEM -> (scale, clamp) -> XOR-swizzled 32 x 32 transpose -> rows of 128 bytes.
@@ -511,7 +513,7 @@ k_fx(FxArgs p) {
     const uint32_t idesc2 = umma_idesc(FZ_M, p.N2e), idesc3 = umma_idesc(FZ_M, p.N3e);
     const long long V = (long long)p.N1 * p.N2 * p.N3;
     const uint32_t tg = tmem + (uint32_t)(g * p.gcols);   // this warpgroup's columns
-    const int units = 3 * p.N1;                          // per x2 tile
+    const int units = p.NC * p.N1;                       // per x2 tile
     const int lanes = (int)(gridDim.x / p.MT) * p.G;
     uint32_t phase = 0, ld_phase = 0;
     int flags = 0;
@@ -671,6 +673,7 @@ struct FpArgs {
     int vec4;              // rows of f are 16-byte aligned (N3 % 4 == 0, aligned base)
     int *status;
     int probe;
+    int NC;                // fields (3 per velocity)
 };
 
 constexpr int FP_KC = 64;   // x3 per field chunk (one 128-byte swizzle atom)
@@ -740,7 +743,7 @@ k_fp(FpArgs p) {
     const long long V = (long long)p.N1 * p.N2 * p.N3;
     const int rows = min(FZ_M, p.N2 - mt * FZ_M);   // x2 rows of this CTA's tile
     const uint32_t tg = tmem + (uint32_t)(g * p.gcols);
-    const int units = 3 * p.N1;
+    const int units = p.NC * p.N1;
     const int lanes = (int)(gridDim.x / p.MT) * p.G;
     const int nchunk = p.K3p / FP_KC;
     const int ep = p.N2p + 1;
@@ -889,15 +892,15 @@ int fz_ctas_per_tile(const blr_plan *P, int MT) {
     const int sms = P->sms > 0 ? P->sms : 148;
     return sms / MT > 1 ? sms / MT : 1;
 }
-int fz_gmax(const blr_plan *P, int MT) {
-    const int per = fz_ctas_per_tile(P, MT), units = 3 * P->N1;
+int fz_gmax(const blr_plan *P, int MT, int nc) {
+    const int per = fz_ctas_per_tile(P, MT), units = nc * P->N1;
     return (units + per - 1) / per;
 }
 // Grid of a fused kernel: at most one CTA per SM, a multiple of MT, and no CTA
 // without units.
-int fz_grid(const blr_plan *P, int G, int MT) {
+int fz_grid(const blr_plan *P, int G, int MT, int nc) {
     int per = fz_ctas_per_tile(P, MT);
-    const int need = (3 * P->N1 + G - 1) / G;
+    const int need = (nc * P->N1 + G - 1) / G;
     if (per > need) per = need;
     return per * MT;
 }
@@ -928,7 +931,7 @@ size_t fz_table_bytes(const blr_plan *P, int kind) {
 // floats of the intermediate: P1 [3][N1][B2 B3] complex, or Q2 [3][N1][MT][B2 B3]
 size_t fz_buffer_floats(const blr_plan *P) {
     const FzGeom g = fz_geometry(P);
-    return (size_t)2 * 3 * P->N1 * g.MT * P->B2 * P->B3;
+    return (size_t)2 * 3 * P->nvel * P->N1 * g.MT * P->B2 * P->B3;
 }
 
 int fz_init_tables(blr_plan *P, cudaStream_t s) {
@@ -945,18 +948,20 @@ int fz_init_tables(blr_plan *P, cudaStream_t s) {
     return BLR_OK;
 }
 
-int fz_expand(blr_plan *P, const float *vt, float *out, float scale, int mode, cudaStream_t s) {
+int fz_expand(blr_plan *P, const float *vt, float *out, float scale, int mode, cudaStream_t s,
+              int nc) {
     const FzGeom g = fz_geometry(P);
     const int nb23 = P->B2 * P->B3;
     float2 *P1 = reinterpret_cast<float2 *>(P->fz_buf);
-    launch_pdl(k_ex1, dim3((unsigned)((nb23 + EX_TC - 1) / EX_TC), (unsigned)((P->N1 + EX_TX - 1) / EX_TX), 3u),
+    launch_pdl(k_ex1, dim3((unsigned)((nb23 + EX_TC - 1) / EX_TC), (unsigned)((P->N1 + EX_TX - 1) / EX_TX), (unsigned)nc),
                dim3(256), 0, s, reinterpret_cast<const float2 *>(vt), (const float *)P->W1, P1,
                P->N1, P->B1, nb23);
     BLR_CK_LAUNCH();
     const int parts = fx_parts(g, P->B2, P->B3);
-    const FzShape sh = fx_shape(g, P->B2, P->B3, fz_gmax(P, g.MT), parts);
+    const FzShape sh = fx_shape(g, P->B2, P->B3, fz_gmax(P, g.MT, nc), parts);
     FxArgs a;
     a.parts = parts;
+    a.NC = nc;
     a.tab2 = P->fz_tab[0];
     a.tab3 = P->fz_tab[1];
     a.P1 = P1;
@@ -980,18 +985,19 @@ int fz_expand(blr_plan *P, const float *vt, float *out, float scale, int mode, c
     a.status = P->dstatus;
     a.probe = g_tc_probe.load(std::memory_order_relaxed);
     BLR_CK(cudaFuncSetAttribute(k_fx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem));
-    launch_pdl(k_fx, dim3(fz_grid(P, sh.G, g.MT)), dim3(128 * sh.G), sh.smem, s, a);
+    launch_pdl(k_fx, dim3(fz_grid(P, sh.G, g.MT, nc)), dim3(128 * sh.G), sh.smem, s, a);
     BLR_CK_LAUNCH();
     return BLR_OK;
 }
 
 int fz_project(blr_plan *P, const float *f, float *ft, const float *vadd, float areg,
-               cudaStream_t s) {
+               cudaStream_t s, int nc) {
     const FzGeom g = fz_geometry(P);
     const int nb23 = P->B2 * P->B3;
     float2 *Q2 = reinterpret_cast<float2 *>(P->fz_buf);
-    const FzShape sh = fp_shape(g, fz_gmax(P, g.MT));
+    const FzShape sh = fp_shape(g, fz_gmax(P, g.MT, nc));
     FpArgs a;
+    a.NC = nc;
     a.tab3 = P->fz_tab[2];
     a.tab2 = P->fz_tab[3];
     a.f = f;
@@ -1013,9 +1019,9 @@ int fz_project(blr_plan *P, const float *f, float *ft, const float *vadd, float 
     a.status = P->dstatus;
     a.probe = g_tc_probe.load(std::memory_order_relaxed);
     BLR_CK(cudaFuncSetAttribute(k_fp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem));
-    launch_pdl(k_fp, dim3(fz_grid(P, sh.G, g.MT)), dim3(128 * sh.G), sh.smem, s, a);
+    launch_pdl(k_fp, dim3(fz_grid(P, sh.G, g.MT, nc)), dim3(128 * sh.G), sh.smem, s, a);
     BLR_CK_LAUNCH();
-    launch_pdl(k_p1, dim3((unsigned)((nb23 + P1_TC - 1) / P1_TC), (unsigned)((P->B1 + P1_TJ - 1) / P1_TJ), 3u),
+    launch_pdl(k_p1, dim3((unsigned)((nb23 + P1_TC - 1) / P1_TC), (unsigned)((P->B1 + P1_TJ - 1) / P1_TJ), (unsigned)nc),
                dim3(256), 0, s,
                (const float2 *)Q2, (const float *)P->W1, reinterpret_cast<float2 *>(ft),
                (const float *)P->A, reinterpret_cast<const float2 *>(vadd), areg, P->N1, P->B1,

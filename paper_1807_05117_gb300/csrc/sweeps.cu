@@ -2005,6 +2005,10 @@ int sweep_adjoint_steps(blr_plan *P, const float *lam_final, float *gout, const 
                         float *b_steps, float *lambda0, cudaStream_t s) {
     const int nt = P->p.nt;
     int cur = 0;
+    // with the fused transforms, every step's body force is kept and all of them
+    // are projected in one launch after the sweep
+    const bool batched = gout && vadd && !b_steps && P->b_all && P->fz_tab[0];
+    if (batched) b_steps = P->b_all;
     for (int j = P->nseg - 1; j >= 0; --j) {
         int rc = ensure_segment(P, j, s);
         if (rc) return rc;
@@ -2017,12 +2021,13 @@ int sweep_adjoint_steps(blr_plan *P, const float *lam_final, float *gout, const 
             use_step(P, n);
             launch_adjoint(P, true, wlam, lin, state_slot(P, n), lout, bn, grad_slot(P, n), s);
             BLR_CK_LAUNCH();
-            if (gout && (rc = dft_project(P, bn, gout + (size_t)n * P->nf1,
-                                          vadd + (size_t)n * P->nf1, s, P->dt)))
+            if (gout && !batched && (rc = dft_project(P, bn, gout + (size_t)n * P->nf1,
+                                                      vadd + (size_t)n * P->nf1, s, P->dt)))
                 return rc;
             cur = 1 - cur;
         }
     }
+    if (batched) return fz_project(P, P->b_all, gout, vadd, P->dt, s, 3 * nt);
     return BLR_OK;
 }
 
@@ -2031,6 +2036,18 @@ int sweep_incremental(blr_plan *P, cudaStream_t s, const float *dvt_steps) {
     const int nt = P->p.nt;
     const float lam_scale = (float)(-2.0 / (P->p.sigma * P->p.sigma));
     int cur = 0;
+    // with the fused transforms, every step's direction is expanded in one launch
+    // and the steps read their own slice (P->dv is pointed at it, then restored)
+    const bool batched = dvt_steps && P->dv_all && P->fz_tab[0];
+    if (batched) {
+        int rc = fz_expand(P, dvt_steps, P->dv_all, 1.f, 0, s, 3 * nt);
+        if (rc) return rc;
+    }
+    struct RestoreDv {
+        blr_plan *P;
+        float *dv;
+        ~RestoreDv() { P->dv = dv; }
+    } restore{P, P->dv};
     for (int j = 0; j < P->nseg; ++j) {
         int rc = ensure_segment(P, j, s);
         if (rc) return rc;
@@ -2042,7 +2059,8 @@ int sweep_incremental(blr_plan *P, cudaStream_t s, const float *dvt_steps) {
                 din = n > 0 ? P->dm_all + (size_t)(n - 1) * P->V : P->dm[0];
                 if (n < nt - 1) dout = P->dm_all + (size_t)n * P->V;
             }
-            if (dvt_steps && (rc = dft_expand(P, dvt_steps + (size_t)n * P->nf1, P->dv, 0, s)))
+            if (batched) P->dv = P->dv_all + (size_t)3 * n * P->V;
+            else if (dvt_steps && (rc = dft_expand(P, dvt_steps + (size_t)n * P->nf1, P->dv, 0, s)))
                 return rc;
             use_step(P, n);
             launch_incstate(P, n == 0, n == nt - 1, din, state_slot(P, n), dout, lam_scale,
