@@ -312,6 +312,13 @@ int capture_pcg(Batch *B) {
     for (int p = 0; p < B->npairs && !rc; ++p) {
         if (!B->solo[p] || B->solo_exec[p]) continue;
         blr_plan *P = B->plans[p];
+        // A member keeps every state (no checkpoints), so whenever the graph is
+        // replayed a forward solve has left the one segment valid.  Capture with
+        // that state, or the product would capture a recomputation of the segment
+        // (the segment flag of a plan that has not run yet) and repeat it on
+        // every replay.
+        const int seg_was = P->seg_valid;
+        if (P->nseg == 1) P->seg_valid = 0;
         rc = capture_graph(B, [&]() {
             int r = hessvec_here(P, P->pv, P->q, B->s);
             if (!r) r = vec_dot(P, P->pv, P->q, nullptr, P->dsc + SC_PQ, B->s);
@@ -319,6 +326,7 @@ int capture_pcg(Batch *B) {
             if (!r) r = pcg_direction(P, B->s);
             return r;
         }, &B->solo_exec[p], &B->solo_launches[p]);
+        P->seg_valid = seg_was;
     }
     return rc;
 }
