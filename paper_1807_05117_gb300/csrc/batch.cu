@@ -28,6 +28,7 @@
 namespace {
 
 constexpr int KINDS = 3;   // 0 state, 1 adjoint, 2 incremental state
+constexpr int SOLO_LANES = 3;   // side streams that run solo pairs concurrently
 
 struct Batch {
     int npairs = 0, nt = 0, device = 0, grid = 0;
@@ -168,6 +169,12 @@ int join(Batch *B) {
 
 cudaStream_t lane_of(Batch *B, int p) { return B->side[p % B->side.size()]; }
 
+// Lane of the k-th solo pair of a pass.
+cudaStream_t solo_lane(Batch *B, int k) {
+    const int n = (int)B->side.size() < SOLO_LANES ? (int)B->side.size() : SOLO_LANES;
+    return B->side[k % n];
+}
+
 int upload_active(Batch *B, const std::vector<int> &sel) {
     B->h_active.assign(sel.begin(), sel.end());
     BLR_CK(cudaMemcpyAsync(B->d_active, B->h_active.data(), B->npairs * sizeof(int),
@@ -205,10 +212,11 @@ int batch_state(Batch *B, const std::vector<int> &sel, const std::vector<const f
         P->have_state = true;
         P->seg_valid = 0;
     }
-    if ((rc = join(B))) return rc;
+    int k = 0;
     for (int p = 0; p < B->npairs; ++p)
-        if (sel[p] && B->solo[p] && (rc = state_at(B->plans[p], vt[p], nullptr, B->s))) return rc;
-    return BLR_OK;
+        if (sel[p] && B->solo[p] && (rc = state_at(B->plans[p], vt[p], nullptr, solo_lane(B, k++))))
+            return rc;
+    return join(B);
 }
 
 // Gradients of the selected pairs at their current points into g[p].
@@ -223,10 +231,11 @@ int batch_gradient_here(Batch *B, const std::vector<int> &sel, const std::vector
         blr_plan *P = B->plans[p];
         if ((rc = dft_project(P, P->b, g[p], P->vt, lane_of(B, p)))) return rc;
     }
-    if ((rc = join(B))) return rc;
+    int k = 0;
     for (int p = 0; p < B->npairs; ++p)
-        if (sel[p] && B->solo[p] && (rc = gradient_here(B->plans[p], g[p], B->s))) return rc;
-    return BLR_OK;
+        if (sel[p] && B->solo[p] && (rc = gradient_here(B->plans[p], g[p], solo_lane(B, k++))))
+            return rc;
+    return join(B);
 }
 
 // Gauss-Newton HVPs of all pairs (flags decide which queued pairs' sweeps run);
@@ -659,15 +668,21 @@ int blr_batch_newton(blr_batch_t b, float *const *vt, int max_newton, int max_pc
             if ((rc = upload_active(B, pcg_on))) return rc;
             bool queued = false;
             for (int p = 0; p < np; ++p) queued = queued || (pcg_on[p] && !B->solo[p]);
+            // the solo pairs' iterations on SOLO_LANES side lanes in turn, so that one
+            // pair's launch tails and transform stages overlap another's sweeps
+            if ((rc = fork(B))) return rc;
             if (queued) {
                 BLR_CK(cudaGraphLaunch(B->pcg_exec, B->s));
                 __atomic_fetch_add(&g_blr_launches, B->pcg_launches, __ATOMIC_RELAXED);
             }
+            int k = 0;
             for (int p = 0; p < np; ++p) {
                 if (!pcg_on[p] || !B->solo[p]) continue;
-                BLR_CK(cudaGraphLaunch(B->solo_exec[p], B->s));
+                cudaStream_t t = solo_lane(B, k++);
+                BLR_CK(cudaGraphLaunch(B->solo_exec[p], t));
                 __atomic_fetch_add(&g_blr_launches, B->solo_launches[p], __ATOMIC_RELAXED);
             }
+            if ((rc = join(B))) return rc;
             if ((rc = fetch_all(B, false))) return rc;
             for (int p = 0; p < np; ++p) {
                 if (!pcg_on[p]) continue;
