@@ -69,8 +69,8 @@ ADJ_BYTES = lambda nt: ((36 + 44 + 48 * (nt - 2)) if nt > 1 else 32)
 # of csrc/sweeps.cu (the text above its host-side marker line) is the code the
 # capture was taken from: SHA-256 of that text.
 SWEEPS_HOST_MARKER = "// ==== host side: launch shapes, launchers, sweep orchestration, autotuner ===="
-ADJ_TRAFFIC = {"sweeps_device_sha256": "c561ef93da9b9b6ad56a04ac73561ad36c6ab5af3b32723f5071039374e49ddd",
-               "bytes": 94933760 + 2162688}
+ADJ_TRAFFIC = {"sweeps_device_sha256": "d2746545fd226568d2cb0f97f583dc47f402a1e9ef153b27eb7a23a58984fc91",
+               "bytes": 94958848 + 2299648}
 
 
 def adjoint_traffic():
