@@ -905,9 +905,10 @@ def measure_differentiation_form(dev, flush, stream, reps=3):
     return out
 
 
-def probe(precision="fp32", hessian=0, tuning=None):
+def probe(precision="fp32", hessian=0, tuning=None, state_equation=0):
     """A few launches of every hot-path kernel at the benchmark size, for ncu
-    (hessian=1: the full Newton Hessian's kernels as well).  tuning: sweep shapes
+    (hessian=1: the full Newton Hessian's kernels as well; state_equation=1: the
+    deformation variant's kernels instead of the image variant's).  tuning: sweep shapes
     (a dict of Plan.tuning() keys) that replace the autotuner's choice, e.g. the
     choice of a run without the profiler, whose interception of every launch
     distorts the autotuner's timings."""
@@ -922,7 +923,8 @@ def probe(precision="fp32", hessian=0, tuning=None):
     dvt = synth.random_direction(BAND, SEED + 2)
     (a, _), (b, _), (c, _), (d, _) = synth.as_device_inputs(I0, I1, vt, dvt)
     prec = blr.BLR_MIXED if precision == "mixed" else blr.BLR_FP32
-    with blr.Plan(N, BAND, NT, precision=prec, hessian=hessian) as plan:
+    with blr.Plan(N, BAND, NT, precision=prec, hessian=hessian,
+                  state_equation=state_equation) as plan:
         plan.set_images(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev))
         if tuning:
             plan.set_tuning(**{k: v for k, v in tuning.items() if k not in ("wide_sweeps", "grad_kept")})
@@ -969,6 +971,8 @@ def main():
                     help="short run for profilers: one gradient, 3 HVPs, 2 adjoint solves")
     ap.add_argument("--probe-hessian", type=int, default=0, choices=[0, 1],
                     help="with --probe: 1 probes a full-Newton plan")
+    ap.add_argument("--probe-state-equation", type=int, default=0, choices=[0, 1],
+                    help="with --probe: 1 probes a deformation-state-equation plan")
     ap.add_argument("--probe-tuning", default=None,
                     help="with --probe: JSON of sweep shapes (Plan.tuning() keys) to use instead of "
                          "the autotuner's choice")
@@ -983,7 +987,8 @@ def main():
         return 0
     if args.probe:
         return probe(args.precision, args.probe_hessian,
-                     json.loads(args.probe_tuning) if args.probe_tuning else None)
+                     json.loads(args.probe_tuning) if args.probe_tuning else None,
+                     args.probe_state_equation)
     if args.impl == "reference":
         return main_reference(args)
     if args.workload == "uneven64":
