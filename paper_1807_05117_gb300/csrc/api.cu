@@ -136,11 +136,9 @@ size_t layout(blr_plan *P, char *base) {
             P->lam_nt = P->lam_all + (size_t)(nt - 1) * V;
             P->dm_all = nt > 1 ? a.take<float>((size_t)(nt - 1) * V) : nullptr;
         }
-        P->nt_kap = a.take<float>((size_t)8 * V);
-        P->nt_lob = a.take<uint8_t>(V);
+        P->nt_kap = a.take<float>((size_t)27 * V);
     } else {
         P->lam_all = P->dm_all = P->nt_kap = nullptr;
-        P->nt_lob = nullptr;
         P->lam_nt = a.take<float>(V);
     }
     if (def) {

@@ -180,9 +180,8 @@ struct blr_plan {
                         // last slot is rho_nt), else nullptr
     float *du_all;      // full Newton Hessian: [nt-1][3][V], slot k-1 = du^k of the last
                         // incremental state (k = 1..nt-1), else nullptr
-    float *nt_kap;      // full Newton Hessian: [8][V] corner weights of the variation of
-                        // S^T for the current direction (newton.cu), else nullptr
-    uint8_t *nt_lob;    // full Newton Hessian: [V] cell-start bits, else nullptr
+    float *nt_kap;      // full Newton Hessian: [27][V] stencil of the variation of S^T for
+                        // the current direction (newton.cu), else nullptr
     float *Gm;          // [nt][3][V] grad of the trilinear cell of m^n at x + d(x) (written by
                         // the state sweep, read by the adjoint and incremental sweeps), or
                         // nullptr (checkpointed plans and batch members compute it on the fly)

@@ -15,12 +15,15 @@
 //
 // The variation of S^T is a transpose whose weights, kappa_o(x) = sum_a dd_a(x)
 // d_a w_o(x) for the 8 corners o of the cell of x, do not change from step to
-// step: k_newton_prep computes them (and the cell offsets) once per product, and
-// each step gathers kappa_o(x) lambda^{n+1}(x) over the 27 neighbours x whose
-// cell can contain y (|d| < 1 voxel per step).  Every (x, o) pair is read by
-// exactly one y, in a fixed order, so the result is deterministic.  One thread
-// per voxel; the cell rule is the sweeps': on each axis the cell starts at -1
-// for d < 0 and at 0 otherwise.
+// step.  k_newton_prep scatters them once per product into a 27-point stencil
+// K_e(y) = kappa_o(x) for y = x + e the corner o of the cell of x (zero where y
+// is no corner of its neighbour's cell; every (y, e) is written by at most one
+// x, so the scatter needs no atomics), and each step applies
+// dlambda^n(y) += sum_e K_e(y) lambda^{n+1}(y - e) over the 27 offsets in a fixed
+// order: dense, coalesced loads instead of a dependent load per neighbour, and
+// the sum of the earlier per-neighbour gather (which skipped the zero terms) bit
+// for bit.  One thread per voxel; the cell rule is the sweeps': on each axis the
+// cell starts at -1 for d < 0 and at 0 otherwise.
 #include "blr_internal.cuh"
 
 namespace {
@@ -66,61 +69,66 @@ __device__ __forceinline__ void corners(const float *__restrict__ f, int i, int 
             for (int e = 0; e < 2; ++e) c[a][b][e] = __ldg(f + p[a] + r[b] + q[e]);
 }
 
-// Per voxel x: lob[x] = cell-start bits (bit 2 - a set when the cell of axis a
-// starts at -1) and kap[o][x] = sum_a dd_a d_a w_o for the 8 corners o = 4 o0 +
-// 2 o1 + o2 of its cell, dd = -dt dv.
+// Per voxel x and offset e: K[e][x + e] = kappa_o(x) = sum_a dd_a d_a w_o when
+// x + e is the corner o = 4 o0 + 2 o1 + o2 of the cell of x (e_a = lo_a + o_a,
+// periodic; dd = -dt dv), else 0.  K is [27][V], e indexed (e0 + 1) 9 + (e1 + 1) 3
+// + (e2 + 1); every entry is written exactly once (by x = y - e).
 __global__ void __launch_bounds__(256)
 k_newton_prep(const float *__restrict__ d, const float *__restrict__ dv, float dt,
-              uint8_t *__restrict__ lob, float *__restrict__ kap, long long V) {
+              float *__restrict__ K, Grid3 g) {
     pdl_wait();
+    const long long V = g.V, plane = (long long)g.N2 * g.N3;
     for (long long x = blockIdx.x * 256LL + threadIdx.x; x < V; x += (long long)gridDim.x * 256) {
         const Cell1 c[3] = {cell_of(__ldg(d + x)), cell_of(__ldg(d + V + x)),
                             cell_of(__ldg(d + 2 * V + x))};
         const float dd[3] = {-dt * __ldg(dv + x), -dt * __ldg(dv + V + x),
                              -dt * __ldg(dv + 2 * V + x)};
-        lob[x] = (uint8_t)(((c[0].lo & 1) << 2) | ((c[1].lo & 1) << 1) | (c[2].lo & 1));
+        const int i = (int)(x / plane), j = (int)((x - (long long)i * plane) / g.N3);
+        const int k = (int)(x - (long long)i * plane - (long long)j * g.N3);
 #pragma unroll
-        for (int o = 0; o < 8; ++o) {
-            const int o0 = (o >> 2) & 1, o1 = (o >> 1) & 1, o2 = o & 1;
-            const float u0 = o0 ? c[0].wh : c[0].wl, u1 = o1 ? c[1].wh : c[1].wl,
-                        u2 = o2 ? c[2].wh : c[2].wl;
-            const float s0 = o0 ? dd[0] : -dd[0], s1 = o1 ? dd[1] : -dd[1],
-                        s2 = o2 ? dd[2] : -dd[2];
-            kap[o * V + x] = s0 * u1 * u2 + u0 * s1 * u2 + u0 * u1 * s2;
+        for (int e0 = -1; e0 <= 1; ++e0) {
+            const int o0 = e0 - c[0].lo;   // corner bit on axis 0 (0 or 1 when a corner)
+            const long long py = (long long)wrap(i + e0, g.N1) * plane;
+#pragma unroll
+            for (int e1 = -1; e1 <= 1; ++e1) {
+                const int o1 = e1 - c[1].lo;
+                const long long ry = py + (long long)wrap(j + e1, g.N2) * g.N3;
+#pragma unroll
+                for (int e2 = -1; e2 <= 1; ++e2) {
+                    const int o2 = e2 - c[2].lo;
+                    float kap = 0.f;
+                    if (o0 >= 0 && o0 <= 1 && o1 >= 0 && o1 <= 1 && o2 >= 0 && o2 <= 1) {
+                        const float u0 = o0 ? c[0].wh : c[0].wl, u1 = o1 ? c[1].wh : c[1].wl,
+                                    u2 = o2 ? c[2].wh : c[2].wl;
+                        const float s0 = o0 ? dd[0] : -dd[0], s1 = o1 ? dd[1] : -dd[1],
+                                    s2 = o2 ? dd[2] : -dd[2];
+                        kap = s0 * u1 * u2 + u0 * s1 * u2 + u0 * u1 * s2;
+                    }
+                    K[(long long)((e0 + 1) * 9 + (e1 + 1) * 3 + (e2 + 1)) * V + ry +
+                      wrap(k + e2, g.N3)] = kap;
+                }
+            }
         }
     }
 }
 
-// Corner index of neighbour x = y - e (per-axis offset e) in its own cell, given
-// its cell-start bit l (1: starts at -1); -1 when y is not a corner of that cell.
-template <int E>
-__device__ __forceinline__ int corner_bit(unsigned l) {
-    if constexpr (E == -1) return l ? 0 : -1;
-    else if constexpr (E == 1) return l ? -1 : 1;
-    else return (int)l;
-}
-
+// One stencil term: the neighbour x = y - e contributes K_e(y) lambda(x).
 template <int E0, int E1, int E2>
-__device__ __forceinline__ void gather_one(const uint8_t *__restrict__ lob,
-                                           const float *__restrict__ kap,
-                                           const float *__restrict__ lam1, long long V,
-                                           const long long *p, const long long *r, const int *q,
-                                           float &acc) {
+__device__ __forceinline__ void stencil_one(const float *__restrict__ K,
+                                            const float *__restrict__ lam1, long long V,
+                                            long long y, const long long *p, const long long *r,
+                                            const int *q, float &acc) {
     const long long x = p[E0 + 1] + r[E1 + 1] + q[E2 + 1];
-    const unsigned bits = __ldg(lob + x);
-    const int o0 = corner_bit<E0>((bits >> 2) & 1u), o1 = corner_bit<E1>((bits >> 1) & 1u),
-              o2 = corner_bit<E2>(bits & 1u);
-    if ((o0 | o1 | o2) < 0) return;
-    acc = fmaf(__ldg(kap + (long long)(4 * o0 + 2 * o1 + o2) * V + x), __ldg(lam1 + x), acc);
+    acc = fmaf(__ldg(K + (long long)((E0 + 1) * 9 + (E1 + 1) * 3 + (E2 + 1)) * V + y),
+               __ldg(lam1 + x), acc);
 }
 
 template <bool TRANSPOSE_TERM, bool HAVE_DM>
 __global__ void __launch_bounds__(NK *NJ)
 k_newton_terms(const float *__restrict__ d, const float *__restrict__ dv,
                const float *__restrict__ lam1, const float *__restrict__ mn,
-               const float *__restrict__ dmn, const uint8_t *__restrict__ lob,
-               const float *__restrict__ kap, float *__restrict__ dlam, float *__restrict__ b,
-               float dt, Grid3 g) {
+               const float *__restrict__ dmn, const float *__restrict__ K,
+               float *__restrict__ dlam, float *__restrict__ b, float dt, Grid3 g) {
     pdl_wait();
     const int k = blockIdx.x * NK + (threadIdx.x & (NK - 1));
     const int j = blockIdx.y * NJ + (threadIdx.x / NK);
@@ -177,7 +185,7 @@ k_newton_terms(const float *__restrict__ d, const float *__restrict__ dv,
                                 (long long)wrap(j - 1, g.N2) * g.N3};
         const int q[3] = {wrap(k + 1, g.N3), k, wrap(k - 1, g.N3)};
         float acc = 0.f;
-#define BLR_G(A, B, C) gather_one<A, B, C>(lob, kap, lam1, V, p, r, q, acc)
+#define BLR_G(A, B, C) stencil_one<A, B, C>(K, lam1, V, y, p, r, q, acc)
         BLR_G(-1, -1, -1); BLR_G(-1, -1, 0); BLR_G(-1, -1, 1);
         BLR_G(-1, 0, -1);  BLR_G(-1, 0, 0);  BLR_G(-1, 0, 1);
         BLR_G(-1, 1, -1);  BLR_G(-1, 1, 0);  BLR_G(-1, 1, 1);
@@ -199,7 +207,7 @@ int newton_prep(blr_plan *P, cudaStream_t s) {
     const long long cap = (long long)P->sms * 8;
     if (blocks > cap) blocks = cap;
     launch_pdl(k_newton_prep, dim3((unsigned)blocks), dim3(256), 0, s, (const float *)P->d,
-               (const float *)P->dv, P->dt, P->nt_lob, P->nt_kap, P->V);
+               (const float *)P->dv, P->dt, P->nt_kap, P->grid);
     BLR_CK_LAUNCH();
     return BLR_OK;
 }
@@ -211,8 +219,8 @@ int newton_terms(blr_plan *P, bool transpose_term, const float *lam1, const floa
     const dim3 block(NK * NJ);
 #define BLR_NT(TT, DM)                                                                       \
     launch_pdl(k_newton_terms<TT, DM>, grid, block, 0, s, (const float *)P->d,                \
-               (const float *)P->dv, lam1, mn, dmn, (const uint8_t *)P->nt_lob,           \
-               (const float *)P->nt_kap, dlam, b, P->dt, P->grid)
+               (const float *)P->dv, lam1, mn, dmn, (const float *)P->nt_kap, dlam, b,    \
+               P->dt, P->grid)
     if (transpose_term && dmn) BLR_NT(true, true);
     else if (transpose_term) BLR_NT(true, false);
     else if (dmn) BLR_NT(false, true);
