@@ -179,8 +179,10 @@ size_t layout(blr_plan *P, char *base) {
         P->T2p = a.take<float>((size_t)4 * P->B2 * P->N2);
     }
     P->A = a.take<float>(P->nb);
-    P->dft_big = a.take<float>((size_t)3 * P->B1 * P->N2 * P->N3 * 2);
-    P->dft_small = a.take<float>((size_t)3 * P->B1 * P->B2 * P->N3 * 2);
+    // the FP32 stages' intermediates (for every step's velocity at once when non-stationary)
+    const size_t dft_vel = (P->p.precision == BLR_FP32 && P->nvel > 1) ? (size_t)P->nvel : 1;
+    P->dft_big = a.take<float>(dft_vel * 3 * P->B1 * P->N2 * P->N3 * 2);
+    P->dft_small = a.take<float>(dft_vel * 3 * P->B1 * P->B2 * P->N3 * 2);
     for (int k = 0; k < 4; ++k) P->fz_tab[k] = nullptr;
     P->fz_buf = nullptr;
     P->dv_all = P->b_all = nullptr;
@@ -205,6 +207,10 @@ size_t layout(blr_plan *P, char *base) {
     } else {
         P->tc_tab_expand = P->tc_tab_project = nullptr;
         P->tc_tab2_expand = P->tc_tab2_project = nullptr;
+        if (P->p.precision == BLR_FP32 && P->nvel > 1) {   // every step in one GEMM pass
+            P->dv_all = a.take<float>((size_t)3 * P->nvel * V);
+            P->b_all = a.take<float>((size_t)3 * P->nvel * V);
+        }
     }
     float **vecs[] = {&P->vt, &P->g, &P->r, &P->pv, &P->q, &P->x, &P->trial, &P->step, &P->vtmp};
     for (float **v : vecs) *v = a.take<float>(P->nfloat);
@@ -252,8 +258,8 @@ int state_at(blr_plan *P, const float *vt, double *energy_out, cudaStream_t s) {
         BLR_CK(cudaMemcpyAsync(P->vt, vt, P->nfloat * sizeof(float), cudaMemcpyDefault, s));
     }
     P->have_lams = false;
-    if (P->nvel > 1 && P->fz_tab[0]) {   // every step's displacement in one fused transform
-        if ((rc = fz_expand(P, P->vt, P->d_base, -P->dt, 1, s, 3 * P->nvel))) return rc;
+    if (P->nvel > 1 && P->dv_all) {   // every step's displacement in one transform
+        if ((rc = dft_expand_nc(P, P->vt, P->d_base, 1, s, 3 * P->nvel))) return rc;
         for (int n = 0; n < P->nvel; ++n) {
             use_step(P, n);
             if ((rc = sweep_pack_d4(P, s))) return rc;

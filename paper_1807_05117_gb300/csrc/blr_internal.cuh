@@ -151,8 +151,8 @@ struct blr_plan {
     int bal_tr;         // blocks per SM of the transport-only grid (0: ADJ_BLOCKS)
     float *lam_keep;    // lambda^1 .. lambda^{nt-1} of the split adjoint solve, or nullptr
     float *rho_keep;    // rho^1 .. rho^{nt-1} ([3][V] each) of the deformation variant's split solve
-    float *dv_all;      // non-stationary, fused transforms: every step's expanded direction [nt][3][V]
-    float *b_all;       // non-stationary, fused transforms: every step's body force [nt][3][V]
+    float *dv_all;      // non-stationary (fused or FP32 transforms): every step's direction [nt][3][V]
+    float *b_all;       // non-stationary (fused or FP32 transforms): every step's body force [nt][3][V]
     int adj2;           // two adjoint steps per launch on a balanced grid of adj2 blocks
                         // per SM (plans that keep Gm), or 0: one step per launch
                         //                                                      (sweep_autotune)
@@ -260,6 +260,11 @@ int plan_create(const blr_params *p, bool grad_cache, blr_plan **out);
 // dft.cu
 int dft_init_tables(blr_plan *P, cudaStream_t s);
 int dft_autotune(blr_plan *P, cudaStream_t s);
+// nc fields (3 per velocity; every step of a non-stationary plan) in one transform
+// (fused mixed-precision kernels or the FP32 GEMM stages; BLR_EINVAL otherwise).
+int dft_expand_nc(blr_plan *P, const float *vt, float *out, int mode, cudaStream_t s, int nc);
+int dft_project_nc(blr_plan *P, const float *f, float *ft, const float *vadd, cudaStream_t s,
+                   float areg, int nc);
 // iota into out (3V). mode 0: out = v; mode 1: out = clamp(-dt*v) + CFL/NaN flags.
 int dft_expand(blr_plan *P, const float *vt, float *out, int mode, cudaStream_t s);
 // pi(f) (+ areg A * vadd when vadd != nullptr) into ft.

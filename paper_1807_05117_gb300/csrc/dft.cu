@@ -413,7 +413,7 @@ int device_sms(const blr_plan *P) {
 // `in` / `out` are the stage's data operand and result; mode 1 (stage C only)
 // stores the displacement.
 int launch_stage(const blr_plan *P, int stage, const float *in, float *out, float scale, int mode,
-                 cudaStream_t s) {
+                 cudaStream_t s, int nc = 3) {
     const long long ncol = (long long)P->N2 * P->N3;
     const int sms = device_sms(P), forced = P->gemm_tile[stage];
     GemmArgs g{};
@@ -434,8 +434,8 @@ int launch_stage(const blr_plan *P, int stage, const float *in, float *out, floa
             g.M = 2 * P->N2;
             g.K = 2 * P->B2;
             g.N = P->N3;
-            return P->T2e ? launch_sgemm<AK_KM, 0>(g, 3 * P->B1, sms, s, forced)
-                          : launch_sgemm<AK_E2, 0>(g, 3 * P->B1, sms, s, forced);
+            return P->T2e ? launch_sgemm<AK_KM, 0>(g, nc * P->B1, sms, s, forced)
+                          : launch_sgemm<AK_E2, 0>(g, nc * P->B1, sms, s, forced);
         case 1:
             g.A = P->W1;
             g.lda = P->N1;
@@ -444,8 +444,8 @@ int launch_stage(const blr_plan *P, int stage, const float *in, float *out, floa
             g.M = P->N1;
             g.K = 2 * P->B1;
             g.N = ncol;
-            return mode == 0 ? launch_sgemm<AK_KM, 0>(g, 3, sms, s, forced)
-                             : launch_sgemm<AK_KM, 1>(g, 3, sms, s, forced);
+            return mode == 0 ? launch_sgemm<AK_KM, 0>(g, nc, sms, s, forced)
+                             : launch_sgemm<AK_KM, 1>(g, nc, sms, s, forced);
         case 2:
             g.A = P->W1t ? P->W1t : P->W1;
             g.lda = P->W1t ? 2 * P->B1 : P->N1;
@@ -454,8 +454,8 @@ int launch_stage(const blr_plan *P, int stage, const float *in, float *out, floa
             g.M = 2 * P->B1;
             g.K = P->N1;
             g.N = ncol;
-            return P->W1t ? launch_sgemm<AK_KM, 0>(g, 3, sms, s, forced)
-                          : launch_sgemm<AK_MK, 0>(g, 3, sms, s, forced);
+            return P->W1t ? launch_sgemm<AK_KM, 0>(g, nc, sms, s, forced)
+                          : launch_sgemm<AK_MK, 0>(g, nc, sms, s, forced);
         case 4:
             g.A = in;
             g.lda = 2 * P->B3;
@@ -463,7 +463,7 @@ int launch_stage(const blr_plan *P, int stage, const float *in, float *out, floa
             g.strideB = 0;
             g.pN3 = P->N3;
             g.pB2 = P->B2;
-            g.M = 3 * P->B1 * P->B2;
+            g.M = nc * P->B1 * P->B2;
             g.K = 2 * P->B3;
             g.N = 2LL * P->N3;
             return launch_sgemm<AK_MK, 0, 1>(g, 1, sms, s, forced);
@@ -475,8 +475,8 @@ int launch_stage(const blr_plan *P, int stage, const float *in, float *out, floa
             g.M = 2 * P->B2;
             g.K = 2 * P->N2;
             g.N = P->N3;
-            return P->T2p ? launch_sgemm<AK_KM, 0>(g, 3 * P->B1, sms, s, forced)
-                          : launch_sgemm<AK_P2, 0>(g, 3 * P->B1, sms, s, forced);
+            return P->T2p ? launch_sgemm<AK_KM, 0>(g, nc * P->B1, sms, s, forced)
+                          : launch_sgemm<AK_P2, 0>(g, nc * P->B1, sms, s, forced);
     }
 }
 
@@ -695,4 +695,33 @@ int dft_autotune(blr_plan *P, cudaStream_t s) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return rc;
+}
+
+// nc fields (3 per velocity) in one transform: the fused kernels, or the FP32 GEMM
+// stages (the plan's intermediates then hold nvel velocities).  Mode 1 writes the
+// displacements without packing d4 (the caller packs each step's copy).
+int dft_expand_nc(blr_plan *P, const float *vt, float *out, int mode, cudaStream_t s, int nc) {
+    if (P->fz_tab[0]) return fz_expand(P, vt, out, mode == 0 ? 1.f : -P->dt, mode, s, nc);
+    if (P->p.precision != BLR_FP32 || !P->T3e || nc > 3 * P->nvel) return BLR_EINVAL;
+    int rc = launch_stage(P, 4, vt, P->dft_small, 1.f, 0, s, nc);
+    if (!rc) rc = launch_stage(P, 0, P->dft_small, P->dft_big, 1.f, 0, s, nc);
+    if (!rc) rc = launch_stage(P, 1, P->dft_big, out, mode == 0 ? 1.f : -P->dt, mode, s, nc);
+    return rc;
+}
+
+int dft_project_nc(blr_plan *P, const float *f, float *ft, const float *vadd, cudaStream_t s,
+                   float areg, int nc) {
+    if (P->fz_tab[0]) return fz_project(P, f, ft, vadd, areg, s, nc);
+    if (P->p.precision != BLR_FP32 || !P->W1t || nc > 3 * P->nvel) return BLR_EINVAL;
+    int rc = launch_stage(P, 2, f, P->dft_big, 1.f, 0, s, nc);
+    if (!rc) rc = launch_stage(P, 3, P->dft_big, P->dft_small, 1.f, 0, s, nc);
+    if (rc) return rc;
+    const int rows = nc * P->B1 * P->B2;
+    const size_t sp = project_axis3_smem(P->B3);
+    BLR_CK(cudaFuncSetAttribute(k_project_axis3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp));
+    launch_pdl(k_project_axis3, dim3((unsigned)ceil_div_ll(rows, XR)), dim3(256), sp, s,
+               (const float *)P->dft_small, (const float *)P->T3c, (const float *)P->T3s, ft,
+               (const float *)P->A, vadd, areg, rows, P->B2, P->B3, P->N3, P->B1 * P->B2);
+    BLR_CK_LAUNCH();
+    return BLR_OK;
 }

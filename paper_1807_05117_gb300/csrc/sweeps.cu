@@ -2007,7 +2007,7 @@ int sweep_adjoint_steps(blr_plan *P, const float *lam_final, float *gout, const 
     int cur = 0;
     // with the fused transforms, every step's body force is kept and all of them
     // are projected in one launch after the sweep
-    const bool batched = gout && vadd && !b_steps && P->b_all && P->fz_tab[0];
+    const bool batched = gout && vadd && !b_steps && P->b_all;
     if (batched) b_steps = P->b_all;
     for (int j = P->nseg - 1; j >= 0; --j) {
         int rc = ensure_segment(P, j, s);
@@ -2027,7 +2027,7 @@ int sweep_adjoint_steps(blr_plan *P, const float *lam_final, float *gout, const 
             cur = 1 - cur;
         }
     }
-    if (batched) return fz_project(P, P->b_all, gout, vadd, P->dt, s, 3 * nt);
+    if (batched) return dft_project_nc(P, P->b_all, gout, vadd, s, P->dt, 3 * nt);
     return BLR_OK;
 }
 
@@ -2038,9 +2038,9 @@ int sweep_incremental(blr_plan *P, cudaStream_t s, const float *dvt_steps) {
     int cur = 0;
     // with the fused transforms, every step's direction is expanded in one launch
     // and the steps read their own slice (P->dv is pointed at it, then restored)
-    const bool batched = dvt_steps && P->dv_all && P->fz_tab[0];
+    const bool batched = dvt_steps && P->dv_all;
     if (batched) {
-        int rc = fz_expand(P, dvt_steps, P->dv_all, 1.f, 0, s, 3 * nt);
+        int rc = dft_expand_nc(P, dvt_steps, P->dv_all, 0, s, 3 * nt);
         if (rc) return rc;
     }
     struct RestoreDv {
