@@ -159,7 +159,8 @@ size_t layout(blr_plan *P, char *base) {
                    P->p.state_equation == BLR_STATE_IMAGE)
                       ? a.take<float>((size_t)(P->p.nt - 1) * V)
                       : nullptr;
-    P->rho_keep = (P->use_gm && P->p.nt > 1 && P->p.state_equation == BLR_STATE_DEFORMATION)
+    P->rho_keep = (P->use_gm && P->p.nt > 1 && P->p.state_equation == BLR_STATE_DEFORMATION &&
+                   P->p.hessian != BLR_NEWTON)
                       ? a.take<float>((size_t)3 * (P->p.nt - 1) * V)
                       : nullptr;
     P->b = a.take<float>(3 * V);
@@ -452,8 +453,7 @@ int plan_create(const blr_params *p, bool grad_cache, blr_plan **out) {
         return BLR_EINVAL;
     }
     P->use_gm = grad_cache && P->sweep_wide && P->ck == p->nt &&
-                (p->state_equation == BLR_STATE_IMAGE ||
-                 (p->hessian == BLR_GAUSS_NEWTON && !p->nonstationary));
+                (p->state_equation == BLR_STATE_IMAGE || !p->nonstationary);
     // L2 persistence for the displacement copy d4 (the autotuner decides whether the
     // sweeps use it): the window covers one step's d4, and the context's
     // persisting set-aside is raised to hold it when the device allows

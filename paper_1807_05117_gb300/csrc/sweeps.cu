@@ -2201,7 +2201,7 @@ int sweep_adjoint_def_newton(blr_plan *P, float *b, cudaStream_t s) {
         const float *dun = n > 0 ? P->du_all + (size_t)(n - 1) * V3 : nullptr;      // du^n
         for (int c = 0; c < 3; ++c) {
             launch_adjoint(P, n == nt - 1 && c == 0, n > 0, rin + c * P->V, def_u(P, n, c),
-                           rout ? rout + c * P->V : nullptr, b, nullptr, s);
+                           rout ? rout + c * P->V : nullptr, b, def_grad_slot(P, n, c), s);
             BLR_CK_LAUNCH();
             int rc = newton_terms(P, n > 0, rho1 + c * P->V, def_u(P, n, c),
                                   dun ? dun + c * P->V : nullptr, rout ? rout + c * P->V : nullptr,
