@@ -669,9 +669,7 @@ __device__ __forceinline__ AdjWRings adjw_rings() {
 
 // USEG: grad m^n(x + d(x)) is read from Gn ([3][V], written by the state sweep)
 // instead of being interpolated from an m^n ring (which is then not kept).
-// BODY false: the transport lambda^n = S^T lambda^{n+1} alone (no body force, no
-// m^n ring; the body force is summed over the steps afterwards, k_body_force).
-template <bool FIRST, bool WRITE_LAM, bool USEG, bool BODY = true>
+template <bool FIRST, bool WRITE_LAM, bool USEG>
 __device__ __forceinline__ void
 adjoint_tile_w(const float *__restrict__ lam_in, const float *__restrict__ m_n,
                const float4 *__restrict__ d4, float *__restrict__ lam_out, float *__restrict__ b,
@@ -693,7 +691,7 @@ adjoint_tile_w(const float *__restrict__ lam_in, const float *__restrict__ m_n,
         const int c = tid + MT * i;
         offq[i] = c < BPL ? win_off(g, j0, k0, c / BW, c % BW) : 0;
     }
-    const bool cl = tid < ASC, cm = BODY && !USEG && tid >= AM0;
+    const bool cl = tid < ASC, cm = !USEG && tid >= AM0;
     const int offl = cl ? win_off(g, j0, k0, tid / BG, 4 * (tid % BG)) : 0;
     const int offm = cm ? win_off(g, j0, k0, (tid - AM0) / BG, 4 * ((tid - AM0) % BG)) : 0;
     const uint32_t q0s = smem_u32(R.Q) + (uint32_t)tid * 16u;
@@ -730,7 +728,7 @@ adjoint_tile_w(const float *__restrict__ lam_in, const float *__restrict__ m_n,
             // first, so the loads of plane s's b and grad m^n have the whole transpose
             // to land
             const int o = s - 1;
-            if (BODY && o >= i0) {
+            if (o >= i0) {
                 const float4 *Qo = R.Q + ((r + 3) & (BQ - 1)) * BPL;   // plane s - 1
                 const float *Lo = R.L + ((r + 3) & (BQ - 1)) * BPL;
                 const float *Ma = R.M + ((uint32_t)(r + 4) % BM) * BPL;          // plane s - 2
@@ -760,7 +758,7 @@ adjoint_tile_w(const float *__restrict__ lam_in, const float *__restrict__ m_n,
                     }
                 }
             }
-            if (BODY && (!FIRST || USEG) && s >= i0 && s < i_end) {
+            if ((!FIRST || USEG) && s >= i0 && s < i_end) {
 #pragma unroll
                 for (int jj = 0; jj < ARJ; ++jj) {
                     const int j = jb + jj;
