@@ -69,8 +69,8 @@ ADJ_BYTES = lambda nt: ((36 + 44 + 48 * (nt - 2)) if nt > 1 else 32)
 # of csrc/sweeps.cu (the text above its host-side marker line) is the code the
 # capture was taken from: SHA-256 of that text.
 SWEEPS_HOST_MARKER = "// ==== host side: launch shapes, launchers, sweep orchestration, autotuner ===="
-ADJ_TRAFFIC = {"sweeps_device_sha256": "d2746545fd226568d2cb0f97f583dc47f402a1e9ef153b27eb7a23a58984fc91",
-               "bytes": 94958848 + 2299648}
+ADJ_TRAFFIC = {"sweeps_device_sha256": "ba19aa452a7d89bcf977181754f0710a2e58859a1431ad5e8612b5f0cfecb67d",
+               "bytes": 95076864 + 2149120}
 
 
 def adjoint_traffic():
