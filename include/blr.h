@@ -284,22 +284,24 @@ int blr_batch_create(const blr_params *params, int npairs, blr_batch_t *out);
 int blr_batch_destroy(blr_batch_t batch);
 
 /* Diagnostic (no counterpart in the paper): the batch's sweep choices into
- * vals[0 .. min(n, 6) - 1]: [0] 1 if every pair keeps its state gradients
+ * vals[0 .. min(n, 7) - 1]: [0] 1 if every pair keeps its state gradients
  * grad m^n(x + d(x)) (3 nt V floats per pair, allocated when they fit),
  * [1] 1 if the batched sweeps use them (the state sweep writes them, the
  * adjoint and incremental-state sweeps read them), [2] the x1 tile length of
  * the adjoint sweep's work items and [3] that of the state and
  * incremental-state sweeps (0: each pair's own one-wave length, else planes for
  * every pair, capped at its N1), [4] the grid size in voxels from which a pair
- * runs "solo" (0: no pair does), [5] the number of solo pairs.  A solo pair's
- * grid fills the GPU by itself: it skips the work queue and runs its own
- * plan's autotuned kernels, one solo pair after another.  [1] to [3] are chosen
- * at creation by timing the batch.  BLR_EINVAL for a NULL batch or vals. */
+ * runs "solo" (0: no pair does), [5] the number of solo pairs, [6] 1 if the
+ * queued incremental-state steps use the gather form (with [1]).  A solo pair
+ * skips the work queue and runs its own plan's autotuned kernels, solo pairs on
+ * three concurrent lanes.  [1] to [3] and [6] are chosen at creation by timing
+ * the batch.  BLR_EINVAL for a NULL batch or vals. */
 int blr_batch_tuning(blr_batch_t batch, int *vals, int n);
 
-/* Diagnostic: force the choices [0] to [4] of blr_batch_tuning (n >= 5;
- * vals[0] must be the batch's own, vals[1] <= vals[0], vals[2..3] 0 or
- * 2..1024, vals[4] >= 0).  Every choice computes the same results bit for bit.
+/* Diagnostic: force the choices [0] to [4] (and, when n >= 7, [6]; [5] is
+ * ignored) of blr_batch_tuning (n >= 5; vals[0] must be the batch's own,
+ * vals[1] <= vals[0], vals[2..3] 0 or 2..1024, vals[4] >= 0, vals[6] <= vals[1]).
+ * Every choice computes the same results bit for bit.
  * A change of vals[1] or of the set of solo pairs drops every pair's current
  * point (the next call must be blr_batch_gradient or blr_batch_newton).
  * Synchronises the device. */

@@ -513,7 +513,7 @@ class Batch:
             pass
 
     TUNING_KEYS = ("kept_gradients", "use_kept_gradients", "adjoint_chunk", "state_chunk",
-                   "solo_min_voxels", "solo_pairs")
+                   "solo_min_voxels", "solo_pairs", "incremental_gather")
 
     def tuning(self) -> dict:
         """The batch's sweep choices (blr_batch_tuning)."""
@@ -529,8 +529,9 @@ class Batch:
             if k not in cur or k == "solo_pairs":
                 raise ValueError(f"unknown or read-only tuning key {k}")
             cur[k] = int(v)
-        keys = self.TUNING_KEYS[:5]
-        vals = (ctypes.c_int * len(keys))(*[cur[k] for k in keys])
+        if not cur["use_kept_gradients"]:
+            cur["incremental_gather"] = 0   # the gather form reads the kept gradients
+        vals = (ctypes.c_int * len(self.TUNING_KEYS))(*[cur[k] for k in self.TUNING_KEYS])
         _check(_lib.blr_batch_set_tuning(_P(self.handle), vals, len(vals)), "blr_batch_set_tuning")
 
     def set_images(self, pair, I0, I1, stream=None):

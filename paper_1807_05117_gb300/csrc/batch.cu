@@ -11,11 +11,12 @@
 // * The x1 chunk of the sweep tiles, and whether the batched sweeps keep the
 //   state gradients, are chosen by timing candidates on the batch itself
 //   (batch_autotune).
-// * A pair whose grid fills the GPU by itself ("solo", at least solo_min voxels)
-//   skips the work queue: it runs its own plan's autotuned kernels (balanced
-//   grids, the two-step adjoint, the gather form of the incremental state), one
-//   pair after the other on the batch stream, and its PCG iteration is a graph
-//   of its own, replayed while the pair is active.
+// * A pair of at least solo_min voxels (2^19 by default) runs "solo": it skips
+//   the work queue and runs its own plan's autotuned kernels (balanced grids, the
+//   split or two-step adjoint, the gather form of the incremental state) on one
+//   of three side lanes, concurrently with other solo pairs and with the queued
+//   pairs' launches; its PCG iteration is a graph of its own, replayed while the
+//   pair is active.
 // Each pair's arithmetic is exactly that of a single plan, so batched results
 // are bit-identical to running the pairs one by one.
 #include <string.h>
@@ -49,9 +50,10 @@ struct Batch {
     bool wide = false;                        // every pair runs the wide-copy sweep tiles
     bool gm = false;                          // every pair keeps its state gradients
     bool useg = false;                        // the batched sweeps write / read them (autotuned)
+    bool inc_gather = false;                  // with useg: incremental steps in the gather form
     std::vector<int> own_chunk[3];            // [kind][pair]: each plan's own x1 chunk
     int chunk_choice[3] = {0, 0, 0};          // [kind]: 0 = own chunks, else planes for all
-    long long solo_min = 1LL << 21;           // voxels from which a pair runs solo (0: none)
+    long long solo_min = 1LL << 19;           // voxels from which a pair runs solo (0: none)
     std::vector<char> solo;                   // [pair]
     int nbatched = 0;                         // pairs in the work queue
     std::vector<cudaGraphExec_t> solo_exec;   // [pair]: PCG iteration of a solo pair
@@ -142,10 +144,13 @@ int launch_sweep(Batch *B, int kind, int n, cudaStream_t s) {
         f1 = n == 0;
         f2 = n == nt - 1;
     }
-    return sweep_batch_launch(kind, f1, f2, B->wide, B->useg, B->d_desc + ((size_t)kind * nt + n) * B->npairs,
+    // the gather form runs on the incremental-state (kind 2) items and descriptors
+    const int launch_kind = (kind == 2 && B->useg && B->inc_gather) ? 3 : kind;
+    return sweep_batch_launch(launch_kind, f1, f2, B->wide, B->useg,
+                              B->d_desc + ((size_t)kind * nt + n) * B->npairs,
                               B->d_starts + (size_t)kind * (B->npairs + 1), B->npairs,
                               B->d_counters + (size_t)kind * nt + n,
-                              sweep_blocks_per_sm(kind, B->wide) * B->grid, s);
+                              sweep_blocks_per_sm(launch_kind, B->wide) * B->grid, s);
 }
 
 int reset_counters(Batch *B, cudaStream_t s) {
@@ -389,8 +394,10 @@ int batch_autotune(Batch *B) {
     const int nu = B->gm ? 2 : 1;
     float total[2] = {0.f, 0.f};
     int best_c[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    bool gather[2] = {false, false};
     for (int u = 0; u < nu && !rc; ++u) {
         B->useg = u == 1;
+        B->inc_gather = false;
         for (int kind = 1; kind <= 2 && !rc; ++kind) {
             float best = 1e30f;
             for (int c = 0; c < 5 && !rc; ++c) {
@@ -414,11 +421,31 @@ int batch_autotune(Batch *B) {
                 }
             }
             apply_chunk(B, kind, best_c[u][kind]);
+            if (kind == 2 && B->useg && !rc) {   // the gather form at that chunk
+                if ((rc = fill_descriptors(B))) break;
+                B->inc_gather = true;
+                float tot = 0.f;
+                for (int rep = 0; rep < 3 && !rc; ++rep) {
+                    if ((rc = reset_counters(B, B->s))) break;
+                    if (cudaEventRecord(e0, B->s) != cudaSuccess) rc = BLR_ECUDA;
+                    if (!rc) rc = launch_sweep(B, kind, n, B->s);
+                    if (!rc && (cudaEventRecord(e1, B->s) != cudaSuccess ||
+                                cudaEventSynchronize(e1) != cudaSuccess))
+                        rc = BLR_ECUDA;
+                    float ms = 0.f;
+                    if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = BLR_ECUDA;
+                    if (rep) tot += ms;
+                }
+                B->inc_gather = tot < best;
+                gather[u] = B->inc_gather;
+                if (tot < best) best = tot;
+            }
             total[u] += best;
         }
     }
     const int u = (nu == 2 && total[1] < total[0]) ? 1 : 0;
     B->useg = u == 1;
+    B->inc_gather = gather[u];
     apply_chunk(B, 1, best_c[u][1]);
     apply_chunk(B, 2, best_c[u][2]);
     if (!rc) rc = fill_descriptors(B);
@@ -531,9 +558,9 @@ int blr_batch_tuning(blr_batch_t b, int *vals, int n) {
     int nsolo = 0;
     for (char c : B->solo) nsolo += c;
     const long long smin = B->solo_min < 0x7fffffffLL ? B->solo_min : 0x7fffffffLL;
-    const int v[6] = {B->gm ? 1 : 0, B->useg ? 1 : 0, B->chunk_choice[1], B->chunk_choice[2],
-                      (int)smin, nsolo};
-    for (int i = 0; i < n && i < 6; ++i) vals[i] = v[i];
+    const int v[7] = {B->gm ? 1 : 0, B->useg ? 1 : 0, B->chunk_choice[1], B->chunk_choice[2],
+                      (int)smin, nsolo, B->inc_gather ? 1 : 0};
+    for (int i = 0; i < n && i < 7; ++i) vals[i] = v[i];
     return BLR_OK;
 }
 
@@ -543,6 +570,8 @@ int blr_batch_set_tuning(blr_batch_t b, const int *vals, int n) {
     if (vals[0] != (B->gm ? 1 : 0) || vals[1] < 0 || vals[1] > vals[0] || vals[4] < 0) return BLR_EINVAL;
     for (int k = 2; k < 4; ++k)
         if (vals[k] != 0 && (vals[k] < 2 || vals[k] > 1024)) return BLR_EINVAL;
+    const bool gather = n >= 7 ? vals[6] != 0 : (B->inc_gather && vals[1] != 0);
+    if (n >= 7 && (vals[6] < 0 || vals[6] > vals[1])) return BLR_EINVAL;
     BLR_CK(cudaDeviceSynchronize());
     drop_graphs(B);   // the captured iterations hold the old launches
     bool moved = (vals[1] != 0) != B->useg;
@@ -557,6 +586,7 @@ int blr_batch_set_tuning(blr_batch_t b, const int *vals, int n) {
     // (or not) for the old path: every pair needs a new forward solve
     if (moved)
         for (blr_plan_t P : B->plans) P->have_state = false;
+    B->inc_gather = gather;
     apply_chunk(B, 1, vals[2]);
     apply_chunk(B, 2, vals[3]);
     return fill_descriptors(B);

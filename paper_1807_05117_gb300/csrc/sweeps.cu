@@ -1199,16 +1199,16 @@ k_incstate_wide(const float *__restrict__ dm_in, const float *__restrict__ m_n,
 // d from d4, dv and grad m^n from their planar arrays.  Nothing waits at a
 // barrier, so the loads of many voxels overlap.  Block: 32 (x3) x 8 (x2) voxels
 // of one x1 plane.  Same arithmetic as incstate_tile.
+// One voxel of the gather form of the incremental step (k_incstate_gather and the
+// batched sweeps' gather tiles share it, so their results agree bit for bit).
 template <bool FIRST, bool LAST>
-__global__ void __launch_bounds__(MT)
-k_incstate_gather(const float *__restrict__ dm_in, const float4 *__restrict__ d4,
-                  const float *__restrict__ dv, const float *__restrict__ Gn,
-                  float *__restrict__ dm_out, float dt, float lam_scale, Grid3 g) {
-    pdl_wait();
-    const int k = blockIdx.x * MK + (threadIdx.x & 31);
-    const int j = blockIdx.y * MJ + (threadIdx.x >> 5);
-    const int i = blockIdx.z;
-    if (k >= g.N3 || j >= g.N2) return;
+__device__ __forceinline__ void incstate_gather_voxel(const float *__restrict__ dm_in,
+                                                      const float4 *__restrict__ d4,
+                                                      const float *__restrict__ dv,
+                                                      const float *__restrict__ Gn,
+                                                      float *__restrict__ dm_out, float dt,
+                                                      float lam_scale, const Grid3 &g, int i, int j,
+                                                      int k) {
     const long long plane = (long long)g.N2 * g.N3;
     const long long idx = (long long)i * plane + (long long)j * g.N3 + k;
     const float gdv = fmaf(__ldg(Gn + idx), __ldg(dv + idx),
@@ -1235,6 +1235,42 @@ k_incstate_gather(const float *__restrict__ dm_in, const float4 *__restrict__ d4
     }
     out = fmaf(-dt, gdv, out);
     dm_out[idx] = LAST ? lam_scale * out : out;
+}
+
+template <bool FIRST, bool LAST>
+__global__ void __launch_bounds__(MT)
+k_incstate_gather(const float *__restrict__ dm_in, const float4 *__restrict__ d4,
+                  const float *__restrict__ dv, const float *__restrict__ Gn,
+                  float *__restrict__ dm_out, float dt, float lam_scale, Grid3 g) {
+    pdl_wait();
+    const int k = blockIdx.x * MK + (threadIdx.x & 31);
+    const int j = blockIdx.y * MJ + (threadIdx.x >> 5);
+    const int i = blockIdx.z;
+    if (k >= g.N3 || j >= g.N2) return;
+    incstate_gather_voxel<FIRST, LAST>(dm_in, d4, dv, Gn, dm_out, dt, lam_scale, g, i, j, k);
+}
+
+// The gather form over a wide-copy tile (32 x3 x AJ x2 x CH planes; each thread two
+// x2 rows of one column), for the batched sweeps.
+template <bool FIRST, bool LAST>
+__device__ __forceinline__ void incstate_gather_tile(const float *__restrict__ dm_in,
+                                                     const float4 *__restrict__ d4,
+                                                     const float *__restrict__ dv,
+                                                     const float *__restrict__ Gn,
+                                                     float *__restrict__ dm_out, float dt,
+                                                     float lam_scale, const Grid3 &g, int CH,
+                                                     int k0, int j0, int i0) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int k = k0 + lane;
+    if (k >= g.N3) return;
+    const int i_end = min(i0 + CH, g.N1);
+    for (int i = i0; i < i_end; ++i)
+#pragma unroll
+        for (int jj = 0; jj < ARJ; ++jj) {
+            const int j = j0 + ARJ * w + jj;
+            if (j < g.N2)
+                incstate_gather_voxel<FIRST, LAST>(dm_in, d4, dv, Gn, dm_out, dt, lam_scale, g, i, j, k);
+        }
 }
 
 // The deformation variant's incremental step for all three components at once,
@@ -1309,8 +1345,9 @@ __global__ void k_pack_d4(const float *__restrict__ d, float4 *__restrict__ d4, 
 // WIDE: the adjoint and incremental-state items use the wide-copy tiles.
 // USEG (with WIDE): those tiles read the kept state gradients P.G instead of
 // interpolating grad m^n; the state items write them whenever P.Gout is set.
+// KIND 3: the incremental state's gather form over the kind-2 (wide) items.
 template <int KIND, bool F1, bool F2, bool WIDE, bool USEG>
-__global__ void __launch_bounds__(MT, KIND == 1 ? ADJ_BLOCKS : (KIND == 2 && WIDE ? INC_BLOCKS : 4))
+__global__ void __launch_bounds__(MT, KIND == 1 ? ADJ_BLOCKS : (KIND == 2 && WIDE ? INC_BLOCKS : (KIND == 3 ? 8 : 4)))
 k_sweep_batch(const SweepPair *__restrict__ pairs, const long long *__restrict__ starts,
               int npairs, unsigned long long *counter) {
     __shared__ long long s_item;
@@ -1333,7 +1370,7 @@ k_sweep_batch(const SweepPair *__restrict__ pairs, const long long *__restrict__
         const int kt = (int)(local % P.tk);
         const int jt = (int)((local / P.tk) % P.tj);
         const int it = (int)(local / ((long long)P.tk * P.tj));
-        const int k0 = kt * MK, j0 = jt * ((KIND == 1 || (KIND == 2 && WIDE)) ? AJ : MJ);
+        const int k0 = kt * MK, j0 = jt * ((KIND == 1 || KIND == 3 || (KIND == 2 && WIDE)) ? AJ : MJ);
         const int i0 = it * P.chunk;
         if constexpr (KIND == 0)
             state_tile<F1>(P.in0, P.d, P.out0, P.g, P.chunk, P.aux, P.out1, P.scale, P.partials,
@@ -1343,6 +1380,9 @@ k_sweep_batch(const SweepPair *__restrict__ pairs, const long long *__restrict__
                                          j0, i0, USEG ? P.G : nullptr);
         else if constexpr (KIND == 1)
             adjoint_tile<F1, F2>(P.in0, P.m, P.d, P.out0, P.out1, P.dt, P.g, P.chunk, k0, j0, i0);
+        else if constexpr (KIND == 3)
+            incstate_gather_tile<F1, F2>(P.in0, P.d4, P.aux, P.G, P.out0, P.dt, P.scale, P.g,
+                                         P.chunk, k0, j0, i0);
         else if constexpr (WIDE)
             incstate_tile_w<F1, F2, USEG>(P.in0, P.m, P.d4, P.aux, P.out0, P.dt, P.scale, P.g,
                                           P.chunk, k0, j0, i0, USEG ? P.G : nullptr);
@@ -2243,6 +2283,9 @@ int sweep_batch_launch(int kind, bool f1, bool f2, bool wide, bool useg, const S
         if (useg) batch_dispatch<1, true, true>(f1, f2, pairs, starts, npairs, counter, grid, s);
         else if (wide) batch_dispatch<1, true, false>(f1, f2, pairs, starts, npairs, counter, grid, s);
         else batch_dispatch<1, false, false>(f1, f2, pairs, starts, npairs, counter, grid, s);
+    } else if (kind == 3) {   // the gather form of the incremental step (kind-2 items)
+        if (!useg) return BLR_EINVAL;
+        batch_dispatch<3, true, true>(f1, f2, pairs, starts, npairs, counter, grid, s);
     } else {
         if (useg) batch_dispatch<2, true, true>(f1, f2, pairs, starts, npairs, counter, grid, s);
         else if (wide) batch_dispatch<2, true, false>(f1, f2, pairs, starts, npairs, counter, grid, s);
@@ -2253,7 +2296,7 @@ int sweep_batch_launch(int kind, bool f1, bool f2, bool wide, bool useg, const S
 }
 
 int sweep_blocks_per_sm(int kind, bool wide) {
-    return kind == 1 ? ADJ_BLOCKS : (kind == 2 && wide ? INC_BLOCKS : 4);
+    return kind == 1 ? ADJ_BLOCKS : (kind == 2 && wide ? INC_BLOCKS : (kind == 3 ? 8 : 4));
 }
 
 int sweep_chunk(const blr_plan *P, int kind) { return kind == 1 ? P->chunk_adj : P->chunk; }

@@ -99,22 +99,25 @@ def _compare_with_single_plans(blr, pairs, batch, plans):
         assert torch.equal(v, vs)
 
 
-@pytest.mark.parametrize("useg", [1, 0], ids=["kept-gradients", "interpolated-gradients"])
-def test_both_gradient_choices_equal_single_plans(setup, useg):
-    """Batched sweeps that read the kept state gradients and ones that
-    interpolate grad m^n give the single plans' results bit for bit."""
+@pytest.mark.parametrize("useg,gather", [(1, 1), (1, 0), (0, 0)],
+                         ids=["kept-gradients-gather", "kept-gradients-march", "interpolated"])
+def test_both_gradient_choices_equal_single_plans(setup, useg, gather):
+    """Batched sweeps that read the kept state gradients (with the incremental
+    steps in the gather or the march form) and ones that interpolate grad m^n
+    give the single plans' results bit for bit."""
     blr, pairs, batch, plans = setup
     tun = batch.tuning()
     assert tun["kept_gradients"] == 1
-    batch.set_tuning(use_kept_gradients=useg)
-    assert batch.tuning()["use_kept_gradients"] == useg
+    batch.set_tuning(use_kept_gradients=useg, incremental_gather=gather)
+    assert (batch.tuning()["use_kept_gradients"], batch.tuning()["incremental_gather"]) == (useg, gather)
     try:
         if useg != tun["use_kept_gradients"]:
             with pytest.raises(blr.BlrError):   # the change dropped the current points
                 batch.hessvec([p["dv"] for p in pairs], [torch.empty_like(p["vt"]) for p in pairs])
         _compare_with_single_plans(blr, pairs, batch, plans)
     finally:
-        batch.set_tuning(use_kept_gradients=tun["use_kept_gradients"])
+        batch.set_tuning(use_kept_gradients=tun["use_kept_gradients"],
+                         incremental_gather=tun["incremental_gather"])
     with pytest.raises(blr.BlrError):
         batch.set_tuning(kept_gradients=0)
 
