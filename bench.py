@@ -69,8 +69,8 @@ ADJ_BYTES = lambda nt: ((36 + 44 + 48 * (nt - 2)) if nt > 1 else 32)
 # of csrc/sweeps.cu (the text above its host-side marker line) is the code the
 # capture was taken from: SHA-256 of that text.
 SWEEPS_HOST_MARKER = "// ==== host side: launch shapes, launchers, sweep orchestration, autotuner ===="
-ADJ_TRAFFIC = {"sweeps_device_sha256": "ba19aa452a7d89bcf977181754f0710a2e58859a1431ad5e8612b5f0cfecb67d",
-               "bytes": 95076864 + 2149120}
+ADJ_TRAFFIC = {"sweeps_device_sha256": "f153a1a1222c166e8e7deb647675bd340398671c7ff688cbbe20bd2fd82ae2ff",
+               "bytes": 95055360 + 2219520}
 
 
 def adjoint_traffic():
