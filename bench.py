@@ -703,7 +703,7 @@ def batch_measure(steps, warmup, dev, flush, stream, one_by_one=True):
     launches = blr.blr_kernel_launches() - l0
     clocks = sampler.stop(0)
     voxels = sum(p["n"][0] * p["n"][1] * p["n"][2] for p in pairs)
-    # stepwise algorithmic bytes of the registrations' operators (survey per-unit figures):
+    # stepwise algorithmic bytes of the registrations' operators (per-unit figures):
     # HVP (24 + 84 nt) V, gradient (32 + 68 nt) V, extra forward solve (20 nt + 12) V
     nbytes = 0
     for p, r in zip(pairs, reps):
