@@ -387,7 +387,10 @@ int batch_autotune(Batch *B) {
     if (rc || B->nbatched == 0) return rc;
     cudaEvent_t e0, e1;
     BLR_CK(cudaEventCreate(&e0));
-    BLR_CK(cudaEventCreate(&e1));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return BLR_ECUDA;
+    }
     std::vector<int> all(B->npairs, 1);
     rc = upload_active(B, all);
     const int n = B->nt > 2 ? 1 : 0;
@@ -526,8 +529,12 @@ int blr_batch_create(const blr_params *params, int npairs, blr_batch_t *out) {
     for (int i = 0; i < nside && !rc; ++i) {
         cudaStream_t t;
         cudaEvent_t e;
-        if (cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+        if (cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking) != cudaSuccess) {
+            rc = BLR_ECUDA;
+            break;
+        }
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaStreamDestroy(t);
             rc = BLR_ECUDA;
             break;
         }

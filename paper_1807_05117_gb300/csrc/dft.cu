@@ -666,7 +666,10 @@ int dft_autotune(blr_plan *P, cudaStream_t s) {
     if (!P->T2e || !P->T2p || !P->W1t || !P->T3e) return BLR_OK;   // FP32 plans only
     cudaEvent_t e0, e1;
     BLR_CK(cudaEventCreate(&e0));
-    BLR_CK(cudaEventCreate(&e1));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return BLR_ECUDA;
+    }
     const float *ins[5] = {P->dft_small, P->dft_big, P->dv, P->dft_big, P->vt};
     float *outs[5] = {P->dft_big, P->dv, P->dft_big, P->dft_small, P->dft_small};
     int rc = BLR_OK;

@@ -2352,7 +2352,10 @@ int time_step(blr_plan *P, int kind, cudaStream_t s) {
 int sweep_autotune(blr_plan *P, cudaStream_t s) {
     cudaEvent_t e0, e1;
     BLR_CK(cudaEventCreate(&e0));
-    BLR_CK(cudaEventCreate(&e1));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return BLR_ECUDA;
+    }
     int rc = BLR_OK;
     // the fastest of four timed runs of four back-to-back steps (as the sweeps
     // run) after one warm-up run; the minimum is the least noisy estimate of a
