@@ -366,7 +366,7 @@ int blr_expand_noalloc(const int n[3], const int band[3], const float *vt, float
 unsigned long long blr_kernel_launches(void);
 
 /* Diagnostic (no counterpart in the paper): the sweep shapes the plan's
- * autotuner chose at creation.  vals: host, n ints; the first min(n, 12) are
+ * autotuner chose at creation.  vals: host, n ints; the first min(n, 13) are
  * written, in this order: wide-copy sweeps (0/1), state gradients kept (0/1),
  * adjoint blocks per SM, adjoint reads the kept gradient (0/1), incremental
  * state form (0 wide-copy, 1 wide-copy reading the kept gradient, 2 gather),
@@ -377,7 +377,11 @@ unsigned long long blr_kernel_launches(void);
  * kernel's grid, or 0 for one step per launch), split adjoint solve (0/1: the
  * steps transport lambda alone into kept adjoint states, (nt - 1) V floats,
  * and one pass sums the body force of all steps, bit-identical to the per-step
- * sums).  Returns BLR_EINVAL for a NULL plan or vals. */
+ * sums), the FP32 transforms' GEMM tiles (3 bits per stage, stage s at bits
+ * 3s..3s+2, stages 0 axis 2 and 1 axis 1 of the expand, 2 axis 1 and 3 axis 2
+ * of the project, 4 axis 3 of the expand; each 1..6 a register tile and thread
+ * count timed at creation, 0 the modelled choice; every tile gives the same
+ * results bit for bit).  Returns BLR_EINVAL for a NULL plan or vals. */
 int blr_plan_tuning(blr_plan_t plan, int *vals, int n);
 
 /* Test hook (no counterpart in the paper): while `on` is non-zero, every launch
@@ -392,7 +396,7 @@ int blr_test_expire_waits(int on);
 
 /* Diagnostic (no counterpart in the paper): set the sweep shapes, in the order
  * and meaning of blr_plan_tuning (n >= 11 values, a 12th sets the split
- * adjoint solve; the first two must be the plan's own), instead of the
+ * adjoint solve, a 13th the GEMM tiles; the first two must be the plan's own), instead of the
  * autotuner's choice, e.g. to reproduce a
  * configuration.  Every shape computes the same results bit for bit.
  * Synchronises the device.  BLR_EINVAL for a value out of range or a shape the

@@ -449,7 +449,7 @@ class Plan:
     TUNING_KEYS = ("wide_sweeps", "grad_kept", "adjoint_blocks_per_sm", "adjoint_reads_grad",
                    "incremental_form", "incremental_blocks_per_sm", "march_blocks_per_sm",
                    "march_chunk", "adjoint_march_chunk", "l2_persist_d4", "adjoint_two_step",
-                   "adjoint_split")
+                   "adjoint_split", "gemm_tiles")
 
     def tuning(self) -> dict:
         """The sweep shapes the autotuner chose (blr_plan_tuning)."""

@@ -521,10 +521,12 @@ extern "C" {
 
 int blr_plan_tuning(blr_plan_t P, int *vals, int n) {
     if (!P || !vals) return BLR_EINVAL;
-    const int v[12] = {P->sweep_wide ? 1 : 0, P->Gm ? 1 : 0, P->bal_adj, P->adj_useg,
+    int tiles = 0;
+    for (int st = 0; st < 5; ++st) tiles |= P->gemm_tile[st] << (3 * st);
+    const int v[13] = {P->sweep_wide ? 1 : 0, P->Gm ? 1 : 0, P->bal_adj, P->adj_useg,
                        P->inc_mode, P->bal_inc, P->bal_sweep, P->chunk, P->chunk_adj,
-                       P->l2_persist, P->adj2, P->adj_split};
-    for (int i = 0; i < n && i < 12; ++i) vals[i] = v[i];
+                       P->l2_persist, P->adj2, P->adj_split, tiles};
+    for (int i = 0; i < n && i < 13; ++i) vals[i] = v[i];
     return BLR_OK;
 }
 
@@ -545,6 +547,15 @@ int blr_plan_set_tuning(blr_plan_t P, const int *vals, int n) {
     const int split = n >= 12 ? vals[11] : P->adj_split;
     if ((split != 0 && split != 1) || (split && ((!P->lam_keep && !P->rho_keep) || !P->d4 || adj2)))
         return BLR_EINVAL;
+    int tiles[5];
+    for (int st = 0; st < 5; ++st) tiles[st] = P->gemm_tile[st];
+    if (n >= 13) {
+        if (vals[12] < 0 || vals[12] >= (1 << 15)) return BLR_EINVAL;
+        for (int st = 0; st < 5; ++st) {
+            tiles[st] = (vals[12] >> (3 * st)) & 7;
+            if (tiles[st] > SG_CANDS) return BLR_EINVAL;
+        }
+    }
     if (cudaDeviceSynchronize() != cudaSuccess) return BLR_ECUDA;
     P->bal_adj = bal_adj;
     P->adj_useg = useg;
@@ -556,6 +567,7 @@ int blr_plan_set_tuning(blr_plan_t P, const int *vals, int n) {
     P->l2_persist = l2;
     P->adj2 = adj2;
     P->adj_split = split;
+    for (int st = 0; st < 5; ++st) P->gemm_tile[st] = tiles[st];
     return BLR_OK;
 }
 

@@ -193,7 +193,7 @@ struct blr_plan {
     float *W1;          // [2*B1][N1]: row 2j = cos, row 2j+1 = -sin (2 pi k_j x / N1)
     float *T2c, *T2s;   // [B2][N2]
     float *W1t;         // FP32 project axis-1 stage: W1 transposed, [N1][2 B1] (or nullptr)
-    int gemm_tile[5];   // FP32 GEMM stages' register tile (0: modelled choice; dft_autotune)
+    int gemm_tile[5];   // FP32 GEMM stages' tile candidate (0: modelled choice; dft_autotune)
     float *T3e;         // FP32 expand axis-3 stage's B operand [2 B3][2 N3] (or nullptr)
     float *T2e, *T2p;   // FP32 axis-2 stages as real GEMMs, A operand [k][m] (or nullptr):
                         // expand [2 B2][2 N2] = [[C, S], [-S, C]]^T-ordered, project [2 N2][2 B2]
@@ -259,6 +259,7 @@ int plan_create(const blr_params *p, bool grad_cache, blr_plan **out);
 
 // dft.cu
 int dft_init_tables(blr_plan *P, cudaStream_t s);
+constexpr int SG_CANDS = 6;   // tile candidates of the FP32 GEMM stages (1 .. SG_CANDS)
 int dft_autotune(blr_plan *P, cudaStream_t s);
 // nc fields (3 per velocity; every step of a non-stationary plan) in one transform
 // (fused mixed-precision kernels or the FP32 GEMM stages; BLR_EINVAL otherwise).

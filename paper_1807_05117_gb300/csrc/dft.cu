@@ -180,11 +180,13 @@ size_t expand_axis3_smem(int B3) { return (size_t)(XR * B3 + B3 * XC) * sizeof(f
 // with C = T2c[k2][x2], S = T2s[k2][x2].  Stage A takes AK_MK (A = v~ as
 // [(c, k1, k2)][(k3, re|im)], B = T3e [(k3, re|im)][(re|im, x3)]) and writes
 // its rows to the planar layout (EPI 1).  Row-major A operands (AK_MK) are
-// fetched k-fastest, the others m-fastest, so that every fetch is coalesced.  Tiles of (16 TM) x (16 TN) outputs,
-// 256 threads as 16 x 16, each thread a TM x TN register tile (rows tm*4 + i + 64 h,
-// columns tn*4 + j + 64 h'); k in chunks of 16 through two shared-memory buffers,
+// fetched k-fastest, the others m-fastest, so that every fetch is coalesced.  NT
+// threads (256 or 128) as TR = NT / 16 rows x 16 columns, each thread a TM x TN
+// register tile (rows tm*4 + i + 4 TR h, columns tn*4 + j + 64 h'): tiles of
+// (TR TM) x (16 TN) outputs; k in chunks of 16 through two shared-memory buffers,
 // the next chunk's loads in flight (registers) during this chunk's products.  The
-// sum over k runs in order.  MODE 1 stores the clamped displacement and latches
+// sum over k runs in order, the same for every tile shape: all shapes give the
+// same results bit for bit.  MODE 1 stores the clamped displacement and latches
 // the CFL / NaN flags.
 enum { AK_KM = 0, AK_MK = 1, AK_E2 = 2, AK_P2 = 3 };
 
@@ -221,10 +223,14 @@ __device__ __forceinline__ float a_elem(const GemmArgs &p, int m, int k) {
 
 constexpr int GK = 16;   // k per chunk
 
-template <int AK, int MODE, int TM, int TN, int EPI = 0>
-__global__ void __launch_bounds__(256, 2)
+template <int AK, int MODE, int TM, int TN, int EPI = 0, int NT = 256>
+__global__ void __launch_bounds__(NT, 512 / NT)
 k_sgemm(GemmArgs p) {
-    constexpr int BM = 16 * TM, BN = 16 * TN, AP = BM + 4;   // padded A rows
+    constexpr int TR = NT / 16;                                // thread rows
+    constexpr int BM = TR * TM, BN = 16 * TN, AP = BM + 4;   // padded A rows
+    constexpr int NB4 = GK * BN / 4 / NT;                      // B float4 per thread and chunk
+    static_assert(NT == 256 || NT == 128, "16 x 16 or 8 x 16 threads");
+    static_assert(NB4 * NT * 4 == GK * BN, "B chunk split over the threads");
     constexpr bool KFAST = AK == AK_MK;
     __shared__ __align__(16) float As[2][GK][AP];
     __shared__ __align__(16) float Bs[2][GK][BN];
@@ -234,17 +240,17 @@ k_sgemm(GemmArgs p) {
     const float *Bz = p.B + blockIdx.z * p.strideB;
     const bool vec = (p.N & 3) == 0;
     float ra[TM];
-    float4 rb[TN / 4];
+    float4 rb[NB4];
     auto load = [&](int k0) {
 #pragma unroll
-        for (int i = 0; i < TM; ++i) {
-            const int e = tid + 256 * i;
+        for (int i = 0; i < TM; ++i) {   // BM x GK = NT TM elements
+            const int e = tid + NT * i;
             const int mm = KFAST ? e / GK : e % BM, kk = KFAST ? e % GK : e / BM;
             ra[i] = a_elem<AK>(p, m0 + mm, k0 + kk);
         }
 #pragma unroll
-        for (int i = 0; i < TN / 4; ++i) {
-            const int e = tid + 256 * i, kk = e / (BN / 4), k = k0 + kk;
+        for (int i = 0; i < NB4; ++i) {
+            const int e = tid + NT * i, kk = e / (BN / 4), k = k0 + kk;
             const long long n = n0 + 4 * (e % (BN / 4));
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (k < p.K) {
@@ -264,13 +270,13 @@ k_sgemm(GemmArgs p) {
     auto store = [&](int buf) {
 #pragma unroll
         for (int i = 0; i < TM; ++i) {
-            const int e = tid + 256 * i;
+            const int e = tid + NT * i;
             const int mm = KFAST ? e / GK : e % BM, kk = KFAST ? e % GK : e / BM;
             As[buf][kk][mm] = ra[i];
         }
 #pragma unroll
-        for (int i = 0; i < TN / 4; ++i) {
-            const int e = tid + 256 * i;
+        for (int i = 0; i < NB4; ++i) {
+            const int e = tid + NT * i;
             *reinterpret_cast<float4 *>(&Bs[buf][e / (BN / 4)][4 * (e % (BN / 4))]) = rb[i];
         }
     };
@@ -291,7 +297,7 @@ k_sgemm(GemmArgs p) {
             float a[TM], b[TN];
 #pragma unroll
             for (int h = 0; h < TM / 4; ++h) {
-                const float4 v = *reinterpret_cast<const float4 *>(&As[cur][kk][64 * h + tm * 4]);
+                const float4 v = *reinterpret_cast<const float4 *>(&As[cur][kk][4 * TR * h + tm * 4]);
                 a[4 * h] = v.x;
                 a[4 * h + 1] = v.y;
                 a[4 * h + 2] = v.z;
@@ -317,7 +323,7 @@ k_sgemm(GemmArgs p) {
     int flags = 0;
 #pragma unroll
     for (int r = 0; r < TM; ++r) {
-        const int m = m0 + 64 * (r / 4) + tm * 4 + (r & 3);
+        const int m = m0 + 4 * TR * (r / 4) + tm * 4 + (r & 3);
         if (m >= p.M) continue;
 #pragma unroll
         for (int h = 0; h < TN / 4; ++h) {
@@ -364,15 +370,20 @@ k_sgemm(GemmArgs p) {
     if (MODE == 1 && flags) atomicOr(p.status, flags);
 }
 
-// Launch k_sgemm with the largest register tile that still gives every SM two
-// blocks (or the smallest tile when even that does not).
-constexpr int SG_CANDS = 4;
+// Launch k_sgemm with the register tile and thread count of candidate `forced`
+// (1 .. SG_CANDS, chosen per plan by timing), else the modelled choice among the
+// 256-thread tiles: the largest that still gives every SM two blocks (or the
+// smallest when even that does not).  The 128-thread tiles (32 rows) serve the
+// stages whose 64-row tiles leave most SMs idle.
 
 template <int AK, int MODE, int EPI = 0>
 int launch_sgemm(const GemmArgs &p, int batch, int sms, cudaStream_t s, int forced = 0) {
+    // candidates: {TM, TN, threads}
+    const int tms[SG_CANDS] = {8, 8, 4, 4, 4, 4}, tns[SG_CANDS] = {8, 4, 8, 4, 4, 8};
+    const int nts[SG_CANDS] = {256, 256, 256, 256, 128, 128};
     // modelled time: waves of resident blocks x a block's padded tile over the
     // register tile's relative FMA rate (smem operand traffic per FMA)
-    const int tms[4] = {8, 8, 4, 4}, tns[4] = {8, 4, 8, 4}, res[4] = {2, 2, 2, 3};
+    const int res[4] = {2, 2, 2, 3};
     const double rate[4] = {1.0, 0.75, 0.75, 0.55};
     int pick = 0;
     double best = 1e300;
@@ -388,13 +399,17 @@ int launch_sgemm(const GemmArgs &p, int batch, int sms, cudaStream_t s, int forc
         }
     }
     if (forced >= 1 && forced <= SG_CANDS) pick = forced - 1;
-    const int TMc = tms[pick], TNc = tns[pick];
-    const dim3 grid((unsigned)ceil_div_ll(p.N, 16LL * TNc), (unsigned)ceil_div_ll(p.M, 16LL * TMc),
+    const int TMc = tms[pick], TNc = tns[pick], NTc = nts[pick];
+    const dim3 grid((unsigned)ceil_div_ll(p.N, 16LL * TNc), (unsigned)ceil_div_ll(p.M, (NTc / 16LL) * TMc),
                     (unsigned)batch);
-    if (TMc == 8 && TNc == 8) launch_pdl(k_sgemm<AK, MODE, 8, 8, EPI>, grid, dim3(256), 0, s, p);
-    else if (TMc == 8) launch_pdl(k_sgemm<AK, MODE, 8, 4, EPI>, grid, dim3(256), 0, s, p);
-    else if (TNc == 8) launch_pdl(k_sgemm<AK, MODE, 4, 8, EPI>, grid, dim3(256), 0, s, p);
-    else launch_pdl(k_sgemm<AK, MODE, 4, 4, EPI>, grid, dim3(256), 0, s, p);
+    switch (pick) {
+        case 0: launch_pdl(k_sgemm<AK, MODE, 8, 8, EPI>, grid, dim3(256), 0, s, p); break;
+        case 1: launch_pdl(k_sgemm<AK, MODE, 8, 4, EPI>, grid, dim3(256), 0, s, p); break;
+        case 2: launch_pdl(k_sgemm<AK, MODE, 4, 8, EPI>, grid, dim3(256), 0, s, p); break;
+        case 3: launch_pdl(k_sgemm<AK, MODE, 4, 4, EPI>, grid, dim3(256), 0, s, p); break;
+        case 4: launch_pdl(k_sgemm<AK, MODE, 4, 4, EPI, 128>, grid, dim3(128), 0, s, p); break;
+        default: launch_pdl(k_sgemm<AK, MODE, 4, 8, EPI, 128>, grid, dim3(128), 0, s, p); break;
+    }
     BLR_CK_LAUNCH();
     return BLR_OK;
 }
