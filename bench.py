@@ -893,7 +893,7 @@ def measure_differentiation_form(dev, flush, stream, reps=3):
     out = {"workload": ("256^3 phantom pair, band 32^3, 20 time steps, state checkpointed every "
                         "4 steps (recomputed per segment in backward), FP32; one step = "
                         "registration_energy forward + backward"),
-           "gradients_per_s": 1000.0 / ms, "ms_per_gradient": ms, "energy": float(E),
+           "gradients_per_s": 1000.0 / ms, "ms_per_gradient": ms, "energy": float(E.detach()),
            "grad_norm": float(torch.linalg.vector_norm(v.grad)), "status": status,
            "roofline": {"kernel": "forward + checkpointed backward (stepwise algorithmic bytes)",
                         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
